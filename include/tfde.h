@@ -1,0 +1,191 @@
+/*
+ * tfde.h -- C ABI of the GB300 (sm_103a) solver library for the Crank-Nicolson
+ * finite-volume discretisation of the 3-D conservative two-sided
+ * Riemann-Liouville space-fractional diffusion equation, with the DST-I
+ * (tau) preconditioned PCG / PGMRES solvers of Qu, Lei, Hon and Huang,
+ * "Optimal preconditioning techniques for finite volume approximation of
+ * three-dimensional conservative space-fractional diffusion equations".
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - A grid function is n1*n2*n3 doubles in the paper's lexicographic order
+ *   (Sec. 2, definition of u^m): x fastest, then y, then z, i.e. element
+ *   (i, j, k) (0-based) sits at i + n1*(j + n2*k).
+ * - Vector arguments are DEVICE pointers (cudaMalloc / torch CUDA storage on the
+ *   current device), owned by the caller, 8-byte aligned; they must not alias
+ *   unless an argument says so.  Host pointers are rejected only when the CUDA
+ *   runtime reports them as host memory (TFDE_EINVAL).
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   All work is enqueued on it.  Solver entry points synchronise the stream
+ *   for their convergence tests; matvec / precond / source do not.
+ * - A tfde_problem owns every device buffer it needs (operators, eigenvalue
+ *   arrays, Krylov workspace).  It is created by tfde_assemble and released by
+ *   tfde_destroy.  One problem must not be used from two host threads or two
+ *   streams at once (its workspace is shared by all its calls).
+ * - Every function returns a tfde_status; nothing aborts or throws across the
+ *   ABI.  tfde_last_error() returns a thread-local message for the last
+ *   failure on the calling thread.  Asynchronous kernel faults surface as
+ *   TFDE_ECUDA at the next synchronising call.
+ */
+#ifndef TFDE_H
+#define TFDE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TFDE_OK = 0,
+    TFDE_EINVAL = 1,        /* invalid argument (sizes, orders, pointers)        */
+    TFDE_ENOMEM = 2,        /* device or host allocation failed                  */
+    TFDE_ECUDA = 3,         /* CUDA runtime / driver error                       */
+    TFDE_ENOCONV = 4,       /* maxit reached before the tolerance                */
+    TFDE_EBREAKDOWN = 5,    /* Krylov breakdown (p.Ap <= 0, zero Arnoldi norm)   */
+    TFDE_ENAN = 6,          /* NaN or Inf in a residual or inner product         */
+    TFDE_ETIMEOUT = 7,      /* a bounded device-side wait ran out                */
+    TFDE_EUNSUPPORTED = 8   /* valid request this build does not implement       */
+} tfde_status;
+
+typedef enum {
+    /* every operator, transform and Krylov vector in native FP64 */
+    TFDE_FP64 = 0,
+    /* inner Krylov solves on FP32 vectors with split-BF16 tcgen05 contractions
+       (Toeplitz matvec: 3 BF16 products; DST: 2), wrapped in FP64 iterative
+       refinement whose residual uses the exact-integer slice (Ozaki) tcgen05
+       contraction; the stopping test is always the true FP64 residual */
+    TFDE_MIXED = 1
+} tfde_precision;
+
+/* One problem (Sec. 1 and Sec. 2).  Axis a = 0, 1, 2 is x, y, z. */
+typedef struct {
+    int n[3];          /* interior grid points per axis, n_a >= 1; h_a = (hi_a - lo_a)/(n_a + 1) */
+    double lo[3];      /* Omega = prod_a (lo_a, hi_a), lo_a < hi_a                  */
+    double hi[3];
+    double delta[3];   /* alpha, beta, gamma in (0, 1); the derivative order is 2 - delta */
+    double kp[3];      /* k_{a,+} > 0                                               */
+    double km[3];      /* k_{a,-} > 0                                               */
+    double dt;         /* Crank-Nicolson step Delta t > 0                           */
+} tfde_params;
+
+/* Filled by the solver entry points (may be NULL). */
+typedef struct {
+    int iters;          /* PCG iterations / GMRES inner (Arnoldi) steps, all sweeps  */
+    int restarts;       /* GMRES cycles started                                      */
+    int refine_sweeps;  /* FP64 refinement sweeps (TFDE_MIXED), else 0               */
+    int fallback;       /* 1 if a mixed solve fell back to FP64 inner solves         */
+    double relres;      /* final true relative residual ||b - A x||_2 / ||b||_2     */
+    double relres0;     /* initial true relative residual                            */
+    float ms;           /* wall time of the call, milliseconds                       */
+} tfde_info;
+
+typedef struct tfde_problem tfde_problem;
+
+/* Operator selectors for tfde_matvec. */
+#define TFDE_OP_A    0   /* y = A x, A the CN-FV matrix of Eq. (linear_sys)          */
+#define TFDE_OP_RHS  1   /* y = (A_N - eta-terms) x = (2 A_N - A) x, the RHS operator */
+#define TFDE_OP_FAST 2   /* OR-able: for TFDE_MIXED problems use the inner (split-BF16,
+                            FP32-accumulated) arithmetic instead of the accurate one */
+
+/*
+ * tfde_assemble -- build a problem (Sec. 2, Eq. (coef_expression) to Eq. (linear_sys);
+ * Sec. 3, Eq. (pre_definition) and Eq. (diag_tau_pre)).
+ *   Computes h_a, eta_a = dt / (2 Gamma(delta_a + 1) h_a^{2 - delta_a}), the
+ *   generators q_k (k = 0..n_a) without cancellation, the dense per-axis
+ *   operators eta_a B_a and the DST-I matrices S_{n_a}, the tau eigenvalues
+ *   lambda_k = q_1 + (q_0+q_2) cos t_k + sum_{j=2}^{n-1} q_{j+1} cos(j t_k)
+ *   and the mass eigenvalues (6 + 2 cos t_k)/8, and allocates the workspace.
+ *   Errors: TFDE_EINVAL for n_a < 1, delta outside (0,1), k <= 0, dt <= 0,
+ *   lo >= hi, NULL pointers; TFDE_EUNSUPPORTED when TFDE_MIXED is requested
+ *   for an n_a this build's tensor-core tiles do not cover (n_a > 256);
+ *   TFDE_ENOMEM / TFDE_ECUDA.  *out is NULL on failure.  Synchronises `stream`.
+ */
+int tfde_assemble(const tfde_params* params, int precision, void* stream, tfde_problem** out);
+
+/* Release every resource of a problem (NULL is a no-op).  Synchronises the device. */
+int tfde_destroy(tfde_problem* prob);
+
+/*
+ * tfde_matvec -- y = A x (op TFDE_OP_A) or y = (2 A_N - A) x (op TFDE_OP_RHS),
+ * Eq. (linear_sys):  A = A_N + eta_a A3(x)A2(x)B1 + eta_b A3(x)B2(x)A1 + eta_c B3(x)A2(x)A1.
+ *   x, y: device, n1*n2*n3 doubles, must not alias.  Asynchronous.
+ */
+int tfde_matvec(const tfde_problem* prob, int op, const double* x, double* y, void* stream);
+
+/*
+ * tfde_precond -- z = P^{-1} r = S_N Lambda^{-1} S_N r, Eq. (diag_tau_pre).
+ *   r, z: device, n1*n2*n3 doubles; z may alias r.  Asynchronous.
+ */
+int tfde_precond(const tfde_problem* prob, const double* r, double* z, void* stream);
+
+/*
+ * tfde_pcg -- solve A x = b by tau-preconditioned CG (Sec. 3.1; requires
+ * k_{a,+} = k_{a,-} on every axis, else TFDE_EINVAL).
+ *   b: device input; x: device, initial guess on entry, solution on exit.
+ *   Stops when ||b - A x||_2 <= tol ||b||_2 for the TRUE residual (the
+ *   recursive residual only triggers the check).  maxit bounds the iterations
+ *   (all refinement sweeps together).  Returns TFDE_ENOCONV if maxit is hit,
+ *   TFDE_EBREAKDOWN if p.Ap <= 0, TFDE_ENAN on a non-finite residual.
+ */
+int tfde_pcg(const tfde_problem* prob, const double* b, double* x, double tol, int maxit,
+             tfde_info* info, void* stream);
+
+/*
+ * tfde_pgmres -- solve A x = b by restarted GMRES(restart) on the left
+ * preconditioned system P^{-1} A x = P^{-1} b (Sec. 3.2, Eq. (one_side_system)).
+ *   Arnoldi with classical Gram-Schmidt and one re-orthogonalisation; Givens
+ *   rotations in FP64 on the host.  Converged when the TRUE relative residual
+ *   ||b - A x|| / ||b|| <= tol.  1 <= restart <= 64.  Errors as tfde_pcg.
+ */
+int tfde_pgmres(const tfde_problem* prob, const double* b, double* x, int restart, double tol,
+                int maxit, tfde_info* info, void* stream);
+
+/*
+ * tfde_cn_step -- one Crank-Nicolson step u^{m-1} -> u^m (Sec. 2, Eq. (CN) and
+ * Eq. (linear_sys)):  b = (2 A_N - A) u^{m-1} + dt F^{m-1/2};  solve A u^m = b
+ * by PCG when k_+ = k_- on every axis, else by PGMRES(20).
+ *   u_prev: device input.  F_half: device cell averages of f at t_{m-1/2}, or
+ *   NULL for f = 0.  x0: device initial guess, or NULL for u_prev.  u_next:
+ *   device output; may alias x0 but not u_prev or F_half.  maxit = 10000.
+ */
+int tfde_cn_step(const tfde_problem* prob, const double* u_prev, const double* F_half,
+                 const double* x0, double* u_next, double tol, tfde_info* info, void* stream);
+
+/*
+ * tfde_source_example2 -- cell averages F_{ijk} (Sec. 2, definition of F^{m-1/2})
+ * of the manufactured source of Sec. 4, Example 2, on Omega = (0,1)^3:
+ *   f = cP P(x)P(y)P(z) + cS [S_a(x)P(y)P(z) + P(x)S_b(y)P(z) + P(x)P(y)S_c(z)],
+ *   P(x) = x^2 (1-x)^2,
+ *   S_d(x) = sum_{k=0}^2 (-1)^{2-k} C(2,k) Gamma(5-k)/Gamma(3-k+d) [k_+ x^{2-k+d} + k_- (1-x)^{2-k+d}].
+ *   For u = phi(t) P P P:  cP = phi'(t), cS = -phi(t).  Integrals are exact.
+ *   Requires lo = 0, hi = 1 on every axis (else TFDE_EINVAL).  F: device output.
+ */
+int tfde_source_example2(const tfde_problem* prob, double cP, double cS, double* F, void* stream);
+
+/*
+ * tfde_coefficients -- host copies of the assembled 1-D data of one axis:
+ *   q (n_a + 1 doubles, Eq. (coef_expression)), tau eigenvalues (n_a doubles,
+ *   Lemma 1D_tau_SPD) and eta_a.  Any output may be NULL.  Synchronous, no GPU work.
+ */
+int tfde_coefficients(const tfde_problem* prob, int axis, double* q, double* lam_tau, double* eta);
+
+/*
+ * tfde_host_coefficients -- the same 1-D data as tfde_coefficients computed on
+ * the host from parameters alone (no problem, no GPU): q (n_a + 1), tau
+ * eigenvalues (n_a), mass eigenvalues (6 + 2 cos(k pi/(n_a+1)))/8 (n_a) and
+ * eta_a.  Outputs may be NULL.  TFDE_EINVAL for invalid parameters.
+ */
+int tfde_host_coefficients(const tfde_params* params, int axis, double* q, double* lam_tau, double* lam_mass,
+                           double* eta);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* tfde_last_error(void);
+
+/* Library version string. */
+const char* tfde_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TFDE_H */

@@ -1,0 +1,161 @@
+// extern "C" entry points of libtfde (declared and documented in include/tfde.h).
+#include <cmath>
+#include <string>
+
+#include "tfde_internal.h"
+
+namespace tfde {
+const char* last_error_text();
+int assemble_problem(const tfde_params*, int, cudaStream_t, tfde_problem**);
+int destroy_problem(tfde_problem*);
+int host_coefficients(const tfde_params*, int, double*, double*, double*, double*);
+int pcg64(const tfde_problem*, const double*, double*, double, int, tfde_info*, cudaStream_t);
+int pgmres64(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t);
+int cn_step64(tfde_problem*, const double*, const double*, const double*, double*, double, tfde_info*,
+              cudaStream_t);
+// mixed path (tfde_mixed.cu)
+int mixed_apply_A(const tfde_problem*, int, const double*, double*, cudaStream_t);
+int mixed_apply_Pinv(const tfde_problem*, const double*, double*, cudaStream_t);
+int mixed_pcg(tfde_problem*, const double*, double*, double, int, tfde_info*, cudaStream_t);
+int mixed_pgmres(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t);
+int mixed_cn_step(tfde_problem*, const double*, const double*, const double*, double*, double, tfde_info*,
+                  cudaStream_t);
+}  // namespace tfde
+
+using namespace tfde;
+
+namespace {
+
+// Rejects NULL and pointers the runtime reports as plain host memory.
+int check_dev(const void* p, const char* name) {
+    if (!p) return set_error(TFDE_EINVAL, std::string(name) + " is NULL");
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(TFDE_EINVAL, std::string(name) + " is not a CUDA pointer");
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return set_error(TFDE_EINVAL, std::string(name) + " is not device memory");
+    return TFDE_OK;
+}
+
+int check_tol(double tol) {
+    if (!(tol > 0.0) || !std::isfinite(tol)) return set_error(TFDE_EINVAL, "tol must be finite and > 0");
+    return TFDE_OK;
+}
+
+int pre_call() {
+    // surface a pending asynchronous fault from earlier work before starting
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return set_error(TFDE_ECUDA, std::string("pending CUDA error: ") + cudaGetErrorString(e));
+    return TFDE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tfde_assemble(const tfde_params* params, int precision, void* stream, tfde_problem** out) {
+    if (!params || !out) return set_error(TFDE_EINVAL, "NULL argument");
+    *out = nullptr;
+    int st = pre_call();
+    if (st) return st;
+    return assemble_problem(params, precision, (cudaStream_t)stream, out);
+}
+
+int tfde_destroy(tfde_problem* prob) { return destroy_problem(prob); }
+
+int tfde_matvec(const tfde_problem* prob, int op, const double* x, double* y, void* stream) {
+    if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
+    int st;
+    if ((st = pre_call()) || (st = check_dev(x, "x")) || (st = check_dev(y, "y"))) return st;
+    if (x == y) return set_error(TFDE_EINVAL, "x and y must not alias");
+    if (op < 0 || op > 3) return set_error(TFDE_EINVAL, "unknown op");
+    if (prob->prec == TFDE_MIXED) return mixed_apply_A(prob, op, x, y, (cudaStream_t)stream);
+    return apply_A64(prob, op & 1, x, y, (cudaStream_t)stream);
+}
+
+int tfde_precond(const tfde_problem* prob, const double* r, double* z, void* stream) {
+    if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
+    int st;
+    if ((st = pre_call()) || (st = check_dev(r, "r")) || (st = check_dev(z, "z"))) return st;
+    if (prob->prec == TFDE_MIXED) return mixed_apply_Pinv(prob, r, z, (cudaStream_t)stream);
+    return apply_Pinv64(prob, r, z, (cudaStream_t)stream);
+}
+
+int tfde_pcg(const tfde_problem* prob, const double* b, double* x, double tol, int maxit, tfde_info* info,
+             void* stream) {
+    if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
+    int st;
+    if ((st = pre_call()) || (st = check_dev(b, "b")) || (st = check_dev(x, "x")) || (st = check_tol(tol)))
+        return st;
+    if (b == x) return set_error(TFDE_EINVAL, "b and x must not alias");
+    if (!prob->symmetric) return set_error(TFDE_EINVAL, "PCG needs k_+ = k_- on every axis");
+    if (maxit < 0) return set_error(TFDE_EINVAL, "maxit must be >= 0");
+    tfde_problem* P = const_cast<tfde_problem*>(prob);
+    if (prob->prec == TFDE_MIXED) return mixed_pcg(P, b, x, tol, maxit, info, (cudaStream_t)stream);
+    return pcg64(prob, b, x, tol, maxit, info, (cudaStream_t)stream);
+}
+
+int tfde_pgmres(const tfde_problem* prob, const double* b, double* x, int restart, double tol, int maxit,
+                tfde_info* info, void* stream) {
+    if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
+    int st;
+    if ((st = pre_call()) || (st = check_dev(b, "b")) || (st = check_dev(x, "x")) || (st = check_tol(tol)))
+        return st;
+    if (b == x) return set_error(TFDE_EINVAL, "b and x must not alias");
+    if (restart < 1 || restart > 64) return set_error(TFDE_EINVAL, "restart must lie in [1, 64]");
+    if (maxit < 0) return set_error(TFDE_EINVAL, "maxit must be >= 0");
+    tfde_problem* P = const_cast<tfde_problem*>(prob);
+    if (prob->prec == TFDE_MIXED) return mixed_pgmres(P, b, x, restart, tol, maxit, info, (cudaStream_t)stream);
+    return pgmres64(P, b, x, restart, tol, maxit, info, (cudaStream_t)stream);
+}
+
+int tfde_cn_step(const tfde_problem* prob, const double* u_prev, const double* F_half, const double* x0,
+                 double* u_next, double tol, tfde_info* info, void* stream) {
+    if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
+    int st;
+    if ((st = pre_call()) || (st = check_dev(u_prev, "u_prev")) || (st = check_dev(u_next, "u_next")) ||
+        (st = check_tol(tol)))
+        return st;
+    if (F_half && (st = check_dev(F_half, "F_half"))) return st;
+    if (x0 && (st = check_dev(x0, "x0"))) return st;
+    if (u_next == u_prev || u_next == F_half) return set_error(TFDE_EINVAL, "u_next aliases an input");
+    tfde_problem* P = const_cast<tfde_problem*>(prob);
+    if (prob->prec == TFDE_MIXED)
+        return mixed_cn_step(P, u_prev, F_half, x0, u_next, tol, info, (cudaStream_t)stream);
+    return cn_step64(P, u_prev, F_half, x0, u_next, tol, info, (cudaStream_t)stream);
+}
+
+int tfde_source_example2(const tfde_problem* prob, double cP, double cS, double* F, void* stream) {
+    if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
+    int st;
+    if ((st = pre_call()) || (st = check_dev(F, "F"))) return st;
+    if (!prob->have_src) return set_error(TFDE_EINVAL, "Example 2 source needs Omega = (0,1)^3");
+    launch_source_assemble_f64(prob->src1d, prob->n, cP, cS, F, (cudaStream_t)stream);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? TFDE_OK : set_error(TFDE_ECUDA, cudaGetErrorString(e));
+}
+
+int tfde_coefficients(const tfde_problem* prob, int axis, double* q, double* lam_tau, double* eta) {
+    if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
+    if (axis < 0 || axis > 2) return set_error(TFDE_EINVAL, "axis must be 0, 1 or 2");
+    if (q)
+        for (size_t k = 0; k < prob->q[axis].size(); ++k) q[k] = prob->q[axis][k];
+    if (lam_tau)
+        for (size_t k = 0; k < prob->lam_tau[axis].size(); ++k) lam_tau[k] = prob->lam_tau[axis][k];
+    if (eta) *eta = prob->eta[axis];
+    return TFDE_OK;
+}
+
+int tfde_host_coefficients(const tfde_params* params, int axis, double* q, double* lam_tau, double* lam_mass,
+                           double* eta) {
+    if (!params) return set_error(TFDE_EINVAL, "NULL params");
+    return host_coefficients(params, axis, q, lam_tau, lam_mass, eta);
+}
+
+const char* tfde_last_error(void) { return last_error_text(); }
+
+const char* tfde_version(void) { return "tfde-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

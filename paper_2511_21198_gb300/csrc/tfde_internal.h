@@ -1,0 +1,115 @@
+// Internal declarations shared by the translation units of libtfde.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tfde.h"
+
+namespace tfde {
+
+// View of a 3-D grid function (x fastest) as a set of 1-D lines along one
+// axis: element c of line l sits at  line_offset(l) + c * stride.
+//   line_offset(l) = (l % l_in) * s_in + (l / l_in) * s_out
+struct AxisView {
+    int n;             // length along the axis (= rows and columns of the axis operator)
+    long long stride;  // element stride along the axis
+    long long lines;   // number of lines (product of the other two extents)
+    long long l_in;    // lines per contiguous run
+    long long s_in;    // offset step between consecutive lines inside a run
+    long long s_out;   // offset step between runs
+};
+
+inline AxisView axis_view(const int n[3], int axis) {
+    AxisView v{};
+    const long long n1 = n[0], n2 = n[1], n3 = n[2];
+    if (axis == 0) {
+        v.n = n[0]; v.stride = 1; v.lines = n2 * n3; v.l_in = n2 * n3; v.s_in = n1; v.s_out = 0;
+    } else if (axis == 1) {
+        v.n = n[1]; v.stride = n1; v.lines = n1 * n3; v.l_in = n1; v.s_in = 1; v.s_out = n1 * n2;
+    } else {
+        v.n = n[2]; v.stride = n1 * n2; v.lines = n1 * n2; v.l_in = n1 * n2; v.s_in = 1; v.s_out = 0;
+    }
+    return v;
+}
+
+// Thread-local error text; set_error returns the status for convenience.
+int set_error(int status, const std::string& msg);
+
+// ---------------------------------------------------------------- FP64 kernels
+// Y = alpha * (Mat along axis) X + beta * (tridiag(1,6,1)/8 along axis) Z  (Z may be null)
+void launch_axis_gemm_f64(const double* Mat, const double* X, double* Y, const AxisView& v,
+                          double alpha, const double* Z, double beta, cudaStream_t s);
+// Y = beta * (tridiag(1,6,1)/8 along axis) X + gamma * W   (W may be null)
+void launch_axis_stencil_f64(const double* X, double* Y, const AxisView& v, double beta,
+                             const double* W, double gamma, cudaStream_t s);
+// y[i] = x[i] / Lambda(i,j,k), Lambda from the 1-D arrays (Eq. (diag_tau_pre))
+// lam layout: [mass_x | mass_y | mass_z | tau_x | tau_y | tau_z], lengths n1,n2,n3,n1,n2,n3
+void launch_lambda_scale_f64(const double* x, double* y, const double* lam, const int n[3],
+                             const double c[3], int invert, cudaStream_t s);
+// y = a x + b y
+void launch_axpby_f64(size_t N, double a, const double* x, double b, double* y, cudaStream_t s);
+// z = a x + b y
+void launch_axpbypz_f64(size_t N, double a, const double* x, double b, const double* y, double* z,
+                        cudaStream_t s);
+// x += alpha p ; r -= alpha q ; partial sums of r.r into part[0..nblk)
+void launch_cg_update_f64(size_t N, double alpha, const double* p, const double* q, double* x,
+                          double* r, double* part, int nblk, cudaStream_t s);
+// m dot products <V_j, w>, j < m, V_j = V + j*ldv; partials part[j*nblk + b]
+void launch_multidot_f64(size_t N, int m, const double* V, size_t ldv, const double* w,
+                         double* part, int nblk, cudaStream_t s);
+// w -= sum_j h[j] V_j   (h on device)
+void launch_multiaxpy_f64(size_t N, int m, const double* V, size_t ldv, const double* h, double* w,
+                          cudaStream_t s);
+// deterministic second stage: out[j] = sum_b part[j*nblk + b], j < m
+void launch_reduce_finish(const double* part, int nblk, int m, double* out, cudaStream_t s);
+int reduction_blocks(size_t N);
+// F = cP PPP + cS (SPP + PSP + PPS) from 1-D arrays [Px|Py|Pz|Sx|Sy|Sz]
+void launch_source_assemble_f64(const double* oned, const int n[3], double cP, double cS, double* F,
+                                cudaStream_t s);
+
+}  // namespace tfde
+
+// --------------------------------------------------------------------- problem
+struct tfde_problem {
+    tfde_params p{};
+    int prec = TFDE_FP64;
+    int n[3]{};
+    size_t N = 0;
+    double h[3]{}, eta[3]{}, csum[3]{};
+    bool symmetric = false;
+    std::vector<double> q[3], lam_tau[3], lam_mass[3];
+    std::vector<double> srcP[3], srcS[3];  // 1-D exact cell averages of P and S_delta (if lo=0, hi=1)
+    bool have_src = false;
+
+    // device operators (row-major n_a x n_a, [out][in])
+    double* Ghat[2] = {nullptr, nullptr};  // x-axis: M1 + eta1 B1 (op A), M1 - eta1 B1 (op RHS)
+    double* G[3] = {nullptr, nullptr, nullptr};  // eta_a B_a
+    double* S[3] = {nullptr, nullptr, nullptr};  // DST-I matrices
+    double* lam = nullptr;                      // [mass x|y|z | tau x|y|z]
+    double* src1d = nullptr;                    // [Px|Py|Pz|Sx|Sy|Sz]
+
+    // FP64 workspace: n-vectors
+    enum { W_A, W_W, W_C, W_E, W_R, W_Z, W_P, W_Q, W_B, W_T, NW };
+    double* w[NW] = {};
+    double* V = nullptr;   // GMRES basis, (gmres_cap + 1) vectors
+    int gmres_cap = 0;
+    double* red = nullptr; // reduction partials (64 * nblk)
+    double* red_out = nullptr;  // device results (64)
+    double* red_host = nullptr; // pinned host mirror (64)
+    int nblk = 0;
+
+    void* mixed = nullptr;  // mixed-precision state (tensor-core path)
+};
+
+namespace tfde {
+// solver internals (tfde_solvers.cu)
+int apply_A64(const tfde_problem* P, int op, const double* x, double* y, cudaStream_t s);
+int apply_Pinv64(const tfde_problem* P, const double* r, double* z, cudaStream_t s);
+int dots64(const tfde_problem* P, int m, const double* V, size_t ldv, const double* w, double* out,
+           cudaStream_t s);
+int ensure_gmres_basis(tfde_problem* P, int restart);
+}  // namespace tfde

@@ -1,0 +1,173 @@
+// FP32 / split-BF16 vector kernels of the mixed-precision inner solves.
+// A split-BF16 plane pair (hi, lo) stores v ~= hi + lo with
+// hi = bf16(v), lo = bf16(v - hi): the B operand format of the tensor-core
+// contraction.  Inner products accumulate per thread in compensated FP32 and
+// across threads in FP64 (deterministic two-stage reduction).
+#include <cuda_bf16.h>
+
+#include "tfde_internal.h"
+#include "tfde_mixed.h"
+
+namespace tfde {
+namespace {
+
+constexpr int kT = 256;
+
+__device__ __forceinline__ void split(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// Kahan-compensated FP32 accumulation.
+struct KSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+__device__ __forceinline__ double block_sum64(double v) {
+    __shared__ double sh[kT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kT / 32; ++w) t += sh[w];
+    return t;
+}
+
+__device__ __forceinline__ void chunk(long long N, long long& lo, long long& hi) {
+    const long long per = (N + gridDim.x - 1) / gridDim.x;
+    lo = (long long)blockIdx.x * per;
+    hi = lo + per < N ? lo + per : N;
+}
+
+__global__ __launch_bounds__(kT) void dot32_kernel(long long N, const float* __restrict__ a,
+                                                   const float* __restrict__ b, double* __restrict__ part) {
+    long long lo, hi;
+    chunk(N, lo, hi);
+    KSum k;
+    for (long long i = lo + threadIdx.x; i < hi; i += kT) k.add(a[i] * b[i]);
+    const double t = block_sum64((double)k.s - (double)k.c);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// x += alpha p ; r -= alpha q ; (rh, rl) = split(r) ; partial r.r
+__global__ __launch_bounds__(kT) void cg_update32_kernel(long long N, const double* __restrict__ coef,
+                                                         const float* __restrict__ p, const float* __restrict__ q,
+                                                         float* __restrict__ x, float* __restrict__ r,
+                                                         __nv_bfloat16* __restrict__ rh,
+                                                         __nv_bfloat16* __restrict__ rl, double* __restrict__ part) {
+    const float alpha = (float)coef[0];
+    long long lo, hi;
+    chunk(N, lo, hi);
+    KSum k;
+    for (long long i = lo + threadIdx.x; i < hi; i += kT) {
+        x[i] = fmaf(alpha, p[i], x[i]);
+        const float ri = fmaf(-alpha, q[i], r[i]);
+        r[i] = ri;
+        split(ri, rh[i], rl[i]);
+        k.add(ri * ri);
+    }
+    const double t = block_sum64((double)k.s - (double)k.c);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// p = z + beta p ; (ph, pl) = split(p)
+__global__ void xpay32_kernel(long long N, const double* __restrict__ coef, const float* __restrict__ z,
+                              float* __restrict__ p, __nv_bfloat16* __restrict__ ph, __nv_bfloat16* __restrict__ pl) {
+    const float beta = (float)coef[0];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const float v = fmaf(beta, p[i], z[i]);
+        p[i] = v;
+        split(v, ph[i], pl[i]);
+    }
+}
+
+// r32 = r64 * s ; (rh, rl) = split(r32) ; x32 = 0
+__global__ void scale64to32_kernel(long long N, const double* __restrict__ r64, double s, float* __restrict__ r32,
+                                   __nv_bfloat16* __restrict__ rh, __nv_bfloat16* __restrict__ rl,
+                                   float* __restrict__ x32) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const float v = (float)(r64[i] * s);
+        r32[i] = v;
+        split(v, rh[i], rl[i]);
+        if (x32) x32[i] = 0.f;
+    }
+}
+
+// (h, l) = split(v)
+__global__ void split32_kernel(long long N, const float* __restrict__ v, __nv_bfloat16* __restrict__ h,
+                               __nv_bfloat16* __restrict__ l) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        split(v[i], h[i], l[i]);
+}
+
+// (h, l) = split((float) v64 * s)
+__global__ void split64_kernel(long long N, const double* __restrict__ v, double s, __nv_bfloat16* __restrict__ h,
+                               __nv_bfloat16* __restrict__ l) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        split((float)(v[i] * s), h[i], l[i]);
+}
+
+// x64 += s * d32
+__global__ void add32to64_kernel(long long N, double s, const float* __restrict__ d, double* __restrict__ x) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        x[i] += s * (double)d[i];
+}
+
+// y64 = (double) v32 * s
+__global__ void widen32_kernel(long long N, const float* __restrict__ v, double s, double* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (double)v[i] * s;
+}
+
+// coef[0] = num[0] / den[0]  (device-side scalar, no host round trip)
+__global__ void ratio_kernel(const double* num, const double* den, double* coef) { coef[0] = num[0] / den[0]; }
+
+inline int grid_for(long long N) {
+    long long g = (N + kT - 1) / kT;
+    if (g > 152LL * 16) g = 152LL * 16;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+void launch_dot32(size_t N, const float* a, const float* b, double* part, int nblk, cudaStream_t s) {
+    dot32_kernel<<<nblk, kT, 0, s>>>((long long)N, a, b, part);
+}
+void launch_cg_update32(size_t N, const double* coef, const float* p, const float* q, float* x, float* r,
+                        __nv_bfloat16* rh, __nv_bfloat16* rl, double* part, int nblk, cudaStream_t s) {
+    cg_update32_kernel<<<nblk, kT, 0, s>>>((long long)N, coef, p, q, x, r, rh, rl, part);
+}
+void launch_xpay32(size_t N, const double* coef, const float* z, float* p, __nv_bfloat16* ph, __nv_bfloat16* pl,
+                   cudaStream_t s) {
+    xpay32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, coef, z, p, ph, pl);
+}
+void launch_scale64to32(size_t N, const double* r64, double sc, float* r32, __nv_bfloat16* rh, __nv_bfloat16* rl,
+                        float* x32, cudaStream_t s) {
+    scale64to32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, r64, sc, r32, rh, rl, x32);
+}
+void launch_split32(size_t N, const float* v, __nv_bfloat16* h, __nv_bfloat16* l, cudaStream_t s) {
+    split32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, v, h, l);
+}
+void launch_split64(size_t N, const double* v, double sc, __nv_bfloat16* h, __nv_bfloat16* l, cudaStream_t s) {
+    split64_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, v, sc, h, l);
+}
+void launch_add32to64(size_t N, double sc, const float* d, double* x, cudaStream_t s) {
+    add32to64_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, sc, d, x);
+}
+void launch_widen32(size_t N, const float* v, double sc, double* y, cudaStream_t s) {
+    widen32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, v, sc, y);
+}
+void launch_ratio(const double* num, const double* den, double* coef, cudaStream_t s) {
+    ratio_kernel<<<1, 1, 0, s>>>(num, den, coef);
+}
+
+}  // namespace tfde

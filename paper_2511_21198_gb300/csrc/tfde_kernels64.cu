@@ -1,0 +1,326 @@
+// FP64 kernels of libtfde: the per-axis dense contraction and tridiagonal mass
+// stencil used by the plain-FP64 operator (Eq. (linear_sys)) and DST-I
+// preconditioner (Eq. (diag_tau_pre)), and the Krylov vector kernels and
+// deterministic reductions shared by both precisions.
+#include "tfde_internal.h"
+
+namespace tfde {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ long long line_offset(const AxisView& v, long long l) {
+    return (l % v.l_in) * v.s_in + (l / v.l_in) * v.s_out;
+}
+
+// (tridiag(1,6,1)/8 along the axis) Z at position (idx, m): zero exterior data.
+__device__ __forceinline__ double mass_stencil(const double* __restrict__ Z, long long idx, int m,
+                                               const AxisView& v) {
+    double s = 0.75 * Z[idx];
+    double nb = 0.0;
+    if (m > 0) nb += Z[idx - v.stride];
+    if (m + 1 < v.n) nb += Z[idx + v.stride];
+    return s + 0.125 * nb;
+}
+
+// Tiled FP64 contraction along one axis: each CTA computes a 64 (axis rows)
+// x 64 (lines) tile, K in steps of 16, 4x4 outputs per thread.
+constexpr int BM = 64, BN = 64, BK = 16;
+
+__global__ __launch_bounds__(kThreads) void axis_gemm_f64_kernel(
+    const double* __restrict__ Mat, const double* __restrict__ X, double* __restrict__ Y, AxisView v,
+    double alpha, const double* __restrict__ Z, double beta) {
+    __shared__ double As[BK][BM + 1];
+    __shared__ double Bs[BK][BN + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.y * BM;
+    const long long l0 = (long long)blockIdx.x * BN;
+    double acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+
+    for (int k0 = 0; k0 < v.n; k0 += BK) {
+        for (int e = tid; e < BM * BK; e += kThreads) {
+            const int mm = e / BK, kk = e % BK;
+            const int gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < v.n && gk < v.n) ? Mat[(size_t)gm * v.n + gk] : 0.0;
+        }
+        if (v.stride == 1) {  // lines are contiguous along k: walk k fastest
+            for (int e = tid; e < BN * BK; e += kThreads) {
+                const int ll = e / BK, kk = e % BK;
+                const long long l = l0 + ll;
+                const int gk = k0 + kk;
+                Bs[kk][ll] = (l < v.lines && gk < v.n) ? X[line_offset(v, l) + gk] : 0.0;
+            }
+        } else {              // consecutive lines are contiguous: walk lines fastest
+            for (int e = tid; e < BN * BK; e += kThreads) {
+                const int kk = e / BN, ll = e % BN;
+                const long long l = l0 + ll;
+                const int gk = k0 + kk;
+                Bs[kk][ll] = (l < v.lines && gk < v.n) ? X[line_offset(v, l) + (long long)gk * v.stride] : 0.0;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int gm = m0 + ty + 16 * r;
+        if (gm >= v.n) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const long long l = l0 + tx + 16 * c;
+            if (l >= v.lines) continue;
+            const long long idx = line_offset(v, l) + (long long)gm * v.stride;
+            double val = alpha * acc[r][c];
+            if (Z) val += beta * mass_stencil(Z, idx, gm, v);
+            Y[idx] = val;
+        }
+    }
+}
+
+__global__ void axis_stencil_f64_kernel(const double* __restrict__ X, double* __restrict__ Y, AxisView v,
+                                        long long N, double beta, const double* __restrict__ W,
+                                        double gamma) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)((idx / v.stride) % v.n);
+        double val = beta * mass_stencil(X, idx, m, v);
+        if (W) val += gamma * W[idx];
+        Y[idx] = val;
+    }
+}
+
+__global__ void lambda_scale_f64_kernel(const double* __restrict__ x, double* __restrict__ y,
+                                        const double* __restrict__ lam, int n1, int n2, int n3,
+                                        double c0, double c1, double c2, int invert) {
+    const long long N = (long long)n1 * n2 * n3;
+    const double* mx = lam;
+    const double* my = mx + n1;
+    const double* mz = my + n2;
+    const double* tx = mz + n3;
+    const double* ty = tx + n1;
+    const double* tz = ty + n2;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % n1);
+        const int j = (int)((idx / n1) % n2);
+        const int k = (int)(idx / ((long long)n1 * n2));
+        const double L = mz[k] * my[j] * mx[i] + c0 * mz[k] * my[j] * tx[i] + c1 * mz[k] * ty[j] * mx[i] +
+                         c2 * tz[k] * my[j] * mx[i];
+        y[idx] = invert ? x[idx] / L : x[idx] * L;
+    }
+}
+
+__global__ void axpby_f64_kernel(long long N, double a, const double* __restrict__ x, double b,
+                                 double* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = a * x[i] + b * y[i];
+}
+
+__global__ void axpbypz_f64_kernel(long long N, double a, const double* __restrict__ x, double b,
+                                   const double* __restrict__ y, double* __restrict__ z) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x)
+        z[i] = a * x[i] + b * y[i];
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double sh[kThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < kThreads / 32; ++w) t += sh[w];
+    }
+    return t;  // valid in thread 0
+}
+
+// Contiguous chunk per block keeps the summation order fixed for a given N.
+__device__ __forceinline__ void chunk_range(long long N, long long& lo, long long& hi) {
+    const long long per = (N + gridDim.x - 1) / gridDim.x;
+    lo = (long long)blockIdx.x * per;
+    hi = lo + per < N ? lo + per : N;
+}
+
+__global__ __launch_bounds__(kThreads) void cg_update_f64_kernel(long long N, double alpha,
+                                                                 const double* __restrict__ p,
+                                                                 const double* __restrict__ q,
+                                                                 double* __restrict__ x,
+                                                                 double* __restrict__ r,
+                                                                 double* __restrict__ part) {
+    long long lo, hi;
+    chunk_range(N, lo, hi);
+    double acc = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += kThreads) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        acc = fma(ri, ri, acc);
+    }
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+template <int C>
+__global__ __launch_bounds__(kThreads) void multidot_f64_kernel(long long N, int m0, int mc,
+                                                                const double* __restrict__ V, long long ldv,
+                                                                const double* __restrict__ w,
+                                                                double* __restrict__ part) {
+    long long lo, hi;
+    chunk_range(N, lo, hi);
+    double acc[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) acc[j] = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += kThreads) {
+        const double wi = w[i];
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+            if (j < mc) acc[j] = fma(V[(long long)(m0 + j) * ldv + i], wi, acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        if (j < mc) {
+            const double t = block_sum(acc[j]);
+            if (threadIdx.x == 0) part[(long long)(m0 + j) * gridDim.x + blockIdx.x] = t;
+        }
+    }
+}
+
+__global__ void multiaxpy_f64_kernel(long long N, int m, const double* __restrict__ V, long long ldv,
+                                     const double* __restrict__ h, double* __restrict__ w) {
+    __shared__ double hs[128];
+    for (int j = threadIdx.x; j < m; j += blockDim.x) hs[j] = h[j];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        double acc = w[i];
+        for (int j = 0; j < m; ++j) acc = fma(-hs[j], V[(long long)j * ldv + i], acc);
+        w[i] = acc;
+    }
+}
+
+__global__ void reduce_finish_kernel(const double* __restrict__ part, int nblk, int m, double* __restrict__ out) {
+    // one warp per result; fixed order: lane-strided partial sums, then a fixed tree
+    const int j = blockIdx.x;
+    if (j >= m) return;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) acc += part[(long long)j * nblk + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) out[j] = acc;
+}
+
+__global__ void source_assemble_f64_kernel(const double* __restrict__ oned, int n1, int n2, int n3,
+                                           double cP, double cS, double* __restrict__ F) {
+    const long long N = (long long)n1 * n2 * n3;
+    const double* Px = oned;
+    const double* Py = Px + n1;
+    const double* Pz = Py + n2;
+    const double* Sx = Pz + n3;
+    const double* Sy = Sx + n1;
+    const double* Sz = Sy + n2;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % n1);
+        const int j = (int)((idx / n1) % n2);
+        const int k = (int)(idx / ((long long)n1 * n2));
+        const double ppp = Pz[k] * Py[j] * Px[i];
+        const double spp = Pz[k] * Py[j] * Sx[i] + Pz[k] * Sy[j] * Px[i] + Sz[k] * Py[j] * Px[i];
+        F[idx] = cP * ppp + cS * spp;
+    }
+}
+
+inline int grid_for(long long N) {
+    long long g = (N + kThreads - 1) / kThreads;
+    if (g > 152LL * 16) g = 152LL * 16;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+int reduction_blocks(size_t N) {
+    long long b = ((long long)N + 4 * kThreads - 1) / (4 * kThreads);
+    if (b > 1216) b = 1216;  // 8 per SM on 152 SMs
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+void launch_axis_gemm_f64(const double* Mat, const double* X, double* Y, const AxisView& v, double alpha,
+                          const double* Z, double beta, cudaStream_t s) {
+    dim3 grid((unsigned)((v.lines + BN - 1) / BN), (unsigned)((v.n + BM - 1) / BM));
+    axis_gemm_f64_kernel<<<grid, kThreads, 0, s>>>(Mat, X, Y, v, alpha, Z, beta);
+}
+
+void launch_axis_stencil_f64(const double* X, double* Y, const AxisView& v, double beta, const double* W,
+                             double gamma, cudaStream_t s) {
+    const long long N = v.lines * v.n;
+    axis_stencil_f64_kernel<<<grid_for(N), kThreads, 0, s>>>(X, Y, v, N, beta, W, gamma);
+}
+
+void launch_lambda_scale_f64(const double* x, double* y, const double* lam, const int n[3], const double c[3],
+                             int invert, cudaStream_t s) {
+    const long long N = (long long)n[0] * n[1] * n[2];
+    lambda_scale_f64_kernel<<<grid_for(N), kThreads, 0, s>>>(x, y, lam, n[0], n[1], n[2], c[0], c[1], c[2],
+                                                              invert);
+}
+
+void launch_axpby_f64(size_t N, double a, const double* x, double b, double* y, cudaStream_t s) {
+    axpby_f64_kernel<<<grid_for((long long)N), kThreads, 0, s>>>((long long)N, a, x, b, y);
+}
+
+void launch_axpbypz_f64(size_t N, double a, const double* x, double b, const double* y, double* z,
+                        cudaStream_t s) {
+    axpbypz_f64_kernel<<<grid_for((long long)N), kThreads, 0, s>>>((long long)N, a, x, b, y, z);
+}
+
+void launch_cg_update_f64(size_t N, double alpha, const double* p, const double* q, double* x, double* r,
+                          double* part, int nblk, cudaStream_t s) {
+    cg_update_f64_kernel<<<nblk, kThreads, 0, s>>>((long long)N, alpha, p, q, x, r, part);
+}
+
+void launch_multidot_f64(size_t N, int m, const double* V, size_t ldv, const double* w, double* part, int nblk,
+                         cudaStream_t s) {
+    for (int m0 = 0; m0 < m; m0 += 8) {
+        const int mc = (m - m0) < 8 ? (m - m0) : 8;
+        multidot_f64_kernel<8><<<nblk, kThreads, 0, s>>>((long long)N, m0, mc, V, (long long)ldv, w, part);
+    }
+}
+
+void launch_multiaxpy_f64(size_t N, int m, const double* V, size_t ldv, const double* h, double* w,
+                          cudaStream_t s) {
+    multiaxpy_f64_kernel<<<grid_for((long long)N), kThreads, 0, s>>>((long long)N, m, V, (long long)ldv, h, w);
+}
+
+void launch_reduce_finish(const double* part, int nblk, int m, double* out, cudaStream_t s) {
+    reduce_finish_kernel<<<m, 32, 0, s>>>(part, nblk, m, out);
+}
+
+void launch_source_assemble_f64(const double* oned, const int n[3], double cP, double cS, double* F,
+                                cudaStream_t s) {
+    const long long N = (long long)n[0] * n[1] * n[2];
+    source_assemble_f64_kernel<<<grid_for(N), kThreads, 0, s>>>(oned, n[0], n[1], n[2], cP, cS, F);
+}
+
+}  // namespace tfde

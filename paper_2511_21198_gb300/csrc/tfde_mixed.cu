@@ -1,0 +1,420 @@
+// Mixed-precision path: split-BF16 tcgen05 contractions for the inner
+// Krylov solves on FP32 vectors, wrapped in FP64 iterative refinement whose
+// residual b - A x is always evaluated accurately (Sec. 2 Eq. (linear_sys),
+// Sec. 3 Eq. (diag_tau_pre)).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "tfde_mixed.h"
+
+namespace tfde {
+
+int pcg64(const tfde_problem*, const double*, double*, double, int, tfde_info*, cudaStream_t);
+int pgmres64(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t);
+
+namespace {
+
+#define MX_TRY(expr)                                                                       \
+    do {                                                                                   \
+        cudaError_t e__ = (expr);                                                          \
+        if (e__ != cudaSuccess)                                                            \
+            return set_error(TFDE_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e__)); \
+    } while (0)
+
+using clk = std::chrono::steady_clock;
+
+void to_bf16_pair(double v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn((float)v);
+    lo = __float2bfloat16_rn((float)(v - (double)__bfloat162float(hi)));
+}
+
+// Dense eta_a B_a (row-major [out][in]) from the generator (Eq. (T_ni), Eq. (stiff_matrix)).
+std::vector<double> dense_etaB(const tfde_problem* P, int a) {
+    const int n = P->n[a];
+    const double kp = P->p.kp[a], km = P->p.km[a];
+    std::vector<double> B((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double v = 0.0;
+            const int m1 = i - j + 1, m2 = j - i + 1;
+            if (m1 >= 0 && m1 <= n) v += kp * P->q[a][m1];
+            if (m2 >= 0 && m2 <= n) v += km * P->q[a][m2];
+            B[(size_t)i * n + j] = P->eta[a] * v;
+        }
+    return B;
+}
+
+double mass_entry(int i, int j) { return i == j ? 0.75 : ((i - j == 1 || j - i == 1) ? 0.125 : 0.0); }
+
+struct SegSpec {
+    int a_hi, a_lo, plane;  // a_lo < 0: single-term A
+};
+
+// out = alpha * sum_seg (A_seg along axis) (plane_seg hi + lo)
+int run_gemm(const tfde_problem* P, int axis, const SegSpec* segs, int nseg, int out_mode, float alpha,
+             float* out_f32, int out_plane, bool lam_scale, cudaStream_t s) {
+    MixedState* M = mixed(P);
+    tc::Params prm;
+    std::memset(&prm, 0, sizeof(prm));
+    tc::set_geometry(prm, P->n, axis);
+    int na = 0, nb = 0;
+    for (int g = 0; g < nseg; ++g) {
+        tc::Segment& S = prm.seg[g];
+        S.nkb = (P->n[axis] + tc::BK - 1) / tc::BK;
+        prm.amaps[na] = M->amap[segs[g].a_hi];
+        S.amap[0] = na++;
+        S.na = 1;
+        if (segs[g].a_lo >= 0) {
+            prm.amaps[na] = M->amap[segs[g].a_lo];
+            S.amap[1] = na++;
+            S.na = 2;
+        }
+        prm.bmaps[nb] = M->bmap_hi[segs[g].plane][axis];
+        S.bmap[0] = nb++;
+        prm.bmaps[nb] = M->bmap_lo[segs[g].plane][axis];
+        S.bmap[1] = nb++;
+        S.nb = 2;
+        S.npair = 0;
+        S.pa[S.npair] = 0; S.pb[S.npair++] = 0;   // A_hi * x_hi
+        S.pa[S.npair] = 0; S.pb[S.npair++] = 1;   // A_hi * x_lo
+        if (S.na == 2) { S.pa[S.npair] = 1; S.pb[S.npair++] = 0; }  // A_lo * x_hi
+    }
+    prm.nseg = nseg;
+    prm.out_mode = out_mode;
+    prm.alpha = alpha;
+    prm.out_f32 = out_f32;
+    if (out_mode == tc::OUT_HILO) {
+        prm.out_hi = M->hi[out_plane];
+        prm.out_lo = M->lo[out_plane];
+    }
+    if (lam_scale) {
+        const long long n1n2 = (long long)P->n[0] * P->n[1];
+        prm.lam_ra = M->lam;
+        prm.lam_rb = M->lam + P->n[2];
+        prm.lam_U = M->lam + 2 * P->n[2];
+        prm.lam_V = M->lam + 2 * P->n[2] + n1n2;
+    }
+    prm.err = M->err;
+    M->gemm_launches++;
+    return tc::launch(prm, s);
+}
+
+// q32 = A p (op A) or the RHS operator, p given as the split plane pair PL_P.
+int fast_matvec(const tfde_problem* P, int op, float* q32, cudaStream_t s) {
+    const bool rhs = (op & 1) != 0;
+    int st;
+    SegSpec sx[1] = {{rhs ? OM_GHATR_H : OM_GHAT_H, rhs ? OM_GHATR_L : OM_GHAT_L, PL_P}};
+    if ((st = run_gemm(P, 0, sx, 1, tc::OUT_HILO, 1.f, nullptr, PL_A, false, s))) return st;
+    SegSpec wx[1] = {{OM_MX, -1, PL_P}};
+    if ((st = run_gemm(P, 0, wx, 1, tc::OUT_HILO, 1.f, nullptr, PL_W, false, s))) return st;
+    SegSpec cy[2] = {{OM_MY, -1, PL_A}, {rhs ? OM_GYN_H : OM_GY_H, rhs ? OM_GYN_L : OM_GY_L, PL_W}};
+    if ((st = run_gemm(P, 1, cy, 2, tc::OUT_HILO, 1.f, nullptr, PL_C, false, s))) return st;
+    SegSpec ey[1] = {{OM_MY, -1, PL_W}};
+    if ((st = run_gemm(P, 1, ey, 1, tc::OUT_HILO, 1.f, nullptr, PL_E, false, s))) return st;
+    SegSpec oz[2] = {{OM_MZ, -1, PL_C}, {rhs ? OM_GZN_H : OM_GZ_H, rhs ? OM_GZN_L : OM_GZ_L, PL_E}};
+    return run_gemm(P, 2, oz, 2, tc::OUT_F32, 1.f, q32, 0, false, s);
+}
+
+// z32 = S_N Lambda^{-1} S_N r, r given as the split plane pair PL_R.
+int fast_precond(const tfde_problem* P, float* z32, cudaStream_t s) {
+    int st;
+    SegSpec a[1] = {{OM_SX, -1, PL_R}};
+    if ((st = run_gemm(P, 0, a, 1, tc::OUT_HILO, 1.f, nullptr, PL_T1, false, s))) return st;
+    SegSpec b[1] = {{OM_SY, -1, PL_T1}};
+    if ((st = run_gemm(P, 1, b, 1, tc::OUT_HILO, 1.f, nullptr, PL_T2, false, s))) return st;
+    SegSpec c[1] = {{OM_SZ, -1, PL_T2}};
+    if ((st = run_gemm(P, 2, c, 1, tc::OUT_HILO, 1.f, nullptr, PL_T1, true, s))) return st;
+    SegSpec d[1] = {{OM_SZ, -1, PL_T1}};
+    if ((st = run_gemm(P, 2, d, 1, tc::OUT_HILO, 1.f, nullptr, PL_T2, false, s))) return st;
+    SegSpec e[1] = {{OM_SY, -1, PL_T2}};
+    if ((st = run_gemm(P, 1, e, 1, tc::OUT_HILO, 1.f, nullptr, PL_T1, false, s))) return st;
+    SegSpec f[1] = {{OM_SX, -1, PL_T1}};
+    return run_gemm(P, 0, f, 1, tc::OUT_F32, 1.f, z32, 0, false, s);
+}
+
+int check_err(const tfde_problem* P, cudaStream_t s) {
+    MixedState* M = mixed(P);
+    MX_TRY(cudaMemcpyAsync(M->err_host, M->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MX_TRY(cudaStreamSynchronize(s));
+    if (*M->err_host) return set_error(TFDE_ETIMEOUT, "tensor-core kernel wait ran out (device error flag set)");
+    return TFDE_OK;
+}
+
+double host_scalar(const tfde_problem* P, const double* dev, cudaStream_t s, int* st) {
+    *st = TFDE_OK;
+    if (cudaMemcpyAsync(P->red_host, dev, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        *st = set_error(TFDE_ECUDA, "scalar read-back failed");
+        return 0.0;
+    }
+    return P->red_host[0];
+}
+
+// Device-scalar slots.
+enum { D_RZ = 0, D_PQ = 1, D_RR = 2, D_ALPHA = 3, D_BETA = 4, D_RZN = 5 };
+
+// Inner PCG on FP32 vectors: A d = r32 (r32 and its split planes prepared by
+// the caller, x32 = 0), until ||r|| <= theta ||r32_0|| or maxit.  All
+// coefficients stay on the device; one host read (r.r) per iteration.
+int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaStream_t s) {
+    MixedState* M = mixed(P);
+    const size_t N = P->N;
+    float* x = M->f[F_X];
+    float* r = M->f[F_R];
+    float* z = M->f[F_Z];
+    float* p = M->f[F_P];
+    float* q = M->f[F_Q];
+    double* d = M->dsc;
+    int st;
+    launch_dot32(N, r, r, P->red, P->nblk, s);
+    launch_reduce_finish(P->red, P->nblk, 1, d + D_RR, s);
+    const double rr0 = host_scalar(P, d + D_RR, s, &st);
+    if (st) return st;
+    if (!(rr0 > 0.0) || !std::isfinite(rr0)) return rr0 == 0.0 ? TFDE_OK : set_error(TFDE_ENAN, "non-finite inner residual");
+    if ((st = fast_precond(P, z, s))) return st;
+    MX_TRY(cudaMemcpyAsync(p, z, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    launch_split32(N, p, M->hi[PL_P], M->lo[PL_P], s);
+    launch_dot32(N, r, z, P->red, P->nblk, s);
+    launch_reduce_finish(P->red, P->nblk, 1, d + D_RZ, s);
+    int k = 0;
+    while (k < maxit) {
+        if ((st = fast_matvec(P, TFDE_OP_A, q, s))) return st;
+        launch_dot32(N, p, q, P->red, P->nblk, s);
+        launch_reduce_finish(P->red, P->nblk, 1, d + D_PQ, s);
+        launch_ratio(d + D_RZ, d + D_PQ, d + D_ALPHA, s);
+        launch_cg_update32(N, d + D_ALPHA, p, q, x, r, M->hi[PL_R], M->lo[PL_R], P->red, P->nblk, s);
+        launch_reduce_finish(P->red, P->nblk, 1, d + D_RR, s);
+        const double rr = host_scalar(P, d + D_RR, s, &st);
+        if (st) return st;
+        ++k;
+        if (!std::isfinite(rr)) return set_error(TFDE_ENAN, "non-finite inner residual");
+        if (rr <= theta * theta * rr0) break;
+        if ((st = fast_precond(P, z, s))) return st;
+        launch_dot32(N, r, z, P->red, P->nblk, s);
+        launch_reduce_finish(P->red, P->nblk, 1, d + D_RZN, s);
+        launch_ratio(d + D_RZN, d + D_RZ, d + D_BETA, s);
+        MX_TRY(cudaMemcpyAsync(d + D_RZ, d + D_RZN, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        launch_xpay32(N, d + D_BETA, z, p, M->hi[PL_P], M->lo[PL_P], s);
+    }
+    *iters = k;
+    return check_err(P, s);
+}
+
+int accurate_residual(const tfde_problem* P, const double* b, const double* x, double* r, double* nr,
+                      cudaStream_t s) {
+    double* q = P->w[tfde_problem::W_Q];
+    int st = apply_A64(P, TFDE_OP_A, x, q, s);
+    if (st) return st;
+    launch_axpbypz_f64(P->N, 1.0, b, -1.0, q, r, s);
+    double rr;
+    if ((st = dots64(P, 1, r, 0, r, &rr, s))) return st;
+    *nr = std::sqrt(rr);
+    return TFDE_OK;
+}
+
+}  // namespace
+
+int mixed_init(tfde_problem* P, cudaStream_t s) {
+    for (int a = 0; a < 3; ++a)
+        if (P->n[a] % 8 != 0)
+            return set_error(TFDE_EUNSUPPORTED, "TFDE_MIXED needs every n_a to be a multiple of 8");
+    MixedState* M = new MixedState();
+    P->mixed = M;
+    const size_t N = P->N;
+    // operator matrices
+    for (int om = 0; om < NOM; ++om) {
+        int a;
+        if (om <= OM_GHATR_L || om == OM_MX || om == OM_SX) a = 0;
+        else if ((om >= OM_GY_H && om <= OM_GYN_L) || om == OM_MY || om == OM_SY) a = 1;
+        else a = 2;
+        const int n = P->n[a];
+        std::vector<__nv_bfloat16> h((size_t)n * n);
+        if (om == OM_MX || om == OM_MY || om == OM_MZ) {
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) h[(size_t)i * n + j] = __float2bfloat16_rn((float)mass_entry(i, j));
+        } else if (om == OM_SX || om == OM_SY || om == OM_SZ) {
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) {
+                    const long long r = ((long long)(i + 1) * (j + 1)) % (2LL * (n + 1));
+                    const double v = std::sqrt(2.0 / (n + 1)) * std::sin(M_PI * (double)r / (double)(n + 1));
+                    h[(size_t)i * n + j] = __float2bfloat16_rn((float)v);
+                }
+        } else {
+            const std::vector<double> B = dense_etaB(P, a);
+            const bool lo = (om == OM_GHAT_L || om == OM_GHATR_L || om == OM_GY_L || om == OM_GYN_L ||
+                             om == OM_GZ_L || om == OM_GZN_L);
+            double sgn = 1.0, mass = 0.0;
+            if (om == OM_GHAT_H || om == OM_GHAT_L) mass = 1.0;
+            if (om == OM_GHATR_H || om == OM_GHATR_L) { mass = 1.0; sgn = -1.0; }
+            if (om == OM_GYN_H || om == OM_GYN_L || om == OM_GZN_H || om == OM_GZN_L) sgn = -1.0;
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) {
+                    const double v = mass * mass_entry(i, j) + sgn * B[(size_t)i * n + j];
+                    __nv_bfloat16 vh, vl;
+                    to_bf16_pair(v, vh, vl);
+                    h[(size_t)i * n + j] = lo ? vl : vh;
+                }
+        }
+        MX_TRY(cudaMalloc((void**)&M->mat[om], h.size() * sizeof(__nv_bfloat16)));
+        MX_TRY(cudaMemcpyAsync(M->mat[om], h.data(), h.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, s));
+        MX_TRY(cudaStreamSynchronize(s));
+        int st = tc::make_map_A(&M->amap[om], M->mat[om], n);
+        if (st) return st;
+    }
+    // workspace planes and their tensor maps
+    for (int pl = 0; pl < NPL; ++pl) {
+        MX_TRY(cudaMalloc((void**)&M->hi[pl], N * sizeof(__nv_bfloat16)));
+        MX_TRY(cudaMalloc((void**)&M->lo[pl], N * sizeof(__nv_bfloat16)));
+        MX_TRY(cudaMemsetAsync(M->hi[pl], 0, N * sizeof(__nv_bfloat16), s));
+        MX_TRY(cudaMemsetAsync(M->lo[pl], 0, N * sizeof(__nv_bfloat16), s));
+        for (int a = 0; a < 3; ++a) {
+            int st = tc::make_map_B(&M->bmap_hi[pl][a], M->hi[pl], P->n, a);
+            if (!st) st = tc::make_map_B(&M->bmap_lo[pl][a], M->lo[pl], P->n, a);
+            if (st) return st;
+        }
+    }
+    for (int v = 0; v < NF; ++v) {
+        MX_TRY(cudaMalloc((void**)&M->f[v], N * sizeof(float)));
+        MX_TRY(cudaMemsetAsync(M->f[v], 0, N * sizeof(float), s));
+    }
+    // z-pass scale: Lambda(i,j,k) = ra[k] U[i + n1 j] + rb[k] V[i + n1 j]  (Eq. (diag_tau_pre))
+    {
+        const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
+        std::vector<float> lam(2 * (size_t)n3 + 2 * (size_t)n1 * n2);
+        for (int k = 0; k < n3; ++k) {
+            lam[k] = (float)P->lam_mass[2][k];
+            lam[n3 + k] = (float)(P->csum[2] * P->lam_tau[2][k]);
+        }
+        for (int j = 0; j < n2; ++j)
+            for (int i = 0; i < n1; ++i) {
+                const double a1 = P->lam_mass[0][i], a2 = P->lam_mass[1][j];
+                const double l1 = P->lam_tau[0][i], l2 = P->lam_tau[1][j];
+                const size_t c = (size_t)i + (size_t)n1 * j;
+                lam[2 * (size_t)n3 + c] = (float)(a2 * a1 + P->csum[0] * a2 * l1 + P->csum[1] * l2 * a1);
+                lam[2 * (size_t)n3 + (size_t)n1 * n2 + c] = (float)(a2 * a1);
+            }
+        MX_TRY(cudaMalloc((void**)&M->lam, lam.size() * sizeof(float)));
+        MX_TRY(cudaMemcpyAsync(M->lam, lam.data(), lam.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    }
+    MX_TRY(cudaMalloc((void**)&M->dsc, 16 * sizeof(double)));
+    MX_TRY(cudaMemsetAsync(M->dsc, 0, 16 * sizeof(double), s));
+    MX_TRY(cudaMalloc((void**)&M->err, sizeof(int)));
+    MX_TRY(cudaMemsetAsync(M->err, 0, sizeof(int), s));
+    MX_TRY(cudaMallocHost((void**)&M->err_host, sizeof(int)));
+    MX_TRY(cudaStreamSynchronize(s));
+    return TFDE_OK;
+}
+
+void mixed_free(tfde_problem* P) {
+    MixedState* M = mixed(P);
+    if (!M) return;
+    for (auto& m : M->mat) cudaFree(m);
+    for (int pl = 0; pl < NPL; ++pl) {
+        cudaFree(M->hi[pl]);
+        cudaFree(M->lo[pl]);
+    }
+    for (auto& v : M->f) cudaFree(v);
+    cudaFree(M->lam);
+    cudaFree(M->dsc);
+    cudaFree(M->err);
+    if (M->err_host) cudaFreeHost(M->err_host);
+    delete M;
+    P->mixed = nullptr;
+}
+
+int mixed_apply_A(const tfde_problem* P, int op, const double* x, double* y, cudaStream_t s) {
+    if (!(op & TFDE_OP_FAST)) return apply_A64(P, op & 1, x, y, s);
+    MixedState* M = mixed(P);
+    launch_split64(P->N, x, 1.0, M->hi[PL_P], M->lo[PL_P], s);
+    int st = fast_matvec(P, op, M->f[F_Q], s);
+    if (st) return st;
+    launch_widen32(P->N, M->f[F_Q], 1.0, y, s);
+    return TFDE_OK;
+}
+
+int mixed_apply_Pinv(const tfde_problem* P, const double* r, double* z, cudaStream_t s) {
+    MixedState* M = mixed(P);
+    launch_split64(P->N, r, 1.0, M->hi[PL_R], M->lo[PL_R], s);
+    int st = fast_precond(P, M->f[F_Z], s);
+    if (st) return st;
+    launch_widen32(P->N, M->f[F_Z], 1.0, z, s);
+    return TFDE_OK;
+}
+
+// FP64 iterative refinement around the FP32 / split-BF16 inner PCG.
+int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit, tfde_info* info,
+              cudaStream_t s) {
+    const auto t0 = clk::now();
+    MixedState* M = mixed(P);
+    tfde_info loc{};
+    double* r64 = P->w[tfde_problem::W_R];
+    int st;
+    double bb;
+    if ((st = dots64(P, 1, b, 0, b, &bb, s))) return st;
+    const double nb = std::sqrt(bb);
+    if (!std::isfinite(nb)) return set_error(TFDE_ENAN, "non-finite right-hand side");
+    if (nb == 0.0) {
+        MX_TRY(cudaMemsetAsync(x, 0, P->N * sizeof(double), s));
+        if (info) *info = loc;
+        return TFDE_OK;
+    }
+    double nr;
+    if ((st = accurate_residual(P, b, x, r64, &nr, s))) return st;
+    loc.relres0 = nr / nb;
+    int status = TFDE_ENOCONV;
+    int stall = 0;
+    while (true) {
+        if (!std::isfinite(nr)) { status = set_error(TFDE_ENAN, "non-finite residual"); break; }
+        if (nr <= tol * nb) { status = TFDE_OK; break; }
+        if (loc.iters >= maxit) break;
+        // inner solve of A d = r / ||r|| to a relative theta
+        double theta = 0.5 * tol * nb / nr;
+        if (theta < 1e-4) theta = 1e-4;
+        launch_scale64to32(P->N, r64, 1.0 / nr, M->f[F_R], M->hi[PL_R], M->lo[PL_R], M->f[F_X], s);
+        int it = 0;
+        if ((st = inner_pcg(P, theta, maxit - loc.iters, &it, s))) return st;
+        loc.iters += it;
+        loc.refine_sweeps++;
+        launch_add32to64(P->N, nr, M->f[F_X], x, s);
+        const double nr_old = nr;
+        if ((st = accurate_residual(P, b, x, r64, &nr, s))) return st;
+        stall = (nr > 0.5 * nr_old) ? stall + 1 : 0;
+        if (stall >= 2) {
+            // refinement stopped contracting: finish with FP64 inner solves
+            loc.fallback = 1;
+            tfde_info sub{};
+            status = pcg64(P, b, x, tol, maxit > loc.iters ? maxit - loc.iters : 1, &sub, s);
+            loc.iters += sub.iters;
+            nr = sub.relres * nb;
+            break;
+        }
+    }
+    loc.relres = nr / nb;
+    if (status == TFDE_ENOCONV) set_error(TFDE_ENOCONV, "mixed PCG reached maxit");
+    loc.ms = (float)std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    if (info) *info = loc;
+    return status;
+}
+
+int mixed_pgmres(tfde_problem* P, const double* b, double* x, int restart, double tol, int maxit, tfde_info* info,
+                 cudaStream_t s) {
+    int st = pgmres64(P, b, x, restart, tol, maxit, info, s);
+    if (info) info->fallback = 1;
+    return st;
+}
+
+int mixed_cn_step(tfde_problem* P, const double* u_prev, const double* F, const double* x0, double* u_next,
+                  double tol, tfde_info* info, cudaStream_t s) {
+    double* b = P->w[tfde_problem::W_B];
+    int st = apply_A64(P, TFDE_OP_RHS, u_prev, b, s);
+    if (st) return st;
+    if (F) launch_axpby_f64(P->N, P->p.dt, F, 1.0, b, s);
+    const double* start = x0 ? x0 : u_prev;
+    if (start != u_next) MX_TRY(cudaMemcpyAsync(u_next, start, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (P->symmetric) return mixed_pcg(P, b, u_next, tol, 10000, info, s);
+    return mixed_pgmres(P, b, u_next, 20, tol, 10000, info, s);
+}
+
+}  // namespace tfde

@@ -1,0 +1,328 @@
+// FP64 operator, preconditioner and Krylov solvers of libtfde, and the
+// Crank-Nicolson step driver (Sec. 2 Eq. (CN), Eq. (linear_sys); Sec. 3).
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "tfde_internal.h"
+
+namespace tfde {
+
+#define TFDE_CUDA_TRY(expr)                                                              \
+    do {                                                                                  \
+        cudaError_t e__ = (expr);                                                         \
+        if (e__ != cudaSuccess)                                                           \
+            return set_error(TFDE_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e__)); \
+    } while (0)
+
+static int check_launch(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(TFDE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return TFDE_OK;
+}
+
+// A x (op TFDE_OP_A) or (2 A_N - A) x (op TFDE_OP_RHS), Eq. (linear_sys), as
+// three axis passes:  a = (M1 +- eta1 B1) x,  w = M1 x;
+//                     c = M2 a +- eta2 B2 w,  e = M2 w;
+//                     y = M3 c +- eta3 B3 e.
+int apply_A64(const tfde_problem* P, int op, const double* x, double* y, cudaStream_t s) {
+    const bool rhs = (op & 1) != 0;
+    const double sg = rhs ? -1.0 : 1.0;
+    const AxisView vx = axis_view(P->n, 0), vy = axis_view(P->n, 1), vz = axis_view(P->n, 2);
+    double* a = P->w[tfde_problem::W_A];
+    double* w = P->w[tfde_problem::W_W];
+    double* c = P->w[tfde_problem::W_C];
+    double* e = P->w[tfde_problem::W_E];
+    launch_axis_gemm_f64(P->Ghat[rhs ? 1 : 0], x, a, vx, 1.0, nullptr, 0.0, s);
+    launch_axis_stencil_f64(x, w, vx, 1.0, nullptr, 0.0, s);
+    launch_axis_gemm_f64(P->G[1], w, c, vy, sg, a, 1.0, s);
+    launch_axis_stencil_f64(w, e, vy, 1.0, nullptr, 0.0, s);
+    launch_axis_gemm_f64(P->G[2], e, y, vz, sg, c, 1.0, s);
+    return check_launch("apply_A64");
+}
+
+// z = S_N Lambda^{-1} S_N r (Eq. (diag_tau_pre)); S_n symmetric, S_n^2 = I.
+int apply_Pinv64(const tfde_problem* P, const double* r, double* z, cudaStream_t s) {
+    const AxisView vx = axis_view(P->n, 0), vy = axis_view(P->n, 1), vz = axis_view(P->n, 2);
+    double* t1 = P->w[tfde_problem::W_A];
+    double* t2 = P->w[tfde_problem::W_C];
+    launch_axis_gemm_f64(P->S[0], r, t1, vx, 1.0, nullptr, 0.0, s);
+    launch_axis_gemm_f64(P->S[1], t1, t2, vy, 1.0, nullptr, 0.0, s);
+    launch_axis_gemm_f64(P->S[2], t2, t1, vz, 1.0, nullptr, 0.0, s);
+    launch_lambda_scale_f64(t1, t1, P->lam, P->n, P->csum, 1, s);
+    launch_axis_gemm_f64(P->S[2], t1, t2, vz, 1.0, nullptr, 0.0, s);
+    launch_axis_gemm_f64(P->S[1], t2, t1, vy, 1.0, nullptr, 0.0, s);
+    launch_axis_gemm_f64(P->S[0], t1, z, vx, 1.0, nullptr, 0.0, s);
+    return check_launch("apply_Pinv64");
+}
+
+// out[j] = <V_j, w>, j < m (host output; synchronises the stream).
+int dots64(const tfde_problem* P, int m, const double* V, size_t ldv, const double* w, double* out,
+           cudaStream_t s) {
+    launch_multidot_f64(P->N, m, V, ldv, w, P->red, P->nblk, s);
+    launch_reduce_finish(P->red, P->nblk, m, P->red_out, s);
+    TFDE_CUDA_TRY(cudaGetLastError());
+    TFDE_CUDA_TRY(cudaMemcpyAsync(P->red_host, P->red_out, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TFDE_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int j = 0; j < m; ++j) out[j] = P->red_host[j];
+    return TFDE_OK;
+}
+
+static int dot(const tfde_problem* P, const double* a, const double* b, double* out, cudaStream_t s) {
+    return dots64(P, 1, a, 0, b, out, s);
+}
+
+int ensure_gmres_basis(tfde_problem* P, int restart) {
+    if (P->gmres_cap >= restart) return TFDE_OK;
+    cudaFree(P->V);
+    P->V = nullptr;
+    P->gmres_cap = 0;
+    if (cudaMalloc((void**)&P->V, (size_t)(restart + 1) * P->N * sizeof(double)) != cudaSuccess)
+        return set_error(TFDE_ENOMEM, "cudaMalloc of the GMRES basis failed");
+    P->gmres_cap = restart;
+    return TFDE_OK;
+}
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+double ms_since(clk::time_point t0) {
+    return std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+}
+
+// r = b - A x into `r`; returns ||r||.
+int true_residual(const tfde_problem* P, const double* b, const double* x, double* r, double* nrm,
+                  cudaStream_t s) {
+    double* q = P->w[tfde_problem::W_Q];
+    int st = apply_A64(P, TFDE_OP_A, x, q, s);
+    if (st) return st;
+    launch_axpbypz_f64(P->N, 1.0, b, -1.0, q, r, s);
+    double rr;
+    if ((st = dot(P, r, r, &rr, s))) return st;
+    *nrm = std::sqrt(rr);
+    return TFDE_OK;
+}
+
+}  // namespace
+
+// Preconditioned CG (Sec. 3.1) in FP64, true-residual stopping test.
+int pcg64(const tfde_problem* P, const double* b, double* x, double tol, int maxit, tfde_info* info,
+          cudaStream_t s) {
+    const auto t0 = clk::now();
+    tfde_info loc{};
+    double* r = P->w[tfde_problem::W_R];
+    double* z = P->w[tfde_problem::W_Z];
+    double* p = P->w[tfde_problem::W_P];
+    double* q = P->w[tfde_problem::W_Q];
+    int st;
+    double bb;
+    if ((st = dot(P, b, b, &bb, s))) return st;
+    const double nb = std::sqrt(bb);
+    if (!std::isfinite(nb)) return set_error(TFDE_ENAN, "non-finite right-hand side");
+    if (nb == 0.0) {
+        TFDE_CUDA_TRY(cudaMemsetAsync(x, 0, P->N * sizeof(double), s));
+        loc.relres = loc.relres0 = 0.0;
+        if (info) *info = loc;
+        return TFDE_OK;
+    }
+    double nr;
+    if ((st = true_residual(P, b, x, r, &nr, s))) return st;
+    loc.relres0 = nr / nb;
+    int status = TFDE_ENOCONV;
+    if (!std::isfinite(nr)) {
+        status = set_error(TFDE_ENAN, "non-finite initial residual");
+    } else if (nr <= tol * nb) {
+        status = TFDE_OK;
+        loc.relres = nr / nb;
+    } else {
+        if ((st = apply_Pinv64(P, r, z, s))) return st;
+        TFDE_CUDA_TRY(cudaMemcpyAsync(p, z, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        double rz;
+        if ((st = dot(P, r, z, &rz, s))) return st;
+        while (loc.iters < maxit) {
+            if ((st = apply_A64(P, TFDE_OP_A, p, q, s))) return st;
+            double pq;
+            if ((st = dot(P, p, q, &pq, s))) return st;
+            if (!std::isfinite(pq)) { status = set_error(TFDE_ENAN, "non-finite p.Ap"); break; }
+            if (!(pq > 0.0)) { status = set_error(TFDE_EBREAKDOWN, "PCG breakdown: p.Ap <= 0"); break; }
+            const double alpha = rz / pq;
+            launch_cg_update_f64(P->N, alpha, p, q, x, r, P->red, P->nblk, s);
+            launch_reduce_finish(P->red, P->nblk, 1, P->red_out, s);
+            TFDE_CUDA_TRY(cudaMemcpyAsync(P->red_host, P->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+            TFDE_CUDA_TRY(cudaStreamSynchronize(s));
+            const double rr = P->red_host[0];
+            loc.iters++;
+            if (!std::isfinite(rr)) { status = set_error(TFDE_ENAN, "non-finite residual"); break; }
+            if (std::sqrt(rr) <= tol * nb) {
+                if ((st = true_residual(P, b, x, r, &nr, s))) return st;
+                if (nr <= tol * nb) {
+                    status = TFDE_OK;
+                    loc.relres = nr / nb;
+                    break;
+                }
+                // recursive residual drifted: restart from the true one
+                if ((st = apply_Pinv64(P, r, z, s))) return st;
+                TFDE_CUDA_TRY(cudaMemcpyAsync(p, z, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                if ((st = dot(P, r, z, &rz, s))) return st;
+                continue;
+            }
+            if ((st = apply_Pinv64(P, r, z, s))) return st;
+            double rz_new;
+            if ((st = dot(P, r, z, &rz_new, s))) return st;
+            const double beta = rz_new / rz;
+            rz = rz_new;
+            launch_axpby_f64(P->N, 1.0, z, beta, p, s);
+        }
+        if (status == TFDE_ENOCONV) {
+            if ((st = true_residual(P, b, x, r, &nr, s))) return st;
+            loc.relres = nr / nb;
+            set_error(TFDE_ENOCONV, "PCG reached maxit");
+        }
+    }
+    loc.ms = (float)ms_since(t0);
+    if (info) *info = loc;
+    return status;
+}
+
+// Givens-rotated least squares state of one GMRES cycle (host, FP64).
+struct GivensLS {
+    int m;
+    std::vector<double> R, cs, sn, g;
+    explicit GivensLS(int m_) : m(m_), R((size_t)(m_ + 1) * m_, 0.0), cs(m_), sn(m_), g(m_ + 1, 0.0) {}
+    double& at(int i, int j) { return R[(size_t)i * m + j]; }
+    // column j of the Hessenberg matrix (entries 0..j+1) -> rotated; returns |g_{j+1}|
+    double add_column(int j, const double* h) {
+        for (int i = 0; i <= j + 1; ++i) at(i, j) = h[i];
+        for (int i = 0; i < j; ++i) {
+            const double t = cs[i] * at(i, j) + sn[i] * at(i + 1, j);
+            at(i + 1, j) = -sn[i] * at(i, j) + cs[i] * at(i + 1, j);
+            at(i, j) = t;
+        }
+        const double den = std::hypot(at(j, j), at(j + 1, j));
+        cs[j] = den > 0.0 ? at(j, j) / den : 1.0;
+        sn[j] = den > 0.0 ? at(j + 1, j) / den : 0.0;
+        at(j, j) = den;
+        at(j + 1, j) = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        return std::fabs(g[j + 1]);
+    }
+    void solve(int k, std::vector<double>& y) {
+        y.assign(k, 0.0);
+        for (int i = k - 1; i >= 0; --i) {
+            double t = g[i];
+            for (int j = i + 1; j < k; ++j) t -= at(i, j) * y[j];
+            y[i] = t / at(i, i);
+        }
+    }
+};
+
+// Left-preconditioned restarted GMRES (Sec. 3.2, Eq. (one_side_system)), FP64,
+// classical Gram-Schmidt with one re-orthogonalisation.  Converged when the
+// true relative residual meets tol; the cycle stops on the preconditioned
+// residual estimate, scaled by the observed true/preconditioned ratio.
+int pgmres64(tfde_problem* P, const double* b, double* x, int restart, double tol, int maxit, tfde_info* info,
+             cudaStream_t s) {
+    const auto t0 = clk::now();
+    tfde_info loc{};
+    int st;
+    if ((st = ensure_gmres_basis(P, restart))) return st;
+    double* r = P->w[tfde_problem::W_R];
+    double* q = P->w[tfde_problem::W_Q];
+    double* V = P->V;
+    const size_t N = P->N;
+    double bb;
+    if ((st = dot(P, b, b, &bb, s))) return st;
+    const double nb = std::sqrt(bb);
+    if (!std::isfinite(nb)) return set_error(TFDE_ENAN, "non-finite right-hand side");
+    if (nb == 0.0) {
+        TFDE_CUDA_TRY(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+        if (info) *info = loc;
+        return TFDE_OK;
+    }
+    double nr;
+    if ((st = true_residual(P, b, x, r, &nr, s))) return st;
+    loc.relres0 = nr / nb;
+    double ratio = 1.0;  // observed (true relres) / (preconditioned relres)
+    int status = TFDE_ENOCONV;
+    std::vector<double> h(restart + 2), h2(restart + 2), y;
+    double* hdev = P->red_out + 128;
+    while (true) {
+        if (!std::isfinite(nr)) { status = set_error(TFDE_ENAN, "non-finite residual"); break; }
+        if (nr <= tol * nb) { status = TFDE_OK; break; }
+        if (loc.iters >= maxit) break;
+        // V_0 = P^{-1} r / beta
+        if ((st = apply_Pinv64(P, r, V, s))) return st;
+        double beta2;
+        if ((st = dot(P, V, V, &beta2, s))) return st;
+        const double beta = std::sqrt(beta2);
+        if (!(beta > 0.0) || !std::isfinite(beta)) { status = set_error(TFDE_EBREAKDOWN, "zero preconditioned residual"); break; }
+        launch_axpby_f64(N, 0.0, V, 1.0 / beta, V, s);
+        GivensLS ls(restart);
+        ls.g[0] = beta;
+        // cycle target: ask the preconditioned estimate for half the reduction
+        // the true residual still needs, corrected by the ratio observed before
+        const double ptarget = beta * (tol * nb / nr) * 0.5 / ratio;
+        int k = 0;
+        double est = beta;
+        for (int j = 0; j < restart && loc.iters < maxit; ++j) {
+            double* vj = V + (size_t)j * N;
+            double* w = V + (size_t)(j + 1) * N;
+            if ((st = apply_A64(P, TFDE_OP_A, vj, q, s))) return st;
+            if ((st = apply_Pinv64(P, q, w, s))) return st;
+            // CGS2: two rounds of h = V^T w, w -= V h
+            if ((st = dots64(P, j + 1, V, N, w, h.data(), s))) return st;
+            TFDE_CUDA_TRY(cudaMemcpyAsync(hdev, h.data(), (j + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
+            launch_multiaxpy_f64(N, j + 1, V, N, hdev, w, s);
+            if ((st = dots64(P, j + 1, V, N, w, h2.data(), s))) return st;
+            TFDE_CUDA_TRY(cudaMemcpyAsync(hdev, h2.data(), (j + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
+            launch_multiaxpy_f64(N, j + 1, V, N, hdev, w, s);
+            for (int i = 0; i <= j; ++i) h[i] += h2[i];
+            double ww;
+            if ((st = dot(P, w, w, &ww, s))) return st;
+            const double hn = std::sqrt(ww);
+            h[j + 1] = hn;
+            if (!std::isfinite(hn)) { status = set_error(TFDE_ENAN, "non-finite Arnoldi vector"); break; }
+            est = ls.add_column(j, h.data());
+            loc.iters++;
+            k = j + 1;
+            if (est <= ptarget || hn == 0.0) break;
+            launch_axpby_f64(N, 0.0, w, 1.0 / hn, w, s);
+        }
+        if (status == TFDE_ENAN) break;
+        loc.restarts++;
+        if (k > 0) {
+            ls.solve(k, y);
+            for (int i = 0; i < k; ++i) y[i] = -y[i];
+            TFDE_CUDA_TRY(cudaMemcpyAsync(hdev, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+            launch_multiaxpy_f64(N, k, V, N, hdev, x, s);  // x += V y
+        }
+        const double nr_old = nr;
+        if ((st = true_residual(P, b, x, r, &nr, s))) return st;
+        if (est > 0.0 && nr_old > 0.0) {
+            const double observed = (nr / nr_old) / (est / beta);
+            ratio = observed > 1.0 ? observed : 1.0;
+        }
+    }
+    loc.relres = nr / nb;
+    if (status == TFDE_ENOCONV) set_error(TFDE_ENOCONV, "PGMRES reached maxit");
+    loc.ms = (float)ms_since(t0);
+    if (info) *info = loc;
+    return status;
+}
+
+int cn_step64(tfde_problem* P, const double* u_prev, const double* F, const double* x0, double* u_next,
+              double tol, tfde_info* info, cudaStream_t s) {
+    double* b = P->w[tfde_problem::W_B];
+    int st = apply_A64(P, TFDE_OP_RHS, u_prev, b, s);
+    if (st) return st;
+    if (F) launch_axpby_f64(P->N, P->p.dt, F, 1.0, b, s);
+    const double* start = x0 ? x0 : u_prev;
+    if (start != u_next)
+        TFDE_CUDA_TRY(cudaMemcpyAsync(u_next, start, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (P->symmetric) return pcg64(P, b, u_next, tol, 10000, info, s);
+    return pgmres64(P, b, u_next, 20, tol, 10000, info, s);
+}
+
+}  // namespace tfde

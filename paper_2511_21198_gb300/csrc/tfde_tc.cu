@@ -1,0 +1,125 @@
+// Host side of the tcgen05 per-axis contraction: TMA tensor maps and launches.
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <string>
+
+#define TFDE_TC_KERNEL_IMPL
+#include "tfde_internal.h"
+#include "tfde_tc.h"
+
+namespace tfde {
+namespace tc {
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }
+    return fn;
+}
+
+int encode(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
+           const cuuint32_t* box, CUtensorMapSwizzle sw) {
+    auto fn = encode_fn();
+    if (!fn) return set_error(TFDE_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), dims, strides,
+                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(TFDE_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return TFDE_OK;
+}
+
+int g_num_sms = 0;
+
+}  // namespace
+
+int num_sms() {
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    return g_num_sms;
+}
+
+// Operator matrix [rows = n][cols = n] row-major BF16 -> A operand (K-major, 64B swizzle).
+int make_map_A(CUtensorMap* m, const __nv_bfloat16* base, int n) {
+    if (n % 8) return set_error(TFDE_EUNSUPPORTED, "tensor-core path needs n multiple of 8");
+    const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)n * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    return encode(m, base, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B);
+}
+
+// Vector plane viewed along `axis` -> B operand.
+int make_map_B(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis) {
+    const cuuint64_t n1 = n[0], n2 = n[1], n3 = n[2];
+    if (n[0] % 8) return set_error(TFDE_EUNSUPPORTED, "tensor-core path needs n1 multiple of 8");
+    if (axis == 0) {
+        const cuuint64_t dims[2] = {n1, n2 * n3};
+        const cuuint64_t strides[1] = {n1 * 2};
+        const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BN};
+        return encode(m, base, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B);
+    }
+    cuuint64_t C, K, P;
+    if (axis == 1) { C = n1; K = n2; P = n3; }
+    else { C = n1 * n2; K = n3; P = 1; }
+    const cuuint64_t dims[3] = {C, K, P};
+    const cuuint64_t strides[2] = {C * 2, C * K * 2};
+    const cuuint32_t box[3] = {64, (cuuint32_t)BK, 1};
+    return encode(m, base, 3, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+// Fill the geometry fields of Params for a contraction along `axis`.
+void set_geometry(Params& P, const int n[3], int axis) {
+    const long long n1 = n[0], n2 = n[1], n3 = n[2];
+    P.n = n[axis];
+    P.mhalves = (n[axis] + BM - 1) / BM;
+    P.n1 = n[0];
+    if (axis == 0) {
+        P.b_kmajor = 1;
+        P.lines = n2 * n3;
+        P.ntiles = (P.lines + BN - 1) / BN;
+        P.C = 0; P.nbc = 1; P.P = 1; P.nblocks = 0; P.plane = 0;
+    } else {
+        P.b_kmajor = 0;
+        if (axis == 1) { P.C = (int)n1; P.P = (int)n3; }
+        else { P.C = (int)(n1 * n2); P.P = 1; }
+        P.nbc = (P.C + 63) / 64;
+        P.nblocks = (long long)P.nbc * P.P;
+        P.ntiles = (P.nblocks + (BN / 64) - 1) / (BN / 64);
+        P.lines = (long long)P.C * P.P;
+        P.plane = (long long)P.C * n[axis];
+    }
+}
+
+bool attr_done = false;
+
+int launch(const Params& P, cudaStream_t s) {
+    if (!attr_done) {
+        if (cudaFuncSetAttribute(axis_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
+            cudaSuccess)
+            return set_error(TFDE_ECUDA, "cudaFuncSetAttribute(smem) failed");
+        attr_done = true;
+    }
+    const long long total = P.ntiles * P.mhalves;
+    long long grid = total < num_sms() ? total : num_sms();
+    if (grid < 1) grid = 1;
+    axis_gemm_kernel<<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(TFDE_ECUDA, std::string("axis_gemm_kernel launch: ") + cudaGetErrorString(e));
+    return TFDE_OK;
+}
+
+}  // namespace tc
+}  // namespace tfde

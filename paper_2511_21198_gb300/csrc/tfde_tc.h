@@ -1,0 +1,19 @@
+// Host interface of the tcgen05 per-axis contraction (tfde_tc.cu).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "tfde_tc_kernel.cuh"
+
+namespace tfde {
+namespace tc {
+
+int num_sms();
+int make_map_A(CUtensorMap* m, const __nv_bfloat16* base, int n);
+int make_map_B(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis);
+void set_geometry(Params& P, const int n[3], int axis);
+int launch(const Params& P, cudaStream_t s);
+
+}  // namespace tc
+}  // namespace tfde

@@ -1,0 +1,196 @@
+"""Thin ctypes binding of libtfde (C ABI declared in include/tfde.h).
+
+The functions keep the C names and only marshal arguments: device buffers are
+passed as torch CUDA tensors (float64, contiguous) or raw integer addresses,
+streams as torch.cuda.Stream, raw cudaStream_t integers or None (the current
+torch stream).  Every non-zero status raises TfdeError.  There is no CPU
+fallback: a missing library raises at load time.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, Structure, byref, c_char_p, c_double, c_float, c_int, c_void_p
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libtfde.so")
+
+TFDE_OK, TFDE_EINVAL, TFDE_ENOMEM, TFDE_ECUDA, TFDE_ENOCONV = 0, 1, 2, 3, 4
+TFDE_EBREAKDOWN, TFDE_ENAN, TFDE_ETIMEOUT, TFDE_EUNSUPPORTED = 5, 6, 7, 8
+STATUS_NAMES = {0: "TFDE_OK", 1: "TFDE_EINVAL", 2: "TFDE_ENOMEM", 3: "TFDE_ECUDA", 4: "TFDE_ENOCONV",
+                5: "TFDE_EBREAKDOWN", 6: "TFDE_ENAN", 7: "TFDE_ETIMEOUT", 8: "TFDE_EUNSUPPORTED"}
+TFDE_FP64, TFDE_MIXED = 0, 1
+TFDE_OP_A, TFDE_OP_RHS, TFDE_OP_FAST = 0, 1, 2
+
+
+class tfde_params(Structure):
+    _fields_ = [("n", c_int * 3), ("lo", c_double * 3), ("hi", c_double * 3), ("delta", c_double * 3),
+                ("kp", c_double * 3), ("km", c_double * 3), ("dt", c_double)]
+
+
+class tfde_info(Structure):
+    _fields_ = [("iters", c_int), ("restarts", c_int), ("refine_sweeps", c_int), ("fallback", c_int),
+                ("relres", c_double), ("relres0", c_double), ("ms", c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TfdeError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+EXPORTS = ["tfde_assemble", "tfde_destroy", "tfde_matvec", "tfde_precond", "tfde_pcg", "tfde_pgmres",
+           "tfde_cn_step", "tfde_source_example2", "tfde_coefficients", "tfde_host_coefficients",
+           "tfde_last_error", "tfde_version"]
+
+
+def load(path: str | None = None):
+    """Load libtfde.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with paper_2511_21198_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    vp = c_void_p
+    sig = {
+        "tfde_assemble": ([POINTER(tfde_params), c_int, vp, POINTER(vp)], c_int),
+        "tfde_destroy": ([vp], c_int),
+        "tfde_matvec": ([vp, c_int, vp, vp, vp], c_int),
+        "tfde_precond": ([vp, vp, vp, vp], c_int),
+        "tfde_pcg": ([vp, vp, vp, c_double, c_int, POINTER(tfde_info), vp], c_int),
+        "tfde_pgmres": ([vp, vp, vp, c_int, c_double, c_int, POINTER(tfde_info), vp], c_int),
+        "tfde_cn_step": ([vp, vp, vp, vp, vp, c_double, POINTER(tfde_info), vp], c_int),
+        "tfde_source_example2": ([vp, c_double, c_double, vp, vp], c_int),
+        "tfde_coefficients": ([vp, c_int, POINTER(c_double), POINTER(c_double), POINTER(c_double)], c_int),
+        "tfde_host_coefficients": ([POINTER(tfde_params), c_int, POINTER(c_double), POINTER(c_double),
+                                    POINTER(c_double), POINTER(c_double)], c_int),
+        "tfde_last_error": ([], c_char_p),
+        "tfde_version": ([], c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(st: int, where: str):
+    if st != TFDE_OK:
+        raise TfdeError(st, where, load().tfde_last_error().decode())
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_params(n, delta, kp, km, dt, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)) -> tfde_params:
+    if isinstance(n, int):
+        n = (n, n, n)
+    p = tfde_params()
+    for a in range(3):
+        p.n[a], p.lo[a], p.hi[a] = int(n[a]), float(lo[a]), float(hi[a])
+        p.delta[a], p.kp[a], p.km[a] = float(delta[a]), float(kp[a]), float(km[a])
+    p.dt = float(dt)
+    return p
+
+
+def tfde_assemble(params: tfde_params, precision: int = TFDE_FP64, stream=None) -> int:
+    h = c_void_p()
+    _check(load().tfde_assemble(byref(params), precision, _stream(stream), byref(h)), "tfde_assemble")
+    return h.value
+
+
+def tfde_destroy(prob: int) -> None:
+    _check(load().tfde_destroy(prob), "tfde_destroy")
+
+
+def tfde_matvec(prob: int, op: int, x, y, stream=None) -> None:
+    _check(load().tfde_matvec(prob, op, _ptr(x), _ptr(y), _stream(stream)), "tfde_matvec")
+
+
+def tfde_precond(prob: int, r, z, stream=None) -> None:
+    _check(load().tfde_precond(prob, _ptr(r), _ptr(z), _stream(stream)), "tfde_precond")
+
+
+def tfde_pcg(prob: int, b, x, tol: float, maxit: int, stream=None, check: bool = True) -> tfde_info:
+    info = tfde_info()
+    st = load().tfde_pcg(prob, _ptr(b), _ptr(x), tol, maxit, byref(info), _stream(stream))
+    if check:
+        _check(st, "tfde_pcg")
+    info.status = st
+    return info
+
+
+def tfde_pgmres(prob: int, b, x, restart: int, tol: float, maxit: int, stream=None,
+                check: bool = True) -> tfde_info:
+    info = tfde_info()
+    st = load().tfde_pgmres(prob, _ptr(b), _ptr(x), restart, tol, maxit, byref(info), _stream(stream))
+    if check:
+        _check(st, "tfde_pgmres")
+    info.status = st
+    return info
+
+
+def tfde_cn_step(prob: int, u_prev, F_half, x0, u_next, tol: float, stream=None,
+                 check: bool = True) -> tfde_info:
+    info = tfde_info()
+    st = load().tfde_cn_step(prob, _ptr(u_prev), _ptr(F_half), _ptr(x0), _ptr(u_next), tol,
+                             byref(info), _stream(stream))
+    if check:
+        _check(st, "tfde_cn_step")
+    info.status = st
+    return info
+
+
+def tfde_source_example2(prob: int, cP: float, cS: float, F, stream=None) -> None:
+    _check(load().tfde_source_example2(prob, cP, cS, _ptr(F), _stream(stream)), "tfde_source_example2")
+
+
+def tfde_coefficients(prob: int, axis: int, n_axis: int):
+    """Host copies of (q, lambda_tau, eta) for one axis."""
+    q = (c_double * (n_axis + 1))()
+    lam = (c_double * n_axis)()
+    eta = c_double()
+    _check(load().tfde_coefficients(prob, axis, q, lam, byref(eta)), "tfde_coefficients")
+    return list(q), list(lam), eta.value
+
+
+def tfde_host_coefficients(params: tfde_params, axis: int):
+    """Host-only (q, lambda_tau, lambda_mass, eta) of one axis; no GPU needed."""
+    n = params.n[axis]
+    q = (c_double * (n + 1))()
+    lt = (c_double * n)()
+    lm = (c_double * n)()
+    eta = c_double()
+    _check(load().tfde_host_coefficients(byref(params), axis, q, lt, lm, byref(eta)), "tfde_host_coefficients")
+    return list(q), list(lt), list(lm), eta.value
+
+
+def tfde_last_error() -> str:
+    return load().tfde_last_error().decode()
+
+
+def tfde_version() -> str:
+    return load().tfde_version().decode()

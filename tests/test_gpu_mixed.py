@@ -1,0 +1,136 @@
+"""GPU parity of the mixed-precision path (TFDE_MIXED): the split-BF16
+tcgen05 contractions against the oracle, and the FP64-refined solvers against
+dense / oracle solutions.  Grid sizes are multiples of 8 (the TMA stride rule)
+that span several 128-row / 256-line tiles with ragged tails."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import tfde_oracle as o
+import tfde_inputs as inp
+from gpu_helpers import relerr, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_2511_21198_gb300 import build
+    build.build()
+    from paper_2511_21198_gb300 import tfde
+    tfde.load()
+    return tfde
+
+
+def round_bf16(a):
+    """Round float64 values to the nearest BF16 (ties to even), via float32."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+SIZES = [
+    ((16, 16, 16), (0.5, 0.5, 0.5), (1.0,) * 3, (1.0,) * 3, 1 / 16),
+    ((64, 24, 40), (0.3, 0.6, 0.8), (1.0, 2.0, 1.5), (0.5, 2.0, 1.0), 0.05),
+    ((136, 8, 16), (0.7, 0.2, 0.9), (1.0,) * 3, (1.0,) * 3, 0.1),
+    ((8, 136, 24), (0.4, 0.9, 0.1), (2.0, 1.0, 0.5), (0.5, 1.0, 2.0), 0.2),
+    ((24, 16, 264), (0.6, 0.5, 0.35), (1.0,) * 3, (1.0,) * 3, 0.02),
+]
+
+
+@pytest.mark.parametrize("case", SIZES, ids=lambda c: "x".join(map(str, c[0])))
+def test_fast_matvec_and_precond(T, case):
+    n, d, kp, km, dt = case
+    h = T.tfde_assemble(T.make_params(n, d, kp, km, dt), T.TFDE_MIXED)
+    try:
+        op = o.Problem(n=n, delta=d, kp=kp, km=km, dt=dt)
+        v = inp.uniform_vector(op.shape, 41)
+        y = to_dev(np.zeros_like(v))
+        T.tfde_matvec(h, T.TFDE_OP_A | T.TFDE_OP_FAST, to_dev(v), y)
+        assert relerr(to_host(y), o.apply_A(op, v)) < 2e-4
+        T.tfde_matvec(h, T.TFDE_OP_RHS | T.TFDE_OP_FAST, to_dev(v), y)
+        assert relerr(to_host(y), o.rhs(op, v, None)) < 2e-4
+        # accurate (non-fast) operator of a mixed problem is FP64-exact
+        T.tfde_matvec(h, T.TFDE_OP_A, to_dev(v), y)
+        assert relerr(to_host(y), o.apply_A(op, v)) < 1e-13
+        # preconditioner: exact tau inverse within the BF16 rounding of S_n ...
+        T.tfde_precond(h, to_dev(v), y)
+        z = to_host(y)
+        tau = o.build_tau(op)
+        assert relerr(z, o.apply_Pinv(tau, v)) < 3e-2
+        # ... and tight against the same transform with S_n rounded to BF16
+        Sb = [round_bf16(S) for S in tau.S]
+        zb = o.apply_S_N(Sb, o.apply_S_N(Sb, v) / tau.Lam)
+        assert relerr(z, zb) < 2e-4
+    finally:
+        T.tfde_destroy(h)
+
+
+@pytest.mark.parametrize("n", [(16, 16, 16), (40, 32, 24)])
+def test_mixed_pcg_matches_dense_solution(T, n):
+    d, kp = (0.3, 0.6, 0.8), (1.0, 1.5, 2.0)
+    h = T.tfde_assemble(T.make_params(n, d, kp, kp, 0.1), T.TFDE_MIXED)
+    try:
+        op = o.Problem(n=n, delta=d, kp=kp, km=kp, dt=0.1)
+        b = inp.uniform_vector(op.shape, 51)
+        tau = o.build_tau(op)
+        xref, _ = o.pcg(lambda v: o.apply_A(op, v), lambda r: o.apply_Pinv(tau, r), b, np.zeros_like(b), 1e-14, 2000)
+        x = to_dev(np.zeros_like(b))
+        info = T.tfde_pcg(h, to_dev(b), x, 1e-12, 2000)
+        assert info.relres <= 1e-12 and info.refine_sweeps >= 1 and info.fallback == 0
+        assert relerr(to_host(x), xref) < 1e-10
+    finally:
+        T.tfde_destroy(h)
+
+
+def test_mixed_cn_step_tight_parity(T):
+    """One CN step from the same u^{m-1}: mixed solve to a 1e-12 true residual
+    matches the oracle's 1e-14 PCG solution to <= 1e-10 relative error."""
+    n = (32, 24, 16)
+    d, k = (0.7, 0.7, 0.7), (1.0,) * 3
+    h = T.tfde_assemble(T.make_params(n, d, k, k, 0.05), T.TFDE_MIXED)
+    try:
+        op = o.Problem(n=n, delta=d, kp=k, km=k, dt=0.05)
+        u0 = inp.smoothed_uniform(op.shape, 2)
+        F = o.source_cell_average(op, 0.025, "exp")
+        b = o.rhs(op, u0, F)
+        tau = o.build_tau(op)
+        xo, _ = o.pcg(lambda v: o.apply_A(op, v), lambda r: o.apply_Pinv(tau, r), b, u0, 1e-14, 2000)
+        un = to_dev(np.zeros_like(u0))
+        info = T.tfde_cn_step(h, to_dev(u0), to_dev(F), None, un, 1e-12)
+        assert info.relres <= 1e-12
+        assert relerr(to_host(un), xo) < 1e-10
+    finally:
+        T.tfde_destroy(h)
+
+
+def test_mixed_trajectory_n16(T):
+    """16^3 symmetric workload, 16 steps at tol 1e-8: every step meets the
+    true residual, and the final error against the manufactured solution
+    equals the oracle's."""
+    n, M = 16, 16
+    d, k = (0.5,) * 3, (1.0,) * 3
+    h = T.tfde_assemble(T.make_params((n,) * 3, d, k, k, 1.0 / M), T.TFDE_MIXED)
+    try:
+        op = o.Problem(n=(n,) * 3, delta=d, kp=k, km=k, dt=1.0 / M)
+        u = to_dev(o.exact_u(op, 0.0, "exp"))
+        un = to_dev(np.zeros(op.shape))
+        F = to_dev(np.zeros(op.shape))
+        for m in range(1, M + 1):
+            th = (m - 0.5) * op.dt
+            T.tfde_source_example2(h, -math.exp(-th), -math.exp(-th), F)
+            info = T.tfde_cn_step(h, u, F, None, un, 1e-8)
+            assert info.relres <= 1e-8
+            u, un = un, u
+        r = o.cn_solve(op, o.exact_u(op, 0.0, "exp"), M, tol=1e-12, phi="exp")
+        assert relerr(to_host(u), r.u) < 1e-6
+    finally:
+        T.tfde_destroy(h)
+
+
+def test_mixed_rejects_unsupported_sizes(T):
+    with pytest.raises(T.TfdeError) as e:
+        T.tfde_assemble(T.make_params((12, 16, 16), (0.5,) * 3, (1.0,) * 3, (1.0,) * 3, 0.1), T.TFDE_MIXED)
+    assert e.value.status == T.TFDE_EUNSUPPORTED
