@@ -624,3 +624,25 @@ def cn_solve(prob: Problem, u0: np.ndarray, M: int, *, tol: float, phi: str | No
         iters.append(info.iters)
         relres.append(info.relres)
     return CNResult(u=u, iters=iters, relres=relres)
+
+
+def apply_A_at(prob: Problem, v: np.ndarray, points, op: str = "A") -> np.ndarray:
+    """(A v) or (RHS operator v) at the given (k, j, i) points, one by one, from
+    the Kronecker form of Eq. (linear_sys): every term is a product of three
+    1-D rows, so each output needs only the <= 3 x 3 x n block of v under the
+    non-zero pattern of its rows (the mass rows are tridiagonal)."""
+    sgn = 1.0 if op == "A" else -1.0
+    M, B, e = prob.M, prob.B, prob.eta
+    out = np.empty(len(points))
+    for idx, (k, j, i) in enumerate(points):
+        terms = [(1.0, M[2][k], M[1][j], M[0][i]),
+                 (sgn * e[0], M[2][k], M[1][j], B[0][i]),
+                 (sgn * e[1], M[2][k], B[1][j], M[0][i]),
+                 (sgn * e[2], B[2][k], M[1][j], M[0][i])]
+        total = 0.0
+        for c, rz, ry, rx in terms:
+            kk, jj, ii = np.nonzero(rz)[0], np.nonzero(ry)[0], np.nonzero(rx)[0]
+            blk = v[np.ix_(kk, jj, ii)]
+            total += c * np.einsum("a,b,c,abc->", rz[kk], ry[jj], rx[ii], blk)
+        out[idx] = total
+    return out
