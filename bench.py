@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""Benchmark of the CN-FV tau-preconditioned solver on one GB300.
+
+Metric: Crank-Nicolson steps per second on the n = 256 symmetric workload
+(16.8 M unknowns, alpha = beta = gamma = 0.7, k+ = k- = 1, dt = 1/20,
+manufactured exp(-t) source, true relative residual 1e-8), mixed precision
+(split-BF16 tcgen05 inner PCG, FP64 refinement, previous-step initial guess),
+with the plain-FP64 GPU path on the same GPU reported beside it.
+
+One bench step = one CN step: the source cell averages at t_{m-1/2}, the RHS
+(2 A_N - A) u^{m-1} + dt F, and the refined PCG solve.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (the single-instance solve does not shard without a collective);
+value = N * K / max-over-ranks time.  --impl reference times the CPU oracle
+on the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import tfde_inputs as inp  # noqa: E402
+
+METRIC = "CN steps/s at 3D N=256, mixed+warm-start vs plain FP64, 1e-8 rel residual"
+UNIT = "CN steps/s"
+WORKLOAD = "n256_sym_exp"
+KERNEL_SOURCES = ["paper_2511_21198_gb300/csrc/tfde_tc_kernel.cuh"]
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=None, help="override the grid size (testing only)")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ----------------------------------------------------------------- distributed
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    if world <= 1:
+        return False
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend=backend, init_method="env://")
+    return True
+
+
+def barrier(on):
+    if on:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x: float, on: bool, device=None) -> float:
+    """Maximum of a host scalar over all ranks (identity without a process group)."""
+    if not on:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(steps_per_rank: int, world: int, max_seconds: float) -> float:
+    """Whole-job throughput: all ranks' steps over the slowest rank's time."""
+    return steps_per_rank * world / max_seconds
+
+
+# ---------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------- helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d.get("hbm_gbs"), "bf16_tflops": d.get("bf16_tflops"),
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained"), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the tcgen05 kernel from the committed ncu
+    summary, or None when absent or taken on a different kernel source."""
+    p = os.path.join(ROOT, "profiles", "axis_gemm_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_sha") != kernel_hash():
+        return None
+    return d.get("dram_bytes_per_launch_n256")
+
+
+def source_factors(t: float):
+    """Time factors (cP, cS) = (phi'(t), -phi(t)) of the exp(-t) manufactured source."""
+    e = math.exp(-t)
+    return -e, -e
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_steps(n, delta, k, dt, tol, budget_s, max_steps=None):
+    """Run oracle CN steps from the manufactured initial data until the time
+    budget is used (at least one step); returns (steps, seconds)."""
+    from oracle import tfde_oracle as o
+    prob = o.Problem(n=(n, n, n), delta=delta, kp=k, km=k, dt=dt)
+    tau = o.build_tau(prob)
+    u = inp.example2_initial(n)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        th = (steps + 0.5) * dt
+        F = o.source_cell_average(prob, th, "exp")
+        b = o.rhs(prob, u, F)
+        u, _ = o.pcg(lambda v: o.apply_A(prob, v), lambda r: o.apply_Pinv(tau, r), b, u, tol, 10 ** 6)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_steps and steps >= max_steps):
+            return steps, el
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    from paper_2511_21198_gb300 import tfde as T
+
+    world, rank, local = dist_env()
+    on = dist_init(world, "nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    T.load()
+    W = inp.WORKLOADS[WORKLOAD]
+    n = args.n or W["n"]
+    M = W["M"]
+    dt = 1.0 / M
+    tol = W["tol"]
+    params = T.make_params((n, n, n), W["delta"], W["kp"], W["km"], dt)
+    stream = torch.cuda.current_stream(dev)
+    tf = source_factors
+
+    def run_steps(h, u, un, F, m0, count):
+        iters = sweeps = 0
+        relres = 0.0
+        for i in range(count):
+            th = (m0 + i + 0.5) * dt
+            cP, cS = tf(th)
+            T.tfde_source_example2(h, cP, cS, F, stream)
+            info = T.tfde_cn_step(h, u, F, None, un, tol, stream)
+            iters += info.iters
+            sweeps += info.refine_sweeps
+            relres = max(relres, info.relres)
+            u, un = un, u
+        return u, un, iters, sweeps, relres
+
+    u0 = torch.from_numpy(inp.example2_initial(n)).to(dev)
+    # ---- mixed precision (the metric)
+    h = T.tfde_assemble(params, T.TFDE_MIXED, stream)
+    u, un, F = u0.clone(), torch.empty_like(u0), torch.empty_like(u0)
+    u, un, _, _, _ = run_steps(h, u, un, F, 0, args.warmup)
+    torch.cuda.synchronize()
+    barrier(on)
+    T.tfde_stats_reset(time_tc=True)
+    clk = ClockSampler(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    u, un, iters, sweeps, relres = run_steps(h, u, un, F, args.warmup, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    barrier(on)
+    ms = e0.elapsed_time(e1)
+    st = T.tfde_stats_get()
+    ms_max = reduce_max(ms, on, dev)
+    value = aggregate_value(args.steps, world, ms_max / 1e3)
+    t_end = (args.warmup + args.steps) * dt
+    exact = torch.from_numpy(inp.example2_initial(n, math.exp(-t_end))).to(dev)
+    err = float((u - exact).abs().max() / exact.abs().max())
+
+    # ---- end to end through the C ABI with host buffers (copies timed)
+    e2e = None
+    if not args.no_e2e:
+        host_u = u.cpu().pin_memory()
+        host_out = torch.empty_like(host_u).pin_memory()
+        m0 = args.warmup + args.steps
+        torch.cuda.synchronize()
+        barrier(on)
+        e0.record(stream)
+        for i in range(args.steps):
+            u.copy_(host_u, non_blocking=True)
+            th = (m0 + i + 0.5) * dt
+            cP, cS = tf(th)
+            T.tfde_source_example2(h, cP, cS, F, stream)
+            T.tfde_cn_step(h, u, F, None, un, tol, stream)
+            host_out.copy_(un, non_blocking=True)
+            host_u, host_out = host_out, host_u
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(on)
+        ms_e = reduce_max(e0.elapsed_time(e1), on, dev)
+        nbytes = u.numel() * u.element_size()
+        e2e = {"value": aggregate_value(args.steps, world, ms_e / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    T.tfde_destroy(h)
+
+    # ---- plain FP64 path on the same GPU (comparison)
+    fp64 = None
+    if args.fp64_steps > 0:
+        h64 = T.tfde_assemble(params, T.TFDE_FP64, stream)
+        u, un = u0.clone(), torch.empty_like(u0)
+        u, un, _, _, _ = run_steps(h64, u, un, F, 0, 1)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        u, un, it64, _, _ = run_steps(h64, u, un, F, 1, args.fp64_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = reduce_max(e0.elapsed_time(e1), on, dev)
+        fp64 = {"value": aggregate_value(args.fp64_steps, world, ms64 / 1e3), "unit": UNIT,
+                "ms_per_step": ms64 / args.fp64_steps, "iters_per_step": it64 / args.fp64_steps,
+                "steps": args.fp64_steps}
+        T.tfde_destroy(h64)
+
+    # ---- roofline of the dominant kernel (tcgen05 per-axis contraction)
+    peaks = measured_peaks()
+    roof = None
+    if st.tc_timed > 0 and st.tc_ms > 0:
+        achieved = st.tc_bytes / (st.tc_ms / 1e3) / 1e9
+        tr = recorded_traffic()
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": tr,
+                "kernel": "tfde::tc::axis_gemm_kernel", "peak_source": peaks["source"] + " (hbm_gbs)",
+                "launches": int(st.tc_launches), "avg_launch_us": 1e3 * st.tc_ms / st.tc_timed,
+                "algorithmic_bytes_per_launch": st.tc_bytes / st.tc_launches,
+                "tensor_tflops": st.tc_flops / (st.tc_ms / 1e3) / 1e12,
+                "kernel_share_of_step": st.tc_ms / ms}
+
+    # ---- CPU baseline (oracle), rank 0 at N = 1 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        steps_c, sec = oracle_steps(n, W["delta"], W["kp"], dt, tol, args.cpu_seconds)
+        cpu = {"value": steps_c / sec, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{steps_c} CN step(s) of the n={n} workload by the numpy FP64 oracle "
+                         f"(PCG, x0 = u^(m-1)), {sec:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16-split/fp32 inner, fp64 refinement",
+            "data": "synthetic: manufactured solution exp(-t) x^2(1-x)^2 y^2(1-y)^2 z^2(1-z)^2",
+            "config": {"workload": WORKLOAD, "n": n, "unknowns": n ** 3, "delta": list(W["delta"]),
+                       "k_plus": list(W["kp"]), "k_minus": list(W["km"]), "dt": dt, "tol": tol,
+                       "solver": "PCG(tau) inner FP32 / split-BF16 tcgen05, FP64 iterative refinement",
+                       "initial_guess": "previous step u^(m-1)",
+                       "l2": "inputs larger than L2 (each FP64 vector 134 MB, working set > 2 GB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st.kernel_launches),
+            "clocks": clocks, "fp64_path": fp64,
+            "iters_per_step": iters / args.steps, "refine_sweeps_per_step": sweeps / args.steps,
+            "max_relres": relres, "max_rel_err_vs_exact": err,
+        }
+        print(json.dumps(line), flush=True)
+    if on:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------- reference arm
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    W = inp.WORKLOADS[WORKLOAD]
+    n = args.n or W["n"]
+    dt = 1.0 / W["M"]
+    # warm-up steps untimed, then timed steps, all bounded by a few minutes
+    budget = 180.0
+    t0 = time.perf_counter()
+    oracle_steps(n, W["delta"], W["kp"], dt, W["tol"], 0.0, max_steps=max(1, min(args.warmup, 1)))
+    per = time.perf_counter() - t0
+    k = max(1, min(args.steps, int(budget / max(per, 1e-9))))
+    steps, sec = oracle_steps(n, W["delta"], W["kp"], dt, W["tol"], 1e30, max_steps=k)
+    value = steps / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": steps, "warmup": 1, "ms_per_step": 1e3 * sec / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "unknowns": n ** 3},
+            "cpu_baseline": {"kind": "oracle", "cores": cpu_cores(), "value": value, "unit": UNIT,
+                             "sample": f"{steps} CN step(s) of the n={n} workload (numpy FP64 oracle)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

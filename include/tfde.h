@@ -179,6 +179,26 @@ int tfde_coefficients(const tfde_problem* prob, int axis, double* q, double* lam
 int tfde_host_coefficients(const tfde_params* params, int axis, double* q, double* lam_tau, double* lam_mass,
                            double* eta);
 
+/* Counters of the library's own GPU work (process-wide). */
+typedef struct {
+    unsigned long long kernel_launches;  /* every kernel this library launched            */
+    unsigned long long tc_launches;      /* tcgen05 per-axis contraction launches          */
+    double tc_ms;        /* summed CUDA-event duration of those launches (timing enabled) */
+    double tc_bytes;     /* their algorithmic bytes: operand planes read + output written */
+    double tc_flops;     /* their tensor-core flops (2 x rows x k x lines per BF16 product) */
+    unsigned long long tc_timed;         /* launches covered by tc_ms                      */
+} tfde_stats;
+
+/*
+ * tfde_stats_reset -- zero the counters; `time_tc` != 0 additionally brackets
+ * every tcgen05 contraction launch with a CUDA event pair on its stream so
+ * that tc_ms is the sum of their device durations.  Not thread-safe.
+ */
+int tfde_stats_reset(int time_tc);
+
+/* tfde_stats_get -- synchronise the device and copy the counters to *out. */
+int tfde_stats_get(tfde_stats* out);
+
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* tfde_last_error(void);
 

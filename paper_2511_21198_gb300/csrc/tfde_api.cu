@@ -3,6 +3,7 @@
 #include <string>
 
 #include "tfde_internal.h"
+#include "tfde_stats.h"
 
 namespace tfde {
 const char* last_error_text();
@@ -152,6 +153,13 @@ int tfde_host_coefficients(const tfde_params* params, int axis, double* q, doubl
                            double* eta) {
     if (!params) return set_error(TFDE_EINVAL, "NULL params");
     return host_coefficients(params, axis, q, lam_tau, lam_mass, eta);
+}
+
+int tfde_stats_reset(int time_tc) { return stats_reset(time_tc); }
+
+int tfde_stats_get(tfde_stats* out) {
+    if (!out) return set_error(TFDE_EINVAL, "NULL stats");
+    return stats_get(out);
 }
 
 const char* tfde_last_error(void) { return last_error_text(); }

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 
 #include "tfde_internal.h"
+#include "tfde_stats.h"
 #include "tfde_mixed.h"
 
 namespace tfde {
@@ -140,33 +141,42 @@ inline int grid_for(long long N) {
 }  // namespace
 
 void launch_dot32(size_t N, const float* a, const float* b, double* part, int nblk, cudaStream_t s) {
+    stats_count_launch();
     dot32_kernel<<<nblk, kT, 0, s>>>((long long)N, a, b, part);
 }
 void launch_cg_update32(size_t N, const double* coef, const float* p, const float* q, float* x, float* r,
                         __nv_bfloat16* rh, __nv_bfloat16* rl, double* part, int nblk, cudaStream_t s) {
+    stats_count_launch();
     cg_update32_kernel<<<nblk, kT, 0, s>>>((long long)N, coef, p, q, x, r, rh, rl, part);
 }
 void launch_xpay32(size_t N, const double* coef, const float* z, float* p, __nv_bfloat16* ph, __nv_bfloat16* pl,
                    cudaStream_t s) {
+    stats_count_launch();
     xpay32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, coef, z, p, ph, pl);
 }
 void launch_scale64to32(size_t N, const double* r64, double sc, float* r32, __nv_bfloat16* rh, __nv_bfloat16* rl,
                         float* x32, cudaStream_t s) {
+    stats_count_launch();
     scale64to32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, r64, sc, r32, rh, rl, x32);
 }
 void launch_split32(size_t N, const float* v, __nv_bfloat16* h, __nv_bfloat16* l, cudaStream_t s) {
+    stats_count_launch();
     split32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, v, h, l);
 }
 void launch_split64(size_t N, const double* v, double sc, __nv_bfloat16* h, __nv_bfloat16* l, cudaStream_t s) {
+    stats_count_launch();
     split64_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, v, sc, h, l);
 }
 void launch_add32to64(size_t N, double sc, const float* d, double* x, cudaStream_t s) {
+    stats_count_launch();
     add32to64_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, sc, d, x);
 }
 void launch_widen32(size_t N, const float* v, double sc, double* y, cudaStream_t s) {
+    stats_count_launch();
     widen32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, v, sc, y);
 }
 void launch_ratio(const double* num, const double* den, double* coef, cudaStream_t s) {
+    stats_count_launch();
     ratio_kernel<<<1, 1, 0, s>>>(num, den, coef);
 }
 

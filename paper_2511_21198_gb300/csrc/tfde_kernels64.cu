@@ -3,6 +3,7 @@
 // preconditioner (Eq. (diag_tau_pre)), and the Krylov vector kernels and
 // deterministic reductions shared by both precisions.
 #include "tfde_internal.h"
+#include "tfde_stats.h"
 
 namespace tfde {
 namespace {
@@ -269,56 +270,67 @@ int reduction_blocks(size_t N) {
 
 void launch_axis_gemm_f64(const double* Mat, const double* X, double* Y, const AxisView& v, double alpha,
                           const double* Z, double beta, cudaStream_t s) {
+    stats_count_launch();
     dim3 grid((unsigned)((v.lines + BN - 1) / BN), (unsigned)((v.n + BM - 1) / BM));
     axis_gemm_f64_kernel<<<grid, kThreads, 0, s>>>(Mat, X, Y, v, alpha, Z, beta);
 }
 
 void launch_axis_stencil_f64(const double* X, double* Y, const AxisView& v, double beta, const double* W,
                              double gamma, cudaStream_t s) {
+    stats_count_launch();
     const long long N = v.lines * v.n;
     axis_stencil_f64_kernel<<<grid_for(N), kThreads, 0, s>>>(X, Y, v, N, beta, W, gamma);
 }
 
 void launch_lambda_scale_f64(const double* x, double* y, const double* lam, const int n[3], const double c[3],
                              int invert, cudaStream_t s) {
+    stats_count_launch();
     const long long N = (long long)n[0] * n[1] * n[2];
     lambda_scale_f64_kernel<<<grid_for(N), kThreads, 0, s>>>(x, y, lam, n[0], n[1], n[2], c[0], c[1], c[2],
                                                               invert);
 }
 
 void launch_axpby_f64(size_t N, double a, const double* x, double b, double* y, cudaStream_t s) {
+    stats_count_launch();
     axpby_f64_kernel<<<grid_for((long long)N), kThreads, 0, s>>>((long long)N, a, x, b, y);
 }
 
 void launch_axpbypz_f64(size_t N, double a, const double* x, double b, const double* y, double* z,
                         cudaStream_t s) {
+    stats_count_launch();
     axpbypz_f64_kernel<<<grid_for((long long)N), kThreads, 0, s>>>((long long)N, a, x, b, y, z);
 }
 
 void launch_cg_update_f64(size_t N, double alpha, const double* p, const double* q, double* x, double* r,
                           double* part, int nblk, cudaStream_t s) {
+    stats_count_launch();
     cg_update_f64_kernel<<<nblk, kThreads, 0, s>>>((long long)N, alpha, p, q, x, r, part);
 }
 
 void launch_multidot_f64(size_t N, int m, const double* V, size_t ldv, const double* w, double* part, int nblk,
                          cudaStream_t s) {
+    stats_count_launch();
     for (int m0 = 0; m0 < m; m0 += 8) {
         const int mc = (m - m0) < 8 ? (m - m0) : 8;
+        if (m0 > 0) stats_count_launch();
         multidot_f64_kernel<8><<<nblk, kThreads, 0, s>>>((long long)N, m0, mc, V, (long long)ldv, w, part);
     }
 }
 
 void launch_multiaxpy_f64(size_t N, int m, const double* V, size_t ldv, const double* h, double* w,
                           cudaStream_t s) {
+    stats_count_launch();
     multiaxpy_f64_kernel<<<grid_for((long long)N), kThreads, 0, s>>>((long long)N, m, V, (long long)ldv, h, w);
 }
 
 void launch_reduce_finish(const double* part, int nblk, int m, double* out, cudaStream_t s) {
+    stats_count_launch();
     reduce_finish_kernel<<<m, 32, 0, s>>>(part, nblk, m, out);
 }
 
 void launch_source_assemble_f64(const double* oned, const int n[3], double cP, double cS, double* F,
                                 cudaStream_t s) {
+    stats_count_launch();
     const long long N = (long long)n[0] * n[1] * n[2];
     source_assemble_f64_kernel<<<grid_for(N), kThreads, 0, s>>>(oned, n[0], n[1], n[2], cP, cS, F);
 }

@@ -98,7 +98,15 @@ int run_gemm(const tfde_problem* P, int axis, const SegSpec* segs, int nseg, int
     }
     prm.err = M->err;
     M->gemm_launches++;
-    return tc::launch(prm, s);
+    // algorithmic traffic: each operand plane pair read once, the output written
+    // once (4 bytes per element either way), the operator matrices read once
+    const double N = (double)P->N, nax = (double)P->n[axis];
+    double bytes = 4.0 * N, flops = 0.0;
+    for (int g = 0; g < nseg; ++g) {
+        bytes += 4.0 * N + 2.0 * nax * nax * prm.seg[g].na;
+        flops += 2.0 * prm.seg[g].npair * nax * N;
+    }
+    return tc::launch(prm, s, bytes, flops);
 }
 
 // q32 = A p (op A) or the RHS operator, p given as the split plane pair PL_P.

@@ -1,0 +1,73 @@
+// Process-wide counters of the library's GPU work (tfde_stats_* in tfde.h).
+#include <vector>
+
+#include "tfde_internal.h"
+#include "tfde_stats.h"
+
+namespace tfde {
+
+namespace {
+struct EvPair {
+    cudaEvent_t a, b;
+};
+tfde_stats g_stats{};
+bool g_time_tc = false;
+std::vector<EvPair> g_pending, g_pool;
+
+void harvest(bool all) {
+    size_t keep = all ? 0 : g_pending.size() / 2;
+    size_t done = g_pending.size() - keep;
+    for (size_t i = 0; i < done; ++i) {
+        float ms = 0.f;
+        cudaEventSynchronize(g_pending[i].b);
+        if (cudaEventElapsedTime(&ms, g_pending[i].a, g_pending[i].b) == cudaSuccess) {
+            g_stats.tc_ms += ms;
+            g_stats.tc_timed++;
+        }
+        g_pool.push_back(g_pending[i]);
+    }
+    g_pending.erase(g_pending.begin(), g_pending.begin() + done);
+}
+}  // namespace
+
+void stats_count_launch(unsigned n) { g_stats.kernel_launches += n; }
+
+void* stats_tc_begin(cudaStream_t s) {
+    g_stats.kernel_launches++;
+    g_stats.tc_launches++;
+    if (!g_time_tc) return nullptr;
+    if (g_pending.size() > 4096) harvest(false);
+    EvPair e;
+    if (!g_pool.empty()) {
+        e = g_pool.back();
+        g_pool.pop_back();
+    } else {
+        cudaEventCreate(&e.a);
+        cudaEventCreate(&e.b);
+    }
+    cudaEventRecord(e.a, s);
+    g_pending.push_back(e);
+    return reinterpret_cast<void*>(1);
+}
+
+void stats_tc_end(void* tok, cudaStream_t s, double bytes, double flops) {
+    g_stats.tc_bytes += bytes;
+    g_stats.tc_flops += flops;
+    if (tok) cudaEventRecord(g_pending.back().b, s);
+}
+
+int stats_reset(int time_tc) {
+    harvest(true);
+    g_stats = tfde_stats{};
+    g_time_tc = time_tc != 0;
+    return TFDE_OK;
+}
+
+int stats_get(tfde_stats* out) {
+    cudaDeviceSynchronize();
+    harvest(true);
+    *out = g_stats;
+    return TFDE_OK;
+}
+
+}  // namespace tfde

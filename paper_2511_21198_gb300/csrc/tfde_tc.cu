@@ -7,6 +7,7 @@
 #define TFDE_TC_KERNEL_IMPL
 #include "tfde_internal.h"
 #include "tfde_tc.h"
+#include "tfde_stats.h"
 
 namespace tfde {
 namespace tc {
@@ -105,7 +106,7 @@ void set_geometry(Params& P, const int n[3], int axis) {
 
 bool attr_done = false;
 
-int launch(const Params& P, cudaStream_t s) {
+int launch(const Params& P, cudaStream_t s, double bytes, double flops) {
     if (!attr_done) {
         if (cudaFuncSetAttribute(axis_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
             cudaSuccess)
@@ -115,8 +116,10 @@ int launch(const Params& P, cudaStream_t s) {
     const long long total = P.ntiles * P.mhalves;
     long long grid = total < num_sms() ? total : num_sms();
     if (grid < 1) grid = 1;
+    void* tok = stats_tc_begin(s);
     axis_gemm_kernel<<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(P);
     cudaError_t e = cudaGetLastError();
+    stats_tc_end(tok, s, bytes, flops);
     if (e != cudaSuccess) return set_error(TFDE_ECUDA, std::string("axis_gemm_kernel launch: ") + cudaGetErrorString(e));
     return TFDE_OK;
 }

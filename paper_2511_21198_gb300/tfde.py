@@ -36,6 +36,15 @@ class tfde_info(Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class tfde_stats(Structure):
+    _fields_ = [("kernel_launches", ctypes.c_ulonglong), ("tc_launches", ctypes.c_ulonglong),
+                ("tc_ms", c_double), ("tc_bytes", c_double), ("tc_flops", c_double),
+                ("tc_timed", ctypes.c_ulonglong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class TfdeError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
@@ -46,7 +55,7 @@ _lib = None
 
 EXPORTS = ["tfde_assemble", "tfde_destroy", "tfde_matvec", "tfde_precond", "tfde_pcg", "tfde_pgmres",
            "tfde_cn_step", "tfde_source_example2", "tfde_coefficients", "tfde_host_coefficients",
-           "tfde_last_error", "tfde_version"]
+           "tfde_stats_reset", "tfde_stats_get", "tfde_last_error", "tfde_version"]
 
 
 def load(path: str | None = None):
@@ -71,6 +80,8 @@ def load(path: str | None = None):
         "tfde_coefficients": ([vp, c_int, POINTER(c_double), POINTER(c_double), POINTER(c_double)], c_int),
         "tfde_host_coefficients": ([POINTER(tfde_params), c_int, POINTER(c_double), POINTER(c_double),
                                     POINTER(c_double), POINTER(c_double)], c_int),
+        "tfde_stats_reset": ([c_int], c_int),
+        "tfde_stats_get": ([POINTER(tfde_stats)], c_int),
         "tfde_last_error": ([], c_char_p),
         "tfde_version": ([], c_char_p),
     }
@@ -186,6 +197,16 @@ def tfde_host_coefficients(params: tfde_params, axis: int):
     eta = c_double()
     _check(load().tfde_host_coefficients(byref(params), axis, q, lt, lm, byref(eta)), "tfde_host_coefficients")
     return list(q), list(lt), list(lm), eta.value
+
+
+def tfde_stats_reset(time_tc: bool = False) -> None:
+    _check(load().tfde_stats_reset(1 if time_tc else 0), "tfde_stats_reset")
+
+
+def tfde_stats_get() -> tfde_stats:
+    st = tfde_stats()
+    _check(load().tfde_stats_get(byref(st)), "tfde_stats_get")
+    return st
 
 
 def tfde_last_error() -> str:

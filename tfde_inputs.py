@@ -59,3 +59,14 @@ WORKLOADS = {
     "n256_sym_exp": dict(n=256, delta=(0.7, 0.7, 0.7), kp=(1.0,) * 3, km=(1.0,) * 3, M=20,
                          source="exp", tol=1e-8),
 }
+
+
+def example2_initial(n, phi0: float = 1.0) -> np.ndarray:
+    """Nodal values phi0 * P(x) P(y) P(z), P(s) = s^2 (1-s)^2, at the interior
+    nodes s_p = p/(n_a+1) of (0,1)^3: the initial data of the manufactured
+    workloads (problem data, shape (n3, n2, n1))."""
+    if isinstance(n, int):
+        n = (n, n, n)
+    ax = [np.arange(1, m + 1, dtype=np.float64) / (m + 1) for m in n]
+    Px, Py, Pz = (a * a * (1.0 - a) ** 2 for a in ax)
+    return phi0 * Pz[:, None, None] * Py[None, :, None] * Px[None, None, :]
