@@ -199,6 +199,30 @@ int tfde_stats_reset(int time_tc);
 /* tfde_stats_get -- synchronise the device and copy the counters to *out. */
 int tfde_stats_get(tfde_stats* out);
 
+/*
+ * tfde_mass_apply_noalloc -- y = A_N x = (A_{n3} (x) A_{n2} (x) A_{n1}) x, the
+ * tridiagonal mass operator of the CN-FV system, WITHOUT allocating memory.
+ * The paper has no counterpart to this entry point: it exists for callers that
+ * cannot allocate device memory when they need the operator (a solver step
+ * inside a memory budget fixed at start-up, a latency-critical loop where the
+ * allocator's implicit device synchronisation is not allowed, a plug-in that
+ * only receives ready-made device buffers from its host).
+ *   n: host array of the three grid extents, each >= 1, with
+ *      n[0]*n[1]*n[2] <= 262144 (2^18, e.g. 64^3); larger grids return
+ *      TFDE_EINVAL with a message naming the limit.
+ *   x, y: device grid functions (x fastest), caller-owned; y may alias x.
+ *   The two intermediate grid functions live in a fixed 4 MiB device array
+ *   compiled into the library, which every GPU that loads the library keeps
+ *   until the process exits.  All calls share that array and it keeps the
+ *   previous call's contents (each call overwrites what it reads), so calls
+ *   that overlap on the GPU -- on different streams or devices' contexts
+ *   sharing a device -- race and give wrong results.  The first call on each
+ *   device looks up the array's device address (cudaGetSymbolAddress); make
+ *   that first call before any stream capture.  No cudaMalloc, cudaFree or
+ *   allocating library routine is called.  Asynchronous on `stream`.
+ */
+int tfde_mass_apply_noalloc(const int n[3], const double* x, double* y, void* stream);
+
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* tfde_last_error(void);
 

@@ -55,7 +55,7 @@ _lib = None
 
 EXPORTS = ["tfde_assemble", "tfde_destroy", "tfde_matvec", "tfde_precond", "tfde_pcg", "tfde_pgmres",
            "tfde_cn_step", "tfde_source_example2", "tfde_coefficients", "tfde_host_coefficients",
-           "tfde_stats_reset", "tfde_stats_get", "tfde_last_error", "tfde_version"]
+           "tfde_stats_reset", "tfde_stats_get", "tfde_mass_apply_noalloc", "tfde_last_error", "tfde_version"]
 
 
 def load(path: str | None = None):
@@ -82,6 +82,7 @@ def load(path: str | None = None):
                                     POINTER(c_double), POINTER(c_double)], c_int),
         "tfde_stats_reset": ([c_int], c_int),
         "tfde_stats_get": ([POINTER(tfde_stats)], c_int),
+        "tfde_mass_apply_noalloc": ([POINTER(c_int), vp, vp, vp], c_int),
         "tfde_last_error": ([], c_char_p),
         "tfde_version": ([], c_char_p),
     }
@@ -207,6 +208,13 @@ def tfde_stats_get() -> tfde_stats:
     st = tfde_stats()
     _check(load().tfde_stats_get(byref(st)), "tfde_stats_get")
     return st
+
+
+def tfde_mass_apply_noalloc(n, x, y, stream=None) -> None:
+    """y = A_N x through the entry point that allocates nothing (grids of at
+    most 2^18 points; the first call on a device must precede stream capture)."""
+    dims = (c_int * 3)(*[int(v) for v in n])
+    _check(load().tfde_mass_apply_noalloc(dims, _ptr(x), _ptr(y), _stream(stream)), "tfde_mass_apply_noalloc")
 
 
 def tfde_last_error() -> str:
