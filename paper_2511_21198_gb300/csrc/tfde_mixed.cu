@@ -213,7 +213,7 @@ int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaSt
 int accurate_residual(const tfde_problem* P, const double* b, const double* x, double* r, double* nr,
                       cudaStream_t s) {
     double* q = P->w[tfde_problem::W_Q];
-    int st = apply_A64(P, TFDE_OP_A, x, q, s);
+    int st = accurate_apply(P, TFDE_OP_A, x, q, s);
     if (st) return st;
     launch_axpbypz_f64(P->N, 1.0, b, -1.0, q, r, s);
     double rr;
@@ -271,6 +271,12 @@ int mixed_init(tfde_problem* P, cudaStream_t s) {
         int st = tc::make_map_A(&M->amap[om], M->mat[om], n);
         if (st) return st;
     }
+    {
+        std::vector<double> etaB[3];
+        for (int a = 0; a < 3; ++a) etaB[a] = dense_etaB(P, a);
+        int st = oz_init(P, etaB, s);
+        if (st) return st;
+    }
     // workspace planes and their tensor maps
     for (int pl = 0; pl < NPL; ++pl) {
         MX_TRY(cudaMalloc((void**)&M->hi[pl], N * sizeof(__nv_bfloat16)));
@@ -324,6 +330,7 @@ void mixed_free(tfde_problem* P) {
         cudaFree(M->lo[pl]);
     }
     for (auto& v : M->f) cudaFree(v);
+    oz_free(M);
     cudaFree(M->lam);
     cudaFree(M->dsc);
     cudaFree(M->err);
@@ -333,7 +340,7 @@ void mixed_free(tfde_problem* P) {
 }
 
 int mixed_apply_A(const tfde_problem* P, int op, const double* x, double* y, cudaStream_t s) {
-    if (!(op & TFDE_OP_FAST)) return apply_A64(P, op & 1, x, y, s);
+    if (!(op & TFDE_OP_FAST)) return accurate_apply(P, op & 1, x, y, s);
     MixedState* M = mixed(P);
     launch_split64(P->N, x, 1.0, M->hi[PL_P], M->lo[PL_P], s);
     int st = fast_matvec(P, op, M->f[F_Q], s);
@@ -416,7 +423,7 @@ int mixed_pgmres(tfde_problem* P, const double* b, double* x, int restart, doubl
 int mixed_cn_step(tfde_problem* P, const double* u_prev, const double* F, const double* x0, double* u_next,
                   double tol, tfde_info* info, cudaStream_t s) {
     double* b = P->w[tfde_problem::W_B];
-    int st = apply_A64(P, TFDE_OP_RHS, u_prev, b, s);
+    int st = accurate_apply(P, TFDE_OP_RHS, u_prev, b, s);
     if (st) return st;
     if (F) launch_axpby_f64(P->N, P->p.dt, F, 1.0, b, s);
     const double* start = x0 ? x0 : u_prev;

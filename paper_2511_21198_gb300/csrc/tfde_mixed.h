@@ -4,6 +4,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <vector>
+
 #include "tfde_internal.h"
 #include "tfde_tc.h"
 
@@ -37,6 +39,10 @@ enum OpMat {
     NOM
 };
 
+// Digit slices of the exact-integer (Ozaki-type) contraction: 7 base-128
+// digits, 49 bits below each row / line maximum.
+constexpr int OZ_SLICES = 7;
+
 struct MixedState {
     __nv_bfloat16* mat[NOM] = {};
     CUtensorMap amap[NOM];
@@ -50,8 +56,19 @@ struct MixedState {
     int* err = nullptr;     // device error flag of the tensor-core kernels
     int* err_host = nullptr;
     long long gemm_launches = 0;
+    // exact-integer slice path (tfde_oz.cu)
+    __nv_bfloat16* oz_op[3] = {};      // per axis: OZ_SLICES digit matrices of eta_a B_a
+    int* oz_rexp[3] = {};              // per axis: row exponents
+    CUtensorMap oz_amap[3][OZ_SLICES];
+    __nv_bfloat16* oz_planes = nullptr;  // OZ_SLICES digit planes of the sliced vector
+    int* oz_lexp = nullptr;            // line exponents of the sliced vector
+    CUtensorMap oz_bmap[OZ_SLICES][3];
 };
 
 inline MixedState* mixed(const tfde_problem* P) { return static_cast<MixedState*>(P->mixed); }
+
+int oz_init(tfde_problem* P, const std::vector<double> etaB[3], cudaStream_t s);
+void oz_free(MixedState* M);
+int accurate_apply(const tfde_problem* P, int op, const double* x, double* y, cudaStream_t s);
 
 }  // namespace tfde

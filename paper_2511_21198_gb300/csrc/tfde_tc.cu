@@ -81,6 +81,16 @@ int make_map_B(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int ax
     return encode(m, base, 3, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
+// Vector plane along the x axis with a custom line box (K-major, 64B swizzle).
+int make_map_B_box(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis, int box_lines) {
+    if (axis != 0) return make_map_B(m, base, n, axis);
+    if (n[0] % 8) return set_error(TFDE_EUNSUPPORTED, "tensor-core path needs n1 multiple of 8");
+    const cuuint64_t dims[2] = {(cuuint64_t)n[0], (cuuint64_t)n[1] * (cuuint64_t)n[2]};
+    const cuuint64_t strides[1] = {(cuuint64_t)n[0] * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_lines};
+    return encode(m, base, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B);
+}
+
 // Fill the geometry fields of Params for a contraction along `axis`.
 void set_geometry(Params& P, const int n[3], int axis) {
     const long long n1 = n[0], n2 = n[1], n3 = n[2];

@@ -12,6 +12,7 @@ namespace tc {
 int num_sms();
 int make_map_A(CUtensorMap* m, const __nv_bfloat16* base, int n);
 int make_map_B(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis);
+int make_map_B_box(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis, int box_lines);
 void set_geometry(Params& P, const int n[3], int axis);
 int launch(const Params& P, cudaStream_t s, double bytes, double flops);
 

@@ -4,7 +4,7 @@
 //
 // m runs along one grid axis (the operator's rows), l over the lines of the
 // grid function along that axis; A_a are small BF16 operator matrices (the
-// split-BF16 parts of eta B, the mass stencil, the DST-I matrix) and B_b BF16
+// split-BF16 parts of eta B, the mass matrix, the DST-I matrix) and B_b BF16
 // planes of the operand vector.  This is the dense per-axis contraction of
 // Eq. (linear_sys) / Eq. (diag_tau_pre) with the line batch as the GEMM N
 // dimension.
@@ -15,8 +15,10 @@
 //               MN-major 128B swizzle, 4 boxes of 64 lines) into a 4-stage ring
 //   warp 1      allocates TMEM (2 x 256 FP32 columns) and issues tcgen05.mma
 //               (M=128, N=256, K=16, BF16 in, FP32 accumulate) from one thread
-//   warps 2..5  epilogue: tcgen05.ld from TMEM, scale, optional Lambda^{-1},
-//               store FP32 or split BF16 (hi, lo) with coalesced stores
+//   warps 2..9  epilogue, two warps per TMEM lane quadrant (one per half of the
+//               256 columns): tcgen05.ld, scale, optional Lambda^{-1}, transpose
+//               through shared memory, 8- or 16-byte coalesced stores of FP32 or
+//               split BF16 (hi, lo) output
 // Every wait on an mbarrier is bounded by a wall-clock limit; on timeout the
 // kernel raises *err, stops issuing work, waits (bounded) for its own copies
 // and MMAs in flight, frees its TMEM and returns.
@@ -40,14 +42,14 @@ constexpr int MAXPAIR = 4;
 constexpr int A_TILE_BYTES = BM * BK * 2;                                  // 8 KB
 constexpr int B_TILE_BYTES = BN * BK * 2;                                  // 16 KB
 constexpr int STAGE_BYTES = MAXA * A_TILE_BYTES + MAXB * B_TILE_BYTES;     // 48 KB
-constexpr int NUM_THREADS = 192;
-constexpr int EPI_WARPS = 4;
+constexpr int EPI_WARPS = 8;
+constexpr int NUM_THREADS = 64 + 32 * EPI_WARPS;                           // 320
 constexpr int EPI_STRIDE = 33;
 constexpr int EPI_FLOATS = EPI_WARPS * 32 * EPI_STRIDE;
 constexpr int NUM_BARS = 2 * STAGES + 5;
 constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + EPI_FLOATS * 4 + NUM_BARS * 8 + 16;
 constexpr uint32_t TMEM_COLS = 2 * BN;
-constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;  // 2 s
+static_assert(SMEM_BYTES <= 232448, "shared memory budget of one CTA");
 
 struct Segment {
     int nkb;                     // k-blocks of BK in this segment
@@ -87,120 +89,33 @@ struct Params {
 };
 
 #ifdef TFDE_TC_KERNEL_IMPL
-// ------------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_fence_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait.  Returns false when the wait gave up (time limit, or another
-// role raised *err and `abort_on_err`).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, bool abort_on_err = true) {
-    if (mbar_try(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    while (true) {
-        if (mbar_try(bar, parity)) return true;
-        if (abort_on_err && *reinterpret_cast<volatile int*>(err) != 0) return false;
-        if (global_ns() - t0 > WAIT_LIMIT_NS) {
-            atomicExch(err, 1);
-            return false;
-        }
+}  // namespace tc
+}  // namespace tfde
+#include "tfde_tc_ptx.cuh"
+namespace tfde {
+namespace tc {
+
+// Four consecutive outputs (already scaled) to global memory at element index idx.
+__device__ __forceinline__ void store4(const Params& p, long long idx, float v0, float v1, float v2, float v3) {
+    if (p.out_mode == OUT_F32) {
+        *reinterpret_cast<float4*>(p.out_f32 + idx) = make_float4(v0, v1, v2, v3);
+    } else {
+        const __nv_bfloat162 h01 = __floats2bfloat162_rn(v0, v1);
+        const __nv_bfloat162 h23 = __floats2bfloat162_rn(v2, v3);
+        const float2 f01 = __bfloat1622float2(h01);
+        const float2 f23 = __bfloat1622float2(h23);
+        const __nv_bfloat162 l01 = __floats2bfloat162_rn(v0 - f01.x, v1 - f01.y);
+        const __nv_bfloat162 l23 = __floats2bfloat162_rn(v2 - f23.x, v3 - f23.y);
+        uint2 hv, lv;
+        hv.x = *reinterpret_cast<const uint32_t*>(&h01);
+        hv.y = *reinterpret_cast<const uint32_t*>(&h23);
+        lv.x = *reinterpret_cast<const uint32_t*>(&l01);
+        lv.y = *reinterpret_cast<const uint32_t*>(&l23);
+        *reinterpret_cast<uint2*>(p.out_hi + idx) = hv;
+        *reinterpret_cast<uint2*>(p.out_lo + idx) = lv;
     }
 }
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-            smem_u32(dst)),
-        "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
-        : "memory");
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
-                                            int c2) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
-            smem_u32(dst)),
-        "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
-        : "memory");
-}
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
-                 "r"(ncols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor (tcgen05): start address, leading / stride
-// byte offsets (16-byte units), descriptor version 1, swizzle layout code
-// (0 none, 2 = 128B, 4 = 64B, 6 = 32B).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)(layout & 7u) << 61;
-    return d;
-}
-// Instruction descriptor for kind::f16: FP32 accumulator, BF16 A and B,
-// A K-major, B K-major (0) or MN-major (1), N >> 3 at bit 17, M >> 4 at bit 24.
-__host__ __device__ constexpr uint32_t instr_desc(int M, int N, int b_mn_major) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)b_mn_major << 16) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
-}
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void store_out(const Params& p, long long idx, float v) {
+__device__ __forceinline__ void store1(const Params& p, long long idx, float v) {
     if (p.out_mode == OUT_F32) {
         p.out_f32[idx] = v;
     } else {
@@ -334,8 +249,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) axis_gemm_kernel(const __grid_
         }
     } else {
         // ---------------------------------------------------- epilogue warps
-        const int q = warp & 3;  // TMEM lane quadrant this warp may access
+        const int q = warp & 3;               // TMEM lane quadrant this warp may access
+        const int half = (warp - 2) >> 2;     // which 128 of the 256 columns
         float* stg = epi + (warp - 2) * 32 * EPI_STRIDE;
+        const int rsub = lane >> 3;           // transposed phase: 4 rows / columns per instruction
+        const int cq = (lane & 7) * 4;        // ... and 4 consecutive elements per lane
         long long it = 0;
         for (long long t = blockIdx.x; t < total; t += gridDim.x, ++it) {
             const int buf = (int)(it & 1);
@@ -348,43 +266,77 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) axis_gemm_kernel(const __grid_
             tc_fence_after();
             const long long tile = t / p.mhalves;
             const int mh = (int)(t % p.mhalves);
-            const int mrow0 = mh * BM + 32 * q;
-            const int m = mrow0 + lane;
-            for (int c0 = 0; c0 < BN; c0 += 32) {
+            const int mrow0 = mh * BM + 32 * q;   // first output row of this warp
+            for (int cc = 0; cc < BN / 2; cc += 32) {
+                const int c0 = half * (BN / 2) + cc;
                 uint32_t r[32];
                 tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN + c0), r);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) stg[lane * EPI_STRIDE + j] = p.alpha * __uint_as_float(r[j]);
+                __syncwarp();
                 if (p.b_kmajor) {
-                    const long long l0 = tile * BN + c0;
-                    if (m < p.n) {
-#pragma unroll 8
-                        for (int j = 0; j < 32; ++j) {
-                            const long long l = l0 + j;
-                            if (l < p.lines) store_out(p, l * p.n1 + m, p.alpha * __uint_as_float(r[j]));
+                    // stg[row][line]; output Y[line * n1 + m], m contiguous
+#pragma unroll 2
+                    for (int i8 = 0; i8 < 8; ++i8) {
+                        const int jl = i8 * 4 + rsub;                 // line within the chunk
+                        const long long l = tile * BN + c0 + jl;
+                        const int m = mrow0 + cq;
+                        if (l < p.lines) {
+                            const float v0 = stg[(cq + 0) * EPI_STRIDE + jl];
+                            const float v1 = stg[(cq + 1) * EPI_STRIDE + jl];
+                            const float v2 = stg[(cq + 2) * EPI_STRIDE + jl];
+                            const float v3 = stg[(cq + 3) * EPI_STRIDE + jl];
+                            const long long idx = l * p.n1 + m;
+                            if (m + 3 < p.n) {
+                                store4(p, idx, v0, v1, v2, v3);
+                            } else {
+                                if (m + 0 < p.n) store1(p, idx + 0, v0);
+                                if (m + 1 < p.n) store1(p, idx + 1, v1);
+                                if (m + 2 < p.n) store1(p, idx + 2, v2);
+                            }
                         }
                     }
                 } else {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) stg[lane * EPI_STRIDE + j] = __uint_as_float(r[j]);
-                    __syncwarp();
+                    // stg[row][c]; output Y[pl * plane + m * C + c], c contiguous
                     const long long gb = tile * (BN / 64) + c0 / 64;
                     const int pl = (int)(gb / p.nbc);
-                    const int c = (int)(gb % p.nbc) * 64 + (c0 & 63) + lane;
-                    if (gb < p.nblocks && c < p.C) {
-                        float U = 0.f, V = 0.f;
-                        if (p.lam_ra) {
-                            U = p.lam_U[c];
-                            V = p.lam_V[c];
-                        }
-                        for (int rr = 0; rr < 32; ++rr) {
-                            const int mr = mrow0 + rr;
-                            if (mr >= p.n) break;
-                            float v = p.alpha * stg[rr * EPI_STRIDE + lane];
-                            if (p.lam_ra) v = v / (p.lam_ra[mr] * U + p.lam_rb[mr] * V);
-                            store_out(p, (long long)pl * p.plane + (long long)mr * p.C + c, v);
+                    const int cbase = (int)(gb % p.nbc) * 64 + (c0 & 63);
+                    const int c = cbase + cq;
+                    const bool cvalid = gb < p.nblocks;
+                    float U[4] = {0.f, 0.f, 0.f, 0.f}, V[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (p.lam_ra && cvalid) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (c + k < p.C) {
+                                U[k] = __ldg(p.lam_U + c + k);
+                                V[k] = __ldg(p.lam_V + c + k);
+                            }
+                    }
+#pragma unroll 2
+                    for (int i8 = 0; i8 < 8; ++i8) {
+                        const int rr = i8 * 4 + rsub;
+                        const int m = mrow0 + rr;
+                        if (cvalid && m < p.n && c < p.C) {
+                            float v[4];
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) v[k] = stg[rr * EPI_STRIDE + cq + k];
+                            if (p.lam_ra) {
+                                const float ra = __ldg(p.lam_ra + m), rb = __ldg(p.lam_rb + m);
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) v[k] = __fdividef(v[k], ra * U[k] + rb * V[k]);
+                            }
+                            const long long idx = (long long)pl * p.plane + (long long)m * p.C + c;
+                            if (c + 3 < p.C) {
+                                store4(p, idx, v[0], v[1], v[2], v[3]);
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < 3; ++k)
+                                    if (c + k < p.C) store1(p, idx + k, v[k]);
+                            }
                         }
                     }
-                    __syncwarp();
                 }
+                __syncwarp();
             }
             tc_fence_before();
             __syncwarp();
