@@ -87,6 +87,8 @@ typedef struct tfde_problem tfde_problem;
 #define TFDE_OP_RHS  1   /* y = (A_N - eta-terms) x = (2 A_N - A) x, the RHS operator */
 #define TFDE_OP_FAST 2   /* OR-able: for TFDE_MIXED problems use the inner (split-BF16,
                             FP32-accumulated) arithmetic instead of the accurate one */
+#define TFDE_OP_STIFF 4  /* y = (A - A_N) x = eta_a A3(x)A2(x)B1 x + eta_b A3(x)B2(x)A1 x +
+                            eta_c B3(x)A2(x)A1 x, the three stiffness terms alone (not with FAST) */
 
 /*
  * tfde_assemble -- build a problem (Sec. 2, Eq. (coef_expression) to Eq. (linear_sys);
@@ -98,7 +100,9 @@ typedef struct tfde_problem tfde_problem;
  *   and the mass eigenvalues (6 + 2 cos t_k)/8, and allocates the workspace.
  *   Errors: TFDE_EINVAL for n_a < 1, delta outside (0,1), k <= 0, dt <= 0,
  *   lo >= hi, NULL pointers; TFDE_EUNSUPPORTED when TFDE_MIXED is requested
- *   for an n_a this build's tensor-core tiles do not cover (n_a > 256);
+ *   with an n_a that is not a multiple of 8 (tensor-map row alignment) or
+ *   above 448 (the exact-integer residual keeps every FP32 accumulator below
+ *   2^24 only up to there);
  *   TFDE_ENOMEM / TFDE_ECUDA.  *out is NULL on failure.  Synchronises `stream`.
  */
 int tfde_assemble(const tfde_params* params, int precision, void* stream, tfde_problem** out);
@@ -151,6 +155,26 @@ int tfde_pgmres(const tfde_problem* prob, const double* b, double* x, int restar
  */
 int tfde_cn_step(const tfde_problem* prob, const double* u_prev, const double* F_half,
                  const double* x0, double* u_next, double tol, tfde_info* info, void* stream);
+
+/*
+ * tfde_cn_advance -- one Crank-Nicolson step u^{m-1} -> u^m IN PLACE, for
+ * marching many steps on one problem (Sec. 2, Eq. (CN) and Eq. (linear_sys)).
+ *   Same result and stopping rule as tfde_cn_step with x0 = u^{m-1}, but the
+ *   problem keeps the right-hand side b^{m-1} and final true residual r^{m-1}
+ *   of the previous call, and uses A u^{m-1} = b^{m-1} - r^{m-1}: the new
+ *   right-hand side needs only the mass operator A_N, and the initial residual
+ *   no operator application at all.  The first call (restart != 0) instead
+ *   evaluates the stiffness terms K u once and uses b = A_N u - K u + dt F,
+ *   r_0 = dt F - 2 K u.
+ *   u: device, in/out.  The chain is valid only while u is the same pointer as
+ *   in the previous call and nothing else wrote it in between; pass restart = 1
+ *   on the first call and whenever that does not hold (also after any other
+ *   solver call on the same problem, which reuses the same workspace).
+ *   F_half: device cell averages at t_{m-1/2}, or NULL for f = 0.
+ *   Errors as tfde_cn_step; after an error the next call must restart.
+ */
+int tfde_cn_advance(const tfde_problem* prob, double* u, const double* F_half, int restart, double tol,
+                    tfde_info* info, void* stream);
 
 /*
  * tfde_source_example2 -- cell averages F_{ijk} (Sec. 2, definition of F^{m-1/2})

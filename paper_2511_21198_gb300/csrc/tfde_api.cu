@@ -10,17 +10,15 @@ const char* last_error_text();
 int assemble_problem(const tfde_params*, int, cudaStream_t, tfde_problem**);
 int destroy_problem(tfde_problem*);
 int host_coefficients(const tfde_params*, int, double*, double*, double*, double*);
-int pcg64(const tfde_problem*, const double*, double*, double, int, tfde_info*, cudaStream_t);
-int pgmres64(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t);
-int cn_step64(tfde_problem*, const double*, const double*, const double*, double*, double, tfde_info*,
-              cudaStream_t);
+int pcg64(const tfde_problem*, const double*, double*, double, int, tfde_info*, cudaStream_t, bool);
+int pgmres64(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t, bool);
+int cn_drive(tfde_problem*, const double*, const double*, const double*, double*, double, tfde_info*, cudaStream_t,
+             bool);
 // mixed path (tfde_mixed.cu)
 int mixed_apply_A(const tfde_problem*, int, const double*, double*, cudaStream_t);
 int mixed_apply_Pinv(const tfde_problem*, const double*, double*, cudaStream_t);
-int mixed_pcg(tfde_problem*, const double*, double*, double, int, tfde_info*, cudaStream_t);
-int mixed_pgmres(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t);
-int mixed_cn_step(tfde_problem*, const double*, const double*, const double*, double*, double, tfde_info*,
-                  cudaStream_t);
+int mixed_pcg(tfde_problem*, const double*, double*, double, int, tfde_info*, cudaStream_t, bool);
+int mixed_pgmres(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t, bool);
 }  // namespace tfde
 
 using namespace tfde;
@@ -71,9 +69,10 @@ int tfde_matvec(const tfde_problem* prob, int op, const double* x, double* y, vo
     int st;
     if ((st = pre_call()) || (st = check_dev(x, "x")) || (st = check_dev(y, "y"))) return st;
     if (x == y) return set_error(TFDE_EINVAL, "x and y must not alias");
-    if (op < 0 || op > 3) return set_error(TFDE_EINVAL, "unknown op");
+    if (op < 0 || op > 7 || ((op & TFDE_OP_STIFF) && (op & TFDE_OP_FAST)))
+        return set_error(TFDE_EINVAL, "unknown op");
     if (prob->prec == TFDE_MIXED) return mixed_apply_A(prob, op, x, y, (cudaStream_t)stream);
-    return apply_A64(prob, op & 1, x, y, (cudaStream_t)stream);
+    return apply_A64(prob, op & ~TFDE_OP_FAST, x, y, (cudaStream_t)stream);
 }
 
 int tfde_precond(const tfde_problem* prob, const double* r, double* z, void* stream) {
@@ -94,8 +93,9 @@ int tfde_pcg(const tfde_problem* prob, const double* b, double* x, double tol, i
     if (!prob->symmetric) return set_error(TFDE_EINVAL, "PCG needs k_+ = k_- on every axis");
     if (maxit < 0) return set_error(TFDE_EINVAL, "maxit must be >= 0");
     tfde_problem* P = const_cast<tfde_problem*>(prob);
-    if (prob->prec == TFDE_MIXED) return mixed_pcg(P, b, x, tol, maxit, info, (cudaStream_t)stream);
-    return pcg64(prob, b, x, tol, maxit, info, (cudaStream_t)stream);
+    P->chain_ok = false;
+    if (prob->prec == TFDE_MIXED) return mixed_pcg(P, b, x, tol, maxit, info, (cudaStream_t)stream, false);
+    return pcg64(prob, b, x, tol, maxit, info, (cudaStream_t)stream, false);
 }
 
 int tfde_pgmres(const tfde_problem* prob, const double* b, double* x, int restart, double tol, int maxit,
@@ -108,8 +108,9 @@ int tfde_pgmres(const tfde_problem* prob, const double* b, double* x, int restar
     if (restart < 1 || restart > 64) return set_error(TFDE_EINVAL, "restart must lie in [1, 64]");
     if (maxit < 0) return set_error(TFDE_EINVAL, "maxit must be >= 0");
     tfde_problem* P = const_cast<tfde_problem*>(prob);
-    if (prob->prec == TFDE_MIXED) return mixed_pgmres(P, b, x, restart, tol, maxit, info, (cudaStream_t)stream);
-    return pgmres64(P, b, x, restart, tol, maxit, info, (cudaStream_t)stream);
+    P->chain_ok = false;
+    if (prob->prec == TFDE_MIXED) return mixed_pgmres(P, b, x, restart, tol, maxit, info, (cudaStream_t)stream, false);
+    return pgmres64(P, b, x, restart, tol, maxit, info, (cudaStream_t)stream, false);
 }
 
 int tfde_cn_step(const tfde_problem* prob, const double* u_prev, const double* F_half, const double* x0,
@@ -122,10 +123,28 @@ int tfde_cn_step(const tfde_problem* prob, const double* u_prev, const double* F
     if (F_half && (st = check_dev(F_half, "F_half"))) return st;
     if (x0 && (st = check_dev(x0, "x0"))) return st;
     if (u_next == u_prev || u_next == F_half) return set_error(TFDE_EINVAL, "u_next aliases an input");
+    if (x0 && x0 == u_prev) x0 = nullptr;
     tfde_problem* P = const_cast<tfde_problem*>(prob);
-    if (prob->prec == TFDE_MIXED)
-        return mixed_cn_step(P, u_prev, F_half, x0, u_next, tol, info, (cudaStream_t)stream);
-    return cn_step64(P, u_prev, F_half, x0, u_next, tol, info, (cudaStream_t)stream);
+    P->chain_ok = false;
+    return cn_drive(P, u_prev, F_half, x0, u_next, tol, info, (cudaStream_t)stream, false);
+}
+
+int tfde_cn_advance(const tfde_problem* prob, double* u, const double* F_half, int restart, double tol,
+                    tfde_info* info, void* stream) {
+    if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
+    int st;
+    if ((st = pre_call()) || (st = check_dev(u, "u")) || (st = check_tol(tol))) return st;
+    if (F_half && (st = check_dev(F_half, "F_half"))) return st;
+    if (F_half == u) return set_error(TFDE_EINVAL, "F_half aliases u");
+    tfde_problem* P = const_cast<tfde_problem*>(prob);
+    const bool chained = !restart && P->chain_ok && P->chain_u == u;
+    P->chain_ok = false;
+    st = cn_drive(P, u, F_half, nullptr, u, tol, info, (cudaStream_t)stream, chained);
+    if (st == TFDE_OK) {
+        P->chain_ok = true;
+        P->chain_u = u;
+    }
+    return st;
 }
 
 int tfde_source_example2(const tfde_problem* prob, double cP, double cS, double* F, void* stream) {

@@ -67,6 +67,11 @@ void launch_multiaxpy_f64(size_t N, int m, const double* V, size_t ldv, const do
 // deterministic second stage: out[j] = sum_b part[j*nblk + b], j < m
 void launch_reduce_finish(const double* part, int nblk, int m, double* out, cudaStream_t s);
 int reduction_blocks(size_t N);
+// b = AN - Ku + dt F, r = dt F - 2 Ku  (first CN step of a chain)
+void launch_cn_first(size_t N, const double* AN, const double* Ku, const double* F, double dt, double* b, double* r,
+                     cudaStream_t s);
+// t = 2 AN + dt F; b <- t + r - b; r <- b_new + r - b_old  (chained CN step)
+void launch_cn_chain(size_t N, const double* AN, const double* F, double dt, double* b, double* r, cudaStream_t s);
 // F = cP PPP + cS (SPP + PSP + PPS) from 1-D arrays [Px|Py|Pz|Sx|Sy|Sz]
 void launch_source_assemble_f64(const double* oned, const int n[3], double cP, double cS, double* F,
                                 cudaStream_t s);
@@ -103,6 +108,10 @@ struct tfde_problem {
     int nblk = 0;
 
     void* mixed = nullptr;  // mixed-precision state (tensor-core path)
+
+    // chained CN advance: W_B / W_R hold b^{m-1} and its final true residual
+    const double* chain_u = nullptr;
+    bool chain_ok = false;
 };
 
 namespace tfde {

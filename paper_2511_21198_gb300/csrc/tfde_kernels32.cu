@@ -132,6 +132,52 @@ __global__ void widen32_kernel(long long N, const float* __restrict__ v, double 
 // coef[0] = num[0] / den[0]  (device-side scalar, no host round trip)
 __global__ void ratio_kernel(const double* num, const double* den, double* coef) { coef[0] = num[0] / den[0]; }
 
+// Up to C dot products <V_j, w>, j = m0 .. m0 + mc - 1, per block into part[j * nblk + b].
+template <int C>
+__global__ __launch_bounds__(kT) void multidot32_kernel(long long N, int m0, int mc, const float* __restrict__ V,
+                                                        long long ldv, const float* __restrict__ w,
+                                                        double* __restrict__ part) {
+    long long lo, hi;
+    chunk(N, lo, hi);
+    KSum k[C];
+    for (long long i = lo + threadIdx.x; i < hi; i += kT) {
+        const float wi = w[i];
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+            if (j < mc) k[j].add(V[(long long)(m0 + j) * ldv + i] * wi);
+    }
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        if (j < mc) {
+            const double t = block_sum64((double)k[j].s - (double)k[j].c);
+            if (threadIdx.x == 0) part[(long long)(m0 + j) * gridDim.x + blockIdx.x] = t;
+        }
+    }
+}
+
+// w -= sum_{j < m} h[j] V_j   (h: FP64 coefficients on the device, m <= 128)
+__global__ void multiaxpy32_kernel(long long N, int m, const float* __restrict__ V, long long ldv,
+                                   const double* __restrict__ h, float* __restrict__ w) {
+    __shared__ float hs[128];
+    for (int j = threadIdx.x; j < m; j += blockDim.x) hs[j] = (float)h[j];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        float acc = w[i];
+        for (int j = 0; j < m; ++j) acc = fmaf(-hs[j], V[(long long)j * ldv + i], acc);
+        w[i] = acc;
+    }
+}
+
+// out = sc * in ; (h, l) = split(out)   (in == out allowed)
+__global__ void scale_split32_kernel(long long N, float sc, const float* in, float* out, __nv_bfloat16* __restrict__ h,
+                                     __nv_bfloat16* __restrict__ l) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const float v = in[i] * sc;
+        out[i] = v;
+        split(v, h[i], l[i]);
+    }
+}
+
 inline int grid_for(long long N) {
     long long g = (N + kT - 1) / kT;
     if (g > 152LL * 16) g = 152LL * 16;
@@ -178,6 +224,24 @@ void launch_widen32(size_t N, const float* v, double sc, double* y, cudaStream_t
 void launch_ratio(const double* num, const double* den, double* coef, cudaStream_t s) {
     stats_count_launch();
     ratio_kernel<<<1, 1, 0, s>>>(num, den, coef);
+}
+
+void launch_multidot32(size_t N, int m, const float* V, size_t ldv, const float* w, double* part, int nblk,
+                       cudaStream_t s) {
+    for (int m0 = 0; m0 < m; m0 += 8) {
+        const int mc = (m - m0) < 8 ? (m - m0) : 8;
+        stats_count_launch();
+        multidot32_kernel<8><<<nblk, kT, 0, s>>>((long long)N, m0, mc, V, (long long)ldv, w, part);
+    }
+}
+void launch_multiaxpy32(size_t N, int m, const float* V, size_t ldv, const double* h, float* w, cudaStream_t s) {
+    stats_count_launch();
+    multiaxpy32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, m, V, (long long)ldv, h, w);
+}
+void launch_scale_split32(size_t N, float sc, const float* in, float* out, __nv_bfloat16* h, __nv_bfloat16* l,
+                          cudaStream_t s) {
+    stats_count_launch();
+    scale_split32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, sc, in, out, h, l);
 }
 
 }  // namespace tfde

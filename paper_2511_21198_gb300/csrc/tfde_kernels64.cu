@@ -95,14 +95,26 @@ __global__ __launch_bounds__(kThreads) void axis_gemm_f64_kernel(
     }
 }
 
-__global__ void axis_stencil_f64_kernel(const double* __restrict__ X, double* __restrict__ Y, AxisView v,
-                                        long long N, double beta, const double* __restrict__ W,
+// Y = beta (tridiag(1,6,1)/8 along the axis) X + gamma W on a 3-D grid; one
+// thread per element of an (i, j, k) block, neighbours along the axis.
+__global__ void axis_stencil_f64_kernel(const double* __restrict__ X, double* __restrict__ Y, int n1, int n2,
+                                        int n3, int axis, double beta, const double* __restrict__ W,
                                         double gamma) {
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int m = (int)((idx / v.stride) % v.n);
-        double val = beta * mass_stencil(X, idx, m, v);
-        if (W) val += gamma * W[idx];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= n1 || j >= n2) return;
+    for (int k = blockIdx.z; k < n3; k += gridDim.z) {
+        const long long idx = ((long long)k * n2 + j) * n1 + i;
+        long long st;
+        int m, n;
+        if (axis == 0) { st = 1; m = i; n = n1; }
+        else if (axis == 1) { st = n1; m = j; n = n2; }
+        else { st = (long long)n1 * n2; m = k; n = n3; }
+        double nb = 0.0;
+        if (m > 0) nb += X[idx - st];
+        if (m + 1 < n) nb += X[idx + st];
+        double val = beta * fma(0.75, X[idx], 0.125 * nb);
+        if (W) val = fma(gamma, W[idx], val);
         Y[idx] = val;
     }
 }
@@ -252,6 +264,30 @@ __global__ void source_assemble_f64_kernel(const double* __restrict__ oned, int 
     }
 }
 
+// b = AN - Ku + dt F ;  r = dt F - 2 Ku   (F may be null)
+__global__ void cn_first_kernel(long long N, const double* __restrict__ AN, const double* __restrict__ Ku,
+                                const double* __restrict__ F, double dt, double* __restrict__ b,
+                                double* __restrict__ r) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const double f = F ? dt * F[i] : 0.0;
+        const double k = Ku[i];
+        b[i] = AN[i] - k + f;
+        r[i] = fma(-2.0, k, f);
+    }
+}
+
+// t = 2 AN + dt F ;  b <- t + r - b ;  r <- b_new + r - b_old
+__global__ void cn_chain_kernel(long long N, const double* __restrict__ AN, const double* __restrict__ F, double dt,
+                                double* __restrict__ b, double* __restrict__ r) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const double t = fma(2.0, AN[i], F ? dt * F[i] : 0.0);
+        const double d = r[i] - b[i];
+        const double bn = t + d;
+        b[i] = bn;
+        r[i] = bn + d;
+    }
+}
+
 inline int grid_for(long long N) {
     long long g = (N + kThreads - 1) / kThreads;
     if (g > 152LL * 16) g = 152LL * 16;
@@ -278,8 +314,18 @@ void launch_axis_gemm_f64(const double* Mat, const double* X, double* Y, const A
 void launch_axis_stencil_f64(const double* X, double* Y, const AxisView& v, double beta, const double* W,
                              double gamma, cudaStream_t s) {
     stats_count_launch();
-    const long long N = v.lines * v.n;
-    axis_stencil_f64_kernel<<<grid_for(N), kThreads, 0, s>>>(X, Y, v, N, beta, W, gamma);
+    // recover (n1, n2, n3) and the axis from the view
+    int n1, n2, n3, axis;
+    if (v.stride == 1) {
+        axis = 0; n1 = v.n; n2 = (int)v.lines; n3 = 1;   // lines of the x axis: any (n2, n3) split works
+    } else if (v.s_out != 0) {
+        axis = 1; n1 = (int)v.l_in; n2 = v.n; n3 = (int)(v.lines / v.l_in);
+    } else {
+        axis = 2; n1 = (int)v.l_in; n2 = 1; n3 = v.n;
+    }
+    dim3 blk(n1 >= 64 ? 64 : 32, 4);
+    dim3 grid((n1 + blk.x - 1) / blk.x, (n2 + blk.y - 1) / blk.y, n3 < 64 ? n3 : 64);
+    axis_stencil_f64_kernel<<<grid, blk, 0, s>>>(X, Y, n1, n2, n3, axis, beta, W, gamma);
 }
 
 void launch_lambda_scale_f64(const double* x, double* y, const double* lam, const int n[3], const double c[3],
@@ -326,6 +372,17 @@ void launch_multiaxpy_f64(size_t N, int m, const double* V, size_t ldv, const do
 void launch_reduce_finish(const double* part, int nblk, int m, double* out, cudaStream_t s) {
     stats_count_launch();
     reduce_finish_kernel<<<m, 32, 0, s>>>(part, nblk, m, out);
+}
+
+void launch_cn_first(size_t N, const double* AN, const double* Ku, const double* F, double dt, double* b, double* r,
+                     cudaStream_t s) {
+    stats_count_launch();
+    cn_first_kernel<<<grid_for((long long)N), kThreads, 0, s>>>((long long)N, AN, Ku, F, dt, b, r);
+}
+
+void launch_cn_chain(size_t N, const double* AN, const double* F, double dt, double* b, double* r, cudaStream_t s) {
+    stats_count_launch();
+    cn_chain_kernel<<<grid_for((long long)N), kThreads, 0, s>>>((long long)N, AN, F, dt, b, r);
 }
 
 void launch_source_assemble_f64(const double* oned, const int n[3], double cP, double cS, double* F,

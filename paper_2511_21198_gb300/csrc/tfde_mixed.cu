@@ -7,12 +7,13 @@
 #include <cstring>
 #include <vector>
 
+#include "tfde_givens.h"
 #include "tfde_mixed.h"
 
 namespace tfde {
 
-int pcg64(const tfde_problem*, const double*, double*, double, int, tfde_info*, cudaStream_t);
-int pgmres64(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t);
+int pcg64(const tfde_problem*, const double*, double*, double, int, tfde_info*, cudaStream_t, bool);
+int pgmres64(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t, bool);
 
 namespace {
 
@@ -109,8 +110,9 @@ int run_gemm(const tfde_problem* P, int axis, const SegSpec* segs, int nseg, int
     return tc::launch(prm, s, bytes, flops);
 }
 
-// q32 = A p (op A) or the RHS operator, p given as the split plane pair PL_P.
-int fast_matvec(const tfde_problem* P, int op, float* q32, cudaStream_t s) {
+// q32 = A p (op A) or the RHS operator, p given as the split plane pair PL_P;
+// with out_plane >= 0 the result goes to that split plane pair instead.
+int fast_matvec(const tfde_problem* P, int op, float* q32, cudaStream_t s, int out_plane = -1) {
     const bool rhs = (op & 1) != 0;
     int st;
     SegSpec sx[1] = {{rhs ? OM_GHATR_H : OM_GHAT_H, rhs ? OM_GHATR_L : OM_GHAT_L, PL_P}};
@@ -122,6 +124,7 @@ int fast_matvec(const tfde_problem* P, int op, float* q32, cudaStream_t s) {
     SegSpec ey[1] = {{OM_MY, -1, PL_W}};
     if ((st = run_gemm(P, 1, ey, 1, tc::OUT_HILO, 1.f, nullptr, PL_E, false, s))) return st;
     SegSpec oz[2] = {{OM_MZ, -1, PL_C}, {rhs ? OM_GZN_H : OM_GZ_H, rhs ? OM_GZN_L : OM_GZ_L, PL_E}};
+    if (out_plane >= 0) return run_gemm(P, 2, oz, 2, tc::OUT_HILO, 1.f, nullptr, out_plane, false, s);
     return run_gemm(P, 2, oz, 2, tc::OUT_F32, 1.f, q32, 0, false, s);
 }
 
@@ -212,22 +215,114 @@ int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaSt
 
 int accurate_residual(const tfde_problem* P, const double* b, const double* x, double* r, double* nr,
                       cudaStream_t s) {
-    double* q = P->w[tfde_problem::W_Q];
-    int st = accurate_apply(P, TFDE_OP_A, x, q, s);
+    int st = accurate_apply_ex(P, TFDE_OP_A, x, r, -1, b, 1.0, s);   // r = b - A x in the last pass
     if (st) return st;
-    launch_axpbypz_f64(P->N, 1.0, b, -1.0, q, r, s);
     double rr;
     if ((st = dots64(P, 1, r, 0, r, &rr, s))) return st;
     *nr = std::sqrt(rr);
     return TFDE_OK;
 }
 
+// Device / host Hessenberg scratch offsets (MixedState::gm).
+enum { GM_H = 0, GM_H2 = 128, GM_WW = 256, GM_Y = 384, GM_SIZE = 512 };
+
+int ensure_v32(const tfde_problem* P, int restart) {
+    MixedState* M = mixed(P);
+    if (!M->gm) {
+        MX_TRY(cudaMalloc((void**)&M->gm, GM_SIZE * sizeof(double)));
+        MX_TRY(cudaMallocHost((void**)&M->gm_host, GM_SIZE * sizeof(double)));
+    }
+    if (M->v32_cap >= restart) return TFDE_OK;
+    cudaFree(M->V32);
+    M->V32 = nullptr;
+    M->v32_cap = 0;
+    if (cudaMalloc((void**)&M->V32, (size_t)(restart + 1) * P->N * sizeof(float)) != cudaSuccess)
+        return set_error(TFDE_ENOMEM, "cudaMalloc of the FP32 GMRES basis failed");
+    M->v32_cap = restart;
+    return TFDE_OK;
+}
+
+// One cycle of left-preconditioned GMRES on P^{-1} A d = P^{-1} r32 (Sec. 3.2,
+// Eq. (one_side_system)) with FP32 basis vectors, split-BF16 tensor-core
+// operator and preconditioner applications, classical Gram-Schmidt with one
+// re-orthogonalisation (coefficients stay on the device) and host Givens
+// rotations: one host read per Arnoldi step.  r32 and its split planes PL_R
+// are prepared by the caller and x32 = 0; on return x32 = d.  The cycle stops
+// after `restart` steps or once the preconditioned residual estimate falls
+// below ptheta * beta.  *est_ratio = final estimate / beta.
+int inner_gmres(const tfde_problem* P, int restart, double ptheta, int maxit, int* iters, double* est_ratio,
+                cudaStream_t s) {
+    MixedState* M = mixed(P);
+    const size_t N = P->N;
+    float* V = M->V32;
+    double* g = M->gm;
+    double* gh = M->gm_host;
+    int st;
+    *iters = 0;
+    *est_ratio = 1.0;
+    // v_0 = P^{-1} r / beta
+    if ((st = fast_precond(P, V, s))) return st;
+    launch_dot32(N, V, V, P->red, P->nblk, s);
+    launch_reduce_finish(P->red, P->nblk, 1, g + GM_WW, s);
+    MX_TRY(cudaMemcpyAsync(gh + GM_WW, g + GM_WW, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MX_TRY(cudaStreamSynchronize(s));
+    const double beta = std::sqrt(gh[GM_WW]);
+    if (!std::isfinite(beta)) return set_error(TFDE_ENAN, "non-finite preconditioned residual");
+    if (!(beta > 0.0)) return TFDE_OK;
+    launch_scale_split32(N, (float)(1.0 / beta), V, V, M->hi[PL_P], M->lo[PL_P], s);
+    GivensLS ls(restart);
+    ls.g[0] = beta;
+    std::vector<double> h(restart + 2);
+    double est = beta;
+    int k = 0;
+    for (int j = 0; j < restart && j < maxit; ++j) {
+        float* w = V + (size_t)(j + 1) * N;
+        // w = P^{-1} A v_j  (A v_j leaves the contraction as split planes PL_R)
+        if ((st = fast_matvec(P, TFDE_OP_A, nullptr, s, PL_R))) return st;
+        if ((st = fast_precond(P, w, s))) return st;
+        // CGS2 with the coefficients on the device
+        launch_multidot32(N, j + 1, V, N, w, P->red, P->nblk, s);
+        launch_reduce_finish(P->red, P->nblk, j + 1, g + GM_H, s);
+        launch_multiaxpy32(N, j + 1, V, N, g + GM_H, w, s);
+        launch_multidot32(N, j + 1, V, N, w, P->red, P->nblk, s);
+        launch_reduce_finish(P->red, P->nblk, j + 1, g + GM_H2, s);
+        launch_multiaxpy32(N, j + 1, V, N, g + GM_H2, w, s);
+        launch_dot32(N, w, w, P->red, P->nblk, s);
+        launch_reduce_finish(P->red, P->nblk, 1, g + GM_WW, s);
+        MX_TRY(cudaMemcpyAsync(gh, g, (GM_WW + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+        MX_TRY(cudaStreamSynchronize(s));
+        for (int i = 0; i <= j; ++i) h[i] = gh[GM_H + i] + gh[GM_H2 + i];
+        const double hn = std::sqrt(gh[GM_WW]);
+        if (!std::isfinite(hn)) return set_error(TFDE_ENAN, "non-finite Arnoldi vector");
+        h[j + 1] = hn;
+        est = ls.add_column(j, h.data());
+        k = j + 1;
+        if (est <= ptheta * beta || hn == 0.0) break;
+        launch_scale_split32(N, (float)(1.0 / hn), w, w, M->hi[PL_P], M->lo[PL_P], s);
+    }
+    *iters = k;
+    *est_ratio = est / beta;
+    if (k > 0) {
+        std::vector<double> y;
+        ls.solve(k, y);
+        for (int i = 0; i < k; ++i) gh[GM_Y + i] = -y[i];
+        MX_TRY(cudaMemcpyAsync(g + GM_Y, gh + GM_Y, k * sizeof(double), cudaMemcpyHostToDevice, s));
+        launch_multiaxpy32(N, k, V, N, g + GM_Y, M->f[F_X], s);   // x32 = sum_i y_i v_i
+    }
+    return check_err(P, s);
+}
+
 }  // namespace
 
 int mixed_init(tfde_problem* P, cudaStream_t s) {
     for (int a = 0; a < 3; ++a)
+    {
         if (P->n[a] % 8 != 0)
             return set_error(TFDE_EUNSUPPORTED, "TFDE_MIXED needs every n_a to be a multiple of 8");
+        // exact FP32 diagonal sums of the slice contraction: n (36864 + 24576 / n) < 2^24
+        if (P->n[a] > 448)
+            return set_error(TFDE_EUNSUPPORTED, "TFDE_MIXED supports n_a <= 448");
+    }
     MixedState* M = new MixedState();
     P->mixed = M;
     const size_t N = P->N;
@@ -330,6 +425,9 @@ void mixed_free(tfde_problem* P) {
         cudaFree(M->lo[pl]);
     }
     for (auto& v : M->f) cudaFree(v);
+    cudaFree(M->V32);
+    cudaFree(M->gm);
+    if (M->gm_host) cudaFreeHost(M->gm_host);
     oz_free(M);
     cudaFree(M->lam);
     cudaFree(M->dsc);
@@ -340,7 +438,7 @@ void mixed_free(tfde_problem* P) {
 }
 
 int mixed_apply_A(const tfde_problem* P, int op, const double* x, double* y, cudaStream_t s) {
-    if (!(op & TFDE_OP_FAST)) return accurate_apply(P, op & 1, x, y, s);
+    if (!(op & TFDE_OP_FAST)) return accurate_apply(P, op, x, y, s);
     MixedState* M = mixed(P);
     launch_split64(P->N, x, 1.0, M->hi[PL_P], M->lo[PL_P], s);
     int st = fast_matvec(P, op, M->f[F_Q], s);
@@ -360,7 +458,7 @@ int mixed_apply_Pinv(const tfde_problem* P, const double* r, double* z, cudaStre
 
 // FP64 iterative refinement around the FP32 / split-BF16 inner PCG.
 int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit, tfde_info* info,
-              cudaStream_t s) {
+              cudaStream_t s, bool r_given) {
     const auto t0 = clk::now();
     MixedState* M = mixed(P);
     tfde_info loc{};
@@ -376,7 +474,13 @@ int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit
         return TFDE_OK;
     }
     double nr;
-    if ((st = accurate_residual(P, b, x, r64, &nr, s))) return st;
+    if (r_given) {
+        double rr0;
+        if ((st = dots64(P, 1, r64, 0, r64, &rr0, s))) return st;
+        nr = std::sqrt(rr0);
+    } else if ((st = accurate_residual(P, b, x, r64, &nr, s))) {
+        return st;
+    }
     loc.relres0 = nr / nb;
     int status = TFDE_ENOCONV;
     int stall = 0;
@@ -400,7 +504,7 @@ int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit
             // refinement stopped contracting: finish with FP64 inner solves
             loc.fallback = 1;
             tfde_info sub{};
-            status = pcg64(P, b, x, tol, maxit > loc.iters ? maxit - loc.iters : 1, &sub, s);
+            status = pcg64(P, b, x, tol, maxit > loc.iters ? maxit - loc.iters : 1, &sub, s, false);
             loc.iters += sub.iters;
             nr = sub.relres * nb;
             break;
@@ -413,23 +517,75 @@ int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit
     return status;
 }
 
+// FP64 iterative refinement around one FP32 / split-BF16 left-preconditioned
+// GMRES cycle per sweep: every sweep restarts from the accurate FP64 residual,
+// so the outer loop is restarted GMRES(restart) whose restarts are exact.
 int mixed_pgmres(tfde_problem* P, const double* b, double* x, int restart, double tol, int maxit, tfde_info* info,
-                 cudaStream_t s) {
-    int st = pgmres64(P, b, x, restart, tol, maxit, info, s);
-    if (info) info->fallback = 1;
-    return st;
-}
-
-int mixed_cn_step(tfde_problem* P, const double* u_prev, const double* F, const double* x0, double* u_next,
-                  double tol, tfde_info* info, cudaStream_t s) {
-    double* b = P->w[tfde_problem::W_B];
-    int st = accurate_apply(P, TFDE_OP_RHS, u_prev, b, s);
-    if (st) return st;
-    if (F) launch_axpby_f64(P->N, P->p.dt, F, 1.0, b, s);
-    const double* start = x0 ? x0 : u_prev;
-    if (start != u_next) MX_TRY(cudaMemcpyAsync(u_next, start, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    if (P->symmetric) return mixed_pcg(P, b, u_next, tol, 10000, info, s);
-    return mixed_pgmres(P, b, u_next, 20, tol, 10000, info, s);
+                 cudaStream_t s, bool r_given) {
+    const auto t0 = clk::now();
+    MixedState* M = mixed(P);
+    tfde_info loc{};
+    double* r64 = P->w[tfde_problem::W_R];
+    int st;
+    if ((st = ensure_v32(P, restart))) return st;
+    double bb;
+    if ((st = dots64(P, 1, b, 0, b, &bb, s))) return st;
+    const double nb = std::sqrt(bb);
+    if (!std::isfinite(nb)) return set_error(TFDE_ENAN, "non-finite right-hand side");
+    if (nb == 0.0) {
+        MX_TRY(cudaMemsetAsync(x, 0, P->N * sizeof(double), s));
+        if (info) *info = loc;
+        return TFDE_OK;
+    }
+    double nr;
+    if (r_given) {
+        double rr0;
+        if ((st = dots64(P, 1, r64, 0, r64, &rr0, s))) return st;
+        nr = std::sqrt(rr0);
+    } else if ((st = accurate_residual(P, b, x, r64, &nr, s))) {
+        return st;
+    }
+    loc.relres0 = nr / nb;
+    int status = TFDE_ENOCONV;
+    int stall = 0;
+    double ratio = 1.0;  // observed (true reduction) / (preconditioned estimate's reduction)
+    while (true) {
+        if (!std::isfinite(nr)) { status = set_error(TFDE_ENAN, "non-finite residual"); break; }
+        if (nr <= tol * nb) { status = TFDE_OK; break; }
+        if (loc.iters >= maxit) break;
+        double theta = 0.5 * tol * nb / nr / ratio;
+        if (theta < 1e-4) theta = 1e-4;
+        launch_scale64to32(P->N, r64, 1.0 / nr, M->f[F_R], M->hi[PL_R], M->lo[PL_R], M->f[F_X], s);
+        int it = 0;
+        double est_ratio = 1.0;
+        if ((st = inner_gmres(P, restart, theta, maxit - loc.iters, &it, &est_ratio, s))) return st;
+        loc.iters += it;
+        loc.restarts++;
+        loc.refine_sweeps++;
+        launch_add32to64(P->N, nr, M->f[F_X], x, s);
+        const double nr_old = nr;
+        if ((st = accurate_residual(P, b, x, r64, &nr, s))) return st;
+        if (est_ratio > 0.0) {
+            const double observed = (nr / nr_old) / est_ratio;
+            ratio = observed > 1.0 ? observed : 1.0;
+        }
+        stall = (nr > 0.5 * nr_old) ? stall + 1 : 0;
+        if (stall >= 2) {
+            // refinement stopped contracting: finish with FP64 inner cycles
+            loc.fallback = 1;
+            tfde_info sub{};
+            status = pgmres64(P, b, x, restart, tol, maxit > loc.iters ? maxit - loc.iters : 1, &sub, s, false);
+            loc.iters += sub.iters;
+            loc.restarts += sub.restarts;
+            nr = sub.relres * nb;
+            break;
+        }
+    }
+    loc.relres = nr / nb;
+    if (status == TFDE_ENOCONV) set_error(TFDE_ENOCONV, "mixed PGMRES reached maxit");
+    loc.ms = (float)std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    if (info) *info = loc;
+    return status;
 }
 
 }  // namespace tfde

@@ -23,6 +23,14 @@ void launch_split64(size_t N, const double* v, double sc, __nv_bfloat16* h, __nv
 void launch_add32to64(size_t N, double sc, const float* d, double* x, cudaStream_t s);
 void launch_widen32(size_t N, const float* v, double sc, double* y, cudaStream_t s);
 void launch_ratio(const double* num, const double* den, double* coef, cudaStream_t s);
+// m dot products <V_j, w> (FP32 vectors), partials part[j*nblk + b]
+void launch_multidot32(size_t N, int m, const float* V, size_t ldv, const float* w, double* part, int nblk,
+                       cudaStream_t s);
+// w -= sum_j h[j] V_j  (h: FP64 on the device, m <= 128)
+void launch_multiaxpy32(size_t N, int m, const float* V, size_t ldv, const double* h, float* w, cudaStream_t s);
+// out = sc * in ; (h, l) = split(out)
+void launch_scale_split32(size_t N, float sc, const float* in, float* out, __nv_bfloat16* h, __nv_bfloat16* l,
+                          cudaStream_t s);
 
 // Split-BF16 plane pairs of the workspace.
 enum Plane { PL_P, PL_A, PL_W, PL_C, PL_E, PL_R, PL_T1, PL_T2, NPL };
@@ -43,6 +51,14 @@ enum OpMat {
 // digits, 49 bits below each row / line maximum.
 constexpr int OZ_SLICES = 7;
 
+// One operator's digit slices (device) with their tensor maps.
+struct OzSet {
+    __nv_bfloat16* dev = nullptr;
+    CUtensorMap amap[OZ_SLICES];
+    int na = 0;          // leading slices that are not all zero
+    int rexp_index = 0;  // row exponents in MixedState::oz_rexp
+};
+
 struct MixedState {
     __nv_bfloat16* mat[NOM] = {};
     CUtensorMap amap[NOM];
@@ -56,13 +72,21 @@ struct MixedState {
     int* err = nullptr;     // device error flag of the tensor-core kernels
     int* err_host = nullptr;
     long long gemm_launches = 0;
+    // inner FP32 GMRES: basis (cap + 1 vectors) and device / pinned host
+    // Hessenberg scratch [h (128) | h2 (128) | |w|^2 | ... | -y (128)]
+    float* V32 = nullptr;
+    int v32_cap = 0;
+    double* gm = nullptr;
+    double* gm_host = nullptr;
     // exact-integer slice path (tfde_oz.cu)
-    __nv_bfloat16* oz_op[3] = {};      // per axis: OZ_SLICES digit matrices of eta_a B_a
-    int* oz_rexp[3] = {};              // per axis: row exponents
-    CUtensorMap oz_amap[3][OZ_SLICES];
-    __nv_bfloat16* oz_planes = nullptr;  // OZ_SLICES digit planes of the sliced vector
-    int* oz_lexp = nullptr;            // line exponents of the sliced vector
-    CUtensorMap oz_bmap[OZ_SLICES][3];
+    OzSet oz_x_plus, oz_x_minus, oz_x_stiff, oz_x_mass;      // A1 + G1, A1 - G1, G1, A1
+    OzSet oz_y_mass_c, oz_y_plus, oz_y_minus, oz_y_mass;     // (A2 | +-G2) common rows; A2 alone
+    OzSet oz_z_mass_c, oz_z_plus, oz_z_minus;                // (A3 | +-G3) common rows
+    std::vector<int*> oz_rexp;                               // row exponent arrays
+    __nv_bfloat16* oz_planes[2] = {nullptr, nullptr};        // digit planes of two inputs
+    CUtensorMap oz_bmap[2][OZ_SLICES][3];
+    int* oz_lexp = nullptr;                                  // joint line exponents
+    int oz_shift[3] = {0, 0, 0};                             // exponent shift of the second input
 };
 
 inline MixedState* mixed(const tfde_problem* P) { return static_cast<MixedState*>(P->mixed); }
@@ -70,5 +94,8 @@ inline MixedState* mixed(const tfde_problem* P) { return static_cast<MixedState*
 int oz_init(tfde_problem* P, const std::vector<double> etaB[3], cudaStream_t s);
 void oz_free(MixedState* M);
 int accurate_apply(const tfde_problem* P, int op, const double* x, double* y, cudaStream_t s);
+// y = vsign * (operator x) + asign * addend (addend may be null)
+int accurate_apply_ex(const tfde_problem* P, int op, const double* x, double* y, int vsign, const double* addend,
+                      double asign, cudaStream_t s);
 
 }  // namespace tfde

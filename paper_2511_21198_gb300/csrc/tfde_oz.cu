@@ -1,11 +1,14 @@
 // FP64-accurate operator application for the mixed path (Eq. (linear_sys)):
 //
-//   A x = A_N x +- [M3 M2 G1 + M3 G2 M1 + G3 M2 M1] x,   G_a = eta_a B_a,
+//   A x = A3 (A2 (A1 + G1) x + G2 A1 x) + G3 A2 A1 x,   G_a = eta_a B_a,
 //
-// evaluated as  y1 = M1 x;  a = y1 +- G1 x;  c = M2 a +- G2 y1;
-//               y  = M3 c +- G3 (M2 y1)
-// with the three dense contractions on the tensor cores in exact-integer
-// digit slices (tfde_oz_kernel.cuh) and the tridiagonal mass sweeps in FP64.
+// as three axis passes of the exact-integer slice contraction
+// (tfde_oz_kernel.cuh), with no FP64 arithmetic per grid point:
+//   x pass: a = (A1 + G1) x,  w = A1 x             (input x sliced along x)
+//   y pass: c = A2 a + G2 w,  e = A2 w             (a and w sliced jointly along y)
+//   z pass: y = A3 c + G3 e                        (c and e sliced jointly along z)
+// The two operators of a two-input pass share one scale per row and the two
+// inputs one scale per line, so both land in the same exact accumulators.
 #define TFDE_OZ_KERNEL_IMPL
 #include <algorithm>
 #include <cmath>
@@ -21,20 +24,33 @@ namespace tfde {
 
 namespace {
 
-constexpr int kT = 256;
-
-__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
-
-// exponent E with |v| < 2^E for the line maximum v (0 for an all-zero line),
-// clamped so that the fixed-point scale 2^{7S - E} stays a normal double
-__device__ __forceinline__ int line_exponent(double vmax) {
-    if (!(vmax > 0.0)) return 0;
-    int e;
-    frexp(vmax, &e);
-    return e < -960 ? -960 : (e > 1000 ? 1000 : e);
+// ------------------------------------------------------------ digit slicing
+// Fixed-point integer round(|x| 2^{7S - E}) with the sign of x, from the FP64
+// bits alone (|x| < 2^E): the mantissa shifted right with round-half-up.
+__device__ __forceinline__ long long fixed_point(long long bits, int S, int E) {
+    const unsigned long long u = (unsigned long long)bits & 0x7FFFFFFFFFFFFFFFull;
+    if (u == 0) return 0;
+    int e = (int)(u >> 52);
+    unsigned long long mant = u & ((1ull << 52) - 1);
+    if (e == 0) e = 1; else mant |= (1ull << 52);
+    const int r = 1075 - e - 7 * S + E;   // right shift; >= 53 - 7S >= 4 for S <= 7
+    long long X;
+    if (r >= 64) X = 0;
+    else if (r <= 0) X = (long long)(mant << (-r));
+    else X = (long long)((mant + (1ull << (r - 1))) >> r);
+    return bits < 0 ? -X : X;
 }
 
-// balanced base-128 digits of X (|X| < 2^{7S}): d[S-1..1] in [-64, 63], d[0] the rest
+// Exponent E with |x| < 2^E for the largest |x| of a line (given as the
+// biased-exponent field of its bit pattern; 0 for an all-zero line).
+__device__ __forceinline__ int line_exponent_from_bits(unsigned long long umax) {
+    if (umax == 0) return 0;
+    const int e = (int)(umax >> 52);
+    return e == 0 ? -1021 : e - 1022;
+}
+
+// balanced base-128 digits of X (|X| <= 2^{7S}): planes[t*N + idx] for t = S-1..1 in
+// [-64, 63], planes[idx] the remaining leading digit
 __device__ __forceinline__ void write_digits(long long X, int S, __nv_bfloat16* planes, long long N, long long idx) {
     for (int t = S - 1; t >= 1; --t) {
         long long r = X & 127;
@@ -45,71 +61,132 @@ __device__ __forceinline__ void write_digits(long long X, int S, __nv_bfloat16* 
     planes[idx] = __float2bfloat16_rn((float)X);
 }
 
-// x axis: one warp per line of n1 contiguous values
-__global__ void slice_x_kernel(const double* __restrict__ x, int n1, long long lines, int S,
-                               __nv_bfloat16* __restrict__ planes, long long N, int* __restrict__ lexp) {
+// x axis: one warp per line of n1 contiguous values, one or two inputs sliced
+// under their joint line maximum.
+// |x| bits of x * 2^sh for a normal or zero x (exponent field moved by sh)
+__device__ __forceinline__ unsigned long long abs_bits_shifted(long long bits, int sh) {
+    const unsigned long long u = (unsigned long long)bits & 0x7FFFFFFFFFFFFFFFull;
+    return u == 0 ? 0 : u + ((unsigned long long)(long long)sh << 52);
+}
+
+__global__ void slice_x_kernel(const double* __restrict__ x0, const double* __restrict__ x1, int sh1, int n1,
+                               long long lines, int S, __nv_bfloat16* __restrict__ p0,
+                               __nv_bfloat16* __restrict__ p1, long long N, int* __restrict__ lexp) {
     const int lane = threadIdx.x & 31;
-    const long long warp_global = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long l = warp_global; l < lines; l += nwarps) {
-        const double* row = x + l * n1;
-        double vmax = 0.0;
-        for (int k = lane; k < n1; k += 32) vmax = fmax(vmax, fabs(row[k]));
+    const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long l = wg; l < lines; l += nw) {
+        const long long* r0 = reinterpret_cast<const long long*>(x0 + l * n1);
+        const long long* r1 = x1 ? reinterpret_cast<const long long*>(x1 + l * n1) : nullptr;
+        unsigned long long umax = 0;
+#pragma unroll 4
+        for (int k = lane; k < n1; k += 32) {
+            umax = max(umax, (unsigned long long)r0[k] & 0x7FFFFFFFFFFFFFFFull);
+            if (r1) umax = max(umax, abs_bits_shifted(r1[k], sh1));
+        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-        const int E = line_exponent(vmax);
-        const double sc = pow2d(7 * S - E);
-        for (int k = lane; k < n1; k += 32) write_digits(__double2ll_rn(row[k] * sc), S, planes, N, l * n1 + k);
+        for (int o = 16; o > 0; o >>= 1) umax = max(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+        const int E = line_exponent_from_bits(umax);
+#pragma unroll 4
+        for (int k = lane; k < n1; k += 32) {
+            write_digits(fixed_point(r0[k], S, E), S, p0, N, l * n1 + k);
+            if (r1) write_digits(fixed_point(r1[k], S, E - sh1), S, p1, N, l * n1 + k);
+        }
         if (lane == 0) lexp[l] = E;
     }
 }
 
-// y / z axes: one thread per line (consecutive lines are contiguous in memory)
-__global__ void slice_strided_kernel(const double* __restrict__ x, AxisView v, int S,
-                                     __nv_bfloat16* __restrict__ planes, long long N, int* __restrict__ lexp) {
-    for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < v.lines;
-         l += (long long)gridDim.x * blockDim.x) {
-        const long long off = (l % v.l_in) * v.s_in + (l / v.l_in) * v.s_out;
-        double vmax = 0.0;
-        for (int k = 0; k < v.n; ++k) vmax = fmax(vmax, fabs(x[off + (long long)k * v.stride]));
-        const int E = line_exponent(vmax);
-        const double sc = pow2d(7 * S - E);
-        for (int k = 0; k < v.n; ++k) {
-            const long long idx = off + (long long)k * v.stride;
-            write_digits(__double2ll_rn(x[idx] * sc), S, planes, N, idx);
+// y / z axes: 32 consecutive lines (contiguous in memory) x 8 k-groups per
+// 256-thread block; the joint line maximum is reduced through shared memory.
+__global__ __launch_bounds__(256) void slice_strided_kernel(const double* __restrict__ x0,
+                                                            const double* __restrict__ x1, int sh1, AxisView v, int S,
+                                                            __nv_bfloat16* __restrict__ p0,
+                                                            __nv_bfloat16* __restrict__ p1, long long N,
+                                                            int* __restrict__ lexp) {
+    __shared__ unsigned long long smax[8][32];
+    __shared__ int sexp[32];
+    const int li = threadIdx.x & 31, kg = threadIdx.x >> 5;
+    const long long* b0 = reinterpret_cast<const long long*>(x0);
+    const long long* b1 = reinterpret_cast<const long long*>(x1);
+    for (long long l0 = (long long)blockIdx.x * 32; l0 < v.lines; l0 += (long long)gridDim.x * 32) {
+        const long long l = l0 + li;
+        const bool valid = l < v.lines;
+        const long long off = valid ? (l % v.l_in) * v.s_in + (l / v.l_in) * v.s_out : 0;
+        unsigned long long umax = 0;
+        if (valid) {
+#pragma unroll 4
+            for (int k = kg; k < v.n; k += 8) {
+                const long long idx = off + (long long)k * v.stride;
+                umax = max(umax, (unsigned long long)b0[idx] & 0x7FFFFFFFFFFFFFFFull);
+                if (b1) umax = max(umax, abs_bits_shifted(b1[idx], sh1));
+            }
         }
-        lexp[l] = E;
+        smax[kg][li] = umax;
+        __syncthreads();
+        if (kg == 0) {
+            unsigned long long m = smax[0][li];
+#pragma unroll
+            for (int g = 1; g < 8; ++g) m = max(m, smax[g][li]);
+            const int E = line_exponent_from_bits(m);
+            sexp[li] = E;
+            if (valid) lexp[l] = E;
+        }
+        __syncthreads();
+        if (valid) {
+            const int E = sexp[li];
+#pragma unroll 4
+            for (int k = kg; k < v.n; k += 8) {
+                const long long idx = off + (long long)k * v.stride;
+                write_digits(fixed_point(b0[idx], S, E), S, p0, N, idx);
+                if (b1) write_digits(fixed_point(b1[idx], S, E - sh1), S, p1, N, idx);
+            }
+        }
+        __syncthreads();
     }
 }
 
 int grid_for(long long n) {
-    long long g = (n + kT - 1) / kT;
+    long long g = (n + 255) / 256;
     if (g > 152LL * 16) g = 152LL * 16;
     return (int)(g < 1 ? 1 : g);
 }
 
-// Host: digit slices of an n x n operator (row-major) and its row exponents.
-void slice_operator_host(const std::vector<double>& G, int n, int S, std::vector<__nv_bfloat16>& slices,
-                         std::vector<int>& rexp) {
-    slices.assign((size_t)S * n * n, __float2bfloat16_rn(0.f));
+// ------------------------------------------------------- operator slicing
+// Digit slices of one or two n x n operators (row-major) under a common
+// power-of-two scale per row: slices[op][t][m][k]; returns the row exponents
+// and, per operator, the number of leading slices that are not all zero.
+void slice_operators_host(const std::vector<const std::vector<double>*>& ops, int n, int S,
+                          std::vector<std::vector<__nv_bfloat16>>& slices, std::vector<int>& rexp,
+                          std::vector<int>& nonzero) {
+    const size_t nn = (size_t)n * n;
+    slices.assign(ops.size(), std::vector<__nv_bfloat16>((size_t)S * nn, __float2bfloat16_rn(0.f)));
+    nonzero.assign(ops.size(), 0);
     rexp.assign(n, 0);
     for (int m = 0; m < n; ++m) {
         double vmax = 0.0;
-        for (int k = 0; k < n; ++k) vmax = std::fmax(vmax, std::fabs(G[(size_t)m * n + k]));
+        for (const auto* G : ops)
+            for (int k = 0; k < n; ++k) vmax = std::fmax(vmax, std::fabs((*G)[(size_t)m * n + k]));
         int E = 0;
         if (vmax > 0.0) std::frexp(vmax, &E);
         rexp[m] = E;
-        for (int k = 0; k < n; ++k) {
-            long long X = std::llrint(std::ldexp(G[(size_t)m * n + k], 7 * S - E));
-            for (int t = S - 1; t >= 1; --t) {
-                long long r = X & 127;
-                if (r >= 64) r -= 128;
-                slices[(size_t)t * n * n + (size_t)m * n + k] = __float2bfloat16_rn((float)r);
-                X = (X - r) >> 7;
+        for (size_t o = 0; o < ops.size(); ++o)
+            for (int k = 0; k < n; ++k) {
+                long long X = std::llrint(std::ldexp((*ops[o])[(size_t)m * n + k], 7 * S - E));
+                for (int t = S - 1; t >= 0; --t) {
+                    long long r;
+                    if (t > 0) {
+                        r = X & 127;
+                        if (r >= 64) r -= 128;
+                        X = (X - r) >> 7;
+                    } else {
+                        r = X;
+                    }
+                    if (r != 0) nonzero[o] = std::max(nonzero[o], t + 1);
+                    slices[o][(size_t)t * nn + (size_t)m * n + k] = __float2bfloat16_rn((float)r);
+                }
             }
-            slices[(size_t)m * n + k] = __float2bfloat16_rn((float)X);
-        }
     }
+    for (auto& z : nonzero) z = std::max(z, 1);
 }
 
 #define OZ_TRY(expr)                                                                       \
@@ -121,76 +198,171 @@ void slice_operator_host(const std::vector<double>& G, int n, int S, std::vector
 
 bool g_oz_attr = false;
 
+// Upload one operator digit set and build its tensor maps.
+int upload_set(OzSet& set, const std::vector<__nv_bfloat16>& sl, int n, int S, int na, int rexp_index,
+               cudaStream_t s) {
+    OZ_TRY(cudaMalloc((void**)&set.dev, sl.size() * sizeof(__nv_bfloat16)));
+    OZ_TRY(cudaMemcpyAsync(set.dev, sl.data(), sl.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, s));
+    set.na = na;
+    set.rexp_index = rexp_index;
+    for (int t = 0; t < S; ++t) {
+        int st = tc::make_map_A(&set.amap[t], set.dev + (size_t)t * n * n, n);
+        if (st) return st;
+    }
+    return TFDE_OK;
+}
+
 }  // namespace
 
 int oz_init(tfde_problem* P, const std::vector<double> etaB[3], cudaStream_t s) {
     MixedState* M = mixed(P);
     const int S = OZ_SLICES;
     const size_t N = P->N;
-    for (int a = 0; a < 3; ++a) {
-        const int n = P->n[a];
-        std::vector<__nv_bfloat16> sl;
-        std::vector<int> rexp;
-        slice_operator_host(etaB[a], n, S, sl, rexp);
-        OZ_TRY(cudaMalloc((void**)&M->oz_op[a], sl.size() * sizeof(__nv_bfloat16)));
-        OZ_TRY(cudaMemcpyAsync(M->oz_op[a], sl.data(), sl.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, s));
-        OZ_TRY(cudaMalloc((void**)&M->oz_rexp[a], n * sizeof(int)));
-        OZ_TRY(cudaMemcpyAsync(M->oz_rexp[a], rexp.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
-        OZ_TRY(cudaStreamSynchronize(s));
-        for (int t = 0; t < S; ++t) {
-            int st = tc::make_map_A(&M->oz_amap[a][t], M->oz_op[a] + (size_t)t * n * n, n);
-            if (st) return st;
+    auto mass = [](int n) {
+        std::vector<double> A((size_t)n * n, 0.0);
+        for (int i = 0; i < n; ++i) {
+            A[(size_t)i * n + i] = 0.75;
+            if (i > 0) A[(size_t)i * n + i - 1] = 0.125;
+            if (i + 1 < n) A[(size_t)i * n + i + 1] = 0.125;
+        }
+        return A;
+    };
+    auto upload_rexp = [&](const std::vector<int>& r) -> int {
+        int* d = nullptr;
+        if (cudaMalloc((void**)&d, r.size() * sizeof(int)) != cudaSuccess) return -1;
+        cudaMemcpyAsync(d, r.data(), r.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+        M->oz_rexp.push_back(d);
+        return (int)M->oz_rexp.size() - 1;
+    };
+    std::vector<std::vector<__nv_bfloat16>> sl;
+    std::vector<int> rexp, nz;
+    int st;
+    // x pass: (A1 + G1), (A1 - G1), G1 and A1, each under its own row scales
+    {
+        const int n = P->n[0];
+        const std::vector<double> A1 = mass(n);
+        std::vector<double> plus(A1), minus(A1);
+        for (size_t i = 0; i < plus.size(); ++i) {
+            plus[i] += etaB[0][i];
+            minus[i] -= etaB[0][i];
+        }
+        const std::vector<double>* single[4] = {&plus, &minus, &etaB[0], &A1};
+        OzSet* sets[4] = {&M->oz_x_plus, &M->oz_x_minus, &M->oz_x_stiff, &M->oz_x_mass};
+        for (int k = 0; k < 4; ++k) {
+            slice_operators_host({single[k]}, n, S, sl, rexp, nz);
+            const int ri = upload_rexp(rexp);
+            if (ri < 0) return set_error(TFDE_ENOMEM, "cudaMalloc of row exponents failed");
+            if ((st = upload_set(*sets[k], sl[0], n, S, nz[0], ri, s))) return st;
         }
     }
-    OZ_TRY(cudaMalloc((void**)&M->oz_planes, (size_t)S * N * sizeof(__nv_bfloat16)));
+    // y and z passes: (A_a | +G_a) and (A_a | -G_a) under common row scales; A2 alone.
+    // The second input (A1 x, resp. A2 A1 x) is smaller than the first by about
+    // max |G_a|; it is sliced as input * 2^k and G_a is stored as G_a * 2^-k
+    // (both exact), so that the two inputs share their line scale without
+    // losing bits.
+    for (int a = 1; a <= 2; ++a) {
+        const int n = P->n[a];
+        double gmax = 0.0;
+        for (double v : etaB[a]) gmax = std::fmax(gmax, std::fabs(v));
+        int k = 0;
+        if (gmax > 0.0) std::frexp(gmax, &k);
+        M->oz_shift[a] = k;
+        std::vector<double> Am = mass(n);
+        std::vector<double> pos(etaB[a]), neg(etaB[a]);
+        for (auto& v : pos) v = std::ldexp(v, -k);
+        for (auto& v : neg) v = -std::ldexp(v, -k);
+        slice_operators_host({&Am, &pos, &neg}, n, S, sl, rexp, nz);
+        const int ri = upload_rexp(rexp);
+        if (ri < 0) return set_error(TFDE_ENOMEM, "cudaMalloc of row exponents failed");
+        OzSet* m_set = a == 1 ? &M->oz_y_mass_c : &M->oz_z_mass_c;
+        OzSet* p_set = a == 1 ? &M->oz_y_plus : &M->oz_z_plus;
+        OzSet* n_set = a == 1 ? &M->oz_y_minus : &M->oz_z_minus;
+        if ((st = upload_set(*m_set, sl[0], n, S, nz[0], ri, s))) return st;
+        if ((st = upload_set(*p_set, sl[1], n, S, nz[1], ri, s))) return st;
+        if ((st = upload_set(*n_set, sl[2], n, S, nz[2], ri, s))) return st;
+        if (a == 1) {
+            // e = A2 w with w sliced as w * 2^k: store A2 * 2^-k
+            for (auto& v : Am) v = std::ldexp(v, -k);
+            slice_operators_host({&Am}, n, S, sl, rexp, nz);
+            const int r2 = upload_rexp(rexp);
+            if (r2 < 0) return set_error(TFDE_ENOMEM, "cudaMalloc of row exponents failed");
+            if ((st = upload_set(M->oz_y_mass, sl[0], n, S, nz[0], r2, s))) return st;
+        }
+    }
+    OZ_TRY(cudaStreamSynchronize(s));
+    // digit planes of two inputs and their maps
+    for (int in = 0; in < 2; ++in) {
+        OZ_TRY(cudaMalloc((void**)&M->oz_planes[in], (size_t)S * N * sizeof(__nv_bfloat16)));
+        for (int t = 0; t < S; ++t)
+            for (int a = 0; a < 3; ++a) {
+                const __nv_bfloat16* base = M->oz_planes[in] + (size_t)t * N;
+                st = (a == 0) ? tc::make_map_B_box(&M->oz_bmap[in][t][a], base, P->n, a, oz::BN)
+                              : tc::make_map_B(&M->oz_bmap[in][t][a], base, P->n, a);
+                if (st) return st;
+            }
+    }
     long long maxlines = 0;
     for (int a = 0; a < 3; ++a) maxlines = std::max(maxlines, (long long)(N / P->n[a]));
     OZ_TRY(cudaMalloc((void**)&M->oz_lexp, maxlines * sizeof(int)));
-    for (int t = 0; t < S; ++t)
-        for (int a = 0; a < 3; ++a) {
-            const __nv_bfloat16* base = M->oz_planes + (size_t)t * N;
-            int st;
-            if (a == 0) {
-                // x axis: 64-line boxes
-                CUtensorMap* m = &M->oz_bmap[t][a];
-                st = tc::make_map_B_box(m, base, P->n, a, oz::BN);
-            } else {
-                st = tc::make_map_B(&M->oz_bmap[t][a], base, P->n, a);
-            }
-            if (st) return st;
-        }
     return TFDE_OK;
 }
 
 void oz_free(MixedState* M) {
-    for (int a = 0; a < 3; ++a) {
-        cudaFree(M->oz_op[a]);
-        cudaFree(M->oz_rexp[a]);
-    }
-    cudaFree(M->oz_planes);
+    OzSet* sets[] = {&M->oz_x_plus, &M->oz_x_minus, &M->oz_x_stiff, &M->oz_x_mass, &M->oz_y_mass_c, &M->oz_y_plus,
+                     &M->oz_y_minus, &M->oz_y_mass, &M->oz_z_mass_c, &M->oz_z_plus, &M->oz_z_minus};
+    for (OzSet* z : sets) cudaFree(z->dev);
+    for (int* r : M->oz_rexp) cudaFree(r);
+    M->oz_rexp.clear();
+    cudaFree(M->oz_planes[0]);
+    cudaFree(M->oz_planes[1]);
     cudaFree(M->oz_lexp);
 }
 
-// out = sign * (G_axis x) + addend, G_axis = eta_a B_a, x sliced along `axis`.
-int oz_contract(const tfde_problem* P, int axis, const double* x, double sign, const double* addend, double* out,
-                cudaStream_t s) {
+namespace {
+
+// Slice one or two FP64 inputs along `axis` into the digit planes 0 / 1, the
+// second one taken as x1 * 2^sh1.
+void oz_slice(const tfde_problem* P, int axis, const double* x0, const double* x1, int sh1, cudaStream_t s) {
     MixedState* M = mixed(P);
-    const int S = OZ_SLICES;
     const AxisView v = axis_view(P->n, axis);
     const long long N = (long long)P->N;
+    stats_count_launch();
     if (axis == 0) {
-        stats_count_launch();
-        slice_x_kernel<<<grid_for(v.lines * 32), kT, 0, s>>>(x, P->n[0], v.lines, S, M->oz_planes, N, M->oz_lexp);
+        slice_x_kernel<<<grid_for(v.lines * 32), 256, 0, s>>>(x0, x1, sh1, P->n[0], v.lines, OZ_SLICES, M->oz_planes[0],
+                                                               M->oz_planes[1], N, M->oz_lexp);
     } else {
-        stats_count_launch();
-        slice_strided_kernel<<<grid_for(v.lines), kT, 0, s>>>(x, v, S, M->oz_planes, N, M->oz_lexp);
+        long long blocks = (v.lines + 31) / 32;
+        if (blocks > 152LL * 8) blocks = 152LL * 8;
+        slice_strided_kernel<<<(unsigned)blocks, 256, 0, s>>>(x0, x1, sh1, v, OZ_SLICES, M->oz_planes[0], M->oz_planes[1],
+                                                              N, M->oz_lexp);
     }
+}
+
+// out = vsign * sum_seg Op_seg (planes of input seg.input) [+ asign * addend]
+struct OzSegSpec {
+    const OzSet* op;
+    int input;  // digit planes 0 or 1
+};
+
+int oz_contract(const tfde_problem* P, int axis, const OzSegSpec* segs, int nseg, int vsign, const double* addend,
+                double asign, double* out, cudaStream_t s) {
+    MixedState* M = mixed(P);
+    const int S = OZ_SLICES;
+    const long long N = (long long)P->N;
     oz::Params prm;
     std::memset(&prm, 0, sizeof(prm));
-    for (int t = 0; t < S; ++t) {
-        prm.amaps[t] = M->oz_amap[axis][t];
-        prm.bmaps[t] = M->oz_bmap[t][axis];
+    double pairs = 0.0;
+    for (int g = 0; g < nseg; ++g) {
+        oz::Segment& G = prm.seg[g];
+        G.na = segs[g].op->na;
+        G.nb = S;
+        for (int t = 0; t < S; ++t) {
+            G.amaps[t] = segs[g].op->amap[t];
+            G.bmaps[t] = M->oz_bmap[segs[g].input][t][axis];
+        }
+        for (int sa = 0; sa < G.na; ++sa) pairs += S - sa;
     }
+    prm.nseg = nseg;
     prm.nslices = S;
     const long long n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
     prm.n = P->n[axis];
@@ -210,9 +382,10 @@ int oz_contract(const tfde_problem* P, int axis, const double* x, double sign, c
         prm.lines = (long long)prm.C * prm.P;
         prm.plane = (long long)prm.C * prm.n;
     }
-    prm.row_exp = M->oz_rexp[axis];
+    prm.row_exp = M->oz_rexp[segs[0].op->rexp_index];
     prm.line_exp = M->oz_lexp;
-    prm.sign = sign;
+    prm.value_sign = vsign;
+    prm.addend_sign = asign;
     prm.addend = addend;
     prm.out = out;
     prm.err = M->err;
@@ -225,29 +398,48 @@ int oz_contract(const tfde_problem* P, int axis, const double* x, double sign, c
     void* tok = stats_tc_begin(s);
     oz::oz_gemm_kernel<<<(unsigned)(grid < 1 ? 1 : grid), oz::NUM_THREADS, oz::SMEM_BYTES, s>>>(prm);
     cudaError_t e = cudaGetLastError();
-    // algorithmic bytes: digit slices read + FP64 out (+ addend) ; flops: every digit pair
-    const double na = prm.n, pairs = S * (S + 1) / 2;
-    stats_tc_end(tok, s, (2.0 * S + 8.0 + (addend ? 8.0 : 0.0)) * N + 2.0 * S * na * na, 2.0 * pairs * na * N);
+    // algorithmic bytes: digit planes of each input read once, FP64 out (+ addend);
+    // flops: 2 n per grid point per digit pair
+    const double na = prm.n;
+    stats_tc_end(tok, s, (2.0 * S * nseg + 8.0 + (addend ? 8.0 : 0.0)) * N, 2.0 * pairs * na * N);
     if (e != cudaSuccess) return set_error(TFDE_ECUDA, std::string("oz_gemm_kernel launch: ") + cudaGetErrorString(e));
     return TFDE_OK;
 }
 
-// y = A x (op A) or (2 A_N - A) x (op RHS), FP64-accurate.
-int accurate_apply(const tfde_problem* P, int op, const double* x, double* y, cudaStream_t s) {
-    const double sg = (op & 1) ? -1.0 : 1.0;
-    const AxisView vx = axis_view(P->n, 0), vy = axis_view(P->n, 1), vz = axis_view(P->n, 2);
-    double* t0 = P->w[tfde_problem::W_W];  // y1 = M1 x
-    double* t1 = P->w[tfde_problem::W_A];  // a, later y2
-    double* t2 = P->w[tfde_problem::W_C];  // M2 a, later M3 c
-    double* t3 = P->w[tfde_problem::W_E];  // c
+}  // namespace
+
+// y = vsign * (A x | (2 A_N - A) x | (A - A_N) x) [+ asign * addend], FP64-accurate.
+int accurate_apply_ex(const tfde_problem* P, int op, const double* x, double* y, int vsign, const double* addend,
+                      double asign, cudaStream_t s) {
+    MixedState* M = mixed(P);
+    const bool rhs = (op & 1) != 0;
+    const bool stiff = (op & TFDE_OP_STIFF) != 0;
+    double* ta = P->w[tfde_problem::W_A];
+    double* tw = P->w[tfde_problem::W_W];
+    double* tc_ = P->w[tfde_problem::W_C];
+    double* te = P->w[tfde_problem::W_E];
     int st;
-    launch_axis_stencil_f64(x, t0, vx, 1.0, nullptr, 0.0, s);
-    if ((st = oz_contract(P, 0, x, sg, t0, t1, s))) return st;          // a = y1 +- G1 x
-    launch_axis_stencil_f64(t1, t2, vy, 1.0, nullptr, 0.0, s);           // M2 a
-    if ((st = oz_contract(P, 1, t0, sg, t2, t3, s))) return st;         // c = M2 a +- G2 y1
-    launch_axis_stencil_f64(t0, t1, vy, 1.0, nullptr, 0.0, s);           // y2 = M2 y1
-    launch_axis_stencil_f64(t3, t2, vz, 1.0, nullptr, 0.0, s);           // M3 c
-    return oz_contract(P, 2, t1, sg, t2, y, s);                           // y = M3 c +- G3 y2
+    // x pass
+    oz_slice(P, 0, x, nullptr, 0, s);
+    const OzSet* xop = stiff ? (rhs ? &M->oz_x_stiff : &M->oz_x_stiff) : (rhs ? &M->oz_x_minus : &M->oz_x_plus);
+    OzSegSpec sa[1] = {{xop, 0}};
+    if ((st = oz_contract(P, 0, sa, 1, (stiff && rhs) ? -1 : 1, nullptr, 0.0, ta, s))) return st;
+    OzSegSpec sw[1] = {{&M->oz_x_mass, 0}};
+    if ((st = oz_contract(P, 0, sw, 1, 1, nullptr, 0.0, tw, s))) return st;
+    // y pass
+    oz_slice(P, 1, ta, tw, M->oz_shift[1], s);
+    OzSegSpec sc[2] = {{&M->oz_y_mass_c, 0}, {rhs ? &M->oz_y_minus : &M->oz_y_plus, 1}};
+    if ((st = oz_contract(P, 1, sc, 2, 1, nullptr, 0.0, tc_, s))) return st;
+    OzSegSpec se[1] = {{&M->oz_y_mass, 1}};
+    if ((st = oz_contract(P, 1, se, 1, 1, nullptr, 0.0, te, s))) return st;
+    // z pass
+    oz_slice(P, 2, tc_, te, M->oz_shift[2], s);
+    OzSegSpec sy[2] = {{&M->oz_z_mass_c, 0}, {rhs ? &M->oz_z_minus : &M->oz_z_plus, 1}};
+    return oz_contract(P, 2, sy, 2, vsign, addend, asign, y, s);
+}
+
+int accurate_apply(const tfde_problem* P, int op, const double* x, double* y, cudaStream_t s) {
+    return accurate_apply_ex(P, op, x, y, 1, nullptr, 0.0, s);
 }
 
 }  // namespace tfde

@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "tfde_internal.h"
+#include "tfde_givens.h"
 
 namespace tfde {
 
@@ -27,13 +28,15 @@ static int check_launch(const char* what) {
 //                     y = M3 c +- eta3 B3 e.
 int apply_A64(const tfde_problem* P, int op, const double* x, double* y, cudaStream_t s) {
     const bool rhs = (op & 1) != 0;
+    const bool stiff = (op & TFDE_OP_STIFF) != 0;   // (A - A_N) x: no mass term in the x pass
     const double sg = rhs ? -1.0 : 1.0;
     const AxisView vx = axis_view(P->n, 0), vy = axis_view(P->n, 1), vz = axis_view(P->n, 2);
     double* a = P->w[tfde_problem::W_A];
     double* w = P->w[tfde_problem::W_W];
     double* c = P->w[tfde_problem::W_C];
     double* e = P->w[tfde_problem::W_E];
-    launch_axis_gemm_f64(P->Ghat[rhs ? 1 : 0], x, a, vx, 1.0, nullptr, 0.0, s);
+    if (stiff) launch_axis_gemm_f64(P->G[0], x, a, vx, sg, nullptr, 0.0, s);
+    else launch_axis_gemm_f64(P->Ghat[rhs ? 1 : 0], x, a, vx, 1.0, nullptr, 0.0, s);
     launch_axis_stencil_f64(x, w, vx, 1.0, nullptr, 0.0, s);
     launch_axis_gemm_f64(P->G[1], w, c, vy, sg, a, 1.0, s);
     launch_axis_stencil_f64(w, e, vy, 1.0, nullptr, 0.0, s);
@@ -108,7 +111,7 @@ int true_residual(const tfde_problem* P, const double* b, const double* x, doubl
 
 // Preconditioned CG (Sec. 3.1) in FP64, true-residual stopping test.
 int pcg64(const tfde_problem* P, const double* b, double* x, double tol, int maxit, tfde_info* info,
-          cudaStream_t s) {
+          cudaStream_t s, bool r_given) {
     const auto t0 = clk::now();
     tfde_info loc{};
     double* r = P->w[tfde_problem::W_R];
@@ -127,7 +130,13 @@ int pcg64(const tfde_problem* P, const double* b, double* x, double tol, int max
         return TFDE_OK;
     }
     double nr;
-    if ((st = true_residual(P, b, x, r, &nr, s))) return st;
+    if (r_given) {
+        double rr0;
+        if ((st = dot(P, r, r, &rr0, s))) return st;
+        nr = std::sqrt(rr0);
+    } else if ((st = true_residual(P, b, x, r, &nr, s))) {
+        return st;
+    }
     loc.relres0 = nr / nb;
     int status = TFDE_ENOCONV;
     if (!std::isfinite(nr)) {
@@ -185,45 +194,13 @@ int pcg64(const tfde_problem* P, const double* b, double* x, double tol, int max
     return status;
 }
 
-// Givens-rotated least squares state of one GMRES cycle (host, FP64).
-struct GivensLS {
-    int m;
-    std::vector<double> R, cs, sn, g;
-    explicit GivensLS(int m_) : m(m_), R((size_t)(m_ + 1) * m_, 0.0), cs(m_), sn(m_), g(m_ + 1, 0.0) {}
-    double& at(int i, int j) { return R[(size_t)i * m + j]; }
-    // column j of the Hessenberg matrix (entries 0..j+1) -> rotated; returns |g_{j+1}|
-    double add_column(int j, const double* h) {
-        for (int i = 0; i <= j + 1; ++i) at(i, j) = h[i];
-        for (int i = 0; i < j; ++i) {
-            const double t = cs[i] * at(i, j) + sn[i] * at(i + 1, j);
-            at(i + 1, j) = -sn[i] * at(i, j) + cs[i] * at(i + 1, j);
-            at(i, j) = t;
-        }
-        const double den = std::hypot(at(j, j), at(j + 1, j));
-        cs[j] = den > 0.0 ? at(j, j) / den : 1.0;
-        sn[j] = den > 0.0 ? at(j + 1, j) / den : 0.0;
-        at(j, j) = den;
-        at(j + 1, j) = 0.0;
-        g[j + 1] = -sn[j] * g[j];
-        g[j] = cs[j] * g[j];
-        return std::fabs(g[j + 1]);
-    }
-    void solve(int k, std::vector<double>& y) {
-        y.assign(k, 0.0);
-        for (int i = k - 1; i >= 0; --i) {
-            double t = g[i];
-            for (int j = i + 1; j < k; ++j) t -= at(i, j) * y[j];
-            y[i] = t / at(i, i);
-        }
-    }
-};
 
 // Left-preconditioned restarted GMRES (Sec. 3.2, Eq. (one_side_system)), FP64,
 // classical Gram-Schmidt with one re-orthogonalisation.  Converged when the
 // true relative residual meets tol; the cycle stops on the preconditioned
 // residual estimate, scaled by the observed true/preconditioned ratio.
 int pgmres64(tfde_problem* P, const double* b, double* x, int restart, double tol, int maxit, tfde_info* info,
-             cudaStream_t s) {
+             cudaStream_t s, bool r_given) {
     const auto t0 = clk::now();
     tfde_info loc{};
     int st;
@@ -242,7 +219,13 @@ int pgmres64(tfde_problem* P, const double* b, double* x, int restart, double to
         return TFDE_OK;
     }
     double nr;
-    if ((st = true_residual(P, b, x, r, &nr, s))) return st;
+    if (r_given) {
+        double rr0;
+        if ((st = dot(P, r, r, &rr0, s))) return st;
+        nr = std::sqrt(rr0);
+    } else if ((st = true_residual(P, b, x, r, &nr, s))) {
+        return st;
+    }
     loc.relres0 = nr / nb;
     double ratio = 1.0;  // observed (true relres) / (preconditioned relres)
     int status = TFDE_ENOCONV;
@@ -312,17 +295,45 @@ int pgmres64(tfde_problem* P, const double* b, double* x, int restart, double to
     return status;
 }
 
-int cn_step64(tfde_problem* P, const double* u_prev, const double* F, const double* x0, double* u_next,
-              double tol, tfde_info* info, cudaStream_t s) {
+int mixed_pcg(tfde_problem*, const double*, double*, double, int, tfde_info*, cudaStream_t, bool);
+int mixed_pgmres(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t, bool);
+int accurate_apply(const tfde_problem*, int, const double*, double*, cudaStream_t);
+
+// A_N u into `out` (three tridiagonal sweeps; W_A and W_W as temporaries).
+static void mass_apply(const tfde_problem* P, const double* u, double* out, cudaStream_t s) {
+    launch_axis_stencil_f64(u, P->w[tfde_problem::W_A], axis_view(P->n, 0), 1.0, nullptr, 0.0, s);
+    launch_axis_stencil_f64(P->w[tfde_problem::W_A], P->w[tfde_problem::W_W], axis_view(P->n, 1), 1.0, nullptr, 0.0, s);
+    launch_axis_stencil_f64(P->w[tfde_problem::W_W], out, axis_view(P->n, 2), 1.0, nullptr, 0.0, s);
+}
+
+// One CN step (Eq. (CN), Eq. (linear_sys)) for either precision.  `chained`:
+// W_B / W_R hold b^{m-1} and the final true residual of u_prev, so that
+// A u_prev = b^{m-1} - r^{m-1} replaces the operator application.
+int cn_drive(tfde_problem* P, const double* u_prev, const double* F, const double* x0, double* u_next, double tol,
+             tfde_info* info, cudaStream_t s, bool chained) {
     double* b = P->w[tfde_problem::W_B];
-    int st = apply_A64(P, TFDE_OP_RHS, u_prev, b, s);
-    if (st) return st;
-    if (F) launch_axpby_f64(P->N, P->p.dt, F, 1.0, b, s);
-    const double* start = x0 ? x0 : u_prev;
+    double* r = P->w[tfde_problem::W_R];
+    double* an = P->w[tfde_problem::W_T];
+    const bool mixed_prec = P->prec == TFDE_MIXED;
+    const bool guess_is_prev = (x0 == nullptr || x0 == u_prev);
+    int st;
+    mass_apply(P, u_prev, an, s);
+    if (chained) {
+        launch_cn_chain(P->N, an, F, P->p.dt, b, r, s);
+    } else {
+        double* ku = P->w[tfde_problem::W_Q];
+        st = mixed_prec ? accurate_apply(P, TFDE_OP_STIFF, u_prev, ku, s) : apply_A64(P, TFDE_OP_STIFF, u_prev, ku, s);
+        if (st) return st;
+        launch_cn_first(P->N, an, ku, F, P->p.dt, b, r, s);
+    }
+    const double* start = guess_is_prev ? u_prev : x0;
     if (start != u_next)
         TFDE_CUDA_TRY(cudaMemcpyAsync(u_next, start, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    if (P->symmetric) return pcg64(P, b, u_next, tol, 10000, info, s);
-    return pgmres64(P, b, u_next, 20, tol, 10000, info, s);
+    const bool rg = guess_is_prev;  // r = b - A u_prev is the residual of the initial guess
+    if (P->symmetric)
+        return mixed_prec ? mixed_pcg(P, b, u_next, tol, 10000, info, s, rg) : pcg64(P, b, u_next, tol, 10000, info, s, rg);
+    return mixed_prec ? mixed_pgmres(P, b, u_next, 20, tol, 10000, info, s, rg)
+                      : pgmres64(P, b, u_next, 20, tol, 10000, info, s, rg);
 }
 
 }  // namespace tfde

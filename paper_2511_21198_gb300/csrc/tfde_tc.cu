@@ -116,21 +116,48 @@ void set_geometry(Params& P, const int n[3], int axis) {
 
 bool attr_done = false;
 
-int launch(const Params& P, cudaStream_t s, double bytes, double flops) {
+int set_attrs() {
     if (!attr_done) {
-        if (cudaFuncSetAttribute(axis_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
-            cudaSuccess)
+        if (cudaFuncSetAttribute(axis_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(axis_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
+                cudaSuccess)
             return set_error(TFDE_ECUDA, "cudaFuncSetAttribute(smem) failed");
         attr_done = true;
     }
+    return TFDE_OK;
+}
+
+int launch(const Params& P, cudaStream_t s, double bytes, double flops) {
+    if (int st = set_attrs()) return st;
     const long long total = P.ntiles * P.mhalves;
     long long grid = total < num_sms() ? total : num_sms();
     if (grid < 1) grid = 1;
     void* tok = stats_tc_begin(s);
-    axis_gemm_kernel<<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(P);
+    axis_gemm_kernel<false><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(P, nullptr, nullptr, 0, nullptr);
     cudaError_t e = cudaGetLastError();
     stats_tc_end(tok, s, bytes, flops);
     if (e != cudaSuccess) return set_error(TFDE_ECUDA, std::string("axis_gemm_kernel launch: ") + cudaGetErrorString(e));
+    return TFDE_OK;
+}
+
+int launch_grouped(const Params* groups, const long long* gstart, int ngroups, long long total, int b_kmajor,
+                   const int* gactive, int* err, cudaStream_t s, double bytes, double flops) {
+    if (int st = set_attrs()) return st;
+    if (total <= 0 || ngroups <= 0) return TFDE_OK;
+    Params p0;
+    std::memset(&p0, 0, sizeof(p0));
+    p0.ntiles = total;
+    p0.mhalves = 1;
+    p0.b_kmajor = b_kmajor;
+    p0.err = err;
+    long long grid = total < num_sms() ? total : num_sms();
+    void* tok = stats_tc_begin(s);
+    axis_gemm_kernel<true><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(p0, groups, gstart, ngroups, gactive);
+    cudaError_t e = cudaGetLastError();
+    stats_tc_end(tok, s, bytes, flops);
+    if (e != cudaSuccess)
+        return set_error(TFDE_ECUDA, std::string("grouped axis_gemm_kernel launch: ") + cudaGetErrorString(e));
     return TFDE_OK;
 }
 

@@ -15,6 +15,11 @@ int make_map_B(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int ax
 int make_map_B_box(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis, int box_lines);
 void set_geometry(Params& P, const int n[3], int axis);
 int launch(const Params& P, cudaStream_t s, double bytes, double flops);
+// One persistent launch over the tiles of `ngroups` contractions along the same
+// axis (descriptors and tile offsets gstart[0..ngroups] in device memory,
+// total = gstart[ngroups]); groups with gactive[g] == 0 are skipped.
+int launch_grouped(const Params* groups, const long long* gstart, int ngroups, long long total, int b_kmajor,
+                   const int* gactive, int* err, cudaStream_t s, double bytes, double flops);
 
 }  // namespace tc
 }  // namespace tfde

@@ -126,7 +126,26 @@ __device__ __forceinline__ void store1(const Params& p, long long idx, float v) 
 }
 
 // ---------------------------------------------------------------------- kernel
-__global__ void __launch_bounds__(NUM_THREADS, 1) axis_gemm_kernel(const __grid_constant__ Params p) {
+// Group of tile t in a grouped launch: the largest g with gstart[g] <= t.
+__device__ __forceinline__ int find_group(const long long* __restrict__ gstart, int ngroups, long long t) {
+    int lo = 0, hi = ngroups - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(gstart + mid) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// GROUPED = false: one contraction described by p0.  GROUPED = true: a work
+// list over `ngroups` independent contractions (one per problem of a batch,
+// same axis) whose descriptors sit in global memory; tile t belongs to group
+// g with gstart[g] <= t < gstart[g+1], and groups with gactive[g] == 0 are
+// skipped by all three roles alike.  p0 then carries only the common fields
+// (b_kmajor, err) and ntiles = gstart[ngroups], mhalves = 1.
+template <bool GROUPED>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    axis_gemm_kernel(const __grid_constant__ Params p0, const Params* __restrict__ groups,
+                     const long long* __restrict__ gstart, int ngroups, const int* __restrict__ gactive) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* stages = smem;
@@ -160,7 +179,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) axis_gemm_kernel(const __grid_
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    const long long total = p.ntiles * p.mhalves;
+    const long long total = p0.ntiles * p0.mhalves;
+    int* const err = p0.err;
+    const int b_kmajor = p0.b_kmajor;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -170,19 +191,28 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) axis_gemm_kernel(const __grid_
             uint32_t filled = 0, last_ph = 0;  // per-stage bitmasks
             bool ok = true;
             for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                const long long tile = t / p.mhalves;
-                const int mh = (int)(t % p.mhalves);
+                long long lt = t;
+                const Params* pp = &p0;
+                if (GROUPED) {
+                    const int g = find_group(gstart, ngroups, t);
+                    if (gactive && !__ldg(gactive + g)) { continue; }
+                    pp = groups + g;
+                    lt = t - __ldg(gstart + g);
+                }
+                const Params& p = *pp;
+                const long long tile = lt / p.mhalves;
+                const int mh = (int)(lt % p.mhalves);
                 for (int sg = 0; sg < p.nseg && ok; ++sg) {
                     const Segment& S = p.seg[sg];
                     for (int kb = 0; kb < S.nkb; ++kb) {
-                        if (!mbar_wait(&empty[s], ph ^ 1u, p.err)) { ok = false; break; }
+                        if (!mbar_wait(&empty[s], ph ^ 1u, err)) { ok = false; break; }
                         uint8_t* st = stages + s * STAGE_BYTES;
                         mbar_expect_tx(&full[s], (uint32_t)(S.na * A_TILE_BYTES + S.nb * B_TILE_BYTES));
                         for (int a = 0; a < S.na; ++a)
                             tma_load_2d(st + a * A_TILE_BYTES, &p.amaps[S.amap[a]], &full[s], kb * BK, mh * BM);
                         for (int b = 0; b < S.nb; ++b) {
                             uint8_t* dst = st + MAXA * A_TILE_BYTES + b * B_TILE_BYTES;
-                            if (p.b_kmajor) {
+                            if (b_kmajor) {
                                 tma_load_2d(dst, &p.bmaps[S.bmap[b]], &full[s], kb * BK, (int)(tile * BN));
                             } else {
                                 for (int blk = 0; blk < BN / 64; ++blk) {
@@ -202,39 +232,51 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) axis_gemm_kernel(const __grid_
             }
             // drain: every issued copy must land before the CTA can exit
             for (int i = 0; i < STAGES; ++i)
-                if (filled & (1u << i)) mbar_wait(&full[i], (last_ph >> i) & 1u, p.err, false);
+                if (filled & (1u << i)) mbar_wait(&full[i], (last_ph >> i) & 1u, err, false);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ------------------------------------------------ MMA issuer
-            const uint32_t idesc = instr_desc(BM, BN, p.b_kmajor ? 0 : 1);
+            const uint32_t idesc = instr_desc(BM, BN, b_kmajor ? 0 : 1);
+            // descriptor templates at stage 0; in-smem offsets are added to the
+            // start-address field (address >> 4, no carry below 256 KB)
+            const uint64_t a_desc0 = smem_desc(smem_u32(stages), 16, 512, 4);
+            const uint64_t b_desc0 = b_kmajor ? smem_desc(smem_u32(stages + MAXA * A_TILE_BYTES), 16, 512, 4)
+                                                : smem_desc(smem_u32(stages + MAXA * A_TILE_BYTES), 64 * BK * 2, 1024, 2);
+            const uint32_t b_k16 = b_kmajor ? (32u >> 4) : (2048u >> 4);
             int s = 0;
             uint32_t ph = 0;
             bool ok = true;
             long long it = 0;
-            for (long long t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
+            for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                long long lt = t;
+                const Params* pp = &p0;
+                if (GROUPED) {
+                    const int g = find_group(gstart, ngroups, t);
+                    if (gactive && !__ldg(gactive + g)) { continue; }
+                    pp = groups + g;
+                    lt = t - __ldg(gstart + g);
+                }
+                const Params& p = *pp;
                 const int buf = (int)(it & 1);
                 const uint32_t use = (uint32_t)(it >> 1);
-                if (!mbar_wait(&tempty[buf], (use & 1u) ^ 1u, p.err)) { ok = false; break; }
+                if (!mbar_wait(&tempty[buf], (use & 1u) ^ 1u, err)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
-                uint32_t acc = 0;
                 for (int sg = 0; sg < p.nseg && ok; ++sg) {
                     const Segment& S = p.seg[sg];
                     for (int kb = 0; kb < S.nkb; ++kb) {
-                        if (!mbar_wait(&full[s], ph, p.err)) { ok = false; break; }
+                        if (!mbar_wait(&full[s], ph, err)) { ok = false; break; }
                         tc_fence_after();
-                        const uint8_t* st = stages + s * STAGE_BYTES;
+                        const uint64_t ad_s = a_desc0 + (uint64_t)((s * STAGE_BYTES) >> 4);
+                        const uint64_t bd_s = b_desc0 + (uint64_t)((s * STAGE_BYTES) >> 4);
                         for (int pr = 0; pr < S.npair; ++pr) {
-                            const uint32_t a_addr = smem_u32(st + S.pa[pr] * A_TILE_BYTES);
-                            const uint32_t b_addr = smem_u32(st + MAXA * A_TILE_BYTES + S.pb[pr] * B_TILE_BYTES);
+                            const uint64_t ad_p = ad_s + (uint64_t)((S.pa[pr] * A_TILE_BYTES) >> 4);
+                            const uint64_t bd_p = bd_s + (uint64_t)((S.pb[pr] * B_TILE_BYTES) >> 4);
 #pragma unroll
                             for (int k16 = 0; k16 < BK / 16; ++k16) {
-                                const uint64_t ad = smem_desc(a_addr + k16 * 32, 16, 512, 4);
-                                const uint64_t bd = p.b_kmajor ? smem_desc(b_addr + k16 * 32, 16, 512, 4)
-                                                               : smem_desc(b_addr + k16 * 2048, 64 * BK * 2, 1024, 2);
-                                umma_bf16(d_tmem, ad, bd, idesc, acc);
-                                acc = 1;
+                                const uint32_t acc = (sg == 0 && kb == 0 && pr == 0 && k16 == 0) ? 0u : 1u;
+                                umma_bf16(d_tmem, ad_p + (uint64_t)(k16 * (32 >> 4)), bd_p + k16 * b_k16, idesc, acc);
                             }
                         }
                         umma_commit(&empty[s]);
@@ -242,10 +284,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) axis_gemm_kernel(const __grid_
                     }
                 }
                 if (ok) umma_commit(&tfull[buf]);
+                ++it;
             }
             // every MMA issued by this thread has completed once mma_done fires
             umma_commit(mma_done);
-            mbar_wait(mma_done, 0, p.err, false);
+            mbar_wait(mma_done, 0, err, false);
         }
     } else {
         // ---------------------------------------------------- epilogue warps
@@ -255,17 +298,26 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) axis_gemm_kernel(const __grid_
         const int rsub = lane >> 3;           // transposed phase: 4 rows / columns per instruction
         const int cq = (lane & 7) * 4;        // ... and 4 consecutive elements per lane
         long long it = 0;
-        for (long long t = blockIdx.x; t < total; t += gridDim.x, ++it) {
+        for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+            long long lt = t;
+            const Params* pp = &p0;
+            if (GROUPED) {
+                const int g = find_group(gstart, ngroups, t);
+                if (gactive && !__ldg(gactive + g)) { continue; }
+                pp = groups + g;
+                lt = t - __ldg(gstart + g);
+            }
+            const Params& p = *pp;
             const int buf = (int)(it & 1);
             const uint32_t use = (uint32_t)(it >> 1);
             int ok = 1;
-            if (lane == 0) ok = mbar_wait(&tfull[buf], use & 1u, p.err) ? 1 : 0;
+            if (lane == 0) ok = mbar_wait(&tfull[buf], use & 1u, err) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;  // warp-uniform: the TMEM loads below are .sync.aligned
             __syncwarp();
             tc_fence_after();
-            const long long tile = t / p.mhalves;
-            const int mh = (int)(t % p.mhalves);
+            const long long tile = lt / p.mhalves;
+            const int mh = (int)(lt % p.mhalves);
             const int mrow0 = mh * BM + 32 * q;   // first output row of this warp
             for (int cc = 0; cc < BN / 2; cc += 32) {
                 const int c0 = half * (BN / 2) + cc;
@@ -274,7 +326,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) axis_gemm_kernel(const __grid_
 #pragma unroll
                 for (int j = 0; j < 32; ++j) stg[lane * EPI_STRIDE + j] = p.alpha * __uint_as_float(r[j]);
                 __syncwarp();
-                if (p.b_kmajor) {
+                if (b_kmajor) {
                     // stg[row][line]; output Y[line * n1 + m], m contiguous
 #pragma unroll 2
                     for (int i8 = 0; i8 < 8; ++i8) {
@@ -341,6 +393,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) axis_gemm_kernel(const __grid_
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[buf]);
+            ++it;
         }
     }
 

@@ -20,7 +20,7 @@ TFDE_EBREAKDOWN, TFDE_ENAN, TFDE_ETIMEOUT, TFDE_EUNSUPPORTED = 5, 6, 7, 8
 STATUS_NAMES = {0: "TFDE_OK", 1: "TFDE_EINVAL", 2: "TFDE_ENOMEM", 3: "TFDE_ECUDA", 4: "TFDE_ENOCONV",
                 5: "TFDE_EBREAKDOWN", 6: "TFDE_ENAN", 7: "TFDE_ETIMEOUT", 8: "TFDE_EUNSUPPORTED"}
 TFDE_FP64, TFDE_MIXED = 0, 1
-TFDE_OP_A, TFDE_OP_RHS, TFDE_OP_FAST = 0, 1, 2
+TFDE_OP_A, TFDE_OP_RHS, TFDE_OP_FAST, TFDE_OP_STIFF = 0, 1, 2, 4
 
 
 class tfde_params(Structure):
@@ -54,7 +54,7 @@ class TfdeError(RuntimeError):
 _lib = None
 
 EXPORTS = ["tfde_assemble", "tfde_destroy", "tfde_matvec", "tfde_precond", "tfde_pcg", "tfde_pgmres",
-           "tfde_cn_step", "tfde_source_example2", "tfde_coefficients", "tfde_host_coefficients",
+           "tfde_cn_step", "tfde_cn_advance", "tfde_source_example2", "tfde_coefficients", "tfde_host_coefficients",
            "tfde_stats_reset", "tfde_stats_get", "tfde_mass_apply_noalloc", "tfde_last_error", "tfde_version"]
 
 
@@ -76,6 +76,7 @@ def load(path: str | None = None):
         "tfde_pcg": ([vp, vp, vp, c_double, c_int, POINTER(tfde_info), vp], c_int),
         "tfde_pgmres": ([vp, vp, vp, c_int, c_double, c_int, POINTER(tfde_info), vp], c_int),
         "tfde_cn_step": ([vp, vp, vp, vp, vp, c_double, POINTER(tfde_info), vp], c_int),
+        "tfde_cn_advance": ([vp, vp, vp, c_int, c_double, POINTER(tfde_info), vp], c_int),
         "tfde_source_example2": ([vp, c_double, c_double, vp, vp], c_int),
         "tfde_coefficients": ([vp, c_int, POINTER(c_double), POINTER(c_double), POINTER(c_double)], c_int),
         "tfde_host_coefficients": ([POINTER(tfde_params), c_int, POINTER(c_double), POINTER(c_double),
@@ -172,6 +173,15 @@ def tfde_cn_step(prob: int, u_prev, F_half, x0, u_next, tol: float, stream=None,
                              byref(info), _stream(stream))
     if check:
         _check(st, "tfde_cn_step")
+    info.status = st
+    return info
+
+
+def tfde_cn_advance(prob: int, u, F_half, restart: bool, tol: float, stream=None, check: bool = True) -> tfde_info:
+    info = tfde_info()
+    st = load().tfde_cn_advance(prob, _ptr(u), _ptr(F_half), 1 if restart else 0, tol, byref(info), _stream(stream))
+    if check:
+        _check(st, "tfde_cn_advance")
     info.status = st
     return info
 

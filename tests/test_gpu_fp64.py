@@ -222,3 +222,53 @@ def test_full_size_matvec_sampled_and_precond_eigenvector(T):
         assert relerr(to_host(z), r / lam) < 1e-12
     finally:
         c.close()
+
+
+def test_stiffness_operator(T):
+    """TFDE_OP_STIFF gives the three Kronecker stiffness terms of Eq. (linear_sys) alone."""
+    c = Case(T, (9, 8, 7), (0.3, 0.6, 0.8), (1.0, 2.0, 0.5), (0.5, 2.0, 1.5), 0.1)
+    try:
+        v = inp.uniform_vector(c.o.shape, 71)
+        y = to_dev(np.zeros_like(v))
+        T.tfde_matvec(c.h, T.TFDE_OP_STIFF, to_dev(v), y)
+        assert relerr(to_host(y), o.stiffness_terms(c.o, v)) < 1e-13
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("sym", [True, False])
+def test_cn_advance_matches_cn_step(T, sym):
+    """The chained in-place advance (A u^{m-1} = b^{m-1} - r^{m-1}) follows the
+    same trajectory as independent CN steps; an intervening solver call or a
+    different buffer breaks the chain and forces a full restart."""
+    n, M = (12, 10, 8), 6
+    c = Case(T, n, (0.4, 0.6, 0.8), (1.0,) * 3, (1.0,) * 3 if sym else (0.5, 0.7, 0.9), 1.0 / M)
+    try:
+        u0 = o.exact_u(c.o, 0.0, "exp")
+        F = to_dev(np.zeros_like(u0))
+        ua = to_dev(u0)
+        us, un = to_dev(u0), to_dev(np.zeros_like(u0))
+        for m in range(1, M + 1):
+            th = (m - 0.5) * c.o.dt
+            T.tfde_source_example2(c.h, -math.exp(-th), -math.exp(-th), F)
+            ia = T.tfde_cn_advance(c.h, ua, F, m == 1, 1e-12)
+            ib = T.tfde_cn_step(c.h, us, F, None, un, 1e-12)   # also invalidates the chain
+            us, un = un, us
+            assert ia.relres <= 1e-12 and ib.relres <= 1e-12
+            assert relerr(to_host(ua), to_host(us)) < 1e-10
+        # a stale chain (tfde_cn_step ran in between) must not be used: the
+        # result still equals the oracle step
+        th = (M + 0.5) * c.o.dt
+        T.tfde_source_example2(c.h, -math.exp(-th), -math.exp(-th), F)
+        ref = to_host(ua).copy()
+        T.tfde_cn_advance(c.h, ua, F, False, 1e-12)
+        b = o.rhs(c.o, ref, to_host(F))
+        tau = o.build_tau(c.o)
+        if sym:
+            xo, _ = o.pcg(lambda v: o.apply_A(c.o, v), lambda r: o.apply_Pinv(tau, r), b, ref, 1e-14, 1000)
+        else:
+            xo, _ = o.gmres_left(lambda v: o.apply_A(c.o, v), lambda r: o.apply_Pinv(tau, r), b, ref, 1e-14, 1000,
+                                 20, "true")
+        assert relerr(to_host(ua), xo) < 1e-10
+    finally:
+        c.close()

@@ -55,6 +55,10 @@ def test_fast_matvec_and_precond(T, case):
         # accurate (non-fast) operator of a mixed problem is FP64-exact
         T.tfde_matvec(h, T.TFDE_OP_A, to_dev(v), y)
         assert relerr(to_host(y), o.apply_A(op, v)) < 1e-13
+        T.tfde_matvec(h, T.TFDE_OP_RHS, to_dev(v), y)
+        assert relerr(to_host(y), o.rhs(op, v, None)) < 1e-13
+        T.tfde_matvec(h, T.TFDE_OP_STIFF, to_dev(v), y)
+        assert relerr(to_host(y), o.stiffness_terms(op, v)) < 1e-13
         # preconditioner: exact tau inverse within the BF16 rounding of S_n ...
         T.tfde_precond(h, to_dev(v), y)
         z = to_host(y)
@@ -133,4 +137,119 @@ def test_mixed_trajectory_n16(T):
 def test_mixed_rejects_unsupported_sizes(T):
     with pytest.raises(T.TfdeError) as e:
         T.tfde_assemble(T.make_params((12, 16, 16), (0.5,) * 3, (1.0,) * 3, (1.0,) * 3, 0.1), T.TFDE_MIXED)
+    assert e.value.status == T.TFDE_EUNSUPPORTED
+
+
+def test_accurate_apply_wide_dynamic_range(T):
+    """Lines whose entries span many orders of magnitude: the exact-integer
+    slice contraction (49-bit fixed point under each row and line maximum) is
+    accurate to the FP64 level in norm, relative to |A| |v|."""
+    n = (32, 24, 40)
+    d, kp, km = (0.35, 0.65, 0.9), (1.0, 2.0, 1.0), (0.5, 1.0, 2.0)
+    h = T.tfde_assemble(T.make_params(n, d, kp, km, 0.3), T.TFDE_MIXED)
+    try:
+        op = o.Problem(n=n, delta=d, kp=kp, km=km, dt=0.3)
+        rng = np.random.default_rng(81)
+        v = inp.uniform_vector(op.shape, 82) * 10.0 ** rng.uniform(-12, 3, size=op.shape)
+        y = to_dev(np.zeros_like(v))
+        T.tfde_matvec(h, T.TFDE_OP_A, to_dev(v), y)
+        ref = o.apply_A(op, v)
+        # |A| |v| elementwise: the same Kronecker terms with absolute-valued factors
+        absop = o.Problem(n=n, delta=d, kp=kp, km=km, dt=0.3)
+        absop.B = [np.abs(B) for B in absop.B]
+        absAv = o.apply_A(absop, np.abs(v))
+        assert np.abs(to_host(y) - ref).max() <= 1e-13 * absAv.max()
+    finally:
+        T.tfde_destroy(h)
+
+
+def test_mixed_cn_advance_trajectory(T):
+    """Chained mixed-precision advance over 8 steps equals FP64 steps at a tight residual."""
+    n, M = (24, 16, 32), 8
+    d, k = (0.6, 0.7, 0.8), (1.0,) * 3
+    hm = T.tfde_assemble(T.make_params(n, d, k, k, 1.0 / M), T.TFDE_MIXED)
+    hf = T.tfde_assemble(T.make_params(n, d, k, k, 1.0 / M), T.TFDE_FP64)
+    try:
+        op = o.Problem(n=n, delta=d, kp=k, km=k, dt=1.0 / M)
+        u0 = o.exact_u(op, 0.0, "exp")
+        F = to_dev(np.zeros_like(u0))
+        um, uf = to_dev(u0), to_dev(u0)
+        for m in range(1, M + 1):
+            th = (m - 0.5) * op.dt
+            T.tfde_source_example2(hm, -math.exp(-th), -math.exp(-th), F)
+            im = T.tfde_cn_advance(hm, um, F, m == 1, 1e-12)
+            T.tfde_cn_advance(hf, uf, F, m == 1, 1e-13)
+            assert im.relres <= 1e-12
+        assert relerr(to_host(um), to_host(uf)) < 1e-10
+    finally:
+        T.tfde_destroy(hm)
+        T.tfde_destroy(hf)
+
+
+@pytest.mark.parametrize("n,restart", [((16, 16, 16), 20), ((40, 32, 24), 20), ((64, 24, 40), 4)])
+def test_mixed_pgmres_matches_dense_solution(T, n, restart):
+    """Non-symmetric system: FP32 inner GMRES cycles inside FP64 refinement
+    reach a 1e-12 true residual without falling back to FP64 cycles, and agree
+    with the oracle's GMRES solution driven to 1e-14."""
+    d, kp, km = (0.3, 0.6, 0.8), (1.0, 1.5, 2.0), (0.5, 2.0, 1.0)
+    h = T.tfde_assemble(T.make_params(n, d, kp, km, 0.1), T.TFDE_MIXED)
+    try:
+        op = o.Problem(n=n, delta=d, kp=kp, km=km, dt=0.1)
+        b = inp.uniform_vector(op.shape, 52)
+        tau = o.build_tau(op)
+        xref, _ = o.gmres_left(lambda v: o.apply_A(op, v), lambda r: o.apply_Pinv(tau, r), b, np.zeros_like(b),
+                               1e-14, 4000, restart=20, criterion="true")
+        x = to_dev(np.zeros_like(b))
+        info = T.tfde_pgmres(h, to_dev(b), x, restart, 1e-12, 2000)
+        assert info.relres <= 1e-12 and info.fallback == 0
+        assert info.refine_sweeps >= 1 and info.restarts == info.refine_sweeps
+        assert relerr(to_host(x), xref) < 1e-10
+    finally:
+        T.tfde_destroy(h)
+
+
+def test_mixed_cn_step_nonsymmetric_tight_parity(T):
+    """One non-symmetric CN step (PGMRES) from the same u^{m-1}, mixed path at a
+    1e-12 true residual against the oracle's 1e-14 GMRES solution."""
+    n = (32, 24, 48)
+    d, kp, km = (0.3, 0.6, 0.8), (1.0,) * 3, (0.5,) * 3
+    h = T.tfde_assemble(T.make_params(n, d, kp, km, 0.02), T.TFDE_MIXED)
+    try:
+        op = o.Problem(n=n, delta=d, kp=kp, km=km, dt=0.02)
+        u0 = inp.smoothed_uniform(op.shape, 2)
+        b = o.rhs(op, u0, None)
+        tau = o.build_tau(op)
+        xo, _ = o.gmres_left(lambda v: o.apply_A(op, v), lambda r: o.apply_Pinv(tau, r), b, u0, 1e-14, 4000,
+                             restart=20, criterion="true")
+        un = to_dev(np.zeros_like(u0))
+        info = T.tfde_cn_step(h, to_dev(u0), None, None, un, 1e-12)
+        assert info.relres <= 1e-12 and info.fallback == 0 and info.restarts >= 1
+        assert relerr(to_host(un), xo) < 1e-10
+    finally:
+        T.tfde_destroy(h)
+
+
+def test_mixed_nonsymmetric_advance_matches_fp64(T):
+    """Chained non-symmetric advance (f = 0, smoothed noise u0) over 6 steps:
+    mixed PGMRES equals the all-FP64 PGMRES path at tight residuals."""
+    n, M = (48, 40, 32), 6
+    d, kp, km = (0.3, 0.6, 0.8), (1.0,) * 3, (0.5,) * 3
+    hm = T.tfde_assemble(T.make_params(n, d, kp, km, 1.0 / M), T.TFDE_MIXED)
+    hf = T.tfde_assemble(T.make_params(n, d, kp, km, 1.0 / M), T.TFDE_FP64)
+    try:
+        u0 = inp.smoothed_uniform(tuple(reversed(n)), 2)
+        um, uf = to_dev(u0), to_dev(u0)
+        for m in range(1, M + 1):
+            im = T.tfde_cn_advance(hm, um, None, m == 1, 1e-12)
+            T.tfde_cn_advance(hf, uf, None, m == 1, 1e-13)
+            assert im.relres <= 1e-12 and im.fallback == 0
+        assert relerr(to_host(um), to_host(uf)) < 1e-10
+    finally:
+        T.tfde_destroy(hm)
+        T.tfde_destroy(hf)
+
+
+def test_mixed_rejects_sizes_beyond_exact_accumulation(T):
+    with pytest.raises(T.TfdeError) as e:
+        T.tfde_assemble(T.make_params((456, 8, 8), (0.5,) * 3, (1.0,) * 3, (1.0,) * 3, 0.1), T.TFDE_MIXED)
     assert e.value.status == T.TFDE_EUNSUPPORTED
