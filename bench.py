@@ -52,6 +52,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--guess-order", type=int, default=2,
+                    help="initial guess of the mixed path: 0 previous step, 1/2 polynomial extrapolation")
     return ap.parse_args(argv)
 
 
@@ -239,6 +241,7 @@ def run_ours(args):
     u0 = torch.from_numpy(inp.example2_initial(n)).to(dev)
     # ---- mixed precision (the metric)
     h = T.tfde_assemble(params, T.TFDE_MIXED, stream)
+    T.tfde_set_guess_order(h, args.guess_order)
     u, un, F = u0.clone(), torch.empty_like(u0), torch.empty_like(u0)
     u, un, _, _, _ = run_steps(h, u, un, F, 0, args.warmup)
     torch.cuda.synchronize()
@@ -337,7 +340,10 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "n": n, "unknowns": n ** 3, "delta": list(W["delta"]),
                        "k_plus": list(W["kp"]), "k_minus": list(W["km"]), "dt": dt, "tol": tol,
                        "solver": "PCG(tau) inner FP32 / split-BF16 tcgen05, FP64 iterative refinement",
-                       "initial_guess": "previous step u^(m-1)",
+                       "initial_guess": ("previous step u^(m-1)" if args.guess_order == 0 else
+                                         f"order-{args.guess_order} polynomial extrapolation in time "
+                                         "(A x0 from stored A u, no extra operator application)"),
+                       "fp64_path_initial_guess": "previous step u^(m-1)",
                        "step_api": "tfde_cn_advance (chained: A u^(m-1) = b^(m-1) - r^(m-1))",
                        "l2": "inputs larger than L2 (each FP64 vector 134 MB, working set > 2 GB)",
                        "parallelism": f"replicas x{world}"},

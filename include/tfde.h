@@ -177,6 +177,68 @@ int tfde_cn_advance(const tfde_problem* prob, double* u, const double* F_half, i
                     tfde_info* info, void* stream);
 
 /*
+ * tfde_set_guess_order -- initial guess of the chained tfde_cn_advance steps:
+ *   order 0 (default): x0 = u^{m-1}, as the paper's solves from the previous
+ *   time level; order 1: x0 = 2u^{m-1} - u^{m-2}; order 2:
+ *   x0 = 3u^{m-1} - 3u^{m-2} + u^{m-3} (polynomial extrapolation in time).
+ *   The problem then keeps (u, A u) of the two previous levels (4 vectors of
+ *   n_1 n_2 n_3 doubles, allocated on first use); A x0, and with it the
+ *   initial residual, is the same combination of the stored A u, so the guess
+ *   costs one fused vector pass.  The order in force is limited by the history
+ *   the chain has built since its last restart (0 on the first two steps).
+ *   The guess changes only the iterations, not the stopping rule.
+ *   Errors: TFDE_EINVAL for order outside 0..2 or a NULL problem.
+ */
+int tfde_set_guess_order(tfde_problem* prob, int order);
+
+/* ------------------------------------------------------------------ batches */
+typedef struct tfde_batch tfde_batch;
+
+/*
+ * tfde_batch_create -- `count` independent problems of possibly different
+ * sizes and coefficients (params[0..count-1], each as for tfde_assemble with
+ * TFDE_MIXED: every n_a a multiple of 8 and at most 448), solved together.
+ *   Each problem takes the CN step of Eq. (CN) / Eq. (linear_sys) with
+ *   left-preconditioned restarted GMRES(restart) (Sec. 3.2, Eq.
+ *   (one_side_system)) inside FP64 iterative refinement, whatever its symmetry.
+ *   The problems advance in lock step through the Arnoldi iterations: every
+ *   split-BF16 operator or preconditioner pass is one persistent tensor-core
+ *   launch over a work list of the tiles of all problems (largest problems
+ *   first), every vector step one launch over all problems, and a problem
+ *   whose inner cycle has met its target drops out of the work lists.  The
+ *   FP64 residual of each refinement sweep is evaluated per problem (exact
+ *   slice contraction) on a pool of streams.
+ *   1 <= count <= 1024, 1 <= restart <= 63.  Errors: as tfde_assemble for any
+ *   problem; TFDE_EINVAL for count/restart out of range.  *out is NULL on
+ *   failure.  Synchronises `stream`.  Device memory: the workspace of each
+ *   problem plus (restart + 1) FP32 basis vectors per problem.
+ */
+int tfde_batch_create(const tfde_params* params, int count, int restart, void* stream, tfde_batch** out);
+
+/* Release a batch and all its problems (NULL is a no-op).  Synchronises the device. */
+int tfde_batch_destroy(tfde_batch* batch);
+
+/* Number of problems of a batch (0 for NULL). */
+int tfde_batch_count(const tfde_batch* batch);
+
+/*
+ * tfde_batch_cn_advance -- one CN step u_i^{m-1} -> u_i^m IN PLACE for every
+ * problem i of the batch, with the chained right-hand side and initial
+ * residual of tfde_cn_advance (x0 = u_i^{m-1}).
+ *   u: host array of `count` device pointers (in/out, distinct), in the order
+ *   of the params given to tfde_batch_create.  F_half: host array of `count`
+ *   device pointers to the source cell averages (entries may be NULL for
+ *   f = 0), or NULL for f = 0 everywhere.  restart: as tfde_cn_advance (1 on
+ *   the first call and whenever any u_i was written in between).  Stopping
+ *   rule per problem: ||b_i - A_i u_i|| <= tol ||b_i|| in FP64.  infos: host
+ *   array of `count` results (may be NULL); ms is the wall time of the whole
+ *   batched step.  Returns TFDE_OK when every problem converged, else the
+ *   first failing status (TFDE_ENOCONV, TFDE_ENAN, ...).  Synchronises `stream`.
+ */
+int tfde_batch_cn_advance(tfde_batch* batch, double* const* u, const double* const* F_half, int restart, double tol,
+                          tfde_info* infos, void* stream);
+
+/*
  * tfde_source_example2 -- cell averages F_{ijk} (Sec. 2, definition of F^{m-1/2})
  * of the manufactured source of Sec. 4, Example 2, on Omega = (0,1)^3:
  *   f = cP P(x)P(y)P(z) + cS [S_a(x)P(y)P(z) + P(x)S_b(y)P(z) + P(x)P(y)S_c(z)],

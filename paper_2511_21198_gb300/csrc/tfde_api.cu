@@ -8,6 +8,9 @@
 namespace tfde {
 const char* last_error_text();
 int assemble_problem(const tfde_params*, int, cudaStream_t, tfde_problem**);
+int batch_create(const tfde_params*, int, int, cudaStream_t, tfde_batch**);
+int batch_destroy(tfde_batch*);
+int batch_cn_advance(tfde_batch*, double* const*, const double* const*, int, double, tfde_info*, cudaStream_t);
 int destroy_problem(tfde_problem*);
 int host_coefficients(const tfde_params*, int, double*, double*, double*, double*);
 int pcg64(const tfde_problem*, const double*, double*, double, int, tfde_info*, cudaStream_t, bool);
@@ -145,6 +148,39 @@ int tfde_cn_advance(const tfde_problem* prob, double* u, const double* F_half, i
         P->chain_u = u;
     }
     return st;
+}
+
+int tfde_set_guess_order(tfde_problem* prob, int order) {
+    if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
+    if (order < 0 || order > 2) return set_error(TFDE_EINVAL, "guess order must be 0, 1 or 2");
+    prob->guess_order = order;
+    return TFDE_OK;
+}
+
+int tfde_batch_create(const tfde_params* params, int count, int restart, void* stream, tfde_batch** out) {
+    if (!params || !out) return set_error(TFDE_EINVAL, "NULL argument");
+    *out = nullptr;
+    int st = pre_call();
+    if (st) return st;
+    return batch_create(params, count, restart, (cudaStream_t)stream, out);
+}
+
+int tfde_batch_destroy(tfde_batch* batch) { return batch_destroy(batch); }
+
+int tfde_batch_cn_advance(tfde_batch* batch, double* const* u, const double* const* F_half, int restart, double tol,
+                          tfde_info* infos, void* stream) {
+    if (!batch || !u) return set_error(TFDE_EINVAL, "NULL argument");
+    int st;
+    if ((st = pre_call()) || (st = check_tol(tol))) return st;
+    const int C = tfde_batch_count(batch);
+    for (int i = 0; i < C; ++i) {
+        if ((st = check_dev(u[i], "u[i]"))) return st;
+        if (F_half && F_half[i] && (st = check_dev(F_half[i], "F_half[i]"))) return st;
+        if (F_half && F_half[i] == u[i]) return set_error(TFDE_EINVAL, "F_half[i] aliases u[i]");
+        for (int k = 0; k < i; ++k)
+            if (u[k] == u[i]) return set_error(TFDE_EINVAL, "two problems share one u buffer");
+    }
+    return batch_cn_advance(batch, u, F_half, restart, tol, infos, (cudaStream_t)stream);
 }
 
 int tfde_source_example2(const tfde_problem* prob, double cP, double cS, double* F, void* stream) {

@@ -312,6 +312,8 @@ int destroy_problem(tfde_problem* P) {
     cudaFree(P->src1d);
     for (auto& v : P->w) cudaFree(v);
     cudaFree(P->V);
+    for (auto& hk : P->H)
+        for (auto& v : hk) cudaFree(v);
     cudaFree(P->red);
     cudaFree(P->red_out);
     if (P->red_host) cudaFreeHost(P->red_host);

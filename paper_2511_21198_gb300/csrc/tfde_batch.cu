@@ -1,0 +1,734 @@
+// Batched solve of many independent problems of uneven size (the same
+// Crank-Nicolson step of Eq. (CN) / Eq. (linear_sys) per problem, Sec. 3.2
+// left-preconditioned GMRES per problem).  The problems advance in lock step
+// through the Arnoldi iterations; every split-BF16 operator or preconditioner
+// pass is ONE persistent tcgen05 launch over a tile work list that spans all
+// problems (largest first), every vector step is one launch over a block table
+// of all problems, and the host reads the Hessenberg columns of all problems
+// with one copy per iteration.  A problem whose cycle has converged is masked
+// out of the work lists.  The FP64 refinement residual of each problem (the
+// exact-integer slice contraction) and the per-problem right-hand sides run
+// on a small pool of streams.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tfde_givens.h"
+#include "tfde_internal.h"
+#include "tfde_mixed.h"
+#include "tfde_stats.h"
+
+namespace tfde {
+
+int assemble_problem(const tfde_params* params, int precision, cudaStream_t s, tfde_problem** out);
+int destroy_problem(tfde_problem* P);
+int cn_prepare(tfde_problem* P, const double* u_prev, const double* F, const double* x0, double* u_next,
+               cudaStream_t s, bool chained, bool* r_given);
+int pgmres64(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t, bool);
+
+namespace {
+
+constexpr int kBT = 256;       // threads per block of the vector kernels
+constexpr int kCH = 4096;      // elements per block chunk
+constexpr int kHS = 192;       // per-problem Hessenberg stride: H (64) | H2 (64) | -y (64)
+constexpr int kSS = 8;         // per-problem scalar stride
+constexpr int kStreams = 8;    // stream pool of the per-problem work
+// scalar slots
+enum { S_SC32 = 0, S_SPLIT = 1, S_ADD = 2, S_BB = 3, S_RR = 4, S_WW = 5 };
+
+// Per-problem vector pointers of the batched kernels.
+struct BVec {
+    long long N;
+    float* x32;
+    float* r32;
+    float* V;          // basis, vector j at V + j N
+    __nv_bfloat16* ph;
+    __nv_bfloat16* pl;
+    __nv_bfloat16* rh;
+    __nv_bfloat16* rl;
+    const double* r64;
+    double* x64;
+};
+
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+struct KSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double sh[kBT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kBT / 32; ++w) t += sh[w];
+    return t;
+}
+
+// The chunk of block b: problem bi[b], elements [bo[b], min(bo[b] + kCH, N)).
+#define BK_PROLOGUE                                        \
+    const int inst = bi[blockIdx.x];                       \
+    if (!act[inst]) return;                                \
+    const BVec& v = vt[inst];                              \
+    const long long e0 = bo[blockIdx.x];                   \
+    const long long e1 = e0 + kCH < v.N ? e0 + kCH : v.N;
+
+// r32 = r64 * sc ; split into (rh, rl) ; x32 = 0
+__global__ __launch_bounds__(kBT) void bk_scale64to32(const BVec* __restrict__ vt, const int* __restrict__ bi,
+                                                     const long long* __restrict__ bo, const int* __restrict__ act,
+                                                     const double* __restrict__ sc) {
+    BK_PROLOGUE
+    const double f = sc[inst * kSS + S_SC32];
+    for (long long e = e0 + threadIdx.x; e < e1; e += kBT) {
+        const float x = (float)(v.r64[e] * f);
+        v.r32[e] = x;
+        split_bf16(x, v.rh[e], v.rl[e]);
+        v.x32[e] = 0.f;
+    }
+}
+
+// <V_{m0+j}, V_jw>, j < mc (<= 8), per block into part[(m0 + j) * NB + b]
+__global__ __launch_bounds__(kBT) void bk_multidot(const BVec* __restrict__ vt, const int* __restrict__ bi,
+                                                  const long long* __restrict__ bo, const int* __restrict__ act,
+                                                  int m0, int mc, int jw, double* __restrict__ part) {
+    const int inst = bi[blockIdx.x];
+    const bool on = act[inst] != 0;
+    KSum k[8];
+    if (on) {
+        const BVec& v = vt[inst];
+        const long long e0 = bo[blockIdx.x];
+        const long long e1 = e0 + kCH < v.N ? e0 + kCH : v.N;
+        const float* w = v.V + (long long)jw * v.N;
+        for (long long e = e0 + threadIdx.x; e < e1; e += kBT) {
+            const float we = w[e];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < mc) k[j].add(v.V[(long long)(m0 + j) * v.N + e] * we);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (j < mc) {
+            const double t = block_sum((double)k[j].s - (double)k[j].c);
+            if (threadIdx.x == 0) part[(long long)(m0 + j) * gridDim.x + blockIdx.x] = t;
+        }
+    }
+}
+
+// out[i * ostride + ooff + j] = sum over problem i's blocks of part[(p0 + j) * NB + b], j < m
+__global__ void bk_reduce(const double* __restrict__ part, int NB, const int* __restrict__ bstart,
+                          const int* __restrict__ act, int p0, double* __restrict__ out, int ostride, int ooff) {
+    const int inst = blockIdx.x, j = blockIdx.y;
+    if (!act[inst]) return;
+    double acc = 0.0;
+    for (int b = bstart[inst] + threadIdx.x; b < bstart[inst + 1]; b += 32) acc += part[(long long)(p0 + j) * NB + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) out[inst * ostride + ooff + j] = acc;
+}
+
+// target -= sum_{j < m} coef[i * kHS + coff + j] V_j ; target = V_jt (jt >= 0) or x32 (jt < 0)
+__global__ __launch_bounds__(kBT) void bk_multiaxpy(const BVec* __restrict__ vt, const int* __restrict__ bi,
+                                                   const long long* __restrict__ bo, const int* __restrict__ act,
+                                                   int m, int jt, const double* __restrict__ coef, int coff) {
+    BK_PROLOGUE
+    __shared__ float hs[64];
+    for (int j = threadIdx.x; j < m; j += blockDim.x) hs[j] = (float)coef[inst * kHS + coff + j];
+    __syncthreads();
+    float* w = jt >= 0 ? v.V + (long long)jt * v.N : v.x32;
+    for (long long e = e0 + threadIdx.x; e < e1; e += kBT) {
+        float acc = w[e];
+        for (int j = 0; j < m; ++j) acc = fmaf(-hs[j], v.V[(long long)j * v.N + e], acc);
+        w[e] = acc;
+    }
+}
+
+// V_jw *= sc ; split into (ph, pl)
+__global__ __launch_bounds__(kBT) void bk_scale_split(const BVec* __restrict__ vt, const int* __restrict__ bi,
+                                                     const long long* __restrict__ bo, const int* __restrict__ act,
+                                                     int jw, const double* __restrict__ sc) {
+    BK_PROLOGUE
+    const float f = (float)sc[inst * kSS + S_SPLIT];
+    float* w = v.V + (long long)jw * v.N;
+    for (long long e = e0 + threadIdx.x; e < e1; e += kBT) {
+        const float x = w[e] * f;
+        w[e] = x;
+        split_bf16(x, v.ph[e], v.pl[e]);
+    }
+}
+
+// x64 += sc * x32
+__global__ __launch_bounds__(kBT) void bk_add32to64(const BVec* __restrict__ vt, const int* __restrict__ bi,
+                                                   const long long* __restrict__ bo, const int* __restrict__ act,
+                                                   const double* __restrict__ sc) {
+    BK_PROLOGUE
+    const double f = sc[inst * kSS + S_ADD];
+    for (long long e = e0 + threadIdx.x; e < e1; e += kBT) v.x64[e] += f * (double)v.x32[e];
+}
+
+#undef BK_PROLOGUE
+
+using clk = std::chrono::steady_clock;
+
+}  // namespace
+}  // namespace tfde
+
+struct tfde_batch {
+    int count = 0;
+    int restart = 20;
+    std::vector<tfde_problem*> P;   // sorted by decreasing size
+    std::vector<int> caller;        // sorted position -> caller index
+    // grouped descriptors: matvec passes [5][count], preconditioner passes
+    // 0..4 [5][count], last preconditioner pass writing V_j [restart+1][count]
+    tfde::tc::Params* d_mv = nullptr;
+    tfde::tc::Params* d_pc = nullptr;
+    tfde::tc::Params* d_pcl = nullptr;
+    int mv_axis[5] = {}, pc_axis[6] = {};
+    double mv_bytes[5] = {}, mv_flops[5] = {}, pc_bytes[6] = {}, pc_flops[6] = {};
+    long long* d_gstart = nullptr;  // [3][count + 1]
+    long long gtotal[3] = {};
+    // vector kernels: per-problem pointers and the block table
+    tfde::BVec* d_vt = nullptr;
+    tfde::BVec* h_vt = nullptr;
+    int* d_bi = nullptr;
+    long long* d_bo = nullptr;
+    int* d_bstart = nullptr;
+    int NB = 0;
+    double* d_part = nullptr;       // (restart + 2) * NB partial sums
+    double* d_h = nullptr;          // count * kHS
+    double* h_h = nullptr;
+    double* d_s = nullptr;          // count * kSS
+    double* h_s = nullptr;
+    int* d_act = nullptr;
+    int* h_act = nullptr;
+    int* d_err = nullptr;
+    int* h_err = nullptr;
+    cudaStream_t aux[tfde::kStreams] = {};
+    cudaEvent_t ev[tfde::kStreams] = {};
+    cudaEvent_t fork_ev = nullptr;
+    bool chain_ok = false;
+    std::vector<double*> chain_u;
+    std::vector<int*> own_err;      // each problem's own error flag while it reports to d_err
+};
+
+namespace tfde {
+namespace {
+
+#define B_TRY(expr)                                                                        \
+    do {                                                                                   \
+        cudaError_t e__ = (expr);                                                          \
+        if (e__ != cudaSuccess)                                                            \
+            return set_error(TFDE_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e__)); \
+    } while (0)
+
+void fork(tfde_batch* B, cudaStream_t s) {
+    cudaEventRecord(B->fork_ev, s);
+    for (auto& a : B->aux) cudaStreamWaitEvent(a, B->fork_ev, 0);
+}
+void join(tfde_batch* B, cudaStream_t s) {
+    for (int k = 0; k < kStreams; ++k) {
+        cudaEventRecord(B->ev[k], B->aux[k]);
+        cudaStreamWaitEvent(s, B->ev[k], 0);
+    }
+}
+
+int free_batch(tfde_batch* B) {
+    if (!B) return TFDE_OK;
+    cudaDeviceSynchronize();
+    for (size_t i = 0; i < B->P.size(); ++i) {
+        if (i < B->own_err.size()) tfde::mixed(B->P[i])->err = B->own_err[i];
+        destroy_problem(B->P[i]);
+    }
+    cudaFree(B->d_mv);
+    cudaFree(B->d_pc);
+    cudaFree(B->d_pcl);
+    cudaFree(B->d_gstart);
+    cudaFree(B->d_vt);
+    if (B->h_vt) cudaFreeHost(B->h_vt);
+    cudaFree(B->d_bi);
+    cudaFree(B->d_bo);
+    cudaFree(B->d_bstart);
+    cudaFree(B->d_part);
+    cudaFree(B->d_h);
+    if (B->h_h) cudaFreeHost(B->h_h);
+    cudaFree(B->d_s);
+    if (B->h_s) cudaFreeHost(B->h_s);
+    cudaFree(B->d_act);
+    if (B->h_act) cudaFreeHost(B->h_act);
+    cudaFree(B->d_err);
+    if (B->h_err) cudaFreeHost(B->h_err);
+    for (int k = 0; k < kStreams; ++k) {
+        if (B->aux[k]) cudaStreamDestroy(B->aux[k]);
+        if (B->ev[k]) cudaEventDestroy(B->ev[k]);
+    }
+    if (B->fork_ev) cudaEventDestroy(B->fork_ev);
+    delete B;
+    return TFDE_OK;
+}
+
+int grouped(tfde_batch* B, const tc::Params* d, int axis, double bytes, double flops, cudaStream_t s) {
+    return tc::launch_grouped(d, B->d_gstart + (size_t)axis * (B->count + 1), B->count, B->gtotal[axis],
+                              axis == 0 ? 1 : 0, B->d_act, B->d_err, s, bytes, flops);
+}
+
+// v_j (split planes PL_P of every active problem) -> PL_R = A v_j
+int grouped_matvec(tfde_batch* B, cudaStream_t s) {
+    for (int k = 0; k < 5; ++k) {
+        int st = grouped(B, B->d_mv + (size_t)k * B->count, B->mv_axis[k], B->mv_bytes[k], B->mv_flops[k], s);
+        if (st) return st;
+    }
+    return TFDE_OK;
+}
+
+// PL_R -> V_j = P^{-1} (PL_R) in FP32
+int grouped_precond(tfde_batch* B, int j, cudaStream_t s) {
+    for (int k = 0; k < 5; ++k) {
+        int st = grouped(B, B->d_pc + (size_t)k * B->count, B->pc_axis[k], B->pc_bytes[k], B->pc_flops[k], s);
+        if (st) return st;
+    }
+    return grouped(B, B->d_pcl + (size_t)j * B->count, B->pc_axis[5], B->pc_bytes[5], B->pc_flops[5], s);
+}
+
+void vec_launch_count() { stats_count_launch(); }
+
+// dots <V_{p0+j}, V_jw>, j < m, of every active problem into out (stride, offset)
+void bdots(tfde_batch* B, int p0, int m, int jw, double* out, int ostride, int ooff, cudaStream_t s) {
+    for (int m0 = p0; m0 < p0 + m; m0 += 8) {
+        const int mc = (p0 + m - m0) < 8 ? (p0 + m - m0) : 8;
+        vec_launch_count();
+        bk_multidot<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, m0, mc, jw, B->d_part);
+    }
+    vec_launch_count();
+    bk_reduce<<<dim3((unsigned)B->count, (unsigned)m), 32, 0, s>>>(B->d_part, B->NB, B->d_bstart, B->d_act, p0, out,
+                                                                  ostride, ooff);
+}
+
+int upload_act_scalars(tfde_batch* B, cudaStream_t s) {
+    B_TRY(cudaMemcpyAsync(B->d_act, B->h_act, B->count * sizeof(int), cudaMemcpyHostToDevice, s));
+    B_TRY(cudaMemcpyAsync(B->d_s, B->h_s, (size_t)B->count * kSS * sizeof(double), cudaMemcpyHostToDevice, s));
+    return TFDE_OK;
+}
+
+int read_back(tfde_batch* B, bool hess, cudaStream_t s) {
+    if (hess) B_TRY(cudaMemcpyAsync(B->h_h, B->d_h, (size_t)B->count * kHS * sizeof(double), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaMemcpyAsync(B->h_s, B->d_s, (size_t)B->count * kSS * sizeof(double), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaMemcpyAsync(B->h_err, B->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaStreamSynchronize(s));
+    if (*B->h_err) return set_error(TFDE_ETIMEOUT, "tensor-core kernel wait ran out (device error flag set)");
+    return TFDE_OK;
+}
+
+// One lock-step left-preconditioned GMRES cycle (Sec. 3.2) for every problem
+// with act[i] set: A d_i = r32_i (x32_i = 0 on entry, d_i on exit), stopping
+// problem i once its preconditioned residual estimate falls below
+// theta[i] * beta_i.  est[i] = final estimate / beta_i; its[i] = steps.
+int batch_cycle(tfde_batch* B, const std::vector<int>& outer, const std::vector<double>& theta,
+                std::vector<double>& est, std::vector<int>& its, cudaStream_t s) {
+    const int C = B->count, R = B->restart;
+    int st;
+    for (int i = 0; i < C; ++i) B->h_act[i] = outer[i];
+    B_TRY(cudaMemcpyAsync(B->d_act, B->h_act, C * sizeof(int), cudaMemcpyHostToDevice, s));
+    if ((st = grouped_precond(B, 0, s))) return st;
+    bdots(B, 0, 1, 0, B->d_s, kSS, S_WW, s);
+    if ((st = read_back(B, false, s))) return st;
+    std::vector<GivensLS> ls;
+    ls.reserve(C);
+    std::vector<double> beta(C, 0.0);
+    std::vector<int> inner(C, 0);
+    int any = 0;
+    for (int i = 0; i < C; ++i) {
+        ls.emplace_back(R);
+        its[i] = 0;
+        est[i] = 1.0;
+        if (!outer[i]) continue;
+        beta[i] = std::sqrt(B->h_s[i * kSS + S_WW]);
+        if (!std::isfinite(beta[i])) return set_error(TFDE_ENAN, "non-finite preconditioned residual");
+        if (beta[i] > 0.0) {
+            inner[i] = 1;
+            ls[i].g[0] = beta[i];
+            B->h_s[i * kSS + S_SPLIT] = 1.0 / beta[i];
+            any = 1;
+        }
+    }
+    for (int i = 0; i < C; ++i) B->h_act[i] = inner[i];
+    if ((st = upload_act_scalars(B, s))) return st;
+    if (any) {
+        vec_launch_count();
+        bk_scale_split<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, 0, B->d_s);
+    }
+    std::vector<double> h(R + 2);
+    for (int j = 0; j < R && any; ++j) {
+        if ((st = grouped_matvec(B, s))) return st;
+        if ((st = grouped_precond(B, j + 1, s))) return st;
+        // CGS2, coefficients on the device
+        bdots(B, 0, j + 1, j + 1, B->d_h, kHS, 0, s);
+        vec_launch_count();
+        bk_multiaxpy<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, j + 1, j + 1, B->d_h, 0);
+        bdots(B, 0, j + 1, j + 1, B->d_h, kHS, 64, s);
+        vec_launch_count();
+        bk_multiaxpy<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, j + 1, j + 1, B->d_h, 64);
+        bdots(B, j + 1, 1, j + 1, B->d_s, kSS, S_WW, s);
+        if ((st = read_back(B, true, s))) return st;
+        any = 0;
+        for (int i = 0; i < C; ++i) {
+            if (!inner[i]) continue;
+            for (int q = 0; q <= j; ++q) h[q] = B->h_h[i * kHS + q] + B->h_h[i * kHS + 64 + q];
+            const double hn = std::sqrt(B->h_s[i * kSS + S_WW]);
+            if (!std::isfinite(hn)) return set_error(TFDE_ENAN, "non-finite Arnoldi vector");
+            h[j + 1] = hn;
+            const double e = ls[i].add_column(j, h.data());
+            its[i] = j + 1;
+            est[i] = e / beta[i];
+            if (e <= theta[i] * beta[i] || hn == 0.0) {
+                inner[i] = 0;
+            } else {
+                B->h_s[i * kSS + S_SPLIT] = 1.0 / hn;
+                any = 1;
+            }
+        }
+        if (!any) break;
+        for (int i = 0; i < C; ++i) B->h_act[i] = inner[i];
+        if ((st = upload_act_scalars(B, s))) return st;
+        vec_launch_count();
+        bk_scale_split<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, j + 1, B->d_s);
+    }
+    // d_i = V_i y_i
+    int kmax = 0;
+    for (int i = 0; i < C; ++i) {
+        for (int q = 0; q < 64; ++q) B->h_h[i * kHS + 128 + q] = 0.0;
+        if (!outer[i] || its[i] == 0) continue;
+        std::vector<double> y;
+        ls[i].solve(its[i], y);
+        for (int q = 0; q < its[i]; ++q) B->h_h[i * kHS + 128 + q] = -y[q];
+        kmax = std::max(kmax, its[i]);
+    }
+    if (kmax > 0) {
+        for (int i = 0; i < C; ++i) B->h_act[i] = outer[i] && its[i] > 0;
+        B_TRY(cudaMemcpyAsync(B->d_act, B->h_act, C * sizeof(int), cudaMemcpyHostToDevice, s));
+        B_TRY(cudaMemcpyAsync(B->d_h, B->h_h, (size_t)C * kHS * sizeof(double), cudaMemcpyHostToDevice, s));
+        vec_launch_count();
+        bk_multiaxpy<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, kmax, -1, B->d_h, 128);
+    }
+    return TFDE_OK;
+}
+
+// FP64 norms of W_B and W_R of every problem with act set, into S_BB / S_RR.
+void batch_norms(tfde_batch* B, const std::vector<int>& act, bool with_b, cudaStream_t s) {
+    fork(B, s);
+    for (int i = 0; i < B->count; ++i) {
+        if (!act[i]) continue;
+        tfde_problem* P = B->P[i];
+        cudaStream_t a = B->aux[i % kStreams];
+        const double* b = P->w[tfde_problem::W_B];
+        const double* r = P->w[tfde_problem::W_R];
+        if (with_b) {
+            launch_multidot_f64(P->N, 1, b, 0, b, P->red, P->nblk, a);
+            launch_reduce_finish(P->red, P->nblk, 1, B->d_s + i * kSS + S_BB, a);
+        }
+        launch_multidot_f64(P->N, 1, r, 0, r, P->red, P->nblk, a);
+        launch_reduce_finish(P->red, P->nblk, 1, B->d_s + i * kSS + S_RR, a);
+    }
+    join(B, s);
+}
+
+}  // namespace
+
+int batch_create(const tfde_params* params, int count, int restart, cudaStream_t s, tfde_batch** out) {
+    *out = nullptr;
+    if (!params || count < 1 || count > 1024) return set_error(TFDE_EINVAL, "batch count must lie in [1, 1024]");
+    if (restart < 1 || restart > 63) return set_error(TFDE_EINVAL, "batch restart must lie in [1, 63]");
+    tfde_batch* B = new tfde_batch();
+    B->count = count;
+    B->restart = restart;
+    int st;
+    // problems, sorted by decreasing size (largest tiles first in the work lists)
+    std::vector<int> idx(count);
+    for (int i = 0; i < count; ++i) idx[i] = i;
+    auto sz = [&](int i) { return (long long)params[i].n[0] * params[i].n[1] * params[i].n[2]; };
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return sz(a) > sz(b); });
+    B->caller = idx;
+    if (cudaMalloc((void**)&B->d_err, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&B->h_err, sizeof(int)) != cudaSuccess || cudaMemset(B->d_err, 0, sizeof(int)) != cudaSuccess) {
+        free_batch(B);
+        return set_error(TFDE_ENOMEM, "allocation of the batch error flag failed");
+    }
+    for (int k = 0; k < count; ++k) {
+        tfde_problem* P = nullptr;
+        if ((st = assemble_problem(&params[idx[k]], TFDE_MIXED, s, &P))) {
+            free_batch(B);
+            return st;
+        }
+        B->P.push_back(P);
+        // every kernel of the batch, per-problem ones included, reports to one flag
+        B->own_err.push_back(mixed(P)->err);
+        mixed(P)->err = B->d_err;
+        if ((st = mixed_prepare_gmres(P, restart))) {
+            free_batch(B);
+            return st;
+        }
+    }
+    auto fail = [&](int code, const char* what) {
+        free_batch(B);
+        return set_error(code, what);
+    };
+    // grouped descriptors
+    const size_t C = count, PS = sizeof(tc::Params);
+    std::vector<tc::Params> mv(5 * C), pc(5 * C), pcl((size_t)(restart + 1) * C);
+    std::vector<long long> gstart(3 * (C + 1), 0);
+    for (size_t i = 0; i < C; ++i) {
+        tfde_problem* P = B->P[i];
+        MixedState* M = mixed(P);
+        tc::Params tmp[6];
+        int axes[6];
+        double by[6], fl[6];
+        fast_pass_descriptors(P, 0, nullptr, tmp, axes, by, fl);
+        for (int k = 0; k < 5; ++k) {
+            mv[k * C + i] = tmp[k];
+            B->mv_axis[k] = axes[k];
+            B->mv_bytes[k] += by[k];
+            B->mv_flops[k] += fl[k];
+        }
+        for (int j = 0; j <= restart; ++j) {
+            fast_pass_descriptors(P, 1, M->V32 + (size_t)j * P->N, tmp, axes, by, fl);
+            if (j == 0)
+                for (int k = 0; k < 6; ++k) {
+                    if (k < 5) pc[k * C + i] = tmp[k];
+                    B->pc_axis[k] = axes[k];
+                    B->pc_bytes[k] += by[k];
+                    B->pc_flops[k] += fl[k];
+                }
+            pcl[(size_t)j * C + i] = tmp[5];
+        }
+        for (int a = 0; a < 3; ++a) {
+            tc::Params g;
+            tc::set_geometry(g, P->n, a);
+            gstart[a * (C + 1) + i + 1] = gstart[a * (C + 1) + i] + g.ntiles * g.mhalves;
+        }
+    }
+    for (int a = 0; a < 3; ++a) B->gtotal[a] = gstart[a * (C + 1) + C];
+    if (cudaMalloc((void**)&B->d_mv, mv.size() * PS) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_pc, pc.size() * PS) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_pcl, pcl.size() * PS) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_gstart, gstart.size() * sizeof(long long)) != cudaSuccess)
+        return fail(TFDE_ENOMEM, "cudaMalloc of the grouped descriptors failed");
+    // block table
+    std::vector<int> bstart(C + 1, 0), bi;
+    std::vector<long long> bo;
+    for (size_t i = 0; i < C; ++i) {
+        const long long N = (long long)B->P[i]->N;
+        const long long nb = (N + kCH - 1) / kCH;
+        for (long long b = 0; b < nb; ++b) {
+            bi.push_back((int)i);
+            bo.push_back(b * kCH);
+        }
+        bstart[i + 1] = bstart[i] + (int)nb;
+    }
+    B->NB = bstart[C];
+    if (cudaMalloc((void**)&B->d_vt, C * sizeof(BVec)) != cudaSuccess ||
+        cudaMallocHost((void**)&B->h_vt, C * sizeof(BVec)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_bi, bi.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_bo, bo.size() * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_bstart, bstart.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_part, (size_t)(restart + 2) * B->NB * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_h, C * kHS * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&B->h_h, C * kHS * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_s, C * kSS * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&B->h_s, C * kSS * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_act, C * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&B->h_act, C * sizeof(int)) != cudaSuccess)
+        return fail(TFDE_ENOMEM, "allocation of the batch workspace failed");
+    for (size_t i = 0; i < C; ++i) {
+        tfde_problem* P = B->P[i];
+        MixedState* M = mixed(P);
+        BVec& v = B->h_vt[i];
+        v.N = (long long)P->N;
+        v.x32 = M->f[F_X];
+        v.r32 = M->f[F_R];
+        v.V = M->V32;
+        v.ph = M->hi[PL_P];
+        v.pl = M->lo[PL_P];
+        v.rh = M->hi[PL_R];
+        v.rl = M->lo[PL_R];
+        v.r64 = P->w[tfde_problem::W_R];
+        v.x64 = nullptr;
+    }
+    std::memset(B->h_s, 0, C * kSS * sizeof(double));
+    std::memset(B->h_h, 0, C * kHS * sizeof(double));
+    if (cudaMemcpyAsync(B->d_mv, mv.data(), mv.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(B->d_pc, pc.data(), pc.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(B->d_pcl, pcl.data(), pcl.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(B->d_gstart, gstart.data(), gstart.size() * sizeof(long long), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(B->d_bi, bi.data(), bi.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(B->d_bo, bo.data(), bo.size() * sizeof(long long), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(B->d_bstart, bstart.data(), bstart.size() * sizeof(int), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemsetAsync(B->d_err, 0, sizeof(int), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(TFDE_ECUDA, "upload of the batch tables failed");
+    for (int k = 0; k < kStreams; ++k) {
+        if (cudaStreamCreateWithFlags(&B->aux[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->ev[k], cudaEventDisableTiming) != cudaSuccess)
+            return fail(TFDE_ECUDA, "stream pool creation failed");
+    }
+    if (cudaEventCreateWithFlags(&B->fork_ev, cudaEventDisableTiming) != cudaSuccess)
+        return fail(TFDE_ECUDA, "event creation failed");
+    *out = B;
+    return TFDE_OK;
+}
+
+int batch_destroy(tfde_batch* B) { return free_batch(B); }
+
+}  // namespace tfde
+
+extern "C" int tfde_batch_count(const tfde_batch* B) { return B ? B->count : 0; }
+
+namespace tfde {
+
+int batch_cn_advance(tfde_batch* B, double* const* u, const double* const* F, int restart_chain, double tol,
+                     tfde_info* infos, cudaStream_t s) {
+    const auto t0 = clk::now();
+    const int C = B->count;
+    int st;
+    // per-problem pointers (sorted order)
+    std::vector<double*> uu(C);
+    std::vector<const double*> ff(C, nullptr);
+    for (int i = 0; i < C; ++i) {
+        uu[i] = u[B->caller[i]];
+        if (F) ff[i] = F[B->caller[i]];
+        B->h_vt[i].x64 = uu[i];
+    }
+    const bool chained = !restart_chain && B->chain_ok && B->chain_u == uu;
+    B->chain_ok = false;
+    B_TRY(cudaMemcpyAsync(B->d_vt, B->h_vt, C * sizeof(BVec), cudaMemcpyHostToDevice, s));
+    // right-hand sides and initial residuals (x0 = u^{m-1}), stream pool
+    fork(B, s);
+    for (int i = 0; i < C; ++i) {
+        bool rg = false;
+        if ((st = cn_prepare(B->P[i], uu[i], ff[i], nullptr, uu[i], B->aux[i % kStreams], chained, &rg))) {
+            join(B, s);
+            return st;
+        }
+    }
+    join(B, s);
+    std::vector<int> all(C, 1);
+    batch_norms(B, all, true, s);
+    if ((st = read_back(B, false, s))) return st;
+    std::vector<double> nb(C), nr(C), ratio(C, 1.0), theta(C), est(C);
+    std::vector<int> its(C), stall(C, 0), done(C, 0), outer(C, 0);
+    std::vector<tfde_info> info(C);
+    std::vector<int> status(C, TFDE_ENOCONV);
+    for (int i = 0; i < C; ++i) {
+        nb[i] = std::sqrt(B->h_s[i * kSS + S_BB]);
+        nr[i] = std::sqrt(B->h_s[i * kSS + S_RR]);
+        info[i] = tfde_info{};
+        info[i].relres0 = nb[i] > 0.0 ? nr[i] / nb[i] : 0.0;
+        if (!std::isfinite(nb[i]) || !std::isfinite(nr[i])) return set_error(TFDE_ENAN, "non-finite right-hand side");
+    }
+    const int max_sweeps = 200;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        int any = 0;
+        for (int i = 0; i < C; ++i) {
+            outer[i] = 0;
+            if (done[i]) continue;
+            if (nb[i] == 0.0 || nr[i] <= tol * nb[i]) {
+                done[i] = 1;
+                status[i] = TFDE_OK;
+                continue;
+            }
+            outer[i] = 1;
+            any = 1;
+            double th = 0.5 * tol * nb[i] / nr[i] / ratio[i];
+            theta[i] = th < 1e-4 ? 1e-4 : th;
+            B->h_s[i * kSS + S_SC32] = 1.0 / nr[i];
+            B->h_s[i * kSS + S_ADD] = nr[i];
+            B->h_act[i] = 1;
+        }
+        if (!any) break;
+        for (int i = 0; i < C; ++i) B->h_act[i] = outer[i];
+        if ((st = upload_act_scalars(B, s))) return st;
+        stats_count_launch();
+        bk_scale64to32<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, B->d_s);
+        if ((st = batch_cycle(B, outer, theta, est, its, s))) return st;
+        for (int i = 0; i < C; ++i) B->h_act[i] = outer[i];
+        B_TRY(cudaMemcpyAsync(B->d_act, B->h_act, C * sizeof(int), cudaMemcpyHostToDevice, s));
+        stats_count_launch();
+        bk_add32to64<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, B->d_s);
+        // accurate FP64 residuals r = b - A x
+        fork(B, s);
+        for (int i = 0; i < C; ++i) {
+            if (!outer[i]) continue;
+            tfde_problem* P = B->P[i];
+            if ((st = accurate_apply_ex(P, TFDE_OP_A, uu[i], P->w[tfde_problem::W_R], -1, P->w[tfde_problem::W_B], 1.0,
+                                        B->aux[i % kStreams]))) {
+                join(B, s);
+                return st;
+            }
+        }
+        join(B, s);
+        batch_norms(B, outer, false, s);
+        if ((st = read_back(B, false, s))) return st;
+        for (int i = 0; i < C; ++i) {
+            if (!outer[i]) continue;
+            const double nr_old = nr[i];
+            nr[i] = std::sqrt(B->h_s[i * kSS + S_RR]);
+            info[i].iters += its[i];
+            info[i].restarts++;
+            info[i].refine_sweeps++;
+            if (!std::isfinite(nr[i])) {
+                done[i] = 1;
+                status[i] = set_error(TFDE_ENAN, "non-finite residual");
+                continue;
+            }
+            if (est[i] > 0.0) {
+                const double observed = (nr[i] / nr_old) / est[i];
+                ratio[i] = observed > 1.0 ? observed : 1.0;
+            }
+            stall[i] = (nr[i] > 0.5 * nr_old) ? stall[i] + 1 : 0;
+            if (stall[i] >= 2 && nr[i] > tol * nb[i]) {
+                // refinement stopped contracting: finish this problem with FP64 cycles
+                tfde_problem* P = B->P[i];
+                tfde_info sub{};
+                info[i].fallback = 1;
+                status[i] = pgmres64(P, P->w[tfde_problem::W_B], uu[i], B->restart, tol, 10000, &sub, s, false);
+                info[i].iters += sub.iters;
+                info[i].restarts += sub.restarts;
+                nr[i] = sub.relres * nb[i];
+                done[i] = 1;
+            }
+        }
+    }
+    const float ms = (float)std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    int worst = TFDE_OK;
+    for (int i = 0; i < C; ++i) {
+        if (!done[i]) status[i] = TFDE_ENOCONV;
+        info[i].relres = nb[i] > 0.0 ? nr[i] / nb[i] : 0.0;
+        info[i].ms = ms;
+        if (infos) infos[B->caller[i]] = info[i];
+        if (status[i] != TFDE_OK && worst == TFDE_OK) worst = status[i];
+    }
+    if (worst == TFDE_OK) {
+        B->chain_ok = true;
+        B->chain_u = uu;
+    } else if (worst == TFDE_ENOCONV) {
+        set_error(TFDE_ENOCONV, "batched solve: a problem reached its sweep limit");
+    }
+    return worst;
+}
+
+}  // namespace tfde

@@ -72,6 +72,10 @@ void launch_cn_first(size_t N, const double* AN, const double* Ku, const double*
                      cudaStream_t s);
 // t = 2 AN + dt F; b <- t + r - b; r <- b_new + r - b_old  (chained CN step)
 void launch_cn_chain(size_t N, const double* AN, const double* F, double dt, double* b, double* r, cudaStream_t s);
+// chained CN step with extrapolated initial guess written into u (see tfde_kernels64.cu)
+void launch_cn_chain_extrap(size_t N, const double* AN, const double* F, double dt, double* b, double* r, double* u,
+                            const double* U1, const double* AU1, double* U2, double* AU2, int order,
+                            cudaStream_t s);
 // F = cP PPP + cS (SPP + PSP + PPS) from 1-D arrays [Px|Py|Pz|Sx|Sy|Sz]
 void launch_source_assemble_f64(const double* oned, const int n[3], double cP, double cS, double* F,
                                 cudaStream_t s);
@@ -112,6 +116,11 @@ struct tfde_problem {
     // chained CN advance: W_B / W_R hold b^{m-1} and its final true residual
     const double* chain_u = nullptr;
     bool chain_ok = false;
+    // polynomial-extrapolation initial guess of the chained advance: order
+    // (0: previous step), and the history (u, A u) of the two steps before
+    int guess_order = 0;
+    int hist = 0;                 // valid history entries (0..2)
+    double* H[2][2] = {};         // H[k] = {u^{m-2-k}, A u^{m-2-k}}
 };
 
 namespace tfde {

@@ -288,6 +288,39 @@ __global__ void cn_chain_kernel(long long N, const double* __restrict__ AN, cons
     }
 }
 
+// Chained CN step with a polynomial-extrapolation initial guess.  In: u =
+// u^{m-1}, AN = A_N u^{m-1}, (b, r) = the previous step's RHS and final true
+// residual (so A u^{m-1} = b - r), history H1 = (u^{m-2}, A u^{m-2}) and
+// H2 = (u^{m-3}, A u^{m-3}).  Out: b = b^m, u = x0 (extrapolation of the given
+// order: 0 u^{m-1}; 1 2u^{m-1} - u^{m-2}; 2 3u^{m-1} - 3u^{m-2} + u^{m-3}),
+// r = b^m - A x0 from the same linear combination of the stored A u (no
+// operator application), and (u^{m-1}, A u^{m-1}) into the H2 slot, which
+// the caller then relabels as H1.
+__global__ void cn_chain_extrap_kernel(long long N, const double* __restrict__ AN, const double* __restrict__ F,
+                                       double dt, double* __restrict__ b, double* __restrict__ r,
+                                       double* __restrict__ u, const double* __restrict__ U1,
+                                       const double* __restrict__ AU1, double* __restrict__ U2,
+                                       double* __restrict__ AU2, int order) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const double ui = u[i];
+        const double au = b[i] - r[i];
+        const double bn = fma(2.0, AN[i], F ? dt * F[i] : 0.0) - au;
+        double x = ui, ax = au;
+        if (order == 1) {
+            x = fma(2.0, ui, -U1[i]);
+            ax = fma(2.0, au, -AU1[i]);
+        } else if (order >= 2) {
+            x = fma(3.0, ui - U1[i], U2[i]);
+            ax = fma(3.0, au - AU1[i], AU2[i]);
+        }
+        b[i] = bn;
+        r[i] = bn - ax;
+        u[i] = x;
+        U2[i] = ui;
+        AU2[i] = au;
+    }
+}
+
 inline int grid_for(long long N) {
     long long g = (N + kThreads - 1) / kThreads;
     if (g > 152LL * 16) g = 152LL * 16;
@@ -383,6 +416,14 @@ void launch_cn_first(size_t N, const double* AN, const double* Ku, const double*
 void launch_cn_chain(size_t N, const double* AN, const double* F, double dt, double* b, double* r, cudaStream_t s) {
     stats_count_launch();
     cn_chain_kernel<<<grid_for((long long)N), kThreads, 0, s>>>((long long)N, AN, F, dt, b, r);
+}
+
+void launch_cn_chain_extrap(size_t N, const double* AN, const double* F, double dt, double* b, double* r, double* u,
+                            const double* U1, const double* AU1, double* U2, double* AU2, int order,
+                            cudaStream_t s) {
+    stats_count_launch();
+    cn_chain_extrap_kernel<<<grid_for((long long)N), kThreads, 0, s>>>((long long)N, AN, F, dt, b, r, u, U1, AU1, U2,
+                                                                       AU2, order);
 }
 
 void launch_source_assemble_f64(const double* oned, const int n[3], double cP, double cS, double* F,

@@ -53,11 +53,12 @@ struct SegSpec {
     int a_hi, a_lo, plane;  // a_lo < 0: single-term A
 };
 
-// out = alpha * sum_seg (A_seg along axis) (plane_seg hi + lo)
-int run_gemm(const tfde_problem* P, int axis, const SegSpec* segs, int nseg, int out_mode, float alpha,
-             float* out_f32, int out_plane, bool lam_scale, cudaStream_t s) {
+// Descriptor of one split-BF16 pass: out = alpha * sum_seg (A_seg along axis)
+// (plane_seg hi + lo); *bytes / *flops receive its algorithmic traffic and
+// tensor-core work.
+void gemm_params(const tfde_problem* P, int axis, const SegSpec* segs, int nseg, int out_mode, float alpha,
+                 float* out_f32, int out_plane, bool lam_scale, tc::Params& prm, double* bytes, double* flops) {
     MixedState* M = mixed(P);
-    tc::Params prm;
     std::memset(&prm, 0, sizeof(prm));
     tc::set_geometry(prm, P->n, axis);
     int na = 0, nb = 0;
@@ -98,51 +99,89 @@ int run_gemm(const tfde_problem* P, int axis, const SegSpec* segs, int nseg, int
         prm.lam_V = M->lam + 2 * P->n[2] + n1n2;
     }
     prm.err = M->err;
-    M->gemm_launches++;
     // algorithmic traffic: each operand plane pair read once, the output written
     // once (4 bytes per element either way), the operator matrices read once
     const double N = (double)P->N, nax = (double)P->n[axis];
-    double bytes = 4.0 * N, flops = 0.0;
+    double by = 4.0 * N, fl = 0.0;
     for (int g = 0; g < nseg; ++g) {
-        bytes += 4.0 * N + 2.0 * nax * nax * prm.seg[g].na;
-        flops += 2.0 * prm.seg[g].npair * nax * N;
+        by += 4.0 * N + 2.0 * nax * nax * prm.seg[g].na;
+        fl += 2.0 * prm.seg[g].npair * nax * N;
     }
+    *bytes = by;
+    *flops = fl;
+}
+
+int run_gemm(const tfde_problem* P, int axis, const SegSpec* segs, int nseg, int out_mode, float alpha,
+             float* out_f32, int out_plane, bool lam_scale, cudaStream_t s) {
+    tc::Params prm;
+    double bytes, flops;
+    gemm_params(P, axis, segs, nseg, out_mode, alpha, out_f32, out_plane, lam_scale, prm, &bytes, &flops);
+    mixed(P)->gemm_launches++;
     return tc::launch(prm, s, bytes, flops);
+}
+
+// Pass list of the fast operator and the preconditioner.  Each entry is one
+// call of run_gemm; the same list serves the single-problem solvers (launched
+// one by one) and the batched solver (descriptors gathered across problems).
+struct Pass {
+    int axis;
+    SegSpec seg[2];
+    int nseg;
+    int out_mode;
+    int out_plane;   // OUT_HILO target plane; OUT_F32 writes the caller's vector
+    bool lam;
+};
+
+// A (op A) or the RHS operator applied to plane PL_P: 5 passes; the last one
+// writes out_plane (split) when out_plane >= 0, else FP32.
+int matvec_passes(int op, int out_plane, Pass* ps) {
+    const bool rhs = (op & 1) != 0;
+    const int gh = rhs ? OM_GHATR_H : OM_GHAT_H, gl = rhs ? OM_GHATR_L : OM_GHAT_L;
+    const int yh = rhs ? OM_GYN_H : OM_GY_H, yl = rhs ? OM_GYN_L : OM_GY_L;
+    const int zh = rhs ? OM_GZN_H : OM_GZ_H, zl = rhs ? OM_GZN_L : OM_GZ_L;
+    ps[0] = {0, {{gh, gl, PL_P}}, 1, tc::OUT_HILO, PL_A, false};
+    ps[1] = {0, {{OM_MX, -1, PL_P}}, 1, tc::OUT_HILO, PL_W, false};
+    ps[2] = {1, {{OM_MY, -1, PL_A}, {yh, yl, PL_W}}, 2, tc::OUT_HILO, PL_C, false};
+    ps[3] = {1, {{OM_MY, -1, PL_W}}, 1, tc::OUT_HILO, PL_E, false};
+    ps[4] = {2, {{OM_MZ, -1, PL_C}, {zh, zl, PL_E}}, 2, out_plane >= 0 ? tc::OUT_HILO : tc::OUT_F32,
+             out_plane >= 0 ? out_plane : 0, false};
+    return 5;
+}
+
+// S_N Lambda^{-1} S_N applied to plane PL_R: 6 passes, the last one FP32.
+int precond_passes(Pass* ps) {
+    ps[0] = {0, {{OM_SX, -1, PL_R}}, 1, tc::OUT_HILO, PL_T1, false};
+    ps[1] = {1, {{OM_SY, -1, PL_T1}}, 1, tc::OUT_HILO, PL_T2, false};
+    ps[2] = {2, {{OM_SZ, -1, PL_T2}}, 1, tc::OUT_HILO, PL_T1, true};
+    ps[3] = {2, {{OM_SZ, -1, PL_T1}}, 1, tc::OUT_HILO, PL_T2, false};
+    ps[4] = {1, {{OM_SY, -1, PL_T2}}, 1, tc::OUT_HILO, PL_T1, false};
+    ps[5] = {0, {{OM_SX, -1, PL_T1}}, 1, tc::OUT_F32, 0, false};
+    return 6;
+}
+
+int run_passes(const tfde_problem* P, const Pass* ps, int np, float* out_f32, cudaStream_t s) {
+    for (int i = 0; i < np; ++i) {
+        const Pass& q = ps[i];
+        int st = run_gemm(P, q.axis, q.seg, q.nseg, q.out_mode, 1.f, q.out_mode == tc::OUT_F32 ? out_f32 : nullptr,
+                          q.out_plane, q.lam, s);
+        if (st) return st;
+    }
+    return TFDE_OK;
 }
 
 // q32 = A p (op A) or the RHS operator, p given as the split plane pair PL_P;
 // with out_plane >= 0 the result goes to that split plane pair instead.
 int fast_matvec(const tfde_problem* P, int op, float* q32, cudaStream_t s, int out_plane = -1) {
-    const bool rhs = (op & 1) != 0;
-    int st;
-    SegSpec sx[1] = {{rhs ? OM_GHATR_H : OM_GHAT_H, rhs ? OM_GHATR_L : OM_GHAT_L, PL_P}};
-    if ((st = run_gemm(P, 0, sx, 1, tc::OUT_HILO, 1.f, nullptr, PL_A, false, s))) return st;
-    SegSpec wx[1] = {{OM_MX, -1, PL_P}};
-    if ((st = run_gemm(P, 0, wx, 1, tc::OUT_HILO, 1.f, nullptr, PL_W, false, s))) return st;
-    SegSpec cy[2] = {{OM_MY, -1, PL_A}, {rhs ? OM_GYN_H : OM_GY_H, rhs ? OM_GYN_L : OM_GY_L, PL_W}};
-    if ((st = run_gemm(P, 1, cy, 2, tc::OUT_HILO, 1.f, nullptr, PL_C, false, s))) return st;
-    SegSpec ey[1] = {{OM_MY, -1, PL_W}};
-    if ((st = run_gemm(P, 1, ey, 1, tc::OUT_HILO, 1.f, nullptr, PL_E, false, s))) return st;
-    SegSpec oz[2] = {{OM_MZ, -1, PL_C}, {rhs ? OM_GZN_H : OM_GZ_H, rhs ? OM_GZN_L : OM_GZ_L, PL_E}};
-    if (out_plane >= 0) return run_gemm(P, 2, oz, 2, tc::OUT_HILO, 1.f, nullptr, out_plane, false, s);
-    return run_gemm(P, 2, oz, 2, tc::OUT_F32, 1.f, q32, 0, false, s);
+    Pass ps[5];
+    const int np = matvec_passes(op, out_plane, ps);
+    return run_passes(P, ps, np, q32, s);
 }
 
 // z32 = S_N Lambda^{-1} S_N r, r given as the split plane pair PL_R.
 int fast_precond(const tfde_problem* P, float* z32, cudaStream_t s) {
-    int st;
-    SegSpec a[1] = {{OM_SX, -1, PL_R}};
-    if ((st = run_gemm(P, 0, a, 1, tc::OUT_HILO, 1.f, nullptr, PL_T1, false, s))) return st;
-    SegSpec b[1] = {{OM_SY, -1, PL_T1}};
-    if ((st = run_gemm(P, 1, b, 1, tc::OUT_HILO, 1.f, nullptr, PL_T2, false, s))) return st;
-    SegSpec c[1] = {{OM_SZ, -1, PL_T2}};
-    if ((st = run_gemm(P, 2, c, 1, tc::OUT_HILO, 1.f, nullptr, PL_T1, true, s))) return st;
-    SegSpec d[1] = {{OM_SZ, -1, PL_T1}};
-    if ((st = run_gemm(P, 2, d, 1, tc::OUT_HILO, 1.f, nullptr, PL_T2, false, s))) return st;
-    SegSpec e[1] = {{OM_SY, -1, PL_T2}};
-    if ((st = run_gemm(P, 1, e, 1, tc::OUT_HILO, 1.f, nullptr, PL_T1, false, s))) return st;
-    SegSpec f[1] = {{OM_SX, -1, PL_T1}};
-    return run_gemm(P, 0, f, 1, tc::OUT_F32, 1.f, z32, 0, false, s);
+    Pass ps[6];
+    const int np = precond_passes(ps);
+    return run_passes(P, ps, np, z32, s);
 }
 
 int check_err(const tfde_problem* P, cudaStream_t s) {
@@ -313,6 +352,21 @@ int inner_gmres(const tfde_problem* P, int restart, double ptheta, int maxit, in
 }
 
 }  // namespace
+
+int fast_pass_descriptors(const tfde_problem* P, int kind, float* out_f32, tc::Params* prm, int* axes, double* bytes,
+                          double* flops) {
+    Pass ps[6];
+    const int np = kind == 0 ? matvec_passes(TFDE_OP_A, PL_R, ps) : precond_passes(ps);
+    for (int i = 0; i < np; ++i) {
+        const Pass& q = ps[i];
+        gemm_params(P, q.axis, q.seg, q.nseg, q.out_mode, 1.f, q.out_mode == tc::OUT_F32 ? out_f32 : nullptr,
+                    q.out_plane, q.lam, prm[i], &bytes[i], &flops[i]);
+        axes[i] = q.axis;
+    }
+    return np;
+}
+
+int mixed_prepare_gmres(const tfde_problem* P, int restart) { return ensure_v32(P, restart); }
 
 int mixed_init(tfde_problem* P, cudaStream_t s) {
     for (int a = 0; a < 3; ++a)

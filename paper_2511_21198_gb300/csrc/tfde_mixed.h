@@ -91,6 +91,15 @@ struct MixedState {
 
 inline MixedState* mixed(const tfde_problem* P) { return static_cast<MixedState*>(P->mixed); }
 
+// Descriptors of the split-BF16 passes of one problem, for grouped launches:
+// kind 0 = operator A on plane PL_P with the result split into PL_R (5 passes),
+// kind 1 = preconditioner on PL_R with FP32 output out_f32 (6 passes).
+// Returns the pass count; axes[i], bytes[i], flops[i] per pass.
+int fast_pass_descriptors(const tfde_problem* P, int kind, float* out_f32, tc::Params* prm, int* axes, double* bytes,
+                          double* flops);
+// Allocate the FP32 GMRES basis (restart + 1 vectors) and Hessenberg scratch.
+int mixed_prepare_gmres(const tfde_problem* P, int restart);
+
 int oz_init(tfde_problem* P, const std::vector<double> etaB[3], cudaStream_t s);
 void oz_free(MixedState* M);
 int accurate_apply(const tfde_problem* P, int op, const double* x, double* y, cudaStream_t s);

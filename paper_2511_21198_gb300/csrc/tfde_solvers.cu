@@ -2,6 +2,7 @@
 // Crank-Nicolson step driver (Sec. 2 Eq. (CN), Eq. (linear_sys); Sec. 3).
 #include <chrono>
 #include <cmath>
+#include <utility>
 #include <vector>
 
 #include "tfde_internal.h"
@@ -309,8 +310,10 @@ static void mass_apply(const tfde_problem* P, const double* u, double* out, cuda
 // One CN step (Eq. (CN), Eq. (linear_sys)) for either precision.  `chained`:
 // W_B / W_R hold b^{m-1} and the final true residual of u_prev, so that
 // A u_prev = b^{m-1} - r^{m-1} replaces the operator application.
-int cn_drive(tfde_problem* P, const double* u_prev, const double* F, const double* x0, double* u_next, double tol,
-             tfde_info* info, cudaStream_t s, bool chained) {
+// cn_prepare forms b^m in W_B, the initial guess in u_next and (when *r_given)
+// its residual in W_R; cn_drive then runs the solver.
+int cn_prepare(tfde_problem* P, const double* u_prev, const double* F, const double* x0, double* u_next,
+               cudaStream_t s, bool chained, bool* r_given) {
     double* b = P->w[tfde_problem::W_B];
     double* r = P->w[tfde_problem::W_R];
     double* an = P->w[tfde_problem::W_T];
@@ -318,18 +321,45 @@ int cn_drive(tfde_problem* P, const double* u_prev, const double* F, const doubl
     const bool guess_is_prev = (x0 == nullptr || x0 == u_prev);
     int st;
     mass_apply(P, u_prev, an, s);
-    if (chained) {
+    bool guess_in_place = false;  // x0 already written into u_next, r = b - A x0
+    if (chained && P->guess_order > 0 && u_next == u_prev) {
+        if (!P->H[0][0]) {
+            for (auto& hk : P->H)
+                for (auto& v : hk)
+                    if (cudaMalloc((void**)&v, P->N * sizeof(double)) != cudaSuccess)
+                        return set_error(TFDE_ENOMEM, "cudaMalloc of the extrapolation history failed");
+            P->hist = 0;
+        }
+        const int order = P->guess_order < P->hist ? P->guess_order : P->hist;
+        launch_cn_chain_extrap(P->N, an, F, P->p.dt, b, r, u_next, P->H[0][0], P->H[0][1], P->H[1][0], P->H[1][1],
+                               order, s);
+        std::swap(P->H[0][0], P->H[1][0]);
+        std::swap(P->H[0][1], P->H[1][1]);
+        P->hist = P->hist < 2 ? P->hist + 1 : 2;
+        guess_in_place = true;
+    } else if (chained) {
         launch_cn_chain(P->N, an, F, P->p.dt, b, r, s);
     } else {
+        P->hist = 0;
         double* ku = P->w[tfde_problem::W_Q];
         st = mixed_prec ? accurate_apply(P, TFDE_OP_STIFF, u_prev, ku, s) : apply_A64(P, TFDE_OP_STIFF, u_prev, ku, s);
         if (st) return st;
         launch_cn_first(P->N, an, ku, F, P->p.dt, b, r, s);
     }
     const double* start = guess_is_prev ? u_prev : x0;
-    if (start != u_next)
+    if (!guess_in_place && start != u_next)
         TFDE_CUDA_TRY(cudaMemcpyAsync(u_next, start, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    const bool rg = guess_is_prev;  // r = b - A u_prev is the residual of the initial guess
+    *r_given = guess_is_prev;  // r = b - A x0 is the residual of the initial guess
+    return TFDE_OK;
+}
+
+int cn_drive(tfde_problem* P, const double* u_prev, const double* F, const double* x0, double* u_next, double tol,
+             tfde_info* info, cudaStream_t s, bool chained) {
+    bool rg = false;
+    int st = cn_prepare(P, u_prev, F, x0, u_next, s, chained, &rg);
+    if (st) return st;
+    double* b = P->w[tfde_problem::W_B];
+    const bool mixed_prec = P->prec == TFDE_MIXED;
     if (P->symmetric)
         return mixed_prec ? mixed_pcg(P, b, u_next, tol, 10000, info, s, rg) : pcg64(P, b, u_next, tol, 10000, info, s, rg);
     return mixed_prec ? mixed_pgmres(P, b, u_next, 20, tol, 10000, info, s, rg)

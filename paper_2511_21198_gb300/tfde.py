@@ -54,8 +54,9 @@ class TfdeError(RuntimeError):
 _lib = None
 
 EXPORTS = ["tfde_assemble", "tfde_destroy", "tfde_matvec", "tfde_precond", "tfde_pcg", "tfde_pgmres",
-           "tfde_cn_step", "tfde_cn_advance", "tfde_source_example2", "tfde_coefficients", "tfde_host_coefficients",
-           "tfde_stats_reset", "tfde_stats_get", "tfde_mass_apply_noalloc", "tfde_last_error", "tfde_version"]
+           "tfde_cn_step", "tfde_cn_advance", "tfde_set_guess_order", "tfde_source_example2", "tfde_coefficients", "tfde_host_coefficients",
+           "tfde_stats_reset", "tfde_stats_get", "tfde_mass_apply_noalloc", "tfde_batch_create", "tfde_batch_destroy",
+           "tfde_batch_count", "tfde_batch_cn_advance", "tfde_last_error", "tfde_version"]
 
 
 def load(path: str | None = None):
@@ -77,6 +78,7 @@ def load(path: str | None = None):
         "tfde_pgmres": ([vp, vp, vp, c_int, c_double, c_int, POINTER(tfde_info), vp], c_int),
         "tfde_cn_step": ([vp, vp, vp, vp, vp, c_double, POINTER(tfde_info), vp], c_int),
         "tfde_cn_advance": ([vp, vp, vp, c_int, c_double, POINTER(tfde_info), vp], c_int),
+        "tfde_set_guess_order": ([vp, c_int], c_int),
         "tfde_source_example2": ([vp, c_double, c_double, vp, vp], c_int),
         "tfde_coefficients": ([vp, c_int, POINTER(c_double), POINTER(c_double), POINTER(c_double)], c_int),
         "tfde_host_coefficients": ([POINTER(tfde_params), c_int, POINTER(c_double), POINTER(c_double),
@@ -84,6 +86,11 @@ def load(path: str | None = None):
         "tfde_stats_reset": ([c_int], c_int),
         "tfde_stats_get": ([POINTER(tfde_stats)], c_int),
         "tfde_mass_apply_noalloc": ([POINTER(c_int), vp, vp, vp], c_int),
+        "tfde_batch_create": ([POINTER(tfde_params), c_int, c_int, vp, POINTER(c_void_p)], c_int),
+        "tfde_batch_destroy": ([vp], c_int),
+        "tfde_batch_count": ([vp], c_int),
+        "tfde_batch_cn_advance": ([vp, POINTER(c_void_p), POINTER(c_void_p), c_int, c_double, POINTER(tfde_info),
+                                   vp], c_int),
         "tfde_last_error": ([], c_char_p),
         "tfde_version": ([], c_char_p),
     }
@@ -177,6 +184,10 @@ def tfde_cn_step(prob: int, u_prev, F_half, x0, u_next, tol: float, stream=None,
     return info
 
 
+def tfde_set_guess_order(prob: int, order: int) -> None:
+    _check(load().tfde_set_guess_order(prob, order), "tfde_set_guess_order")
+
+
 def tfde_cn_advance(prob: int, u, F_half, restart: bool, tol: float, stream=None, check: bool = True) -> tfde_info:
     info = tfde_info()
     st = load().tfde_cn_advance(prob, _ptr(u), _ptr(F_half), 1 if restart else 0, tol, byref(info), _stream(stream))
@@ -233,3 +244,31 @@ def tfde_last_error() -> str:
 
 def tfde_version() -> str:
     return load().tfde_version().decode()
+
+
+def tfde_batch_create(params_list, restart: int = 20, stream=None) -> int:
+    """Batch of independent mixed-precision problems (see tfde_batch_create in tfde.h)."""
+    arr = (tfde_params * len(params_list))(*params_list)
+    h = c_void_p()
+    _check(load().tfde_batch_create(arr, len(params_list), restart, _stream(stream), byref(h)), "tfde_batch_create")
+    return h.value
+
+
+def tfde_batch_destroy(batch: int) -> None:
+    _check(load().tfde_batch_destroy(batch), "tfde_batch_destroy")
+
+
+def tfde_batch_cn_advance(batch: int, u_list, F_list, restart: bool, tol: float, stream=None,
+                          check: bool = True) -> list:
+    """One in-place CN step of every problem; returns the per-problem tfde_info list."""
+    C = len(u_list)
+    us = (c_void_p * C)(*[_ptr(u) for u in u_list])
+    Fs = None if F_list is None else (c_void_p * C)(*[_ptr(f) for f in F_list])
+    infos = (tfde_info * C)()
+    st = load().tfde_batch_cn_advance(batch, us, Fs, 1 if restart else 0, tol, infos, _stream(stream))
+    if check:
+        _check(st, "tfde_batch_cn_advance")
+    out = list(infos)
+    for i in out:
+        i.status = st
+    return out

@@ -1,0 +1,135 @@
+"""GPU parity of the batched solve (tfde_batch_*): problems of uneven size and
+coefficients advanced together in lock step must give, problem by problem,
+the same CN trajectory as the single-problem solvers (and the oracle)."""
+import numpy as np
+import pytest
+
+from oracle import tfde_oracle as o
+import tfde_inputs as inp
+from gpu_helpers import relerr, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_2511_21198_gb300 import build
+    build.build()
+    from paper_2511_21198_gb300 import tfde
+    tfde.load()
+    return tfde
+
+
+def small_batch(count, seed, sizes=(8, 16, 24, 32, 40)):
+    """Uneven problems in the recipe of the batched workload, on small grids:
+    every axis size drawn separately, delta ~ U(0.1, 0.9), k+- ~ U(0.5, 2)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = tuple(int(v) for v in rng.choice(sizes, 3))
+        out.append(dict(n=n, delta=tuple(rng.uniform(0.1, 0.9, 3)), kp=tuple(rng.uniform(0.5, 2.0, 3)),
+                        km=tuple(rng.uniform(0.5, 2.0, 3))))
+    return out
+
+
+def test_batch_first_step_matches_oracle(T):
+    """One batched step from smoothed-noise data equals, for every problem,
+    the oracle's left-preconditioned GMRES solution of its CN system."""
+    probs = small_batch(4, 11, sizes=(8, 16, 24))
+    dt = 0.1
+    params = [T.make_params(p["n"], p["delta"], p["kp"], p["km"], dt) for p in probs]
+    B = T.tfde_batch_create(params, 20)
+    try:
+        u0 = [inp.smoothed_uniform(tuple(reversed(p["n"])), 20 + i) for i, p in enumerate(probs)]
+        us = [to_dev(u) for u in u0]
+        infos = T.tfde_batch_cn_advance(B, us, None, True, 1e-12)
+        for i, p in enumerate(probs):
+            op = o.Problem(n=p["n"], delta=p["delta"], kp=p["kp"], km=p["km"], dt=dt)
+            b = o.rhs(op, u0[i], None)
+            tau = o.build_tau(op)
+            xo, _ = o.gmres_left(lambda v: o.apply_A(op, v), lambda r: o.apply_Pinv(tau, r), b, u0[i], 1e-14, 4000,
+                                 restart=20, criterion="true")
+            assert infos[i].relres <= 1e-12 and infos[i].fallback == 0
+            assert relerr(to_host(us[i]), xo) < 1e-10
+    finally:
+        T.tfde_batch_destroy(B)
+
+
+def test_batch_trajectory_matches_single_problem_fp64(T):
+    """Six uneven problems (one symmetric), 5 chained steps with sources on
+    two of them: the batched trajectories equal the all-FP64 single-problem
+    advance at tight residuals."""
+    probs = small_batch(6, 12)
+    probs[2]["km"] = probs[2]["kp"]          # a symmetric one rides along
+    dt = 0.05
+    params = [T.make_params(p["n"], p["delta"], p["kp"], p["km"], dt) for p in probs]
+    B = T.tfde_batch_create(params, 20)
+    singles = [T.tfde_assemble(pp, T.TFDE_FP64) for pp in params]
+    try:
+        u0 = [inp.smoothed_uniform(tuple(reversed(p["n"])), 30 + i) for i, p in enumerate(probs)]
+        ub = [to_dev(u) for u in u0]
+        us = [to_dev(u) for u in u0]
+        Fs = [None] * len(probs)
+        Fs[1] = to_dev(inp.uniform_vector(tuple(reversed(probs[1]["n"])), 7))
+        Fs[4] = to_dev(inp.uniform_vector(tuple(reversed(probs[4]["n"])), 8))
+        for m in range(5):
+            infos = T.tfde_batch_cn_advance(B, ub, Fs, m == 0, 1e-12)
+            for i in range(len(probs)):
+                T.tfde_cn_advance(singles[i], us[i], Fs[i], m == 0, 1e-13)
+                assert infos[i].relres <= 1e-12
+        for i in range(len(probs)):
+            assert relerr(to_host(ub[i]), to_host(us[i])) < 1e-10
+    finally:
+        T.tfde_batch_destroy(B)
+        for h in singles:
+            T.tfde_destroy(h)
+
+
+def test_batch_large_uneven_sizes(T):
+    """Sizes of the batched workload (32..128 per axis, tiles with ragged
+    tails in both the row and the line direction) at the metric tolerance."""
+    probs = inp.batched_instances(count=5, seed=4)
+    dt = 0.1
+    params = [T.make_params(p["n"], p["delta"], p["kp"], p["km"], dt) for p in probs]
+    B = T.tfde_batch_create(params, 20)
+    singles = [T.tfde_assemble(pp, T.TFDE_FP64) for pp in params]
+    try:
+        u0 = [inp.smoothed_uniform(tuple(reversed(p["n"])), 40 + i) for i, p in enumerate(probs)]
+        ub = [to_dev(u) for u in u0]
+        us = [to_dev(u) for u in u0]
+        for m in range(2):
+            infos = T.tfde_batch_cn_advance(B, ub, None, m == 0, 1e-10)
+            for i in range(len(probs)):
+                T.tfde_cn_advance(singles[i], us[i], None, m == 0, 1e-13)
+                assert infos[i].relres <= 1e-10 and infos[i].fallback == 0
+        for i in range(len(probs)):
+            # both solutions within their residual bounds of the exact one
+            assert relerr(to_host(ub[i]), to_host(us[i])) < 1e-8
+    finally:
+        T.tfde_batch_destroy(B)
+        for h in singles:
+            T.tfde_destroy(h)
+
+
+def test_batch_argument_errors(T):
+    good = T.make_params((16, 16, 16), (0.5,) * 3, (1.0,) * 3, (0.5,) * 3, 0.1)
+    with pytest.raises(T.TfdeError) as e:
+        T.tfde_batch_create([], 20)
+    assert e.value.status == T.TFDE_EINVAL
+    with pytest.raises(T.TfdeError) as e:
+        T.tfde_batch_create([good, T.make_params((12, 16, 16), (0.5,) * 3, (1.0,) * 3, (1.0,) * 3, 0.1)], 20)
+    assert e.value.status == T.TFDE_EUNSUPPORTED
+    B = T.tfde_batch_create([good, good], 20)
+    try:
+        assert T.load().tfde_batch_count(B) == 2
+        u = to_dev(np.zeros((16, 16, 16)))
+        with pytest.raises(T.TfdeError) as e:
+            T.tfde_batch_cn_advance(B, [u, u], None, True, 1e-8)
+        assert e.value.status == T.TFDE_EINVAL
+        # zero data: every problem converges at once with a zero solution
+        v = to_dev(np.zeros((16, 16, 16)))
+        infos = T.tfde_batch_cn_advance(B, [u, v], None, True, 1e-8)
+        assert all(i.iters == 0 for i in infos)
+        assert float(np.abs(to_host(u)).max()) == 0.0
+    finally:
+        T.tfde_batch_destroy(B)

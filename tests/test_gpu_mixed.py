@@ -253,3 +253,45 @@ def test_mixed_rejects_sizes_beyond_exact_accumulation(T):
     with pytest.raises(T.TfdeError) as e:
         T.tfde_assemble(T.make_params((456, 8, 8), (0.5,) * 3, (1.0,) * 3, (1.0,) * 3, 0.1), T.TFDE_MIXED)
     assert e.value.status == T.TFDE_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_extrapolated_guess_same_solution_fewer_iterations(T, prec):
+    """Chained advance with the order-2 extrapolated initial guess reaches the
+    same trajectory (tight residuals) as the previous-step guess, with fewer
+    inner iterations once the history is built."""
+    n, M = (32, 24, 40), 10
+    d, k = (0.7, 0.7, 0.7), (1.0,) * 3
+    p = T.TFDE_MIXED if prec == "mixed" else T.TFDE_FP64
+    h0 = T.tfde_assemble(T.make_params(n, d, k, k, 1.0 / M), p)
+    h2 = T.tfde_assemble(T.make_params(n, d, k, k, 1.0 / M), p)
+    T.tfde_set_guess_order(h2, 2)
+    try:
+        op = o.Problem(n=n, delta=d, kp=k, km=k, dt=1.0 / M)
+        u0 = o.exact_u(op, 0.0, "exp")
+        F = to_dev(np.zeros_like(u0))
+        ua, ub = to_dev(u0), to_dev(u0)
+        it0 = it2 = 0
+        for m in range(1, M + 1):
+            th = (m - 0.5) * op.dt
+            T.tfde_source_example2(h0, -math.exp(-th), -math.exp(-th), F)
+            ia = T.tfde_cn_advance(h0, ua, F, m == 1, 1e-12)
+            ib = T.tfde_cn_advance(h2, ub, F, m == 1, 1e-12)
+            assert ia.relres <= 1e-12 and ib.relres <= 1e-12
+            if m > 3:
+                it0 += ia.iters
+                it2 += ib.iters
+        assert relerr(to_host(ua), to_host(ub)) < 1e-10
+        assert it2 < it0
+    finally:
+        T.tfde_destroy(h0)
+        T.tfde_destroy(h2)
+
+
+def test_guess_order_rejects_bad_values(T):
+    h = T.tfde_assemble(T.make_params((16, 16, 16), (0.5,) * 3, (1.0,) * 3, (1.0,) * 3, 0.1), T.TFDE_MIXED)
+    try:
+        with pytest.raises(T.TfdeError):
+            T.tfde_set_guess_order(h, 3)
+    finally:
+        T.tfde_destroy(h)
