@@ -1,0 +1,131 @@
+"""Pins of the warm-start network's CPU oracle (no GPU): a library
+correlation, closed-form shifts, the adjoint identity and central finite
+differences, chosen so that a transposed tap, a flipped sign, a dropped term
+or a wrong channel index each fail one of them."""
+import numpy as np
+import pytest
+from scipy import ndimage
+
+from oracle import cnn_oracle as C
+
+
+def rand_params(rng, chans):
+    out = []
+    for cin, cout in zip(chans[:-1], chans[1:]):
+        W = rng.standard_normal((cout, cin, 3, 3, 3)) / np.sqrt(27 * cin)
+        b = 0.1 * rng.standard_normal(cout)
+        out.append((W, b))
+    return out
+
+
+def test_single_channel_equals_library_correlation():
+    """One input and one output channel: y = correlate(x, w) with zero
+    padding, as scipy.ndimage.correlate computes it."""
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((1, 5, 6, 7))
+    W = rng.standard_normal((1, 1, 3, 3, 3))
+    y = C.conv3d(x, W)
+    ref = ndimage.correlate(x[0], W[0, 0], mode="constant", cval=0.0)
+    assert np.allclose(y[0], ref, rtol=0, atol=1e-12)
+
+
+def test_multichannel_is_sum_of_library_correlations():
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((3, 4, 5, 6))
+    W = rng.standard_normal((2, 3, 3, 3, 3))
+    b = rng.standard_normal(2)
+    y = C.conv3d(x, W, b)
+    for o in range(2):
+        ref = b[o] + sum(ndimage.correlate(x[i], W[o, i], mode="constant", cval=0.0) for i in range(3))
+        assert np.allclose(y[o], ref, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("t", [(0, 0, 1), (0, 1, 0), (1, 0, 0), (-1, 1, -1)])
+def test_delta_kernel_is_a_shift(t):
+    """W = e_t on channel (0 <- 1): y_0[p] = x_1[p + t] (0 outside), y_1 = 0."""
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((2, 4, 4, 5))
+    W = np.zeros((2, 2, 3, 3, 3))
+    W[0, 1, t[0] + 1, t[1] + 1, t[2] + 1] = 1.0
+    y = C.conv3d(x, W)
+    n3, n2, n1 = x.shape[1:]
+    for z in range(n3):
+        for yy in range(n2):
+            for xx in range(n1):
+                q = (z + t[0], yy + t[1], xx + t[2])
+                inside = 0 <= q[0] < n3 and 0 <= q[1] < n2 and 0 <= q[2] < n1
+                assert y[0, z, yy, xx] == (x[1][q] if inside else 0.0)
+    assert not y[1].any()
+
+
+def test_adjoint_identity_pins_input_gradient():
+    """<conv(x), y> = <x, conv^T(y)>: the input gradient of the backward pass
+    is the adjoint of the forward convolution."""
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((3, 4, 5, 6))
+    W = rng.standard_normal((2, 3, 3, 3, 3))
+    dy = rng.standard_normal((2, 4, 5, 6))
+    dx, _, db = C.conv3d_backward(x, W, dy)
+    assert np.isclose(np.sum(C.conv3d(x, W) * dy), np.sum(x * dx), rtol=1e-12)
+    assert np.allclose(db, dy.reshape(2, -1).sum(axis=1))
+
+
+def test_weight_gradient_by_central_differences():
+    """sum(dy * conv(x, W)) is linear in W: central differences are exact up to
+    rounding, entry by entry."""
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((2, 3, 4, 3))
+    W = rng.standard_normal((2, 2, 3, 3, 3))
+    dy = rng.standard_normal((2, 3, 4, 3))
+    _, dW, _ = C.conv3d_backward(x, W, dy)
+    h = 1e-3
+    for idx in [(0, 0, 0, 0, 0), (1, 0, 2, 1, 0), (0, 1, 1, 1, 1), (1, 1, 0, 2, 2), (0, 1, 2, 0, 1)]:
+        Wp, Wm = W.copy(), W.copy()
+        Wp[idx] += h
+        Wm[idx] -= h
+        fd = (np.sum(dy * C.conv3d(x, Wp)) - np.sum(dy * C.conv3d(x, Wm))) / (2 * h)
+        assert np.isclose(dW[idx], fd, rtol=1e-9, atol=1e-9)
+
+
+def test_network_gradient_by_central_differences():
+    """Four layers with ReLU, MSE loss: backpropagated gradients match central
+    differences of the loss on a tiny grid."""
+    rng = np.random.default_rng(6)
+    params = rand_params(rng, [3, 4, 4, 4, 1])
+    x = rng.standard_normal((3, 3, 4, 4))
+    target = rng.standard_normal((1, 3, 4, 4))
+    L, grads = C.loss_and_grads(params, x, target)
+    h = 1e-6
+    for k in range(4):
+        W, b = params[k]
+        for idx in [(0, 0, 1, 1, 1), (0, W.shape[1] - 1, 2, 0, 1)]:
+            W[idx] += h
+            Lp, _ = C.loss_and_grads(params, x, target)
+            W[idx] -= 2 * h
+            Lm, _ = C.loss_and_grads(params, x, target)
+            W[idx] += h
+            assert np.isclose(grads[k][0][idx], (Lp - Lm) / (2 * h), rtol=1e-5, atol=1e-9)
+        b[0] += h
+        Lp, _ = C.loss_and_grads(params, x, target)
+        b[0] -= 2 * h
+        Lm, _ = C.loss_and_grads(params, x, target)
+        b[0] += h
+        assert np.isclose(grads[k][1][0], (Lp - Lm) / (2 * h), rtol=1e-5, atol=1e-9)
+
+
+def test_adam_first_step_moves_by_learning_rate():
+    """Adam's first bias-corrected step is lr * g / (|g| + eps): a move of
+    about lr against the sign of every gradient entry."""
+    p = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -4.0, 1e-3])
+    m, v = np.zeros(3), np.zeros(3)
+    C.adam_step(p, g, m, v, 1, 0.01)
+    assert np.allclose(p, [1.0 - 0.01, -2.0 + 0.01, 0.5 - 0.01 * 1e-3 / (1e-3 + 1e-8)], rtol=1e-12)
+
+
+def test_input_channels_layout():
+    u = np.arange(24, dtype=float).reshape(2, 3, 4) - 5.0
+    ch, s = C.input_channels(u, 2 * u, (0.1, 0.2, 0.3), (1, 2, 3), (4, 5, 6))
+    assert s == 18.0 and ch.shape == (11, 2, 3, 4)
+    assert np.allclose(ch[0], u / 18.0) and np.allclose(ch[1], 2 * u / 18.0)
+    assert np.allclose(ch[2:11, 0, 0, 0], [0.1, 0.2, 0.3, 1, 2, 3, 4, 5, 6])
