@@ -177,6 +177,20 @@ int tfde_cn_advance(const tfde_problem* prob, double* u, const double* F_half, i
                     tfde_info* info, void* stream);
 
 /*
+ * tfde_cn_advance_guess -- tfde_cn_advance with a candidate initial guess x0
+ * (e.g. from the warm-start network): the solve starts from x0 if its FP64
+ * residual ||b^m - A x0|| is smaller than that of u^{m-1}, else from u^{m-1}
+ * (the previous-step guess stays the fallback; the stopping rule is the same).
+ *   The residual of x0 costs one accurate operator application on
+ *   x0 - u^{m-1} (A u^{m-1} is known from the chain).  *used_guess (may be
+ *   NULL) is set to 1 when x0 was used.  x0: device, not aliasing u.  The
+ *   polynomial extrapolation of tfde_set_guess_order is not applied on such a
+ *   step, and its history restarts.  Errors as tfde_cn_advance.
+ */
+int tfde_cn_advance_guess(const tfde_problem* prob, double* u, const double* F_half, const double* x0, int restart,
+                          double tol, tfde_info* info, int* used_guess, void* stream);
+
+/*
  * tfde_set_guess_order -- initial guess of the chained tfde_cn_advance steps:
  *   order 0 (default): x0 = u^{m-1}, as the paper's solves from the previous
  *   time level; order 1: x0 = 2u^{m-1} - u^{m-2}; order 2:
@@ -238,6 +252,56 @@ int tfde_batch_count(const tfde_batch* batch);
 int tfde_batch_cn_advance(tfde_batch* batch, double* const* u, const double* const* F_half, int restart, double tol,
                           tfde_info* infos, void* stream);
 
+/* ------------------------------------------------------ warm-start network */
+/*
+ * The learned initial guess of the CN solves (no counterpart in the paper,
+ * whose solves start from the previous time level).  Four 3x3x3 convolutions
+ * with zero padding, ReLU between them, 16 channels, BF16 weights and
+ * activations, FP32 accumulation on the tensor cores.  Per grid point the 11
+ * inputs are (u / s, dt F / s, c_1..c_9), s = max |u|, c the nine constants
+ * the caller passes (the package's driver uses delta_1..3 and the logarithms of
+ * the stiffness scales eta_a k+_a, eta_a k-_a, which fix the discrete operator at any
+ * resolution), and the output is the predicted (u^{m+1} - u^m) / s.
+ *
+ * Parameters (host FP32, TFDE_CNN_PARAMS floats): for layers l = 0..3 in
+ * order, W_l[co][ci][tap] (16 x 16 x 27; tap = (dz+1) 9 + (dy+1) 3 + (dx+1),
+ * the weight of input point p + (dz, dy, dx) for output point p) followed by
+ * b_l[co] (16).  Layer 0 reads input channels 0..10, layer 3 writes output
+ * channel 0; weights of the unused channels must be zero.
+ */
+#define TFDE_CNN_PARAMS (4 * (16 * 16 * 27 + 16))
+typedef struct tfde_cnn tfde_cnn;
+
+/* Network with workspace for grids of n[0] x n[1] x n[2] points (any n_a >= 1);
+ * parameters start at zero.  Errors: TFDE_EINVAL, TFDE_ENOMEM, TFDE_ECUDA. */
+int tfde_cnn_create(const int n[3], tfde_cnn** out);
+int tfde_cnn_destroy(tfde_cnn* net);
+/* Upload / download parameters (layout above); set also clears the gradient
+ * accumulator and the Adam moments.  Synchronous. */
+int tfde_cnn_set_params(tfde_cnn* net, const float* params);
+int tfde_cnn_get_params(const tfde_cnn* net, float* params);
+/* Download the accumulated gradients (sum over tfde_cnn_accumulate calls since
+ * the last Adam step), same layout as the parameters.  Synchronous. */
+int tfde_cnn_get_grads(const tfde_cnn* net, float* grads);
+/*
+ * tfde_cnn_predict -- x0 = u + s * net(u / s, dtF / s, coef), the initial guess
+ * of the step from u.  u, dtF (NULL for f = 0), x0: device FP64 grids of the
+ * network's size (x fastest); coef: host, the 9 constants (delta_1..3,
+ * k+_1..3, k-_1..3).  Synchronises `stream`.
+ */
+int tfde_cnn_predict(tfde_cnn* net, const double* u, const double* dtF, const double* coef, double* x0, void* stream);
+/*
+ * tfde_cnn_accumulate -- one training sample (u^m, dt F, coef) -> u^{m+1}:
+ * forward pass, loss = mean over points of (out - (u^{m+1} - u^m) / s)^2 into
+ * *loss (may be NULL), and the gradients of the loss added to the
+ * accumulator.  Synchronises `stream`.
+ */
+int tfde_cnn_accumulate(tfde_cnn* net, const double* u, const double* dtF, const double* coef, const double* u_next,
+                        double* loss, void* stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) with the accumulated gradients
+ * averaged over the samples, then clears the accumulator.  lr > 0. */
+int tfde_cnn_adam_step(tfde_cnn* net, float lr, void* stream);
+
 /*
  * tfde_source_example2 -- cell averages F_{ijk} (Sec. 2, definition of F^{m-1/2})
  * of the manufactured source of Sec. 4, Example 2, on Omega = (0,1)^3:
@@ -265,20 +329,28 @@ int tfde_coefficients(const tfde_problem* prob, int axis, double* q, double* lam
 int tfde_host_coefficients(const tfde_params* params, int axis, double* q, double* lam_tau, double* lam_mass,
                            double* eta);
 
-/* Counters of the library's own GPU work (process-wide). */
+/* Counters of the library's own GPU work (process-wide), per kind of
+ * tensor-core kernel: TFDE_KIND_SPLIT = the split-BF16 per-axis contraction
+ * (fast operator and preconditioner), TFDE_KIND_EXACT = the exact-integer
+ * slice contraction (FP64-accurate operator), TFDE_KIND_CONV = the
+ * warm-start network's convolution. */
+enum { TFDE_KIND_SPLIT = 0, TFDE_KIND_EXACT = 1, TFDE_KIND_CONV = 2, TFDE_NKINDS = 3 };
 typedef struct {
-    unsigned long long kernel_launches;  /* every kernel this library launched            */
-    unsigned long long tc_launches;      /* tcgen05 per-axis contraction launches          */
-    double tc_ms;        /* summed CUDA-event duration of those launches (timing enabled) */
-    double tc_bytes;     /* their algorithmic bytes: operand planes read + output written */
-    double tc_flops;     /* their tensor-core flops (2 x rows x k x lines per BF16 product) */
-    unsigned long long tc_timed;         /* launches covered by tc_ms                      */
+    unsigned long long launches;  /* launches of this kind                               */
+    unsigned long long timed;     /* launches covered by ms                               */
+    double ms;                    /* summed CUDA-event duration (timing enabled)          */
+    double bytes;                 /* algorithmic bytes: operands read once, output written */
+    double flops;                 /* tensor-core flops (2 x m x k x n per BF16 product)    */
+} tfde_kernel_stats;
+typedef struct {
+    unsigned long long kernel_launches;  /* every kernel this library launched */
+    tfde_kernel_stats kind[TFDE_NKINDS];
 } tfde_stats;
 
 /*
  * tfde_stats_reset -- zero the counters; `time_tc` != 0 additionally brackets
- * every tcgen05 contraction launch with a CUDA event pair on its stream so
- * that tc_ms is the sum of their device durations.  Not thread-safe.
+ * every tensor-core kernel launch with a CUDA event pair on its stream so that
+ * kind[k].ms is the sum of their device durations.  Not thread-safe.
  */
 int tfde_stats_reset(int time_tc);
 

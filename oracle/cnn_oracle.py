@@ -4,8 +4,10 @@ product path).
 
 The network is not part of the paper; it is the learned initial guess of the
 CN solves.  It maps, per grid point, the input channels
-    (u^m, dt F^{m+1/2}, delta_1, delta_2, delta_3, k+_1, k+_2, k+_3, k-_1, k-_2, k-_3)
-(u and dt F scaled by 1/s, s = max |u^m|; the coefficients as constant planes)
+    (u^m, dt F^{m+1/2}, c_1, ..., c_9)
+(u and dt F scaled by 1/s, s = max |u^m|; nine problem coefficients as
+constant planes -- the caller's choice; the package passes delta_1..3 and
+the logarithms of the per-axis stiffness scales eta_a k+_a, eta_a k-_a)
 to Delta / s, Delta = u^{m+1} - u^m, through four 3x3x3 convolutions with
 zero padding ("same" size) and ReLU between them.
 
@@ -116,13 +118,14 @@ def loss_and_grads(params, x: np.ndarray, target: np.ndarray):
     return L, grads
 
 
-def input_channels(u: np.ndarray, dtF: np.ndarray | None, delta, kp, km) -> tuple[np.ndarray, float]:
-    """The 11 input channels of one sample and its scale s = max |u| (1 for u = 0)."""
+def input_channels(u: np.ndarray, dtF: np.ndarray | None, c1, c2, c3) -> tuple[np.ndarray, float]:
+    """The 11 input channels of one sample (constants c1 + c2 + c3, three each)
+    and its scale s = max |u| (1 for u = 0)."""
     s = float(np.abs(u).max())
     if s == 0.0:
         s = 1.0
     ch = [u / s, (dtF / s) if dtF is not None else np.zeros_like(u)]
-    for v in list(delta) + list(kp) + list(km):
+    for v in list(c1) + list(c2) + list(c3):
         ch.append(np.full_like(u, float(v)))
     return np.stack(ch), s
 

@@ -9,6 +9,16 @@ namespace tfde {
 const char* last_error_text();
 int assemble_problem(const tfde_params*, int, cudaStream_t, tfde_problem**);
 int batch_create(const tfde_params*, int, int, cudaStream_t, tfde_batch**);
+namespace cnn {
+int cnn_create(const int n[3], tfde_cnn** out);
+int cnn_destroy(tfde_cnn* C);
+int cnn_set_params(tfde_cnn* C, const float* host);
+int cnn_get(const tfde_cnn* C, int what, float* host);
+int cnn_predict(tfde_cnn* C, const double* u, const double* dtF, const double coef[9], double* x0, cudaStream_t s);
+int cnn_accumulate(tfde_cnn* C, const double* u, const double* dtF, const double coef[9], const double* u_next,
+                   double* loss, cudaStream_t s);
+int cnn_adam(tfde_cnn* C, float lr, cudaStream_t s);
+}  // namespace cnn
 int batch_destroy(tfde_batch*);
 int batch_cn_advance(tfde_batch*, double* const*, const double* const*, int, double, tfde_info*, cudaStream_t);
 int destroy_problem(tfde_problem*);
@@ -16,7 +26,7 @@ int host_coefficients(const tfde_params*, int, double*, double*, double*, double
 int pcg64(const tfde_problem*, const double*, double*, double, int, tfde_info*, cudaStream_t, bool);
 int pgmres64(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t, bool);
 int cn_drive(tfde_problem*, const double*, const double*, const double*, double*, double, tfde_info*, cudaStream_t,
-             bool);
+             bool, const double*, int*);
 // mixed path (tfde_mixed.cu)
 int mixed_apply_A(const tfde_problem*, int, const double*, double*, cudaStream_t);
 int mixed_apply_Pinv(const tfde_problem*, const double*, double*, cudaStream_t);
@@ -129,7 +139,7 @@ int tfde_cn_step(const tfde_problem* prob, const double* u_prev, const double* F
     if (x0 && x0 == u_prev) x0 = nullptr;
     tfde_problem* P = const_cast<tfde_problem*>(prob);
     P->chain_ok = false;
-    return cn_drive(P, u_prev, F_half, x0, u_next, tol, info, (cudaStream_t)stream, false);
+    return cn_drive(P, u_prev, F_half, x0, u_next, tol, info, (cudaStream_t)stream, false, nullptr, nullptr);
 }
 
 int tfde_cn_advance(const tfde_problem* prob, double* u, const double* F_half, int restart, double tol,
@@ -142,7 +152,25 @@ int tfde_cn_advance(const tfde_problem* prob, double* u, const double* F_half, i
     tfde_problem* P = const_cast<tfde_problem*>(prob);
     const bool chained = !restart && P->chain_ok && P->chain_u == u;
     P->chain_ok = false;
-    st = cn_drive(P, u, F_half, nullptr, u, tol, info, (cudaStream_t)stream, chained);
+    st = cn_drive(P, u, F_half, nullptr, u, tol, info, (cudaStream_t)stream, chained, nullptr, nullptr);
+    if (st == TFDE_OK) {
+        P->chain_ok = true;
+        P->chain_u = u;
+    }
+    return st;
+}
+
+int tfde_cn_advance_guess(const tfde_problem* prob, double* u, const double* F_half, const double* x0, int restart,
+                          double tol, tfde_info* info, int* used_guess, void* stream) {
+    if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
+    int st;
+    if ((st = pre_call()) || (st = check_dev(u, "u")) || (st = check_dev(x0, "x0")) || (st = check_tol(tol))) return st;
+    if (F_half && (st = check_dev(F_half, "F_half"))) return st;
+    if (F_half == u || x0 == u) return set_error(TFDE_EINVAL, "F_half or x0 aliases u");
+    tfde_problem* P = const_cast<tfde_problem*>(prob);
+    const bool chained = !restart && P->chain_ok && P->chain_u == u;
+    P->chain_ok = false;
+    st = cn_drive(P, u, F_half, nullptr, u, tol, info, (cudaStream_t)stream, chained, x0, used_guess);
     if (st == TFDE_OK) {
         P->chain_ok = true;
         P->chain_u = u;
@@ -181,6 +209,54 @@ int tfde_batch_cn_advance(tfde_batch* batch, double* const* u, const double* con
             if (u[k] == u[i]) return set_error(TFDE_EINVAL, "two problems share one u buffer");
     }
     return batch_cn_advance(batch, u, F_half, restart, tol, infos, (cudaStream_t)stream);
+}
+
+int tfde_cnn_create(const int n[3], tfde_cnn** out) {
+    if (!n || !out) return set_error(TFDE_EINVAL, "NULL argument");
+    *out = nullptr;
+    int st = pre_call();
+    if (st) return st;
+    return cnn::cnn_create(n, out);
+}
+
+int tfde_cnn_destroy(tfde_cnn* net) { return cnn::cnn_destroy(net); }
+
+int tfde_cnn_set_params(tfde_cnn* net, const float* params) {
+    if (!net || !params) return set_error(TFDE_EINVAL, "NULL argument");
+    return cnn::cnn_set_params(net, params);
+}
+
+int tfde_cnn_get_params(const tfde_cnn* net, float* params) {
+    if (!net || !params) return set_error(TFDE_EINVAL, "NULL argument");
+    return cnn::cnn_get(net, 0, params);
+}
+
+int tfde_cnn_get_grads(const tfde_cnn* net, float* grads) {
+    if (!net || !grads) return set_error(TFDE_EINVAL, "NULL argument");
+    return cnn::cnn_get(net, 1, grads);
+}
+
+int tfde_cnn_predict(tfde_cnn* net, const double* u, const double* dtF, const double* coef, double* x0, void* stream) {
+    if (!net || !coef) return set_error(TFDE_EINVAL, "NULL argument");
+    int st;
+    if ((st = pre_call()) || (st = check_dev(u, "u")) || (st = check_dev(x0, "x0"))) return st;
+    if (dtF && (st = check_dev(dtF, "dtF"))) return st;
+    return cnn::cnn_predict(net, u, dtF, coef, x0, (cudaStream_t)stream);
+}
+
+int tfde_cnn_accumulate(tfde_cnn* net, const double* u, const double* dtF, const double* coef, const double* u_next,
+                        double* loss, void* stream) {
+    if (!net || !coef) return set_error(TFDE_EINVAL, "NULL argument");
+    int st;
+    if ((st = pre_call()) || (st = check_dev(u, "u")) || (st = check_dev(u_next, "u_next"))) return st;
+    if (dtF && (st = check_dev(dtF, "dtF"))) return st;
+    return cnn::cnn_accumulate(net, u, dtF, coef, u_next, loss, (cudaStream_t)stream);
+}
+
+int tfde_cnn_adam_step(tfde_cnn* net, float lr, void* stream) {
+    if (!net) return set_error(TFDE_EINVAL, "NULL argument");
+    if (!(lr > 0.f)) return set_error(TFDE_EINVAL, "learning rate must be > 0");
+    return cnn::cnn_adam(net, lr, (cudaStream_t)stream);
 }
 
 int tfde_source_example2(const tfde_problem* prob, double cP, double cS, double* F, void* stream) {

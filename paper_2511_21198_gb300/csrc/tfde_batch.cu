@@ -26,7 +26,7 @@ namespace tfde {
 int assemble_problem(const tfde_params* params, int precision, cudaStream_t s, tfde_problem** out);
 int destroy_problem(tfde_problem* P);
 int cn_prepare(tfde_problem* P, const double* u_prev, const double* F, const double* x0, double* u_next,
-               cudaStream_t s, bool chained, bool* r_given);
+               cudaStream_t s, bool chained, bool* r_given, const double* guess, int* used_guess);
 int pgmres64(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t, bool);
 
 namespace {
@@ -620,7 +620,8 @@ int batch_cn_advance(tfde_batch* B, double* const* u, const double* const* F, in
     fork(B, s);
     for (int i = 0; i < C; ++i) {
         bool rg = false;
-        if ((st = cn_prepare(B->P[i], uu[i], ff[i], nullptr, uu[i], B->aux[i % kStreams], chained, &rg))) {
+        if ((st = cn_prepare(B->P[i], uu[i], ff[i], nullptr, uu[i], B->aux[i % kStreams], chained, &rg, nullptr,
+                             nullptr))) {
             join(B, s);
             return st;
         }
@@ -675,7 +676,7 @@ int batch_cn_advance(tfde_batch* B, double* const* u, const double* const* F, in
             if (!outer[i]) continue;
             tfde_problem* P = B->P[i];
             if ((st = accurate_apply_ex(P, TFDE_OP_A, uu[i], P->w[tfde_problem::W_R], -1, P->w[tfde_problem::W_B], 1.0,
-                                        B->aux[i % kStreams]))) {
+                                        B->aux[i % kStreams], oz_slices_for_tol(tol)))) {
                 join(B, s);
                 return st;
             }

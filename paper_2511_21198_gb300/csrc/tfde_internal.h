@@ -67,15 +67,18 @@ void launch_multiaxpy_f64(size_t N, int m, const double* V, size_t ldv, const do
 // deterministic second stage: out[j] = sum_b part[j*nblk + b], j < m
 void launch_reduce_finish(const double* part, int nblk, int m, double* out, cudaStream_t s);
 int reduction_blocks(size_t N);
-// b = AN - Ku + dt F, r = dt F - 2 Ku  (first CN step of a chain)
+// b = AN - Ku + dt F, r = dt F - 2 Ku  (first CN step of a chain); with
+// norms2 set, also ||b||^2 and ||r||^2 into norms2[0..1] (device; part =
+// scratch of at least 2 * 2432 doubles)
 void launch_cn_first(size_t N, const double* AN, const double* Ku, const double* F, double dt, double* b, double* r,
-                     cudaStream_t s);
-// t = 2 AN + dt F; b <- t + r - b; r <- b_new + r - b_old  (chained CN step)
-void launch_cn_chain(size_t N, const double* AN, const double* F, double dt, double* b, double* r, cudaStream_t s);
+                     double* part, double* norms2, cudaStream_t s);
+// t = 2 AN + dt F; b <- t + r - b; r <- b_new + r - b_old  (chained CN step; norms as above)
+void launch_cn_chain(size_t N, const double* AN, const double* F, double dt, double* b, double* r, double* part,
+                     double* norms2, cudaStream_t s);
 // chained CN step with extrapolated initial guess written into u (see tfde_kernels64.cu)
 void launch_cn_chain_extrap(size_t N, const double* AN, const double* F, double dt, double* b, double* r, double* u,
-                            const double* U1, const double* AU1, double* U2, double* AU2, int order,
-                            cudaStream_t s);
+                            const double* U1, const double* AU1, double* U2, double* AU2, int order, double* part,
+                            double* norms2, cudaStream_t s);
 // F = cP PPP + cS (SPP + PSP + PPS) from 1-D arrays [Px|Py|Pz|Sx|Sy|Sz]
 void launch_source_assemble_f64(const double* oned, const int n[3], double cP, double cS, double* F,
                                 cudaStream_t s);
@@ -119,11 +122,15 @@ struct tfde_problem {
     // polynomial-extrapolation initial guess of the chained advance: order
     // (0: previous step), and the history (u, A u) of the two steps before
     int guess_order = 0;
+    // ||b||^2, ||r_0||^2 of the last cn_prepare in red_out[NORMS_SLOT..+1] (device)
+    bool norms_ready = false;
     int hist = 0;                 // valid history entries (0..2)
     double* H[2][2] = {};         // H[k] = {u^{m-2-k}, A u^{m-2-k}}
 };
 
 namespace tfde {
+// red_out slot of the fused ||b||^2, ||r_0||^2 of cn_prepare
+constexpr int kNormsSlot = 250;
 // solver internals (tfde_solvers.cu)
 int apply_A64(const tfde_problem* P, int op, const double* x, double* y, cudaStream_t s);
 int apply_Pinv64(const tfde_problem* P, const double* r, double* z, cudaStream_t s);

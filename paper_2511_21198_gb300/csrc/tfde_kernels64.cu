@@ -264,27 +264,53 @@ __global__ void source_assemble_f64_kernel(const double* __restrict__ oned, int 
     }
 }
 
-// b = AN - Ku + dt F ;  r = dt F - 2 Ku   (F may be null)
+// b = AN - Ku + dt F ;  r = dt F - 2 Ku   (F may be null); with part set,
+// per-block sums of b^2 and r^2 into part[block] and part[grid + block]
 __global__ void cn_first_kernel(long long N, const double* __restrict__ AN, const double* __restrict__ Ku,
                                 const double* __restrict__ F, double dt, double* __restrict__ b,
-                                double* __restrict__ r) {
+                                double* __restrict__ r, double* __restrict__ part) {
+    double bb = 0.0, rr = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const double f = F ? dt * F[i] : 0.0;
         const double k = Ku[i];
-        b[i] = AN[i] - k + f;
-        r[i] = fma(-2.0, k, f);
+        const double bi = AN[i] - k + f;
+        const double ri = fma(-2.0, k, f);
+        b[i] = bi;
+        r[i] = ri;
+        bb = fma(bi, bi, bb);
+        rr = fma(ri, ri, rr);
+    }
+    if (part) {
+        const double t1 = block_sum(bb);
+        const double t2 = block_sum(rr);
+        if (threadIdx.x == 0) {
+            part[blockIdx.x] = t1;
+            part[gridDim.x + blockIdx.x] = t2;
+        }
     }
 }
 
-// t = 2 AN + dt F ;  b <- t + r - b ;  r <- b_new + r - b_old
+// t = 2 AN + dt F ;  b <- t + r - b ;  r <- b_new + r - b_old  (norm partials as cn_first_kernel)
 __global__ void cn_chain_kernel(long long N, const double* __restrict__ AN, const double* __restrict__ F, double dt,
-                                double* __restrict__ b, double* __restrict__ r) {
+                                double* __restrict__ b, double* __restrict__ r, double* __restrict__ part) {
+    double bb = 0.0, rr = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const double t = fma(2.0, AN[i], F ? dt * F[i] : 0.0);
         const double d = r[i] - b[i];
         const double bn = t + d;
+        const double rn = bn + d;
         b[i] = bn;
-        r[i] = bn + d;
+        r[i] = rn;
+        bb = fma(bn, bn, bb);
+        rr = fma(rn, rn, rr);
+    }
+    if (part) {
+        const double t1 = block_sum(bb);
+        const double t2 = block_sum(rr);
+        if (threadIdx.x == 0) {
+            part[blockIdx.x] = t1;
+            part[gridDim.x + blockIdx.x] = t2;
+        }
     }
 }
 
@@ -300,7 +326,8 @@ __global__ void cn_chain_extrap_kernel(long long N, const double* __restrict__ A
                                        double dt, double* __restrict__ b, double* __restrict__ r,
                                        double* __restrict__ u, const double* __restrict__ U1,
                                        const double* __restrict__ AU1, double* __restrict__ U2,
-                                       double* __restrict__ AU2, int order) {
+                                       double* __restrict__ AU2, int order, double* __restrict__ part) {
+    double bb = 0.0, rr = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const double ui = u[i];
         const double au = b[i] - r[i];
@@ -313,11 +340,22 @@ __global__ void cn_chain_extrap_kernel(long long N, const double* __restrict__ A
             x = fma(3.0, ui - U1[i], U2[i]);
             ax = fma(3.0, au - AU1[i], AU2[i]);
         }
+        const double rn = bn - ax;
         b[i] = bn;
-        r[i] = bn - ax;
+        r[i] = rn;
         u[i] = x;
         U2[i] = ui;
         AU2[i] = au;
+        bb = fma(bn, bn, bb);
+        rr = fma(rn, rn, rr);
+    }
+    if (part) {
+        const double t1 = block_sum(bb);
+        const double t2 = block_sum(rr);
+        if (threadIdx.x == 0) {
+            part[blockIdx.x] = t1;
+            part[gridDim.x + blockIdx.x] = t2;
+        }
     }
 }
 
@@ -407,23 +445,35 @@ void launch_reduce_finish(const double* part, int nblk, int m, double* out, cuda
     reduce_finish_kernel<<<m, 32, 0, s>>>(part, nblk, m, out);
 }
 
-void launch_cn_first(size_t N, const double* AN, const double* Ku, const double* F, double dt, double* b, double* r,
-                     cudaStream_t s) {
-    stats_count_launch();
-    cn_first_kernel<<<grid_for((long long)N), kThreads, 0, s>>>((long long)N, AN, Ku, F, dt, b, r);
+// ||b||^2 and ||r||^2 of the chain kernels: partials of `grid` blocks -> norms2[0..1]
+static void finish_norms(double* part, int grid, double* norms2, cudaStream_t s) {
+    if (norms2) launch_reduce_finish(part, grid, 2, norms2, s);
 }
 
-void launch_cn_chain(size_t N, const double* AN, const double* F, double dt, double* b, double* r, cudaStream_t s) {
+void launch_cn_first(size_t N, const double* AN, const double* Ku, const double* F, double dt, double* b, double* r,
+                     double* part, double* norms2, cudaStream_t s) {
     stats_count_launch();
-    cn_chain_kernel<<<grid_for((long long)N), kThreads, 0, s>>>((long long)N, AN, F, dt, b, r);
+    const int g = grid_for((long long)N);
+    cn_first_kernel<<<g, kThreads, 0, s>>>((long long)N, AN, Ku, F, dt, b, r, norms2 ? part : nullptr);
+    finish_norms(part, g, norms2, s);
+}
+
+void launch_cn_chain(size_t N, const double* AN, const double* F, double dt, double* b, double* r, double* part,
+                     double* norms2, cudaStream_t s) {
+    stats_count_launch();
+    const int g = grid_for((long long)N);
+    cn_chain_kernel<<<g, kThreads, 0, s>>>((long long)N, AN, F, dt, b, r, norms2 ? part : nullptr);
+    finish_norms(part, g, norms2, s);
 }
 
 void launch_cn_chain_extrap(size_t N, const double* AN, const double* F, double dt, double* b, double* r, double* u,
-                            const double* U1, const double* AU1, double* U2, double* AU2, int order,
-                            cudaStream_t s) {
+                            const double* U1, const double* AU1, double* U2, double* AU2, int order, double* part,
+                            double* norms2, cudaStream_t s) {
     stats_count_launch();
-    cn_chain_extrap_kernel<<<grid_for((long long)N), kThreads, 0, s>>>((long long)N, AN, F, dt, b, r, u, U1, AU1, U2,
-                                                                       AU2, order);
+    const int g = grid_for((long long)N);
+    cn_chain_extrap_kernel<<<g, kThreads, 0, s>>>((long long)N, AN, F, dt, b, r, u, U1, AU1, U2, AU2, order,
+                                                  norms2 ? part : nullptr);
+    finish_norms(part, g, norms2, s);
 }
 
 void launch_source_assemble_f64(const double* oned, const int n[3], double cP, double cS, double* F,

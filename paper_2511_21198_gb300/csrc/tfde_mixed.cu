@@ -252,13 +252,36 @@ int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaSt
     return check_err(P, s);
 }
 
-int accurate_residual(const tfde_problem* P, const double* b, const double* x, double* r, double* nr,
-                      cudaStream_t s) {
-    int st = accurate_apply_ex(P, TFDE_OP_A, x, r, -1, b, 1.0, s);   // r = b - A x in the last pass
+// r = b - A x (accurate) and ||r||, the norm accumulated by the last pass of
+// the contraction with the terms scaled by 2^-ilogb(nb).
+int accurate_residual(const tfde_problem* P, const double* b, const double* x, double* r, double* nr, double tol,
+                      double nb, cudaStream_t s) {
+    const int shift = nb > 0.0 && std::isfinite(nb) ? -std::ilogb(nb) : 0;
+    double* acc = P->red_out + kNormsSlot + 2;
+    int st = accurate_apply_ex(P, TFDE_OP_A, x, r, -1, b, 1.0, s, oz_slices_for_tol(tol), acc, shift);
     if (st) return st;
-    double rr;
-    if ((st = dots64(P, 1, r, 0, r, &rr, s))) return st;
-    *nr = std::sqrt(rr);
+    MX_TRY(cudaMemcpyAsync(P->red_host, acc, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MX_TRY(cudaStreamSynchronize(s));
+    *nr = std::ldexp(std::sqrt(P->red_host[0]), -shift);
+    return TFDE_OK;
+}
+
+// ||b||^2 and (when r_given) ||r_0||^2: from the chain kernels of cn_prepare
+// when it left them in red_out, else by FP64 dots.
+int initial_norms(tfde_problem* P, const double* b, const double* r, bool r_given, double* bb, double* rr,
+                  cudaStream_t s) {
+    int st;
+    if (r_given && P->norms_ready) {
+        P->norms_ready = false;
+        MX_TRY(cudaMemcpyAsync(P->red_host, P->red_out + kNormsSlot, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        MX_TRY(cudaStreamSynchronize(s));
+        *bb = P->red_host[0];
+        *rr = P->red_host[1];
+        return TFDE_OK;
+    }
+    P->norms_ready = false;
+    if ((st = dots64(P, 1, b, 0, b, bb, s))) return st;
+    if (r_given && (st = dots64(P, 1, r, 0, r, rr, s))) return st;
     return TFDE_OK;
 }
 
@@ -518,8 +541,8 @@ int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit
     tfde_info loc{};
     double* r64 = P->w[tfde_problem::W_R];
     int st;
-    double bb;
-    if ((st = dots64(P, 1, b, 0, b, &bb, s))) return st;
+    double bb, rr0 = 0.0;
+    if ((st = initial_norms(const_cast<tfde_problem*>(P), b, r64, r_given, &bb, &rr0, s))) return st;
     const double nb = std::sqrt(bb);
     if (!std::isfinite(nb)) return set_error(TFDE_ENAN, "non-finite right-hand side");
     if (nb == 0.0) {
@@ -529,10 +552,8 @@ int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit
     }
     double nr;
     if (r_given) {
-        double rr0;
-        if ((st = dots64(P, 1, r64, 0, r64, &rr0, s))) return st;
         nr = std::sqrt(rr0);
-    } else if ((st = accurate_residual(P, b, x, r64, &nr, s))) {
+    } else if ((st = accurate_residual(P, b, x, r64, &nr, tol, nb, s))) {
         return st;
     }
     loc.relres0 = nr / nb;
@@ -552,7 +573,7 @@ int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit
         loc.refine_sweeps++;
         launch_add32to64(P->N, nr, M->f[F_X], x, s);
         const double nr_old = nr;
-        if ((st = accurate_residual(P, b, x, r64, &nr, s))) return st;
+        if ((st = accurate_residual(P, b, x, r64, &nr, tol, nb, s))) return st;
         stall = (nr > 0.5 * nr_old) ? stall + 1 : 0;
         if (stall >= 2) {
             // refinement stopped contracting: finish with FP64 inner solves
@@ -582,8 +603,8 @@ int mixed_pgmres(tfde_problem* P, const double* b, double* x, int restart, doubl
     double* r64 = P->w[tfde_problem::W_R];
     int st;
     if ((st = ensure_v32(P, restart))) return st;
-    double bb;
-    if ((st = dots64(P, 1, b, 0, b, &bb, s))) return st;
+    double bb, rr0 = 0.0;
+    if ((st = initial_norms(const_cast<tfde_problem*>(P), b, r64, r_given, &bb, &rr0, s))) return st;
     const double nb = std::sqrt(bb);
     if (!std::isfinite(nb)) return set_error(TFDE_ENAN, "non-finite right-hand side");
     if (nb == 0.0) {
@@ -593,10 +614,8 @@ int mixed_pgmres(tfde_problem* P, const double* b, double* x, int restart, doubl
     }
     double nr;
     if (r_given) {
-        double rr0;
-        if ((st = dots64(P, 1, r64, 0, r64, &rr0, s))) return st;
         nr = std::sqrt(rr0);
-    } else if ((st = accurate_residual(P, b, x, r64, &nr, s))) {
+    } else if ((st = accurate_residual(P, b, x, r64, &nr, tol, nb, s))) {
         return st;
     }
     loc.relres0 = nr / nb;
@@ -618,7 +637,7 @@ int mixed_pgmres(tfde_problem* P, const double* b, double* x, int restart, doubl
         loc.refine_sweeps++;
         launch_add32to64(P->N, nr, M->f[F_X], x, s);
         const double nr_old = nr;
-        if ((st = accurate_residual(P, b, x, r64, &nr, s))) return st;
+        if ((st = accurate_residual(P, b, x, r64, &nr, tol, nb, s))) return st;
         if (est_ratio > 0.0) {
             const double observed = (nr / nr_old) / est_ratio;
             ratio = observed > 1.0 ? observed : 1.0;

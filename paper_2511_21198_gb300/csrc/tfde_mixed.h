@@ -79,8 +79,8 @@ struct MixedState {
     double* gm = nullptr;
     double* gm_host = nullptr;
     // exact-integer slice path (tfde_oz.cu)
-    OzSet oz_x_plus, oz_x_minus, oz_x_stiff, oz_x_mass;      // A1 + G1, A1 - G1, G1, A1
-    OzSet oz_y_mass_c, oz_y_plus, oz_y_minus, oz_y_mass;     // (A2 | +-G2) common rows; A2 alone
+    OzSet oz_x_plus, oz_x_minus, oz_x_stiff;                 // A1 + G1, A1 - G1, G1
+    OzSet oz_y_mass_c, oz_y_plus, oz_y_minus;                // (A2 | +-G2) common rows
     OzSet oz_z_mass_c, oz_z_plus, oz_z_minus;                // (A3 | +-G3) common rows
     std::vector<int*> oz_rexp;                               // row exponent arrays
     __nv_bfloat16* oz_planes[2] = {nullptr, nullptr};        // digit planes of two inputs
@@ -104,7 +104,14 @@ int oz_init(tfde_problem* P, const std::vector<double> etaB[3], cudaStream_t s);
 void oz_free(MixedState* M);
 int accurate_apply(const tfde_problem* P, int op, const double* x, double* y, cudaStream_t s);
 // y = vsign * (operator x) + asign * addend (addend may be null)
+// norm2 (optional, device): receives sum_i (y_i 2^norm_shift)^2 accumulated
+// in FP32 terms by the last pass (24-bit terms: enough for stopping tests).
 int accurate_apply_ex(const tfde_problem* P, int op, const double* x, double* y, int vsign, const double* addend,
-                      double asign, cudaStream_t s);
+                      double asign, cudaStream_t s, int slices = OZ_SLICES, double* norm2 = nullptr,
+                      int norm_shift = 0);
+// Digit slices for a refinement residual at relative tolerance tol: 6 (42
+// bits, a worst-case error n 2^-42 < 1.1e-10 of |A||x| for n <= 448) while
+// tol >= 1e-9, else 7.
+inline int oz_slices_for_tol(double tol) { return tol >= 1e-9 ? 6 : OZ_SLICES; }
 
 }  // namespace tfde

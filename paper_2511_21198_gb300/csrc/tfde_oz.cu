@@ -61,51 +61,81 @@ __device__ __forceinline__ void write_digits(long long X, int S, __nv_bfloat16* 
     planes[idx] = __float2bfloat16_rn((float)X);
 }
 
-// x axis: one warp per line of n1 contiguous values, one or two inputs sliced
-// under their joint line maximum.
 // |x| bits of x * 2^sh for a normal or zero x (exponent field moved by sh)
 __device__ __forceinline__ unsigned long long abs_bits_shifted(long long bits, int sh) {
     const unsigned long long u = (unsigned long long)bits & 0x7FFFFFFFFFFFFFFFull;
     return u == 0 ? 0 : u + ((unsigned long long)(long long)sh << 52);
 }
 
-__global__ void slice_x_kernel(const double* __restrict__ x0, const double* __restrict__ x1, int sh1, int n1,
-                               long long lines, int S, __nv_bfloat16* __restrict__ p0,
-                               __nv_bfloat16* __restrict__ p1, long long N, int* __restrict__ lexp) {
+// The double Y * 2^s for an integer |Y| < 2^53 (exact; results below the
+// normal range are flushed to zero), from the integer bits alone.
+__device__ __forceinline__ double i64_ldexp_exact(long long Y, int s) {
+    if (Y == 0) return 0.0;
+    const unsigned long long neg = Y < 0 ? 1ull : 0ull;
+    const unsigned long long mag = (unsigned long long)(Y < 0 ? -Y : Y);
+    const int nbits = 64 - __clzll((long long)mag);
+    const int be = nbits - 1 + s + 1023;
+    if (be <= 0) return 0.0;
+    const unsigned long long m = mag << (53 - nbits);
+    return __longlong_as_double((long long)((neg << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1))));
+}
+
+// x axis: one warp per line of n1 contiguous values.  Writes the digit planes
+// of x under its line maximum and, when wout is set, w = A_{n1} x along the
+// line from the same fixed-point integers X (w_k = (X_{k-1} + 6 X_k +
+// X_{k+1}) 2^{E - 7S - 3}, |sum| < 2^53: exact).
+__global__ void slice_x_kernel(const double* __restrict__ x0, int n1, long long lines, int S,
+                               __nv_bfloat16* __restrict__ p0, long long N, int* __restrict__ lexp,
+                               double* __restrict__ wout) {
     const int lane = threadIdx.x & 31;
     const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long l = wg; l < lines; l += nw) {
         const long long* r0 = reinterpret_cast<const long long*>(x0 + l * n1);
-        const long long* r1 = x1 ? reinterpret_cast<const long long*>(x1 + l * n1) : nullptr;
         unsigned long long umax = 0;
 #pragma unroll 4
-        for (int k = lane; k < n1; k += 32) {
-            umax = max(umax, (unsigned long long)r0[k] & 0x7FFFFFFFFFFFFFFFull);
-            if (r1) umax = max(umax, abs_bits_shifted(r1[k], sh1));
-        }
+        for (int k = lane; k < n1; k += 32) umax = max(umax, (unsigned long long)r0[k] & 0x7FFFFFFFFFFFFFFFull);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) umax = max(umax, __shfl_xor_sync(0xffffffffu, umax, o));
         const int E = line_exponent_from_bits(umax);
-#pragma unroll 4
-        for (int k = lane; k < n1; k += 32) {
-            write_digits(fixed_point(r0[k], S, E), S, p0, N, l * n1 + k);
-            if (r1) write_digits(fixed_point(r1[k], S, E - sh1), S, p1, N, l * n1 + k);
+        long long left_carry = 0;   // X_{base - 1}
+        long long Xc = lane < n1 ? fixed_point(r0[lane], S, E) : 0;
+        for (int base = 0; base < n1; base += 32) {
+            const int k = base + lane;
+            const int kn = k + 32;
+            const long long Xn = kn < n1 ? fixed_point(r0[kn], S, E) : 0;
+            if (k < n1) write_digits(Xc, S, p0, N, l * n1 + k);
+            if (wout) {
+                long long left = __shfl_up_sync(0xffffffffu, Xc, 1);
+                long long right = __shfl_down_sync(0xffffffffu, Xc, 1);
+                const long long first_next = __shfl_sync(0xffffffffu, Xn, 0);
+                if (lane == 0) left = left_carry;
+                if (lane == 31) right = first_next;
+                if (k < n1) wout[l * n1 + k] = i64_ldexp_exact(left + 6 * Xc + right, E - 7 * S - 3);
+                left_carry = __shfl_sync(0xffffffffu, Xc, 31);
+            }
+            Xc = Xn;
         }
         if (lane == 0) lexp[l] = E;
     }
 }
 
-// y / z axes: 32 consecutive lines (contiguous in memory) x 8 k-groups per
-// 256-thread block; the joint line maximum is reduced through shared memory.
+// y / z axes: 32 consecutive lines (contiguous in memory) x 8 warps per
+// 256-thread block, warp g taking the g-th contiguous chunk of the line; the
+// joint line maximum of x0 and x1 * 2^sh1 is reduced through shared memory.
+// When eout is set, e = A_n x1 along the line from the fixed-point integers
+// W of x1 (exact as in slice_x_kernel).
 __global__ __launch_bounds__(256) void slice_strided_kernel(const double* __restrict__ x0,
                                                             const double* __restrict__ x1, int sh1, AxisView v, int S,
                                                             __nv_bfloat16* __restrict__ p0,
                                                             __nv_bfloat16* __restrict__ p1, long long N,
-                                                            int* __restrict__ lexp) {
+                                                            int* __restrict__ lexp, double* __restrict__ eout) {
     __shared__ unsigned long long smax[8][32];
     __shared__ int sexp[32];
     const int li = threadIdx.x & 31, kg = threadIdx.x >> 5;
+    const int kc = (v.n + 7) / 8;
+    const int k0 = kg * kc;
+    const int k1 = k0 + kc < v.n ? k0 + kc : v.n;
     const long long* b0 = reinterpret_cast<const long long*>(x0);
     const long long* b1 = reinterpret_cast<const long long*>(x1);
     for (long long l0 = (long long)blockIdx.x * 32; l0 < v.lines; l0 += (long long)gridDim.x * 32) {
@@ -114,8 +144,8 @@ __global__ __launch_bounds__(256) void slice_strided_kernel(const double* __rest
         const long long off = valid ? (l % v.l_in) * v.s_in + (l / v.l_in) * v.s_out : 0;
         unsigned long long umax = 0;
         if (valid) {
-#pragma unroll 4
-            for (int k = kg; k < v.n; k += 8) {
+#pragma unroll 8
+            for (int k = k0; k < k1; ++k) {
                 const long long idx = off + (long long)k * v.stride;
                 umax = max(umax, (unsigned long long)b0[idx] & 0x7FFFFFFFFFFFFFFFull);
                 if (b1) umax = max(umax, abs_bits_shifted(b1[idx], sh1));
@@ -132,13 +162,29 @@ __global__ __launch_bounds__(256) void slice_strided_kernel(const double* __rest
             if (valid) lexp[l] = E;
         }
         __syncthreads();
-        if (valid) {
+        if (valid && k0 < k1) {
             const int E = sexp[li];
+            const int E1 = E - sh1;
+            if (b1 && eout) {
+                long long Wp = k0 > 0 ? fixed_point(b1[off + (long long)(k0 - 1) * v.stride], S, E1) : 0;
+                long long Wc = fixed_point(b1[off + (long long)k0 * v.stride], S, E1);
 #pragma unroll 4
-            for (int k = kg; k < v.n; k += 8) {
-                const long long idx = off + (long long)k * v.stride;
-                write_digits(fixed_point(b0[idx], S, E), S, p0, N, idx);
-                if (b1) write_digits(fixed_point(b1[idx], S, E - sh1), S, p1, N, idx);
+                for (int k = k0; k < k1; ++k) {
+                    const long long idx = off + (long long)k * v.stride;
+                    const long long Wn = k + 1 < v.n ? fixed_point(b1[idx + v.stride], S, E1) : 0;
+                    write_digits(fixed_point(b0[idx], S, E), S, p0, N, idx);
+                    write_digits(Wc, S, p1, N, idx);
+                    eout[idx] = i64_ldexp_exact(Wp + 6 * Wc + Wn, E1 - 7 * S - 3);
+                    Wp = Wc;
+                    Wc = Wn;
+                }
+            } else {
+#pragma unroll 4
+                for (int k = k0; k < k1; ++k) {
+                    const long long idx = off + (long long)k * v.stride;
+                    write_digits(fixed_point(b0[idx], S, E), S, p0, N, idx);
+                    if (b1) write_digits(fixed_point(b1[idx], S, E1), S, p1, N, idx);
+                }
             }
         }
         __syncthreads();
@@ -237,7 +283,8 @@ int oz_init(tfde_problem* P, const std::vector<double> etaB[3], cudaStream_t s) 
     std::vector<std::vector<__nv_bfloat16>> sl;
     std::vector<int> rexp, nz;
     int st;
-    // x pass: (A1 + G1), (A1 - G1), G1 and A1, each under its own row scales
+    // x pass: (A1 + G1), (A1 - G1) and G1, each under its own row scales
+    // (A1 x itself comes out of the slicing, exactly)
     {
         const int n = P->n[0];
         const std::vector<double> A1 = mass(n);
@@ -246,16 +293,16 @@ int oz_init(tfde_problem* P, const std::vector<double> etaB[3], cudaStream_t s) 
             plus[i] += etaB[0][i];
             minus[i] -= etaB[0][i];
         }
-        const std::vector<double>* single[4] = {&plus, &minus, &etaB[0], &A1};
-        OzSet* sets[4] = {&M->oz_x_plus, &M->oz_x_minus, &M->oz_x_stiff, &M->oz_x_mass};
-        for (int k = 0; k < 4; ++k) {
+        const std::vector<double>* single[3] = {&plus, &minus, &etaB[0]};
+        OzSet* sets[3] = {&M->oz_x_plus, &M->oz_x_minus, &M->oz_x_stiff};
+        for (int k = 0; k < 3; ++k) {
             slice_operators_host({single[k]}, n, S, sl, rexp, nz);
             const int ri = upload_rexp(rexp);
             if (ri < 0) return set_error(TFDE_ENOMEM, "cudaMalloc of row exponents failed");
             if ((st = upload_set(*sets[k], sl[0], n, S, nz[0], ri, s))) return st;
         }
     }
-    // y and z passes: (A_a | +G_a) and (A_a | -G_a) under common row scales; A2 alone.
+    // y and z passes: (A_a | +G_a) and (A_a | -G_a) under common row scales.
     // The second input (A1 x, resp. A2 A1 x) is smaller than the first by about
     // max |G_a|; it is sliced as input * 2^k and G_a is stored as G_a * 2^-k
     // (both exact), so that the two inputs share their line scale without
@@ -280,14 +327,6 @@ int oz_init(tfde_problem* P, const std::vector<double> etaB[3], cudaStream_t s) 
         if ((st = upload_set(*m_set, sl[0], n, S, nz[0], ri, s))) return st;
         if ((st = upload_set(*p_set, sl[1], n, S, nz[1], ri, s))) return st;
         if ((st = upload_set(*n_set, sl[2], n, S, nz[2], ri, s))) return st;
-        if (a == 1) {
-            // e = A2 w with w sliced as w * 2^k: store A2 * 2^-k
-            for (auto& v : Am) v = std::ldexp(v, -k);
-            slice_operators_host({&Am}, n, S, sl, rexp, nz);
-            const int r2 = upload_rexp(rexp);
-            if (r2 < 0) return set_error(TFDE_ENOMEM, "cudaMalloc of row exponents failed");
-            if ((st = upload_set(M->oz_y_mass, sl[0], n, S, nz[0], r2, s))) return st;
-        }
     }
     OZ_TRY(cudaStreamSynchronize(s));
     // digit planes of two inputs and their maps
@@ -308,8 +347,8 @@ int oz_init(tfde_problem* P, const std::vector<double> etaB[3], cudaStream_t s) 
 }
 
 void oz_free(MixedState* M) {
-    OzSet* sets[] = {&M->oz_x_plus, &M->oz_x_minus, &M->oz_x_stiff, &M->oz_x_mass, &M->oz_y_mass_c, &M->oz_y_plus,
-                     &M->oz_y_minus, &M->oz_y_mass, &M->oz_z_mass_c, &M->oz_z_plus, &M->oz_z_minus};
+    OzSet* sets[] = {&M->oz_x_plus, &M->oz_x_minus, &M->oz_x_stiff, &M->oz_y_mass_c, &M->oz_y_plus,
+                     &M->oz_y_minus, &M->oz_z_mass_c, &M->oz_z_plus, &M->oz_z_minus};
     for (OzSet* z : sets) cudaFree(z->dev);
     for (int* r : M->oz_rexp) cudaFree(r);
     M->oz_rexp.clear();
@@ -321,20 +360,24 @@ void oz_free(MixedState* M) {
 namespace {
 
 // Slice one or two FP64 inputs along `axis` into the digit planes 0 / 1, the
-// second one taken as x1 * 2^sh1.
-void oz_slice(const tfde_problem* P, int axis, const double* x0, const double* x1, int sh1, cudaStream_t s) {
+// second one taken as x1 * 2^sh1; mass_out (optional) receives the mass
+// operator along `axis` applied to x1 (x0 on the x axis), exactly from the
+// fixed-point integers.
+void oz_slice(const tfde_problem* P, int axis, const double* x0, const double* x1, int sh1, double* mass_out,
+              int S, cudaStream_t s) {
     MixedState* M = mixed(P);
     const AxisView v = axis_view(P->n, axis);
     const long long N = (long long)P->N;
     stats_count_launch();
     if (axis == 0) {
-        slice_x_kernel<<<grid_for(v.lines * 32), 256, 0, s>>>(x0, x1, sh1, P->n[0], v.lines, OZ_SLICES, M->oz_planes[0],
-                                                               M->oz_planes[1], N, M->oz_lexp);
+        slice_x_kernel<<<grid_for(v.lines * 32), 256, 0, s>>>(x0, P->n[0], v.lines, S, M->oz_planes[0], N,
+                                                               M->oz_lexp, mass_out);
     } else {
+        // a few blocks per SM keep the lines of both passes over the input in L2
         long long blocks = (v.lines + 31) / 32;
-        if (blocks > 152LL * 8) blocks = 152LL * 8;
-        slice_strided_kernel<<<(unsigned)blocks, 256, 0, s>>>(x0, x1, sh1, v, OZ_SLICES, M->oz_planes[0], M->oz_planes[1],
-                                                              N, M->oz_lexp);
+        if (blocks > 152LL * 4) blocks = 152LL * 4;
+        slice_strided_kernel<<<(unsigned)blocks, 256, 0, s>>>(x0, x1, sh1, v, S, M->oz_planes[0],
+                                                              M->oz_planes[1], N, M->oz_lexp, mass_out);
     }
 }
 
@@ -345,16 +388,15 @@ struct OzSegSpec {
 };
 
 int oz_contract(const tfde_problem* P, int axis, const OzSegSpec* segs, int nseg, int vsign, const double* addend,
-                double asign, double* out, cudaStream_t s) {
+                double asign, double* out, int S, cudaStream_t s, double* norm2 = nullptr, int norm_shift = 0) {
     MixedState* M = mixed(P);
-    const int S = OZ_SLICES;
     const long long N = (long long)P->N;
     oz::Params prm;
     std::memset(&prm, 0, sizeof(prm));
     double pairs = 0.0;
     for (int g = 0; g < nseg; ++g) {
         oz::Segment& G = prm.seg[g];
-        G.na = segs[g].op->na;
+        G.na = std::min(segs[g].op->na, S);
         G.nb = S;
         for (int t = 0; t < S; ++t) {
             G.amaps[t] = segs[g].op->amap[t];
@@ -388,6 +430,8 @@ int oz_contract(const tfde_problem* P, int axis, const OzSegSpec* segs, int nseg
     prm.addend_sign = asign;
     prm.addend = addend;
     prm.out = out;
+    prm.norm2 = norm2;
+    prm.norm_shift = norm_shift;
     prm.err = M->err;
     if (!g_oz_attr) {
         OZ_TRY(cudaFuncSetAttribute(oz::oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM_BYTES));
@@ -395,13 +439,13 @@ int oz_contract(const tfde_problem* P, int axis, const OzSegSpec* segs, int nseg
     }
     const long long total = prm.ntiles * prm.mhalves;
     long long grid = total < tc::num_sms() ? total : tc::num_sms();
-    void* tok = stats_tc_begin(s);
+    void* tok = stats_tc_begin(s, TFDE_KIND_EXACT);
     oz::oz_gemm_kernel<<<(unsigned)(grid < 1 ? 1 : grid), oz::NUM_THREADS, oz::SMEM_BYTES, s>>>(prm);
     cudaError_t e = cudaGetLastError();
     // algorithmic bytes: digit planes of each input read once, FP64 out (+ addend);
     // flops: 2 n per grid point per digit pair
     const double na = prm.n;
-    stats_tc_end(tok, s, (2.0 * S * nseg + 8.0 + (addend ? 8.0 : 0.0)) * N, 2.0 * pairs * na * N);
+    stats_tc_end(tok, s, TFDE_KIND_EXACT, (2.0 * S * nseg + 8.0 + (addend ? 8.0 : 0.0)) * N, 2.0 * pairs * na * N);
     if (e != cudaSuccess) return set_error(TFDE_ECUDA, std::string("oz_gemm_kernel launch: ") + cudaGetErrorString(e));
     return TFDE_OK;
 }
@@ -410,7 +454,8 @@ int oz_contract(const tfde_problem* P, int axis, const OzSegSpec* segs, int nseg
 
 // y = vsign * (A x | (2 A_N - A) x | (A - A_N) x) [+ asign * addend], FP64-accurate.
 int accurate_apply_ex(const tfde_problem* P, int op, const double* x, double* y, int vsign, const double* addend,
-                      double asign, cudaStream_t s) {
+                      double asign, cudaStream_t s, int slices, double* norm2, int norm_shift) {
+    if (slices < 2 || slices > OZ_SLICES) slices = OZ_SLICES;
     MixedState* M = mixed(P);
     const bool rhs = (op & 1) != 0;
     const bool stiff = (op & TFDE_OP_STIFF) != 0;
@@ -419,23 +464,20 @@ int accurate_apply_ex(const tfde_problem* P, int op, const double* x, double* y,
     double* tc_ = P->w[tfde_problem::W_C];
     double* te = P->w[tfde_problem::W_E];
     int st;
-    // x pass
-    oz_slice(P, 0, x, nullptr, 0, s);
-    const OzSet* xop = stiff ? (rhs ? &M->oz_x_stiff : &M->oz_x_stiff) : (rhs ? &M->oz_x_minus : &M->oz_x_plus);
+    // x pass: a = (A1 +- G1) x (or G1 x), w = A1 x (in the slicing, exact)
+    oz_slice(P, 0, x, nullptr, 0, tw, slices, s);
+    const OzSet* xop = stiff ? &M->oz_x_stiff : (rhs ? &M->oz_x_minus : &M->oz_x_plus);
     OzSegSpec sa[1] = {{xop, 0}};
-    if ((st = oz_contract(P, 0, sa, 1, (stiff && rhs) ? -1 : 1, nullptr, 0.0, ta, s))) return st;
-    OzSegSpec sw[1] = {{&M->oz_x_mass, 0}};
-    if ((st = oz_contract(P, 0, sw, 1, 1, nullptr, 0.0, tw, s))) return st;
-    // y pass
-    oz_slice(P, 1, ta, tw, M->oz_shift[1], s);
+    if ((st = oz_contract(P, 0, sa, 1, (stiff && rhs) ? -1 : 1, nullptr, 0.0, ta, slices, s))) return st;
+    // y pass: c = A2 a +- G2 w, e = A2 w (in the slicing, exact)
+    oz_slice(P, 1, ta, tw, M->oz_shift[1], te, slices, s);
     OzSegSpec sc[2] = {{&M->oz_y_mass_c, 0}, {rhs ? &M->oz_y_minus : &M->oz_y_plus, 1}};
-    if ((st = oz_contract(P, 1, sc, 2, 1, nullptr, 0.0, tc_, s))) return st;
-    OzSegSpec se[1] = {{&M->oz_y_mass, 1}};
-    if ((st = oz_contract(P, 1, se, 1, 1, nullptr, 0.0, te, s))) return st;
-    // z pass
-    oz_slice(P, 2, tc_, te, M->oz_shift[2], s);
+    if ((st = oz_contract(P, 1, sc, 2, 1, nullptr, 0.0, tc_, slices, s))) return st;
+    // z pass: y = A3 c +- G3 e
+    oz_slice(P, 2, tc_, te, M->oz_shift[2], nullptr, slices, s);
     OzSegSpec sy[2] = {{&M->oz_z_mass_c, 0}, {rhs ? &M->oz_z_minus : &M->oz_z_plus, 1}};
-    return oz_contract(P, 2, sy, 2, vsign, addend, asign, y, s);
+    if (norm2) OZ_TRY(cudaMemsetAsync(norm2, 0, sizeof(double), s));
+    return oz_contract(P, 2, sy, 2, vsign, addend, asign, y, slices, s, norm2, norm_shift);
 }
 
 int accurate_apply(const tfde_problem* P, int op, const double* x, double* y, cudaStream_t s) {

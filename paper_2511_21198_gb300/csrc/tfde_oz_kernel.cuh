@@ -71,6 +71,8 @@ struct Params {
     double addend_sign;
     const double* addend;      // may be null
     double* out;
+    double* norm2;             // optional: += sum over outputs of (out 2^norm_shift)^2 (FP32 terms)
+    int norm_shift;
     int* err;
 };
 
@@ -120,6 +122,37 @@ __device__ __forceinline__ double i128_ldexp(__int128 I, int s) {
     const unsigned long long bits =
         ((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1));
     return __longlong_as_double((long long)bits);
+}
+
+// The double nearest to I * 2^s for a signed 64-bit I (|I| < 2^62), rounded
+// to nearest even from the integer bits, without branches: normalise the
+// magnitude to bit 63, keep 53 bits, round on the guard bit with the sticky
+// bits and the last kept bit, and add the (possibly carried) mantissa onto the
+// exponent field.  Zero and results below the normal range give 0.
+__device__ __forceinline__ double i64_ldexp(long long I, int s) {
+    const unsigned long long sign = (unsigned long long)I & 0x8000000000000000ull;
+    const unsigned long long mag = (unsigned long long)(I < 0 ? -I : I);
+    const int lz = __clzll((long long)mag);                          // 64 for mag == 0
+    const unsigned long long nrm = mag << (lz & 63);                  // leading one at bit 63
+    const unsigned long long kept = nrm >> 11;                        // 53 bits, hidden bit at 52
+    const unsigned long long guard = (nrm >> 10) & 1ull;
+    const unsigned long long sticky = (nrm & 0x3FFull) != 0ull ? 1ull : 0ull;
+    const unsigned long long m = kept + (guard & (sticky | (kept & 1ull)));   // may carry to 2^53
+    const int be = 63 - lz + s + 1023;                                // biased exponent of the leading one
+    const unsigned long long bits = ((unsigned long long)(long long)(be - 1) << 52) + m;
+    return (mag == 0ull || be <= 0) ? 0.0 : __longlong_as_double((long long)(sign | bits));
+}
+
+// FP32 value of v * 2^shift from the FP64 bits (mantissa truncated to 24
+// bits; 0 below and +-inf above the FP32 range): the terms of a norm.
+__device__ __forceinline__ float scaled_f32(double v, int shift) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7FF);
+    const int fe = e - 1023 + 127 + shift;
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const unsigned int mant = (unsigned int)((b >> 29) & 0x7FFFFFu);
+    const unsigned int bits = fe >= 255 ? (sign | 0x7F800000u) : (sign | ((unsigned int)fe << 23) | mant);
+    return (e == 0 || fe <= 0) ? 0.f : __uint_as_float(bits);
 }
 
 __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_constant__ Params p) {
@@ -246,6 +279,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
         const int q = warp & 3;                 // TMEM lane quadrant
         const int half = (warp - 2) >> 2;       // columns [32 half, 32 half + 32)
         long long it = 0;
+        float nacc = 0.f;                       // this thread's share of the output norm
         for (long long t = blockIdx.x; t < total; t += gridDim.x, ++it) {
             int ok = 1;
             if (lane == 0) ok = mbar_wait(tfull, (uint32_t)it & 1u, p.err) ? 1 : 0;
@@ -287,26 +321,27 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                     double o[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
-                        // I = sum_d a_d 2^{7(D-d)} exactly (adjacent diagonals pair in int32)
+                        // I = sum_d a_d 2^{7(D-d)} exactly; |a_d| < 2^24
+                        if (S == 6) {
+                            long long I6 = 0;
+#pragma unroll
+                            for (int dd = 0; dd < 6; ++dd)
+                                I6 = I6 * 128 + (long long)__float2int_rn(__uint_as_float(r[dd][j]));
+                            o[j] = i64_ldexp(p.value_sign < 0 ? -I6 : I6, es + el[j] - 7 * (D + 2));
+                            continue;
+                        }
                         __int128 I = 0;
                         if (S == 7) {
-                            int av[7];
+                            long long av[7];
 #pragma unroll
                             for (int dd = 0; dd < 7; ++dd) av[dd] = __float2int_rn(__uint_as_float(r[dd][j]));
-                            const long long hi = (long long)(av[0] * 128 + av[1]) * 16384 + (av[2] * 128 + av[3]);
-                            const long long lo = (long long)(av[4] * 128 + av[5]) * 128 + av[6];
+                            const long long hi = ((av[0] * 128 + av[1]) * 128 + av[2]) * 128 + av[3];
+                            const long long lo = (av[4] * 128 + av[5]) * 128 + av[6];
                             I = (__int128)hi * (1 << 21) + lo;
                         } else {
 #pragma unroll
-                            for (int dd = 0; dd < MAXS; dd += 2) {
-                                if (dd + 1 < S) {
-                                    const int pr = __float2int_rn(__uint_as_float(r[dd][j])) * 128 +
-                                                   __float2int_rn(__uint_as_float(r[dd + 1][j]));
-                                    I = I * 16384 + pr;
-                                } else if (dd < S) {
-                                    I = I * 128 + __float2int_rn(__uint_as_float(r[dd][j]));
-                                }
-                            }
+                            for (int dd = 0; dd < MAXS; ++dd)
+                                if (dd < S) I = I * 128 + __float2int_rn(__uint_as_float(r[dd][j]));
                         }
                         o[j] = i128_ldexp(p.value_sign < 0 ? -I : I, es + el[j] - 7 * (D + 2));
                     }
@@ -318,6 +353,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                             double v = o[j];
                             if (p.addend) v = fma(p.addend_sign, p.addend[idx], v);
                             p.out[idx] = v;
+                            if (p.norm2) {
+                                const float f = scaled_f32(v, p.norm_shift);
+                                nacc = fmaf(f, f, nacc);
+                            }
                         }
                     } else {
                         // the 8 columns are 64 contiguous, 64-byte aligned bytes of row m
@@ -333,6 +372,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                         }
 #pragma unroll
                         for (int v = 0; v < 4; ++v) dst[v] = make_double2(o[2 * v], o[2 * v + 1]);
+                        if (p.norm2) {
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const float f = scaled_f32(o[j], p.norm_shift);
+                                nacc = fmaf(f, f, nacc);
+                            }
+                        }
                     }
                 }
                 __syncwarp();
@@ -340,6 +386,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty);
+        }
+        if (p.norm2) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) nacc += __shfl_xor_sync(0xffffffffu, nacc, o);
+            if (lane == 0) atomicAdd(p.norm2, (double)nacc);
         }
     }
 

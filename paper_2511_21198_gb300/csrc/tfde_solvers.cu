@@ -299,6 +299,8 @@ int pgmres64(tfde_problem* P, const double* b, double* x, int restart, double to
 int mixed_pcg(tfde_problem*, const double*, double*, double, int, tfde_info*, cudaStream_t, bool);
 int mixed_pgmres(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t, bool);
 int accurate_apply(const tfde_problem*, int, const double*, double*, cudaStream_t);
+int accurate_apply_ex(const tfde_problem*, int, const double*, double*, int, const double*, double, cudaStream_t, int,
+                      double*, int);
 
 // A_N u into `out` (three tridiagonal sweeps; W_A and W_W as temporaries).
 static void mass_apply(const tfde_problem* P, const double* u, double* out, cudaStream_t s) {
@@ -313,7 +315,7 @@ static void mass_apply(const tfde_problem* P, const double* u, double* out, cuda
 // cn_prepare forms b^m in W_B, the initial guess in u_next and (when *r_given)
 // its residual in W_R; cn_drive then runs the solver.
 int cn_prepare(tfde_problem* P, const double* u_prev, const double* F, const double* x0, double* u_next,
-               cudaStream_t s, bool chained, bool* r_given) {
+               cudaStream_t s, bool chained, bool* r_given, const double* guess, int* used_guess) {
     double* b = P->w[tfde_problem::W_B];
     double* r = P->w[tfde_problem::W_R];
     double* an = P->w[tfde_problem::W_T];
@@ -322,7 +324,8 @@ int cn_prepare(tfde_problem* P, const double* u_prev, const double* F, const dou
     int st;
     mass_apply(P, u_prev, an, s);
     bool guess_in_place = false;  // x0 already written into u_next, r = b - A x0
-    if (chained && P->guess_order > 0 && u_next == u_prev) {
+    if (used_guess) *used_guess = 0;
+    if (chained && P->guess_order > 0 && u_next == u_prev && !guess) {
         if (!P->H[0][0]) {
             for (auto& hk : P->H)
                 for (auto& v : hk)
@@ -332,31 +335,55 @@ int cn_prepare(tfde_problem* P, const double* u_prev, const double* F, const dou
         }
         const int order = P->guess_order < P->hist ? P->guess_order : P->hist;
         launch_cn_chain_extrap(P->N, an, F, P->p.dt, b, r, u_next, P->H[0][0], P->H[0][1], P->H[1][0], P->H[1][1],
-                               order, s);
+                               order, P->red, P->red_out + kNormsSlot, s);
         std::swap(P->H[0][0], P->H[1][0]);
         std::swap(P->H[0][1], P->H[1][1]);
         P->hist = P->hist < 2 ? P->hist + 1 : 2;
         guess_in_place = true;
     } else if (chained) {
-        launch_cn_chain(P->N, an, F, P->p.dt, b, r, s);
+        if (guess) P->hist = 0;
+        launch_cn_chain(P->N, an, F, P->p.dt, b, r, P->red, P->red_out + kNormsSlot, s);
     } else {
         P->hist = 0;
         double* ku = P->w[tfde_problem::W_Q];
         st = mixed_prec ? accurate_apply(P, TFDE_OP_STIFF, u_prev, ku, s) : apply_A64(P, TFDE_OP_STIFF, u_prev, ku, s);
         if (st) return st;
-        launch_cn_first(P->N, an, ku, F, P->p.dt, b, r, s);
+        launch_cn_first(P->N, an, ku, F, P->p.dt, b, r, P->red, P->red_out + kNormsSlot, s);
     }
     const double* start = guess_is_prev ? u_prev : x0;
     if (!guess_in_place && start != u_next)
         TFDE_CUDA_TRY(cudaMemcpyAsync(u_next, start, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     *r_given = guess_is_prev;  // r = b - A x0 is the residual of the initial guess
+    P->norms_ready = guess_is_prev;
+    if (guess && guess_is_prev) {
+        // candidate guess: r_g = r - A (guess - u_prev); keep it if its FP64
+        // residual is smaller than that of u_prev (the previous-step guess)
+        double* d = P->w[tfde_problem::W_P];
+        double* rg = P->w[tfde_problem::W_Z];
+        launch_axpbypz_f64(P->N, 1.0, guess, -1.0, u_prev, d, s);
+        if (mixed_prec) {
+            st = accurate_apply_ex(P, TFDE_OP_A, d, rg, -1, r, 1.0, s, 7, nullptr, 0);
+        } else {
+            st = apply_A64(P, TFDE_OP_A, d, rg, s);
+            if (!st) launch_axpby_f64(P->N, 1.0, r, -1.0, rg, s);
+        }
+        if (st) return st;
+        double rr[2];
+        if ((st = dots64(P, 1, r, 0, r, &rr[0], s)) || (st = dots64(P, 1, rg, 0, rg, &rr[1], s))) return st;
+        if (std::isfinite(rr[1]) && rr[1] < rr[0]) {
+            TFDE_CUDA_TRY(cudaMemcpyAsync(u_next, guess, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            TFDE_CUDA_TRY(cudaMemcpyAsync(r, rg, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            P->norms_ready = false;
+            if (used_guess) *used_guess = 1;
+        }
+    }
     return TFDE_OK;
 }
 
 int cn_drive(tfde_problem* P, const double* u_prev, const double* F, const double* x0, double* u_next, double tol,
-             tfde_info* info, cudaStream_t s, bool chained) {
+             tfde_info* info, cudaStream_t s, bool chained, const double* guess, int* used_guess) {
     bool rg = false;
-    int st = cn_prepare(P, u_prev, F, x0, u_next, s, chained, &rg);
+    int st = cn_prepare(P, u_prev, F, x0, u_next, s, chained, &rg, guess, used_guess);
     if (st) return st;
     double* b = P->w[tfde_problem::W_B];
     const bool mixed_prec = P->prec == TFDE_MIXED;

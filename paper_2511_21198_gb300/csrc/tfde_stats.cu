@@ -9,6 +9,7 @@ namespace tfde {
 namespace {
 struct EvPair {
     cudaEvent_t a, b;
+    int kind;
 };
 tfde_stats g_stats{};
 bool g_time_tc = false;
@@ -21,8 +22,8 @@ void harvest(bool all) {
         float ms = 0.f;
         cudaEventSynchronize(g_pending[i].b);
         if (cudaEventElapsedTime(&ms, g_pending[i].a, g_pending[i].b) == cudaSuccess) {
-            g_stats.tc_ms += ms;
-            g_stats.tc_timed++;
+            g_stats.kind[g_pending[i].kind].ms += ms;
+            g_stats.kind[g_pending[i].kind].timed++;
         }
         g_pool.push_back(g_pending[i]);
     }
@@ -32,9 +33,9 @@ void harvest(bool all) {
 
 void stats_count_launch(unsigned n) { g_stats.kernel_launches += n; }
 
-void* stats_tc_begin(cudaStream_t s) {
+void* stats_tc_begin(cudaStream_t s, int kind) {
     g_stats.kernel_launches++;
-    g_stats.tc_launches++;
+    g_stats.kind[kind].launches++;
     if (!g_time_tc) return nullptr;
     if (g_pending.size() > 4096) harvest(false);
     EvPair e;
@@ -45,14 +46,15 @@ void* stats_tc_begin(cudaStream_t s) {
         cudaEventCreate(&e.a);
         cudaEventCreate(&e.b);
     }
+    e.kind = kind;
     cudaEventRecord(e.a, s);
     g_pending.push_back(e);
     return reinterpret_cast<void*>(1);
 }
 
-void stats_tc_end(void* tok, cudaStream_t s, double bytes, double flops) {
-    g_stats.tc_bytes += bytes;
-    g_stats.tc_flops += flops;
+void stats_tc_end(void* tok, cudaStream_t s, int kind, double bytes, double flops) {
+    g_stats.kind[kind].bytes += bytes;
+    g_stats.kind[kind].flops += flops;
     if (tok) cudaEventRecord(g_pending.back().b, s);
 }
 

@@ -4,8 +4,8 @@
 
 namespace tfde {
 void stats_count_launch(unsigned n = 1);
-void* stats_tc_begin(cudaStream_t s);
-void stats_tc_end(void* tok, cudaStream_t s, double bytes, double flops);
+void* stats_tc_begin(cudaStream_t s, int kind);
+void stats_tc_end(void* tok, cudaStream_t s, int kind, double bytes, double flops);
 int stats_reset(int time_tc);
 int stats_get(tfde_stats* out);
 }  // namespace tfde

@@ -43,6 +43,11 @@ int g_num_sms = 0;
 
 }  // namespace
 
+int encode_map(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
+               const cuuint32_t* box, CUtensorMapSwizzle sw) {
+    return encode(m, base, rank, dims, strides, box, sw);
+}
+
 int num_sms() {
     if (!g_num_sms) {
         int dev = 0;
@@ -133,10 +138,10 @@ int launch(const Params& P, cudaStream_t s, double bytes, double flops) {
     const long long total = P.ntiles * P.mhalves;
     long long grid = total < num_sms() ? total : num_sms();
     if (grid < 1) grid = 1;
-    void* tok = stats_tc_begin(s);
+    void* tok = stats_tc_begin(s, TFDE_KIND_SPLIT);
     axis_gemm_kernel<false><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(P, nullptr, nullptr, 0, nullptr);
     cudaError_t e = cudaGetLastError();
-    stats_tc_end(tok, s, bytes, flops);
+    stats_tc_end(tok, s, TFDE_KIND_SPLIT, bytes, flops);
     if (e != cudaSuccess) return set_error(TFDE_ECUDA, std::string("axis_gemm_kernel launch: ") + cudaGetErrorString(e));
     return TFDE_OK;
 }
@@ -152,10 +157,10 @@ int launch_grouped(const Params* groups, const long long* gstart, int ngroups, l
     p0.b_kmajor = b_kmajor;
     p0.err = err;
     long long grid = total < num_sms() ? total : num_sms();
-    void* tok = stats_tc_begin(s);
+    void* tok = stats_tc_begin(s, TFDE_KIND_SPLIT);
     axis_gemm_kernel<true><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(p0, groups, gstart, ngroups, gactive);
     cudaError_t e = cudaGetLastError();
-    stats_tc_end(tok, s, bytes, flops);
+    stats_tc_end(tok, s, TFDE_KIND_SPLIT, bytes, flops);
     if (e != cudaSuccess)
         return set_error(TFDE_ECUDA, std::string("grouped axis_gemm_kernel launch: ") + cudaGetErrorString(e));
     return TFDE_OK;

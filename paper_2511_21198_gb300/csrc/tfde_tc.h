@@ -10,6 +10,10 @@ namespace tfde {
 namespace tc {
 
 int num_sms();
+// BF16 tiled tensor map (rank <= 5): dims / box innermost first, strides in
+// bytes for dimensions 1.. (rank - 1 entries).
+int encode_map(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
+               const cuuint32_t* box, CUtensorMapSwizzle sw);
 int make_map_A(CUtensorMap* m, const __nv_bfloat16* base, int n);
 int make_map_B(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis);
 int make_map_B_box(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis, int box_lines);

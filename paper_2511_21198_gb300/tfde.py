@@ -36,10 +36,16 @@ class tfde_info(Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class tfde_kernel_stats(Structure):
+    _fields_ = [("launches", ctypes.c_ulonglong), ("timed", ctypes.c_ulonglong), ("ms", c_double),
+                ("bytes", c_double), ("flops", c_double)]
+
+
+TFDE_KIND_SPLIT, TFDE_KIND_EXACT, TFDE_KIND_CONV = 0, 1, 2
+
+
 class tfde_stats(Structure):
-    _fields_ = [("kernel_launches", ctypes.c_ulonglong), ("tc_launches", ctypes.c_ulonglong),
-                ("tc_ms", c_double), ("tc_bytes", c_double), ("tc_flops", c_double),
-                ("tc_timed", ctypes.c_ulonglong)]
+    _fields_ = [("kernel_launches", ctypes.c_ulonglong), ("kind", tfde_kernel_stats * 3)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -56,7 +62,9 @@ _lib = None
 EXPORTS = ["tfde_assemble", "tfde_destroy", "tfde_matvec", "tfde_precond", "tfde_pcg", "tfde_pgmres",
            "tfde_cn_step", "tfde_cn_advance", "tfde_set_guess_order", "tfde_source_example2", "tfde_coefficients", "tfde_host_coefficients",
            "tfde_stats_reset", "tfde_stats_get", "tfde_mass_apply_noalloc", "tfde_batch_create", "tfde_batch_destroy",
-           "tfde_batch_count", "tfde_batch_cn_advance", "tfde_last_error", "tfde_version"]
+           "tfde_batch_count", "tfde_batch_cn_advance", "tfde_cn_advance_guess", "tfde_cnn_create", "tfde_cnn_destroy",
+           "tfde_cnn_set_params", "tfde_cnn_get_params", "tfde_cnn_get_grads", "tfde_cnn_predict", "tfde_cnn_accumulate",
+           "tfde_cnn_adam_step", "tfde_last_error", "tfde_version"]
 
 
 def load(path: str | None = None):
@@ -91,6 +99,15 @@ def load(path: str | None = None):
         "tfde_batch_count": ([vp], c_int),
         "tfde_batch_cn_advance": ([vp, POINTER(c_void_p), POINTER(c_void_p), c_int, c_double, POINTER(tfde_info),
                                    vp], c_int),
+        "tfde_cn_advance_guess": ([vp, vp, vp, vp, c_int, c_double, POINTER(tfde_info), POINTER(c_int), vp], c_int),
+        "tfde_cnn_create": ([POINTER(c_int), POINTER(c_void_p)], c_int),
+        "tfde_cnn_destroy": ([vp], c_int),
+        "tfde_cnn_set_params": ([vp, POINTER(c_float)], c_int),
+        "tfde_cnn_get_params": ([vp, POINTER(c_float)], c_int),
+        "tfde_cnn_get_grads": ([vp, POINTER(c_float)], c_int),
+        "tfde_cnn_predict": ([vp, vp, vp, POINTER(c_double), vp, vp], c_int),
+        "tfde_cnn_accumulate": ([vp, vp, vp, POINTER(c_double), vp, POINTER(c_double), vp], c_int),
+        "tfde_cnn_adam_step": ([vp, c_float, vp], c_int),
         "tfde_last_error": ([], c_char_p),
         "tfde_version": ([], c_char_p),
     }
@@ -272,3 +289,75 @@ def tfde_batch_cn_advance(batch: int, u_list, F_list, restart: bool, tol: float,
     for i in out:
         i.status = st
     return out
+
+
+CNN_PARAMS = 4 * (16 * 16 * 27 + 16)
+
+
+def tfde_cn_advance_guess(prob: int, u, F_half, x0, restart: bool, tol: float, stream=None,
+                          check: bool = True):
+    """Chained CN step starting from x0 when its FP64 residual beats u^{m-1}'s;
+    returns (info, used_guess)."""
+    info = tfde_info()
+    used = c_int(0)
+    st = load().tfde_cn_advance_guess(prob, _ptr(u), _ptr(F_half), _ptr(x0), 1 if restart else 0, tol, byref(info),
+                                      byref(used), _stream(stream))
+    if check:
+        _check(st, "tfde_cn_advance_guess")
+    info.status = st
+    return info, bool(used.value)
+
+
+def tfde_cnn_create(n) -> int:
+    arr = (c_int * 3)(*[int(v) for v in n])
+    h = c_void_p()
+    _check(load().tfde_cnn_create(arr, byref(h)), "tfde_cnn_create")
+    return h.value
+
+
+def tfde_cnn_destroy(net: int) -> None:
+    _check(load().tfde_cnn_destroy(net), "tfde_cnn_destroy")
+
+
+def _f32(a):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.size != CNN_PARAMS:
+        raise ValueError(f"expected {CNN_PARAMS} parameters, got {a.size}")
+    return a
+
+
+def tfde_cnn_set_params(net: int, params) -> None:
+    a = _f32(params)
+    _check(load().tfde_cnn_set_params(net, a.ctypes.data_as(POINTER(c_float))), "tfde_cnn_set_params")
+
+
+def tfde_cnn_get_params(net: int):
+    import numpy as np
+    a = np.zeros(CNN_PARAMS, dtype=np.float32)
+    _check(load().tfde_cnn_get_params(net, a.ctypes.data_as(POINTER(c_float))), "tfde_cnn_get_params")
+    return a
+
+
+def tfde_cnn_get_grads(net: int):
+    import numpy as np
+    a = np.zeros(CNN_PARAMS, dtype=np.float32)
+    _check(load().tfde_cnn_get_grads(net, a.ctypes.data_as(POINTER(c_float))), "tfde_cnn_get_grads")
+    return a
+
+
+def tfde_cnn_predict(net: int, u, dtF, coef, x0, stream=None) -> None:
+    c = (c_double * 9)(*[float(v) for v in coef])
+    _check(load().tfde_cnn_predict(net, _ptr(u), _ptr(dtF), c, _ptr(x0), _stream(stream)), "tfde_cnn_predict")
+
+
+def tfde_cnn_accumulate(net: int, u, dtF, coef, u_next, stream=None) -> float:
+    c = (c_double * 9)(*[float(v) for v in coef])
+    loss = c_double(0.0)
+    _check(load().tfde_cnn_accumulate(net, _ptr(u), _ptr(dtF), c, _ptr(u_next), byref(loss), _stream(stream)),
+           "tfde_cnn_accumulate")
+    return loss.value
+
+
+def tfde_cnn_adam_step(net: int, lr: float, stream=None) -> None:
+    _check(load().tfde_cnn_adam_step(net, lr, _stream(stream)), "tfde_cnn_adam_step")

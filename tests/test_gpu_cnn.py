@@ -1,0 +1,174 @@
+"""GPU parity of the warm-start network (tfde_cnn_*): the tensor-core
+convolutions, the backward pass and the Adam update against the CPU oracle,
+and the guard that keeps the previous-step guess when the proposed one is not
+better (tfde_cn_advance_guess)."""
+import numpy as np
+import pytest
+
+from oracle import cnn_oracle as C
+from oracle import tfde_oracle as o
+import tfde_inputs as inp
+from gpu_helpers import relerr, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_2511_21198_gb300 import build
+    build.build()
+    from paper_2511_21198_gb300 import tfde
+    tfde.load()
+    return tfde
+
+
+@pytest.fixture(scope="module")
+def W():
+    from paper_2511_21198_gb300 import warmstart
+    return warmstart
+
+
+def bf16(a):
+    """Round to the nearest BF16 (ties to even), returned as float64."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def bf16_forward(layers, x):
+    """The oracle's forward pass with the storage precision of the kernels:
+    BF16 inputs, weights and hidden activations, exact accumulation."""
+    a = bf16(x)
+    for k, (Wt, b) in enumerate(layers):
+        z = C.conv3d(a, bf16(Wt), b.astype(np.float32).astype(np.float64))
+        a = bf16(np.maximum(z, 0.0)) if k + 1 < len(layers) else z
+    return a
+
+
+def random_net(W, seed):
+    flat = W.init_params(seed, last_scale=1.0)
+    rng = np.random.default_rng(seed + 1)
+    for l in range(4):
+        cout = W.CHANNELS[l + 1]
+        flat[l * W.PSZ + W.WSZ:l * W.PSZ + W.WSZ + cout] = 0.05 * rng.standard_normal(cout)
+    return flat
+
+
+@pytest.mark.parametrize("n", [(10, 7, 5), (33, 4, 6)])
+def test_forward_matches_oracle(T, W, n):
+    """x0 - u = s * net(...) on grids whose 128-slot tiles span several lines
+    and planes with ragged ends."""
+    flat = random_net(W, 3)
+    net = T.tfde_cnn_create(n)
+    try:
+        T.tfde_cnn_set_params(net, flat)
+        shape = tuple(reversed(n))
+        u = inp.uniform_vector(shape, 5) - 0.3
+        dtF = 0.1 * inp.uniform_vector(shape, 6)
+        coef = [0.3, 0.6, 0.8, 1.0, 1.5, 0.7, 0.5, 2.0, 1.2]
+        x0 = to_dev(np.zeros(shape))
+        T.tfde_cnn_predict(net, to_dev(u), to_dev(dtF), coef, x0)
+        x, s = C.input_channels(u, dtF, coef[0:3], coef[3:6], coef[6:9])
+        ref = bf16_forward(W.flat_to_layers(flat), x)[0]
+        got = (to_host(x0) - u) / s
+        assert relerr(got, ref) < 1e-2
+        assert np.abs(got - ref).max() <= 3e-2 * np.abs(ref).max()
+    finally:
+        T.tfde_cnn_destroy(net)
+
+
+def test_gradients_match_oracle(T, W):
+    """One accumulated sample: loss and the gradient of every layer against the
+    oracle's backpropagation (on the BF16-rounded inputs and weights)."""
+    n = (12, 9, 6)
+    flat = random_net(W, 7)
+    net = T.tfde_cnn_create(n)
+    try:
+        T.tfde_cnn_set_params(net, flat)
+        shape = tuple(reversed(n))
+        u = inp.uniform_vector(shape, 8) - 0.5
+        un = u + 0.05 * (inp.uniform_vector(shape, 9) - 0.5)
+        coef = [0.5, 0.5, 0.5, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0]
+        loss = T.tfde_cnn_accumulate(net, to_dev(u), None, coef, to_dev(un))
+        g = W.flat_to_layers(T.tfde_cnn_get_grads(net))
+        x, s = C.input_channels(u, None, coef[0:3], coef[3:6], coef[6:9])
+        layers = [(bf16(Wt), b.astype(np.float32).astype(np.float64)) for Wt, b in W.flat_to_layers(flat)]
+        L, ref = C.loss_and_grads(layers, bf16(x), (un - u)[None] / s)
+        assert abs(loss - L) <= 2e-2 * L
+        for k in range(4):
+            for got, want in ((g[k][0], ref[k][0]), (g[k][1], ref[k][1])):
+                assert relerr(got, want) < 6e-2
+                cos = float(np.sum(got * want) / (np.linalg.norm(got) * np.linalg.norm(want)))
+                assert cos > 0.995
+    finally:
+        T.tfde_cnn_destroy(net)
+
+
+def test_adam_step_matches_oracle(T, W):
+    """Two accumulated samples then one Adam step: the parameters move as the
+    oracle's Adam with the averaged gradient."""
+    n = (8, 8, 8)
+    flat = random_net(W, 11)
+    net = T.tfde_cnn_create(n)
+    try:
+        T.tfde_cnn_set_params(net, flat)
+        shape = tuple(reversed(n))
+        coef = [0.4, 0.5, 0.6, 1.0, 1.0, 1.0, 0.8, 0.8, 0.8]
+        for sd in (1, 2):
+            u = inp.uniform_vector(shape, 20 + sd)
+            T.tfde_cnn_accumulate(net, to_dev(u), None, coef, to_dev(1.01 * u))
+        g = T.tfde_cnn_get_grads(net).astype(np.float64) / 2.0
+        T.tfde_cnn_adam_step(net, 1e-3)
+        got = T.tfde_cnn_get_params(net).astype(np.float64)
+        want = flat.astype(np.float64).copy()
+        C.adam_step(want, g, np.zeros_like(want), np.zeros_like(want), 1, 1e-3)
+        assert np.abs(got - want).max() <= 1e-6
+        assert not T.tfde_cnn_get_grads(net).any()
+    finally:
+        T.tfde_cnn_destroy(net)
+
+
+def test_training_reduces_loss(T, W):
+    """Adam on trajectories the solver generates (n = 16) lowers the loss."""
+    import torch
+    data = W.generate_trajectories(16, [100, 101, 102], 4, 0.01, with_source=True, device="cuda")
+    net = T.tfde_cnn_create((16, 16, 16))
+    try:
+        T.tfde_cnn_set_params(net, W.init_params(0))
+        hist = W.train(net, data, 80, 4, 3e-3, 0)
+        assert np.mean(hist[-10:]) < 0.5 * np.mean(hist[:5])
+    finally:
+        T.tfde_cnn_destroy(net)
+        torch.cuda.synchronize()
+
+
+def test_advance_guess_keeps_better_start(T):
+    """tfde_cn_advance_guess: a guess no better than u^{m-1} is refused and the
+    step equals tfde_cn_advance; the converged solution as guess is taken and
+    needs (almost) no iterations."""
+    n = (24, 16, 32)
+    d, kp, km = (0.3, 0.6, 0.8), (1.0,) * 3, (0.5,) * 3
+    prm = T.make_params(n, d, kp, km, 0.02)
+    ha = T.tfde_assemble(prm, T.TFDE_MIXED)
+    hb = T.tfde_assemble(prm, T.TFDE_MIXED)
+    try:
+        u0 = inp.smoothed_uniform(tuple(reversed(n)), 2)
+        ua, ub = to_dev(u0), to_dev(u0)
+        ia = T.tfde_cn_advance(ha, ua, None, True, 1e-12)
+        worse = to_dev(u0 + 0.5)
+        ib, used = T.tfde_cn_advance_guess(hb, ub, None, worse, True, 1e-12)
+        assert not used
+        assert relerr(to_host(ub), to_host(ua)) < 1e-10
+        # next step: the exact solution as guess
+        op = o.Problem(n=n, delta=d, kp=kp, km=km, dt=0.02)
+        b = o.rhs(op, to_host(ua), None)
+        tau = o.build_tau(op)
+        xo, _ = o.gmres_left(lambda v: o.apply_A(op, v), lambda r: o.apply_Pinv(tau, r), b, to_host(ua), 1e-14,
+                             4000, restart=20, criterion="true")
+        ic, used = T.tfde_cn_advance_guess(hb, ub, None, to_dev(xo), False, 1e-10)
+        assert used and ic.iters <= 1 and ic.relres <= 1e-10
+        assert relerr(to_host(ub), xo) < 1e-9
+    finally:
+        T.tfde_destroy(ha)
+        T.tfde_destroy(hb)

@@ -295,3 +295,26 @@ def test_guess_order_rejects_bad_values(T):
             T.tfde_set_guess_order(h, 3)
     finally:
         T.tfde_destroy(h)
+
+
+@pytest.mark.parametrize("nonsym", [False, True])
+def test_six_slice_residual_is_honest(T, nonsym):
+    """At tol >= 1e-9 the refinement residual uses 6 digit slices (42 bits).
+    The residual the library reports must agree with the oracle's FP64
+    residual of the returned solution, and that residual must meet tol."""
+    n = (48, 32, 40)
+    d = (0.3, 0.6, 0.8)
+    kp, km = ((1.0,) * 3, (0.5,) * 3) if nonsym else ((1.0,) * 3, (1.0,) * 3)
+    h = T.tfde_assemble(T.make_params(n, d, kp, km, 0.05), T.TFDE_MIXED)
+    try:
+        op = o.Problem(n=n, delta=d, kp=kp, km=km, dt=0.05)
+        b = inp.uniform_vector(op.shape, 61)
+        x = to_dev(np.zeros_like(b))
+        solve = T.tfde_pgmres if nonsym else T.tfde_pcg
+        info = solve(h, to_dev(b), x, 20, 1e-8, 2000) if nonsym else solve(h, to_dev(b), x, 1e-8, 2000)
+        xr = to_host(x)
+        true_rel = np.linalg.norm(b - o.apply_A(op, xr)) / np.linalg.norm(b)
+        assert true_rel <= 1e-8
+        assert abs(true_rel - info.relres) <= 1e-11
+    finally:
+        T.tfde_destroy(h)
