@@ -35,6 +35,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+import numpy as np  # noqa: E402
+
 import tfde_inputs as inp  # noqa: E402
 
 METRIC = "CN steps/s at 3D N=256, mixed+warm-start vs plain FP64, 1e-8 rel residual"
@@ -57,6 +59,9 @@ def parse_args(argv=None):
     ap.add_argument("--batch-count", type=int, default=64,
                     help="problems of the uneven batched workload (0 skips it)")
     ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--cnn-steps", type=int, default=100,
+                    help="CN steps of the warm-start evaluation at n = 128 (0 skips training and evaluation)")
+    ap.add_argument("--cnn-train-steps", type=int, default=600, help="Adam steps of the warm-start training")
     ap.add_argument("--guess-order", type=int, default=2,
                     help="initial guess of the mixed path: 0 previous step, 1/2 polynomial extrapolation")
     return ap.parse_args(argv)
@@ -319,6 +324,11 @@ def run_ours(args):
     if args.batch_count > 0 and args.batch_steps > 0:
         batched = run_batched(T, args.batch_count, args.batch_steps, dev, stream)
 
+    # ---- learned warm start: train at n = 64, evaluate at n = 128
+    warm = None
+    if args.cnn_steps > 0 and args.cnn_train_steps > 0:
+        warm = run_warm_start(T, args.cnn_train_steps, args.cnn_steps, dev, stream)
+
     # ---- roofline of the dominant kernel (tcgen05 per-axis contraction)
     peaks = measured_peaks()
     roof = None
@@ -370,7 +380,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (each FP64 vector 134 MB, working set > 2 GB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st.kernel_launches),
-            "clocks": clocks, "fp64_path": fp64, "batched": batched,
+            "clocks": clocks, "fp64_path": fp64, "batched": batched, "warm_start": warm,
             "iters_per_step": iters / args.steps, "refine_sweeps_per_step": sweeps / args.steps,
             "max_relres": relres, "max_rel_err_vs_exact": err,
         }
@@ -378,6 +388,78 @@ def run_ours(args):
     if on:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_warm_start(T, train_steps, eval_steps, dev, stream):
+    """The learned warm start: trajectories of the solver at n = 64 (64 seeds,
+    6 steps each, random delta, k+-, dt in {0.005, 0.01, 0.02, 0.04},
+    manufactured source), Adam on mini-batches of 8 samples, then `eval_steps`
+    chained CN steps at n = 128 (delta = (0.3, 0.6, 0.8), k+ = 1, k- = 0.5,
+    dt = 0.01, f = 0, smoothed-noise u0, tol 1e-8) with the network's guess
+    (kept only when its FP64 residual beats the previous-step guess) against
+    the previous-step guess alone.  Timed with CUDA events."""
+    import torch
+
+    from paper_2511_21198_gb300 import warmstart as W
+    t0 = time.time()
+    data = W.generate_trajectories(64, list(range(100, 164)), 6, [0.005, 0.01, 0.02, 0.04], with_source=True,
+                                   stream=stream, device=dev)
+    net = T.tfde_cnn_create((64, 64, 64))
+    try:
+        T.tfde_cnn_set_params(net, W.init_params(0))
+        torch.cuda.synchronize()
+        t1 = time.time()
+        hist = W.train(net, data, train_steps, 8, 2e-3, 0, stream)
+        torch.cuda.synchronize()
+        t2 = time.time()
+        params = T.tfde_cnn_get_params(net)
+    finally:
+        T.tfde_cnn_destroy(net)
+    del data
+    n, dt = 128, 0.01
+    d, kp, km = (0.3, 0.6, 0.8), (1.0,) * 3, (0.5,) * 3
+    prm = T.make_params((n, n, n), d, kp, km, dt)
+    coef = W.coefficients(prm)
+    u0 = torch.from_numpy(inp.smoothed_uniform((n, n, n), 5)).to(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"train": {"grid": 64, "trajectories": 64, "samples": 64 * 6, "adam_steps": train_steps, "batch": 8,
+                     "loss_first10": float(np.mean(hist[:10])), "loss_last10": float(np.mean(hist[-10:])),
+                     "data_s": t1 - t0, "train_s": t2 - t1},
+           "eval": {"grid": n, "steps": eval_steps, "tol": 1e-8}}
+    ne = T.tfde_cnn_create((n, n, n))
+    T.tfde_cnn_set_params(ne, params)
+    try:
+        for mode in ("previous_step", "network"):
+            h = T.tfde_assemble(prm, T.TFDE_MIXED, stream)
+            try:
+                u = u0.clone()
+                x0 = torch.empty_like(u)
+                T.tfde_cn_advance(h, u, None, True, 1e-8, stream)     # step 1 (no guess yet)
+                its, used, r0 = 0, 0, []
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for m in range(eval_steps):
+                    if mode == "network":
+                        T.tfde_cnn_predict(ne, u, None, coef, x0, stream)
+                        info, ug = T.tfde_cn_advance_guess(h, u, None, x0, False, 1e-8, stream)
+                        used += int(ug)
+                    else:
+                        info = T.tfde_cn_advance(h, u, None, False, 1e-8, stream)
+                    its += info.iters
+                    r0.append(info.relres0)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                out["eval"][mode] = {"iters_per_step": its / eval_steps, "ms_per_step": ms / eval_steps,
+                                     "median_initial_relres": float(np.median(r0))}
+                if mode == "network":
+                    out["eval"][mode]["guess_used_steps"] = used
+                    out["eval"][mode]["fallback_steps"] = eval_steps - used
+            finally:
+                T.tfde_destroy(h)
+    finally:
+        T.tfde_cnn_destroy(ne)
+    return out
 
 
 def run_batched(T, count, steps, dev, stream):

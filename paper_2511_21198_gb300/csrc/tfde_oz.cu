@@ -120,70 +120,86 @@ __global__ void slice_x_kernel(const double* __restrict__ x0, int n1, long long 
     }
 }
 
-// y / z axes: 32 consecutive lines (contiguous in memory) x 8 warps per
-// 256-thread block, warp g taking the g-th contiguous chunk of the line; the
-// joint line maximum of x0 and x1 * 2^sh1 is reduced through shared memory.
-// When eout is set, e = A_n x1 along the line from the fixed-point integers
-// W of x1 (exact as in slice_x_kernel).
-__global__ __launch_bounds__(256) void slice_strided_kernel(const double* __restrict__ x0,
-                                                            const double* __restrict__ x1, int sh1, AxisView v, int S,
-                                                            __nv_bfloat16* __restrict__ p0,
-                                                            __nv_bfloat16* __restrict__ p1, long long N,
-                                                            int* __restrict__ lexp, double* __restrict__ eout) {
-    __shared__ unsigned long long smax[8][32];
-    __shared__ int sexp[32];
-    const int li = threadIdx.x & 31, kg = threadIdx.x >> 5;
-    const int kc = (v.n + 7) / 8;
-    const int k0 = kg * kc;
-    const int k1 = k0 + kc < v.n ? k0 + kc : v.n;
+// y / z axes: LB consecutive lines (contiguous in memory) per 512-thread
+// block.  The block's lines of both inputs are copied once into shared memory
+// (8-byte cp.async, all in flight together), the joint line maximum of x0 and
+// x1 * 2^sh1 is reduced there, and the digits are written from shared memory:
+// every input element crosses HBM once.  When eout is set, e = A_n x1 along
+// the line from the fixed-point integers W of x1 (exact as in slice_x_kernel).
+constexpr int SL_THREADS = 512;
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
+template <int LB>
+__global__ __launch_bounds__(SL_THREADS) void slice_staged_kernel(const double* __restrict__ x0,
+                                                                  const double* __restrict__ x1, int sh1, AxisView v,
+                                                                  int S, __nv_bfloat16* __restrict__ p0,
+                                                                  __nv_bfloat16* __restrict__ p1, long long N,
+                                                                  int* __restrict__ lexp, double* __restrict__ eout) {
+    constexpr int NKG = SL_THREADS / LB;
+    extern __shared__ unsigned long long sl_smem[];   // [input][k][LB]
+    __shared__ unsigned long long smax[NKG][LB];
+    __shared__ int sexp[LB];
+    unsigned long long* s0 = sl_smem;
+    unsigned long long* s1 = sl_smem + (size_t)v.n * LB;
+    const int li = threadIdx.x % LB, kg = threadIdx.x / LB;
     const long long* b0 = reinterpret_cast<const long long*>(x0);
     const long long* b1 = reinterpret_cast<const long long*>(x1);
-    for (long long l0 = (long long)blockIdx.x * 32; l0 < v.lines; l0 += (long long)gridDim.x * 32) {
+    for (long long l0 = (long long)blockIdx.x * LB; l0 < v.lines; l0 += (long long)gridDim.x * LB) {
         const long long l = l0 + li;
         const bool valid = l < v.lines;
         const long long off = valid ? (l % v.l_in) * v.s_in + (l / v.l_in) * v.s_out : 0;
+        if (valid) {
+            for (int k = kg; k < v.n; k += NKG) {
+                const long long idx = off + (long long)k * v.stride;
+                cp_async8(s0 + k * LB + li, b0 + idx);
+                if (b1) cp_async8(s1 + k * LB + li, b1 + idx);
+            }
+        }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
         unsigned long long umax = 0;
         if (valid) {
-#pragma unroll 8
-            for (int k = k0; k < k1; ++k) {
-                const long long idx = off + (long long)k * v.stride;
-                umax = max(umax, (unsigned long long)b0[idx] & 0x7FFFFFFFFFFFFFFFull);
-                if (b1) umax = max(umax, abs_bits_shifted(b1[idx], sh1));
+            for (int k = kg; k < v.n; k += NKG) {
+                umax = max(umax, s0[k * LB + li] & 0x7FFFFFFFFFFFFFFFull);
+                if (b1) umax = max(umax, abs_bits_shifted((long long)s1[k * LB + li], sh1));
             }
         }
         smax[kg][li] = umax;
         __syncthreads();
         if (kg == 0) {
             unsigned long long m = smax[0][li];
-#pragma unroll
-            for (int g = 1; g < 8; ++g) m = max(m, smax[g][li]);
+#pragma unroll 8
+            for (int g = 1; g < NKG; ++g) m = max(m, smax[g][li]);
             const int E = line_exponent_from_bits(m);
             sexp[li] = E;
             if (valid) lexp[l] = E;
         }
         __syncthreads();
-        if (valid && k0 < k1) {
-            const int E = sexp[li];
-            const int E1 = E - sh1;
-            if (b1 && eout) {
-                long long Wp = k0 > 0 ? fixed_point(b1[off + (long long)(k0 - 1) * v.stride], S, E1) : 0;
-                long long Wc = fixed_point(b1[off + (long long)k0 * v.stride], S, E1);
-#pragma unroll 4
-                for (int k = k0; k < k1; ++k) {
-                    const long long idx = off + (long long)k * v.stride;
-                    const long long Wn = k + 1 < v.n ? fixed_point(b1[idx + v.stride], S, E1) : 0;
-                    write_digits(fixed_point(b0[idx], S, E), S, p0, N, idx);
-                    write_digits(Wc, S, p1, N, idx);
-                    eout[idx] = i64_ldexp_exact(Wp + 6 * Wc + Wn, E1 - 7 * S - 3);
-                    Wp = Wc;
-                    Wc = Wn;
+        const int E = sexp[li];
+        const int E1 = E - sh1;
+        if (valid) {
+            for (int k = kg; k < v.n; k += NKG) {
+                const long long idx = off + (long long)k * v.stride;
+                write_digits(fixed_point((long long)s0[k * LB + li], S, E), S, p0, N, idx);
+                if (b1) {
+                    const long long W = fixed_point((long long)s1[k * LB + li], S, E1);
+                    write_digits(W, S, p1, N, idx);
+                    if (eout) s1[k * LB + li] = (unsigned long long)W;
                 }
-            } else {
-#pragma unroll 4
-                for (int k = k0; k < k1; ++k) {
-                    const long long idx = off + (long long)k * v.stride;
-                    write_digits(fixed_point(b0[idx], S, E), S, p0, N, idx);
-                    if (b1) write_digits(fixed_point(b1[idx], S, E1), S, p1, N, idx);
+            }
+        }
+        if (eout && b1) {
+            __syncthreads();
+            if (valid) {
+                for (int k = kg; k < v.n; k += NKG) {
+                    const long long Wp = k > 0 ? (long long)s1[(k - 1) * LB + li] : 0;
+                    const long long Wn = k + 1 < v.n ? (long long)s1[(k + 1) * LB + li] : 0;
+                    const long long W = (long long)s1[k * LB + li];
+                    eout[off + (long long)k * v.stride] = i64_ldexp_exact(Wp + 6 * W + Wn, E1 - 7 * S - 3);
                 }
             }
         }
@@ -243,6 +259,7 @@ void slice_operators_host(const std::vector<const std::vector<double>*>& ops, in
     } while (0)
 
 bool g_oz_attr = false;
+bool g_sl_attr[2] = {false, false};
 
 // Upload one operator digit set and build its tensor maps.
 int upload_set(OzSet& set, const std::vector<__nv_bfloat16>& sl, int n, int S, int na, int rexp_index,
@@ -373,11 +390,29 @@ void oz_slice(const tfde_problem* P, int axis, const double* x0, const double* x
         slice_x_kernel<<<grid_for(v.lines * 32), 256, 0, s>>>(x0, P->n[0], v.lines, S, M->oz_planes[0], N,
                                                                M->oz_lexp, mass_out);
     } else {
-        // a few blocks per SM keep the lines of both passes over the input in L2
-        long long blocks = (v.lines + 31) / 32;
-        if (blocks > 152LL * 4) blocks = 152LL * 4;
-        slice_strided_kernel<<<(unsigned)blocks, 256, 0, s>>>(x0, x1, sh1, v, S, M->oz_planes[0],
-                                                              M->oz_planes[1], N, M->oz_lexp, mass_out);
+        // 32 lines per block while both inputs fit in 200 KB of shared memory, else 16
+        const int nin = x1 ? 2 : 1;
+        const bool wide = (size_t)nin * v.n * 32 * 8 <= 200 * 1024;
+        const int LB = wide ? 32 : 16;
+        const size_t smem = (size_t)nin * v.n * LB * 8;
+        long long blocks = (v.lines + LB - 1) / LB;
+        const long long per_sm = std::max<long long>(1, (long long)(220 * 1024 / std::max<size_t>(smem, 1)));
+        if (blocks > 152LL * per_sm) blocks = 152LL * per_sm;
+        if (wide) {
+            if (!g_sl_attr[0]) {
+                cudaFuncSetAttribute(slice_staged_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                g_sl_attr[0] = true;
+            }
+            slice_staged_kernel<32><<<(unsigned)blocks, SL_THREADS, smem, s>>>(x0, x1, sh1, v, S, M->oz_planes[0],
+                                                                             M->oz_planes[1], N, M->oz_lexp, mass_out);
+        } else {
+            if (!g_sl_attr[1]) {
+                cudaFuncSetAttribute(slice_staged_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                g_sl_attr[1] = true;
+            }
+            slice_staged_kernel<16><<<(unsigned)blocks, SL_THREADS, smem, s>>>(x0, x1, sh1, v, S, M->oz_planes[0],
+                                                                             M->oz_planes[1], N, M->oz_lexp, mass_out);
+        }
     }
 }
 
