@@ -330,19 +330,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                             o[j] = i64_ldexp(p.value_sign < 0 ? -I6 : I6, es + el[j] - 7 * (D + 2));
                             continue;
                         }
-                        __int128 I = 0;
                         if (S == 7) {
+                            // I = hi 2^21 + lo needs up to 67 bits.  Below 2^62 it is formed exactly in
+                            // int64; above, floor(I / 2^8) keeps at least 54 significant bits, so the
+                            // rounded double moves by at most one ulp
                             long long av[7];
 #pragma unroll
                             for (int dd = 0; dd < 7; ++dd) av[dd] = __float2int_rn(__uint_as_float(r[dd][j]));
                             const long long hi = ((av[0] * 128 + av[1]) * 128 + av[2]) * 128 + av[3];
                             const long long lo = (av[4] * 128 + av[5]) * 128 + av[6];
-                            I = (__int128)hi * (1 << 21) + lo;
-                        } else {
-#pragma unroll
-                            for (int dd = 0; dd < MAXS; ++dd)
-                                if (dd < S) I = I * 128 + __float2int_rn(__uint_as_float(r[dd][j]));
+                            const bool big = hi >= (1LL << 40) || hi <= -(1LL << 40);
+                            const long long Iv = big ? hi * (1LL << 13) + (lo >> 8) : hi * (1LL << 21) + lo;
+                            o[j] = i64_ldexp(p.value_sign < 0 ? -Iv : Iv, es + el[j] - 7 * (D + 2) + (big ? 8 : 0));
+                            continue;
                         }
+                        __int128 I = 0;
+#pragma unroll
+                        for (int dd = 0; dd < MAXS; ++dd)
+                            if (dd < S) I = I * 128 + __float2int_rn(__uint_as_float(r[dd][j]));
                         o[j] = i128_ldexp(p.value_sign < 0 ? -I : I, es + el[j] - 7 * (D + 2));
                     }
                     if (p.b_kmajor) {
