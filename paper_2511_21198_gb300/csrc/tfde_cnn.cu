@@ -15,8 +15,9 @@
 // per tap, 27 MMAs per tile.  For each of the 9 (dz, dy) rows one TMA box of
 // 130 slots x 8 channels per channel half is staged (non-swizzled K-major:
 // the two halves are the K-adjacent core matrices); the three dx taps of a
-// row are the same staged rows shifted by 16 bytes.  Warp 0 loads, warp 1
-// issues the MMAs into a double-buffered TMEM accumulator, warps 2..5 run the
+// row are the same staged rows shifted by 16 bytes.  Warps 0..3 load (the 18
+// boxes of a tile dealt round-robin), warp 4 issues the MMAs into a
+// double-buffered TMEM accumulator, warps 5..8 run the
 // epilogue (bias, ReLU or ReLU-gradient mask, BF16 store of interior slots, or
 // the FP32 output channel on the plain grid).  Weight gradients and the small
 // element-wise steps run on CUDA cores.
@@ -50,7 +51,9 @@ constexpr int STAGES = 2;
 constexpr int W_BYTES = NTAP * 2 * CH * 16;              // 13824: [tap][khalf][co][8 ci]
 constexpr int NUM_BARS = 2 * STAGES + 5;
 constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + W_BYTES + NUM_BARS * 8 + 16;
-constexpr int NUM_THREADS = 192;   // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int PRODUCERS = 4;       // warps 0..3 issue the 18 row boxes of a tile round-robin
+constexpr int MMA_WARP = PRODUCERS;
+constexpr int NUM_THREADS = 32 * (PRODUCERS + 1 + 4);   // + MMA warp + 4 epilogue warps
 constexpr uint32_t TMEM_COLS = 32; // 2 x 16 columns
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 
@@ -102,7 +105,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_kernel(const __grid_const
     }
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full[s], 1);
+            mbar_init(&full[s], PRODUCERS);
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -112,27 +115,30 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_kernel(const __grid_const
         mbar_init(mma_done, 1);
         mbar_fence_init();
     }
-    if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
+    if (warp == MMA_WARP) tmem_alloc(tmem_slot, TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     const long long total = p.ntiles;
 
-    if (warp == 0) {
+    if (warp < PRODUCERS) {
         if (lane == 0) {
+            const int pw = warp;
             int s = 0;
             uint32_t ph = 0, filled = 0, last_ph = 0;
             for (long long t = blockIdx.x; t < total; t += gridDim.x) {
                 if (!mbar_wait(&empty[s], ph ^ 1u, p.err)) break;
                 uint8_t* st = stages + s * STAGE_BYTES;
-                mbar_expect_tx(&full[s], 18u * BOX * 16u);
+                uint32_t mine = 0;
+                for (int i = pw; i < 18; i += PRODUCERS) mine += BOX * 16u;
+                mbar_expect_tx(&full[s], mine);
                 const long long s0 = p.first + t * TM;
-                for (int r = 0; r < 9; ++r) {
+                for (int i = pw; i < 18; i += PRODUCERS) {
+                    const int r = i >> 1, h = i & 1;
                     const int dz = r / 3 - 1, dy = r % 3 - 1;
                     const long long start = s0 - 1 + dz * p.P + dy * p.R;   // >= 0 by the guard planes
-                    for (int h = 0; h < 2; ++h)
-                        tma_load_2d(st + r * ROW_BYTES + h * HALF_BYTES, &p.amap, &full[s], 8 * h, (int)start);
+                    tma_load_2d(st + r * ROW_BYTES + h * HALF_BYTES, &p.amap, &full[s], 8 * h, (int)start);
                 }
                 filled |= 1u << s;
                 if (ph) last_ph |= 1u << s; else last_ph &= ~(1u << s);
@@ -141,7 +147,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_kernel(const __grid_const
             for (int i = 0; i < STAGES; ++i)
                 if (filled & (1u << i)) mbar_wait(&full[i], (last_ph >> i) & 1u, p.err, false);
         }
-    } else if (warp == 1) {
+    } else if (warp == MMA_WARP) {
         if (lane == 0) {
             const uint32_t idesc = instr_desc(TM, CH, 0);
             // non-swizzled K-major: LBO = K-adjacent core matrix (channel half), SBO = next 8 rows
@@ -233,7 +239,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_kernel(const __grid_const
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 1) tmem_dealloc(tmem_base, TMEM_COLS);
+    if (warp == MMA_WARP) tmem_dealloc(tmem_base, TMEM_COLS);
 }
 
 // ------------------------------------------------------------ CUDA-core kernels

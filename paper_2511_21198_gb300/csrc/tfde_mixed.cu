@@ -61,22 +61,39 @@ void gemm_params(const tfde_problem* P, int axis, const SegSpec* segs, int nseg,
     MixedState* M = mixed(P);
     std::memset(&prm, 0, sizeof(prm));
     tc::set_geometry(prm, P->n, axis);
+    // tensor maps: merged boxes where the allocation allows one copy per operand
+    // (hi/lo operator pair; hi/lo plane pair with, on y/z, all line blocks)
     int na = 0, nb = 0;
     for (int g = 0; g < nseg; ++g) {
         tc::Segment& S = prm.seg[g];
         S.nkb = (P->n[axis] + tc::BK - 1) / tc::BK;
-        prm.amaps[na] = M->amap[segs[g].a_hi];
-        S.amap[0] = na++;
-        S.na = 1;
-        if (segs[g].a_lo >= 0) {
-            prm.amaps[na] = M->amap[segs[g].a_lo];
-            S.amap[1] = na++;
+        S.amap2 = -1;
+        S.bmap2 = -1;
+        if (segs[g].a_lo >= 0 && M->has_amap2[segs[g].a_hi]) {
+            prm.amaps[na] = M->amap2[segs[g].a_hi];
+            S.amap2 = na++;
             S.na = 2;
+        } else {
+            prm.amaps[na] = M->amap[segs[g].a_hi];
+            S.amap[0] = na++;
+            S.na = 1;
+            if (segs[g].a_lo >= 0) {
+                prm.amaps[na] = M->amap[segs[g].a_lo];
+                S.amap[1] = na++;
+                S.na = 2;
+            }
         }
-        prm.bmaps[nb] = M->bmap_hi[segs[g].plane][axis];
-        S.bmap[0] = nb++;
-        prm.bmaps[nb] = M->bmap_lo[segs[g].plane][axis];
-        S.bmap[1] = nb++;
+        const int rank = M->bmap2_rank[segs[g].plane][axis];
+        if (rank > 0) {
+            prm.bmaps[nb] = M->bmap2[segs[g].plane][axis];
+            S.bmap2 = nb++;
+            prm.b_rank = rank;
+        } else {
+            prm.bmaps[nb] = M->bmap_hi[segs[g].plane][axis];
+            S.bmap[0] = nb++;
+            prm.bmaps[nb] = M->bmap_lo[segs[g].plane][axis];
+            S.bmap[1] = nb++;
+        }
         S.nb = 2;
         S.npair = 0;
         S.pa[S.npair] = 0; S.pb[S.npair++] = 0;   // A_hi * x_hi
@@ -437,11 +454,28 @@ int mixed_init(tfde_problem* P, cudaStream_t s) {
                     h[(size_t)i * n + j] = lo ? vl : vh;
                 }
         }
-        MX_TRY(cudaMalloc((void**)&M->mat[om], h.size() * sizeof(__nv_bfloat16)));
+        const bool pair_hi = om == OM_GHAT_H || om == OM_GHATR_H || om == OM_GY_H || om == OM_GYN_H || om == OM_GZ_H ||
+                             om == OM_GZN_H;
+        const bool pair_lo = om == OM_GHAT_L || om == OM_GHATR_L || om == OM_GY_L || om == OM_GYN_L || om == OM_GZ_L ||
+                             om == OM_GZN_L;
+        if (pair_lo) {
+            M->mat[om] = M->mat[om - 1] + h.size();   // second half of the pair's allocation
+        } else {
+            MX_TRY(cudaMalloc((void**)&M->mat[om], (pair_hi ? 2 : 1) * h.size() * sizeof(__nv_bfloat16)));
+            M->own_mat[om] = true;
+        }
         MX_TRY(cudaMemcpyAsync(M->mat[om], h.data(), h.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, s));
         MX_TRY(cudaStreamSynchronize(s));
         int st = tc::make_map_A(&M->amap[om], M->mat[om], n);
         if (st) return st;
+        if (pair_hi) {
+            // hi and lo of the pair as one 3-D tensor (k, row, term)
+            const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, 2};
+            const cuuint64_t strides[2] = {(cuuint64_t)n * 2, (cuuint64_t)n * n * 2};
+            const cuuint32_t box[3] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM, 2};
+            M->has_amap2[om] = tc::encode_map(&M->amap2[om], M->mat[om], 3, dims, strides, box,
+                                              CU_TENSOR_MAP_SWIZZLE_64B) == TFDE_OK;
+        }
     }
     {
         std::vector<double> etaB[3];
@@ -451,14 +485,14 @@ int mixed_init(tfde_problem* P, cudaStream_t s) {
     }
     // workspace planes and their tensor maps
     for (int pl = 0; pl < NPL; ++pl) {
-        MX_TRY(cudaMalloc((void**)&M->hi[pl], N * sizeof(__nv_bfloat16)));
-        MX_TRY(cudaMalloc((void**)&M->lo[pl], N * sizeof(__nv_bfloat16)));
-        MX_TRY(cudaMemsetAsync(M->hi[pl], 0, N * sizeof(__nv_bfloat16), s));
-        MX_TRY(cudaMemsetAsync(M->lo[pl], 0, N * sizeof(__nv_bfloat16), s));
+        MX_TRY(cudaMalloc((void**)&M->hi[pl], 2 * N * sizeof(__nv_bfloat16)));
+        M->lo[pl] = M->hi[pl] + N;
+        MX_TRY(cudaMemsetAsync(M->hi[pl], 0, 2 * N * sizeof(__nv_bfloat16), s));
         for (int a = 0; a < 3; ++a) {
             int st = tc::make_map_B(&M->bmap_hi[pl][a], M->hi[pl], P->n, a);
             if (!st) st = tc::make_map_B(&M->bmap_lo[pl][a], M->lo[pl], P->n, a);
             if (st) return st;
+            M->bmap2_rank[pl][a] = tc::make_map_B_pair(&M->bmap2[pl][a], M->hi[pl], P->n, a);
         }
     }
     for (int v = 0; v < NF; ++v) {
@@ -496,11 +530,9 @@ int mixed_init(tfde_problem* P, cudaStream_t s) {
 void mixed_free(tfde_problem* P) {
     MixedState* M = mixed(P);
     if (!M) return;
-    for (auto& m : M->mat) cudaFree(m);
-    for (int pl = 0; pl < NPL; ++pl) {
-        cudaFree(M->hi[pl]);
-        cudaFree(M->lo[pl]);
-    }
+    for (int om = 0; om < NOM; ++om)
+        if (M->own_mat[om]) cudaFree(M->mat[om]);
+    for (int pl = 0; pl < NPL; ++pl) cudaFree(M->hi[pl]);   // lo lives in the same allocation
     for (auto& v : M->f) cudaFree(v);
     cudaFree(M->V32);
     cudaFree(M->gm);

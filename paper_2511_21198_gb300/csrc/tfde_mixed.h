@@ -55,17 +55,24 @@ constexpr int OZ_SLICES = 7;
 struct OzSet {
     __nv_bfloat16* dev = nullptr;
     CUtensorMap amap[OZ_SLICES];
+    CUtensorMap amapk[OZ_SLICES];   // leading k + 1 slices in one box {32, 128, k + 1}
+    bool amapk_ok[OZ_SLICES] = {};
     int na = 0;          // leading slices that are not all zero
     int rexp_index = 0;  // row exponents in MixedState::oz_rexp
 };
 
 struct MixedState {
-    __nv_bfloat16* mat[NOM] = {};
+    __nv_bfloat16* mat[NOM] = {};   // hi/lo pairs share one allocation (lo = hi + n^2)
+    bool own_mat[NOM] = {};
     CUtensorMap amap[NOM];
-    __nv_bfloat16* hi[NPL] = {};
+    CUtensorMap amap2[NOM];          // for the hi of a pair: one 3-D box {32, 128, 2} loads hi and lo
+    bool has_amap2[NOM] = {};
+    __nv_bfloat16* hi[NPL] = {};   // one allocation per plane pair: lo = hi + N
     __nv_bfloat16* lo[NPL] = {};
     CUtensorMap bmap_hi[NPL][3];
     CUtensorMap bmap_lo[NPL][3];
+    CUtensorMap bmap2[NPL][3];     // both planes (and on y/z all four 64-line blocks) in one box
+    int bmap2_rank[NPL][3] = {};   // 3 (x), 5 (y/z), 0 = not available
     float* f[NF] = {};
     float* lam = nullptr;   // [ra (n3) | rb (n3) | U (n1 n2) | V (n1 n2)]
     double* dsc = nullptr;  // device scalars
@@ -85,6 +92,8 @@ struct MixedState {
     std::vector<int*> oz_rexp;                               // row exponent arrays
     __nv_bfloat16* oz_planes[2] = {nullptr, nullptr};        // digit planes of two inputs
     CUtensorMap oz_bmap[2][OZ_SLICES][3];
+    CUtensorMap oz_bmapm[2][3][OZ_SLICES];                   // leading k + 1 slices of an input in one box
+    bool oz_bmapm_ok[2][3][OZ_SLICES] = {};
     int* oz_lexp = nullptr;                                  // joint line exponents
     int oz_shift[3] = {0, 0, 0};                             // exponent shift of the second input
 };

@@ -271,6 +271,12 @@ int upload_set(OzSet& set, const std::vector<__nv_bfloat16>& sl, int n, int S, i
     for (int t = 0; t < S; ++t) {
         int st = tc::make_map_A(&set.amap[t], set.dev + (size_t)t * n * n, n);
         if (st) return st;
+        // slices 0..t as one 3-D tensor (k, row, slice)
+        const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)S};
+        const cuuint64_t strides[2] = {(cuuint64_t)n * 2, (cuuint64_t)n * n * 2};
+        const cuuint32_t box[3] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM, (cuuint32_t)(t + 1)};
+        // a merged map the driver refuses leaves the per-slice copies in use
+        set.amapk_ok[t] = tc::encode_map(&set.amapk[t], set.dev, 3, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B) == TFDE_OK;
     }
     return TFDE_OK;
 }
@@ -355,6 +361,29 @@ int oz_init(tfde_problem* P, const std::vector<double> etaB[3], cudaStream_t s) 
                 st = (a == 0) ? tc::make_map_B_box(&M->oz_bmap[in][t][a], base, P->n, a, oz::BN)
                               : tc::make_map_B(&M->oz_bmap[in][t][a], base, P->n, a);
                 if (st) return st;
+                // slices 0..t of input `in` along axis a in one box
+                const cuuint64_t n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
+                int es;
+                if (a == 0) {
+                    const cuuint64_t dims[3] = {n1, n2 * n3, (cuuint64_t)S};
+                    const cuuint64_t strides[2] = {n1 * 2, (cuuint64_t)N * 2};
+                    const cuuint32_t box[3] = {(cuuint32_t)tc::BK, (cuuint32_t)oz::BN, (cuuint32_t)(t + 1)};
+                    es = tc::encode_map(&M->oz_bmapm[in][a][t], M->oz_planes[in], 3, dims, strides, box,
+                                        CU_TENSOR_MAP_SWIZZLE_64B);
+                } else if (a == 1) {
+                    const cuuint64_t dims[4] = {n1, n2, n3, (cuuint64_t)S};
+                    const cuuint64_t strides[3] = {n1 * 2, n1 * n2 * 2, (cuuint64_t)N * 2};
+                    const cuuint32_t box[4] = {64, (cuuint32_t)tc::BK, 1, (cuuint32_t)(t + 1)};
+                    es = tc::encode_map(&M->oz_bmapm[in][a][t], M->oz_planes[in], 4, dims, strides, box,
+                                        CU_TENSOR_MAP_SWIZZLE_128B);
+                } else {
+                    const cuuint64_t dims[3] = {n1 * n2, n3, (cuuint64_t)S};
+                    const cuuint64_t strides[2] = {n1 * n2 * 2, (cuuint64_t)N * 2};
+                    const cuuint32_t box[3] = {64, (cuuint32_t)tc::BK, (cuuint32_t)(t + 1)};
+                    es = tc::encode_map(&M->oz_bmapm[in][a][t], M->oz_planes[in], 3, dims, strides, box,
+                                        CU_TENSOR_MAP_SWIZZLE_128B);
+                }
+                M->oz_bmapm_ok[in][a][t] = es == TFDE_OK;
             }
     }
     long long maxlines = 0;
@@ -433,6 +462,9 @@ int oz_contract(const tfde_problem* P, int axis, const OzSegSpec* segs, int nseg
         oz::Segment& G = prm.seg[g];
         G.na = std::min(segs[g].op->na, S);
         G.nb = S;
+        G.merged = segs[g].op->amapk_ok[G.na - 1] && M->oz_bmapm_ok[segs[g].input][axis][S - 1] ? 1 : 0;
+        G.amapm = segs[g].op->amapk[G.na - 1];
+        G.bmapm = M->oz_bmapm[segs[g].input][axis][S - 1];
         for (int t = 0; t < S; ++t) {
             G.amaps[t] = segs[g].op->amap[t];
             G.bmaps[t] = M->oz_bmap[segs[g].input][t][axis];
@@ -451,8 +483,8 @@ int oz_contract(const tfde_problem* P, int axis, const OzSegSpec* segs, int nseg
         prm.ntiles = (prm.lines + oz::BN - 1) / oz::BN;
     } else {
         prm.b_kmajor = 0;
-        if (axis == 1) { prm.C = (int)n1; prm.P = (int)n3; }
-        else { prm.C = (int)(n1 * n2); prm.P = 1; }
+        if (axis == 1) { prm.C = (int)n1; prm.P = (int)n3; prm.bm_rank = 4; }
+        else { prm.C = (int)(n1 * n2); prm.P = 1; prm.bm_rank = 3; }
         prm.nbc = (prm.C + 63) / 64;
         prm.nblocks = (long long)prm.nbc * prm.P;
         prm.ntiles = prm.nblocks;

@@ -16,9 +16,10 @@
 // absolute error is about 2^{-7(D+1)} times the row maximum times the line
 // maximum.
 //
-// One CTA per SM, persistent over tiles of 128 rows x 64 lines; warp 0 TMA,
-// warp 1 TMEM allocation + MMA issue (M=128, N=64, K=16), warps 2..9 epilogue
-// (two per TMEM lane quadrant, 32 columns each).  Bounded waits as in the
+// One CTA per SM, persistent over tiles of 128 rows x 64 lines; warps 0..3
+// TMA (the boxes of a stage dealt round-robin to four issuing threads), warp 4
+// TMEM allocation + MMA issue (M=128, N=64, K=16), warps 5..12 epilogue (two
+// per TMEM lane quadrant, 32 columns each).  Bounded waits as in the
 // split-BF16 kernel.
 #pragma once
 
@@ -39,7 +40,10 @@ constexpr int A_TILE_BYTES = BM * BK * 2;                        // 8 KB
 constexpr int B_TILE_BYTES = BN * BK * 2;                        // 4 KB
 constexpr int STAGE_BYTES = MAXS * (A_TILE_BYTES + B_TILE_BYTES);  // 84 KB
 constexpr int EPI_WARPS = 8;
-constexpr int NUM_THREADS = 64 + 32 * EPI_WARPS;                   // 320
+constexpr int PRODUCERS = 4;                                     // TMA issuing warps (boxes dealt round-robin)
+constexpr int MMA_WARP = PRODUCERS;
+constexpr int EPI_WARP0 = PRODUCERS + 1;
+constexpr int NUM_THREADS = 32 * (PRODUCERS + 1 + EPI_WARPS);     // 416
 constexpr int NUM_BARS = 2 * STAGES + 3;
 constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + NUM_BARS * 8 + 16;
 constexpr uint32_t TMEM_COLS = 512;                              // (D + 1) x 64 <= 448 columns used
@@ -50,6 +54,9 @@ struct Segment {
     int nb;                    // input digit slices (= D + 1)
     CUtensorMap amaps[MAXS];   // operator slices: BF16 [n][n], K-major, box {32, 128}, 64B swizzle
     CUtensorMap bmaps[MAXS];   // input slices: x axis box {32, 64} (64B swizzle); y/z {64, 32, 1} (128B)
+    CUtensorMap amapm;         // all na operator slices in one box {32, 128, na} (slices stored contiguously)
+    CUtensorMap bmapm;         // all nb input slices in one box: x {32, 64, nb}; y/z {64, 32, 1, nb}
+    int merged;                // 1: amapm / bmapm are valid, one copy each per stage
 };
 
 struct Params {
@@ -57,6 +64,7 @@ struct Params {
     int nseg;
     int nslices;               // D + 1
     int b_kmajor;
+    int bm_rank;               // rank of the merged input map on y / z (4: y, 3: z)
     int mhalves;
     int n;
     long long lines;
@@ -175,7 +183,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full[s], 1);
+            mbar_init(&full[s], PRODUCERS);
             mbar_init(&empty[s], 1);
         }
         mbar_init(tfull, 1);
@@ -183,15 +191,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
         mbar_init(mma_done, 1);
         mbar_fence_init();
     }
-    if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
+    if (warp == MMA_WARP) tmem_alloc(tmem_slot, TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     const long long total = p.ntiles * p.mhalves;
 
-    if (warp == 0) {
+    if (warp < PRODUCERS) {
         if (lane == 0) {
+            const int pw = warp;
             int s = 0;
             uint32_t ph = 0, filled = 0, last_ph = 0;
             bool ok = true;
@@ -203,10 +212,40 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                     for (int kb = 0; kb < nkb; ++kb) {
                         if (!mbar_wait(&empty[s], ph ^ 1u, p.err)) { ok = false; break; }
                         uint8_t* st = stages + s * STAGE_BYTES;
-                        mbar_expect_tx(&full[s], (uint32_t)(G.na * A_TILE_BYTES + G.nb * B_TILE_BYTES));
-                        for (int a = 0; a < G.na; ++a)
-                            tma_load_2d(st + a * A_TILE_BYTES, &G.amaps[a], &full[s], kb * BK, mh * BM);
-                        for (int b = 0; b < G.nb; ++b) {
+                        // box i of this stage (operator slices, then input slices) belongs to issuer i % PRODUCERS
+                        uint32_t mine = 0;
+                        if (G.merged) {
+                            // two copies per stage: all operator slices, all input slices
+                            if (pw == 0) mine = (uint32_t)(G.na * A_TILE_BYTES);
+                            if (pw == 1 % PRODUCERS) mine += (uint32_t)(G.nb * B_TILE_BYTES);
+                            mbar_expect_tx(&full[s], mine);
+                            if (pw == 0) tma_load_3d(st, &G.amapm, &full[s], kb * BK, mh * BM, 0);
+                            if (pw == 1 % PRODUCERS) {
+                                uint8_t* dst = st + MAXS * A_TILE_BYTES;
+                                if (p.b_kmajor) {
+                                    tma_load_3d(dst, &G.bmapm, &full[s], kb * BK, (int)(tile * BN), 0);
+                                } else if (p.bm_rank == 4) {
+                                    const int pl = (int)(tile / p.nbc);
+                                    const int c0 = (int)(tile % p.nbc) * 64;
+                                    tma_load_4d(dst, &G.bmapm, &full[s], c0, kb * BK, pl, 0);
+                                } else {
+                                    tma_load_3d(dst, &G.bmapm, &full[s], (int)(tile % p.nbc) * 64, kb * BK, 0);
+                                }
+                            }
+                            filled |= 1u << s;
+                            if (ph) last_ph |= 1u << s; else last_ph &= ~(1u << s);
+                            if (++s == STAGES) { s = 0; ph ^= 1u; }
+                            continue;
+                        }
+                        for (int i = pw; i < G.na + G.nb; i += PRODUCERS)
+                            mine += i < G.na ? (uint32_t)A_TILE_BYTES : (uint32_t)B_TILE_BYTES;
+                        mbar_expect_tx(&full[s], mine);
+                        for (int i = pw; i < G.na + G.nb; i += PRODUCERS) {
+                            if (i < G.na) {
+                                tma_load_2d(st + i * A_TILE_BYTES, &G.amaps[i], &full[s], kb * BK, mh * BM);
+                                continue;
+                            }
+                            const int b = i - G.na;
                             uint8_t* dst = st + MAXS * A_TILE_BYTES + b * B_TILE_BYTES;
                             if (p.b_kmajor) {
                                 tma_load_2d(dst, &G.bmaps[b], &full[s], kb * BK, (int)(tile * BN));
@@ -225,7 +264,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
             for (int i = 0; i < STAGES; ++i)
                 if (filled & (1u << i)) mbar_wait(&full[i], (last_ph >> i) & 1u, p.err, false);
         }
-    } else if (warp == 1) {
+    } else if (warp == MMA_WARP) {
         if (lane == 0) {
             const uint32_t idesc = instr_desc(BM, BN, p.b_kmajor ? 0 : 1);
             // descriptor templates at stage 0, tile 0; the start-address field
@@ -277,7 +316,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
         }
     } else {
         const int q = warp & 3;                 // TMEM lane quadrant
-        const int half = (warp - 2) >> 2;       // columns [32 half, 32 half + 32)
+        const int half = (warp - EPI_WARP0) >> 2;   // columns [32 half, 32 half + 32)
         long long it = 0;
         float nacc = 0.f;                       // this thread's share of the output norm
         for (long long t = blockIdx.x; t < total; t += gridDim.x, ++it) {
@@ -402,7 +441,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 1) tmem_dealloc(tmem_base, TMEM_COLS);
+    if (warp == MMA_WARP) tmem_dealloc(tmem_base, TMEM_COLS);
 }
 
 #endif  // TFDE_OZ_KERNEL_IMPL

@@ -31,7 +31,7 @@ int encode(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims, c
            const cuuint32_t* box, CUtensorMapSwizzle sw) {
     auto fn = encode_fn();
     if (!fn) return set_error(TFDE_ECUDA, "cuTensorMapEncodeTiled is unavailable");
-    cuuint32_t es[3] = {1, 1, 1};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};   // element strides, one per dimension (rank <= 5)
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), dims, strides,
                     box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -94,6 +94,34 @@ int make_map_B_box(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], in
     const cuuint64_t strides[1] = {(cuuint64_t)n[0] * 2};
     const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_lines};
     return encode(m, base, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B);
+}
+
+// Both planes of a split pair (hi at base, lo at base + N) along `axis` as one
+// tensor: x axis 3-D (k, line, plane) with box {BK, BN, 2}; y / z axes, when the
+// contiguous line extent C is a multiple of BN, 5-D (line in block, k, block,
+// outer plane, hi/lo) with box {64, BK, BN / 64, 1, 2}, so that a single copy
+// fills the whole B stage in the layout of the per-plane boxes.  Returns the
+// rank, or 0 when no merged map applies.
+int make_map_B_pair(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis) {
+    const cuuint64_t n1 = n[0], n2 = n[1], n3 = n[2], N = n1 * n2 * n3;
+    if (axis == 0) {
+        const cuuint64_t dims[3] = {n1, n2 * n3, 2};
+        const cuuint64_t strides[2] = {n1 * 2, N * 2};
+        const cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)BN, 2};
+        return encode(m, base, 3, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B) == TFDE_OK ? 3 : 0;
+    }
+    cuuint64_t C, K, P;
+    if (axis == 1) { C = n1; K = n2; P = n3; }
+    else { C = n1 * n2; K = n3; P = 1; }
+    if (C % BN != 0) return 0;
+    const cuuint64_t dims[5] = {64, K, C / 64, P, 2};
+    const cuuint64_t strides[4] = {C * 2, 128, C * K * 2, N * 2};
+    const cuuint32_t box[5] = {64, (cuuint32_t)BK, (cuuint32_t)(BN / 64), 1, 2};
+    if (encode(m, base, 5, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != TFDE_OK) {
+        set_error(TFDE_OK, "");
+        return 0;
+    }
+    return 5;
 }
 
 // Fill the geometry fields of Params for a contraction along `axis`.

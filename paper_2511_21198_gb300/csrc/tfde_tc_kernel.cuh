@@ -10,12 +10,16 @@
 // dimension.
 //
 // Design (one CTA per SM, persistent over tiles of 128 rows x 256 lines):
-//   warp 0      TMA producer: A tiles [128 x 32] (K-major, 64B swizzle) and
+//   warps 0..3  TMA producers: A tiles [128 x 32] (K-major, 64B swizzle) and
 //               B tiles [32 x 256] (x axis: K-major 64B swizzle; y/z axes:
-//               MN-major 128B swizzle, 4 boxes of 64 lines) into a 4-stage ring
-//   warp 1      allocates TMEM (2 x 256 FP32 columns) and issues tcgen05.mma
+//               MN-major 128B swizzle, 4 boxes of 64 lines) into a 4-stage ring;
+//               the boxes of a stage are dealt round-robin to the four issuing
+//               threads (a thread issues one tensor copy at a time, so the copy
+//               rate grows with the number of issuers), each of which arrives
+//               on the stage barrier with its own byte count
+//   warp 4      allocates TMEM (2 x 256 FP32 columns) and issues tcgen05.mma
 //               (M=128, N=256, K=16, BF16 in, FP32 accumulate) from one thread
-//   warps 2..9  epilogue, two warps per TMEM lane quadrant (one per half of the
+//   warps 5..12 epilogue, two warps per TMEM lane quadrant (one per half of the
 //               256 columns): tcgen05.ld, scale, optional Lambda^{-1}, transpose
 //               through shared memory, 8- or 16-byte coalesced stores of FP32 or
 //               split BF16 (hi, lo) output
@@ -43,7 +47,10 @@ constexpr int A_TILE_BYTES = BM * BK * 2;                                  // 8 
 constexpr int B_TILE_BYTES = BN * BK * 2;                                  // 16 KB
 constexpr int STAGE_BYTES = MAXA * A_TILE_BYTES + MAXB * B_TILE_BYTES;     // 48 KB
 constexpr int EPI_WARPS = 8;
-constexpr int NUM_THREADS = 64 + 32 * EPI_WARPS;                           // 320
+constexpr int PRODUCERS = 4;           // TMA issuing warps: one box per thread is issued at a time,
+constexpr int MMA_WARP = PRODUCERS;    // so several issuers keep more copies in flight
+constexpr int EPI_WARP0 = PRODUCERS + 1;
+constexpr int NUM_THREADS = 32 * (PRODUCERS + 1 + EPI_WARPS);             // 416
 constexpr int EPI_STRIDE = 33;
 constexpr int EPI_FLOATS = EPI_WARPS * 32 * EPI_STRIDE;
 constexpr int NUM_BARS = 2 * STAGES + 5;
@@ -54,7 +61,9 @@ static_assert(SMEM_BYTES <= 232448, "shared memory budget of one CTA");
 struct Segment {
     int nkb;                     // k-blocks of BK in this segment
     int na, nb;                  // A / B terms loaded per stage
-    int amap[MAXA], bmap[MAXB];  // tensor-map indices
+    int amap[MAXA], bmap[MAXB];  // tensor-map indices, one box per term
+    int amap2;                   // >= 0: one 3-D box {BK, BM, na} loads all A terms (stored contiguously)
+    int bmap2;                   // >= 0: one box loads both B planes (and, on y/z, all BN/64 line blocks)
     int npair;
     int pa[MAXPAIR], pb[MAXPAIR];
 };
@@ -67,6 +76,7 @@ struct Params {
     Segment seg[MAXSEG];
     int nseg;
     int b_kmajor;        // 1: B stored with k contiguous (x axis); 0: lines contiguous (y, z axes)
+    int b_rank;          // rank of the bmap2 box: 3 (x axis), 5 (y/z axes: blocks, plane, hi/lo)
     int mhalves;         // ceil(n / 128)
     int n;               // valid rows along the axis
     long long lines;     // valid lines (K-major case)
@@ -163,7 +173,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full[s], 1);
+            mbar_init(&full[s], PRODUCERS);
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -173,7 +183,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         mbar_init(mma_done, 1);
         mbar_fence_init();
     }
-    if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
+    if (warp == MMA_WARP) tmem_alloc(tmem_slot, TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -183,9 +193,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     int* const err = p0.err;
     const int b_kmajor = p0.b_kmajor;
 
-    if (warp == 0) {
+    if (warp < PRODUCERS) {
         if (lane == 0) {
-            // ------------------------------------------------ TMA producer
+            // ------------------------------------------------ TMA producers
+            const int pw = warp;
             int s = 0;
             uint32_t ph = 0;
             uint32_t filled = 0, last_ph = 0;  // per-stage bitmasks
@@ -207,21 +218,46 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     for (int kb = 0; kb < S.nkb; ++kb) {
                         if (!mbar_wait(&empty[s], ph ^ 1u, err)) { ok = false; break; }
                         uint8_t* st = stages + s * STAGE_BYTES;
-                        mbar_expect_tx(&full[s], (uint32_t)(S.na * A_TILE_BYTES + S.nb * B_TILE_BYTES));
-                        for (int a = 0; a < S.na; ++a)
-                            tma_load_2d(st + a * A_TILE_BYTES, &p.amaps[S.amap[a]], &full[s], kb * BK, mh * BM);
-                        for (int b = 0; b < S.nb; ++b) {
+                        // boxes of this stage in a fixed order; box i belongs to issuer i % PRODUCERS
+                        // merged boxes: one copy for all A terms and one for both B planes
+                        const int na_box = S.amap2 >= 0 ? 1 : S.na;
+                        const uint32_t abytes = S.amap2 >= 0 ? (uint32_t)(S.na * A_TILE_BYTES) : (uint32_t)A_TILE_BYTES;
+                        const int bbox = S.bmap2 >= 0 ? 1 : (b_kmajor ? 1 : BN / 64);
+                        const int nb_box = S.bmap2 >= 0 ? 1 : S.nb * bbox;
+                        const uint32_t bbytes = S.bmap2 >= 0 ? (uint32_t)(S.nb * B_TILE_BYTES)
+                                                             : (b_kmajor ? (uint32_t)B_TILE_BYTES : (uint32_t)(64 * BK * 2));
+                        uint32_t mine = 0;
+                        for (int i = pw; i < na_box + nb_box; i += PRODUCERS) mine += i < na_box ? abytes : bbytes;
+                        mbar_expect_tx(&full[s], mine);
+                        for (int i = pw; i < na_box + nb_box; i += PRODUCERS) {
+                            if (i < na_box) {
+                                if (S.amap2 >= 0)
+                                    tma_load_3d(st, &p.amaps[S.amap2], &full[s], kb * BK, mh * BM, 0);
+                                else
+                                    tma_load_2d(st + i * A_TILE_BYTES, &p.amaps[S.amap[i]], &full[s], kb * BK, mh * BM);
+                                continue;
+                            }
+                            if (S.bmap2 >= 0) {
+                                uint8_t* dstb = st + MAXA * A_TILE_BYTES;
+                                if (p.b_rank == 3) {
+                                    tma_load_3d(dstb, &p.bmaps[S.bmap2], &full[s], kb * BK, (int)(tile * BN), 0);
+                                } else {
+                                    const long long gb = tile * (BN / 64);
+                                    tma_load_5d(dstb, &p.bmaps[S.bmap2], &full[s], 0, kb * BK, (int)(gb % p.nbc),
+                                                (int)(gb / p.nbc), 0);
+                                }
+                                continue;
+                            }
+                            const int jb = i - na_box;   // B box index in the per-plane enumeration
+                            const int b = jb / bbox, blk = jb % bbox;
                             uint8_t* dst = st + MAXA * A_TILE_BYTES + b * B_TILE_BYTES;
                             if (b_kmajor) {
                                 tma_load_2d(dst, &p.bmaps[S.bmap[b]], &full[s], kb * BK, (int)(tile * BN));
                             } else {
-                                for (int blk = 0; blk < BN / 64; ++blk) {
-                                    const long long gb = tile * (BN / 64) + blk;
-                                    const int pl = (int)(gb / p.nbc);
-                                    const int c0 = (int)(gb % p.nbc) * 64;
-                                    tma_load_3d(dst + blk * (64 * BK * 2), &p.bmaps[S.bmap[b]], &full[s], c0,
-                                                kb * BK, pl);
-                                }
+                                const long long gb = tile * (BN / 64) + blk;
+                                const int pl = (int)(gb / p.nbc);
+                                const int c0 = (int)(gb % p.nbc) * 64;
+                                tma_load_3d(dst + blk * (64 * BK * 2), &p.bmaps[S.bmap[b]], &full[s], c0, kb * BK, pl);
                             }
                         }
                         filled |= 1u << s;
@@ -234,7 +270,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             for (int i = 0; i < STAGES; ++i)
                 if (filled & (1u << i)) mbar_wait(&full[i], (last_ph >> i) & 1u, err, false);
         }
-    } else if (warp == 1) {
+    } else if (warp == MMA_WARP) {
         if (lane == 0) {
             // ------------------------------------------------ MMA issuer
             const uint32_t idesc = instr_desc(BM, BN, b_kmajor ? 0 : 1);
@@ -293,8 +329,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     } else {
         // ---------------------------------------------------- epilogue warps
         const int q = warp & 3;               // TMEM lane quadrant this warp may access
-        const int half = (warp - 2) >> 2;     // which 128 of the 256 columns
-        float* stg = epi + (warp - 2) * 32 * EPI_STRIDE;
+        const int half = (warp - EPI_WARP0) >> 2;   // which 128 of the 256 columns
+        float* stg = epi + (warp - EPI_WARP0) * 32 * EPI_STRIDE;
         const int rsub = lane >> 3;           // transposed phase: 4 rows / columns per instruction
         const int cq = (lane & 7) * 4;        // ... and 4 consecutive elements per lane
         long long it = 0;
@@ -400,7 +436,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 1) tmem_dealloc(tmem_base, TMEM_COLS);
+    if (warp == MMA_WARP) tmem_dealloc(tmem_base, TMEM_COLS);
 }
 
 #endif  // TFDE_TC_KERNEL_IMPL
