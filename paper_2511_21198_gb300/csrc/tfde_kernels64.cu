@@ -244,23 +244,44 @@ __global__ void reduce_finish_kernel(const double* __restrict__ part, int nblk, 
     if (threadIdx.x == 0) out[j] = acc;
 }
 
+// F = cP Pz Py Px + cS (Pz Py Sx + Pz Sy Px + Sz Py Px), regrouped per line as
+// F = a_jk X1_i + b_jk X2_i with a = Pz Py, b = cS (Pz Sy + Sz Py),
+// X1 = cP Px + cS Sx, X2 = Px: the per-line and per-column factors are formed
+// once per block in shared memory, so each grid point costs one multiply and
+// one fused multiply-add in FP64.  A block covers SRC_LINES lines (j, k).
+constexpr int SRC_LINES = 8;
 __global__ void source_assemble_f64_kernel(const double* __restrict__ oned, int n1, int n2, int n3,
                                            double cP, double cS, double* __restrict__ F) {
-    const long long N = (long long)n1 * n2 * n3;
+    extern __shared__ double src_sm[];    // X1[n1], X2[n1], a[SRC_LINES], b[SRC_LINES]
+    double* X1 = src_sm;
+    double* X2 = X1 + n1;
+    double* la = X2 + n1;
+    double* lb = la + SRC_LINES;
     const double* Px = oned;
     const double* Py = Px + n1;
     const double* Pz = Py + n2;
     const double* Sx = Pz + n3;
     const double* Sy = Sx + n1;
     const double* Sz = Sy + n2;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(idx % n1);
-        const int j = (int)((idx / n1) % n2);
-        const int k = (int)(idx / ((long long)n1 * n2));
-        const double ppp = Pz[k] * Py[j] * Px[i];
-        const double spp = Pz[k] * Py[j] * Sx[i] + Pz[k] * Sy[j] * Px[i] + Sz[k] * Py[j] * Px[i];
-        F[idx] = cP * ppp + cS * spp;
+    const long long lines = (long long)n2 * n3;
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) {
+        X1[i] = fma(cP, Px[i], cS * Sx[i]);
+        X2[i] = Px[i];
+    }
+    for (long long l0 = (long long)blockIdx.x * SRC_LINES; l0 < lines; l0 += (long long)gridDim.x * SRC_LINES) {
+        __syncthreads();
+        if (threadIdx.x < SRC_LINES && l0 + threadIdx.x < lines) {
+            const long long l = l0 + threadIdx.x;
+            const int j = (int)(l % n2), k = (int)(l / n2);
+            la[threadIdx.x] = Pz[k] * Py[j];
+            lb[threadIdx.x] = cS * fma(Pz[k], Sy[j], Sz[k] * Py[j]);
+        }
+        __syncthreads();
+        const int nl = (int)(lines - l0 < SRC_LINES ? lines - l0 : SRC_LINES);
+        for (int e = threadIdx.x; e < nl * n1; e += blockDim.x) {
+            const int t = e / n1, i = e - t * n1;
+            F[(l0 + t) * n1 + i] = fma(la[t], X1[i], lb[t] * X2[i]);
+        }
     }
 }
 
@@ -480,7 +501,14 @@ void launch_source_assemble_f64(const double* oned, const int n[3], double cP, d
                                 cudaStream_t s) {
     stats_count_launch();
     const long long N = (long long)n[0] * n[1] * n[2];
-    source_assemble_f64_kernel<<<grid_for(N), kThreads, 0, s>>>(oned, n[0], n[1], n[2], cP, cS, F);
+    const long long lines = (long long)n[1] * n[2];
+    long long blocks = (lines + SRC_LINES - 1) / SRC_LINES;
+    if (blocks > 152LL * 8) blocks = 152LL * 8;
+    const size_t smem = (2 * (size_t)n[0] + 2 * SRC_LINES) * sizeof(double);
+    (void)N;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(source_assemble_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    source_assemble_f64_kernel<<<(unsigned)blocks, kThreads, smem, s>>>(oned, n[0], n[1], n[2], cP, cS, F);
 }
 
 }  // namespace tfde

@@ -49,16 +49,36 @@ __device__ __forceinline__ int line_exponent_from_bits(unsigned long long umax) 
     return e == 0 ? -1021 : e - 1022;
 }
 
-// balanced base-128 digits of X (|X| <= 2^{7S}): planes[t*N + idx] for t = S-1..1 in
-// [-64, 63], planes[idx] the remaining leading digit
-__device__ __forceinline__ void write_digits(long long X, int S, __nv_bfloat16* planes, long long N, long long idx) {
-    for (int t = S - 1; t >= 1; --t) {
-        long long r = X & 127;
-        if (r >= 64) r -= 128;
-        planes[(long long)t * N + idx] = __float2bfloat16_rn((float)r);
-        X = (X - r) >> 7;
+// Balanced base-128 digits of X (|X| <= 2^{7S}): X = sum_t d_t 128^{S-1-t} with
+// d_t in [-64, 63] for t >= 1 and the leading d_0 in [-128, 128].  Adding 64 to
+// every digit below the leading one, Y = X + 64 (128^{S-1} - 1) / 127, turns
+// them into plain base-128 digits of Y, so d_t = ((Y >> 7 (S-1-t)) & 127) - 64
+// for t >= 1 and d_0 = Y >> 7 (S-1) (arithmetic shift): no carry chain.  BF16
+// bits of a digit: the top half of its FP32 bits (exact: at most 8 significant
+// bits).
+__device__ __forceinline__ long long digit_bias(int S) {
+    long long b = 0;
+    for (int t = 1; t < S; ++t) b = b * 128 + 64;
+    return b;
+}
+__device__ __forceinline__ uint32_t bf16_bits_of(long long d) {
+    return __float_as_uint((float)(int)d) >> 16;
+}
+// digits of two neighbouring grid points (idx even, idx + 1) as packed BF16 pairs
+__device__ __forceinline__ void write_digits2(long long Xa, long long Xb, int S, __nv_bfloat16* planes, long long N,
+                                              long long idx, long long bias) {
+    const long long Ya = Xa + bias, Yb = Xb + bias;
+#pragma unroll
+    for (int t = 1; t < 7; ++t) {
+        if (t < S) {
+            const int sh = 7 * (S - 1 - t);
+            const uint32_t lo = bf16_bits_of(((Ya >> sh) & 127) - 64);
+            const uint32_t hi = bf16_bits_of(((Yb >> sh) & 127) - 64);
+            *reinterpret_cast<uint32_t*>(planes + (long long)t * N + idx) = lo | (hi << 16);
+        }
     }
-    planes[idx] = __float2bfloat16_rn((float)X);
+    const int sh0 = 7 * (S - 1);
+    *reinterpret_cast<uint32_t*>(planes + idx) = bf16_bits_of(Ya >> sh0) | (bf16_bits_of(Yb >> sh0) << 16);
 }
 
 // |x| bits of x * 2^sh for a normal or zero x (exponent field moved by sh)
@@ -80,56 +100,80 @@ __device__ __forceinline__ double i64_ldexp_exact(long long Y, int s) {
     return __longlong_as_double((long long)((neg << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1))));
 }
 
-// x axis: one warp per line of n1 contiguous values.  Writes the digit planes
-// of x under its line maximum and, when wout is set, w = A_{n1} x along the
-// line from the same fixed-point integers X (w_k = (X_{k-1} + 6 X_k +
-// X_{k+1}) 2^{E - 7S - 3}, |sum| < 2^53: exact).
+// x axis: one warp per line of n1 contiguous values, each lane taking pairs of
+// neighbouring points (16-byte loads, packed BF16 digit pairs).  Writes the
+// digit planes of x under its line maximum and, when wout is set,
+// w = A_{n1} x along the line from the same fixed-point integers X
+// (w_k = (X_{k-1} + 6 X_k + X_{k+1}) 2^{E - 7S - 3}, |sum| < 2^53: exact).
 __global__ void slice_x_kernel(const double* __restrict__ x0, int n1, long long lines, int S,
                                __nv_bfloat16* __restrict__ p0, long long N, int* __restrict__ lexp,
                                double* __restrict__ wout) {
     const int lane = threadIdx.x & 31;
     const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long bias = digit_bias(S);
     for (long long l = wg; l < lines; l += nw) {
-        const long long* r0 = reinterpret_cast<const long long*>(x0 + l * n1);
+        const longlong2* r2 = reinterpret_cast<const longlong2*>(x0 + l * n1);   // n1 even: pairs stay in the line
+        const int np = n1 / 2;
         unsigned long long umax = 0;
 #pragma unroll 4
-        for (int k = lane; k < n1; k += 32) umax = max(umax, (unsigned long long)r0[k] & 0x7FFFFFFFFFFFFFFFull);
+        for (int q = lane; q < np; q += 32) {
+            const longlong2 v = r2[q];
+            umax = max(umax, max((unsigned long long)v.x & 0x7FFFFFFFFFFFFFFFull,
+                                 (unsigned long long)v.y & 0x7FFFFFFFFFFFFFFFull));
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) umax = max(umax, __shfl_xor_sync(0xffffffffu, umax, o));
         const int E = line_exponent_from_bits(umax);
-        long long left_carry = 0;   // X_{base - 1}
-        long long Xc = lane < n1 ? fixed_point(r0[lane], S, E) : 0;
-        for (int base = 0; base < n1; base += 32) {
-            const int k = base + lane;
-            const int kn = k + 32;
-            const long long Xn = kn < n1 ? fixed_point(r0[kn], S, E) : 0;
-            if (k < n1) write_digits(Xc, S, p0, N, l * n1 + k);
+        long long left_carry = 0;   // X just before this iteration's first point
+        long long Xa = 0, Xb = 0;
+        if (lane < np) {
+            const longlong2 v = r2[lane];
+            Xa = fixed_point(v.x, S, E);
+            Xb = fixed_point(v.y, S, E);
+        }
+        for (int base = 0; base < np; base += 32) {
+            const int q = base + lane;
+            const int qn = q + 32;
+            long long Na = 0, Nb = 0;
+            if (qn < np) {
+                const longlong2 v = r2[qn];
+                Na = fixed_point(v.x, S, E);
+                Nb = fixed_point(v.y, S, E);
+            }
+            if (q < np) write_digits2(Xa, Xb, S, p0, N, l * n1 + 2 * q, bias);
             if (wout) {
-                long long left = __shfl_up_sync(0xffffffffu, Xc, 1);
-                long long right = __shfl_down_sync(0xffffffffu, Xc, 1);
-                const long long first_next = __shfl_sync(0xffffffffu, Xn, 0);
+                long long left = __shfl_up_sync(0xffffffffu, Xb, 1);
+                long long right = __shfl_down_sync(0xffffffffu, Xa, 1);
+                const long long first_next = __shfl_sync(0xffffffffu, Na, 0);
                 if (lane == 0) left = left_carry;
                 if (lane == 31) right = first_next;
-                if (k < n1) wout[l * n1 + k] = i64_ldexp_exact(left + 6 * Xc + right, E - 7 * S - 3);
-                left_carry = __shfl_sync(0xffffffffu, Xc, 31);
+                if (q < np) {
+                    const int sc = E - 7 * S - 3;
+                    *reinterpret_cast<double2*>(wout + l * n1 + 2 * q) =
+                        make_double2(i64_ldexp_exact(left + 6 * Xa + Xb, sc), i64_ldexp_exact(Xa + 6 * Xb + right, sc));
+                }
+                left_carry = __shfl_sync(0xffffffffu, Xb, 31);
             }
-            Xc = Xn;
+            Xa = Na;
+            Xb = Nb;
         }
         if (lane == 0) lexp[l] = E;
     }
 }
 
 // y / z axes: LB consecutive lines (contiguous in memory) per 512-thread
-// block.  The block's lines of both inputs are copied once into shared memory
-// (8-byte cp.async, all in flight together), the joint line maximum of x0 and
-// x1 * 2^sh1 is reduced there, and the digits are written from shared memory:
-// every input element crosses HBM once.  When eout is set, e = A_n x1 along
-// the line from the fixed-point integers W of x1 (exact as in slice_x_kernel).
+// block, each thread taking a pair of neighbouring lines.  The block's lines
+// of both inputs are copied once into shared memory (16-byte cp.async, all in
+// flight together), the joint line maximum of x0 and x1 * 2^sh1 is reduced
+// there, and the digits go out as packed BF16 pairs: every input element
+// crosses HBM once and every store covers two grid points.  When eout is set,
+// e = A_n x1 along the line from the fixed-point integers W of x1 (exact as in
+// slice_x_kernel).
 constexpr int SL_THREADS = 512;
 
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                  : "memory");
 }
 
@@ -139,56 +183,68 @@ __global__ __launch_bounds__(SL_THREADS) void slice_staged_kernel(const double* 
                                                                   int S, __nv_bfloat16* __restrict__ p0,
                                                                   __nv_bfloat16* __restrict__ p1, long long N,
                                                                   int* __restrict__ lexp, double* __restrict__ eout) {
-    constexpr int NKG = SL_THREADS / LB;
+    constexpr int LP = LB / 2;               // line pairs per block
+    constexpr int NKG = SL_THREADS / LP;     // k rows in flight
     extern __shared__ unsigned long long sl_smem[];   // [input][k][LB]
     __shared__ unsigned long long smax[NKG][LB];
     __shared__ int sexp[LB];
     unsigned long long* s0 = sl_smem;
     unsigned long long* s1 = sl_smem + (size_t)v.n * LB;
-    const int li = threadIdx.x % LB, kg = threadIdx.x / LB;
+    const int lp = threadIdx.x % LP, kg = threadIdx.x / LP;
+    const int la = 2 * lp;                   // first line of the pair within the block
     const long long* b0 = reinterpret_cast<const long long*>(x0);
     const long long* b1 = reinterpret_cast<const long long*>(x1);
+    const long long bias = digit_bias(S);
     for (long long l0 = (long long)blockIdx.x * LB; l0 < v.lines; l0 += (long long)gridDim.x * LB) {
-        const long long l = l0 + li;
+        const long long l = l0 + la;          // lines l, l + 1 (same run: runs hold a multiple of 8 lines)
         const bool valid = l < v.lines;
         const long long off = valid ? (l % v.l_in) * v.s_in + (l / v.l_in) * v.s_out : 0;
         if (valid) {
             for (int k = kg; k < v.n; k += NKG) {
                 const long long idx = off + (long long)k * v.stride;
-                cp_async8(s0 + k * LB + li, b0 + idx);
-                if (b1) cp_async8(s1 + k * LB + li, b1 + idx);
+                cp_async16(s0 + k * LB + la, b0 + idx);
+                if (b1) cp_async16(s1 + k * LB + la, b1 + idx);
             }
         }
         asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
         __syncthreads();
-        unsigned long long umax = 0;
+        unsigned long long ma = 0, mb = 0;
         if (valid) {
             for (int k = kg; k < v.n; k += NKG) {
-                umax = max(umax, s0[k * LB + li] & 0x7FFFFFFFFFFFFFFFull);
-                if (b1) umax = max(umax, abs_bits_shifted((long long)s1[k * LB + li], sh1));
+                ma = max(ma, s0[k * LB + la] & 0x7FFFFFFFFFFFFFFFull);
+                mb = max(mb, s0[k * LB + la + 1] & 0x7FFFFFFFFFFFFFFFull);
+                if (b1) {
+                    ma = max(ma, abs_bits_shifted((long long)s1[k * LB + la], sh1));
+                    mb = max(mb, abs_bits_shifted((long long)s1[k * LB + la + 1], sh1));
+                }
             }
         }
-        smax[kg][li] = umax;
+        smax[kg][la] = ma;
+        smax[kg][la + 1] = mb;
         __syncthreads();
-        if (kg == 0) {
-            unsigned long long m = smax[0][li];
+        if (threadIdx.x < LB) {
+            unsigned long long m = smax[0][threadIdx.x];
 #pragma unroll 8
-            for (int g = 1; g < NKG; ++g) m = max(m, smax[g][li]);
+            for (int g = 1; g < NKG; ++g) m = max(m, smax[g][threadIdx.x]);
             const int E = line_exponent_from_bits(m);
-            sexp[li] = E;
-            if (valid) lexp[l] = E;
+            sexp[threadIdx.x] = E;
+            if (l0 + threadIdx.x < v.lines) lexp[l0 + threadIdx.x] = E;
         }
         __syncthreads();
-        const int E = sexp[li];
-        const int E1 = E - sh1;
+        const int Ea = sexp[la], Eb = sexp[la + 1];
         if (valid) {
             for (int k = kg; k < v.n; k += NKG) {
                 const long long idx = off + (long long)k * v.stride;
-                write_digits(fixed_point((long long)s0[k * LB + li], S, E), S, p0, N, idx);
+                write_digits2(fixed_point((long long)s0[k * LB + la], S, Ea),
+                              fixed_point((long long)s0[k * LB + la + 1], S, Eb), S, p0, N, idx, bias);
                 if (b1) {
-                    const long long W = fixed_point((long long)s1[k * LB + li], S, E1);
-                    write_digits(W, S, p1, N, idx);
-                    if (eout) s1[k * LB + li] = (unsigned long long)W;
+                    const long long Wa = fixed_point((long long)s1[k * LB + la], S, Ea - sh1);
+                    const long long Wb = fixed_point((long long)s1[k * LB + la + 1], S, Eb - sh1);
+                    write_digits2(Wa, Wb, S, p1, N, idx, bias);
+                    if (eout) {
+                        s1[k * LB + la] = (unsigned long long)Wa;
+                        s1[k * LB + la + 1] = (unsigned long long)Wb;
+                    }
                 }
             }
         }
@@ -196,10 +252,16 @@ __global__ __launch_bounds__(SL_THREADS) void slice_staged_kernel(const double* 
             __syncthreads();
             if (valid) {
                 for (int k = kg; k < v.n; k += NKG) {
-                    const long long Wp = k > 0 ? (long long)s1[(k - 1) * LB + li] : 0;
-                    const long long Wn = k + 1 < v.n ? (long long)s1[(k + 1) * LB + li] : 0;
-                    const long long W = (long long)s1[k * LB + li];
-                    eout[off + (long long)k * v.stride] = i64_ldexp_exact(Wp + 6 * W + Wn, E1 - 7 * S - 3);
+                    double e2[2];
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const int c = la + q;
+                        const long long Wp = k > 0 ? (long long)s1[(k - 1) * LB + c] : 0;
+                        const long long Wn = k + 1 < v.n ? (long long)s1[(k + 1) * LB + c] : 0;
+                        const long long W = (long long)s1[k * LB + c];
+                        e2[q] = i64_ldexp_exact(Wp + 6 * W + Wn, (q ? Eb : Ea) - sh1 - 7 * S - 3);
+                    }
+                    *reinterpret_cast<double2*>(eout + off + (long long)k * v.stride) = make_double2(e2[0], e2[1]);
                 }
             }
         }
@@ -259,6 +321,8 @@ void slice_operators_host(const std::vector<const std::vector<double>*>& ops, in
     } while (0)
 
 bool g_oz_attr = false;
+// swizzle of the MN-major input tiles: one atom spans the tile's BN lines
+constexpr CUtensorMapSwizzle kMnSwizzle = oz::BN * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
 bool g_sl_attr[2] = {false, false};
 
 // Upload one operator digit set and build its tensor maps.
@@ -358,8 +422,17 @@ int oz_init(tfde_problem* P, const std::vector<double> etaB[3], cudaStream_t s) 
         for (int t = 0; t < S; ++t)
             for (int a = 0; a < 3; ++a) {
                 const __nv_bfloat16* base = M->oz_planes[in] + (size_t)t * N;
-                st = (a == 0) ? tc::make_map_B_box(&M->oz_bmap[in][t][a], base, P->n, a, oz::BN)
-                              : tc::make_map_B(&M->oz_bmap[in][t][a], base, P->n, a);
+                if (a == 0) {
+                    st = tc::make_map_B_box(&M->oz_bmap[in][t][a], base, P->n, a, oz::BN);
+                } else {
+                    // MN-major slice: box {BN lines, BK, 1 plane}, swizzle span BN x 2 bytes
+                    const cuuint64_t c1 = P->n[0], c2 = P->n[1], c3 = P->n[2];
+                    const cuuint64_t C = a == 1 ? c1 : c1 * c2, K = a == 1 ? c2 : c3, Pl = a == 1 ? c3 : 1;
+                    const cuuint64_t dims[3] = {C, K, Pl};
+                    const cuuint64_t strides[2] = {C * 2, C * K * 2};
+                    const cuuint32_t box[3] = {(cuuint32_t)oz::BN, (cuuint32_t)tc::BK, 1};
+                    st = tc::encode_map(&M->oz_bmap[in][t][a], base, 3, dims, strides, box, kMnSwizzle);
+                }
                 if (st) return st;
                 // slices 0..t of input `in` along axis a in one box
                 const cuuint64_t n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
@@ -369,19 +442,17 @@ int oz_init(tfde_problem* P, const std::vector<double> etaB[3], cudaStream_t s) 
                     const cuuint64_t strides[2] = {n1 * 2, (cuuint64_t)N * 2};
                     const cuuint32_t box[3] = {(cuuint32_t)tc::BK, (cuuint32_t)oz::BN, (cuuint32_t)(t + 1)};
                     es = tc::encode_map(&M->oz_bmapm[in][a][t], M->oz_planes[in], 3, dims, strides, box,
-                                        CU_TENSOR_MAP_SWIZZLE_64B);
+                                        CU_TENSOR_MAP_SWIZZLE_64B);   // K-major rows of BK x 2 = 64 bytes
                 } else if (a == 1) {
                     const cuuint64_t dims[4] = {n1, n2, n3, (cuuint64_t)S};
                     const cuuint64_t strides[3] = {n1 * 2, n1 * n2 * 2, (cuuint64_t)N * 2};
-                    const cuuint32_t box[4] = {64, (cuuint32_t)tc::BK, 1, (cuuint32_t)(t + 1)};
-                    es = tc::encode_map(&M->oz_bmapm[in][a][t], M->oz_planes[in], 4, dims, strides, box,
-                                        CU_TENSOR_MAP_SWIZZLE_128B);
+                    const cuuint32_t box[4] = {(cuuint32_t)oz::BN, (cuuint32_t)tc::BK, 1, (cuuint32_t)(t + 1)};
+                    es = tc::encode_map(&M->oz_bmapm[in][a][t], M->oz_planes[in], 4, dims, strides, box, kMnSwizzle);
                 } else {
                     const cuuint64_t dims[3] = {n1 * n2, n3, (cuuint64_t)S};
                     const cuuint64_t strides[2] = {n1 * n2 * 2, (cuuint64_t)N * 2};
-                    const cuuint32_t box[3] = {64, (cuuint32_t)tc::BK, (cuuint32_t)(t + 1)};
-                    es = tc::encode_map(&M->oz_bmapm[in][a][t], M->oz_planes[in], 3, dims, strides, box,
-                                        CU_TENSOR_MAP_SWIZZLE_128B);
+                    const cuuint32_t box[3] = {(cuuint32_t)oz::BN, (cuuint32_t)tc::BK, (cuuint32_t)(t + 1)};
+                    es = tc::encode_map(&M->oz_bmapm[in][a][t], M->oz_planes[in], 3, dims, strides, box, kMnSwizzle);
                 }
                 M->oz_bmapm_ok[in][a][t] = es == TFDE_OK;
             }
@@ -485,7 +556,7 @@ int oz_contract(const tfde_problem* P, int axis, const OzSegSpec* segs, int nseg
         prm.b_kmajor = 0;
         if (axis == 1) { prm.C = (int)n1; prm.P = (int)n3; prm.bm_rank = 4; }
         else { prm.C = (int)(n1 * n2); prm.P = 1; prm.bm_rank = 3; }
-        prm.nbc = (prm.C + 63) / 64;
+        prm.nbc = (prm.C + oz::BN - 1) / oz::BN;
         prm.nblocks = (long long)prm.nbc * prm.P;
         prm.ntiles = prm.nblocks;
         prm.lines = (long long)prm.C * prm.P;

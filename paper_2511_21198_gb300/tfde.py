@@ -68,11 +68,12 @@ EXPORTS = ["tfde_assemble", "tfde_destroy", "tfde_matvec", "tfde_precond", "tfde
 
 
 def load(path: str | None = None):
-    """Load libtfde.so (raises if it has not been built)."""
+    """Load libtfde.so (raises if it has not been built); TFDE_LIB in the
+    environment names another build of the same library."""
     global _lib
     if _lib is not None and path is None:
         return _lib
-    p = path or LIB_PATH
+    p = path or os.environ.get("TFDE_LIB") or LIB_PATH
     if not os.path.exists(p):
         raise RuntimeError(f"{p} is missing: build it with paper_2511_21198_gb300.build.build()")
     lib = ctypes.CDLL(p)
