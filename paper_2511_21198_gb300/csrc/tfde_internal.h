@@ -46,6 +46,9 @@ void launch_axis_gemm_f64(const double* Mat, const double* X, double* Y, const A
 // Y = beta * (tridiag(1,6,1)/8 along axis) X + gamma * W   (W may be null)
 void launch_axis_stencil_f64(const double* X, double* Y, const AxisView& v, double beta,
                              const double* W, double gamma, cudaStream_t s);
+// Y = A_N X = (T_{n3} (x) T_{n2} (x) T_{n1}) X, T = tridiag(1,6,1)/8: the three
+// sweeps of launch_axis_stencil_f64 (x, then y, then z) fused, same result
+void launch_mass3d_f64(const double* X, double* Y, const int n[3], cudaStream_t s);
 // y[i] = x[i] / Lambda(i,j,k), Lambda from the 1-D arrays (Eq. (diag_tau_pre))
 // lam layout: [mass_x | mass_y | mass_z | tau_x | tau_y | tau_z], lengths n1,n2,n3,n1,n2,n3
 void launch_lambda_scale_f64(const double* x, double* y, const double* lam, const int n[3],

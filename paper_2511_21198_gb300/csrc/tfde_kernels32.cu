@@ -59,13 +59,18 @@ __global__ __launch_bounds__(kT) void dot32_kernel(long long N, const float* __r
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// x += alpha p ; r -= alpha q ; (rh, rl) = split(r) ; partial r.r
-__global__ __launch_bounds__(kT) void cg_update32_kernel(long long N, const double* __restrict__ coef,
-                                                         const float* __restrict__ p, const float* __restrict__ q,
-                                                         float* __restrict__ x, float* __restrict__ r,
-                                                         __nv_bfloat16* __restrict__ rh,
-                                                         __nv_bfloat16* __restrict__ rl, double* __restrict__ part) {
-    const float alpha = (float)coef[0];
+// alpha = num / den (device scalars, formed once per block); x += alpha p ;
+// r -= alpha q ; (rh, rl) = split(r) ; *rr += r.r (compensated per thread,
+// FP64 across the block, one atomic add per block)
+__global__ __launch_bounds__(kT) void cg_update32_kernel(long long N, const double* __restrict__ num,
+                                                         const double* __restrict__ den, const float* __restrict__ p,
+                                                         const float* __restrict__ q, float* __restrict__ x,
+                                                         float* __restrict__ r, __nv_bfloat16* __restrict__ rh,
+                                                         __nv_bfloat16* __restrict__ rl, double* __restrict__ rr) {
+    __shared__ float s_alpha;
+    if (threadIdx.x == 0) s_alpha = (float)(num[0] / den[0]);
+    __syncthreads();
+    const float alpha = s_alpha;
     long long lo, hi;
     chunk(N, lo, hi);
     KSum k;
@@ -77,13 +82,17 @@ __global__ __launch_bounds__(kT) void cg_update32_kernel(long long N, const doub
         k.add(ri * ri);
     }
     const double t = block_sum64((double)k.s - (double)k.c);
-    if (threadIdx.x == 0) part[blockIdx.x] = t;
+    if (threadIdx.x == 0) atomicAdd(rr, t);
 }
 
-// p = z + beta p ; (ph, pl) = split(p)
-__global__ void xpay32_kernel(long long N, const double* __restrict__ coef, const float* __restrict__ z,
-                              float* __restrict__ p, __nv_bfloat16* __restrict__ ph, __nv_bfloat16* __restrict__ pl) {
-    const float beta = (float)coef[0];
+// beta = num / den (device scalars); p = z + beta p ; (ph, pl) = split(p)
+__global__ void xpay32_kernel(long long N, const double* __restrict__ num, const double* __restrict__ den,
+                              const float* __restrict__ z, float* __restrict__ p, __nv_bfloat16* __restrict__ ph,
+                              __nv_bfloat16* __restrict__ pl) {
+    __shared__ float s_beta;
+    if (threadIdx.x == 0) s_beta = (float)(num[0] / den[0]);
+    __syncthreads();
+    const float beta = s_beta;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const float v = fmaf(beta, p[i], z[i]);
         p[i] = v;
@@ -190,15 +199,15 @@ void launch_dot32(size_t N, const float* a, const float* b, double* part, int nb
     stats_count_launch();
     dot32_kernel<<<nblk, kT, 0, s>>>((long long)N, a, b, part);
 }
-void launch_cg_update32(size_t N, const double* coef, const float* p, const float* q, float* x, float* r,
-                        __nv_bfloat16* rh, __nv_bfloat16* rl, double* part, int nblk, cudaStream_t s) {
+void launch_cg_update32(size_t N, const double* num, const double* den, const float* p, const float* q, float* x,
+                        float* r, __nv_bfloat16* rh, __nv_bfloat16* rl, double* rr, cudaStream_t s) {
     stats_count_launch();
-    cg_update32_kernel<<<nblk, kT, 0, s>>>((long long)N, coef, p, q, x, r, rh, rl, part);
+    cg_update32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, num, den, p, q, x, r, rh, rl, rr);
 }
-void launch_xpay32(size_t N, const double* coef, const float* z, float* p, __nv_bfloat16* ph, __nv_bfloat16* pl,
-                   cudaStream_t s) {
+void launch_xpay32(size_t N, const double* num, const double* den, const float* z, float* p, __nv_bfloat16* ph,
+                   __nv_bfloat16* pl, cudaStream_t s) {
     stats_count_launch();
-    xpay32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, coef, z, p, ph, pl);
+    xpay32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, num, den, z, p, ph, pl);
 }
 void launch_scale64to32(size_t N, const double* r64, double sc, float* r32, __nv_bfloat16* rh, __nv_bfloat16* rl,
                         float* x32, cudaStream_t s) {

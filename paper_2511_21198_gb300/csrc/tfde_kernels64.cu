@@ -119,6 +119,79 @@ __global__ void axis_stencil_f64_kernel(const double* __restrict__ X, double* __
     }
 }
 
+// Y = (T_{n3} (x) T_{n2} (x) T_{n1}) X, T = tridiag(1,6,1)/8, zero exterior
+// data: the three axis sweeps of axis_stencil_f64_kernel in one pass.  A CTA
+// owns an MX x MY column of (x, y) points and marches through MZ planes of z
+// (plus one halo plane on each side): per plane it stages the (MX+2) x (MY+2)
+// tile in shared memory, applies T along x, then along y, and keeps the last
+// two results per point in registers to apply T along z.  Every sum is formed
+// in the same order as the three separate sweeps, so the result is identical
+// to them; X is read about once and Y written once (the halo rows and columns
+// come from L2), against three reads and three writes for the sweeps.
+constexpr int MX = 64, MYT = 4, MY = 8, MZ = 32;   // (MX, MYT) threads, MY / MYT rows each
+
+__device__ __forceinline__ double tri(double l, double c, double r) { return fma(0.75, c, 0.125 * (l + r)); }
+
+__global__ __launch_bounds__(MX * MYT) void mass3d_f64_kernel(const double* __restrict__ X, double* __restrict__ Y,
+                                                              int n1, int n2, int n3) {
+    __shared__ double u[MY + 2][MX + 2];   // staged plane, one halo on each side
+    __shared__ double a[MY + 2][MX];       // T along x
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * MX + tx;
+    const int x0 = blockIdx.x * MX, y0 = blockIdx.y * MY, z0 = blockIdx.z * MZ;
+    const int z1 = min(z0 + MZ, n3);
+    const long long plane = (long long)n1 * n2;
+    const int gx = x0 + tx;
+    constexpr int ROWS = (MY + 2 + MYT - 1) / MYT;   // staged rows per thread (interior columns)
+    double ri[ROWS], rh = 0.0;                       // the next plane, in flight
+    auto load = [&](int k) {
+        const bool kin = k >= 0 && k < n3;
+        const double* Xk = X + (long long)k * plane;
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const int row = ty + q * MYT, gy = y0 - 1 + row;
+            ri[q] = (row < MY + 2 && kin && gx < n1 && gy >= 0 && gy < n2) ? Xk[(long long)gy * n1 + gx] : 0.0;
+        }
+        if (tid < 2 * (MY + 2)) {   // the two halo columns
+            const int row = tid >> 1, gy = y0 - 1 + row;
+            const int hx = (tid & 1) ? x0 + MX : x0 - 1;
+            rh = (kin && hx >= 0 && hx < n1 && gy >= 0 && gy < n2) ? Xk[(long long)gy * n1 + hx] : 0.0;
+        }
+    };
+    double s1[MY / MYT], s2[MY / MYT];   // T_y T_x X on planes k - 1 and k - 2
+#pragma unroll
+    for (int q = 0; q < MY / MYT; ++q) s1[q] = s2[q] = 0.0;
+    load(z0 - 1);
+    for (int k = z0 - 1; k <= z1; ++k) {
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const int row = ty + q * MYT;
+            if (row < MY + 2) u[row][tx + 1] = ri[q];
+        }
+        if (tid < 2 * (MY + 2)) u[tid >> 1][(tid & 1) ? MX + 1 : 0] = rh;
+        __syncthreads();
+        if (k < z1) load(k + 1);   // overlaps the arithmetic below
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const int row = ty + q * MYT;
+            if (row < MY + 2) a[row][tx] = tri(u[row][tx], u[row][tx + 1], u[row][tx + 2]);
+        }
+        __syncthreads();
+        const bool kin = k >= 0 && k < n3;
+#pragma unroll
+        for (int q = 0; q < MY / MYT; ++q) {
+            const int row = 1 + ty + q * MYT;   // tile row of output y0 + ty + q MYT
+            const int gy = y0 + ty + q * MYT;
+            // T along y of the rows inside the grid (rows outside are zero already)
+            const double s0 = kin && gy < n2 ? tri(a[row - 1][tx], a[row][tx], a[row + 1][tx]) : 0.0;
+            if (k - 1 >= z0 && gx < n1 && gy < n2)
+                Y[(long long)(k - 1) * plane + (long long)gy * n1 + gx] = tri(s2[q], s1[q], s0);
+            s2[q] = s1[q];
+            s1[q] = s0;
+        }
+    }
+}
+
 __global__ void lambda_scale_f64_kernel(const double* __restrict__ x, double* __restrict__ y,
                                         const double* __restrict__ lam, int n1, int n2, int n3,
                                         double c0, double c1, double c2, int invert) {
@@ -418,6 +491,12 @@ void launch_axis_stencil_f64(const double* X, double* Y, const AxisView& v, doub
     dim3 blk(n1 >= 64 ? 64 : 32, 4);
     dim3 grid((n1 + blk.x - 1) / blk.x, (n2 + blk.y - 1) / blk.y, n3 < 64 ? n3 : 64);
     axis_stencil_f64_kernel<<<grid, blk, 0, s>>>(X, Y, n1, n2, n3, axis, beta, W, gamma);
+}
+
+void launch_mass3d_f64(const double* X, double* Y, const int n[3], cudaStream_t s) {
+    stats_count_launch();
+    dim3 grid((unsigned)((n[0] + MX - 1) / MX), (unsigned)((n[1] + MY - 1) / MY), (unsigned)((n[2] + MZ - 1) / MZ));
+    mass3d_f64_kernel<<<grid, dim3(MX, MYT), 0, s>>>(X, Y, n[0], n[1], n[2]);
 }
 
 void launch_lambda_scale_f64(const double* x, double* y, const double* lam, const int n[3], const double c[3],

@@ -129,10 +129,15 @@ void gemm_params(const tfde_problem* P, int axis, const SegSpec* segs, int nseg,
 }
 
 int run_gemm(const tfde_problem* P, int axis, const SegSpec* segs, int nseg, int out_mode, float alpha,
-             float* out_f32, int out_plane, bool lam_scale, cudaStream_t s) {
+             float* out_f32, int out_plane, bool lam_scale, cudaStream_t s, const float* dot_vec = nullptr,
+             double* dot_out = nullptr) {
     tc::Params prm;
     double bytes, flops;
     gemm_params(P, axis, segs, nseg, out_mode, alpha, out_f32, out_plane, lam_scale, prm, &bytes, &flops);
+    if (out_mode == tc::OUT_F32 && dot_out) {
+        prm.dot_vec = dot_vec;
+        prm.dot_out = dot_out;
+    }
     mixed(P)->gemm_launches++;
     return tc::launch(prm, s, bytes, flops);
 }
@@ -176,11 +181,15 @@ int precond_passes(Pass* ps) {
     return 6;
 }
 
-int run_passes(const tfde_problem* P, const Pass* ps, int np, float* out_f32, cudaStream_t s) {
+// The last pass's FP32 output may also be dotted with dot_vec into *dot_out
+// (accumulated: the caller zeroes it).
+int run_passes(const tfde_problem* P, const Pass* ps, int np, float* out_f32, cudaStream_t s,
+               const float* dot_vec = nullptr, double* dot_out = nullptr) {
     for (int i = 0; i < np; ++i) {
         const Pass& q = ps[i];
+        const bool last = i + 1 == np;
         int st = run_gemm(P, q.axis, q.seg, q.nseg, q.out_mode, 1.f, q.out_mode == tc::OUT_F32 ? out_f32 : nullptr,
-                          q.out_plane, q.lam, s);
+                          q.out_plane, q.lam, s, last ? dot_vec : nullptr, last ? dot_out : nullptr);
         if (st) return st;
     }
     return TFDE_OK;
@@ -188,17 +197,19 @@ int run_passes(const tfde_problem* P, const Pass* ps, int np, float* out_f32, cu
 
 // q32 = A p (op A) or the RHS operator, p given as the split plane pair PL_P;
 // with out_plane >= 0 the result goes to that split plane pair instead.
-int fast_matvec(const tfde_problem* P, int op, float* q32, cudaStream_t s, int out_plane = -1) {
+int fast_matvec(const tfde_problem* P, int op, float* q32, cudaStream_t s, int out_plane = -1,
+                const float* dot_vec = nullptr, double* dot_out = nullptr) {
     Pass ps[5];
     const int np = matvec_passes(op, out_plane, ps);
-    return run_passes(P, ps, np, q32, s);
+    return run_passes(P, ps, np, q32, s, dot_vec, dot_out);
 }
 
 // z32 = S_N Lambda^{-1} S_N r, r given as the split plane pair PL_R.
-int fast_precond(const tfde_problem* P, float* z32, cudaStream_t s) {
+int fast_precond(const tfde_problem* P, float* z32, cudaStream_t s, const float* dot_vec = nullptr,
+                 double* dot_out = nullptr) {
     Pass ps[6];
     const int np = precond_passes(ps);
-    return run_passes(P, ps, np, z32, s);
+    return run_passes(P, ps, np, z32, s, dot_vec, dot_out);
 }
 
 int check_err(const tfde_problem* P, cudaStream_t s) {
@@ -219,12 +230,17 @@ double host_scalar(const tfde_problem* P, const double* dev, cudaStream_t s, int
     return P->red_host[0];
 }
 
-// Device-scalar slots.
-enum { D_RZ = 0, D_PQ = 1, D_RR = 2, D_ALPHA = 3, D_BETA = 4, D_RZN = 5 };
+// Device-scalar slots: <p, A p>, <r, r>, and <r, z> of the current / next
+// iteration in alternating slots (a kernel that reads one writes the other).
+enum { D_PQ = 0, D_RR = 1, D_RZ0 = 2, D_RZ1 = 3 };
 
 // Inner PCG on FP32 vectors: A d = r32 (r32 and its split planes prepared by
-// the caller, x32 = 0), until ||r|| <= theta ||r32_0|| or maxit.  All
-// coefficients stay on the device; one host read (r.r) per iteration.
+// the caller, x32 = 0), until ||r|| <= theta ||r32_0|| or maxit.  The inner
+// products ride on the kernels that produce their operands (<p, Ap> in the
+// operator's last pass, <r, z> in the preconditioner's, <r, r> in the update),
+// the coefficients alpha = <r,z>/<p,Ap> and beta = <r,z>_new/<r,z> are formed
+// on the device by the update kernels, and the host reads <r, r> once per
+// iteration for the stopping test.
 int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaStream_t s) {
     MixedState* M = mixed(P);
     const size_t N = P->N;
@@ -240,30 +256,26 @@ int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaSt
     const double rr0 = host_scalar(P, d + D_RR, s, &st);
     if (st) return st;
     if (!(rr0 > 0.0) || !std::isfinite(rr0)) return rr0 == 0.0 ? TFDE_OK : set_error(TFDE_ENAN, "non-finite inner residual");
-    if ((st = fast_precond(P, z, s))) return st;
+    int rz = D_RZ0;
+    MX_TRY(cudaMemsetAsync(d + rz, 0, sizeof(double), s));
+    if ((st = fast_precond(P, z, s, r, d + rz))) return st;
     MX_TRY(cudaMemcpyAsync(p, z, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
     launch_split32(N, p, M->hi[PL_P], M->lo[PL_P], s);
-    launch_dot32(N, r, z, P->red, P->nblk, s);
-    launch_reduce_finish(P->red, P->nblk, 1, d + D_RZ, s);
     int k = 0;
     while (k < maxit) {
-        if ((st = fast_matvec(P, TFDE_OP_A, q, s))) return st;
-        launch_dot32(N, p, q, P->red, P->nblk, s);
-        launch_reduce_finish(P->red, P->nblk, 1, d + D_PQ, s);
-        launch_ratio(d + D_RZ, d + D_PQ, d + D_ALPHA, s);
-        launch_cg_update32(N, d + D_ALPHA, p, q, x, r, M->hi[PL_R], M->lo[PL_R], P->red, P->nblk, s);
-        launch_reduce_finish(P->red, P->nblk, 1, d + D_RR, s);
+        MX_TRY(cudaMemsetAsync(d + D_PQ, 0, 2 * sizeof(double), s));   // <p, Ap> and <r, r>
+        if ((st = fast_matvec(P, TFDE_OP_A, q, s, -1, p, d + D_PQ))) return st;
+        launch_cg_update32(N, d + rz, d + D_PQ, p, q, x, r, M->hi[PL_R], M->lo[PL_R], d + D_RR, s);
         const double rr = host_scalar(P, d + D_RR, s, &st);
         if (st) return st;
         ++k;
         if (!std::isfinite(rr)) return set_error(TFDE_ENAN, "non-finite inner residual");
         if (rr <= theta * theta * rr0) break;
-        if ((st = fast_precond(P, z, s))) return st;
-        launch_dot32(N, r, z, P->red, P->nblk, s);
-        launch_reduce_finish(P->red, P->nblk, 1, d + D_RZN, s);
-        launch_ratio(d + D_RZN, d + D_RZ, d + D_BETA, s);
-        MX_TRY(cudaMemcpyAsync(d + D_RZ, d + D_RZN, sizeof(double), cudaMemcpyDeviceToDevice, s));
-        launch_xpay32(N, d + D_BETA, z, p, M->hi[PL_P], M->lo[PL_P], s);
+        const int rzn = rz == D_RZ0 ? D_RZ1 : D_RZ0;
+        MX_TRY(cudaMemsetAsync(d + rzn, 0, sizeof(double), s));
+        if ((st = fast_precond(P, z, s, r, d + rzn))) return st;
+        launch_xpay32(N, d + rzn, d + rz, z, p, M->hi[PL_P], M->lo[PL_P], s);
+        rz = rzn;
     }
     *iters = k;
     return check_err(P, s);

@@ -12,10 +12,12 @@
 namespace tfde {
 
 void launch_dot32(size_t N, const float* a, const float* b, double* part, int nblk, cudaStream_t s);
-void launch_cg_update32(size_t N, const double* coef, const float* p, const float* q, float* x, float* r,
-                        __nv_bfloat16* rh, __nv_bfloat16* rl, double* part, int nblk, cudaStream_t s);
-void launch_xpay32(size_t N, const double* coef, const float* z, float* p, __nv_bfloat16* ph, __nv_bfloat16* pl,
-                   cudaStream_t s);
+// alpha = *num / *den on the device; x += alpha p; r -= alpha q; split r; *rr += r.r
+void launch_cg_update32(size_t N, const double* num, const double* den, const float* p, const float* q, float* x,
+                        float* r, __nv_bfloat16* rh, __nv_bfloat16* rl, double* rr, cudaStream_t s);
+// beta = *num / *den on the device; p = z + beta p; split p
+void launch_xpay32(size_t N, const double* num, const double* den, const float* z, float* p, __nv_bfloat16* ph,
+                   __nv_bfloat16* pl, cudaStream_t s);
 void launch_scale64to32(size_t N, const double* r64, double sc, float* r32, __nv_bfloat16* rh, __nv_bfloat16* rl,
                         float* x32, cudaStream_t s);
 void launch_split32(size_t N, const float* v, __nv_bfloat16* h, __nv_bfloat16* l, cudaStream_t s);

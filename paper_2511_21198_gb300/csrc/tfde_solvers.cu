@@ -302,11 +302,9 @@ int accurate_apply(const tfde_problem*, int, const double*, double*, cudaStream_
 int accurate_apply_ex(const tfde_problem*, int, const double*, double*, int, const double*, double, cudaStream_t, int,
                       double*, int);
 
-// A_N u into `out` (three tridiagonal sweeps; W_A and W_W as temporaries).
+// A_N u into `out` (the three tridiagonal sweeps in one pass).
 static void mass_apply(const tfde_problem* P, const double* u, double* out, cudaStream_t s) {
-    launch_axis_stencil_f64(u, P->w[tfde_problem::W_A], axis_view(P->n, 0), 1.0, nullptr, 0.0, s);
-    launch_axis_stencil_f64(P->w[tfde_problem::W_A], P->w[tfde_problem::W_W], axis_view(P->n, 1), 1.0, nullptr, 0.0, s);
-    launch_axis_stencil_f64(P->w[tfde_problem::W_W], out, axis_view(P->n, 2), 1.0, nullptr, 0.0, s);
+    launch_mass3d_f64(u, out, P->n, s);
 }
 
 // One CN step (Eq. (CN), Eq. (linear_sys)) for either precision.  `chained`:

@@ -95,6 +95,9 @@ struct Params {
     const float* lam_rb;
     const float* lam_U;
     const float* lam_V;
+    // optional fused inner product (OUT_F32 only): *dot_out += sum out[i] dot_vec[i]
+    const float* dot_vec;
+    double* dot_out;
     int* err;
 };
 
@@ -104,6 +107,29 @@ struct Params {
 #include "tfde_tc_ptx.cuh"
 namespace tfde {
 namespace tc {
+
+// Compensated FP32 sum of the fused inner product (one per epilogue thread).
+struct DotAcc {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+// The dot_vec elements matching cnt (0..4) consecutive outputs at idx, zero
+// beyond cnt; read through the non-coherent path so that the loads can be
+// issued ahead of the chunk's stores.
+__device__ __forceinline__ float4 dot_load(const float* __restrict__ w, long long idx, int cnt) {
+    if (cnt == 4) return __ldg(reinterpret_cast<const float4*>(w + idx));
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (cnt > 0) r.x = __ldg(w + idx);
+    if (cnt > 1) r.y = __ldg(w + idx + 1);
+    if (cnt > 2) r.z = __ldg(w + idx + 2);
+    return r;
+}
 
 // Four consecutive outputs (already scaled) to global memory at element index idx.
 __device__ __forceinline__ void store4(const Params& p, long long idx, float v0, float v1, float v2, float v3) {
@@ -334,6 +360,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int rsub = lane >> 3;           // transposed phase: 4 rows / columns per instruction
         const int cq = (lane & 7) * 4;        // ... and 4 consecutive elements per lane
         long long it = 0;
+        DotAcc da;                            // fused inner product (single launches only)
         for (long long t = blockIdx.x; t < total; t += gridDim.x) {
             long long lt = t;
             const Params* pp = &p0;
@@ -357,70 +384,92 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const int mrow0 = mh * BM + 32 * q;   // first output row of this warp
             for (int cc = 0; cc < BN / 2; cc += 32) {
                 const int c0 = half * (BN / 2) + cc;
+                // Output positions of this lane: 8 groups i8 of up to 4 consecutive
+                // elements, group i8 at oidx0 + i8 * ostep, cnt0 valid ones when
+                // bit i8 of vmask is set, none otherwise.
+                long long oidx0, ostep;
+                int cnt0;
+                unsigned vmask = 0;
+                if (b_kmajor) {
+                    // stg[row][line]; output Y[line * n1 + m], m contiguous
+                    const int m = mrow0 + cq;
+                    const long long l0 = tile * BN + c0 + rsub;
+                    cnt0 = m + 4 <= p.n ? 4 : (m < p.n ? p.n - m : 0);
+                    oidx0 = l0 * p.n1 + m;
+                    ostep = 4LL * p.n1;
+#pragma unroll
+                    for (int i8 = 0; i8 < 8; ++i8)
+                        if (l0 + i8 * 4 < p.lines) vmask |= 1u << i8;
+                } else {
+                    // stg[row][c]; output Y[pl * plane + m * C + c], c contiguous
+                    const long long gb = tile * (BN / 64) + c0 / 64;
+                    const int pl = (int)(gb / p.nbc);
+                    const int c = (int)(gb % p.nbc) * 64 + (c0 & 63) + cq;
+                    const int m0 = mrow0 + rsub;
+                    cnt0 = gb < p.nblocks ? (c + 4 <= p.C ? 4 : (c < p.C ? p.C - c : 0)) : 0;
+                    oidx0 = (long long)pl * p.plane + (long long)m0 * p.C + c;
+                    ostep = 4LL * p.C;
+#pragma unroll
+                    for (int i8 = 0; i8 < 8; ++i8)
+                        if (m0 + i8 * 4 < p.n) vmask |= 1u << i8;
+                }
+                if (cnt0 == 0) vmask = 0;
+                const bool dot = p.dot_vec != nullptr;
+                float4 w[8];
+                if (dot) {
+#pragma unroll
+                    for (int i8 = 0; i8 < 8; ++i8)
+                        w[i8] = dot_load(p.dot_vec, oidx0 + i8 * ostep, (vmask >> i8) & 1u ? cnt0 : 0);
+                }
                 uint32_t r[32];
                 tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN + c0), r);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) stg[lane * EPI_STRIDE + j] = p.alpha * __uint_as_float(r[j]);
                 __syncwarp();
-                if (b_kmajor) {
-                    // stg[row][line]; output Y[line * n1 + m], m contiguous
-#pragma unroll 2
-                    for (int i8 = 0; i8 < 8; ++i8) {
-                        const int jl = i8 * 4 + rsub;                 // line within the chunk
-                        const long long l = tile * BN + c0 + jl;
-                        const int m = mrow0 + cq;
-                        if (l < p.lines) {
-                            const float v0 = stg[(cq + 0) * EPI_STRIDE + jl];
-                            const float v1 = stg[(cq + 1) * EPI_STRIDE + jl];
-                            const float v2 = stg[(cq + 2) * EPI_STRIDE + jl];
-                            const float v3 = stg[(cq + 3) * EPI_STRIDE + jl];
-                            const long long idx = l * p.n1 + m;
-                            if (m + 3 < p.n) {
-                                store4(p, idx, v0, v1, v2, v3);
-                            } else {
-                                if (m + 0 < p.n) store1(p, idx + 0, v0);
-                                if (m + 1 < p.n) store1(p, idx + 1, v1);
-                                if (m + 2 < p.n) store1(p, idx + 2, v2);
-                            }
-                        }
-                    }
-                } else {
-                    // stg[row][c]; output Y[pl * plane + m * C + c], c contiguous
-                    const long long gb = tile * (BN / 64) + c0 / 64;
-                    const int pl = (int)(gb / p.nbc);
-                    const int cbase = (int)(gb % p.nbc) * 64 + (c0 & 63);
-                    const int c = cbase + cq;
-                    const bool cvalid = gb < p.nblocks;
-                    float U[4] = {0.f, 0.f, 0.f, 0.f}, V[4] = {0.f, 0.f, 0.f, 0.f};
-                    if (p.lam_ra && cvalid) {
+                float U[4] = {0.f, 0.f, 0.f, 0.f}, V[4] = {0.f, 0.f, 0.f, 0.f};
+                if (!b_kmajor && p.lam_ra && (vmask & 1u)) {   // rows ascend: none valid if the first is not
+                    const int c = (int)((tile * (BN / 64) + c0 / 64) % p.nbc) * 64 + (c0 & 63) + cq;
 #pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            if (c + k < p.C) {
-                                U[k] = __ldg(p.lam_U + c + k);
-                                V[k] = __ldg(p.lam_V + c + k);
-                            }
-                    }
-#pragma unroll 2
-                    for (int i8 = 0; i8 < 8; ++i8) {
-                        const int rr = i8 * 4 + rsub;
-                        const int m = mrow0 + rr;
-                        if (cvalid && m < p.n && c < p.C) {
-                            float v[4];
+                    for (int k = 0; k < 4; ++k)
+                        if (c + k < p.C) {
+                            U[k] = __ldg(p.lam_U + c + k);
+                            V[k] = __ldg(p.lam_V + c + k);
+                        }
+                }
+#pragma unroll
+                for (int i8 = 0; i8 < 8; ++i8) {
+                    const int cnt = cnt0;
+                    if ((vmask >> i8) & 1u) {
+                        float v[4];
+                        if (b_kmajor) {
+                            const int jl = i8 * 4 + rsub;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) v[k] = stg[(cq + k) * EPI_STRIDE + jl];
+                        } else {
+                            const int rr = i8 * 4 + rsub;
 #pragma unroll
                             for (int k = 0; k < 4; ++k) v[k] = stg[rr * EPI_STRIDE + cq + k];
                             if (p.lam_ra) {
+                                const int m = mrow0 + rr;
                                 const float ra = __ldg(p.lam_ra + m), rb = __ldg(p.lam_rb + m);
 #pragma unroll
                                 for (int k = 0; k < 4; ++k) v[k] = __fdividef(v[k], ra * U[k] + rb * V[k]);
                             }
-                            const long long idx = (long long)pl * p.plane + (long long)m * p.C + c;
-                            if (c + 3 < p.C) {
-                                store4(p, idx, v[0], v[1], v[2], v[3]);
-                            } else {
+                        }
+                        const long long idx = oidx0 + i8 * ostep;
+                        if (cnt == 4) {
+                            store4(p, idx, v[0], v[1], v[2], v[3]);
+                        } else {
 #pragma unroll
-                                for (int k = 0; k < 3; ++k)
-                                    if (c + k < p.C) store1(p, idx + k, v[k]);
-                            }
+                            for (int k = 0; k < 3; ++k)
+                                if (k < cnt) store1(p, idx + k, v[k]);
+                        }
+                        if (dot) {
+#pragma unroll
+                            for (int k = 1; k < 4; ++k)
+                                if (k >= cnt) v[k] = 0.f;   // outside the grid (may be 0 / 0 above)
+                            const float4 wv = w[i8];
+                            da.add(fmaf(v[0], wv.x, fmaf(v[1], wv.y, fmaf(v[2], wv.z, v[3] * wv.w))));
                         }
                     }
                 }
@@ -430,6 +479,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[buf]);
             ++it;
+        }
+        if (p0.dot_out) {
+            double t = (double)da.s - (double)da.c;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) atomicAdd(p0.dot_out, t);
         }
     }
 

@@ -138,11 +138,13 @@ def test_cn_trajectory_n16_exp(T):
         c.close()
 
 
+@pytest.mark.parametrize("n", [(20, 18, 16), (67, 11, 37)], ids=lambda n: "x".join(map(str, n)))
 @pytest.mark.parametrize("sym", [True, False])
-def test_cn_step_tight_parity(T, sym):
+def test_cn_step_tight_parity(T, sym, n):
     """One step from the same u^{m-1}, both sides to a 1e-13 true residual:
-    relative error <= 1e-12 (the all-FP64 parity gate)."""
-    n = (20, 18, 16)
+    relative error <= 1e-12 (the all-FP64 parity gate).  The second grid is
+    ragged against every tile of the fused mass stencil (64 x 8 x 32 points)
+    and spans two of its z chunks."""
     c = Case(T, n, (0.3, 0.6, 0.8), (1.0,) * 3, (1.0,) * 3 if sym else (0.5,) * 3, 0.02)
     try:
         u0 = inp.smoothed_uniform(c.o.shape, 2)
