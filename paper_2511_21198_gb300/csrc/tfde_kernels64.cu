@@ -124,13 +124,16 @@ __global__ void axis_stencil_f64_kernel(const double* __restrict__ X, double* __
 // owns an MX x MY column of (x, y) points and marches through MZ planes of z
 // (plus one halo plane on each side): per plane it stages the (MX+2) x (MY+2)
 // tile in shared memory, applies T along x, then along y, and keeps the last
-// two results per point in registers to apply T along z.  Every sum is formed
-// in the same order as the three separate sweeps, so the result is identical
-// to them; X is read about once and Y written once (the halo rows and columns
-// come from L2), against three reads and three writes for the sweeps.
+// two results per point in registers to apply T along z.  Each axis applies
+// 8 T = tridiag(1,6,1) as fma(6, c, l + r) and the product is scaled by 1/512
+// once at the end: two FP64 operations per axis instead of three (the FP64
+// pipe, not HBM, bounds this kernel).  Power-of-two scaling commutes with
+// rounding, so the result is identical to the three sweeps; X is read about
+// once and Y written once (the halo rows and columns come from L2), against
+// three reads and three writes for the sweeps.
 constexpr int MX = 64, MYT = 4, MY = 8, MZ = 32;   // (MX, MYT) threads, MY / MYT rows each
 
-__device__ __forceinline__ double tri(double l, double c, double r) { return fma(0.75, c, 0.125 * (l + r)); }
+__device__ __forceinline__ double tri(double l, double c, double r) { return fma(6.0, c, l + r); }
 
 __global__ __launch_bounds__(MX * MYT) void mass3d_f64_kernel(const double* __restrict__ X, double* __restrict__ Y,
                                                               int n1, int n2, int n3) {
@@ -185,7 +188,7 @@ __global__ __launch_bounds__(MX * MYT) void mass3d_f64_kernel(const double* __re
             // T along y of the rows inside the grid (rows outside are zero already)
             const double s0 = kin && gy < n2 ? tri(a[row - 1][tx], a[row][tx], a[row + 1][tx]) : 0.0;
             if (k - 1 >= z0 && gx < n1 && gy < n2)
-                Y[(long long)(k - 1) * plane + (long long)gy * n1 + gx] = tri(s2[q], s1[q], s0);
+                Y[(long long)(k - 1) * plane + (long long)gy * n1 + gx] = tri(s2[q], s1[q], s0) * (1.0 / 512.0);
             s2[q] = s1[q];
             s1[q] = s0;
         }
