@@ -200,6 +200,7 @@ struct tfde_batch {
     tfde::tc::Params* d_pc = nullptr;
     tfde::tc::Params* d_pcl = nullptr;
     int mv_axis[5] = {}, pc_axis[6] = {};
+    int mv_out[5] = {}, pc_out[6] = {};   // output mode of each pass
     double mv_bytes[5] = {}, mv_flops[5] = {}, pc_bytes[6] = {}, pc_flops[6] = {};
     long long* d_gstart = nullptr;  // [3][count + 1]
     long long gtotal[3] = {};
@@ -282,15 +283,16 @@ int free_batch(tfde_batch* B) {
     return TFDE_OK;
 }
 
-int grouped(tfde_batch* B, const tc::Params* d, int axis, double bytes, double flops, cudaStream_t s) {
+int grouped(tfde_batch* B, const tc::Params* d, int axis, int out_mode, double bytes, double flops, cudaStream_t s) {
     return tc::launch_grouped(d, B->d_gstart + (size_t)axis * (B->count + 1), B->count, B->gtotal[axis],
-                              axis == 0 ? 1 : 0, B->d_act, B->d_err, s, bytes, flops);
+                              axis == 0 ? 1 : 0, out_mode, B->d_act, B->d_err, s, bytes, flops);
 }
 
 // v_j (split planes PL_P of every active problem) -> PL_R = A v_j
 int grouped_matvec(tfde_batch* B, cudaStream_t s) {
     for (int k = 0; k < 5; ++k) {
-        int st = grouped(B, B->d_mv + (size_t)k * B->count, B->mv_axis[k], B->mv_bytes[k], B->mv_flops[k], s);
+        int st = grouped(B, B->d_mv + (size_t)k * B->count, B->mv_axis[k], B->mv_out[k], B->mv_bytes[k],
+                         B->mv_flops[k], s);
         if (st) return st;
     }
     return TFDE_OK;
@@ -299,10 +301,12 @@ int grouped_matvec(tfde_batch* B, cudaStream_t s) {
 // PL_R -> V_j = P^{-1} (PL_R) in FP32
 int grouped_precond(tfde_batch* B, int j, cudaStream_t s) {
     for (int k = 0; k < 5; ++k) {
-        int st = grouped(B, B->d_pc + (size_t)k * B->count, B->pc_axis[k], B->pc_bytes[k], B->pc_flops[k], s);
+        int st = grouped(B, B->d_pc + (size_t)k * B->count, B->pc_axis[k], B->pc_out[k], B->pc_bytes[k],
+                         B->pc_flops[k], s);
         if (st) return st;
     }
-    return grouped(B, B->d_pcl + (size_t)j * B->count, B->pc_axis[5], B->pc_bytes[5], B->pc_flops[5], s);
+    return grouped(B, B->d_pcl + (size_t)j * B->count, B->pc_axis[5], B->pc_out[5], B->pc_bytes[5],
+                   B->pc_flops[5], s);
 }
 
 void vec_launch_count() { stats_count_launch(); }
@@ -501,6 +505,7 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
         for (int k = 0; k < 5; ++k) {
             mv[k * C + i] = tmp[k];
             B->mv_axis[k] = axes[k];
+            B->mv_out[k] = tmp[k].out_mode;
             B->mv_bytes[k] += by[k];
             B->mv_flops[k] += fl[k];
         }
@@ -510,6 +515,7 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
                 for (int k = 0; k < 6; ++k) {
                     if (k < 5) pc[k * C + i] = tmp[k];
                     B->pc_axis[k] = axes[k];
+                    B->pc_out[k] = tmp[k].out_mode;
                     B->pc_bytes[k] += by[k];
                     B->pc_flops[k] += fl[k];
                 }

@@ -149,16 +149,39 @@ void set_geometry(Params& P, const int n[3], int axis) {
 
 bool attr_done = false;
 
+template <bool G, int KM, int OM>
+bool set_attr_one() {
+    return cudaFuncSetAttribute(axis_gemm_kernel<G, KM, OM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                SMEM_BYTES) == cudaSuccess;
+}
+
 int set_attrs() {
     if (!attr_done) {
-        if (cudaFuncSetAttribute(axis_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(axis_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
-                cudaSuccess)
-            return set_error(TFDE_ECUDA, "cudaFuncSetAttribute(smem) failed");
+        const bool ok = set_attr_one<false, 0, OUT_F32>() && set_attr_one<false, 0, OUT_HILO>() &&
+                        set_attr_one<false, 1, OUT_F32>() && set_attr_one<false, 1, OUT_HILO>() &&
+                        set_attr_one<true, 0, OUT_F32>() && set_attr_one<true, 0, OUT_HILO>() &&
+                        set_attr_one<true, 1, OUT_F32>() && set_attr_one<true, 1, OUT_HILO>();
+        if (!ok) return set_error(TFDE_ECUDA, "cudaFuncSetAttribute(smem) failed");
         attr_done = true;
     }
     return TFDE_OK;
+}
+
+// The kernel instance for (layout, output mode).
+template <bool G>
+void launch_instance(int kmajor, int out_mode, unsigned grid, cudaStream_t s, const Params& p0, const Params* groups,
+                     const long long* gstart, int ngroups, const int* gactive) {
+    if (kmajor) {
+        if (out_mode == OUT_F32)
+            axis_gemm_kernel<G, 1, OUT_F32><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(p0, groups, gstart, ngroups, gactive);
+        else
+            axis_gemm_kernel<G, 1, OUT_HILO><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(p0, groups, gstart, ngroups, gactive);
+    } else {
+        if (out_mode == OUT_F32)
+            axis_gemm_kernel<G, 0, OUT_F32><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(p0, groups, gstart, ngroups, gactive);
+        else
+            axis_gemm_kernel<G, 0, OUT_HILO><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(p0, groups, gstart, ngroups, gactive);
+    }
 }
 
 int launch(const Params& P, cudaStream_t s, double bytes, double flops) {
@@ -167,7 +190,7 @@ int launch(const Params& P, cudaStream_t s, double bytes, double flops) {
     long long grid = total < num_sms() ? total : num_sms();
     if (grid < 1) grid = 1;
     void* tok = stats_tc_begin(s, TFDE_KIND_SPLIT);
-    axis_gemm_kernel<false><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(P, nullptr, nullptr, 0, nullptr);
+    launch_instance<false>(P.b_kmajor, P.out_mode, (unsigned)grid, s, P, nullptr, nullptr, 0, nullptr);
     cudaError_t e = cudaGetLastError();
     stats_tc_end(tok, s, TFDE_KIND_SPLIT, bytes, flops);
     if (e != cudaSuccess) return set_error(TFDE_ECUDA, std::string("axis_gemm_kernel launch: ") + cudaGetErrorString(e));
@@ -175,7 +198,7 @@ int launch(const Params& P, cudaStream_t s, double bytes, double flops) {
 }
 
 int launch_grouped(const Params* groups, const long long* gstart, int ngroups, long long total, int b_kmajor,
-                   const int* gactive, int* err, cudaStream_t s, double bytes, double flops) {
+                   int out_mode, const int* gactive, int* err, cudaStream_t s, double bytes, double flops) {
     if (int st = set_attrs()) return st;
     if (total <= 0 || ngroups <= 0) return TFDE_OK;
     Params p0;
@@ -183,10 +206,11 @@ int launch_grouped(const Params* groups, const long long* gstart, int ngroups, l
     p0.ntiles = total;
     p0.mhalves = 1;
     p0.b_kmajor = b_kmajor;
+    p0.out_mode = out_mode;
     p0.err = err;
     long long grid = total < num_sms() ? total : num_sms();
     void* tok = stats_tc_begin(s, TFDE_KIND_SPLIT);
-    axis_gemm_kernel<true><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(p0, groups, gstart, ngroups, gactive);
+    launch_instance<true>(b_kmajor, out_mode, (unsigned)grid, s, p0, groups, gstart, ngroups, gactive);
     cudaError_t e = cudaGetLastError();
     stats_tc_end(tok, s, TFDE_KIND_SPLIT, bytes, flops);
     if (e != cudaSuccess)

@@ -22,9 +22,10 @@ void set_geometry(Params& P, const int n[3], int axis);
 int launch(const Params& P, cudaStream_t s, double bytes, double flops);
 // One persistent launch over the tiles of `ngroups` contractions along the same
 // axis (descriptors and tile offsets gstart[0..ngroups] in device memory,
-// total = gstart[ngroups]); groups with gactive[g] == 0 are skipped.
+// total = gstart[ngroups]); groups with gactive[g] == 0 are skipped.  All
+// groups share the layout b_kmajor and the output mode out_mode.
 int launch_grouped(const Params* groups, const long long* gstart, int ngroups, long long total, int b_kmajor,
-                   const int* gactive, int* err, cudaStream_t s, double bytes, double flops);
+                   int out_mode, const int* gactive, int* err, cudaStream_t s, double bytes, double flops);
 
 }  // namespace tc
 }  // namespace tfde

@@ -132,8 +132,9 @@ __device__ __forceinline__ float4 dot_load(const float* __restrict__ w, long lon
 }
 
 // Four consecutive outputs (already scaled) to global memory at element index idx.
+template <int OM>
 __device__ __forceinline__ void store4(const Params& p, long long idx, float v0, float v1, float v2, float v3) {
-    if (p.out_mode == OUT_F32) {
+    if constexpr (OM == OUT_F32) {
         *reinterpret_cast<float4*>(p.out_f32 + idx) = make_float4(v0, v1, v2, v3);
     } else {
         const __nv_bfloat162 h01 = __floats2bfloat162_rn(v0, v1);
@@ -151,8 +152,9 @@ __device__ __forceinline__ void store4(const Params& p, long long idx, float v0,
         *reinterpret_cast<uint2*>(p.out_lo + idx) = lv;
     }
 }
+template <int OM>
 __device__ __forceinline__ void store1(const Params& p, long long idx, float v) {
-    if (p.out_mode == OUT_F32) {
+    if constexpr (OM == OUT_F32) {
         p.out_f32[idx] = v;
     } else {
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
@@ -177,8 +179,10 @@ __device__ __forceinline__ int find_group(const long long* __restrict__ gstart, 
 // same axis) whose descriptors sit in global memory; tile t belongs to group
 // g with gstart[g] <= t < gstart[g+1], and groups with gactive[g] == 0 are
 // skipped by all three roles alike.  p0 then carries only the common fields
-// (b_kmajor, err) and ntiles = gstart[ngroups], mhalves = 1.
-template <bool GROUPED>
+// (err) and ntiles = gstart[ngroups], mhalves = 1.  KM (= Params::b_kmajor)
+// and OM (= Params::out_mode) are compile-time so that each instance carries
+// one straight-line epilogue.
+template <bool GROUPED, int KM, int OM>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     axis_gemm_kernel(const __grid_constant__ Params p0, const Params* __restrict__ groups,
                      const long long* __restrict__ gstart, int ngroups, const int* __restrict__ gactive) {
@@ -217,7 +221,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
     const long long total = p0.ntiles * p0.mhalves;
     int* const err = p0.err;
-    const int b_kmajor = p0.b_kmajor;
+    constexpr int b_kmajor = KM;
 
     if (warp < PRODUCERS) {
         if (lane == 0) {
@@ -414,7 +418,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         if (m0 + i8 * 4 < p.n) vmask |= 1u << i8;
                 }
                 if (cnt0 == 0) vmask = 0;
-                const bool dot = p.dot_vec != nullptr;
+                const bool dot = OM == OUT_F32 && p.dot_vec != nullptr;
                 float4 w[8];
                 if (dot) {
 #pragma unroll
@@ -426,54 +430,57 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
                 for (int j = 0; j < 32; ++j) stg[lane * EPI_STRIDE + j] = p.alpha * __uint_as_float(r[j]);
                 __syncwarp();
-                float U[4] = {0.f, 0.f, 0.f, 0.f}, V[4] = {0.f, 0.f, 0.f, 0.f};
+                // Every staged value of this lane first (32 independent shared
+                // loads), then the conversions and stores: with two epilogue
+                // warps per scheduler the chunk is latency-bound, so the
+                // independent work is laid out for the scheduler to overlap.
+                float v[8][4];
+#pragma unroll
+                for (int i8 = 0; i8 < 8; ++i8)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        v[i8][k] = b_kmajor ? stg[(cq + k) * EPI_STRIDE + i8 * 4 + rsub]
+                                            : stg[(i8 * 4 + rsub) * EPI_STRIDE + cq + k];
+                __syncwarp();   // the staging buffer is free for the next chunk
                 if (!b_kmajor && p.lam_ra && (vmask & 1u)) {   // rows ascend: none valid if the first is not
                     const int c = (int)((tile * (BN / 64) + c0 / 64) % p.nbc) * 64 + (c0 & 63) + cq;
+                    float U[4] = {0.f, 0.f, 0.f, 0.f}, V[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
                         if (c + k < p.C) {
                             U[k] = __ldg(p.lam_U + c + k);
                             V[k] = __ldg(p.lam_V + c + k);
                         }
+#pragma unroll
+                    for (int i8 = 0; i8 < 8; ++i8)
+                        if ((vmask >> i8) & 1u) {
+                            const int m = mrow0 + i8 * 4 + rsub;
+                            const float ra = __ldg(p.lam_ra + m), rb = __ldg(p.lam_rb + m);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) v[i8][k] = __fdividef(v[i8][k], ra * U[k] + rb * V[k]);
+                        }
                 }
 #pragma unroll
                 for (int i8 = 0; i8 < 8; ++i8) {
                     const int cnt = cnt0;
                     if ((vmask >> i8) & 1u) {
-                        float v[4];
-                        if (b_kmajor) {
-                            const int jl = i8 * 4 + rsub;
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) v[k] = stg[(cq + k) * EPI_STRIDE + jl];
-                        } else {
-                            const int rr = i8 * 4 + rsub;
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) v[k] = stg[rr * EPI_STRIDE + cq + k];
-                            if (p.lam_ra) {
-                                const int m = mrow0 + rr;
-                                const float ra = __ldg(p.lam_ra + m), rb = __ldg(p.lam_rb + m);
-#pragma unroll
-                                for (int k = 0; k < 4; ++k) v[k] = __fdividef(v[k], ra * U[k] + rb * V[k]);
-                            }
-                        }
                         const long long idx = oidx0 + i8 * ostep;
                         if (cnt == 4) {
-                            store4(p, idx, v[0], v[1], v[2], v[3]);
+                            store4<OM>(p, idx, v[i8][0], v[i8][1], v[i8][2], v[i8][3]);
                         } else {
 #pragma unroll
                             for (int k = 0; k < 3; ++k)
-                                if (k < cnt) store1(p, idx + k, v[k]);
+                                if (k < cnt) store1<OM>(p, idx + k, v[i8][k]);
                         }
                         if (dot) {
 #pragma unroll
                             for (int k = 1; k < 4; ++k)
-                                if (k >= cnt) v[k] = 0.f;   // outside the grid (may be 0 / 0 above)
+                                if (k >= cnt) v[i8][k] = 0.f;   // outside the grid (may be 0 / 0 above)
                             const float4 wv = w[i8];
-                            da.add(fmaf(v[0], wv.x, fmaf(v[1], wv.y, fmaf(v[2], wv.z, v[3] * wv.w))));
+                            da.add(fmaf(v[i8][0], wv.x, fmaf(v[i8][1], wv.y, fmaf(v[i8][2], wv.z, v[i8][3] * wv.w))));
                         }
                     }
                 }
-                __syncwarp();
             }
             tc_fence_before();
             __syncwarp();
