@@ -266,7 +266,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
         }
     } else if (warp == MMA_WARP) {
         if (lane == 0) {
-            const uint32_t idesc = instr_desc(BM, BN, p.b_kmajor ? 0 : 1);
+            // One MMA multiplies operator slice sa by up to four input slices at
+            // once: the input slices sit at a uniform stride in a stage (the next
+            // 64 rows on x, the next 64-column atom on y / z), so tb0..tb0+nn-1
+            // form one B operand with N = 64 nn, and their products land in the
+            // adjacent accumulators of diagonals sa+tb0 .. sa+tb0+nn-1.  A slice
+            // is read once per 256 columns instead of once per 64.
+            uint32_t idesc[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) idesc[c] = instr_desc(BM, BN * (c + 1), p.b_kmajor ? 0 : 1);
             // descriptor templates at stage 0, tile 0; the start-address field
             // (bits 0..13, address >> 4) absorbs every in-smem offset without carry
             const uint64_t a_desc0 = smem_desc(smem_u32(stages), 16, 512, 4);
@@ -292,16 +300,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                         for (int sa = 0; sa < MAXS; ++sa) {
                             if (sa >= na) break;
 #pragma unroll
-                            for (int tb = 0; tb < MAXS; ++tb) {
-                                if (sa + tb > D) break;
+                            for (int tb0 = 0; tb0 < MAXS; tb0 += 4) {
+                                if (sa + tb0 > D) break;
+                                const int nn = min(4, D - sa - tb0 + 1);   // input slices in this MMA
 #pragma unroll
                                 for (int k16 = 0; k16 < BK / 16; ++k16) {
                                     const uint64_t ad = ad_s + (uint64_t)((sa * A_TILE_BYTES + k16 * 32) >> 4);
-                                    const uint64_t bd = bd_s + (uint64_t)((tb * B_TILE_BYTES) >> 4) + k16 * b_k16;
-                                    // the first product into each diagonal of a tile (segment 0,
-                                    // k-block 0, digit 0 of the operator, first K step) overwrites it
+                                    const uint64_t bd = bd_s + (uint64_t)((tb0 * B_TILE_BYTES) >> 4) + k16 * b_k16;
+                                    // the first products into the diagonals of a tile (segment 0,
+                                    // k-block 0, digit 0 of the operator, first K step) overwrite them
                                     const uint32_t acc = (first && sa == 0 && k16 == 0) ? 0u : 1u;
-                                    umma_bf16(tmem_base + (uint32_t)((sa + tb) * BN), ad, bd, idesc, acc);
+                                    umma_bf16(tmem_base + (uint32_t)((sa + tb0) * BN), ad, bd, idesc[nn - 1], acc);
                                 }
                             }
                         }
