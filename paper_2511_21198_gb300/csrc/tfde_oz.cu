@@ -490,9 +490,13 @@ void oz_slice(const tfde_problem* P, int axis, const double* x0, const double* x
         slice_x_kernel<<<grid_for(v.lines * 32), 256, 0, s>>>(x0, P->n[0], v.lines, S, M->oz_planes[0], N,
                                                                M->oz_lexp, mass_out);
     } else {
-        // 32 lines per block while both inputs fit in 200 KB of shared memory, else 16
+        // 16 lines per block: with 64 KB of staged lines per block (n = 256, two
+        // inputs) three blocks share an SM, so one block's loads overlap another's
+        // digit writes; 32-line blocks would fill an SM alone and alternate the
+        // two phases.  32 lines only for short lines, where a 16-line block would
+        // stage too little to stream well.
         const int nin = x1 ? 2 : 1;
-        const bool wide = (size_t)nin * v.n * 32 * 8 <= 200 * 1024;
+        const bool wide = (size_t)nin * v.n * 16 * 8 < 16 * 1024;
         const int LB = wide ? 32 : 16;
         const size_t smem = (size_t)nin * v.n * LB * 8;
         long long blocks = (v.lines + LB - 1) / LB;

@@ -347,6 +347,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                 for (int d = 0; d < MAXS; ++d)
                     if (d < S) tmem_ld8(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(d * BN + c0), r[d]);
                 tmem_wait_ld();
+                if (cc == 24) {
+                    // last TMEM read of this tile: the accumulators go back to the MMA
+                    // warp now, so the next tile's products overlap this chunk's epilogue
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(tempty);
+                }
                 long long lbase, base;
                 int cbase = 0;
                 if (p.b_kmajor) {
@@ -436,9 +443,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                 }
                 __syncwarp();
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(tempty);
         }
         if (p.norm2) {
 #pragma unroll
