@@ -35,17 +35,26 @@ constexpr int BN = 64;
 constexpr int BK = 32;
 constexpr int MAXS = 7;          // digit slices per operand (D + 1, D <= 6)
 constexpr int MAXSEG = 2;
-constexpr int STAGES = 2;
+constexpr int STAGES = 3;         // ring slots; a launch uses as many of them as fit (see stage_count)
 constexpr int A_TILE_BYTES = BM * BK * 2;                        // 8 KB
 constexpr int B_TILE_BYTES = BN * BK * 2;                        // 4 KB
-constexpr int STAGE_BYTES = MAXS * (A_TILE_BYTES + B_TILE_BYTES);  // 84 KB
+constexpr int STAGE_BYTES = MAXS * (A_TILE_BYTES + B_TILE_BYTES);  // 84 KB: largest stage (7 slices)
+// The ring holds three 72 KB stages (6 slices) or two 84 KB ones (7 slices): a
+// stage holds S operator tiles then S input tiles, S = the launch's slices.
+constexpr int RING_BYTES = 3 * 6 * (A_TILE_BYTES + B_TILE_BYTES);    // 216 KB
 constexpr int EPI_WARPS = 8;
 constexpr int PRODUCERS = 4;                                     // TMA issuing warps (boxes dealt round-robin)
 constexpr int MMA_WARP = PRODUCERS;
 constexpr int EPI_WARP0 = PRODUCERS + 1;
 constexpr int NUM_THREADS = 32 * (PRODUCERS + 1 + EPI_WARPS);     // 416
 constexpr int NUM_BARS = 2 * STAGES + 3;
-constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + NUM_BARS * 8 + 16;
+constexpr int SMEM_BYTES = 1024 + RING_BYTES + NUM_BARS * 8 + 16;
+static_assert(2 * STAGE_BYTES <= RING_BYTES, "two stages of the largest slice count fit the ring");
+// stages of S slices in one ring (at most STAGES)
+__host__ __device__ constexpr int stage_count(int S) {
+    return RING_BYTES / (S * (A_TILE_BYTES + B_TILE_BYTES)) < STAGES ? RING_BYTES / (S * (A_TILE_BYTES + B_TILE_BYTES))
+                                                                      : STAGES;
+}
 constexpr uint32_t TMEM_COLS = 512;                              // (D + 1) x 64 <= 448 columns used
 static_assert(SMEM_BYTES <= 232448, "shared memory budget of one CTA");
 
@@ -167,7 +176,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* stages = smem;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RING_BYTES);
     uint64_t* full = bars;
     uint64_t* empty = bars + STAGES;
     uint64_t* tfull = bars + 2 * STAGES;
@@ -180,6 +189,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
     const int S = p.nslices;
     const int D = S - 1;
     const int nkb = (p.n + BK - 1) / BK;
+    const int nst = stage_count(S);                              // ring stages in use
+    const int stage_bytes = S * (A_TILE_BYTES + B_TILE_BYTES);   // 1024-byte multiple
+    const int b_off = S * A_TILE_BYTES;                          // input tiles within a stage
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -211,7 +223,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                     const Segment& G = p.seg[sg];
                     for (int kb = 0; kb < nkb; ++kb) {
                         if (!mbar_wait(&empty[s], ph ^ 1u, p.err)) { ok = false; break; }
-                        uint8_t* st = stages + s * STAGE_BYTES;
+                        uint8_t* st = stages + s * stage_bytes;
                         // box i of this stage (operator slices, then input slices) belongs to issuer i % PRODUCERS
                         uint32_t mine = 0;
                         if (G.merged) {
@@ -221,7 +233,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                             mbar_expect_tx(&full[s], mine);
                             if (pw == 0) tma_load_3d(st, &G.amapm, &full[s], kb * BK, mh * BM, 0);
                             if (pw == 1 % PRODUCERS) {
-                                uint8_t* dst = st + MAXS * A_TILE_BYTES;
+                                uint8_t* dst = st + b_off;
                                 if (p.b_kmajor) {
                                     tma_load_3d(dst, &G.bmapm, &full[s], kb * BK, (int)(tile * BN), 0);
                                 } else if (p.bm_rank == 4) {
@@ -234,7 +246,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                             }
                             filled |= 1u << s;
                             if (ph) last_ph |= 1u << s; else last_ph &= ~(1u << s);
-                            if (++s == STAGES) { s = 0; ph ^= 1u; }
+                            if (++s == nst) { s = 0; ph ^= 1u; }
                             continue;
                         }
                         for (int i = pw; i < G.na + G.nb; i += PRODUCERS)
@@ -246,7 +258,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                                 continue;
                             }
                             const int b = i - G.na;
-                            uint8_t* dst = st + MAXS * A_TILE_BYTES + b * B_TILE_BYTES;
+                            uint8_t* dst = st + b_off + b * B_TILE_BYTES;
                             if (p.b_kmajor) {
                                 tma_load_2d(dst, &G.bmaps[b], &full[s], kb * BK, (int)(tile * BN));
                             } else {
@@ -257,11 +269,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                         }
                         filled |= 1u << s;
                         if (ph) last_ph |= 1u << s; else last_ph &= ~(1u << s);
-                        if (++s == STAGES) { s = 0; ph ^= 1u; }
+                        if (++s == nst) { s = 0; ph ^= 1u; }
                     }
                 }
             }
-            for (int i = 0; i < STAGES; ++i)
+            for (int i = 0; i < nst; ++i)
                 if (filled & (1u << i)) mbar_wait(&full[i], (last_ph >> i) & 1u, p.err, false);
         }
     } else if (warp == MMA_WARP) {
@@ -278,8 +290,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
             // descriptor templates at stage 0, tile 0; the start-address field
             // (bits 0..13, address >> 4) absorbs every in-smem offset without carry
             const uint64_t a_desc0 = smem_desc(smem_u32(stages), 16, 512, 4);
-            const uint64_t b_desc0 = p.b_kmajor ? smem_desc(smem_u32(stages + MAXS * A_TILE_BYTES), 16, 512, 4)
-                                                : smem_desc(smem_u32(stages + MAXS * A_TILE_BYTES), 4096, 1024, 2);
+            const uint64_t b_desc0 = p.b_kmajor ? smem_desc(smem_u32(stages + b_off), 16, 512, 4)
+                                                : smem_desc(smem_u32(stages + b_off), 4096, 1024, 2);
             const uint32_t b_k16 = p.b_kmajor ? (32u >> 4) : (2048u >> 4);
             int s = 0;
             uint32_t ph = 0;
@@ -293,8 +305,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                     for (int kb = 0; kb < nkb; ++kb) {
                         if (!mbar_wait(&full[s], ph, p.err)) { ok = false; break; }
                         tc_fence_after();
-                        const uint64_t ad_s = a_desc0 + (uint64_t)((s * STAGE_BYTES) >> 4);
-                        const uint64_t bd_s = b_desc0 + (uint64_t)((s * STAGE_BYTES) >> 4);
+                        const uint64_t ad_s = a_desc0 + (uint64_t)((s * stage_bytes) >> 4);
+                        const uint64_t bd_s = b_desc0 + (uint64_t)((s * stage_bytes) >> 4);
                         const bool first = (sg == 0 && kb == 0);
 #pragma unroll
                         for (int sa = 0; sa < MAXS; ++sa) {
@@ -315,7 +327,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                             }
                         }
                         umma_commit(&empty[s]);
-                        if (++s == STAGES) { s = 0; ph ^= 1u; }
+                        if (++s == nst) { s = 0; ph ^= 1u; }
                     }
                 }
                 if (ok) umma_commit(tfull);
