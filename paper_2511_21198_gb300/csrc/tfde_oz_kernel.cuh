@@ -18,9 +18,11 @@
 //
 // One CTA per SM, persistent over tiles of 128 rows x 64 lines; warps 0..3
 // TMA (the boxes of a stage dealt round-robin to four issuing threads), warp 4
-// TMEM allocation + MMA issue (M=128, N=64, K=16), warps 5..12 epilogue (two
-// per TMEM lane quadrant, 32 columns each).  Bounded waits as in the
-// split-BF16 kernel.
+// TMEM allocation + MMA issue (M=128, N = 64 per input slice, K=16), warps
+// 5..20 epilogue (four per TMEM lane quadrant, 16 columns each, read four at
+// a time: the epilogue is integer-ALU work that cannot overlap the next
+// tile's MMAs, so it gets every warp the register file allows).  Bounded
+// waits as in the split-BF16 kernel.
 #pragma once
 
 #include <cuda.h>
@@ -42,7 +44,9 @@ constexpr int STAGE_BYTES = MAXS * (A_TILE_BYTES + B_TILE_BYTES);  // 84 KB: lar
 // The ring holds three 72 KB stages (6 slices) or two 84 KB ones (7 slices): a
 // stage holds S operator tiles then S input tiles, S = the launch's slices.
 constexpr int RING_BYTES = 3 * 6 * (A_TILE_BYTES + B_TILE_BYTES);    // 216 KB
-constexpr int EPI_WARPS = 8;
+constexpr int EPI_WARPS = 16;
+constexpr int EPI_COLS = BN / (EPI_WARPS / 4);   // columns of a tile per epilogue warp
+constexpr int CH = 4;                             // columns per epilogue chunk
 constexpr int PRODUCERS = 4;                                     // TMA issuing warps (boxes dealt round-robin)
 constexpr int MMA_WARP = PRODUCERS;
 constexpr int EPI_WARP0 = PRODUCERS + 1;
@@ -102,11 +106,10 @@ namespace oz {
 
 using namespace tfde::tc;
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-        : "r"(taddr));
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -337,7 +340,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
         }
     } else {
         const int q = warp & 3;                 // TMEM lane quadrant
-        const int half = (warp - EPI_WARP0) >> 2;   // columns [32 half, 32 half + 32)
+        const int part = (warp - EPI_WARP0) >> 2;   // columns [EPI_COLS part, EPI_COLS (part + 1))
         long long it = 0;
         float nacc = 0.f;                       // this thread's share of the output norm
         for (long long t = blockIdx.x; t < total; t += gridDim.x, ++it) {
@@ -352,14 +355,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
             const int m = mh * BM + 32 * q + lane;
             const bool mvalid = m < p.n;
             const int es = mvalid ? __ldg(p.row_exp + m) : 0;
-            for (int cc = 0; cc < 32; cc += 8) {
-                const int c0 = half * 32 + cc;
-                uint32_t r[MAXS][8];
+            for (int cc = 0; cc < EPI_COLS; cc += CH) {
+                const int c0 = part * EPI_COLS + cc;
+                uint32_t r[MAXS][CH];
 #pragma unroll
                 for (int d = 0; d < MAXS; ++d)
-                    if (d < S) tmem_ld8(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(d * BN + c0), r[d]);
+                    if (d < S) tmem_ld4(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(d * BN + c0), r[d]);
                 tmem_wait_ld();
-                if (cc == 24) {
+                if (cc == EPI_COLS - CH) {
                     // last TMEM read of this tile: the accumulators go back to the MMA
                     // warp now, so the next tile's products overlap this chunk's epilogue
                     tc_fence_before();
@@ -377,17 +380,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                     lbase = (long long)pl * p.C + cbase;
                     base = (long long)pl * p.plane + (long long)m * p.C + cbase;   // column j at + j
                 }
-                // every 8-column chunk is either wholly valid or wholly outside: the
+                // every CH-column chunk is either wholly valid or wholly outside: the
                 // line count (x axis) and the plane width C (y, z axes) are multiples of 8
                 const bool cvalid = p.b_kmajor ? (lbase < p.lines) : (tile < p.nblocks && cbase < p.C);
                 if (mvalid && cvalid) {
-                    // line exponents of the 8 columns: consecutive lines, 32-byte aligned
+                    // line exponents of the CH columns: consecutive lines, 16-byte aligned
                     const int4 e0 = __ldg(reinterpret_cast<const int4*>(p.line_exp + lbase));
-                    const int4 e1 = __ldg(reinterpret_cast<const int4*>(p.line_exp + lbase) + 1);
-                    const int el[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
-                    double o[8];
+                    const int el[CH] = {e0.x, e0.y, e0.z, e0.w};
+                    double o[CH];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
+                    for (int j = 0; j < CH; ++j) {
                         // I = sum_d a_d 2^{7(D-d)} exactly; |a_d| < 2^24
                         if (S == 6) {
                             long long I6 = 0;
@@ -420,7 +422,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                     if (p.b_kmajor) {
                         // lanes are consecutive rows m: each store is one coalesced 256-byte row
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
+                        for (int j = 0; j < CH; ++j) {
                             const long long idx = base + (long long)j * p.n1;
                             double v = o[j];
                             if (p.addend) v = fma(p.addend_sign, p.addend[idx], v);
@@ -431,22 +433,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                             }
                         }
                     } else {
-                        // the 8 columns are 64 contiguous, 64-byte aligned bytes of row m
+                        // the CH columns are 8 CH contiguous, 8 CH-byte aligned bytes of row m
                         double2* dst = reinterpret_cast<double2*>(p.out + base);
                         if (p.addend) {
                             const double2* ad = reinterpret_cast<const double2*>(p.addend + base);
 #pragma unroll
-                            for (int v = 0; v < 4; ++v) {
+                            for (int v = 0; v < CH / 2; ++v) {
                                 const double2 a2 = ad[v];
                                 o[2 * v] = fma(p.addend_sign, a2.x, o[2 * v]);
                                 o[2 * v + 1] = fma(p.addend_sign, a2.y, o[2 * v + 1]);
                             }
                         }
 #pragma unroll
-                        for (int v = 0; v < 4; ++v) dst[v] = make_double2(o[2 * v], o[2 * v + 1]);
+                        for (int v = 0; v < CH / 2; ++v) dst[v] = make_double2(o[2 * v], o[2 * v + 1]);
                         if (p.norm2) {
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) {
+                            for (int j = 0; j < CH; ++j) {
                                 const float f = scaled_f32(o[j], p.norm_shift);
                                 nacc = fmaf(f, f, nacc);
                             }
