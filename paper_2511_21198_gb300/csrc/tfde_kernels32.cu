@@ -132,6 +132,16 @@ __global__ void add32to64_kernel(long long N, double s, const float* __restrict_
         x[i] += s * (double)d[i];
 }
 
+// c64 = s * d32 ; x64 += c64
+__global__ void widen_add32_kernel(long long N, double s, const float* __restrict__ d, double* __restrict__ c,
+                                   double* __restrict__ x) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const double v = s * (double)d[i];
+        c[i] = v;
+        x[i] += v;
+    }
+}
+
 // y64 = (double) v32 * s
 __global__ void widen32_kernel(long long N, const float* __restrict__ v, double s, double* __restrict__ y) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
@@ -203,6 +213,10 @@ void launch_cg_update32(size_t N, const double* num, const double* den, const fl
                         float* r, __nv_bfloat16* rh, __nv_bfloat16* rl, double* rr, cudaStream_t s) {
     stats_count_launch();
     cg_update32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, num, den, p, q, x, r, rh, rl, rr);
+}
+void launch_widen_add32(size_t N, double sc, const float* d, double* c, double* x, cudaStream_t s) {
+    stats_count_launch();
+    widen_add32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, sc, d, c, x);
 }
 void launch_xpay32(size_t N, const double* num, const double* den, const float* z, float* p, __nv_bfloat16* ph,
                    __nv_bfloat16* pl, cudaStream_t s) {

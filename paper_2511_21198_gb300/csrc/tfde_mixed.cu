@@ -241,7 +241,7 @@ enum { D_PQ = 0, D_RR = 1, D_RZ0 = 2, D_RZ1 = 3 };
 // the coefficients alpha = <r,z>/<p,Ap> and beta = <r,z>_new/<r,z> are formed
 // on the device by the update kernels, and the host reads <r, r> once per
 // iteration for the stopping test.
-int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaStream_t s) {
+int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaStream_t s, double* reached = nullptr) {
     MixedState* M = mixed(P);
     const size_t N = P->N;
     float* x = M->f[F_X];
@@ -255,6 +255,7 @@ int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaSt
     launch_reduce_finish(P->red, P->nblk, 1, d + D_RR, s);
     const double rr0 = host_scalar(P, d + D_RR, s, &st);
     if (st) return st;
+    if (reached) *reached = 0.0;
     if (!(rr0 > 0.0) || !std::isfinite(rr0)) return rr0 == 0.0 ? TFDE_OK : set_error(TFDE_ENAN, "non-finite inner residual");
     int rz = D_RZ0;
     MX_TRY(cudaMemsetAsync(d + rz, 0, sizeof(double), s));
@@ -270,6 +271,7 @@ int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaSt
         if (st) return st;
         ++k;
         if (!std::isfinite(rr)) return set_error(TFDE_ENAN, "non-finite inner residual");
+        if (reached) *reached = std::sqrt(rr / rr0);
         if (rr <= theta * theta * rr0) break;
         const int rzn = rz == D_RZ0 ? D_RZ1 : D_RZ0;
         MX_TRY(cudaMemsetAsync(d + rzn, 0, sizeof(double), s));
@@ -577,6 +579,10 @@ int mixed_apply_Pinv(const tfde_problem* P, const double* r, double* z, cudaStre
     return TFDE_OK;
 }
 
+// Measured reduction of the true FP64 residual by one inner split-BF16 solve
+// when the inner solve itself goes further (the split operator's accuracy).
+constexpr double kInnerFloor = 1e-4;
+
 // FP64 iterative refinement around the FP32 / split-BF16 inner PCG.
 int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit, tfde_info* info,
               cudaStream_t s, bool r_given) {
@@ -612,12 +618,36 @@ int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit
         if (theta < 1e-4) theta = 1e-4;
         launch_scale64to32(P->N, r64, 1.0 / nr, M->f[F_R], M->hi[PL_R], M->lo[PL_R], M->f[F_X], s);
         int it = 0;
-        if ((st = inner_pcg(P, theta, maxit - loc.iters, &it, s))) return st;
+        double reached = 1.0;
+        if ((st = inner_pcg(P, theta, maxit - loc.iters, &it, s, &reached))) return st;
         loc.iters += it;
         loc.refine_sweeps++;
-        launch_add32to64(P->N, nr, M->f[F_X], x, s);
         const double nr_old = nr;
-        if ((st = accurate_residual(P, b, x, r64, &nr, tol, nb, s))) return st;
+        // A sweep that cannot end the solve updates the residual by its correction,
+        // r <- r - A c with c = ||r|| d, instead of recomputing b - A x.  The
+        // product is exact-integer at few digits: c is small (||c|| ~ ||r|| / ||A||
+        // relative to x), so 4 or 5 slices give it to far below the next sweep's
+        // target.  A sweep predicted to end the solve (the inner solve reduces the
+        // true residual by about max(its own reduction, kInnerFloor)) recomputes
+        // the true residual b - A x at full width, and so does any sweep whose
+        // updated residual meets the tolerance: the residual that stops the
+        // solve, and that the next CN step chains on, is always the recomputed one.
+        const bool predict_done = nr * std::max(reached, kInnerFloor) <= tol * nb;
+        if (!predict_done) {
+            double* c64 = P->w[tfde_problem::W_T];
+            launch_widen_add32(P->N, nr, M->f[F_X], c64, x, s);   // c = nr d, x += c
+            const int shift = -std::ilogb(nb);
+            double* acc = P->red_out + kNormsSlot + 2;
+            const int sc = nr <= 1e-2 * nb ? 4 : (nr <= nb ? 5 : oz_slices_for_tol(tol));
+            if ((st = accurate_apply_ex(P, TFDE_OP_A, c64, r64, -1, r64, 1.0, s, sc, acc, shift))) return st;
+            MX_TRY(cudaMemcpyAsync(P->red_host, acc, sizeof(double), cudaMemcpyDeviceToHost, s));
+            MX_TRY(cudaStreamSynchronize(s));
+            nr = std::ldexp(std::sqrt(P->red_host[0]), -shift);
+            if (nr <= tol * nb && (st = accurate_residual(P, b, x, r64, &nr, tol, nb, s))) return st;
+        } else {
+            launch_add32to64(P->N, nr, M->f[F_X], x, s);
+            if ((st = accurate_residual(P, b, x, r64, &nr, tol, nb, s))) return st;
+        }
         stall = (nr > 0.5 * nr_old) ? stall + 1 : 0;
         if (stall >= 2) {
             // refinement stopped contracting: finish with FP64 inner solves

@@ -15,6 +15,8 @@ void launch_dot32(size_t N, const float* a, const float* b, double* part, int nb
 // alpha = *num / *den on the device; x += alpha p; r -= alpha q; split r; *rr += r.r
 void launch_cg_update32(size_t N, const double* num, const double* den, const float* p, const float* q, float* x,
                         float* r, __nv_bfloat16* rh, __nv_bfloat16* rl, double* rr, cudaStream_t s);
+// c64 = sc * d32; x64 += c64
+void launch_widen_add32(size_t N, double sc, const float* d, double* c, double* x, cudaStream_t s);
 // beta = *num / *den on the device; p = z + beta p; split p
 void launch_xpay32(size_t N, const double* num, const double* den, const float* z, float* p, __nv_bfloat16* ph,
                    __nv_bfloat16* pl, cudaStream_t s);

@@ -391,11 +391,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
 #pragma unroll
                     for (int j = 0; j < CH; ++j) {
                         // I = sum_d a_d 2^{7(D-d)} exactly; |a_d| < 2^24
-                        if (S == 6) {
+                        if (S <= 6) {   // |I| < 2^{24 + 35}: int64
                             long long I6 = 0;
 #pragma unroll
                             for (int dd = 0; dd < 6; ++dd)
-                                I6 = I6 * 128 + (long long)__float2int_rn(__uint_as_float(r[dd][j]));
+                                if (dd < S) I6 = I6 * 128 + (long long)__float2int_rn(__uint_as_float(r[dd][j]));
                             o[j] = i64_ldexp(p.value_sign < 0 ? -I6 : I6, es + el[j] - 7 * (D + 2));
                             continue;
                         }
