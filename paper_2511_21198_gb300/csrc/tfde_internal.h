@@ -127,6 +127,9 @@ struct tfde_problem {
     int guess_order = 0;
     // ||b||^2, ||r_0||^2 of the last cn_prepare in red_out[NORMS_SLOT..+1] (device)
     bool norms_ready = false;
+    // W_T holds A_N of the mixed solver's final iterate (set by its last
+    // full-width residual, cleared by anything else that writes W_T)
+    bool an_ready = false;
     int hist = 0;                 // valid history entries (0..2)
     double* H[2][2] = {};         // H[k] = {u^{m-2-k}, A u^{m-2-k}}
 };

@@ -285,11 +285,12 @@ int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaSt
 
 // r = b - A x (accurate) and ||r||, the norm accumulated by the last pass of
 // the contraction with the terms scaled by 2^-ilogb(nb).
+// With an_out, A_N x also goes there (from the z-pass digit slicing).
 int accurate_residual(const tfde_problem* P, const double* b, const double* x, double* r, double* nr, double tol,
-                      double nb, cudaStream_t s) {
+                      double nb, cudaStream_t s, double* an_out = nullptr) {
     const int shift = nb > 0.0 && std::isfinite(nb) ? -std::ilogb(nb) : 0;
     double* acc = P->red_out + kNormsSlot + 2;
-    int st = accurate_apply_ex(P, TFDE_OP_A, x, r, -1, b, 1.0, s, oz_slices_for_tol(tol), acc, shift);
+    int st = accurate_apply_ex(P, TFDE_OP_A, x, r, -1, b, 1.0, s, oz_slices_for_tol(tol), acc, shift, an_out);
     if (st) return st;
     MX_TRY(cudaMemcpyAsync(P->red_host, acc, sizeof(double), cudaMemcpyDeviceToHost, s));
     MX_TRY(cudaStreamSynchronize(s));
@@ -583,6 +584,47 @@ int mixed_apply_Pinv(const tfde_problem* P, const double* r, double* z, cudaStre
 // when the inner solve itself goes further (the split operator's accuracy).
 constexpr double kInnerFloor = 1e-4;
 
+// b - A x at full width, with A_N x into W_T for the next chained CN step.
+int exact_residual(tfde_problem* P, const double* b, const double* x, double* r64, double* nr, double tol, double nb,
+                   cudaStream_t s) {
+    const int st = accurate_residual(P, b, x, r64, nr, tol, nb, s, P->w[tfde_problem::W_T]);
+    P->an_ready = st == TFDE_OK;
+    return st;
+}
+
+// x += c, c = nr d (d: the inner solution in F_X for the residual scaled by
+// 1/nr), and the new residual with its norm into r64 / *nr.  A sweep that
+// cannot end the solve (predicted true reduction `pred`) updates the
+// residual by its correction, r <- r - A c, instead of recomputing b - A x:
+// the product is exact-integer at few digits, because c is small (about
+// ||r|| / ||A|| against ||x||), so 4 or 5 slices give it far below the next
+// sweep's target.  A sweep predicted to end the solve recomputes the true
+// residual b - A x at full width, and so does any sweep whose updated
+// residual meets the tolerance: the residual that stops the solve, and that
+// the next CN step chains on, is always the recomputed one.
+int apply_correction(tfde_problem* P, const double* b, double* x, double* r64, double* nr, double pred, double tol,
+                     double nb, cudaStream_t s) {
+    MixedState* M = mixed(P);
+    int st;
+    double* an = P->w[tfde_problem::W_T];
+    if (*nr * pred > tol * nb) {
+        double* c64 = an;
+        P->an_ready = false;
+        launch_widen_add32(P->N, *nr, M->f[F_X], c64, x, s);   // c = nr d, x += c
+        const int shift = -std::ilogb(nb);
+        double* acc = P->red_out + kNormsSlot + 2;
+        const int sc = *nr <= 1e-2 * nb ? 4 : (*nr <= nb ? 5 : oz_slices_for_tol(tol));
+        if ((st = accurate_apply_ex(P, TFDE_OP_A, c64, r64, -1, r64, 1.0, s, sc, acc, shift))) return st;
+        MX_TRY(cudaMemcpyAsync(P->red_host, acc, sizeof(double), cudaMemcpyDeviceToHost, s));
+        MX_TRY(cudaStreamSynchronize(s));
+        *nr = std::ldexp(std::sqrt(P->red_host[0]), -shift);
+        if (*nr <= tol * nb) return exact_residual(P, b, x, r64, nr, tol, nb, s);
+        return TFDE_OK;
+    }
+    launch_add32to64(P->N, *nr, M->f[F_X], x, s);
+    return exact_residual(P, b, x, r64, nr, tol, nb, s);
+}
+
 // FP64 iterative refinement around the FP32 / split-BF16 inner PCG.
 int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit, tfde_info* info,
               cudaStream_t s, bool r_given) {
@@ -603,7 +645,7 @@ int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit
     double nr;
     if (r_given) {
         nr = std::sqrt(rr0);
-    } else if ((st = accurate_residual(P, b, x, r64, &nr, tol, nb, s))) {
+    } else if ((st = exact_residual(P, b, x, r64, &nr, tol, nb, s))) {
         return st;
     }
     loc.relres0 = nr / nb;
@@ -623,35 +665,12 @@ int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit
         loc.iters += it;
         loc.refine_sweeps++;
         const double nr_old = nr;
-        // A sweep that cannot end the solve updates the residual by its correction,
-        // r <- r - A c with c = ||r|| d, instead of recomputing b - A x.  The
-        // product is exact-integer at few digits: c is small (||c|| ~ ||r|| / ||A||
-        // relative to x), so 4 or 5 slices give it to far below the next sweep's
-        // target.  A sweep predicted to end the solve (the inner solve reduces the
-        // true residual by about max(its own reduction, kInnerFloor)) recomputes
-        // the true residual b - A x at full width, and so does any sweep whose
-        // updated residual meets the tolerance: the residual that stops the
-        // solve, and that the next CN step chains on, is always the recomputed one.
-        const bool predict_done = nr * std::max(reached, kInnerFloor) <= tol * nb;
-        if (!predict_done) {
-            double* c64 = P->w[tfde_problem::W_T];
-            launch_widen_add32(P->N, nr, M->f[F_X], c64, x, s);   // c = nr d, x += c
-            const int shift = -std::ilogb(nb);
-            double* acc = P->red_out + kNormsSlot + 2;
-            const int sc = nr <= 1e-2 * nb ? 4 : (nr <= nb ? 5 : oz_slices_for_tol(tol));
-            if ((st = accurate_apply_ex(P, TFDE_OP_A, c64, r64, -1, r64, 1.0, s, sc, acc, shift))) return st;
-            MX_TRY(cudaMemcpyAsync(P->red_host, acc, sizeof(double), cudaMemcpyDeviceToHost, s));
-            MX_TRY(cudaStreamSynchronize(s));
-            nr = std::ldexp(std::sqrt(P->red_host[0]), -shift);
-            if (nr <= tol * nb && (st = accurate_residual(P, b, x, r64, &nr, tol, nb, s))) return st;
-        } else {
-            launch_add32to64(P->N, nr, M->f[F_X], x, s);
-            if ((st = accurate_residual(P, b, x, r64, &nr, tol, nb, s))) return st;
-        }
+        if ((st = apply_correction(P, b, x, r64, &nr, std::max(reached, kInnerFloor), tol, nb, s))) return st;
         stall = (nr > 0.5 * nr_old) ? stall + 1 : 0;
         if (stall >= 2) {
             // refinement stopped contracting: finish with FP64 inner solves
             loc.fallback = 1;
+            P->an_ready = false;
             tfde_info sub{};
             status = pcg64(P, b, x, tol, maxit > loc.iters ? maxit - loc.iters : 1, &sub, s, false);
             loc.iters += sub.iters;
@@ -689,7 +708,7 @@ int mixed_pgmres(tfde_problem* P, const double* b, double* x, int restart, doubl
     double nr;
     if (r_given) {
         nr = std::sqrt(rr0);
-    } else if ((st = accurate_residual(P, b, x, r64, &nr, tol, nb, s))) {
+    } else if ((st = exact_residual(P, b, x, r64, &nr, tol, nb, s))) {
         return st;
     }
     loc.relres0 = nr / nb;
@@ -709,9 +728,9 @@ int mixed_pgmres(tfde_problem* P, const double* b, double* x, int restart, doubl
         loc.iters += it;
         loc.restarts++;
         loc.refine_sweeps++;
-        launch_add32to64(P->N, nr, M->f[F_X], x, s);
         const double nr_old = nr;
-        if ((st = accurate_residual(P, b, x, r64, &nr, tol, nb, s))) return st;
+        const double pred = est_ratio > 0.0 ? std::max(est_ratio * ratio, kInnerFloor) : 1.0;
+        if ((st = apply_correction(P, b, x, r64, &nr, pred, tol, nb, s))) return st;
         if (est_ratio > 0.0) {
             const double observed = (nr / nr_old) / est_ratio;
             ratio = observed > 1.0 ? observed : 1.0;
@@ -720,6 +739,7 @@ int mixed_pgmres(tfde_problem* P, const double* b, double* x, int restart, doubl
         if (stall >= 2) {
             // refinement stopped contracting: finish with FP64 inner cycles
             loc.fallback = 1;
+            P->an_ready = false;
             tfde_info sub{};
             status = pgmres64(P, b, x, restart, tol, maxit > loc.iters ? maxit - loc.iters : 1, &sub, s, false);
             loc.iters += sub.iters;

@@ -119,9 +119,12 @@ int accurate_apply(const tfde_problem* P, int op, const double* x, double* y, cu
 // y = vsign * (operator x) + asign * addend (addend may be null)
 // norm2 (optional, device): receives sum_i (y_i 2^norm_shift)^2 accumulated
 // in FP32 terms by the last pass (24-bit terms: enough for stopping tests).
+// an_out (optional, op = A only): receives A_N x = A3 A2 A1 x, formed exactly
+// from the fixed-point digits in the z-pass slicing (error ~2^{-7 slices} of
+// the line maxima), at the cost of one extra FP64 write.
 int accurate_apply_ex(const tfde_problem* P, int op, const double* x, double* y, int vsign, const double* addend,
                       double asign, cudaStream_t s, int slices = OZ_SLICES, double* norm2 = nullptr,
-                      int norm_shift = 0);
+                      int norm_shift = 0, double* an_out = nullptr);
 // Digit slices for a refinement residual at relative tolerance tol: 6 (42
 // bits, a worst-case error n 2^-42 < 1.1e-10 of |A||x| for n <= 448) while
 // tol >= 1e-9, else 7.

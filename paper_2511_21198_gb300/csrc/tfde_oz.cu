@@ -596,7 +596,7 @@ int oz_contract(const tfde_problem* P, int axis, const OzSegSpec* segs, int nseg
 
 // y = vsign * (A x | (2 A_N - A) x | (A - A_N) x) [+ asign * addend], FP64-accurate.
 int accurate_apply_ex(const tfde_problem* P, int op, const double* x, double* y, int vsign, const double* addend,
-                      double asign, cudaStream_t s, int slices, double* norm2, int norm_shift) {
+                      double asign, cudaStream_t s, int slices, double* norm2, int norm_shift, double* an_out) {
     if (slices < 2 || slices > OZ_SLICES) slices = OZ_SLICES;
     MixedState* M = mixed(P);
     const bool rhs = (op & 1) != 0;
@@ -615,8 +615,8 @@ int accurate_apply_ex(const tfde_problem* P, int op, const double* x, double* y,
     oz_slice(P, 1, ta, tw, M->oz_shift[1], te, slices, s);
     OzSegSpec sc[2] = {{&M->oz_y_mass_c, 0}, {rhs ? &M->oz_y_minus : &M->oz_y_plus, 1}};
     if ((st = oz_contract(P, 1, sc, 2, 1, nullptr, 0.0, tc_, slices, s))) return st;
-    // z pass: y = A3 c +- G3 e
-    oz_slice(P, 2, tc_, te, M->oz_shift[2], nullptr, slices, s);
+    // z pass: y = A3 c +- G3 e (and, for op = A, A_N x = A3 e in the slicing)
+    oz_slice(P, 2, tc_, te, M->oz_shift[2], (op == TFDE_OP_A) ? an_out : nullptr, slices, s);
     OzSegSpec sy[2] = {{&M->oz_z_mass_c, 0}, {rhs ? &M->oz_z_minus : &M->oz_z_plus, 1}};
     if (norm2) OZ_TRY(cudaMemsetAsync(norm2, 0, sizeof(double), s));
     return oz_contract(P, 2, sy, 2, vsign, addend, asign, y, slices, s, norm2, norm_shift);

@@ -300,7 +300,7 @@ int mixed_pcg(tfde_problem*, const double*, double*, double, int, tfde_info*, cu
 int mixed_pgmres(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t, bool);
 int accurate_apply(const tfde_problem*, int, const double*, double*, cudaStream_t);
 int accurate_apply_ex(const tfde_problem*, int, const double*, double*, int, const double*, double, cudaStream_t, int,
-                      double*, int);
+                      double*, int, double*);
 
 // A_N u into `out` (the three tridiagonal sweeps in one pass).
 static void mass_apply(const tfde_problem* P, const double* u, double* out, cudaStream_t s) {
@@ -320,7 +320,11 @@ int cn_prepare(tfde_problem* P, const double* u_prev, const double* F, const dou
     const bool mixed_prec = P->prec == TFDE_MIXED;
     const bool guess_is_prev = (x0 == nullptr || x0 == u_prev);
     int st;
-    mass_apply(P, u_prev, an, s);
+    // A_N u_prev: left in W_T by the mixed solver's last (full-width) residual
+    // of a chained step, whose z-pass digit slicing forms it exactly; else the
+    // fused stencil
+    if (!(chained && P->an_ready)) mass_apply(P, u_prev, an, s);
+    P->an_ready = false;
     bool guess_in_place = false;  // x0 already written into u_next, r = b - A x0
     if (used_guess) *used_guess = 0;
     if (chained && P->guess_order > 0 && u_next == u_prev && !guess) {
@@ -360,7 +364,7 @@ int cn_prepare(tfde_problem* P, const double* u_prev, const double* F, const dou
         double* rg = P->w[tfde_problem::W_Z];
         launch_axpbypz_f64(P->N, 1.0, guess, -1.0, u_prev, d, s);
         if (mixed_prec) {
-            st = accurate_apply_ex(P, TFDE_OP_A, d, rg, -1, r, 1.0, s, 7, nullptr, 0);
+            st = accurate_apply_ex(P, TFDE_OP_A, d, rg, -1, r, 1.0, s, 7, nullptr, 0, nullptr);
         } else {
             st = apply_A64(P, TFDE_OP_A, d, rg, s);
             if (!st) launch_axpby_f64(P->N, 1.0, r, -1.0, rg, s);
