@@ -104,7 +104,7 @@ void gemm_params(const tfde_problem* P, int axis, const SegSpec* segs, int nseg,
     prm.out_mode = out_mode;
     prm.alpha = alpha;
     prm.out_f32 = out_f32;
-    if (out_mode == tc::OUT_HILO) {
+    if (out_mode == tc::OUT_HILO || out_mode == tc::OUT_XPAY) {
         prm.out_hi = M->hi[out_plane];
         prm.out_lo = M->lo[out_plane];
     }
@@ -205,6 +205,37 @@ int fast_matvec(const tfde_problem* P, int op, float* q32, cudaStream_t s, int o
 }
 
 // z32 = S_N Lambda^{-1} S_N r, r given as the split plane pair PL_R.
+// z = S_N Lambda^{-1} S_N r (plane PL_R) fused into the CG direction update:
+// *rz += <r, z>, accumulated in the Lambda pass as <t, Lambda^{-1} t> with
+// t = S_N r (S_N is orthogonal), and p = z + beta p with beta = *num / *den
+// (0 when den is null), written by the last pass to p32 and to the split
+// planes PL_P: z itself is never stored.
+int fast_precond_cg(const tfde_problem* P, float* p32, double* rz, const double* num, const double* den,
+                    cudaStream_t s) {
+    Pass ps[6];
+    const int np = precond_passes(ps);
+    for (int i = 0; i < np; ++i) {
+        const Pass& q = ps[i];
+        const bool last = i + 1 == np;
+        tc::Params prm;
+        double bytes, flops;
+        gemm_params(P, q.axis, q.seg, q.nseg, last ? tc::OUT_XPAY : q.out_mode, 1.f, last ? p32 : nullptr,
+                    last ? PL_P : q.out_plane, q.lam, prm, &bytes, &flops);
+        if (q.lam) {
+            prm.dot_lam = 1;
+            prm.dot_out = rz;
+        }
+        if (last) {
+            prm.xp_num = num;
+            prm.xp_den = den;
+            bytes += 8.0 * (double)P->N;   // the old p in, the split planes out
+        }
+        mixed(P)->gemm_launches++;
+        if (int st = tc::launch(prm, s, bytes, flops)) return st;
+    }
+    return TFDE_OK;
+}
+
 int fast_precond(const tfde_problem* P, float* z32, cudaStream_t s, const float* dot_vec = nullptr,
                  double* dot_out = nullptr) {
     Pass ps[6];
@@ -237,16 +268,16 @@ enum { D_PQ = 0, D_RR = 1, D_RZ0 = 2, D_RZ1 = 3 };
 // Inner PCG on FP32 vectors: A d = r32 (r32 and its split planes prepared by
 // the caller, x32 = 0), until ||r|| <= theta ||r32_0|| or maxit.  The inner
 // products ride on the kernels that produce their operands (<p, Ap> in the
-// operator's last pass, <r, z> in the preconditioner's, <r, r> in the update),
-// the coefficients alpha = <r,z>/<p,Ap> and beta = <r,z>_new/<r,z> are formed
-// on the device by the update kernels, and the host reads <r, r> once per
-// iteration for the stopping test.
+// operator's last pass, <r, z> in the preconditioner's Lambda pass, <r, r> in
+// the update), the coefficients alpha = <r,z>/<p,Ap> and beta =
+// <r,z>_new/<r,z> are formed on the device (alpha by the update kernel, beta
+// by the preconditioner's last pass, which writes p = z + beta p directly),
+// and the host reads <r, r> once per iteration for the stopping test.
 int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaStream_t s, double* reached = nullptr) {
     MixedState* M = mixed(P);
     const size_t N = P->N;
     float* x = M->f[F_X];
     float* r = M->f[F_R];
-    float* z = M->f[F_Z];
     float* p = M->f[F_P];
     float* q = M->f[F_Q];
     double* d = M->dsc;
@@ -259,9 +290,7 @@ int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaSt
     if (!(rr0 > 0.0) || !std::isfinite(rr0)) return rr0 == 0.0 ? TFDE_OK : set_error(TFDE_ENAN, "non-finite inner residual");
     int rz = D_RZ0;
     MX_TRY(cudaMemsetAsync(d + rz, 0, sizeof(double), s));
-    if ((st = fast_precond(P, z, s, r, d + rz))) return st;
-    MX_TRY(cudaMemcpyAsync(p, z, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    launch_split32(N, p, M->hi[PL_P], M->lo[PL_P], s);
+    if ((st = fast_precond_cg(P, p, d + rz, nullptr, nullptr, s))) return st;   // p = z
     int k = 0;
     while (k < maxit) {
         MX_TRY(cudaMemsetAsync(d + D_PQ, 0, 2 * sizeof(double), s));   // <p, Ap> and <r, r>
@@ -275,8 +304,8 @@ int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaSt
         if (rr <= theta * theta * rr0) break;
         const int rzn = rz == D_RZ0 ? D_RZ1 : D_RZ0;
         MX_TRY(cudaMemsetAsync(d + rzn, 0, sizeof(double), s));
-        if ((st = fast_precond(P, z, s, r, d + rzn))) return st;
-        launch_xpay32(N, d + rzn, d + rz, z, p, M->hi[PL_P], M->lo[PL_P], s);
+        // p = z + beta p, beta = <r, z>_new / <r, z>
+        if ((st = fast_precond_cg(P, p, d + rzn, d + rzn, d + rz, s))) return st;
         rz = rzn;
     }
     *iters = k;

@@ -160,7 +160,8 @@ int set_attrs() {
         const bool ok = set_attr_one<false, 0, OUT_F32>() && set_attr_one<false, 0, OUT_HILO>() &&
                         set_attr_one<false, 1, OUT_F32>() && set_attr_one<false, 1, OUT_HILO>() &&
                         set_attr_one<true, 0, OUT_F32>() && set_attr_one<true, 0, OUT_HILO>() &&
-                        set_attr_one<true, 1, OUT_F32>() && set_attr_one<true, 1, OUT_HILO>();
+                        set_attr_one<true, 1, OUT_F32>() && set_attr_one<true, 1, OUT_HILO>() &&
+                        set_attr_one<false, 0, OUT_XPAY>() && set_attr_one<false, 1, OUT_XPAY>();
         if (!ok) return set_error(TFDE_ECUDA, "cudaFuncSetAttribute(smem) failed");
         attr_done = true;
     }
@@ -171,6 +172,17 @@ int set_attrs() {
 template <bool G>
 void launch_instance(int kmajor, int out_mode, unsigned grid, cudaStream_t s, const Params& p0, const Params* groups,
                      const long long* gstart, int ngroups, const int* gactive) {
+    if constexpr (!G) {   // the fused direction update exists for single launches only
+        if (out_mode == OUT_XPAY) {
+            if (kmajor)
+                axis_gemm_kernel<G, 1, OUT_XPAY><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(p0, groups, gstart, ngroups,
+                                                                                        gactive);
+            else
+                axis_gemm_kernel<G, 0, OUT_XPAY><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(p0, groups, gstart, ngroups,
+                                                                                        gactive);
+            return;
+        }
+    }
     if (kmajor) {
         if (out_mode == OUT_F32)
             axis_gemm_kernel<G, 1, OUT_F32><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(p0, groups, gstart, ngroups, gactive);

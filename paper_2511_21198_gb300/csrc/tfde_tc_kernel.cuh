@@ -68,7 +68,11 @@ struct Segment {
     int pa[MAXPAIR], pb[MAXPAIR];
 };
 
-enum { OUT_F32 = 0, OUT_HILO = 1 };
+// OUT_XPAY: p = Y + beta p (beta = *xp_num / *xp_den, 0 when xp_den is null),
+// written both as FP32 (out_f32 = p, read and written in place) and as the
+// split planes (out_hi, out_lo): the CG direction update fused into the last
+// pass of the preconditioner.
+enum { OUT_F32 = 0, OUT_HILO = 1, OUT_XPAY = 2 };
 
 struct Params {
     CUtensorMap amaps[4];
@@ -98,6 +102,11 @@ struct Params {
     // optional fused inner product (OUT_F32 only): *dot_out += sum out[i] dot_vec[i]
     const float* dot_vec;
     double* dot_out;
+    // optional, with lam_ra (z-axis DST pass): *dot_out += sum t[i] (t / Lambda)[i],
+    // t the pass's output before the Lambda^{-1} scale: <r, S Lambda^{-1} S r>
+    int dot_lam;
+    const double* xp_num;   // OUT_XPAY: beta = *xp_num / *xp_den
+    const double* xp_den;
     int* err;
 };
 
@@ -131,12 +140,24 @@ __device__ __forceinline__ float4 dot_load(const float* __restrict__ w, long lon
     return r;
 }
 
+// The old values of cnt (0..4) consecutive in/out elements at idx (zero
+// beyond cnt), by plain loads: this kernel overwrites them afterwards.
+__device__ __forceinline__ float4 old_load(const float* w, long long idx, int cnt) {
+    if (cnt == 4) return *reinterpret_cast<const float4*>(w + idx);
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (cnt > 0) r.x = w[idx];
+    if (cnt > 1) r.y = w[idx + 1];
+    if (cnt > 2) r.z = w[idx + 2];
+    return r;
+}
+
 // Four consecutive outputs (already scaled) to global memory at element index idx.
 template <int OM>
 __device__ __forceinline__ void store4(const Params& p, long long idx, float v0, float v1, float v2, float v3) {
     if constexpr (OM == OUT_F32) {
         *reinterpret_cast<float4*>(p.out_f32 + idx) = make_float4(v0, v1, v2, v3);
     } else {
+        if constexpr (OM == OUT_XPAY) *reinterpret_cast<float4*>(p.out_f32 + idx) = make_float4(v0, v1, v2, v3);
         const __nv_bfloat162 h01 = __floats2bfloat162_rn(v0, v1);
         const __nv_bfloat162 h23 = __floats2bfloat162_rn(v2, v3);
         const float2 f01 = __bfloat1622float2(h01);
@@ -157,6 +178,7 @@ __device__ __forceinline__ void store1(const Params& p, long long idx, float v) 
     if constexpr (OM == OUT_F32) {
         p.out_f32[idx] = v;
     } else {
+        if constexpr (OM == OUT_XPAY) p.out_f32[idx] = v;
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         p.out_hi[idx] = hi;
         p.out_lo[idx] = __float2bfloat16_rn(v - __bfloat162float(hi));
@@ -365,6 +387,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int cq = (lane & 7) * 4;        // ... and 4 consecutive elements per lane
         long long it = 0;
         DotAcc da;                            // fused inner product (single launches only)
+        float xp_beta = 0.f;                  // OUT_XPAY coefficient
+        if constexpr (OM == OUT_XPAY) {
+            if (p0.xp_den) xp_beta = (float)(__ldg(p0.xp_num) / __ldg(p0.xp_den));
+        }
         for (long long t = blockIdx.x; t < total; t += gridDim.x) {
             long long lt = t;
             const Params* pp = &p0;
@@ -419,11 +445,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 }
                 if (cnt0 == 0) vmask = 0;
                 const bool dot = OM == OUT_F32 && p.dot_vec != nullptr;
-                float4 w[8];
+                float4 w[8];   // dot_vec (fused inner product) or the old p (OUT_XPAY) at the outputs
                 if (dot) {
 #pragma unroll
                     for (int i8 = 0; i8 < 8; ++i8)
                         w[i8] = dot_load(p.dot_vec, oidx0 + i8 * ostep, (vmask >> i8) & 1u ? cnt0 : 0);
+                }
+                if constexpr (OM == OUT_XPAY) {
+                    if (xp_beta != 0.f) {
+#pragma unroll
+                        for (int i8 = 0; i8 < 8; ++i8)
+                            w[i8] = old_load(p.out_f32, oidx0 + i8 * ostep, (vmask >> i8) & 1u ? cnt0 : 0);
+                    }
                 }
                 uint32_t r[32];
                 tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN + c0), r);
@@ -456,9 +489,26 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         if ((vmask >> i8) & 1u) {
                             const int m = mrow0 + i8 * 4 + rsub;
                             const float ra = __ldg(p.lam_ra + m), rb = __ldg(p.lam_rb + m);
+                            float tl = 0.f;
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) v[i8][k] = __fdividef(v[i8][k], ra * U[k] + rb * V[k]);
+                            for (int k = 0; k < 4; ++k) {
+                                const float t = v[i8][k];
+                                v[i8][k] = __fdividef(t, ra * U[k] + rb * V[k]);
+                                if (k < cnt0) tl = fmaf(t, v[i8][k], tl);
+                            }
+                            if (p.dot_lam) da.add(tl);
                         }
+                }
+                if constexpr (OM == OUT_XPAY) {
+                    if (xp_beta != 0.f) {
+#pragma unroll
+                        for (int i8 = 0; i8 < 8; ++i8) {
+                            v[i8][0] = fmaf(xp_beta, w[i8].x, v[i8][0]);
+                            v[i8][1] = fmaf(xp_beta, w[i8].y, v[i8][1]);
+                            v[i8][2] = fmaf(xp_beta, w[i8].z, v[i8][2]);
+                            v[i8][3] = fmaf(xp_beta, w[i8].w, v[i8][3]);
+                        }
+                    }
                 }
 #pragma unroll
                 for (int i8 = 0; i8 < 8; ++i8) {
