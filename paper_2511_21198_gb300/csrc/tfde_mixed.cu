@@ -273,7 +273,10 @@ enum { D_PQ = 0, D_RR = 1, D_RZ0 = 2, D_RZ1 = 3 };
 // <r,z>_new/<r,z> are formed on the device (alpha by the update kernel, beta
 // by the preconditioner's last pass, which writes p = z + beta p directly),
 // and the host reads <r, r> once per iteration for the stopping test.
-int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaStream_t s, double* reached = nullptr) {
+// rr0_known > 0: the caller's ||r32||^2 (the refinement scales r to unit
+// norm), which spares a reduction and a host read.
+int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaStream_t s, double* reached = nullptr,
+              double rr0_known = 0.0) {
     MixedState* M = mixed(P);
     const size_t N = P->N;
     float* x = M->f[F_X];
@@ -281,11 +284,14 @@ int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaSt
     float* p = M->f[F_P];
     float* q = M->f[F_Q];
     double* d = M->dsc;
-    int st;
-    launch_dot32(N, r, r, P->red, P->nblk, s);
-    launch_reduce_finish(P->red, P->nblk, 1, d + D_RR, s);
-    const double rr0 = host_scalar(P, d + D_RR, s, &st);
-    if (st) return st;
+    int st = TFDE_OK;
+    double rr0 = rr0_known;
+    if (!(rr0 > 0.0)) {
+        launch_dot32(N, r, r, P->red, P->nblk, s);
+        launch_reduce_finish(P->red, P->nblk, 1, d + D_RR, s);
+        rr0 = host_scalar(P, d + D_RR, s, &st);
+        if (st) return st;
+    }
     if (reached) *reached = 0.0;
     if (!(rr0 > 0.0) || !std::isfinite(rr0)) return rr0 == 0.0 ? TFDE_OK : set_error(TFDE_ENAN, "non-finite inner residual");
     int rz = D_RZ0;
@@ -690,7 +696,8 @@ int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit
         launch_scale64to32(P->N, r64, 1.0 / nr, M->f[F_R], M->hi[PL_R], M->lo[PL_R], M->f[F_X], s);
         int it = 0;
         double reached = 1.0;
-        if ((st = inner_pcg(P, theta, maxit - loc.iters, &it, s, &reached))) return st;
+        // r32 = r / ||r||: unit norm up to the FP32 rounding of its elements
+        if ((st = inner_pcg(P, theta, maxit - loc.iters, &it, s, &reached, 1.0))) return st;
         loc.iters += it;
         loc.refine_sweeps++;
         const double nr_old = nr;
