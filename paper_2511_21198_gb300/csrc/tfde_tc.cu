@@ -168,31 +168,43 @@ int set_attrs() {
     return TFDE_OK;
 }
 
+// Launch with programmatic stream serialisation: the kernel's set-up (barrier
+// initialisation, TMEM allocation) may start while the previous kernel on the
+// stream drains; the kernel waits for that kernel's completion
+// (griddepcontrol.wait) before its first global memory access.
+template <bool G, int KM, int OM>
+void launch_one(unsigned grid, cudaStream_t s, const Params& p0, const Params* groups, const long long* gstart,
+                int ngroups, const int* gactive) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(NUM_THREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, axis_gemm_kernel<G, KM, OM>, p0, groups, gstart, ngroups, gactive);
+}
+
 // The kernel instance for (layout, output mode).
 template <bool G>
 void launch_instance(int kmajor, int out_mode, unsigned grid, cudaStream_t s, const Params& p0, const Params* groups,
                      const long long* gstart, int ngroups, const int* gactive) {
     if constexpr (!G) {   // the fused direction update exists for single launches only
         if (out_mode == OUT_XPAY) {
-            if (kmajor)
-                axis_gemm_kernel<G, 1, OUT_XPAY><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(p0, groups, gstart, ngroups,
-                                                                                        gactive);
-            else
-                axis_gemm_kernel<G, 0, OUT_XPAY><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(p0, groups, gstart, ngroups,
-                                                                                        gactive);
+            if (kmajor) launch_one<G, 1, OUT_XPAY>(grid, s, p0, groups, gstart, ngroups, gactive);
+            else launch_one<G, 0, OUT_XPAY>(grid, s, p0, groups, gstart, ngroups, gactive);
             return;
         }
     }
     if (kmajor) {
-        if (out_mode == OUT_F32)
-            axis_gemm_kernel<G, 1, OUT_F32><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(p0, groups, gstart, ngroups, gactive);
-        else
-            axis_gemm_kernel<G, 1, OUT_HILO><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(p0, groups, gstart, ngroups, gactive);
+        if (out_mode == OUT_F32) launch_one<G, 1, OUT_F32>(grid, s, p0, groups, gstart, ngroups, gactive);
+        else launch_one<G, 1, OUT_HILO>(grid, s, p0, groups, gstart, ngroups, gactive);
     } else {
-        if (out_mode == OUT_F32)
-            axis_gemm_kernel<G, 0, OUT_F32><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(p0, groups, gstart, ngroups, gactive);
-        else
-            axis_gemm_kernel<G, 0, OUT_HILO><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(p0, groups, gstart, ngroups, gactive);
+        if (out_mode == OUT_F32) launch_one<G, 0, OUT_F32>(grid, s, p0, groups, gstart, ngroups, gactive);
+        else launch_one<G, 0, OUT_HILO>(grid, s, p0, groups, gstart, ngroups, gactive);
     }
 }
 

@@ -240,6 +240,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // launched with programmatic stream serialisation: the set-up above may
+    // overlap the previous kernel, nothing below touches global memory before
+    // that kernel has completed; the next kernel may begin its own set-up now
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     const long long total = p0.ntiles * p0.mhalves;
     int* const err = p0.err;
