@@ -51,7 +51,7 @@ constexpr int PRODUCERS = 4;                                     // TMA issuing 
 constexpr int MMA_WARP = PRODUCERS;
 constexpr int EPI_WARP0 = PRODUCERS + 1;
 constexpr int NUM_THREADS = 32 * (PRODUCERS + 1 + EPI_WARPS);     // 416
-constexpr int NUM_BARS = 2 * STAGES + 3;
+constexpr int NUM_BARS = 2 * STAGES + 5;
 constexpr int SMEM_BYTES = 1024 + RING_BYTES + NUM_BARS * 8 + 16;
 static_assert(2 * STAGE_BYTES <= RING_BYTES, "two stages of the largest slice count fit the ring");
 // stages of S slices in one ring (at most STAGES)
@@ -182,9 +182,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RING_BYTES);
     uint64_t* full = bars;
     uint64_t* empty = bars + STAGES;
-    uint64_t* tfull = bars + 2 * STAGES;
-    uint64_t* tempty = bars + 2 * STAGES + 1;
-    uint64_t* mma_done = bars + 2 * STAGES + 2;
+    uint64_t* tfull = bars + 2 * STAGES;        // [2]
+    uint64_t* tempty = bars + 2 * STAGES + 2;   // [2]
+    uint64_t* mma_done = bars + 2 * STAGES + 4;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NUM_BARS);
 
     const int warp = threadIdx.x >> 5;
@@ -193,6 +193,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
     const int D = S - 1;
     const int nkb = (p.n + BK - 1) / BK;
     const int nst = stage_count(S);                              // ring stages in use
+    // TMEM buffers: two when the S diagonals of a tile fit in half of TMEM
+    // (S <= 4), so that the epilogue of one tile overlaps the next tile's MMAs
+    const int nbuf = S * BN * 2 <= (int)TMEM_COLS ? 2 : 1;
     const int stage_bytes = S * (A_TILE_BYTES + B_TILE_BYTES);   // 1024-byte multiple
     const int b_off = S * A_TILE_BYTES;                          // input tiles within a stage
 
@@ -201,8 +204,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
             mbar_init(&full[s], PRODUCERS);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(tfull, 1);
-        mbar_init(tempty, EPI_WARPS);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], EPI_WARPS);
+        }
         mbar_init(mma_done, 1);
         mbar_fence_init();
     }
@@ -301,7 +306,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
             bool ok = true;
             long long it = 0;
             for (long long t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
-                if (!mbar_wait(tempty, ((uint32_t)it & 1u) ^ 1u, p.err)) { ok = false; break; }
+                const int buf = (int)(it % nbuf);
+                const uint32_t use = (uint32_t)(it / nbuf);
+                const uint32_t dbase = tmem_base + (uint32_t)(buf * (TMEM_COLS / 2));
+                if (!mbar_wait(&tempty[buf], (use & 1u) ^ 1u, p.err)) { ok = false; break; }
                 tc_fence_after();
                 for (int sg = 0; sg < p.nseg && ok; ++sg) {
                     const int na = p.seg[sg].na;
@@ -325,7 +333,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                                     // the first products into the diagonals of a tile (segment 0,
                                     // k-block 0, digit 0 of the operator, first K step) overwrite them
                                     const uint32_t acc = (first && sa == 0 && k16 == 0) ? 0u : 1u;
-                                    umma_bf16(tmem_base + (uint32_t)((sa + tb0) * BN), ad, bd, idesc[nn - 1], acc);
+                                    umma_bf16(dbase + (uint32_t)((sa + tb0) * BN), ad, bd, idesc[nn - 1], acc);
                                 }
                             }
                         }
@@ -333,7 +341,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                         if (++s == nst) { s = 0; ph ^= 1u; }
                     }
                 }
-                if (ok) umma_commit(tfull);
+                if (ok) umma_commit(&tfull[buf]);
             }
             umma_commit(mma_done);
             mbar_wait(mma_done, 0, p.err, false);
@@ -344,8 +352,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
         long long it = 0;
         float nacc = 0.f;                       // this thread's share of the output norm
         for (long long t = blockIdx.x; t < total; t += gridDim.x, ++it) {
+            const int buf = (int)(it % nbuf);
+            const uint32_t use = (uint32_t)(it / nbuf);
+            const uint32_t dbase = tmem_base + (uint32_t)(buf * (TMEM_COLS / 2));
             int ok = 1;
-            if (lane == 0) ok = mbar_wait(tfull, (uint32_t)it & 1u, p.err) ? 1 : 0;
+            if (lane == 0) ok = mbar_wait(&tfull[buf], use & 1u, p.err) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             __syncwarp();
@@ -360,14 +371,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                 uint32_t r[MAXS][CH];
 #pragma unroll
                 for (int d = 0; d < MAXS; ++d)
-                    if (d < S) tmem_ld4(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(d * BN + c0), r[d]);
+                    if (d < S) tmem_ld4(dbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(d * BN + c0), r[d]);
                 tmem_wait_ld();
                 if (cc == EPI_COLS - CH) {
                     // last TMEM read of this tile: the accumulators go back to the MMA
                     // warp now, so the next tile's products overlap this chunk's epilogue
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(tempty);
+                    if (lane == 0) mbar_arrive(&tempty[buf]);
                 }
                 long long lbase, base;
                 int cbase = 0;
