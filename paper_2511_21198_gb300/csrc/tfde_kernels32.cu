@@ -85,6 +85,66 @@ __global__ __launch_bounds__(kT) void cg_update32_kernel(long long N, const doub
     if (threadIdx.x == 0) atomicAdd(rr, t);
 }
 
+// alpha = num / den; r -= alpha q ; (rh, rl) = split(r) ; *rr += r.r ; alpha
+// (double) to *alpha_out for the later combination of the solution
+__global__ __launch_bounds__(kT) void cg_update_r32_kernel(long long N, const double* __restrict__ num,
+                                                           const double* __restrict__ den,
+                                                           const float* __restrict__ q, float* __restrict__ r,
+                                                           __nv_bfloat16* __restrict__ rh,
+                                                           __nv_bfloat16* __restrict__ rl, double* __restrict__ rr,
+                                                           double* __restrict__ alpha_out) {
+    __shared__ float s_alpha;
+    if (threadIdx.x == 0) {
+        const double a = num[0] / den[0];
+        s_alpha = (float)a;
+        if (blockIdx.x == 0) *alpha_out = (double)(float)a;   // the value the update used
+    }
+    __syncthreads();
+    const float alpha = s_alpha;
+    long long lo, hi;
+    chunk(N, lo, hi);
+    KSum k;
+    for (long long i = lo + threadIdx.x; i < hi; i += kT) {
+        const float ri = fmaf(-alpha, q[i], r[i]);
+        r[i] = ri;
+        split(ri, rh[i], rl[i]);
+        k.add(ri * ri);
+    }
+    const double t = block_sum64((double)k.s - (double)k.c);
+    if (threadIdx.x == 0) atomicAdd(rr, t);
+}
+
+// d = (x32 when fold) + sum_j alpha_j p_j (FP32, in the order of the
+// directions, as the per-iteration update x += alpha p would form it); then
+// c64 = sc d and x64 += c64 (c64 set), x64 += sc d (x64 only), or acc32 = d
+struct CombineArgs {
+    int cnt;
+    int fold;
+    const float* p[kPRing];
+    const double* alpha[kPRing];
+};
+__global__ void pcg_combine_kernel(long long N, CombineArgs a, const float* __restrict__ x32, double sc,
+                                   double* __restrict__ c64, double* __restrict__ x64, float* __restrict__ acc32) {
+    __shared__ float s_al[kPRing];
+    if (threadIdx.x < a.cnt) s_al[threadIdx.x] = (float)*a.alpha[threadIdx.x];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        float d = a.fold ? x32[i] : 0.f;
+#pragma unroll
+        for (int j = 0; j < kPRing; ++j)
+            if (j < a.cnt) d = fmaf(s_al[j], a.p[j][i], d);
+        if (acc32) {
+            acc32[i] = d;
+        } else if (c64) {
+            const double v = sc * (double)d;
+            c64[i] = v;
+            x64[i] += v;
+        } else {
+            x64[i] += sc * (double)d;
+        }
+    }
+}
+
 // beta = num / den (device scalars); p = z + beta p ; (ph, pl) = split(p)
 __global__ void xpay32_kernel(long long N, const double* __restrict__ num, const double* __restrict__ den,
                               const float* __restrict__ z, float* __restrict__ p, __nv_bfloat16* __restrict__ ph,
@@ -213,6 +273,23 @@ void launch_cg_update32(size_t N, const double* num, const double* den, const fl
                         float* r, __nv_bfloat16* rh, __nv_bfloat16* rl, double* rr, cudaStream_t s) {
     stats_count_launch();
     cg_update32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, num, den, p, q, x, r, rh, rl, rr);
+}
+void launch_cg_update_r32(size_t N, const double* num, const double* den, const float* q, float* r,
+                          __nv_bfloat16* rh, __nv_bfloat16* rl, double* rr, double* alpha_out, cudaStream_t s) {
+    stats_count_launch();
+    cg_update_r32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, num, den, q, r, rh, rl, rr, alpha_out);
+}
+void launch_pcg_combine(size_t N, const PcgPending& pend, const float* x32, double sc, double* c64, double* x64,
+                        float* acc32, cudaStream_t s) {
+    stats_count_launch();
+    CombineArgs a;
+    a.cnt = pend.cnt;
+    a.fold = pend.fold ? 1 : 0;
+    for (int j = 0; j < kPRing; ++j) {
+        a.p[j] = j < pend.cnt ? pend.p[j] : nullptr;
+        a.alpha[j] = j < pend.cnt ? pend.alpha[j] : nullptr;
+    }
+    pcg_combine_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, a, x32, sc, c64, x64, acc32);
 }
 void launch_widen_add32(size_t N, double sc, const float* d, double* c, double* x, cudaStream_t s) {
     stats_count_launch();

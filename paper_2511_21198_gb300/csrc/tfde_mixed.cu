@@ -208,10 +208,10 @@ int fast_matvec(const tfde_problem* P, int op, float* q32, cudaStream_t s, int o
 // z = S_N Lambda^{-1} S_N r (plane PL_R) fused into the CG direction update:
 // *rz += <r, z>, accumulated in the Lambda pass as <t, Lambda^{-1} t> with
 // t = S_N r (S_N is orthogonal), and p = z + beta p with beta = *num / *den
-// (0 when den is null), written by the last pass to p32 and to the split
-// planes PL_P: z itself is never stored.
-int fast_precond_cg(const tfde_problem* P, float* p32, double* rz, const double* num, const double* den,
-                    cudaStream_t s) {
+// (0 when den is null; p_old the previous direction), written by the last
+// pass to p32 and to the split planes PL_P: z itself is never stored.
+int fast_precond_cg(const tfde_problem* P, float* p32, const float* p_old, double* rz, const double* num,
+                    const double* den, cudaStream_t s) {
     Pass ps[6];
     const int np = precond_passes(ps);
     for (int i = 0; i < np; ++i) {
@@ -228,6 +228,7 @@ int fast_precond_cg(const tfde_problem* P, float* p32, double* rz, const double*
         if (last) {
             prm.xp_num = num;
             prm.xp_den = den;
+            prm.xp_old = p_old;
             bytes += 8.0 * (double)P->N;   // the old p in, the split planes out
         }
         mixed(P)->gemm_launches++;
@@ -274,17 +275,23 @@ enum { D_PQ = 0, D_RR = 1, D_RZ0 = 2, D_RZ1 = 3 };
 // by the preconditioner's last pass, which writes p = z + beta p directly),
 // and the host reads <r, r> once per iteration for the stopping test.
 // rr0_known > 0: the caller's ||r32||^2 (the refinement scales r to unit
-// norm), which spares a reduction and a host read.
-int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaStream_t s, double* reached = nullptr,
-              double rr0_known = 0.0) {
+// norm), which spares a reduction and a host read.  The solution is not
+// updated per iteration: the directions p_j and their alpha_j stay in a ring
+// of kPRing vectors, folded into F_X when the ring is full, and *pend
+// describes what is left (d = fold ? F_X : 0, + sum alpha_j p_j), combined by
+// the caller in the same pass that adds the correction to the FP64 solution:
+// 12 of the update's 28 bytes per point and iteration are saved.
+int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, PcgPending* pend, cudaStream_t s,
+              double* reached = nullptr, double rr0_known = 0.0) {
     MixedState* M = mixed(P);
     const size_t N = P->N;
-    float* x = M->f[F_X];
     float* r = M->f[F_R];
-    float* p = M->f[F_P];
     float* q = M->f[F_Q];
     double* d = M->dsc;
     int st = TFDE_OK;
+    *pend = PcgPending();
+    if (!M->pring) MX_TRY(cudaMalloc((void**)&M->pring, (size_t)kPRing * N * sizeof(float)));
+    auto pbuf = [&](int j) { return M->pring + (size_t)(j % kPRing) * N; };
     double rr0 = rr0_known;
     if (!(rr0 > 0.0)) {
         launch_dot32(N, r, r, P->red, P->nblk, s);
@@ -296,23 +303,44 @@ int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, cudaSt
     if (!(rr0 > 0.0) || !std::isfinite(rr0)) return rr0 == 0.0 ? TFDE_OK : set_error(TFDE_ENAN, "non-finite inner residual");
     int rz = D_RZ0;
     MX_TRY(cudaMemsetAsync(d + rz, 0, sizeof(double), s));
-    if ((st = fast_precond_cg(P, p, d + rz, nullptr, nullptr, s))) return st;   // p = z
-    int k = 0;
+    if ((st = fast_precond_cg(P, pbuf(0), nullptr, d + rz, nullptr, nullptr, s))) return st;   // p_0 = z
+    int k = 0, j0 = 0;   // directions j0 .. k not yet folded
+    bool folded = false;
     while (k < maxit) {
         MX_TRY(cudaMemsetAsync(d + D_PQ, 0, 2 * sizeof(double), s));   // <p, Ap> and <r, r>
-        if ((st = fast_matvec(P, TFDE_OP_A, q, s, -1, p, d + D_PQ))) return st;
-        launch_cg_update32(N, d + rz, d + D_PQ, p, q, x, r, M->hi[PL_R], M->lo[PL_R], d + D_RR, s);
+        if ((st = fast_matvec(P, TFDE_OP_A, q, s, -1, pbuf(k), d + D_PQ))) return st;
+        launch_cg_update_r32(N, d + rz, d + D_PQ, q, r, M->hi[PL_R], M->lo[PL_R], d + D_RR,
+                             d + kAlphaSlot + k % kPRing, s);
         const double rr = host_scalar(P, d + D_RR, s, &st);
         if (st) return st;
         ++k;
         if (!std::isfinite(rr)) return set_error(TFDE_ENAN, "non-finite inner residual");
         if (reached) *reached = std::sqrt(rr / rr0);
-        if (rr <= theta * theta * rr0) break;
+        if (rr <= theta * theta * rr0 || k >= maxit) break;
+        if (k - j0 == kPRing) {
+            // the next direction reuses the oldest slot: fold the window into F_X
+            PcgPending w;
+            w.cnt = kPRing;
+            w.fold = folded;
+            for (int j = 0; j < kPRing; ++j) {
+                w.p[j] = pbuf(j0 + j);
+                w.alpha[j] = d + kAlphaSlot + (j0 + j) % kPRing;
+            }
+            launch_pcg_combine(N, w, M->f[F_X], 0.0, nullptr, nullptr, M->f[F_X], s);
+            folded = true;
+            j0 = k;
+        }
         const int rzn = rz == D_RZ0 ? D_RZ1 : D_RZ0;
         MX_TRY(cudaMemsetAsync(d + rzn, 0, sizeof(double), s));
-        // p = z + beta p, beta = <r, z>_new / <r, z>
-        if ((st = fast_precond_cg(P, p, d + rzn, d + rzn, d + rz, s))) return st;
+        // p_k = z + beta p_{k-1}, beta = <r, z>_new / <r, z>
+        if ((st = fast_precond_cg(P, pbuf(k), pbuf(k - 1), d + rzn, d + rzn, d + rz, s))) return st;
         rz = rzn;
+    }
+    pend->cnt = k - j0;
+    pend->fold = folded;
+    for (int j = 0; j < pend->cnt; ++j) {
+        pend->p[j] = pbuf(j0 + j);
+        pend->alpha[j] = d + kAlphaSlot + (j0 + j) % kPRing;
     }
     *iters = k;
     return check_err(P, s);
@@ -568,8 +596,8 @@ int mixed_init(tfde_problem* P, cudaStream_t s) {
         MX_TRY(cudaMalloc((void**)&M->lam, lam.size() * sizeof(float)));
         MX_TRY(cudaMemcpyAsync(M->lam, lam.data(), lam.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     }
-    MX_TRY(cudaMalloc((void**)&M->dsc, 16 * sizeof(double)));
-    MX_TRY(cudaMemsetAsync(M->dsc, 0, 16 * sizeof(double), s));
+    MX_TRY(cudaMalloc((void**)&M->dsc, 32 * sizeof(double)));
+    MX_TRY(cudaMemsetAsync(M->dsc, 0, 32 * sizeof(double), s));
     MX_TRY(cudaMalloc((void**)&M->err, sizeof(int)));
     MX_TRY(cudaMemsetAsync(M->err, 0, sizeof(int), s));
     MX_TRY(cudaMallocHost((void**)&M->err_host, sizeof(int)));
@@ -585,6 +613,7 @@ void mixed_free(tfde_problem* P) {
     for (int pl = 0; pl < NPL; ++pl) cudaFree(M->hi[pl]);   // lo lives in the same allocation
     for (auto& v : M->f) cudaFree(v);
     cudaFree(M->V32);
+    cudaFree(M->pring);
     cudaFree(M->gm);
     if (M->gm_host) cudaFreeHost(M->gm_host);
     oz_free(M);
@@ -638,14 +667,15 @@ int exact_residual(tfde_problem* P, const double* b, const double* x, double* r6
 // residual meets the tolerance: the residual that stops the solve, and that
 // the next CN step chains on, is always the recomputed one.
 int apply_correction(tfde_problem* P, const double* b, double* x, double* r64, double* nr, double pred, double tol,
-                     double nb, cudaStream_t s) {
+                     double nb, cudaStream_t s, const PcgPending* pend = nullptr) {
     MixedState* M = mixed(P);
     int st;
     double* an = P->w[tfde_problem::W_T];
     if (*nr * pred > tol * nb) {
         double* c64 = an;
         P->an_ready = false;
-        launch_widen_add32(P->N, *nr, M->f[F_X], c64, x, s);   // c = nr d, x += c
+        if (pend) launch_pcg_combine(P->N, *pend, M->f[F_X], *nr, c64, x, nullptr, s);   // c = nr d, x += c
+        else launch_widen_add32(P->N, *nr, M->f[F_X], c64, x, s);
         const int shift = -std::ilogb(nb);
         double* acc = P->red_out + kNormsSlot + 2;
         const int sc = *nr <= 1e-2 * nb ? 4 : (*nr <= nb ? 5 : oz_slices_for_tol(tol));
@@ -656,7 +686,8 @@ int apply_correction(tfde_problem* P, const double* b, double* x, double* r64, d
         if (*nr <= tol * nb) return exact_residual(P, b, x, r64, nr, tol, nb, s);
         return TFDE_OK;
     }
-    launch_add32to64(P->N, *nr, M->f[F_X], x, s);
+    if (pend) launch_pcg_combine(P->N, *pend, M->f[F_X], *nr, nullptr, x, nullptr, s);   // x += nr d
+    else launch_add32to64(P->N, *nr, M->f[F_X], x, s);
     return exact_residual(P, b, x, r64, nr, tol, nb, s);
 }
 
@@ -697,11 +728,12 @@ int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit
         int it = 0;
         double reached = 1.0;
         // r32 = r / ||r||: unit norm up to the FP32 rounding of its elements
-        if ((st = inner_pcg(P, theta, maxit - loc.iters, &it, s, &reached, 1.0))) return st;
+        PcgPending pend;
+        if ((st = inner_pcg(P, theta, maxit - loc.iters, &it, &pend, s, &reached, 1.0))) return st;
         loc.iters += it;
         loc.refine_sweeps++;
         const double nr_old = nr;
-        if ((st = apply_correction(P, b, x, r64, &nr, std::max(reached, kInnerFloor), tol, nb, s))) return st;
+        if ((st = apply_correction(P, b, x, r64, &nr, std::max(reached, kInnerFloor), tol, nb, s, &pend))) return st;
         stall = (nr > 0.5 * nr_old) ? stall + 1 : 0;
         if (stall >= 2) {
             // refinement stopped contracting: finish with FP64 inner solves

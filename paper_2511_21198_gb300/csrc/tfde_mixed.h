@@ -11,10 +11,28 @@
 
 namespace tfde {
 
+constexpr int kPRing = 3;          // inner PCG directions kept before folding into F_X
+constexpr int kAlphaSlot = 8;      // device scalars: alpha of direction j at kAlphaSlot + j % kPRing
+// Deferred inner solution: d = (fold ? F_X : 0) + sum_{j < cnt} alpha_j p_j.
+struct PcgPending {
+    int cnt = 0;
+    bool fold = false;
+    const float* p[kPRing] = {};
+    const double* alpha[kPRing] = {};
+};
+
 void launch_dot32(size_t N, const float* a, const float* b, double* part, int nblk, cudaStream_t s);
 // alpha = *num / *den on the device; x += alpha p; r -= alpha q; split r; *rr += r.r
 void launch_cg_update32(size_t N, const double* num, const double* den, const float* p, const float* q, float* x,
                         float* r, __nv_bfloat16* rh, __nv_bfloat16* rl, double* rr, cudaStream_t s);
+// alpha = *num / *den on the device (also stored to *alpha_out by one thread);
+// r -= alpha q; split r; *rr += r.r  (the solution is left to the combination)
+void launch_cg_update_r32(size_t N, const double* num, const double* den, const float* q, float* r,
+                          __nv_bfloat16* rh, __nv_bfloat16* rl, double* rr, double* alpha_out, cudaStream_t s);
+// d = (fold ? x32 : 0) + sum_j alpha_j p_j ; with c64: c64 = sc d, x64 += c64 ;
+// without: x64 += sc d ; with acc32 (and no x64): acc32 = d (the fold itself)
+void launch_pcg_combine(size_t N, const PcgPending& pend, const float* x32, double sc, double* c64, double* x64,
+                        float* acc32, cudaStream_t s);
 // c64 = sc * d32; x64 += c64
 void launch_widen_add32(size_t N, double sc, const float* d, double* c, double* x, cudaStream_t s);
 // beta = *num / *den on the device; p = z + beta p; split p
@@ -87,6 +105,9 @@ struct MixedState {
     // Hessenberg scratch [h (128) | h2 (128) | |w|^2 | ... | -y (128)]
     float* V32 = nullptr;
     int v32_cap = 0;
+    // inner PCG: the search directions of the current window (the solution is
+    // combined from them once per sweep, see inner_pcg)
+    float* pring = nullptr;   // kPRing vectors
     double* gm = nullptr;
     double* gm_host = nullptr;
     // exact-integer slice path (tfde_oz.cu)

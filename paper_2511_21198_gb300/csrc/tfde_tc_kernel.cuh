@@ -68,10 +68,10 @@ struct Segment {
     int pa[MAXPAIR], pb[MAXPAIR];
 };
 
-// OUT_XPAY: p = Y + beta p (beta = *xp_num / *xp_den, 0 when xp_den is null),
-// written both as FP32 (out_f32 = p, read and written in place) and as the
-// split planes (out_hi, out_lo): the CG direction update fused into the last
-// pass of the preconditioner.
+// OUT_XPAY: p = Y + beta p_old (beta = *xp_num / *xp_den, 0 when xp_den is
+// null), written both as FP32 (out_f32) and as the split planes (out_hi,
+// out_lo): the CG direction update fused into the last pass of the
+// preconditioner.  p_old is xp_old, or out_f32 itself (in place).
 enum { OUT_F32 = 0, OUT_HILO = 1, OUT_XPAY = 2 };
 
 struct Params {
@@ -107,6 +107,7 @@ struct Params {
     int dot_lam;
     const double* xp_num;   // OUT_XPAY: beta = *xp_num / *xp_den
     const double* xp_den;
+    const float* xp_old;    // OUT_XPAY: the old p (null: out_f32 itself, updated in place)
     int* err;
 };
 
@@ -460,7 +461,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     if (xp_beta != 0.f) {
 #pragma unroll
                         for (int i8 = 0; i8 < 8; ++i8)
-                            w[i8] = old_load(p.out_f32, oidx0 + i8 * ostep, (vmask >> i8) & 1u ? cnt0 : 0);
+                            w[i8] = old_load(p.xp_old ? p.xp_old : p.out_f32, oidx0 + i8 * ostep,
+                                             (vmask >> i8) & 1u ? cnt0 : 0);
                     }
                 }
                 uint32_t r[32];

@@ -89,6 +89,32 @@ def test_mixed_pcg_matches_dense_solution(T, n):
         T.tfde_destroy(h)
 
 
+def test_mixed_pcg_long_inner_solves(T):
+    """Inner solves longer than the ring of kept search directions (3): the
+    solution of the inner PCG is combined from the directions and their
+    step lengths, and a window that fills the ring is folded into the FP32
+    accumulator before the oldest direction is overwritten.  A stiff, high
+    order problem from x0 = 0 at a tight tolerance runs sweeps of four or
+    more inner iterations; the result must still match the oracle's
+    solution."""
+    n, d, kp = (32, 24, 16), (0.9, 0.85, 0.95), (1.0, 2.0, 1.5)
+    dt = 1.0
+    h = T.tfde_assemble(T.make_params(n, d, kp, kp, dt), T.TFDE_MIXED)
+    try:
+        op = o.Problem(n=n, delta=d, kp=kp, km=kp, dt=dt)
+        b = inp.uniform_vector(op.shape, 57)
+        tau = o.build_tau(op)
+        xref, _ = o.pcg(lambda v: o.apply_A(op, v), lambda r: o.apply_Pinv(tau, r), b, np.zeros_like(b), 1e-14, 4000)
+        x = to_dev(np.zeros_like(b))
+        info = T.tfde_pcg(h, to_dev(b), x, 1e-12, 4000)
+        assert info.relres <= 1e-12 and info.fallback == 0
+        # at least one sweep ran more inner iterations than the ring holds
+        assert info.iters > 3 * info.refine_sweeps, (info.iters, info.refine_sweeps)
+        assert relerr(to_host(x), xref) < 1e-10
+    finally:
+        T.tfde_destroy(h)
+
+
 def test_mixed_cn_step_tight_parity(T):
     """One CN step from the same u^{m-1}: mixed solve to a 1e-12 true residual
     matches the oracle's 1e-14 PCG solution to <= 1e-10 relative error."""
