@@ -197,11 +197,53 @@ int run_passes(const tfde_problem* P, const Pass* ps, int np, float* out_f32, cu
 
 // q32 = A p (op A) or the RHS operator, p given as the split plane pair PL_P;
 // with out_plane >= 0 the result goes to that split plane pair instead.
+// The operator's passes 0, 1 (x axis: Ghat p, M_x p) and 2, 3 (y axis:
+// M_y a + G_y w, M_y w) are independent pairs along one axis: each pair runs
+// as one grouped persistent launch (the tile list of both), so the second
+// contraction starts while the first one's last tiles drain.
+int ensure_pairs(const tfde_problem* P, cudaStream_t s) {
+    MixedState* M = mixed(P);
+    if (M->pair_d) return TFDE_OK;
+    Pass ps[5];
+    matvec_passes(TFDE_OP_A, -1, ps);
+    tc::Params prm[4];
+    long long gst[6];
+    for (int g = 0; g < 2; ++g) {
+        gst[3 * g] = 0;
+        M->pair_bytes[g] = M->pair_flops[g] = 0.0;
+        for (int i = 0; i < 2; ++i) {
+            const Pass& q = ps[2 * g + i];
+            double by, fl;
+            gemm_params(P, q.axis, q.seg, q.nseg, q.out_mode, 1.f, nullptr, q.out_plane, q.lam, prm[2 * g + i], &by, &fl);
+            gst[3 * g + i + 1] = gst[3 * g + i] + prm[2 * g + i].ntiles * prm[2 * g + i].mhalves;
+            M->pair_bytes[g] += by;
+            M->pair_flops[g] += fl;
+        }
+        M->pair_total[g] = gst[3 * g + 2];
+    }
+    MX_TRY(cudaMalloc((void**)&M->pair_d, sizeof(prm)));
+    MX_TRY(cudaMalloc((void**)&M->pair_gstart, sizeof(gst)));
+    MX_TRY(cudaMemcpyAsync(M->pair_d, prm, sizeof(prm), cudaMemcpyHostToDevice, s));
+    MX_TRY(cudaMemcpyAsync(M->pair_gstart, gst, sizeof(gst), cudaMemcpyHostToDevice, s));
+    MX_TRY(cudaStreamSynchronize(s));   // the host arrays go out of scope
+    return TFDE_OK;
+}
+
 int fast_matvec(const tfde_problem* P, int op, float* q32, cudaStream_t s, int out_plane = -1,
                 const float* dot_vec = nullptr, double* dot_out = nullptr) {
     Pass ps[5];
     const int np = matvec_passes(op, out_plane, ps);
-    return run_passes(P, ps, np, q32, s, dot_vec, dot_out);
+    if (op != TFDE_OP_A) return run_passes(P, ps, np, q32, s, dot_vec, dot_out);
+    MixedState* M = mixed(P);
+    int st;
+    if ((st = ensure_pairs(P, s))) return st;
+    for (int g = 0; g < 2; ++g) {
+        M->gemm_launches++;
+        st = tc::launch_grouped(M->pair_d + 2 * g, M->pair_gstart + 3 * g, 2, M->pair_total[g], g == 0 ? 1 : 0,
+                                tc::OUT_HILO, nullptr, M->err, s, M->pair_bytes[g], M->pair_flops[g]);
+        if (st) return st;
+    }
+    return run_passes(P, ps + 4, 1, q32, s, dot_vec, dot_out);
 }
 
 // z32 = S_N Lambda^{-1} S_N r, r given as the split plane pair PL_R.
@@ -614,6 +656,8 @@ void mixed_free(tfde_problem* P) {
     for (auto& v : M->f) cudaFree(v);
     cudaFree(M->V32);
     cudaFree(M->pring);
+    cudaFree(M->pair_d);
+    cudaFree(M->pair_gstart);
     cudaFree(M->gm);
     if (M->gm_host) cudaFreeHost(M->gm_host);
     oz_free(M);

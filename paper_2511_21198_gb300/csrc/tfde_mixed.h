@@ -108,6 +108,12 @@ struct MixedState {
     // inner PCG: the search directions of the current window (the solution is
     // combined from them once per sweep, see inner_pcg)
     float* pring = nullptr;   // kPRing vectors
+    // the operator's first four split passes as two grouped launches (device
+    // descriptors, tile offsets, totals and algorithmic work per launch)
+    tc::Params* pair_d = nullptr;
+    long long* pair_gstart = nullptr;   // [2][3]
+    long long pair_total[2] = {};
+    double pair_bytes[2] = {}, pair_flops[2] = {};
     double* gm = nullptr;
     double* gm_host = nullptr;
     // exact-integer slice path (tfde_oz.cu)
