@@ -765,9 +765,13 @@ int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit
         if (!std::isfinite(nr)) { status = set_error(TFDE_ENAN, "non-finite residual"); break; }
         if (nr <= tol * nb) { status = TFDE_OK; break; }
         if (loc.iters >= maxit) break;
-        // inner solve of A d = r / ||r|| to a relative theta
+        // inner solve of A d = r / ||r|| to a relative theta.  One sweep lowers
+        // the true residual by at most ~kInnerFloor (the split operator's
+        // accuracy); when the target needs more, two sweeps share it evenly
+        // (theta = sqrt of the target, floored) instead of the first one
+        // spending iterations below what it can deliver.
         double theta = 0.5 * tol * nb / nr;
-        if (theta < 1e-4) theta = 1e-4;
+        if (theta < kInnerFloor) theta = std::max(kInnerFloor, std::sqrt(theta));
         launch_scale64to32(P->N, r64, 1.0 / nr, M->f[F_R], M->hi[PL_R], M->lo[PL_R], M->f[F_X], s);
         int it = 0;
         double reached = 1.0;
