@@ -661,7 +661,8 @@ int batch_cn_advance(tfde_batch* B, double* const* u, const double* const* F, in
             outer[i] = 1;
             any = 1;
             double th = 0.5 * tol * nb[i] / nr[i] / ratio[i];
-            theta[i] = th < 1e-4 ? 1e-4 : th;
+            // beyond one sweep's reach (~1e-4): two sweeps share the reduction
+            theta[i] = th < 1e-4 ? std::max(1e-4, std::sqrt(th)) : th;
             B->h_s[i * kSS + S_SC32] = 1.0 / nr[i];
             B->h_s[i * kSS + S_ADD] = nr[i];
             B->h_act[i] = 1;

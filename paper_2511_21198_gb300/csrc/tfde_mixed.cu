@@ -836,7 +836,7 @@ int mixed_pgmres(tfde_problem* P, const double* b, double* x, int restart, doubl
         if (nr <= tol * nb) { status = TFDE_OK; break; }
         if (loc.iters >= maxit) break;
         double theta = 0.5 * tol * nb / nr / ratio;
-        if (theta < 1e-4) theta = 1e-4;
+        if (theta < kInnerFloor) theta = std::max(kInnerFloor, std::sqrt(theta));   // as in mixed_pcg
         launch_scale64to32(P->N, r64, 1.0 / nr, M->f[F_R], M->hi[PL_R], M->lo[PL_R], M->f[F_X], s);
         int it = 0;
         double est_ratio = 1.0;
