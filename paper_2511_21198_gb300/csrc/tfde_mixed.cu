@@ -104,7 +104,7 @@ void gemm_params(const tfde_problem* P, int axis, const SegSpec* segs, int nseg,
     prm.out_mode = out_mode;
     prm.alpha = alpha;
     prm.out_f32 = out_f32;
-    if (out_mode == tc::OUT_HILO || out_mode == tc::OUT_XPAY) {
+    if (out_mode == tc::OUT_HILO || out_mode == tc::OUT_XPAY || out_mode == tc::OUT_HI) {
         prm.out_hi = M->hi[out_plane];
         prm.out_lo = M->lo[out_plane];
     }
@@ -252,8 +252,15 @@ int fast_matvec(const tfde_problem* P, int op, float* q32, cudaStream_t s, int o
 // t = S_N r (S_N is orthogonal), and p = z + beta p with beta = *num / *den
 // (0 when den is null; p_old the previous direction), written by the last
 // pass to p32 and to the split planes PL_P: z itself is never stored.
+// The passes carry the hi (BF16) plane alone: the inner PCG stops at
+// tolerances of ~1e-4 .. 1e-1, far above the ~2^-9 relative perturbation
+// that BF16 intermediates give the preconditioner (measured: the same
+// iteration counts as with split intermediates), and each pass then moves
+// and converts half the data.  The last pass still writes p in FP32 and in
+// split planes, for the operator.
 int fast_precond_cg(const tfde_problem* P, float* p32, const float* p_old, double* rz, const double* num,
                     const double* den, cudaStream_t s) {
+    MixedState* M = mixed(P);
     Pass ps[6];
     const int np = precond_passes(ps);
     for (int i = 0; i < np; ++i) {
@@ -261,8 +268,18 @@ int fast_precond_cg(const tfde_problem* P, float* p32, const float* p_old, doubl
         const bool last = i + 1 == np;
         tc::Params prm;
         double bytes, flops;
-        gemm_params(P, q.axis, q.seg, q.nseg, last ? tc::OUT_XPAY : q.out_mode, 1.f, last ? p32 : nullptr,
+        gemm_params(P, q.axis, q.seg, q.nseg, last ? tc::OUT_XPAY : tc::OUT_HI, 1.f, last ? p32 : nullptr,
                     last ? PL_P : q.out_plane, q.lam, prm, &bytes, &flops);
+        // one B plane (hi) and one product per pass
+        const int pl = q.seg[0].plane;
+        tc::Segment& S = prm.seg[0];
+        if (M->bmap1_rank[pl][q.axis] > 0 && S.bmap2 >= 0) {
+            prm.bmaps[S.bmap2] = M->bmap1[pl][q.axis];
+            prm.b_rank = M->bmap1_rank[pl][q.axis];
+        }
+        S.nb = 1;
+        S.npair = 1;
+        bytes -= 2.0 * (double)P->N * (last ? 1.0 : 2.0);   // lo plane neither read nor (but the last) written
         if (q.lam) {
             prm.dot_lam = 1;
             prm.dot_out = rz;
@@ -613,6 +630,7 @@ int mixed_init(tfde_problem* P, cudaStream_t s) {
             if (!st) st = tc::make_map_B(&M->bmap_lo[pl][a], M->lo[pl], P->n, a);
             if (st) return st;
             M->bmap2_rank[pl][a] = tc::make_map_B_pair(&M->bmap2[pl][a], M->hi[pl], P->n, a);
+            M->bmap1_rank[pl][a] = tc::make_map_B_pair(&M->bmap1[pl][a], M->hi[pl], P->n, a, 1);
         }
     }
     for (int v = 0; v < NF; ++v) {

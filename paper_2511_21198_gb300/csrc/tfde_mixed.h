@@ -95,6 +95,8 @@ struct MixedState {
     CUtensorMap bmap_lo[NPL][3];
     CUtensorMap bmap2[NPL][3];     // both planes (and on y/z all four 64-line blocks) in one box
     int bmap2_rank[NPL][3] = {};   // 3 (x), 5 (y/z), 0 = not available
+    CUtensorMap bmap1[NPL][3];     // the hi plane alone, same box otherwise
+    int bmap1_rank[NPL][3] = {};
     float* f[NF] = {};
     float* lam = nullptr;   // [ra (n3) | rb (n3) | U (n1 n2) | V (n1 n2)]
     double* dsc = nullptr;  // device scalars

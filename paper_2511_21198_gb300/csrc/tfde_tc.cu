@@ -102,12 +102,12 @@ int make_map_B_box(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], in
 // outer plane, hi/lo) with box {64, BK, BN / 64, 1, 2}, so that a single copy
 // fills the whole B stage in the layout of the per-plane boxes.  Returns the
 // rank, or 0 when no merged map applies.
-int make_map_B_pair(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis) {
+int make_map_B_pair(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis, int planes) {
     const cuuint64_t n1 = n[0], n2 = n[1], n3 = n[2], N = n1 * n2 * n3;
     if (axis == 0) {
         const cuuint64_t dims[3] = {n1, n2 * n3, 2};
         const cuuint64_t strides[2] = {n1 * 2, N * 2};
-        const cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)BN, 2};
+        const cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)BN, (cuuint32_t)planes};
         return encode(m, base, 3, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B) == TFDE_OK ? 3 : 0;
     }
     cuuint64_t C, K, P;
@@ -116,7 +116,7 @@ int make_map_B_pair(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], i
     if (C % BN != 0) return 0;
     const cuuint64_t dims[5] = {64, K, C / 64, P, 2};
     const cuuint64_t strides[4] = {C * 2, 128, C * K * 2, N * 2};
-    const cuuint32_t box[5] = {64, (cuuint32_t)BK, (cuuint32_t)(BN / 64), 1, 2};
+    const cuuint32_t box[5] = {64, (cuuint32_t)BK, (cuuint32_t)(BN / 64), 1, (cuuint32_t)planes};
     if (encode(m, base, 5, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != TFDE_OK) {
         set_error(TFDE_OK, "");
         return 0;
@@ -161,7 +161,8 @@ int set_attrs() {
                         set_attr_one<false, 1, OUT_F32>() && set_attr_one<false, 1, OUT_HILO>() &&
                         set_attr_one<true, 0, OUT_F32>() && set_attr_one<true, 0, OUT_HILO>() &&
                         set_attr_one<true, 1, OUT_F32>() && set_attr_one<true, 1, OUT_HILO>() &&
-                        set_attr_one<false, 0, OUT_XPAY>() && set_attr_one<false, 1, OUT_XPAY>();
+                        set_attr_one<false, 0, OUT_XPAY>() && set_attr_one<false, 1, OUT_XPAY>() &&
+                        set_attr_one<false, 0, OUT_HI>() && set_attr_one<false, 1, OUT_HI>();
         if (!ok) return set_error(TFDE_ECUDA, "cudaFuncSetAttribute(smem) failed");
         attr_done = true;
     }
@@ -196,6 +197,11 @@ void launch_instance(int kmajor, int out_mode, unsigned grid, cudaStream_t s, co
         if (out_mode == OUT_XPAY) {
             if (kmajor) launch_one<G, 1, OUT_XPAY>(grid, s, p0, groups, gstart, ngroups, gactive);
             else launch_one<G, 0, OUT_XPAY>(grid, s, p0, groups, gstart, ngroups, gactive);
+            return;
+        }
+        if (out_mode == OUT_HI) {
+            if (kmajor) launch_one<G, 1, OUT_HI>(grid, s, p0, groups, gstart, ngroups, gactive);
+            else launch_one<G, 0, OUT_HI>(grid, s, p0, groups, gstart, ngroups, gactive);
             return;
         }
     }

@@ -17,7 +17,8 @@ int encode_map(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dim
 int make_map_A(CUtensorMap* m, const __nv_bfloat16* base, int n);
 int make_map_B(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis);
 int make_map_B_box(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis, int box_lines);
-int make_map_B_pair(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis);
+// planes: 2 (hi and lo in one box) or 1 (the hi plane alone)
+int make_map_B_pair(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis, int planes = 2);
 void set_geometry(Params& P, const int n[3], int axis);
 int launch(const Params& P, cudaStream_t s, double bytes, double flops);
 // One persistent launch over the tiles of `ngroups` contractions along the same

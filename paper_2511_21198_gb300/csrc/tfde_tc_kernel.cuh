@@ -72,7 +72,9 @@ struct Segment {
 // null), written both as FP32 (out_f32) and as the split planes (out_hi,
 // out_lo): the CG direction update fused into the last pass of the
 // preconditioner.  p_old is xp_old, or out_f32 itself (in place).
-enum { OUT_F32 = 0, OUT_HILO = 1, OUT_XPAY = 2 };
+// OUT_HI: the BF16 rounding of Y alone (out_hi), for consumers that read
+// only the hi plane.
+enum { OUT_F32 = 0, OUT_HILO = 1, OUT_XPAY = 2, OUT_HI = 3 };
 
 struct Params {
     CUtensorMap amaps[4];
@@ -157,6 +159,13 @@ template <int OM>
 __device__ __forceinline__ void store4(const Params& p, long long idx, float v0, float v1, float v2, float v3) {
     if constexpr (OM == OUT_F32) {
         *reinterpret_cast<float4*>(p.out_f32 + idx) = make_float4(v0, v1, v2, v3);
+    } else if constexpr (OM == OUT_HI) {
+        const __nv_bfloat162 h01 = __floats2bfloat162_rn(v0, v1);
+        const __nv_bfloat162 h23 = __floats2bfloat162_rn(v2, v3);
+        uint2 hv;
+        hv.x = *reinterpret_cast<const uint32_t*>(&h01);
+        hv.y = *reinterpret_cast<const uint32_t*>(&h23);
+        *reinterpret_cast<uint2*>(p.out_hi + idx) = hv;
     } else {
         if constexpr (OM == OUT_XPAY) *reinterpret_cast<float4*>(p.out_f32 + idx) = make_float4(v0, v1, v2, v3);
         const __nv_bfloat162 h01 = __floats2bfloat162_rn(v0, v1);
@@ -178,6 +187,8 @@ template <int OM>
 __device__ __forceinline__ void store1(const Params& p, long long idx, float v) {
     if constexpr (OM == OUT_F32) {
         p.out_f32[idx] = v;
+    } else if constexpr (OM == OUT_HI) {
+        p.out_hi[idx] = __float2bfloat16_rn(v);
     } else {
         if constexpr (OM == OUT_XPAY) p.out_f32[idx] = v;
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
