@@ -107,7 +107,8 @@ __global__ __launch_bounds__(kT) void cg_update_r32_kernel(long long N, const do
     for (long long i = lo + threadIdx.x; i < hi; i += kT) {
         const float ri = fmaf(-alpha, q[i], r[i]);
         r[i] = ri;
-        split(ri, rh[i], rl[i]);
+        if (rl) split(ri, rh[i], rl[i]);
+        else rh[i] = __float2bfloat16_rn(ri);
         k.add(ri * ri);
     }
     const double t = block_sum64((double)k.s - (double)k.c);
@@ -157,6 +158,16 @@ __global__ void xpay32_kernel(long long N, const double* __restrict__ num, const
         const float v = fmaf(beta, p[i], z[i]);
         p[i] = v;
         split(v, ph[i], pl[i]);
+    }
+}
+
+// r32 = r64 * s ; rh = bf16(r32) (the hi plane alone, for consumers that read no lo plane)
+__global__ void scale64to32_hi_kernel(long long N, const double* __restrict__ r64, double s, float* __restrict__ r32,
+                                      __nv_bfloat16* __restrict__ rh) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const float v = (float)(r64[i] * s);
+        r32[i] = v;
+        rh[i] = __float2bfloat16_rn(v);
     }
 }
 
@@ -290,6 +301,10 @@ void launch_pcg_combine(size_t N, const PcgPending& pend, const float* x32, doub
         a.alpha[j] = j < pend.cnt ? pend.alpha[j] : nullptr;
     }
     pcg_combine_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, a, x32, sc, c64, x64, acc32);
+}
+void launch_scale64to32_hi(size_t N, const double* r64, double sc, float* r32, __nv_bfloat16* rh, cudaStream_t s) {
+    stats_count_launch();
+    scale64to32_hi_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, r64, sc, r32, rh);
 }
 void launch_widen_add32(size_t N, double sc, const float* d, double* c, double* x, cudaStream_t s) {
     stats_count_launch();

@@ -368,8 +368,9 @@ int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, PcgPen
     while (k < maxit) {
         MX_TRY(cudaMemsetAsync(d + D_PQ, 0, 2 * sizeof(double), s));   // <p, Ap> and <r, r>
         if ((st = fast_matvec(P, TFDE_OP_A, q, s, -1, pbuf(k), d + D_PQ))) return st;
-        launch_cg_update_r32(N, d + rz, d + D_PQ, q, r, M->hi[PL_R], M->lo[PL_R], d + D_RR,
-                             d + kAlphaSlot + k % kPRing, s);
+        // the preconditioner reads the hi plane of r alone
+        launch_cg_update_r32(N, d + rz, d + D_PQ, q, r, M->hi[PL_R], nullptr, d + D_RR, d + kAlphaSlot + k % kPRing,
+                             s);
         const double rr = host_scalar(P, d + D_RR, s, &st);
         if (st) return st;
         ++k;
@@ -790,7 +791,7 @@ int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit
         // spending iterations below what it can deliver.
         double theta = 0.5 * tol * nb / nr;
         if (theta < kInnerFloor) theta = std::max(kInnerFloor, std::sqrt(theta));
-        launch_scale64to32(P->N, r64, 1.0 / nr, M->f[F_R], M->hi[PL_R], M->lo[PL_R], M->f[F_X], s);
+        launch_scale64to32_hi(P->N, r64, 1.0 / nr, M->f[F_R], M->hi[PL_R], s);   // the inner PCG reads no lo plane
         int it = 0;
         double reached = 1.0;
         // r32 = r / ||r||: unit norm up to the FP32 rounding of its elements

@@ -25,8 +25,11 @@ void launch_dot32(size_t N, const float* a, const float* b, double* part, int nb
 // alpha = *num / *den on the device; x += alpha p; r -= alpha q; split r; *rr += r.r
 void launch_cg_update32(size_t N, const double* num, const double* den, const float* p, const float* q, float* x,
                         float* r, __nv_bfloat16* rh, __nv_bfloat16* rl, double* rr, cudaStream_t s);
+// r32 = r64 sc; rh = bf16(r32)
+void launch_scale64to32_hi(size_t N, const double* r64, double sc, float* r32, __nv_bfloat16* rh, cudaStream_t s);
 // alpha = *num / *den on the device (also stored to *alpha_out by one thread);
-// r -= alpha q; split r; *rr += r.r  (the solution is left to the combination)
+// r -= alpha q; split r (rl null: the hi plane alone); *rr += r.r  (the
+// solution is left to the combination)
 void launch_cg_update_r32(size_t N, const double* num, const double* den, const float* q, float* r,
                           __nv_bfloat16* rh, __nv_bfloat16* rl, double* rr, double* alpha_out, cudaStream_t s);
 // d = (fold ? x32 : 0) + sum_j alpha_j p_j ; with c64: c64 = sc d, x64 += c64 ;
