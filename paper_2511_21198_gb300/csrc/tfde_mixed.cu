@@ -273,9 +273,15 @@ int fast_precond_cg(const tfde_problem* P, float* p32, const float* p_old, doubl
         // one B plane (hi) and one product per pass
         const int pl = q.seg[0].plane;
         tc::Segment& S = prm.seg[0];
-        if (M->bmap1_rank[pl][q.axis] > 0 && S.bmap2 >= 0) {
-            prm.bmaps[S.bmap2] = M->bmap1[pl][q.axis];
-            prm.b_rank = M->bmap1_rank[pl][q.axis];
+        if (S.bmap2 >= 0) {
+            if (M->bmap1_rank[pl][q.axis] > 0) {
+                prm.bmaps[S.bmap2] = M->bmap1[pl][q.axis];
+                prm.b_rank = M->bmap1_rank[pl][q.axis];
+            } else {   // the merged box would carry both planes: per-plane boxes, hi alone
+                prm.bmaps[S.bmap2] = M->bmap_hi[pl][q.axis];
+                S.bmap[0] = S.bmap2;
+                S.bmap2 = -1;
+            }
         }
         S.nb = 1;
         S.npair = 1;

@@ -230,6 +230,8 @@ int launch(const Params& P, cudaStream_t s, double bytes, double flops) {
 int launch_grouped(const Params* groups, const long long* gstart, int ngroups, long long total, int b_kmajor,
                    int out_mode, const int* gactive, int* err, cudaStream_t s, double bytes, double flops) {
     if (int st = set_attrs()) return st;
+    if (out_mode == OUT_HI || out_mode == OUT_XPAY)
+        return set_error(TFDE_EUNSUPPORTED, "grouped axis_gemm_kernel: split or FP32 output only");   // no such instances
     if (total <= 0 || ngroups <= 0) return TFDE_OK;
     Params p0;
     std::memset(&p0, 0, sizeof(p0));
