@@ -8,6 +8,7 @@
 #include "tfde_internal.h"
 #include "tfde_stats.h"
 #include "tfde_mixed.h"
+#include "tfde_pow2conv.cuh"
 
 namespace tfde {
 namespace {
@@ -115,6 +116,56 @@ __global__ __launch_bounds__(kT) void cg_update_r32_kernel(long long N, const do
     if (threadIdx.x == 0) atomicAdd(rr, t);
 }
 
+// The same update four elements at a time (N4 = N / 4 groups; 16-byte
+// loads and stores, packed BF16 conversions with the same rounding).
+__device__ __forceinline__ uint2 bf16x4_hi(float4 v) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    return make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+}
+__device__ __forceinline__ uint2 bf16x4_lo(float4 v, uint2 h) {
+    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&h.x);
+    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&h.y);
+    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    const __nv_bfloat162 la = __floats2bfloat162_rn(v.x - fa.x, v.y - fa.y), lb = __floats2bfloat162_rn(v.z - fb.x, v.w - fb.y);
+    return make_uint2(*reinterpret_cast<const uint32_t*>(&la), *reinterpret_cast<const uint32_t*>(&lb));
+}
+__global__ __launch_bounds__(kT) void cg_update_r32_v4_kernel(long long N4, const double* __restrict__ num,
+                                                              const double* __restrict__ den,
+                                                              const float4* __restrict__ q, float4* __restrict__ r,
+                                                              uint2* __restrict__ rh, uint2* __restrict__ rl,
+                                                              double* __restrict__ rr, double* __restrict__ alpha_out) {
+    __shared__ float s_alpha;
+    if (threadIdx.x == 0) {
+        const double a = num[0] / den[0];
+        s_alpha = (float)a;
+        if (blockIdx.x == 0) *alpha_out = (double)(float)a;
+    }
+    __syncthreads();
+    const float alpha = s_alpha;
+    long long lo, hi;
+    chunk(N4, lo, hi);
+    KSum k;
+#pragma unroll 2
+    for (long long i = lo + threadIdx.x; i < hi; i += kT) {
+        const float4 qv = q[i];
+        float4 v = r[i];
+        v.x = fmaf(-alpha, qv.x, v.x);
+        v.y = fmaf(-alpha, qv.y, v.y);
+        v.z = fmaf(-alpha, qv.z, v.z);
+        v.w = fmaf(-alpha, qv.w, v.w);
+        r[i] = v;
+        const uint2 h = bf16x4_hi(v);
+        rh[i] = h;
+        if (rl) rl[i] = bf16x4_lo(v, h);
+        k.add(v.x * v.x);
+        k.add(v.y * v.y);
+        k.add(v.z * v.z);
+        k.add(v.w * v.w);
+    }
+    const double t = block_sum64((double)k.s - (double)k.c);
+    if (threadIdx.x == 0) atomicAdd(rr, t);
+}
+
 // d = (x32 when fold) + sum_j alpha_j p_j (FP32, in the order of the
 // directions, as the per-iteration update x += alpha p would form it); then
 // c64 = sc d and x64 += c64 (c64 set), x64 += sc d (x64 only), or acc32 = d
@@ -146,6 +197,41 @@ __global__ void pcg_combine_kernel(long long N, CombineArgs a, const float* __re
     }
 }
 
+// The same for sc = 2^j (c64 / x64 modes), four elements at a time: sc d
+// formed exactly from the FP32 bits (no FP64 multiply or conversion), one
+// FP64 addition per element.
+__global__ void pcg_combine_pow2_kernel(long long N4, CombineArgs a, const float4* __restrict__ x32, int j,
+                                        double2* __restrict__ c64, double2* __restrict__ x64) {
+    __shared__ float s_al[kPRing];
+    if (threadIdx.x < a.cnt) s_al[threadIdx.x] = (float)*a.alpha[threadIdx.x];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N4; i += (long long)gridDim.x * blockDim.x) {
+        float4 d = a.fold ? x32[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < kPRing; ++t)
+            if (t < a.cnt) {
+                const float4 pv = reinterpret_cast<const float4*>(a.p[t])[i];
+                d.x = fmaf(s_al[t], pv.x, d.x);
+                d.y = fmaf(s_al[t], pv.y, d.y);
+                d.z = fmaf(s_al[t], pv.z, d.z);
+                d.w = fmaf(s_al[t], pv.w, d.w);
+            }
+        const double2 v0 = make_double2(f32_pow2_to_f64(d.x, j), f32_pow2_to_f64(d.y, j));
+        const double2 v1 = make_double2(f32_pow2_to_f64(d.z, j), f32_pow2_to_f64(d.w, j));
+        if (c64) {
+            c64[2 * i] = v0;
+            c64[2 * i + 1] = v1;
+        }
+        double2 x0 = x64[2 * i], x1 = x64[2 * i + 1];
+        x0.x += v0.x;
+        x0.y += v0.y;
+        x1.x += v1.x;
+        x1.y += v1.y;
+        x64[2 * i] = x0;
+        x64[2 * i + 1] = x1;
+    }
+}
+
 // beta = num / den (device scalars); p = z + beta p ; (ph, pl) = split(p)
 __global__ void xpay32_kernel(long long N, const double* __restrict__ num, const double* __restrict__ den,
                               const float* __restrict__ z, float* __restrict__ p, __nv_bfloat16* __restrict__ ph,
@@ -168,6 +254,19 @@ __global__ void scale64to32_hi_kernel(long long N, const double* __restrict__ r6
         const float v = (float)(r64[i] * s);
         r32[i] = v;
         rh[i] = __float2bfloat16_rn(v);
+    }
+}
+
+// The same with s = 2^k, four elements at a time (N4 = N / 4 groups): the
+// scaled conversion by integer operations (no FP64 arithmetic).
+__global__ void scale64to32_hi_pow2_kernel(long long N4, const ulonglong2* __restrict__ r64, int k,
+                                           float4* __restrict__ r32, uint2* __restrict__ rh) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N4; i += (long long)gridDim.x * blockDim.x) {
+        const ulonglong2 a = r64[2 * i], b = r64[2 * i + 1];
+        const float4 v = make_float4(f64_pow2_to_f32(a.x, k), f64_pow2_to_f32(a.y, k), f64_pow2_to_f32(b.x, k),
+                                     f64_pow2_to_f32(b.y, k));
+        r32[i] = v;
+        rh[i] = bf16x4_hi(v);
     }
 }
 
@@ -268,6 +367,13 @@ __global__ void scale_split32_kernel(long long N, float sc, const float* in, flo
     }
 }
 
+// N a multiple of 4 and every (non-null) vector 16-byte aligned: the
+// four-element kernels apply
+inline bool aligned16(size_t N, const void* a, const void* b, const void* c, const void* d) {
+    const uintptr_t m = (uintptr_t)a | (uintptr_t)b | (uintptr_t)c | (uintptr_t)d;
+    return N % 4 == 0 && (m & 15) == 0;
+}
+
 inline int grid_for(long long N) {
     long long g = (N + kT - 1) / kT;
     if (g > 152LL * 16) g = 152LL * 16;
@@ -288,6 +394,13 @@ void launch_cg_update32(size_t N, const double* num, const double* den, const fl
 void launch_cg_update_r32(size_t N, const double* num, const double* den, const float* q, float* r,
                           __nv_bfloat16* rh, __nv_bfloat16* rl, double* rr, double* alpha_out, cudaStream_t s) {
     stats_count_launch();
+    if (aligned16(N, q, r, rh, rl)) {
+        const long long N4 = (long long)N / 4;
+        cg_update_r32_v4_kernel<<<grid_for(N4), kT, 0, s>>>(N4, num, den, reinterpret_cast<const float4*>(q),
+                                                            reinterpret_cast<float4*>(r), reinterpret_cast<uint2*>(rh),
+                                                            reinterpret_cast<uint2*>(rl), rr, alpha_out);
+        return;
+    }
     cg_update_r32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, num, den, q, r, rh, rl, rr, alpha_out);
 }
 void launch_pcg_combine(size_t N, const PcgPending& pend, const float* x32, double sc, double* c64, double* x64,
@@ -300,10 +413,28 @@ void launch_pcg_combine(size_t N, const PcgPending& pend, const float* x32, doub
         a.p[j] = j < pend.cnt ? pend.p[j] : nullptr;
         a.alpha[j] = j < pend.cnt ? pend.alpha[j] : nullptr;
     }
+    int j = 0;
+    bool vec = x64 && !acc32 && pow2_exponent(sc, &j) && aligned16(N, x32, c64, x64, nullptr);
+    for (int t = 0; t < pend.cnt; ++t) vec = vec && aligned16(N, pend.p[t], nullptr, nullptr, nullptr);
+    if (vec) {
+        const long long N4 = (long long)N / 4;
+        pcg_combine_pow2_kernel<<<grid_for(N4), kT, 0, s>>>(N4, a, reinterpret_cast<const float4*>(x32), j,
+                                                            reinterpret_cast<double2*>(c64),
+                                                            reinterpret_cast<double2*>(x64));
+        return;
+    }
     pcg_combine_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, a, x32, sc, c64, x64, acc32);
 }
 void launch_scale64to32_hi(size_t N, const double* r64, double sc, float* r32, __nv_bfloat16* rh, cudaStream_t s) {
     stats_count_launch();
+    int k = 0;
+    if (pow2_exponent(sc, &k) && aligned16(N, r64, r32, rh, nullptr)) {
+        const long long N4 = (long long)N / 4;
+        scale64to32_hi_pow2_kernel<<<grid_for(N4), kT, 0, s>>>(N4, reinterpret_cast<const ulonglong2*>(r64), k,
+                                                               reinterpret_cast<float4*>(r32),
+                                                               reinterpret_cast<uint2*>(rh));
+        return;
+    }
     scale64to32_hi_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, r64, sc, r32, rh);
 }
 void launch_widen_add32(size_t N, double sc, const float* d, double* c, double* x, cudaStream_t s) {

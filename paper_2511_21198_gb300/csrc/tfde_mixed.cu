@@ -339,8 +339,8 @@ enum { D_PQ = 0, D_RR = 1, D_RZ0 = 2, D_RZ1 = 3 };
 // <r,z>_new/<r,z> are formed on the device (alpha by the update kernel, beta
 // by the preconditioner's last pass, which writes p = z + beta p directly),
 // and the host reads <r, r> once per iteration for the stopping test.
-// rr0_known > 0: the caller's ||r32||^2 (the refinement scales r to unit
-// norm), which spares a reduction and a host read.  The solution is not
+// rr0_known > 0: the caller's ||r32||^2 (the refinement scales r by a power
+// of two to a norm in [1/2, 1)), which spares a reduction and a host read.  The solution is not
 // updated per iteration: the directions p_j and their alpha_j stay in a ring
 // of kPRing vectors, folded into F_X when the ring is full, and *pend
 // describes what is left (d = fold ? F_X : 0, + sum alpha_j p_j), combined by
@@ -725,8 +725,8 @@ int exact_residual(tfde_problem* P, const double* b, const double* x, double* r6
     return st;
 }
 
-// x += c, c = nr d (d: the inner solution in F_X for the residual scaled by
-// 1/nr), and the new residual with its norm into r64 / *nr.  A sweep that
+// x += c, c = dsc d (d: the inner solution in F_X for the residual scaled by
+// 1/dsc), and the new residual with its norm into r64 / *nr.  A sweep that
 // cannot end the solve (predicted true reduction `pred`) updates the
 // residual by its correction, r <- r - A c, instead of recomputing b - A x:
 // the product is exact-integer at few digits, because c is small (about
@@ -736,15 +736,15 @@ int exact_residual(tfde_problem* P, const double* b, const double* x, double* r6
 // residual meets the tolerance: the residual that stops the solve, and that
 // the next CN step chains on, is always the recomputed one.
 int apply_correction(tfde_problem* P, const double* b, double* x, double* r64, double* nr, double pred, double tol,
-                     double nb, cudaStream_t s, const PcgPending* pend = nullptr) {
+                     double nb, double dsc, cudaStream_t s, const PcgPending* pend = nullptr) {
     MixedState* M = mixed(P);
     int st;
     double* an = P->w[tfde_problem::W_T];
     if (*nr * pred > tol * nb) {
         double* c64 = an;
         P->an_ready = false;
-        if (pend) launch_pcg_combine(P->N, *pend, M->f[F_X], *nr, c64, x, nullptr, s);   // c = nr d, x += c
-        else launch_widen_add32(P->N, *nr, M->f[F_X], c64, x, s);
+        if (pend) launch_pcg_combine(P->N, *pend, M->f[F_X], dsc, c64, x, nullptr, s);   // c = dsc d, x += c
+        else launch_widen_add32(P->N, dsc, M->f[F_X], c64, x, s);
         const int shift = -std::ilogb(nb);
         double* acc = P->red_out + kNormsSlot + 2;
         const int sc = *nr <= 1e-2 * nb ? 4 : (*nr <= nb ? 5 : oz_slices_for_tol(tol));
@@ -755,8 +755,8 @@ int apply_correction(tfde_problem* P, const double* b, double* x, double* r64, d
         if (*nr <= tol * nb) return exact_residual(P, b, x, r64, nr, tol, nb, s);
         return TFDE_OK;
     }
-    if (pend) launch_pcg_combine(P->N, *pend, M->f[F_X], *nr, nullptr, x, nullptr, s);   // x += nr d
-    else launch_add32to64(P->N, *nr, M->f[F_X], x, s);
+    if (pend) launch_pcg_combine(P->N, *pend, M->f[F_X], dsc, nullptr, x, nullptr, s);   // x += dsc d
+    else launch_add32to64(P->N, dsc, M->f[F_X], x, s);
     return exact_residual(P, b, x, r64, nr, tol, nb, s);
 }
 
@@ -797,16 +797,23 @@ int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit
         // spending iterations below what it can deliver.
         double theta = 0.5 * tol * nb / nr;
         if (theta < kInnerFloor) theta = std::max(kInnerFloor, std::sqrt(theta));
-        launch_scale64to32_hi(P->N, r64, 1.0 / nr, M->f[F_R], M->hi[PL_R], s);   // the inner PCG reads no lo plane
+        // r32 = r 2^k with 2^k the power of two nearest below 1 / ||r|| (an
+        // exact scale: the conversion and, later, the scale back of the
+        // correction need no FP64 arithmetic), so ||r32|| lies in [1/2, 1)
+        // up to the FP32 rounding of its elements; the inner PCG reads no lo plane
+        const int k = -std::ilogb(nr) - 1;
+        const double un = std::ldexp(nr, k);
+        launch_scale64to32_hi(P->N, r64, std::ldexp(1.0, k), M->f[F_R], M->hi[PL_R], s);
         int it = 0;
         double reached = 1.0;
-        // r32 = r / ||r||: unit norm up to the FP32 rounding of its elements
         PcgPending pend;
-        if ((st = inner_pcg(P, theta, maxit - loc.iters, &it, &pend, s, &reached, 1.0))) return st;
+        if ((st = inner_pcg(P, theta, maxit - loc.iters, &it, &pend, s, &reached, un * un))) return st;
         loc.iters += it;
         loc.refine_sweeps++;
         const double nr_old = nr;
-        if ((st = apply_correction(P, b, x, r64, &nr, std::max(reached, kInnerFloor), tol, nb, s, &pend))) return st;
+        if ((st = apply_correction(P, b, x, r64, &nr, std::max(reached, kInnerFloor), tol, nb, std::ldexp(1.0, -k), s,
+                                   &pend)))
+            return st;
         stall = (nr > 0.5 * nr_old) ? stall + 1 : 0;
         if (stall >= 2) {
             // refinement stopped contracting: finish with FP64 inner solves
@@ -871,7 +878,7 @@ int mixed_pgmres(tfde_problem* P, const double* b, double* x, int restart, doubl
         loc.refine_sweeps++;
         const double nr_old = nr;
         const double pred = est_ratio > 0.0 ? std::max(est_ratio * ratio, kInnerFloor) : 1.0;
-        if ((st = apply_correction(P, b, x, r64, &nr, pred, tol, nb, s))) return st;
+        if ((st = apply_correction(P, b, x, r64, &nr, pred, tol, nb, nr, s))) return st;
         if (est_ratio > 0.0) {
             const double observed = (nr / nr_old) / est_ratio;
             ratio = observed > 1.0 ? observed : 1.0;

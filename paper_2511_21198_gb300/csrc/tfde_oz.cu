@@ -26,8 +26,10 @@ namespace {
 
 // ------------------------------------------------------------ digit slicing
 // Fixed-point integer round(|x| 2^{7S - E}) with the sign of x, from the FP64
-// bits alone (|x| < 2^E): the mantissa shifted right with round-half-up.
-__device__ __forceinline__ long long fixed_point(long long bits, int S, int E) {
+// bits alone (|x| < 2^E): the mantissa m shifted right by r with
+// round-half-up, floor((m + 2^{r-1}) / 2^r) = floor((floor(m / 2^{r-1}) + 1) / 2).
+template <int S>
+__device__ __forceinline__ long long fixed_point(long long bits, int E) {
     const unsigned long long u = (unsigned long long)bits & 0x7FFFFFFFFFFFFFFFull;
     if (u == 0) return 0;
     int e = (int)(u >> 52);
@@ -35,56 +37,65 @@ __device__ __forceinline__ long long fixed_point(long long bits, int S, int E) {
     if (e == 0) e = 1; else mant |= (1ull << 52);
     const int r = 1075 - e - 7 * S + E;   // right shift; >= 53 - 7S >= 4 for S <= 7
     long long X;
-    if (r >= 64) X = 0;
+    if (r > 64) X = 0;
     else if (r <= 0) X = (long long)(mant << (-r));
-    else X = (long long)((mant + (1ull << (r - 1))) >> r);
+    else X = (long long)(((mant >> (r - 1)) + 1) >> 1);
     return bits < 0 ? -X : X;
 }
 
-// Exponent E with |x| < 2^E for the largest |x| of a line (given as the
-// biased-exponent field of its bit pattern; 0 for an all-zero line).
-__device__ __forceinline__ int line_exponent_from_bits(unsigned long long umax) {
-    if (umax == 0) return 0;
-    const int e = (int)(umax >> 52);
+// Exponent E with |x| < 2^E for the largest |x| of a line, from the largest
+// high word of |x| over the line (bits 20..30: the biased exponent) and the OR
+// of the low words (nonzero with a zero high word: a subnormal maximum); 0 for
+// an all-zero line.
+__device__ __forceinline__ int line_exponent(uint32_t hmax, uint32_t lor) {
+    if (hmax == 0) return lor ? -1021 : 0;
+    const int e = (int)(hmax >> 20);
     return e == 0 ? -1021 : e - 1022;
+}
+// high word of |x| 2^sh (exponent field moved by sh) for a normal or zero x
+__device__ __forceinline__ uint32_t abs_hi_shifted(unsigned long long bits, int sh) {
+    const uint32_t h = (uint32_t)(bits >> 32) & 0x7FFFFFFFu;
+    return (h | (uint32_t)bits) ? h + ((uint32_t)sh << 20) : 0u;
 }
 
 // Balanced base-128 digits of X (|X| <= 2^{7S}): X = sum_t d_t 128^{S-1-t} with
 // d_t in [-64, 63] for t >= 1 and the leading d_0 in [-128, 128].  Adding 64 to
 // every digit below the leading one, Y = X + 64 (128^{S-1} - 1) / 127, turns
 // them into plain base-128 digits of Y, so d_t = ((Y >> 7 (S-1-t)) & 127) - 64
-// for t >= 1 and d_0 = Y >> 7 (S-1) (arithmetic shift): no carry chain.  BF16
-// bits of a digit: the top half of its FP32 bits (exact: at most 8 significant
-// bits).
-__device__ __forceinline__ long long digit_bias(int S) {
+// for t >= 1 and d_0 = Y >> 7 (S-1) (arithmetic shift): no carry chain.
+template <int S>
+__host__ __device__ constexpr long long digit_bias() {
     long long b = 0;
     for (int t = 1; t < S; ++t) b = b * 128 + 64;
     return b;
 }
-__device__ __forceinline__ uint32_t bf16_bits_of(long long d) {
-    return __float_as_uint((float)(int)d) >> 16;
+// A small integer d (|d| < 2^22) as an FP32 value without a conversion
+// instruction: the bit pattern of 1.5 2^23 + d (same binade) minus 1.5 2^23,
+// both exact.  The digit field f in [0, 127] gives f - 64 the same way.  The
+// BF16 bits of such a value are the top half of its FP32 bits (exact: at most
+// 8 significant bits), and two of them pack with one byte permutation.
+constexpr uint32_t kMagic = 0x4B400000u;   // 1.5 2^23
+__device__ __forceinline__ float small_int_float(int d) { return __int_as_float((int)kMagic + d) - 12582912.0f; }
+__device__ __forceinline__ float digit_float(uint32_t f) { return __uint_as_float(kMagic | f) - 12582976.0f; }
+__device__ __forceinline__ uint32_t pack_bf16_tops(float a, float b) {
+    return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
 }
 // digits of two neighbouring grid points (idx even, idx + 1) as packed BF16 pairs
-__device__ __forceinline__ void write_digits2(long long Xa, long long Xb, int S, __nv_bfloat16* planes, long long N,
-                                              long long idx, long long bias) {
+template <int S>
+__device__ __forceinline__ void write_digits2(long long Xa, long long Xb, __nv_bfloat16* planes, long long N,
+                                              long long idx) {
+    constexpr long long bias = digit_bias<S>();
     const long long Ya = Xa + bias, Yb = Xb + bias;
 #pragma unroll
-    for (int t = 1; t < 7; ++t) {
-        if (t < S) {
-            const int sh = 7 * (S - 1 - t);
-            const uint32_t lo = bf16_bits_of(((Ya >> sh) & 127) - 64);
-            const uint32_t hi = bf16_bits_of(((Yb >> sh) & 127) - 64);
-            *reinterpret_cast<uint32_t*>(planes + (long long)t * N + idx) = lo | (hi << 16);
-        }
+    for (int t = 1; t < S; ++t) {
+        const int sh = 7 * (S - 1 - t);
+        const float da = digit_float((uint32_t)(Ya >> sh) & 127u);
+        const float db = digit_float((uint32_t)(Yb >> sh) & 127u);
+        *reinterpret_cast<uint32_t*>(planes + (long long)t * N + idx) = pack_bf16_tops(da, db);
     }
-    const int sh0 = 7 * (S - 1);
-    *reinterpret_cast<uint32_t*>(planes + idx) = bf16_bits_of(Ya >> sh0) | (bf16_bits_of(Yb >> sh0) << 16);
-}
-
-// |x| bits of x * 2^sh for a normal or zero x (exponent field moved by sh)
-__device__ __forceinline__ unsigned long long abs_bits_shifted(long long bits, int sh) {
-    const unsigned long long u = (unsigned long long)bits & 0x7FFFFFFFFFFFFFFFull;
-    return u == 0 ? 0 : u + ((unsigned long long)(long long)sh << 52);
+    constexpr int sh0 = 7 * (S - 1);
+    *reinterpret_cast<uint32_t*>(planes + idx) =
+        pack_bf16_tops(small_int_float((int)(Ya >> sh0)), small_int_float((int)(Yb >> sh0)));
 }
 
 // The double Y * 2^s for an integer |Y| < 2^53 (exact; results below the
@@ -105,32 +116,37 @@ __device__ __forceinline__ double i64_ldexp_exact(long long Y, int s) {
 // digit planes of x under its line maximum and, when wout is set,
 // w = A_{n1} x along the line from the same fixed-point integers X
 // (w_k = (X_{k-1} + 6 X_k + X_{k+1}) 2^{E - 7S - 3}, |sum| < 2^53: exact).
-__global__ void slice_x_kernel(const double* __restrict__ x0, int n1, long long lines, int S,
+// S (digits) is a template argument: every digit shift is a constant.
+template <int S>
+__global__ void slice_x_kernel(const double* __restrict__ x0, int n1, long long lines,
                                __nv_bfloat16* __restrict__ p0, long long N, int* __restrict__ lexp,
                                double* __restrict__ wout) {
     const int lane = threadIdx.x & 31;
     const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long bias = digit_bias(S);
     for (long long l = wg; l < lines; l += nw) {
         const longlong2* r2 = reinterpret_cast<const longlong2*>(x0 + l * n1);   // n1 even: pairs stay in the line
         const int np = n1 / 2;
-        unsigned long long umax = 0;
+        uint32_t hmax = 0, lor = 0;
 #pragma unroll 4
         for (int q = lane; q < np; q += 32) {
             const longlong2 v = r2[q];
-            umax = max(umax, max((unsigned long long)v.x & 0x7FFFFFFFFFFFFFFFull,
-                                 (unsigned long long)v.y & 0x7FFFFFFFFFFFFFFFull));
+            hmax = max(hmax, max((uint32_t)((unsigned long long)v.x >> 32) & 0x7FFFFFFFu,
+                                 (uint32_t)((unsigned long long)v.y >> 32) & 0x7FFFFFFFu));
+            lor |= (uint32_t)v.x | (uint32_t)v.y;
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) umax = max(umax, __shfl_xor_sync(0xffffffffu, umax, o));
-        const int E = line_exponent_from_bits(umax);
+        for (int o = 16; o > 0; o >>= 1) {
+            hmax = max(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+            lor |= __shfl_xor_sync(0xffffffffu, lor, o);
+        }
+        const int E = line_exponent(hmax, lor);
         long long left_carry = 0;   // X just before this iteration's first point
         long long Xa = 0, Xb = 0;
         if (lane < np) {
             const longlong2 v = r2[lane];
-            Xa = fixed_point(v.x, S, E);
-            Xb = fixed_point(v.y, S, E);
+            Xa = fixed_point<S>(v.x, E);
+            Xb = fixed_point<S>(v.y, E);
         }
         for (int base = 0; base < np; base += 32) {
             const int q = base + lane;
@@ -138,10 +154,10 @@ __global__ void slice_x_kernel(const double* __restrict__ x0, int n1, long long 
             long long Na = 0, Nb = 0;
             if (qn < np) {
                 const longlong2 v = r2[qn];
-                Na = fixed_point(v.x, S, E);
-                Nb = fixed_point(v.y, S, E);
+                Na = fixed_point<S>(v.x, E);
+                Nb = fixed_point<S>(v.y, E);
             }
-            if (q < np) write_digits2(Xa, Xb, S, p0, N, l * n1 + 2 * q, bias);
+            if (q < np) write_digits2<S>(Xa, Xb, p0, N, l * n1 + 2 * q);
             if (wout) {
                 long long left = __shfl_up_sync(0xffffffffu, Xb, 1);
                 long long right = __shfl_down_sync(0xffffffffu, Xa, 1);
@@ -177,16 +193,19 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
                  : "memory");
 }
 
-template <int LB>
-__global__ __launch_bounds__(SL_THREADS) void slice_staged_kernel(const double* __restrict__ x0,
+constexpr int SL_BLOCKS_PER_SM = 3;   // 3 x (64 KB staged + 8 KB) per SM at n = 256 with two inputs
+
+template <int LB, int S>
+__global__ __launch_bounds__(SL_THREADS, SL_BLOCKS_PER_SM) void slice_staged_kernel(const double* __restrict__ x0,
                                                                   const double* __restrict__ x1, int sh1, AxisView v,
-                                                                  int S, __nv_bfloat16* __restrict__ p0,
+                                                                  __nv_bfloat16* __restrict__ p0,
                                                                   __nv_bfloat16* __restrict__ p1, long long N,
                                                                   int* __restrict__ lexp, double* __restrict__ eout) {
     constexpr int LP = LB / 2;               // line pairs per block
     constexpr int NKG = SL_THREADS / LP;     // k rows in flight
     extern __shared__ unsigned long long sl_smem[];   // [input][k][LB]
-    __shared__ unsigned long long smax[NKG][LB];
+    __shared__ uint32_t shmax[NKG][LB];
+    __shared__ uint32_t slor[NKG][LB];
     __shared__ int sexp[LB];
     unsigned long long* s0 = sl_smem;
     unsigned long long* s1 = sl_smem + (size_t)v.n * LB;
@@ -194,7 +213,6 @@ __global__ __launch_bounds__(SL_THREADS) void slice_staged_kernel(const double* 
     const int la = 2 * lp;                   // first line of the pair within the block
     const long long* b0 = reinterpret_cast<const long long*>(x0);
     const long long* b1 = reinterpret_cast<const long long*>(x1);
-    const long long bias = digit_bias(S);
     for (long long l0 = (long long)blockIdx.x * LB; l0 < v.lines; l0 += (long long)gridDim.x * LB) {
         const long long l = l0 + la;          // lines l, l + 1 (same run: runs hold a multiple of 8 lines)
         const bool valid = l < v.lines;
@@ -208,25 +226,36 @@ __global__ __launch_bounds__(SL_THREADS) void slice_staged_kernel(const double* 
         }
         asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
         __syncthreads();
-        unsigned long long ma = 0, mb = 0;
+        uint32_t ha = 0, hb = 0, oa = 0, ob = 0;
         if (valid) {
             for (int k = kg; k < v.n; k += NKG) {
-                ma = max(ma, s0[k * LB + la] & 0x7FFFFFFFFFFFFFFFull);
-                mb = max(mb, s0[k * LB + la + 1] & 0x7FFFFFFFFFFFFFFFull);
+                const unsigned long long wa = s0[k * LB + la], wb = s0[k * LB + la + 1];
+                ha = max(ha, (uint32_t)(wa >> 32) & 0x7FFFFFFFu);
+                hb = max(hb, (uint32_t)(wb >> 32) & 0x7FFFFFFFu);
+                oa |= (uint32_t)wa;
+                ob |= (uint32_t)wb;
                 if (b1) {
-                    ma = max(ma, abs_bits_shifted((long long)s1[k * LB + la], sh1));
-                    mb = max(mb, abs_bits_shifted((long long)s1[k * LB + la + 1], sh1));
+                    const unsigned long long ua = s1[k * LB + la], ub = s1[k * LB + la + 1];
+                    ha = max(ha, abs_hi_shifted(ua, sh1));
+                    hb = max(hb, abs_hi_shifted(ub, sh1));
+                    oa |= (uint32_t)ua;
+                    ob |= (uint32_t)ub;
                 }
             }
         }
-        smax[kg][la] = ma;
-        smax[kg][la + 1] = mb;
+        shmax[kg][la] = ha;
+        shmax[kg][la + 1] = hb;
+        slor[kg][la] = oa;
+        slor[kg][la + 1] = ob;
         __syncthreads();
         if (threadIdx.x < LB) {
-            unsigned long long m = smax[0][threadIdx.x];
+            uint32_t m = shmax[0][threadIdx.x], o = slor[0][threadIdx.x];
 #pragma unroll 8
-            for (int g = 1; g < NKG; ++g) m = max(m, smax[g][threadIdx.x]);
-            const int E = line_exponent_from_bits(m);
+            for (int g = 1; g < NKG; ++g) {
+                m = max(m, shmax[g][threadIdx.x]);
+                o |= slor[g][threadIdx.x];
+            }
+            const int E = line_exponent(m, o);
             sexp[threadIdx.x] = E;
             if (l0 + threadIdx.x < v.lines) lexp[l0 + threadIdx.x] = E;
         }
@@ -235,12 +264,12 @@ __global__ __launch_bounds__(SL_THREADS) void slice_staged_kernel(const double* 
         if (valid) {
             for (int k = kg; k < v.n; k += NKG) {
                 const long long idx = off + (long long)k * v.stride;
-                write_digits2(fixed_point((long long)s0[k * LB + la], S, Ea),
-                              fixed_point((long long)s0[k * LB + la + 1], S, Eb), S, p0, N, idx, bias);
+                write_digits2<S>(fixed_point<S>((long long)s0[k * LB + la], Ea),
+                                 fixed_point<S>((long long)s0[k * LB + la + 1], Eb), p0, N, idx);
                 if (b1) {
-                    const long long Wa = fixed_point((long long)s1[k * LB + la], S, Ea - sh1);
-                    const long long Wb = fixed_point((long long)s1[k * LB + la + 1], S, Eb - sh1);
-                    write_digits2(Wa, Wb, S, p1, N, idx, bias);
+                    const long long Wa = fixed_point<S>((long long)s1[k * LB + la], Ea - sh1);
+                    const long long Wb = fixed_point<S>((long long)s1[k * LB + la + 1], Eb - sh1);
+                    write_digits2<S>(Wa, Wb, p1, N, idx);
                     if (eout) {
                         s1[k * LB + la] = (unsigned long long)Wa;
                         s1[k * LB + la + 1] = (unsigned long long)Wb;
@@ -267,12 +296,6 @@ __global__ __launch_bounds__(SL_THREADS) void slice_staged_kernel(const double* 
         }
         __syncthreads();
     }
-}
-
-int grid_for(long long n) {
-    long long g = (n + 255) / 256;
-    if (g > 152LL * 16) g = 152LL * 16;
-    return (int)(g < 1 ? 1 : g);
 }
 
 // ------------------------------------------------------- operator slicing
@@ -323,7 +346,6 @@ void slice_operators_host(const std::vector<const std::vector<double>*>& ops, in
 bool g_oz_attr = false;
 // swizzle of the MN-major input tiles: one atom spans the tile's BN lines
 constexpr CUtensorMapSwizzle kMnSwizzle = oz::BN * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
-bool g_sl_attr[2] = {false, false};
 
 // Upload one operator digit set and build its tensor maps.
 int upload_set(OzSet& set, const std::vector<__nv_bfloat16>& sl, int n, int S, int na, int rexp_index,
@@ -476,48 +498,83 @@ void oz_free(MixedState* M) {
 
 namespace {
 
-// Slice one or two FP64 inputs along `axis` into the digit planes 0 / 1, the
-// second one taken as x1 * 2^sh1; mass_out (optional) receives the mass
-// operator along `axis` applied to x1 (x0 on the x axis), exactly from the
-// fixed-point integers.
-void oz_slice(const tfde_problem* P, int axis, const double* x0, const double* x1, int sh1, double* mass_out,
-              int S, cudaStream_t s) {
+// One y / z slicing launch: the largest shared-memory carve-out (so that
+// several blocks share an SM) and one wave of resident blocks over the line
+// groups (a partial second wave would leave SMs idle at the end).
+template <int LB, int S>
+void staged_launch(long long groups, size_t smem, cudaStream_t s, const double* x0, const double* x1, int sh1,
+                   const AxisView& v, __nv_bfloat16* p0, __nv_bfloat16* p1, long long N, int* lexp, double* eout) {
+    static bool attr = false;
+    static size_t occ_smem = 0;
+    static int occ = 0;
+    if (!attr) {
+        cudaFuncSetAttribute(slice_staged_kernel<LB, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(slice_staged_kernel<LB, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        attr = true;
+    }
+    if (occ_smem != smem) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, slice_staged_kernel<LB, S>, SL_THREADS, smem) !=
+                cudaSuccess || occ < 1)
+            occ = 1;
+        occ_smem = smem;
+    }
+    const long long blocks = std::max<long long>(1, std::min<long long>(groups, (long long)tc::num_sms() * occ));
+    slice_staged_kernel<LB, S><<<(unsigned)blocks, SL_THREADS, smem, s>>>(x0, x1, sh1, v, p0, p1, N, lexp, eout);
+}
+
+// One slicing launch with S digits (see oz_slice).
+template <int S>
+void oz_slice_s(const tfde_problem* P, int axis, const double* x0, const double* x1, int sh1, double* mass_out,
+                cudaStream_t s) {
     MixedState* M = mixed(P);
     const AxisView v = axis_view(P->n, axis);
     const long long N = (long long)P->N;
-    stats_count_launch();
     if (axis == 0) {
-        slice_x_kernel<<<grid_for(v.lines * 32), 256, 0, s>>>(x0, P->n[0], v.lines, S, M->oz_planes[0], N,
-                                                               M->oz_lexp, mass_out);
-    } else {
-        // 16 lines per block: with 64 KB of staged lines per block (n = 256, two
-        // inputs) three blocks share an SM, so one block's loads overlap another's
-        // digit writes; 32-line blocks would fill an SM alone and alternate the
-        // two phases.  32 lines only for short lines, where a 16-line block would
-        // stage too little to stream well.
-        const int nin = x1 ? 2 : 1;
-        const bool wide = (size_t)nin * v.n * 16 * 8 < 16 * 1024;
-        const int LB = wide ? 32 : 16;
-        const size_t smem = (size_t)nin * v.n * LB * 8;
-        long long blocks = (v.lines + LB - 1) / LB;
-        const long long per_sm = std::max<long long>(1, (long long)(220 * 1024 / std::max<size_t>(smem, 1)));
-        if (blocks > 152LL * per_sm) blocks = 152LL * per_sm;
-        if (wide) {
-            if (!g_sl_attr[0]) {
-                cudaFuncSetAttribute(slice_staged_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-                g_sl_attr[0] = true;
-            }
-            slice_staged_kernel<32><<<(unsigned)blocks, SL_THREADS, smem, s>>>(x0, x1, sh1, v, S, M->oz_planes[0],
-                                                                             M->oz_planes[1], N, M->oz_lexp, mass_out);
-        } else {
-            if (!g_sl_attr[1]) {
-                cudaFuncSetAttribute(slice_staged_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-                g_sl_attr[1] = true;
-            }
-            slice_staged_kernel<16><<<(unsigned)blocks, SL_THREADS, smem, s>>>(x0, x1, sh1, v, S, M->oz_planes[0],
-                                                                             M->oz_planes[1], N, M->oz_lexp, mass_out);
-        }
+        // one wave of resident blocks, each warp looping over lines
+        static int occ_x = 0;
+        if (!occ_x && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_x, slice_x_kernel<S>, 256, 0) != cudaSuccess ||
+                       occ_x < 1))
+            occ_x = 1;
+        long long blocks = (v.lines + 7) / 8;
+        blocks = std::min<long long>(blocks, (long long)tc::num_sms() * occ_x);
+        slice_x_kernel<S><<<(unsigned)std::max<long long>(blocks, 1), 256, 0, s>>>(x0, P->n[0], v.lines,
+                                                                                   M->oz_planes[0], N, M->oz_lexp,
+                                                                                   mass_out);
+        return;
     }
+    // 16 lines per block: with 64 KB of staged lines per block (n = 256, two
+    // inputs) three blocks share an SM, so one block's loads overlap another's
+    // digit writes; 32-line blocks would fill an SM alone and alternate the
+    // two phases.  32 lines only for short lines, where a 16-line block would
+    // stage too little to stream well.
+    const int nin = x1 ? 2 : 1;
+    const bool wide = (size_t)nin * v.n * 16 * 8 < 16 * 1024;
+    const int LB = wide ? 32 : 16;
+    const size_t smem = (size_t)nin * v.n * LB * 8;
+    const long long groups = (v.lines + LB - 1) / LB;
+    if (wide) staged_launch<32, S>(groups, smem, s, x0, x1, sh1, v, M->oz_planes[0], M->oz_planes[1], N, M->oz_lexp,
+                                   mass_out);
+    else staged_launch<16, S>(groups, smem, s, x0, x1, sh1, v, M->oz_planes[0], M->oz_planes[1], N, M->oz_lexp,
+                              mass_out);
+}
+
+// Slice one or two FP64 inputs along `axis` into the digit planes 0 / 1, the
+// second one taken as x1 * 2^sh1; mass_out (optional) receives the mass
+// operator along `axis` applied to x1 (x0 on the x axis), exactly from the
+// fixed-point integers.  S in [2, OZ_SLICES] (checked by the caller).
+void oz_slice(const tfde_problem* P, int axis, const double* x0, const double* x1, int sh1, double* mass_out,
+              int S, cudaStream_t s) {
+    stats_count_launch();
+    switch (S) {
+        case 2: oz_slice_s<2>(P, axis, x0, x1, sh1, mass_out, s); break;
+        case 3: oz_slice_s<3>(P, axis, x0, x1, sh1, mass_out, s); break;
+        case 4: oz_slice_s<4>(P, axis, x0, x1, sh1, mass_out, s); break;
+        case 5: oz_slice_s<5>(P, axis, x0, x1, sh1, mass_out, s); break;
+        case 6: oz_slice_s<6>(P, axis, x0, x1, sh1, mass_out, s); break;
+        default: oz_slice_s<7>(P, axis, x0, x1, sh1, mass_out, s); break;
+    }
+    static_assert(OZ_SLICES == 7, "one slicing instance per digit count");
 }
 
 // out = vsign * sum_seg Op_seg (planes of input seg.input) [+ asign * addend]
