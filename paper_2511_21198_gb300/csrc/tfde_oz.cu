@@ -193,10 +193,8 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
                  : "memory");
 }
 
-constexpr int SL_BLOCKS_PER_SM = 3;   // 3 x (64 KB staged + 8 KB) per SM at n = 256 with two inputs
-
 template <int LB, int S>
-__global__ __launch_bounds__(SL_THREADS, SL_BLOCKS_PER_SM) void slice_staged_kernel(const double* __restrict__ x0,
+__global__ __launch_bounds__(SL_THREADS) void slice_staged_kernel(const double* __restrict__ x0,
                                                                   const double* __restrict__ x1, int sh1, AxisView v,
                                                                   __nv_bfloat16* __restrict__ p0,
                                                                   __nv_bfloat16* __restrict__ p1, long long N,
@@ -498,28 +496,21 @@ void oz_free(MixedState* M) {
 
 namespace {
 
-// One y / z slicing launch: the largest shared-memory carve-out (so that
-// several blocks share an SM) and one wave of resident blocks over the line
-// groups (a partial second wave would leave SMs idle at the end).
+// One y / z slicing launch (grid: the line groups, at most as many blocks as
+// fit the SMs' shared memory three times over; blocks loop over groups).
+// Measured on GB300: sizing the grid to one wave of resident blocks with the
+// largest carve-out (3 blocks per SM instead of 2) was no faster: the
+// integer pipe, not latency, bounds these kernels.
 template <int LB, int S>
 void staged_launch(long long groups, size_t smem, cudaStream_t s, const double* x0, const double* x1, int sh1,
                    const AxisView& v, __nv_bfloat16* p0, __nv_bfloat16* p1, long long N, int* lexp, double* eout) {
     static bool attr = false;
-    static size_t occ_smem = 0;
-    static int occ = 0;
     if (!attr) {
         cudaFuncSetAttribute(slice_staged_kernel<LB, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(slice_staged_kernel<LB, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
         attr = true;
     }
-    if (occ_smem != smem) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, slice_staged_kernel<LB, S>, SL_THREADS, smem) !=
-                cudaSuccess || occ < 1)
-            occ = 1;
-        occ_smem = smem;
-    }
-    const long long blocks = std::max<long long>(1, std::min<long long>(groups, (long long)tc::num_sms() * occ));
+    const long long per_sm = std::max<long long>(1, (long long)(220 * 1024 / std::max<size_t>(smem, 1)));
+    const long long blocks = std::max<long long>(1, std::min<long long>(groups, 152LL * per_sm));
     slice_staged_kernel<LB, S><<<(unsigned)blocks, SL_THREADS, smem, s>>>(x0, x1, sh1, v, p0, p1, N, lexp, eout);
 }
 
@@ -531,16 +522,10 @@ void oz_slice_s(const tfde_problem* P, int axis, const double* x0, const double*
     const AxisView v = axis_view(P->n, axis);
     const long long N = (long long)P->N;
     if (axis == 0) {
-        // one wave of resident blocks, each warp looping over lines
-        static int occ_x = 0;
-        if (!occ_x && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_x, slice_x_kernel<S>, 256, 0) != cudaSuccess ||
-                       occ_x < 1))
-            occ_x = 1;
-        long long blocks = (v.lines + 7) / 8;
-        blocks = std::min<long long>(blocks, (long long)tc::num_sms() * occ_x);
-        slice_x_kernel<S><<<(unsigned)std::max<long long>(blocks, 1), 256, 0, s>>>(x0, P->n[0], v.lines,
-                                                                                   M->oz_planes[0], N, M->oz_lexp,
-                                                                                   mass_out);
+        // one warp per line; up to 16 blocks of 8 warps per SM, warps looping over lines
+        const long long blocks = std::max<long long>(1, std::min<long long>((v.lines + 7) / 8, 152LL * 16));
+        slice_x_kernel<S><<<(unsigned)blocks, 256, 0, s>>>(x0, P->n[0], v.lines, M->oz_planes[0], N, M->oz_lexp,
+                                                          mass_out);
         return;
     }
     // 16 lines per block: with 64 KB of staged lines per block (n = 256, two
