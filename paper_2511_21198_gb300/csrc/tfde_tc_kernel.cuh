@@ -429,6 +429,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const long long tile = lt / p.mhalves;
             const int mh = (int)(lt % p.mhalves);
             const int mrow0 = mh * BM + 32 * q;   // first output row of this warp
+            // Lambda row factors of this lane's 8 rows, once per tile (the rows
+            // are the same for every column chunk below; grouped instances,
+            // short of registers, load them per chunk)
+            float lra[8], lrb[8];
+            const bool lam = !b_kmajor && p.lam_ra != nullptr;
+            if (!GROUPED && lam) {
+#pragma unroll
+                for (int i8 = 0; i8 < 8; ++i8) {
+                    const int m = mrow0 + i8 * 4 + rsub;
+                    lra[i8] = m < p.n ? __ldg(p.lam_ra + m) : 1.f;
+                    lrb[i8] = m < p.n ? __ldg(p.lam_rb + m) : 0.f;
+                }
+            }
             for (int cc = 0; cc < BN / 2; cc += 32) {
                 const int c0 = half * (BN / 2) + cc;
                 // Output positions of this lane: 8 groups i8 of up to 4 consecutive
@@ -476,6 +489,26 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                                              (vmask >> i8) & 1u ? cnt0 : 0);
                     }
                 }
+                // Lambda column factors of this lane's 4 columns, issued before
+                // the accumulator read so that their latency overlaps it
+                float U[4] = {0.f, 0.f, 0.f, 0.f}, V[4] = {0.f, 0.f, 0.f, 0.f};
+                if (lam && (vmask & 1u)) {
+                    const int c = (int)((tile * (BN / 64) + c0 / 64) % p.nbc) * 64 + (c0 & 63) + cq;
+                    if (c + 4 <= p.C && ((reinterpret_cast<uintptr_t>(p.lam_U + c) |
+                                          reinterpret_cast<uintptr_t>(p.lam_V + c)) & 15) == 0) {
+                        const float4 u4 = __ldg(reinterpret_cast<const float4*>(p.lam_U + c));
+                        const float4 v4 = __ldg(reinterpret_cast<const float4*>(p.lam_V + c));
+                        U[0] = u4.x; U[1] = u4.y; U[2] = u4.z; U[3] = u4.w;
+                        V[0] = v4.x; V[1] = v4.y; V[2] = v4.z; V[3] = v4.w;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (c + k < p.C) {
+                                U[k] = __ldg(p.lam_U + c + k);
+                                V[k] = __ldg(p.lam_V + c + k);
+                            }
+                    }
+                }
                 uint32_t r[32];
                 tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN + c0), r);
 #pragma unroll
@@ -493,20 +526,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         v[i8][k] = b_kmajor ? stg[(cq + k) * EPI_STRIDE + i8 * 4 + rsub]
                                             : stg[(i8 * 4 + rsub) * EPI_STRIDE + cq + k];
                 __syncwarp();   // the staging buffer is free for the next chunk
-                if (!b_kmajor && p.lam_ra && (vmask & 1u)) {   // rows ascend: none valid if the first is not
-                    const int c = (int)((tile * (BN / 64) + c0 / 64) % p.nbc) * 64 + (c0 & 63) + cq;
-                    float U[4] = {0.f, 0.f, 0.f, 0.f}, V[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (c + k < p.C) {
-                            U[k] = __ldg(p.lam_U + c + k);
-                            V[k] = __ldg(p.lam_V + c + k);
-                        }
+                if (lam && (vmask & 1u)) {   // rows ascend: none valid if the first is not
 #pragma unroll
                     for (int i8 = 0; i8 < 8; ++i8)
                         if ((vmask >> i8) & 1u) {
                             const int m = mrow0 + i8 * 4 + rsub;
-                            const float ra = __ldg(p.lam_ra + m), rb = __ldg(p.lam_rb + m);
+                            const float ra = GROUPED ? __ldg(p.lam_ra + m) : lra[i8];
+                            const float rb = GROUPED ? __ldg(p.lam_rb + m) : lrb[i8];
                             float tl = 0.f;
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
