@@ -62,8 +62,9 @@ def parse_args(argv=None):
     ap.add_argument("--cnn-steps", type=int, default=100,
                     help="CN steps of the warm-start evaluation at n = 128 (0 skips training and evaluation)")
     ap.add_argument("--cnn-train-steps", type=int, default=600, help="Adam steps of the warm-start training")
-    ap.add_argument("--guess-order", type=int, default=2,
-                    help="initial guess of the mixed path: 0 previous step, 1/2 polynomial extrapolation")
+    ap.add_argument("--guess-order", type=int, default=3,
+                    help="initial guess of the mixed path: 0 previous step, 1/2 polynomial extrapolation, "
+                         "3 order 2 with its minimal-residual correction over the stored history")
     return ap.parse_args(argv)
 
 
@@ -373,8 +374,10 @@ def run_ours(args):
                        "k_plus": list(W["kp"]), "k_minus": list(W["km"]), "dt": dt, "tol": tol,
                        "solver": "PCG(tau) inner FP32 / split-BF16 tcgen05, FP64 iterative refinement",
                        "initial_guess": ("previous step u^(m-1)" if args.guess_order == 0 else
-                                         f"order-{args.guess_order} polynomial extrapolation in time "
-                                         "(A x0 from stored A u, no extra operator application)"),
+                                         f"order-{min(args.guess_order, 2)} polynomial extrapolation in time"
+                                         + (" with a minimal-residual correction over the history differences"
+                                            if args.guess_order >= 3 else "")
+                                         + " (A x0 from stored A u, no extra operator application)"),
                        "fp64_path_initial_guess": "previous step u^(m-1)",
                        "step_api": "tfde_cn_advance (chained: A u^(m-1) = b^(m-1) - r^(m-1))",
                        "l2": "inputs larger than L2 (each FP64 vector 134 MB, working set > 2 GB)",

@@ -180,7 +180,7 @@ int tfde_cn_advance_guess(const tfde_problem* prob, double* u, const double* F_h
 
 int tfde_set_guess_order(tfde_problem* prob, int order) {
     if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
-    if (order < 0 || order > 2) return set_error(TFDE_EINVAL, "guess order must be 0, 1 or 2");
+    if (order < 0 || order > 3) return set_error(TFDE_EINVAL, "guess order must be 0, 1, 2 or 3");
     prob->guess_order = order;
     return TFDE_OK;
 }

@@ -78,10 +78,15 @@ void launch_cn_first(size_t N, const double* AN, const double* Ku, const double*
 // t = 2 AN + dt F; b <- t + r - b; r <- b_new + r - b_old  (chained CN step; norms as above)
 void launch_cn_chain(size_t N, const double* AN, const double* F, double dt, double* b, double* r, double* part,
                      double* norms2, cudaStream_t s);
-// chained CN step with extrapolated initial guess written into u (see tfde_kernels64.cu)
+// chained CN step with extrapolated initial guess written into u (see
+// tfde_kernels64.cu); order 3: x0 = g[0] u + g[1] U1 + g[2] U2 (order 2 when g is null)
 void launch_cn_chain_extrap(size_t N, const double* AN, const double* F, double dt, double* b, double* r, double* u,
-                            const double* U1, const double* AU1, double* U2, double* AU2, int order, double* part,
-                            double* norms2, cudaStream_t s);
+                            const double* U1, const double* AU1, double* U2, double* AU2, int order, const double* g,
+                            double* part, double* norms2, cudaStream_t s);
+// the five sums of the minimal-residual correction of the order-2 guess into
+// out5 (device): <e1,e1>, <e1,e2>, <e2,e2>, <e1,r_e>, <e2,r_e> (see tfde_kernels64.cu)
+void launch_cn_mr_dots(size_t N, const double* AN, const double* F, double dt, const double* b, const double* r,
+                       const double* AU1, const double* AU2, double* part, double* out5, cudaStream_t s);
 // F = cP PPP + cS (SPP + PSP + PPS) from 1-D arrays [Px|Py|Pz|Sx|Sy|Sz]
 void launch_source_assemble_f64(const double* oned, const int n[3], double cP, double cS, double* F,
                                 cudaStream_t s);
@@ -122,8 +127,10 @@ struct tfde_problem {
     // chained CN advance: W_B / W_R hold b^{m-1} and its final true residual
     const double* chain_u = nullptr;
     bool chain_ok = false;
-    // polynomial-extrapolation initial guess of the chained advance: order
-    // (0: previous step), and the history (u, A u) of the two steps before
+    // initial guess of the chained advance: polynomial extrapolation of this
+    // order (0: previous step; 3: order 2 with its minimal-residual
+    // correction over the history), and the history (u, A u) of the two
+    // steps before
     int guess_order = 0;
     // ||b||^2, ||r_0||^2 of the last cn_prepare in red_out[NORMS_SLOT..+1] (device)
     bool norms_ready = false;
@@ -137,6 +144,8 @@ struct tfde_problem {
 namespace tfde {
 // red_out slot of the fused ||b||^2, ||r_0||^2 of cn_prepare
 constexpr int kNormsSlot = 250;
+// red_out slots of the five sums of the minimal-residual guess correction
+constexpr int kMrSlot = 240;
 // solver internals (tfde_solvers.cu)
 int apply_A64(const tfde_problem* P, int op, const double* x, double* y, cudaStream_t s);
 int apply_Pinv64(const tfde_problem* P, const double* r, double* z, cudaStream_t s);

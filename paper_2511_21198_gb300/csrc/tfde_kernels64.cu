@@ -3,6 +3,7 @@
 // preconditioner (Eq. (diag_tau_pre)), and the Krylov vector kernels and
 // deterministic reductions shared by both precisions.
 #include "tfde_internal.h"
+#include "tfde_pow2conv.cuh"
 #include "tfde_stats.h"
 
 namespace tfde {
@@ -419,11 +420,14 @@ __global__ void cn_chain_kernel(long long N, const double* __restrict__ AN, cons
 // r = b^m - A x0 from the same linear combination of the stored A u (no
 // operator application), and (u^{m-1}, A u^{m-1}) into the H2 slot, which
 // the caller then relabels as H1.
+// order 3: x0 = g0 u^{m-1} + g1 u^{m-2} + g2 u^{m-3} with the caller's
+// coefficients (the order-2 extrapolation corrected by cn_mr_dots_kernel).
 __global__ void cn_chain_extrap_kernel(long long N, const double* __restrict__ AN, const double* __restrict__ F,
                                        double dt, double* __restrict__ b, double* __restrict__ r,
                                        double* __restrict__ u, const double* __restrict__ U1,
                                        const double* __restrict__ AU1, double* __restrict__ U2,
-                                       double* __restrict__ AU2, int order, double* __restrict__ part) {
+                                       double* __restrict__ AU2, int order, double g0, double g1, double g2,
+                                       double* __restrict__ part) {
     double bb = 0.0, rr = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const double ui = u[i];
@@ -433,9 +437,12 @@ __global__ void cn_chain_extrap_kernel(long long N, const double* __restrict__ A
         if (order == 1) {
             x = fma(2.0, ui, -U1[i]);
             ax = fma(2.0, au, -AU1[i]);
-        } else if (order >= 2) {
+        } else if (order == 2) {
             x = fma(3.0, ui - U1[i], U2[i]);
             ax = fma(3.0, au - AU1[i], AU2[i]);
+        } else if (order >= 3) {
+            x = fma(g0, ui, fma(g1, U1[i], g2 * U2[i]));
+            ax = fma(g0, au, fma(g1, AU1[i], g2 * AU2[i]));
         }
         const double rn = bn - ax;
         b[i] = bn;
@@ -453,6 +460,45 @@ __global__ void cn_chain_extrap_kernel(long long N, const double* __restrict__ A
             part[blockIdx.x] = t1;
             part[gridDim.x + blockIdx.x] = t2;
         }
+    }
+}
+
+// Minimal-residual correction of the order-2 extrapolated guess of a chained
+// CN step.  With a_k = A u^{m-1-k} (a_0 = b^{m-1} - r^{m-1}, a_1, a_2 from the
+// history), the extrapolation's residual is r_e = b^m - (3 a_0 - 3 a_1 + a_2),
+// b^m = 2 A_N u^{m-1} + dt F - a_0, and the history differences
+// e_1 = a_0 - a_1, e_2 = a_0 - 2 a_1 + a_2 are the operator images of
+// d_1 = u^{m-1} - u^{m-2}, d_2 = u^{m-1} - 2 u^{m-2} + u^{m-3}.  Sums over the
+// grid: part[q] for q = <e1,e1>, <e1,e2>, <e2,e2>, <e1,r_e>, <e2,r_e>; the
+// caller solves the 2 x 2 normal equations for the c minimising
+// ||r_e - c1 e1 - c2 e2|| and takes x0 = x_e + c1 d1 + c2 d2 (no operator
+// application).  The sums only set two coefficients (their error changes
+// the guess, not the solution): every term is formed in FP32 from the FP64
+// values truncated by integer operations (no FP64 arithmetic), per-thread
+// sums in FP32, the block and grid sums in FP64.
+__global__ void cn_mr_dots_kernel(long long N, const double* __restrict__ AN, const double* __restrict__ F, float dtf,
+                                  const double* __restrict__ b, const double* __restrict__ r,
+                                  const double* __restrict__ AU1, const double* __restrict__ AU2,
+                                  double* __restrict__ part) {
+    auto cv = [](const double* p, long long i) {
+        return f64_to_f32_rz((unsigned long long)__double_as_longlong(__ldg(p + i)));
+    };
+    float s[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const float a0 = cv(b, i) - cv(r, i), a1 = cv(AU1, i), a2 = cv(AU2, i);
+        const float bn = fmaf(2.f, cv(AN, i), F ? dtf * cv(F, i) : 0.f) - a0;
+        const float e1 = a0 - a1, e2 = e1 - (a1 - a2);
+        const float re = bn - fmaf(3.f, e1, a2);
+        s[0] = fmaf(e1, e1, s[0]);
+        s[1] = fmaf(e1, e2, s[1]);
+        s[2] = fmaf(e2, e2, s[2]);
+        s[3] = fmaf(e1, re, s[3]);
+        s[4] = fmaf(e2, re, s[4]);
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const double t = block_sum((double)s[q]);
+        if (threadIdx.x == 0) part[(long long)q * gridDim.x + blockIdx.x] = t;
     }
 }
 
@@ -570,13 +616,23 @@ void launch_cn_chain(size_t N, const double* AN, const double* F, double dt, dou
 }
 
 void launch_cn_chain_extrap(size_t N, const double* AN, const double* F, double dt, double* b, double* r, double* u,
-                            const double* U1, const double* AU1, double* U2, double* AU2, int order, double* part,
-                            double* norms2, cudaStream_t s) {
+                            const double* U1, const double* AU1, double* U2, double* AU2, int order, const double* g,
+                            double* part, double* norms2, cudaStream_t s) {
     stats_count_launch();
-    const int g = grid_for((long long)N);
-    cn_chain_extrap_kernel<<<g, kThreads, 0, s>>>((long long)N, AN, F, dt, b, r, u, U1, AU1, U2, AU2, order,
-                                                  norms2 ? part : nullptr);
-    finish_norms(part, g, norms2, s);
+    const int grid = grid_for((long long)N);
+    const double g0 = g ? g[0] : 0.0, g1 = g ? g[1] : 0.0, g2 = g ? g[2] : 0.0;
+    cn_chain_extrap_kernel<<<grid, kThreads, 0, s>>>((long long)N, AN, F, dt, b, r, u, U1, AU1, U2, AU2,
+                                                     order >= 3 && !g ? 2 : order, g0, g1, g2,
+                                                     norms2 ? part : nullptr);
+    finish_norms(part, grid, norms2, s);
+}
+
+void launch_cn_mr_dots(size_t N, const double* AN, const double* F, double dt, const double* b, const double* r,
+                       const double* AU1, const double* AU2, double* part, double* out5, cudaStream_t s) {
+    stats_count_launch();
+    const int grid = grid_for((long long)N);
+    cn_mr_dots_kernel<<<grid, kThreads, 0, s>>>((long long)N, AN, F, (float)dt, b, r, AU1, AU2, part);
+    launch_reduce_finish(part, grid, 5, out5, s);
 }
 
 void launch_source_assemble_f64(const double* oned, const int n[3], double cP, double cS, double* F,

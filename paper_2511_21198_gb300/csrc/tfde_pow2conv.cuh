@@ -94,6 +94,18 @@ TFDE_HD double f32_pow2_to_f64(float f, int j) {
     return bits_to_f64(sign | (E << 52) | ((unsigned long long)frac << 29));
 }
 
+// x (FP64 bits u) rounded toward zero to FP32 precision, for sums that need
+// only a few digits: values below the FP32 normal range become signed zero,
+// values above it (and infinities, NaNs) signed infinity.
+TFDE_HD float f64_to_f32_rz(unsigned long long u) {
+    const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+    const uint32_t sign = hi & 0x80000000u;
+    const int E = (int)((hi >> 20) & 0x7FFu) - 896;
+    if (E <= 0) return bits_to_f32(sign);
+    if (E >= 255) return bits_to_f32(sign | 0x7F800000u);
+    return bits_to_f32(sign | ((uint32_t)E << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+
 // k with sc = 2^k exactly and |k| < 512, else false
 inline bool pow2_exponent(double sc, int* k) {
     int e = 0;
