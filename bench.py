@@ -163,6 +163,12 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
+def workload_config(n: int, W: dict, dt: float, tol: float) -> dict:
+    """The keys that name the workload, shared by both arms' JSON lines."""
+    return {"workload": WORKLOAD, "n": n, "unknowns": n ** 3, "delta": list(W["delta"]),
+            "k_plus": list(W["kp"]), "k_minus": list(W["km"]), "dt": dt, "tol": tol}
+
+
 def kernel_hash() -> str:
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
@@ -370,8 +376,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16-split/fp32 inner, fp64 refinement",
             "data": "synthetic: manufactured solution exp(-t) x^2(1-x)^2 y^2(1-y)^2 z^2(1-z)^2",
-            "config": {"workload": WORKLOAD, "n": n, "unknowns": n ** 3, "delta": list(W["delta"]),
-                       "k_plus": list(W["kp"]), "k_minus": list(W["km"]), "dt": dt, "tol": tol,
+            "config": {**workload_config(n, W, dt, tol),
                        "solver": "PCG(tau) inner FP32 / split-BF16 tcgen05, FP64 iterative refinement",
                        "initial_guess": ("previous step u^(m-1)" if args.guess_order == 0 else
                                          f"order-{min(args.guess_order, 2)} polynomial extrapolation in time"
@@ -544,7 +549,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": steps, "warmup": 1, "ms_per_step": 1e3 * sec / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "unknowns": n ** 3},
+            "config": {**workload_config(n, W, dt, W["tol"]), "solver": "oracle PCG(tau), FP64, x0 = u^(m-1)"},
             "cpu_baseline": {"kind": "oracle", "cores": cpu_cores(), "value": value, "unit": UNIT,
                              "sample": f"{steps} CN step(s) of the n={n} workload (numpy FP64 oracle)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
