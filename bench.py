@@ -59,6 +59,8 @@ def parse_args(argv=None):
     ap.add_argument("--batch-count", type=int, default=64,
                     help="problems of the uneven batched workload (0 skips it)")
     ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--batch-guess-order", type=int, default=3,
+                    help="initial guess of the batched workload's chained steps (as --guess-order)")
     ap.add_argument("--cnn-steps", type=int, default=100,
                     help="CN steps of the warm-start evaluation at n = 128 (0 skips training and evaluation)")
     ap.add_argument("--cnn-train-steps", type=int, default=600, help="Adam steps of the warm-start training")
@@ -329,7 +331,7 @@ def run_ours(args):
     # ---- batched workload: uneven problems, lock-step batched solve vs a loop
     batched = None
     if args.batch_count > 0 and args.batch_steps > 0:
-        batched = run_batched(T, args.batch_count, args.batch_steps, dev, stream)
+        batched = run_batched(T, args.batch_count, args.batch_steps, dev, stream, args.batch_guess_order)
 
     # ---- learned warm start: train at n = 64, evaluate at n = 128
     warm = None
@@ -470,13 +472,14 @@ def run_warm_start(T, train_steps, eval_steps, dev, stream):
     return out
 
 
-def run_batched(T, count, steps, dev, stream):
+def run_batched(T, count, steps, dev, stream, guess_order=0):
     """The uneven batched workload: `count` problems (n per axis from
     {32, 48, 64, 96, 128}, delta ~ U(0.1, 0.9), k+- ~ U(0.5, 2), seed 4),
     smoothed-noise u0, f = 0, dt = 1/steps, tol 1e-8; `steps` chained CN steps
     through tfde_batch_cn_advance, then the same steps through a loop of
-    single-problem tfde_cn_advance calls.  Timed with CUDA events on the
-    stream; inputs resident on the device."""
+    single-problem tfde_cn_advance calls, both with the initial guess of
+    `guess_order`.  Timed with CUDA events on the stream; inputs resident on
+    the device."""
     import torch
     probs = inp.batched_instances(count=count, seed=4)
     dt = 1.0 / steps
@@ -487,7 +490,9 @@ def run_batched(T, count, steps, dev, stream):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {"workload": f"{count} problems, n in {{32,48,64,96,128}}, non-symmetric, {steps} CN steps, tol 1e-8",
            "unknowns": unknowns}
+    out["initial_guess_order"] = guess_order
     B = T.tfde_batch_create(params, 20, stream)
+    T.tfde_batch_set_guess_order(B, guess_order)
     try:
         us = [u.clone() for u in u0]
         T.tfde_batch_cn_advance(B, us, None, True, 1e-8, stream)    # warm-up step (restarts the chain)
@@ -506,6 +511,8 @@ def run_batched(T, count, steps, dev, stream):
     finally:
         T.tfde_batch_destroy(B)
     hs = [T.tfde_assemble(p, T.TFDE_MIXED, stream) for p in params]
+    for h in hs:
+        T.tfde_set_guess_order(h, guess_order)
     try:
         us = [u.clone() for u in u0]
         for i, h in enumerate(hs):

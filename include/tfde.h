@@ -243,6 +243,15 @@ int tfde_batch_destroy(tfde_batch* batch);
 int tfde_batch_count(const tfde_batch* batch);
 
 /*
+ * tfde_batch_set_guess_order -- the initial guess of tfde_batch_cn_advance's
+ *   chained steps for every problem of the batch, as tfde_set_guess_order
+ *   (orders 0..3, 0 by default; each problem keeps its own history, and
+ *   order 3 reads its correction sums back once per problem and step).
+ *   Errors: TFDE_EINVAL for a NULL batch or an order outside 0..3.
+ */
+int tfde_batch_set_guess_order(tfde_batch* batch, int order);
+
+/*
  * tfde_batch_cn_advance -- one CN step u_i^{m-1} -> u_i^m IN PLACE for every
  * problem i of the batch, with the chained right-hand side and initial
  * residual of tfde_cn_advance (x0 = u_i^{m-1}).

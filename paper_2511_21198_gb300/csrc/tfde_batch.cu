@@ -604,6 +604,13 @@ int batch_destroy(tfde_batch* B) { return free_batch(B); }
 
 extern "C" int tfde_batch_count(const tfde_batch* B) { return B ? B->count : 0; }
 
+extern "C" int tfde_batch_set_guess_order(tfde_batch* B, int order) {
+    if (!B) return tfde::set_error(TFDE_EINVAL, "NULL batch");
+    if (order < 0 || order > 3) return tfde::set_error(TFDE_EINVAL, "guess order must be 0, 1, 2 or 3");
+    for (tfde_problem* P : B->P) P->guess_order = order;
+    return TFDE_OK;
+}
+
 namespace tfde {
 
 int batch_cn_advance(tfde_batch* B, double* const* u, const double* const* F, int restart_chain, double tol,

@@ -62,7 +62,7 @@ _lib = None
 EXPORTS = ["tfde_assemble", "tfde_destroy", "tfde_matvec", "tfde_precond", "tfde_pcg", "tfde_pgmres",
            "tfde_cn_step", "tfde_cn_advance", "tfde_set_guess_order", "tfde_source_example2", "tfde_coefficients", "tfde_host_coefficients",
            "tfde_stats_reset", "tfde_stats_get", "tfde_mass_apply_noalloc", "tfde_batch_create", "tfde_batch_destroy",
-           "tfde_batch_count", "tfde_batch_cn_advance", "tfde_cn_advance_guess", "tfde_cnn_create", "tfde_cnn_destroy",
+           "tfde_batch_count", "tfde_batch_set_guess_order", "tfde_batch_cn_advance", "tfde_cn_advance_guess", "tfde_cnn_create", "tfde_cnn_destroy",
            "tfde_cnn_set_params", "tfde_cnn_get_params", "tfde_cnn_get_grads", "tfde_cnn_predict", "tfde_cnn_accumulate",
            "tfde_cnn_adam_step", "tfde_last_error", "tfde_version"]
 
@@ -98,6 +98,7 @@ def load(path: str | None = None):
         "tfde_batch_create": ([POINTER(tfde_params), c_int, c_int, vp, POINTER(c_void_p)], c_int),
         "tfde_batch_destroy": ([vp], c_int),
         "tfde_batch_count": ([vp], c_int),
+        "tfde_batch_set_guess_order": ([vp, c_int], c_int),
         "tfde_batch_cn_advance": ([vp, POINTER(c_void_p), POINTER(c_void_p), c_int, c_double, POINTER(tfde_info),
                                    vp], c_int),
         "tfde_cn_advance_guess": ([vp, vp, vp, vp, c_int, c_double, POINTER(tfde_info), POINTER(c_int), vp], c_int),
@@ -204,6 +205,10 @@ def tfde_cn_step(prob: int, u_prev, F_half, x0, u_next, tol: float, stream=None,
 
 def tfde_set_guess_order(prob: int, order: int) -> None:
     _check(load().tfde_set_guess_order(prob, order), "tfde_set_guess_order")
+
+
+def tfde_batch_set_guess_order(batch: int, order: int) -> None:
+    _check(load().tfde_batch_set_guess_order(batch, order), "tfde_batch_set_guess_order")
 
 
 def tfde_cn_advance(prob: int, u, F_half, restart: bool, tol: float, stream=None, check: bool = True) -> tfde_info:

@@ -111,6 +111,38 @@ def test_batch_large_uneven_sizes(T):
             T.tfde_destroy(h)
 
 
+def test_batch_guess_order_same_trajectory(T):
+    """Batched chained steps with the corrected extrapolated guess (order 3)
+    reach the trajectories of the previous-step guess at tight residuals, in
+    fewer iterations once the history is built."""
+    probs = small_batch(5, 13, sizes=(16, 24, 32))
+    dt = 0.05
+    params = [T.make_params(p["n"], p["delta"], p["kp"], p["km"], dt) for p in probs]
+    B0 = T.tfde_batch_create(params, 20)
+    B3 = T.tfde_batch_create(params, 20)
+    T.tfde_batch_set_guess_order(B3, 3)
+    try:
+        u0 = [inp.smoothed_uniform(tuple(reversed(p["n"])), 40 + i) for i, p in enumerate(probs)]
+        ua = [to_dev(u) for u in u0]
+        ub = [to_dev(u) for u in u0]
+        it0 = it3 = 0
+        for m in range(8):
+            ia = T.tfde_batch_cn_advance(B0, ua, None, m == 0, 1e-12)
+            ib = T.tfde_batch_cn_advance(B3, ub, None, m == 0, 1e-12)
+            assert all(i.relres <= 1e-12 for i in ia) and all(i.relres <= 1e-12 for i in ib)
+            if m >= 3:
+                it0 += sum(i.iters for i in ia)
+                it3 += sum(i.iters for i in ib)
+        for a, b in zip(ua, ub):
+            assert relerr(to_host(a), to_host(b)) < 1e-10
+        assert it3 < it0
+        with pytest.raises(T.TfdeError):
+            T.tfde_batch_set_guess_order(B3, 4)
+    finally:
+        T.tfde_batch_destroy(B0)
+        T.tfde_batch_destroy(B3)
+
+
 def test_batch_argument_errors(T):
     good = T.make_params((16, 16, 16), (0.5,) * 3, (1.0,) * 3, (0.5,) * 3, 0.1)
     with pytest.raises(T.TfdeError) as e:
