@@ -178,12 +178,14 @@ int tfde_cn_advance(const tfde_problem* prob, double* u, const double* F_half, i
 
 /*
  * tfde_cn_advance_guess -- tfde_cn_advance with a candidate initial guess x0
- * (e.g. from the warm-start network): the solve starts from x0 if its FP64
- * residual ||b^m - A x0|| is smaller than that of u^{m-1}, else from u^{m-1}
- * (the previous-step guess stays the fallback; the stopping rule is the same).
- *   The residual of x0 costs one accurate operator application on
- *   x0 - u^{m-1} (A u^{m-1} is known from the chain).  *used_guess (may be
- *   NULL) is set to 1 when x0 was used.  x0: device, not aliasing u.  The
+ * (e.g. from the warm-start network): the solve starts from the point
+ * u^{m-1} + c (x0 - u^{m-1}) of least FP64 residual ||b^m - A x||, c >= 0
+ * (c = 1: x0 itself), when that residual is smaller than the one of u^{m-1},
+ * else from u^{m-1} (the previous-step guess stays the fallback; the
+ * stopping rule is the same).  The residual of x0 costs one accurate
+ * operator application on x0 - u^{m-1} (A u^{m-1} is known from the chain);
+ * c costs three inner products.  *used_guess (may be NULL) is set to 1 when
+ * x0 contributed (c > 0).  x0: device, not aliasing u.  The
  *   polynomial extrapolation of tfde_set_guess_order is not applied on such a
  *   step, and its history restarts.  Errors as tfde_cn_advance.
  */

@@ -406,11 +406,25 @@ int cn_prepare(tfde_problem* P, const double* u_prev, const double* F, const dou
             if (!st) launch_axpby_f64(P->N, 1.0, r, -1.0, rg, s);
         }
         if (st) return st;
-        double rr[2];
-        if ((st = dots64(P, 1, r, 0, r, &rr[0], s)) || (st = dots64(P, 1, rg, 0, rg, &rr[1], s))) return st;
-        if (std::isfinite(rr[1]) && rr[1] < rr[0]) {
-            TFDE_CUDA_TRY(cudaMemcpyAsync(u_next, guess, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-            TFDE_CUDA_TRY(cudaMemcpyAsync(r, rg, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        // the point of the line u_prev + c (guess - u_prev) with the least
+        // residual: r(c) = (1 - c) r + c r_g, c = <r, r - r_g> / ||r - r_g||^2
+        // (c = 1: the candidate itself, c = 0: the previous-step guess)
+        double rr[3];
+        if ((st = dots64(P, 1, r, 0, r, &rr[0], s)) || (st = dots64(P, 1, rg, 0, rg, &rr[1], s)) ||
+            (st = dots64(P, 1, r, 0, rg, &rr[2], s)))
+            return st;
+        const double den = rr[0] - 2.0 * rr[2] + rr[1];
+        double c = den > 0.0 ? (rr[0] - rr[2]) / den : 0.0;
+        if (!std::isfinite(c) || c < 0.0 || c > 4.0) c = (std::isfinite(rr[1]) && rr[1] < rr[0]) ? 1.0 : 0.0;
+        const double rc2 = (1.0 - c) * (1.0 - c) * rr[0] + 2.0 * c * (1.0 - c) * rr[2] + c * c * rr[1];
+        if (c > 0.0 && std::isfinite(rc2) && rc2 < rr[0]) {
+            if (c == 1.0) {
+                TFDE_CUDA_TRY(cudaMemcpyAsync(u_next, guess, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                TFDE_CUDA_TRY(cudaMemcpyAsync(r, rg, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            } else {
+                launch_axpby_f64(P->N, c, guess, 1.0 - c, u_next, s);   // u_next = (1 - c) u_prev + c guess
+                launch_axpby_f64(P->N, c, rg, 1.0 - c, r, s);
+            }
             P->norms_ready = false;
             if (used_guess) *used_guess = 1;
         }

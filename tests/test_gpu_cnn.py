@@ -144,9 +144,10 @@ def test_training_reduces_loss(T, W):
 
 
 def test_advance_guess_keeps_better_start(T):
-    """tfde_cn_advance_guess: a guess no better than u^{m-1} is refused and the
-    step equals tfde_cn_advance; the converged solution as guess is taken and
-    needs (almost) no iterations."""
+    """tfde_cn_advance_guess: the start is the least-residual point of the
+    line from u^{m-1} towards the guess, so a poor guess never starts worse
+    than u^{m-1} and the step equals tfde_cn_advance; the converged solution
+    as guess is taken and needs (almost) no iterations."""
     n = (24, 16, 32)
     d, kp, km = (0.3, 0.6, 0.8), (1.0,) * 3, (0.5,) * 3
     prm = T.make_params(n, d, kp, km, 0.02)
@@ -158,7 +159,7 @@ def test_advance_guess_keeps_better_start(T):
         ia = T.tfde_cn_advance(ha, ua, None, True, 1e-12)
         worse = to_dev(u0 + 0.5)
         ib, used = T.tfde_cn_advance_guess(hb, ub, None, worse, True, 1e-12)
-        assert not used
+        assert ib.relres0 <= ia.relres0 * (1 + 1e-12)
         assert relerr(to_host(ub), to_host(ua)) < 1e-10
         # next step: the exact solution as guess
         op = o.Problem(n=n, delta=d, kp=kp, km=km, dt=0.02)
