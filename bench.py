@@ -52,7 +52,13 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=None, help="override the grid size (testing only)")
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--c2-steps", type=int, default=50,
+                    help="CN steps of the n = 128 non-symmetric workload, mixed vs plain FP64 (0 skips it)")
+    ap.add_argument("--no-c3-protocol", action="store_true",
+                    help="skip the n = 256 run with one warm-up step and steps m = 2..20 (T = 1)")
+    ap.add_argument("--no-parity", action="store_true",
+                    help="skip the full-size tight-residual comparison of the mixed and FP64 GPU paths")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -190,6 +196,22 @@ def recorded_traffic():
     return d.get("dram_bytes_per_launch_n256")
 
 
+def survey_bytes_per_iteration(n: int) -> float:
+    """Algorithmic bytes of the split contraction per inner Krylov iteration:
+    the Toeplitz matvec reads p and writes A p, the preconditioner reads r
+    and writes z, FP32 vectors of n^3 elements."""
+    return 4.0 * n ** 3 * 4
+
+
+def survey_bytes_per_step(n: int, iters: float, sweeps: float) -> float:
+    """Algorithmic bytes of one CN step: 13 FP32 vector passes per inner
+    iteration (matvec 2, x/r update 6, preconditioner 2, direction 3), the
+    right-hand side (3 FP64 passes) and one FP64 residual per refinement
+    sweep (4 FP64 passes)."""
+    N = float(n) ** 3
+    return iters * 13 * N * 4 + 3 * N * 8 + sweeps * 4 * N * 8
+
+
 def source_factors(t: float):
     """Time factors (cP, cS) = (phi'(t), -phi(t)) of the exp(-t) manufactured source."""
     e = math.exp(-t)
@@ -197,23 +219,63 @@ def source_factors(t: float):
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_steps(n, delta, k, dt, tol, budget_s, max_steps=None):
+def oracle_steps(n, delta, k, dt, tol, budget_s, max_steps=None, with_iters=False):
     """Run oracle CN steps from the manufactured initial data until the time
-    budget is used (at least one step); returns (steps, seconds)."""
+    budget is used (at least one step); returns (steps, seconds), and with
+    with_iters=True (steps, seconds, PCG iterations)."""
     from oracle import tfde_oracle as o
     prob = o.Problem(n=(n, n, n), delta=delta, kp=k, km=k, dt=dt)
     tau = o.build_tau(prob)
     u = inp.example2_initial(n)
-    steps, t0 = 0, time.perf_counter()
+    steps, iters, t0 = 0, 0, time.perf_counter()
     while True:
         th = (steps + 0.5) * dt
         F = o.source_cell_average(prob, th, "exp")
         b = o.rhs(prob, u, F)
-        u, _ = o.pcg(lambda v: o.apply_A(prob, v), lambda r: o.apply_Pinv(tau, r), b, u, tol, 10 ** 6)
+        u, info = o.pcg(lambda v: o.apply_A(prob, v), lambda r: o.apply_Pinv(tau, r), b, u, tol, 10 ** 6)
         steps += 1
+        iters += info.iters
         el = time.perf_counter() - t0
         if el >= budget_s or (max_steps and steps >= max_steps):
-            return steps, el
+            return (steps, el, iters) if with_iters else (steps, el)
+
+
+def oracle_iteration_seconds(n, delta, k, dt):
+    """Seconds of one oracle PCG iteration's operator and preconditioner
+    application, and of one right-hand side, on the n^3 workload (numpy FP64,
+    as many BLAS threads as the process is given)."""
+    from oracle import tfde_oracle as o
+    prob = o.Problem(n=(n, n, n), delta=delta, kp=k, km=k, dt=dt)
+    tau = o.build_tau(prob)
+    u = inp.example2_initial(n)
+    t0 = time.perf_counter()
+    o.rhs(prob, u, None)
+    t1 = time.perf_counter()
+    v = o.apply_A(prob, u)
+    o.apply_Pinv(tau, v)
+    t2 = time.perf_counter()
+    return t2 - t1, t1 - t0
+
+
+def oracle_one_core(n, delta, k, dt, iters_per_step):
+    """The oracle's CN steps/s on one host core: one iteration's operator and
+    preconditioner and one right-hand side timed in a child process pinned
+    to one core with one BLAS thread, scaled by the iterations per step."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[v] = "1"
+    code = ("import json, os, sys; sys.path.insert(0, %r); os.sched_setaffinity(0, {min(os.sched_getaffinity(0))}); "
+            "import bench; print(json.dumps(bench.oracle_iteration_seconds(%d, %r, %r, %r)))"
+            % (ROOT, n, tuple(delta), tuple(k), dt))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return None
+    it_s, rhs_s = json.loads(r.stdout.strip().splitlines()[-1])
+    step_s = rhs_s + iters_per_step * it_s
+    return {"value": 1.0 / step_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one operator + preconditioner application ({it_s:.1f} s) and one right-hand side "
+                      f"({rhs_s:.1f} s) of the n={n} workload on one core with one BLAS thread, scaled by "
+                      f"{iters_per_step:.1f} PCG iterations per step (the all-core sample's count)"}
 
 
 def cpu_cores():
@@ -224,6 +286,23 @@ def cpu_cores():
 
 
 # ----------------------------------------------------------------- our arm
+def chained_steps(T, h, u, F, dt, m0, count, tol, stream):
+    """`count` chained in-place CN steps m0+1 .. m0+count of the exp(-t)
+    manufactured workload (source assembled on the device each step); the
+    chain restarts when m0 == 0.  Returns (inner iterations, refinement
+    sweeps, largest final relative residual)."""
+    iters = sweeps = 0
+    relres = 0.0
+    for i in range(count):
+        cP, cS = source_factors((m0 + i + 0.5) * dt)
+        T.tfde_source_example2(h, cP, cS, F, stream)
+        info = T.tfde_cn_advance(h, u, F, m0 + i == 0, tol, stream)
+        iters += info.iters
+        sweeps += info.refine_sweeps
+        relres = max(relres, info.relres)
+    return iters, sweeps, relres
+
+
 def run_ours(args):
     import torch
 
@@ -241,37 +320,22 @@ def run_ours(args):
     tol = W["tol"]
     params = T.make_params((n, n, n), W["delta"], W["kp"], W["km"], dt)
     stream = torch.cuda.current_stream(dev)
-    tf = source_factors
-
-    def run_steps(h, u, un, F, m0, count):
-        # in-place chained CN advance; the chain starts at m0 == 0
-        iters = sweeps = 0
-        relres = 0.0
-        for i in range(count):
-            th = (m0 + i + 0.5) * dt
-            cP, cS = tf(th)
-            T.tfde_source_example2(h, cP, cS, F, stream)
-            info = T.tfde_cn_advance(h, u, F, m0 + i == 0, tol, stream)
-            iters += info.iters
-            sweeps += info.refine_sweeps
-            relres = max(relres, info.relres)
-        return u, un, iters, sweeps, relres
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     u0 = torch.from_numpy(inp.example2_initial(n)).to(dev)
     # ---- mixed precision (the metric)
     h = T.tfde_assemble(params, T.TFDE_MIXED, stream)
     T.tfde_set_guess_order(h, args.guess_order)
-    u, un, F = u0.clone(), torch.empty_like(u0), torch.empty_like(u0)
-    u, un, _, _, _ = run_steps(h, u, un, F, 0, args.warmup)
+    u, F = u0.clone(), torch.empty_like(u0)
+    chained_steps(T, h, u, F, dt, 0, args.warmup, tol, stream)
     torch.cuda.synchronize()
     barrier(on)
     T.tfde_stats_reset(time_tc=True)
     clk = ClockSampler(local)
     clk.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    u, un, iters, sweeps, relres = run_steps(h, u, un, F, args.warmup, args.steps)
+    iters, sweeps, relres = chained_steps(T, h, u, F, dt, args.warmup, args.steps, tol, stream)
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
@@ -283,6 +347,7 @@ def run_ours(args):
     t_end = (args.warmup + args.steps) * dt
     exact = torch.from_numpy(inp.example2_initial(n, math.exp(-t_end))).to(dev)
     err = float((u - exact).abs().max() / exact.abs().max())
+    u_end = u.clone()
 
     # ---- end to end through the C ABI with host buffers (copies timed)
     e2e = None
@@ -296,8 +361,7 @@ def run_ours(args):
         for i in range(args.steps):
             # the host copy holds exactly the previous output, so the chain stays valid
             u.copy_(host_u, non_blocking=True)
-            th = (m0 + i + 0.5) * dt
-            cP, cS = tf(th)
+            cP, cS = source_factors((m0 + i + 0.5) * dt)
             T.tfde_source_example2(h, cP, cS, F, stream)
             T.tfde_cn_advance(h, u, F, False, tol, stream)
             host_out.copy_(u, non_blocking=True)
@@ -309,24 +373,53 @@ def run_ours(args):
         nbytes = u.numel() * u.element_size()
         e2e = {"value": aggregate_value(args.steps, world, ms_e / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    # ---- the survey's C-3 protocol: one warm-up step, then steps m = 2 .. 20 (T = 1)
+    c3 = None
+    if not args.no_c3_protocol and args.n is None:
+        u = u0.clone()
+        chained_steps(T, h, u, F, dt, 0, 1, tol, stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        it3, sw3, rr3 = chained_steps(T, h, u, F, dt, 1, M - 1, tol, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms3 = e0.elapsed_time(e1)
+        ex3 = torch.from_numpy(inp.example2_initial(n, math.exp(-1.0))).to(dev)
+        c3 = {"value": (M - 1) / (ms3 / 1e3), "unit": UNIT, "warmup_steps": 1, "timed_steps": f"m = 2..{M}",
+              "ms_per_step": ms3 / (M - 1), "iters_per_step": it3 / (M - 1),
+              "refine_sweeps_per_step": sw3 / (M - 1), "max_relres": rr3,
+              "max_rel_err_vs_exact_at_T1": float((u - ex3).abs().max() / ex3.abs().max())}
     T.tfde_destroy(h)
 
     # ---- plain FP64 path on the same GPU (comparison)
     fp64 = None
     if args.fp64_steps > 0:
         h64 = T.tfde_assemble(params, T.TFDE_FP64, stream)
-        u, un = u0.clone(), torch.empty_like(u0)
-        u, un, _, _, _ = run_steps(h64, u, un, F, 0, 1)
+        T.tfde_set_guess_order(h64, args.guess_order)
+        u = u0.clone()
+        chained_steps(T, h64, u, F, dt, 0, 1, tol, stream)
         torch.cuda.synchronize()
         e0.record(stream)
-        u, un, it64, _, _ = run_steps(h64, u, un, F, 1, args.fp64_steps)
+        it64, _, rr64 = chained_steps(T, h64, u, F, dt, 1, args.fp64_steps, tol, stream)
         e1.record(stream)
         torch.cuda.synchronize()
         ms64 = reduce_max(e0.elapsed_time(e1), on, dev)
         fp64 = {"value": aggregate_value(args.fp64_steps, world, ms64 / 1e3), "unit": UNIT,
                 "ms_per_step": ms64 / args.fp64_steps, "iters_per_step": it64 / args.fp64_steps,
-                "steps": args.fp64_steps}
+                "steps": args.fp64_steps, "warmup_steps": 1, "max_relres": rr64,
+                "initial_guess": "as the mixed path"}
         T.tfde_destroy(h64)
+
+    # ---- full-size parity: mixed and FP64 GPU paths from the same state, tight residual
+    parity = None
+    if not args.no_parity:
+        parity = full_size_parity(T, params, u_end, (args.warmup + args.steps + 0.5) * dt, dev, stream)
+
+    # ---- the non-symmetric workload: n = 128, PGMRES(20), mixed vs plain FP64
+    c2 = None
+    if args.c2_steps > 0 and args.n is None:
+        c2 = run_c2(T, args.c2_steps, args.guess_order, dev, stream, check_oracle=rank == 0)
 
     # ---- batched workload: uneven problems, lock-step batched solve vs a loop
     batched = None
@@ -345,16 +438,29 @@ def run_ours(args):
     kx = st.kind[T.TFDE_KIND_EXACT]
     if ks.timed > 0 and ks.ms > 0:
         # dominant kernel: the split-BF16 per-axis contraction (fast operator and
-        # preconditioner of every inner iteration), timed alone by event pairs
-        achieved = ks.bytes / (ks.ms / 1e3) / 1e9
-        tr = recorded_traffic()
+        # preconditioner of every inner iteration), timed alone by event pairs.
+        # frac: the algorithmic bytes of the inner iterations (matvec read p,
+        # write Ap; preconditioner read r, write z; FP32) over the summed
+        # launch time; schedule_frac: the bytes the launches' schedule moves.
+        alg = iters * survey_bytes_per_iteration(n)
+        achieved = alg / (ks.ms / 1e3) / 1e9
+        sched = ks.bytes / (ks.ms / 1e3) / 1e9
+        step_bytes = survey_bytes_per_step(n, iters / args.steps, sweeps / args.steps)
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": tr,
+                "frac": achieved / peaks["hbm_gbs"], "traffic": recorded_traffic(),
                 "kernel": "tfde::tc::axis_gemm_kernel", "peak_source": peaks["source"] + " (hbm_gbs)",
                 "launches": int(ks.launches), "avg_launch_us": 1e3 * ks.ms / ks.timed,
-                "algorithmic_bytes_per_launch": ks.bytes / ks.launches,
+                "algorithmic_bytes_per_launch": alg / ks.launches,
+                "algorithmic_bytes_basis": "16 n^3 bytes per inner iteration (FP32 matvec p -> Ap, "
+                                           "preconditioner r -> z)",
+                "split_us_per_inner_iteration": 1e3 * ks.ms / max(iters, 1),
+                "schedule_bytes_per_launch": ks.bytes / ks.launches, "schedule_achieved": sched,
+                "schedule_frac": sched / peaks["hbm_gbs"],
                 "tensor_tflops": ks.flops / (ks.ms / 1e3) / 1e12,
-                "kernel_share_of_step": ks.ms / ms}
+                "kernel_share_of_step": ks.ms / ms,
+                "step": {"algorithmic_bytes_per_step": step_bytes,
+                         "achieved": step_bytes / (ms / args.steps / 1e3) / 1e9,
+                         "frac": step_bytes / (ms / args.steps / 1e3) / 1e9 / peaks["hbm_gbs"]}}
         if kx.timed > 0 and kx.ms > 0:
             roof["exact_residual_kernel"] = {
                 "kernel": "tfde::oz::oz_gemm_kernel", "bound": "tensor", "launches": int(kx.launches),
@@ -367,10 +473,13 @@ def run_ours(args):
     # ---- CPU baseline (oracle), rank 0 at N = 1 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        steps_c, sec = oracle_steps(n, W["delta"], W["kp"], dt, tol, args.cpu_seconds)
+        steps_c, sec, it_c = oracle_steps(n, W["delta"], W["kp"], dt, tol, args.cpu_seconds, with_iters=True)
         cpu = {"value": steps_c / sec, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                "sample": f"{steps_c} CN step(s) of the n={n} workload by the numpy FP64 oracle "
-                         f"(PCG, x0 = u^(m-1)), {sec:.1f} s"}
+                         f"(PCG, x0 = u^(m-1), {it_c / steps_c:.1f} iterations per step), {sec:.1f} s"}
+        one = oracle_one_core(n, W["delta"], W["kp"], dt, it_c / steps_c)
+        if one:
+            cpu["one_core"] = one
 
     if rank == 0:
         line = {
@@ -380,17 +489,19 @@ def run_ours(args):
             "data": "synthetic: manufactured solution exp(-t) x^2(1-x)^2 y^2(1-y)^2 z^2(1-z)^2",
             "config": {**workload_config(n, W, dt, tol),
                        "solver": "PCG(tau) inner FP32 / split-BF16 tcgen05, FP64 iterative refinement",
-                       "initial_guess": ("previous step u^(m-1)" if args.guess_order == 0 else
-                                         f"order-{min(args.guess_order, 2)} polynomial extrapolation in time"
-                                         + (" with a minimal-residual correction over the history differences"
-                                            if args.guess_order >= 3 else "")
-                                         + " (A x0 from stored A u, no extra operator application)"),
-                       "fp64_path_initial_guess": "previous step u^(m-1)",
+                       "warm_start": ("none: previous step u^(m-1)" if args.guess_order == 0 else
+                                      "extrapolated (not learned): "
+                                      f"order-{min(args.guess_order, 2)} polynomial extrapolation in time"
+                                      + (" with a minimal-residual correction over the history differences"
+                                         if args.guess_order >= 3 else "")
+                                      + " (A x0 from stored A u, no extra operator application); the learned "
+                                        "network's comparison is the warm_start sub-object"),
                        "step_api": "tfde_cn_advance (chained: A u^(m-1) = b^(m-1) - r^(m-1))",
                        "l2": "inputs larger than L2 (each FP64 vector 134 MB, working set > 2 GB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st.kernel_launches),
-            "clocks": clocks, "fp64_path": fp64, "batched": batched, "warm_start": warm,
+            "clocks": clocks, "fp64_path": fp64, "c3_protocol": c3, "parity_n256": parity,
+            "c2_nonsymmetric_n128": c2, "batched": batched, "warm_start": warm,
             "iters_per_step": iters / args.steps, "refine_sweeps_per_step": sweeps / args.steps,
             "max_relres": relres, "max_rel_err_vs_exact": err,
         }
@@ -398,6 +509,101 @@ def run_ours(args):
     if on:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def full_size_parity(T, params, u_prev, t_half, dev, stream):
+    """One CN step from the same state u^{m-1} through the mixed and the FP64
+    GPU paths at a 1e-12 true residual (tfde_cn_step, x0 = u^{m-1}), and the
+    mixed step at the benchmark's 1e-8: their relative 2-norm differences."""
+    import torch
+    out = {"state": "u^(m-1) after the timed steps", "tight_tol": 1e-12}
+    hm = T.tfde_assemble(params, T.TFDE_MIXED, stream)
+    h64 = T.tfde_assemble(params, T.TFDE_FP64, stream)
+    try:
+        F = torch.empty_like(u_prev)
+        cP, cS = source_factors(t_half)
+        T.tfde_source_example2(hm, cP, cS, F, stream)
+        xm, x64, x8 = torch.empty_like(u_prev), torch.empty_like(u_prev), torch.empty_like(u_prev)
+        im = T.tfde_cn_step(hm, u_prev, F, None, xm, 1e-12, stream)
+        i64 = T.tfde_cn_step(h64, u_prev, F, None, x64, 1e-12, stream)
+        i8 = T.tfde_cn_step(hm, u_prev, F, None, x8, 1e-8, stream)
+        nrm = float(torch.linalg.vector_norm(x64))
+        out.update({"rel_err_mixed_vs_fp64": float(torch.linalg.vector_norm(xm - x64)) / nrm,
+                    "relres_mixed": im.relres, "relres_fp64": i64.relres,
+                    "rel_err_tol1e8_vs_tight": float(torch.linalg.vector_norm(x8 - x64)) / nrm,
+                    "relres_tol1e8": i8.relres})
+    finally:
+        T.tfde_destroy(hm)
+        T.tfde_destroy(h64)
+    return out
+
+
+def run_c2(T, steps, guess_order, dev, stream, check_oracle=True):
+    """The non-symmetric workload (n = 128, delta = (0.3, 0.6, 0.8), k+ = 1,
+    k- = 0.5, f = 0, smoothed-noise u0 with seed 2, dt = 1/50, PGMRES(20),
+    tol 1e-8): `steps` chained CN steps through the mixed path and through
+    the plain FP64 path, each timed with CUDA events after one warm-up step,
+    and their trajectories compared; the last mixed step is also compared
+    with the oracle's GMRES step at a tight residual from the same state."""
+    import torch
+    Wc = inp.WORKLOADS["n128_nonsym"]
+    n, dt, tol = Wc["n"], 1.0 / Wc["M"], Wc["tol"]
+    prm = T.make_params((n, n, n), Wc["delta"], Wc["kp"], Wc["km"], dt)
+    u0 = torch.from_numpy(inp.smoothed_uniform((n, n, n), Wc["u0_seed"])).to(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": "n=128 non-symmetric, PGMRES(20), f = 0, tol 1e-8", "steps": steps, "warmup_steps": 1}
+    finals = {}
+    prev_state = None
+    for name, prec in (("mixed", T.TFDE_MIXED), ("fp64", T.TFDE_FP64)):
+        h = T.tfde_assemble(prm, prec, stream)
+        try:
+            T.tfde_set_guess_order(h, guess_order)
+            u = u0.clone()
+            T.tfde_cn_advance(h, u, None, True, tol, stream)
+            torch.cuda.synchronize()
+            its, rr = 0, 0.0
+            e0.record(stream)
+            for m in range(1, steps):
+                if name == "mixed" and m == steps - 1:
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms_part = e0.elapsed_time(e1)
+                    prev_state = u.clone()
+                    e0.record(stream)
+                info = T.tfde_cn_advance(h, u, None, False, tol, stream)
+                its += info.iters
+                rr = max(rr, info.relres)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) + (ms_part if name == "mixed" else 0.0)
+            finals[name] = u
+            out[name] = {"value": (steps - 1) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / (steps - 1),
+                         "iters_per_step": its / (steps - 1), "max_relres": rr}
+        finally:
+            T.tfde_destroy(h)
+    out["speedup_mixed_vs_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    out["rel_err_mixed_vs_fp64_trajectory"] = float(torch.linalg.vector_norm(finals["mixed"] - finals["fp64"])
+                                                    / torch.linalg.vector_norm(finals["fp64"]))
+    if check_oracle and prev_state is not None:
+        from oracle import tfde_oracle as o
+        op = o.Problem(n=(n, n, n), delta=Wc["delta"], kp=Wc["kp"], km=Wc["km"], dt=dt)
+        up = prev_state.cpu().numpy()
+        b = o.rhs(op, up, None)
+        tau = o.build_tau(op)
+        t0 = time.perf_counter()
+        xo, _ = o.gmres_left(lambda v: o.apply_A(op, v), lambda r: o.apply_Pinv(tau, r), b, up, 1e-13, 4000,
+                             restart=20, criterion="true")
+        h = T.tfde_assemble(prm, T.TFDE_MIXED, stream)
+        try:
+            xm = torch.empty_like(prev_state)
+            info = T.tfde_cn_step(h, prev_state, None, None, xm, 1e-12, stream)
+            out["last_step_vs_oracle"] = {
+                "rel_err_tight": float(np.linalg.norm(xm.cpu().numpy() - xo) / np.linalg.norm(xo)),
+                "rel_err_tol1e8": float(np.linalg.norm(finals["mixed"].cpu().numpy() - xo) / np.linalg.norm(xo)),
+                "relres_mixed_tight": info.relres, "oracle_tol": 1e-13, "oracle_s": time.perf_counter() - t0}
+        finally:
+            T.tfde_destroy(h)
+    return out
 
 
 def run_warm_start(T, train_steps, eval_steps, dev, stream):
@@ -439,9 +645,11 @@ def run_warm_start(T, train_steps, eval_steps, dev, stream):
     ne = T.tfde_cnn_create((n, n, n))
     T.tfde_cnn_set_params(ne, params)
     try:
-        for mode in ("previous_step", "network"):
+        for mode in ("previous_step", "extrapolated_order3", "network"):
             h = T.tfde_assemble(prm, T.TFDE_MIXED, stream)
             try:
+                if mode == "extrapolated_order3":
+                    T.tfde_set_guess_order(h, 3)
                 u = u0.clone()
                 x0 = torch.empty_like(u)
                 T.tfde_cn_advance(h, u, None, True, 1e-8, stream)     # step 1 (no guess yet)
@@ -469,6 +677,13 @@ def run_warm_start(T, train_steps, eval_steps, dev, stream):
                 T.tfde_destroy(h)
     finally:
         T.tfde_cnn_destroy(ne)
+    ev = out["eval"]
+    ev["network_vs_previous_step"] = {
+        "iters_ratio": ev["network"]["iters_per_step"] / ev["previous_step"]["iters_per_step"],
+        "ms_ratio": ev["network"]["ms_per_step"] / ev["previous_step"]["ms_per_step"]}
+    ev["network_vs_extrapolated_order3"] = {
+        "iters_ratio": ev["network"]["iters_per_step"] / ev["extrapolated_order3"]["iters_per_step"],
+        "ms_ratio": ev["network"]["ms_per_step"] / ev["extrapolated_order3"]["ms_per_step"]}
     return out
 
 

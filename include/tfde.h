@@ -399,6 +399,23 @@ int tfde_stats_get(tfde_stats* out);
  */
 int tfde_mass_apply_noalloc(const int n[3], const double* x, double* y, void* stream);
 
+/*
+ * tfde_selftest_wait -- diagnostic of the bounded device-side waits (no
+ * counterpart in the paper).  Every mbarrier wait of the library's
+ * tensor-core kernels gives up after a wall-clock limit (2 s), raises the
+ * kernel's error flag, releases the kernel's tensor memory and returns, so
+ * that a lost arrival surfaces as TFDE_ETIMEOUT instead of a hung GPU.  This
+ * entry point runs that path on purpose: one CTA allocates tensor memory,
+ * waits with the shared bounded-wait routine and limit_ns (1000 ..
+ * 2000000000) on an mbarrier that nothing ever arrives on, releases the
+ * tensor memory and exits; no copy or MMA is in flight.
+ *   Returns TFDE_ETIMEOUT when the wait ran out as designed (the expected
+ *   result) with *tmem_freed (may be NULL) = 1 once the kernel released its
+ *   tensor memory; TFDE_EINVAL for a limit out of range; TFDE_ECUDA otherwise.
+ *   The device stays usable afterwards.  Synchronises `stream`.
+ */
+int tfde_selftest_wait(long long limit_ns, int* tmem_freed, void* stream);
+
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* tfde_last_error(void);
 

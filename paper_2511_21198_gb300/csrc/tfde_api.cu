@@ -32,6 +32,9 @@ int mixed_apply_A(const tfde_problem*, int, const double*, double*, cudaStream_t
 int mixed_apply_Pinv(const tfde_problem*, const double*, double*, cudaStream_t);
 int mixed_pcg(tfde_problem*, const double*, double*, double, int, tfde_info*, cudaStream_t, bool);
 int mixed_pgmres(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t, bool);
+namespace tc {
+int wait_selftest(long long limit_ns, int* tmem_freed, cudaStream_t s);
+}
 }  // namespace tfde
 
 using namespace tfde;
@@ -291,6 +294,11 @@ int tfde_stats_reset(int time_tc) { return stats_reset(time_tc); }
 int tfde_stats_get(tfde_stats* out) {
     if (!out) return set_error(TFDE_EINVAL, "NULL stats");
     return stats_get(out);
+}
+
+int tfde_selftest_wait(long long limit_ns, int* tmem_freed, void* stream) {
+    if (int st = pre_call()) return st;
+    return tc::wait_selftest(limit_ns, tmem_freed, (cudaStream_t)stream);
 }
 
 const char* tfde_last_error(void) { return last_error_text(); }

@@ -102,22 +102,24 @@ __global__ void axis_stencil_f64_kernel(const double* __restrict__ X, double* __
                                         int n3, int axis, double beta, const double* __restrict__ W,
                                         double gamma) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= n1 || j >= n2) return;
-    for (int k = blockIdx.z; k < n3; k += gridDim.z) {
-        const long long idx = ((long long)k * n2 + j) * n1 + i;
-        long long st;
-        int m, n;
-        if (axis == 0) { st = 1; m = i; n = n1; }
-        else if (axis == 1) { st = n1; m = j; n = n2; }
-        else { st = (long long)n1 * n2; m = k; n = n3; }
-        double nb = 0.0;
-        if (m > 0) nb += X[idx - st];
-        if (m + 1 < n) nb += X[idx + st];
-        double val = beta * fma(0.75, X[idx], 0.125 * nb);
-        if (W) val = fma(gamma, W[idx], val);
-        Y[idx] = val;
-    }
+    if (i >= n1) return;
+    // j and k both stride over the grid: gridDim.y is capped at 65535, and on
+    // the x axis n2 counts every line (n2 n3 of the grid)
+    for (long long j = (long long)blockIdx.y * blockDim.y + threadIdx.y; j < n2; j += (long long)gridDim.y * blockDim.y)
+        for (int k = blockIdx.z; k < n3; k += gridDim.z) {
+            const long long idx = ((long long)k * n2 + j) * n1 + i;
+            long long st;
+            long long m, n;
+            if (axis == 0) { st = 1; m = i; n = n1; }
+            else if (axis == 1) { st = n1; m = j; n = n2; }
+            else { st = (long long)n1 * n2; m = k; n = n3; }
+            double nb = 0.0;
+            if (m > 0) nb += X[idx - st];
+            if (m + 1 < n) nb += X[idx + st];
+            double val = beta * fma(0.75, X[idx], 0.125 * nb);
+            if (W) val = fma(gamma, W[idx], val);
+            Y[idx] = val;
+        }
 }
 
 // Y = (T_{n3} (x) T_{n2} (x) T_{n1}) X, T = tridiag(1,6,1)/8, zero exterior
@@ -538,7 +540,8 @@ void launch_axis_stencil_f64(const double* X, double* Y, const AxisView& v, doub
         axis = 2; n1 = (int)v.l_in; n2 = 1; n3 = v.n;
     }
     dim3 blk(n1 >= 64 ? 64 : 32, 4);
-    dim3 grid((n1 + blk.x - 1) / blk.x, (n2 + blk.y - 1) / blk.y, n3 < 64 ? n3 : 64);
+    const long long gy = ((long long)n2 + blk.y - 1) / blk.y;
+    dim3 grid((n1 + blk.x - 1) / blk.x, (unsigned)(gy < 65535 ? gy : 65535), n3 < 64 ? n3 : 64);
     axis_stencil_f64_kernel<<<grid, blk, 0, s>>>(X, Y, n1, n2, n3, axis, beta, W, gamma);
 }
 

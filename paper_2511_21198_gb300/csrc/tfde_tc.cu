@@ -250,5 +250,53 @@ int launch_grouped(const Params* groups, const long long* gstart, int ngroups, l
     return TFDE_OK;
 }
 
+// Self-test of the bounded-wait path shared by the tensor-core kernels: one
+// CTA allocates TMEM, waits on an mbarrier that nothing ever arrives on, gives
+// up after limit_ns (raising *err exactly as the contraction kernels do),
+// releases its TMEM and returns.  No copy or MMA is in flight at any point.
+// report[0] = 2 when the wait gave up (1 if it completed), report[1] = 1
+// once TMEM has been released.
+__global__ void __launch_bounds__(64, 1) wait_selftest_kernel(unsigned long long limit_ns, int* err, int* report) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t slot;
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    if (warp == 0) tmem_alloc(&slot, 32);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x == 32) report[0] = mbar_wait(&bar, 0, err, false, limit_ns) ? 1 : 2;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(slot, 32);
+    __syncthreads();
+    if (threadIdx.x == 0) report[1] = 1;
+}
+
+int wait_selftest(long long limit_ns, int* tmem_freed, cudaStream_t s) {
+    if (limit_ns < 1000 || limit_ns > (long long)WAIT_LIMIT_NS)
+        return set_error(TFDE_EINVAL, "wait limit must lie in [1 us, 2 s]");
+    int* d = nullptr;
+    int h[3] = {0, 0, 0};
+    if (cudaMalloc((void**)&d, 3 * sizeof(int)) != cudaSuccess) return set_error(TFDE_ENOMEM, "cudaMalloc failed");
+    cudaError_t e = cudaMemsetAsync(d, 0, 3 * sizeof(int), s);
+    if (e == cudaSuccess) {
+        stats_count_launch();
+        wait_selftest_kernel<<<1, 64, 0, s>>>((unsigned long long)limit_ns, d, d + 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return set_error(TFDE_ECUDA, std::string("wait self-test: ") + cudaGetErrorString(e));
+    if (tmem_freed) *tmem_freed = h[2];
+    if (h[0] != 0 && h[1] == 2) return set_error(TFDE_ETIMEOUT, "bounded wait ran out (self-test, as designed)");
+    return set_error(TFDE_ECUDA, "wait self-test: the wait did not run out");
+}
+
 }  // namespace tc
 }  // namespace tfde

@@ -25,6 +25,8 @@ int launch(const Params& P, cudaStream_t s, double bytes, double flops);
 // axis (descriptors and tile offsets gstart[0..ngroups] in device memory,
 // total = gstart[ngroups]); groups with gactive[g] == 0 are skipped.  All
 // groups share the layout b_kmajor and the output mode out_mode.
+// Bounded-wait self-test (tfde_selftest_wait).
+int wait_selftest(long long limit_ns, int* tmem_freed, cudaStream_t s);
 int launch_grouped(const Params* groups, const long long* gstart, int ngroups, long long total, int b_kmajor,
                    int out_mode, const int* gactive, int* err, cudaStream_t s, double bytes, double flops);
 

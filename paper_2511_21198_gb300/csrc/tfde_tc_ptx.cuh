@@ -44,14 +44,15 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
 // role raised *err and `abort_on_err`).  try_wait suspends in hardware until
 // the phase completes or a short internal time limit passes, so the global
 // error flag and the timer are only polled every 64 tries.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, bool abort_on_err = true) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, bool abort_on_err = true,
+                                          unsigned long long limit_ns = WAIT_LIMIT_NS) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t i = 1;; ++i) {
         if (mbar_try(bar, parity)) return true;
         if ((i & 63u) == 0u) {
             if (abort_on_err && *reinterpret_cast<volatile int*>(err) != 0) return false;
-            if (global_ns() - t0 > WAIT_LIMIT_NS) {
+            if (global_ns() - t0 > limit_ns) {
                 atomicExch(err, 1);
                 return false;
             }

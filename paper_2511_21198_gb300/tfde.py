@@ -10,7 +10,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import POINTER, Structure, byref, c_char_p, c_double, c_float, c_int, c_void_p
+from ctypes import POINTER, Structure, byref, c_char_p, c_double, c_float, c_int, c_longlong, c_void_p
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libtfde.so")
@@ -64,16 +64,16 @@ EXPORTS = ["tfde_assemble", "tfde_destroy", "tfde_matvec", "tfde_precond", "tfde
            "tfde_stats_reset", "tfde_stats_get", "tfde_mass_apply_noalloc", "tfde_batch_create", "tfde_batch_destroy",
            "tfde_batch_count", "tfde_batch_set_guess_order", "tfde_batch_cn_advance", "tfde_cn_advance_guess", "tfde_cnn_create", "tfde_cnn_destroy",
            "tfde_cnn_set_params", "tfde_cnn_get_params", "tfde_cnn_get_grads", "tfde_cnn_predict", "tfde_cnn_accumulate",
-           "tfde_cnn_adam_step", "tfde_last_error", "tfde_version"]
+           "tfde_cnn_adam_step", "tfde_selftest_wait", "tfde_last_error", "tfde_version"]
 
 
 def load(path: str | None = None):
-    """Load libtfde.so (raises if it has not been built); TFDE_LIB in the
-    environment names another build of the same library."""
+    """Load the in-tree libtfde.so (raises if it has not been built); `path`
+    loads another build of the same library without making it the default."""
     global _lib
     if _lib is not None and path is None:
         return _lib
-    p = path or os.environ.get("TFDE_LIB") or LIB_PATH
+    p = path or LIB_PATH
     if not os.path.exists(p):
         raise RuntimeError(f"{p} is missing: build it with paper_2511_21198_gb300.build.build()")
     lib = ctypes.CDLL(p)
@@ -110,6 +110,7 @@ def load(path: str | None = None):
         "tfde_cnn_predict": ([vp, vp, vp, POINTER(c_double), vp, vp], c_int),
         "tfde_cnn_accumulate": ([vp, vp, vp, POINTER(c_double), vp, POINTER(c_double), vp], c_int),
         "tfde_cnn_adam_step": ([vp, c_float, vp], c_int),
+        "tfde_selftest_wait": ([c_longlong, POINTER(c_int), vp], c_int),
         "tfde_last_error": ([], c_char_p),
         "tfde_version": ([], c_char_p),
     }
@@ -259,6 +260,14 @@ def tfde_mass_apply_noalloc(n, x, y, stream=None) -> None:
     most 2^18 points; the first call on a device must precede stream capture)."""
     dims = (c_int * 3)(*[int(v) for v in n])
     _check(load().tfde_mass_apply_noalloc(dims, _ptr(x), _ptr(y), _stream(stream)), "tfde_mass_apply_noalloc")
+
+
+def tfde_selftest_wait(limit_ns: int, stream=None) -> tuple[int, int]:
+    """Run the bounded-wait diagnostic; returns (status, tmem_freed) without
+    raising (TFDE_ETIMEOUT is the expected status)."""
+    freed = c_int(0)
+    st = load().tfde_selftest_wait(int(limit_ns), ctypes.byref(freed), _stream(stream))
+    return st, freed.value
 
 
 def tfde_last_error() -> str:

@@ -123,6 +123,39 @@ def test_adam_first_step_moves_by_learning_rate():
     assert np.allclose(p, [1.0 - 0.01, -2.0 + 0.01, 0.5 - 0.01 * 1e-3 / (1e-3 + 1e-8)], rtol=1e-12)
 
 
+def test_adam_three_steps_against_unrolled_moment_averages():
+    """Three Adam steps with a different gradient each step, against the
+    unrolled form of the moments (Kingma & Ba, Sec. 3: m_t = (1 - b1)
+    sum_i b1^(t-i) g_i, likewise v_t with g_i^2 and b2), evaluated in exact
+    rational arithmetic with b1 = 1/2, b2 = 3/4 and eps = 0: a wrong decay,
+    bias-correction exponent or moment update from step 2 on fails."""
+    from fractions import Fraction as Fr
+    b1, b2, lr = 0.5, 0.75, 0.125
+    gs = [np.array([0.5, -2.0, 1.0]), np.array([-1.0, 4.0, 1.0]), np.array([0.25, 1.0, -3.0])]
+    p = np.array([1.0, -1.0, 0.0])
+    m, v = np.zeros(3), np.zeros(3)
+    expect = [Fr(1), Fr(-1), Fr(0)]
+    for t in range(1, 4):
+        C.adam_step(p, gs[t - 1], m, v, t, lr, b1=b1, b2=b2, eps=0.0)
+        for e in range(3):
+            mt = sum((1 - Fr(1, 2)) * Fr(1, 2) ** (t - i) * Fr(gs[i - 1][e]) for i in range(1, t + 1))
+            vt = sum((1 - Fr(3, 4)) * Fr(3, 4) ** (t - i) * Fr(gs[i - 1][e]) ** 2 for i in range(1, t + 1))
+            mh = mt / (1 - Fr(1, 2) ** t)
+            vh = vt / (1 - Fr(3, 4) ** t)
+            expect[e] -= Fr(lr) * mh / Fr(float(np.sqrt(float(vh))))
+        np.testing.assert_allclose(p, [float(x) for x in expect], rtol=1e-14, atol=1e-15)
+
+
+def test_adam_constant_gradient_moves_lr_per_step():
+    """With the same gradient at every step the bias-corrected moments equal
+    g and g^2 exactly, so every step moves each weight by lr * g / (|g| + eps)."""
+    g = np.array([0.3, -4.0, 2.0])
+    p, m, v = np.zeros(3), np.zeros(3), np.zeros(3)
+    for t in range(1, 6):
+        C.adam_step(p, g, m, v, t, 0.01)
+    np.testing.assert_allclose(p, -5 * 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+
+
 def test_input_channels_layout():
     u = np.arange(24, dtype=float).reshape(2, 3, 4) - 5.0
     ch, s = C.input_channels(u, 2 * u, (0.1, 0.2, 0.3), (1, 2, 3), (4, 5, 6))

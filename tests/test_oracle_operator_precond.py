@@ -152,3 +152,26 @@ def test_skew_vs_hermitian_quadratic_forms(d):
         T = o.toeplitz_T(q, n)
         ev = linalg.eigh(1j * 0.5 * (T - T.T), 0.5 * (T + T.T), eigvals_only=True)
         assert np.abs(ev).max() <= math.tan(d * math.pi / 2) + 1e-12
+
+
+@pytest.mark.parametrize("sym", [True, False])
+def test_pointwise_operator_matches_kronecker_rows(sym):
+    """apply_A_at (used by the full-size sampled GPU checks) against rows of
+    the explicit N x N Kronecker matrices of Eq. (linear_sys): op "A" is a
+    row of A, op "RHS" a row of the right-hand-side operator 2 A_N - A, at
+    random points of a 7 x 6 x 5 grid that include every face and corner."""
+    p = _prob(n=(7, 6, 5), kp=(1.0, 2.0, 0.7), km=(1.0, 2.0, 0.7) if sym else (0.5, 1.0, 1.9))
+    v = inp.uniform_vector(p.shape, 11)
+    A = o.dense_A(p)
+    AN = np.kron(p.M[2], np.kron(p.M[1], p.M[0]))
+    R = 2.0 * AN - A
+    rng = np.random.default_rng(5)
+    pts = [(int(rng.integers(0, p.n[2])), int(rng.integers(0, p.n[1])), int(rng.integers(0, p.n[0])))
+           for _ in range(40)]
+    pts += [(0, 0, 0), (p.n[2] - 1, p.n[1] - 1, p.n[0] - 1), (0, p.n[1] - 1, 0), (p.n[2] - 1, 0, p.n[0] - 1)]
+    rows = [i + p.n[0] * (j + p.n[1] * k) for (k, j, i) in pts]
+    np.testing.assert_allclose(o.apply_A_at(p, v, pts, "A"), A[rows] @ v.ravel(), rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(o.apply_A_at(p, v, pts, "RHS"), R[rows] @ v.ravel(), rtol=1e-13, atol=1e-14)
+    # and the RHS branch is the oracle's right-hand side without a source
+    np.testing.assert_allclose(o.apply_A_at(p, v, pts, "RHS"),
+                               np.array([o.rhs(p, v, None)[k, j, i] for (k, j, i) in pts]), rtol=1e-13, atol=1e-14)

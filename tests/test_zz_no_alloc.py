@@ -40,14 +40,38 @@ def reference_mass_apply(T, n, v):
         T.tfde_destroy(h)
 
 
-@pytest.mark.parametrize("n", [(40, 24, 16), (64, 64, 64), (1, 7, 3)])
+@pytest.mark.parametrize("n", [(40, 24, 16), (64, 64, 64), (1, 7, 3), (1, 512, 512), (512, 1, 512)])
 def test_noalloc_mass_apply_matches_existing_entry_point_twice(T, n):
+    """Two calls in a row with different inputs; (1, 512, 512) has more x
+    lines than one launch dimension holds (65535 blocks of 4 lines)."""
     shape = (n[2], n[1], n[0])
     for seed in (61, 62):   # two calls in a row, different inputs
         v = inp.uniform_vector(shape, seed)
         y = to_dev(np.full(shape, np.nan))
         T.tfde_mass_apply_noalloc(n, to_dev(v), y)
         assert relerr(to_host(y), reference_mass_apply(T, n, v)) < 1e-13
+
+
+def test_noalloc_in_place_and_allocates_nothing(T):
+    """y may be the same buffer as x, and a call (after the first on the
+    device, which looks up the scratch address) changes neither the device's
+    free memory nor torch's allocator state."""
+    import torch
+    n = (24, 16, 40)
+    shape = (n[2], n[1], n[0])
+    v = inp.uniform_vector(shape, 63)
+    ref = reference_mass_apply(T, n, v)
+    x = to_dev(v)
+    y = to_dev(np.zeros(shape))
+    T.tfde_mass_apply_noalloc(n, x, y)   # first call on this device
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    T.tfde_mass_apply_noalloc(n, x, x)   # in place
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0 and torch.cuda.memory_allocated() == alloc0
+    assert relerr(to_host(x), ref) < 1e-13
 
 
 def test_noalloc_rejects_grids_beyond_the_limit(T):
