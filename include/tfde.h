@@ -348,11 +348,13 @@ int tfde_host_coefficients(const tfde_params* params, int axis, double* q, doubl
                            double* eta);
 
 /* Counters of the library's own GPU work (process-wide), per kind of
- * tensor-core kernel: TFDE_KIND_SPLIT = the split-BF16 per-axis contraction
+ * per-axis kernel: TFDE_KIND_SPLIT = the split-BF16 tensor-core contraction
  * (fast operator and preconditioner), TFDE_KIND_EXACT = the exact-integer
  * slice contraction (FP64-accurate operator), TFDE_KIND_CONV = the
- * warm-start network's convolution. */
-enum { TFDE_KIND_SPLIT = 0, TFDE_KIND_EXACT = 1, TFDE_KIND_CONV = 2, TFDE_NKINDS = 3 };
+ * warm-start network's convolution, TFDE_KIND_FFT = the FFT-embedded Toeplitz
+ * and DST-I passes (bytes: the grid functions read and written once; flops:
+ * 5 L log2 L per complex transform of length L plus the spectral products). */
+enum { TFDE_KIND_SPLIT = 0, TFDE_KIND_EXACT = 1, TFDE_KIND_CONV = 2, TFDE_KIND_FFT = 3, TFDE_NKINDS = 4 };
 typedef struct {
     unsigned long long launches;  /* launches of this kind                               */
     unsigned long long timed;     /* launches covered by ms                               */

@@ -7,6 +7,7 @@
 #include <mutex>
 #include <string>
 
+#include "tfde_fft.h"
 #include "tfde_internal.h"
 
 namespace tfde {
@@ -268,6 +269,7 @@ int assemble_problem(const tfde_params* params, int precision, cudaStream_t s, t
     if ((st = dalloc(&P->red, (size_t)128 * P->nblk)) || (st = dalloc(&P->red_out, 256))) return fail(st);
     if (cudaMallocHost((void**)&P->red_host, 256 * sizeof(double)) != cudaSuccess)
         return fail(set_error(TFDE_ENOMEM, "cudaMallocHost failed"));
+    if ((st = fft::init(P, s))) return fail(st);
     if (precision == TFDE_MIXED) {
         if ((st = mixed_init(P, s))) return fail(st);
     }
@@ -303,6 +305,7 @@ int destroy_problem(tfde_problem* P) {
     if (!P) return TFDE_OK;
     cudaDeviceSynchronize();
     mixed_free(P);
+    fft::free_state(P);
     for (auto& g : P->Ghat) cudaFree(g);
     for (int a = 0; a < 3; ++a) {
         cudaFree(P->G[a]);

@@ -123,6 +123,7 @@ struct tfde_problem {
     int nblk = 0;
 
     void* mixed = nullptr;  // mixed-precision state (tensor-core path)
+    void* fft = nullptr;    // FFT tables of the FFT-embedded passes (tfde_fft.h), null: dense FP64
 
     // chained CN advance: W_B / W_R hold b^{m-1} and its final true residual
     const double* chain_u = nullptr;

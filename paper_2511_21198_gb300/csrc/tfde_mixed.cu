@@ -66,7 +66,7 @@ void gemm_params(const tfde_problem* P, int axis, const SegSpec* segs, int nseg,
     int na = 0, nb = 0;
     for (int g = 0; g < nseg; ++g) {
         tc::Segment& S = prm.seg[g];
-        S.nkb = (P->n[axis] + tc::BK - 1) / tc::BK;
+        S.nkb = (P->n[axis] + tc::SK - 1) / tc::SK;
         S.amap2 = -1;
         S.bmap2 = -1;
         if (segs[g].a_lo >= 0 && M->has_amap2[segs[g].a_hi]) {
@@ -104,9 +104,12 @@ void gemm_params(const tfde_problem* P, int axis, const SegSpec* segs, int nseg,
     prm.out_mode = out_mode;
     prm.alpha = alpha;
     prm.out_f32 = out_f32;
+    if (out_f32) tc::make_out_map(&prm.omap_f32, out_f32, P->n, axis, true);
     if (out_mode == tc::OUT_HILO || out_mode == tc::OUT_XPAY || out_mode == tc::OUT_HI) {
         prm.out_hi = M->hi[out_plane];
         prm.out_lo = M->lo[out_plane];
+        prm.omap_hi = M->omap_hi[out_plane][axis];
+        prm.omap_lo = M->omap_lo[out_plane][axis];
     }
     if (lam_scale) {
         const long long n1n2 = (long long)P->n[0] * P->n[1];
@@ -610,15 +613,15 @@ int mixed_init(tfde_problem* P, cudaStream_t s) {
         }
         MX_TRY(cudaMemcpyAsync(M->mat[om], h.data(), h.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, s));
         MX_TRY(cudaStreamSynchronize(s));
-        int st = tc::make_map_A(&M->amap[om], M->mat[om], n);
+        int st = tc::make_split_map_A(&M->amap[om], M->mat[om], n);
         if (st) return st;
         if (pair_hi) {
             // hi and lo of the pair as one 3-D tensor (k, row, term)
             const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, 2};
             const cuuint64_t strides[2] = {(cuuint64_t)n * 2, (cuuint64_t)n * n * 2};
-            const cuuint32_t box[3] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM, 2};
+            const cuuint32_t box[3] = {(cuuint32_t)tc::SK, (cuuint32_t)tc::BM, 2};
             M->has_amap2[om] = tc::encode_map(&M->amap2[om], M->mat[om], 3, dims, strides, box,
-                                              CU_TENSOR_MAP_SWIZZLE_64B) == TFDE_OK;
+                                              CU_TENSOR_MAP_SWIZZLE_128B) == TFDE_OK;
         }
     }
     {
@@ -638,6 +641,9 @@ int mixed_init(tfde_problem* P, cudaStream_t s) {
             if (st) return st;
             M->bmap2_rank[pl][a] = tc::make_map_B_pair(&M->bmap2[pl][a], M->hi[pl], P->n, a);
             M->bmap1_rank[pl][a] = tc::make_map_B_pair(&M->bmap1[pl][a], M->hi[pl], P->n, a, 1);
+            if ((st = tc::make_out_map(&M->omap_hi[pl][a], M->hi[pl], P->n, a, false)) ||
+                (st = tc::make_out_map(&M->omap_lo[pl][a], M->lo[pl], P->n, a, false)))
+                return st;
         }
     }
     for (int v = 0; v < NF; ++v) {

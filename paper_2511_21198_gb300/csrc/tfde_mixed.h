@@ -90,7 +90,7 @@ struct MixedState {
     __nv_bfloat16* mat[NOM] = {};   // hi/lo pairs share one allocation (lo = hi + n^2)
     bool own_mat[NOM] = {};
     CUtensorMap amap[NOM];
-    CUtensorMap amap2[NOM];          // for the hi of a pair: one 3-D box {32, 128, 2} loads hi and lo
+    CUtensorMap amap2[NOM];          // for the hi of a pair: one 3-D box {64, 128, 2} loads hi and lo
     bool has_amap2[NOM] = {};
     __nv_bfloat16* hi[NPL] = {};   // one allocation per plane pair: lo = hi + N
     __nv_bfloat16* lo[NPL] = {};
@@ -100,6 +100,8 @@ struct MixedState {
     int bmap2_rank[NPL][3] = {};   // 3 (x), 5 (y/z), 0 = not available
     CUtensorMap bmap1[NPL][3];     // the hi plane alone, same box otherwise
     int bmap1_rank[NPL][3] = {};
+    CUtensorMap omap_hi[NPL][3];   // the planes as outputs of the epilogue's tensor stores
+    CUtensorMap omap_lo[NPL][3];
     float* f[NF] = {};
     float* lam = nullptr;   // [ra (n3) | rb (n3) | U (n1 n2) | V (n1 n2)]
     double* dsc = nullptr;  // device scalars

@@ -5,6 +5,7 @@
 #include <utility>
 #include <vector>
 
+#include "tfde_fft.h"
 #include "tfde_internal.h"
 #include "tfde_givens.h"
 
@@ -28,6 +29,9 @@ static int check_launch(const char* what) {
 //                     c = M2 a +- eta2 B2 w,  e = M2 w;
 //                     y = M3 c +- eta3 B3 e.
 int apply_A64(const tfde_problem* P, int op, const double* x, double* y, cudaStream_t s) {
+    if (P->fft)   // FFT-embedded Toeplitz passes (O(n log n) per line)
+        return fft::apply_A<double>(P, op, x, y, P->w[tfde_problem::W_A], P->w[tfde_problem::W_W],
+                                    P->w[tfde_problem::W_C], P->w[tfde_problem::W_E], s);
     const bool rhs = (op & 1) != 0;
     const bool stiff = (op & TFDE_OP_STIFF) != 0;   // (A - A_N) x: no mass term in the x pass
     const double sg = rhs ? -1.0 : 1.0;
@@ -47,6 +51,8 @@ int apply_A64(const tfde_problem* P, int op, const double* x, double* y, cudaStr
 
 // z = S_N Lambda^{-1} S_N r (Eq. (diag_tau_pre)); S_n symmetric, S_n^2 = I.
 int apply_Pinv64(const tfde_problem* P, const double* r, double* z, cudaStream_t s) {
+    if (P->fft)   // DST-I by FFT (Bluestein), the z pair and Lambda^{-1} in one pass
+        return fft::apply_Pinv<double>(P, r, z, P->w[tfde_problem::W_A], P->w[tfde_problem::W_C], s);
     const AxisView vx = axis_view(P->n, 0), vy = axis_view(P->n, 1), vz = axis_view(P->n, 2);
     double* t1 = P->w[tfde_problem::W_A];
     double* t2 = P->w[tfde_problem::W_C];

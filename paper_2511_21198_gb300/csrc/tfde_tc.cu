@@ -28,11 +28,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 int encode(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
-           const cuuint32_t* box, CUtensorMapSwizzle sw) {
+           const cuuint32_t* box, CUtensorMapSwizzle sw,
+           CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) {
     auto fn = encode_fn();
     if (!fn) return set_error(TFDE_ECUDA, "cuTensorMapEncodeTiled is unavailable");
     cuuint32_t es[5] = {1, 1, 1, 1, 1};   // element strides, one per dimension (rank <= 5)
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), dims, strides,
+    CUresult r = fn(m, dt, (cuuint32_t)rank, const_cast<void*>(base), dims, strides,
                     box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(TFDE_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
@@ -58,7 +59,17 @@ int num_sms() {
     return g_num_sms;
 }
 
-// Operator matrix [rows = n][cols = n] row-major BF16 -> A operand (K-major, 64B swizzle).
+// Operator matrix [rows = n][cols = n] row-major BF16 -> A operand of the
+// split contraction: boxes {SK, BM}, K-major, 128B swizzle.
+int make_split_map_A(CUtensorMap* m, const __nv_bfloat16* base, int n) {
+    if (n % 8) return set_error(TFDE_EUNSUPPORTED, "tensor-core path needs n multiple of 8");
+    const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)n * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)SK, (cuuint32_t)BM};
+    return encode(m, base, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+// Operator matrix -> A operand of the exact-slice contraction: boxes {BK, BM}, K-major, 64B swizzle.
 int make_map_A(CUtensorMap* m, const __nv_bfloat16* base, int n) {
     if (n % 8) return set_error(TFDE_EUNSUPPORTED, "tensor-core path needs n multiple of 8");
     const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
@@ -67,28 +78,31 @@ int make_map_A(CUtensorMap* m, const __nv_bfloat16* base, int n) {
     return encode(m, base, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B);
 }
 
-// Vector plane viewed along `axis` -> B operand.
+// Vector plane viewed along `axis` -> B operand of the split contraction
+// (k-blocks of SK, 128B swizzle): x axis K-major box {SK, BN}; y / z axes
+// MN-major box {64 lines, SK, 1}.
 int make_map_B(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis) {
     const cuuint64_t n1 = n[0], n2 = n[1], n3 = n[2];
     if (n[0] % 8) return set_error(TFDE_EUNSUPPORTED, "tensor-core path needs n1 multiple of 8");
     if (axis == 0) {
         const cuuint64_t dims[2] = {n1, n2 * n3};
         const cuuint64_t strides[1] = {n1 * 2};
-        const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BN};
-        return encode(m, base, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B);
+        const cuuint32_t box[2] = {(cuuint32_t)SK, (cuuint32_t)BN};
+        return encode(m, base, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B);
     }
     cuuint64_t C, K, P;
     if (axis == 1) { C = n1; K = n2; P = n3; }
     else { C = n1 * n2; K = n3; P = 1; }
     const cuuint64_t dims[3] = {C, K, P};
     const cuuint64_t strides[2] = {C * 2, C * K * 2};
-    const cuuint32_t box[3] = {64, (cuuint32_t)BK, 1};
+    const cuuint32_t box[3] = {64, (cuuint32_t)SK, 1};
     return encode(m, base, 3, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
-// Vector plane along the x axis with a custom line box (K-major, 64B swizzle).
+// Vector plane along the x axis with a custom line box for the exact-slice
+// contraction (K-major, k-blocks of BK, 64B swizzle).
 int make_map_B_box(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis, int box_lines) {
-    if (axis != 0) return make_map_B(m, base, n, axis);
+    if (axis != 0) return set_error(TFDE_EINVAL, "make_map_B_box: x axis only");
     if (n[0] % 8) return set_error(TFDE_EUNSUPPORTED, "tensor-core path needs n1 multiple of 8");
     const cuuint64_t dims[2] = {(cuuint64_t)n[0], (cuuint64_t)n[1] * (cuuint64_t)n[2]};
     const cuuint64_t strides[1] = {(cuuint64_t)n[0] * 2};
@@ -97,18 +111,18 @@ int make_map_B_box(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], in
 }
 
 // Both planes of a split pair (hi at base, lo at base + N) along `axis` as one
-// tensor: x axis 3-D (k, line, plane) with box {BK, BN, 2}; y / z axes, when the
-// contiguous line extent C is a multiple of BN, 5-D (line in block, k, block,
-// outer plane, hi/lo) with box {64, BK, BN / 64, 1, 2}, so that a single copy
-// fills the whole B stage in the layout of the per-plane boxes.  Returns the
-// rank, or 0 when no merged map applies.
+// tensor: x axis 3-D (k, line, plane) with box {SK, BN, planes}; y / z axes,
+// when the contiguous line extent C is a multiple of BN, 5-D (line in block,
+// k, block, outer plane, hi/lo) with box {64, SK, BN / 64, 1, planes}, so that
+// a single copy fills the whole B stage in the layout of the per-plane boxes.
+// Returns the rank, or 0 when no merged map applies.
 int make_map_B_pair(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis, int planes) {
     const cuuint64_t n1 = n[0], n2 = n[1], n3 = n[2], N = n1 * n2 * n3;
     if (axis == 0) {
         const cuuint64_t dims[3] = {n1, n2 * n3, 2};
         const cuuint64_t strides[2] = {n1 * 2, N * 2};
-        const cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)BN, (cuuint32_t)planes};
-        return encode(m, base, 3, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B) == TFDE_OK ? 3 : 0;
+        const cuuint32_t box[3] = {(cuuint32_t)SK, (cuuint32_t)BN, (cuuint32_t)planes};
+        return encode(m, base, 3, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B) == TFDE_OK ? 3 : 0;
     }
     cuuint64_t C, K, P;
     if (axis == 1) { C = n1; K = n2; P = n3; }
@@ -116,12 +130,50 @@ int make_map_B_pair(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], i
     if (C % BN != 0) return 0;
     const cuuint64_t dims[5] = {64, K, C / 64, P, 2};
     const cuuint64_t strides[4] = {C * 2, 128, C * K * 2, N * 2};
-    const cuuint32_t box[5] = {64, (cuuint32_t)BK, (cuuint32_t)(BN / 64), 1, (cuuint32_t)planes};
+    const cuuint32_t box[5] = {64, (cuuint32_t)SK, (cuuint32_t)(BN / 64), 1, (cuuint32_t)planes};
     if (encode(m, base, 5, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != TFDE_OK) {
         set_error(TFDE_OK, "");
         return 0;
     }
     return 5;
+}
+
+// Output of the split contraction along `axis` (FP32 vector or one BF16
+// plane) for the epilogue's tensor stores, box 32 x 32: x axis {n1, lines}
+// (element (m, line) at line * n1 + m), no swizzle; y / z axes {C, n, P}
+// (element (c, m, plane)), swizzled 128B (FP32) / 64B (BF16) as the
+// epilogue lays out its slots.
+int make_out_map(CUtensorMap* m, const void* base, const int n[3], int axis, bool f32) {
+    const cuuint64_t n1 = n[0], n2 = n[1], n3 = n[2];
+    const cuuint64_t es = f32 ? 4 : 2;
+    const CUtensorMapDataType dt = f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    if (axis == 0) {
+        const cuuint64_t dims[2] = {n1, n2 * n3};
+        const cuuint64_t strides[1] = {n1 * es};
+        const cuuint32_t box[2] = {32, 32};
+        return encode(m, base, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE, dt);
+    }
+    cuuint64_t C, K, P;
+    if (axis == 1) { C = n1; K = n2; P = n3; }
+    else { C = n1 * n2; K = n3; P = 1; }
+    const cuuint64_t dims[3] = {C, K, P};
+    const cuuint64_t strides[2] = {C * es, C * K * es};
+    const cuuint32_t box[3] = {32, 32, 1};
+    return encode(m, base, 3, dims, strides, box, f32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, dt);
+}
+
+// Ring geometry of a launch from its segments: A terms at the start of a
+// stage, B planes after the largest A region, as many stages as fit.
+void set_ring(Params& P) {
+    int na = 1, nb = 1;
+    for (int g = 0; g < P.nseg; ++g) {
+        if (P.seg[g].na > na) na = P.seg[g].na;
+        if (P.seg[g].nb > nb) nb = P.seg[g].nb;
+    }
+    P.stage_b_off = na * A_TILE_BYTES;
+    P.stage_bytes = P.stage_b_off + nb * B_TILE_BYTES;
+    const int ns = RING_BYTES / P.stage_bytes;
+    P.nstages = ns < MAX_STAGES ? ns : MAX_STAGES;
 }
 
 // Fill the geometry fields of Params for a contraction along `axis`.
@@ -214,8 +266,10 @@ void launch_instance(int kmajor, int out_mode, unsigned grid, cudaStream_t s, co
     }
 }
 
-int launch(const Params& P, cudaStream_t s, double bytes, double flops) {
+int launch(const Params& P0, cudaStream_t s, double bytes, double flops) {
     if (int st = set_attrs()) return st;
+    Params P = P0;
+    set_ring(P);
     const long long total = P.ntiles * P.mhalves;
     long long grid = total < num_sms() ? total : num_sms();
     if (grid < 1) grid = 1;
@@ -237,6 +291,10 @@ int launch_grouped(const Params* groups, const long long* gstart, int ngroups, l
     std::memset(&p0, 0, sizeof(p0));
     p0.ntiles = total;
     p0.mhalves = 1;
+    // the largest stage any group may need: two operator terms, two planes
+    p0.stage_b_off = MAXA * A_TILE_BYTES;
+    p0.stage_bytes = p0.stage_b_off + MAXB * B_TILE_BYTES;
+    p0.nstages = RING_BYTES / p0.stage_bytes;
     p0.b_kmajor = b_kmajor;
     p0.out_mode = out_mode;
     p0.err = err;

@@ -15,6 +15,9 @@ int num_sms();
 int encode_map(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
                const cuuint32_t* box, CUtensorMapSwizzle sw);
 int make_map_A(CUtensorMap* m, const __nv_bfloat16* base, int n);
+int make_split_map_A(CUtensorMap* m, const __nv_bfloat16* base, int n);
+int make_out_map(CUtensorMap* m, const void* base, const int n[3], int axis, bool f32);
+void set_ring(Params& P);
 int make_map_B(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis);
 int make_map_B_box(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis, int box_lines);
 // planes: 2 (hi and lo in one box) or 1 (the hi plane alone)

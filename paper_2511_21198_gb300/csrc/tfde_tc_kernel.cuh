@@ -10,22 +10,25 @@
 // dimension.
 //
 // Design (one CTA per SM, persistent over tiles of 128 rows x 256 lines):
-//   warps 0..3  TMA producers: A tiles [128 x 32] (K-major, 64B swizzle) and
-//               B tiles [32 x 256] (x axis: K-major 64B swizzle; y/z axes:
-//               MN-major 128B swizzle, 4 boxes of 64 lines) into a 4-stage ring;
-//               the boxes of a stage are dealt round-robin to the four issuing
-//               threads (a thread issues one tensor copy at a time, so the copy
-//               rate grows with the number of issuers), each of which arrives
-//               on the stage barrier with its own byte count
-//   warp 4      allocates TMEM (2 x 256 FP32 columns) and issues tcgen05.mma
+//   warps 0..2  TMA producers: A tiles [128 x 64] (K-major, 128B swizzle; the
+//               hi and lo terms of a split operator in one 3-D box) and B
+//               tiles [64 x 256] (x axis: K-major 128B swizzle; y/z axes:
+//               MN-major 128B swizzle, 4 line blocks of 64 in one box with
+//               both planes) into a ring of 192 KB: 2 stages of 96 KB when a
+//               segment carries two operator terms and two planes, 4 stages
+//               of 48 KB for one term and one plane.  A stage moves 48-96 KB
+//               in two copies: the issue cost of a copy (~0.2-0.4 us, measured
+//               by an in-kernel timeline) is paid per copy, not per byte, so
+//               64-wide k-blocks halve it against 32-wide ones.  The boxes of
+//               a stage are dealt round-robin to the issuing threads.
+//   warp 3      allocates TMEM (2 x 256 FP32 columns) and issues tcgen05.mma
 //               (M=128, N=256, K=16, BF16 in, FP32 accumulate) from one thread
-//   warps 5..12 epilogue, two warps per TMEM lane quadrant (one per half of the
-//               256 columns): tcgen05.ld, scale, optional Lambda^{-1}, transpose
-//               through shared memory, 8- or 16-byte coalesced stores of FP32 or
-//               split BF16 (hi, lo) output
-// Every wait on an mbarrier is bounded by a wall-clock limit; on timeout the
-// kernel raises *err, stops issuing work, waits (bounded) for its own copies
-// and MMAs in flight, frees its TMEM and returns.
+//   warps 4..11 epilogue, two warps per TMEM lane quadrant (one per half of the
+//               256 columns), per 32 x 32 chunk: tcgen05.ld, scale, optional
+//               Lambda^{-1}, direction update and fused inner products, the
+//               chunk written to a swizzled shared-memory slot and sent to
+//               global memory by one TMA tensor store per output plane (the
+//               tensor map clips rows and columns beyond the grid)
 #pragma once
 
 #include <cuda.h>
@@ -37,24 +40,24 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int BN = 256;
-constexpr int BK = 32;
-constexpr int STAGES = 4;
+constexpr int BK = 32;             // k-block of the exact-slice contraction's operator maps (tfde_oz.cu)
+constexpr int SK = 64;             // k-block of this contraction: 128-byte rows of 64 BF16
 constexpr int MAXA = 2;
 constexpr int MAXB = 2;
 constexpr int MAXSEG = 2;
 constexpr int MAXPAIR = 4;
-constexpr int A_TILE_BYTES = BM * BK * 2;                                  // 8 KB
-constexpr int B_TILE_BYTES = BN * BK * 2;                                  // 16 KB
-constexpr int STAGE_BYTES = MAXA * A_TILE_BYTES + MAXB * B_TILE_BYTES;     // 48 KB
+constexpr int A_TILE_BYTES = BM * SK * 2;                                  // 16 KB
+constexpr int B_TILE_BYTES = BN * SK * 2;                                  // 32 KB
+constexpr int RING_BYTES = 2 * (MAXA * A_TILE_BYTES + MAXB * B_TILE_BYTES);  // 192 KB
+constexpr int MAX_STAGES = 4;
 constexpr int EPI_WARPS = 8;
-constexpr int PRODUCERS = 4;           // TMA issuing warps: one box per thread is issued at a time,
+constexpr int PRODUCERS = 3;           // TMA issuing warps: one box per thread is issued at a time,
 constexpr int MMA_WARP = PRODUCERS;    // so several issuers keep more copies in flight
 constexpr int EPI_WARP0 = PRODUCERS + 1;
-constexpr int NUM_THREADS = 32 * (PRODUCERS + 1 + EPI_WARPS);             // 416
-constexpr int EPI_STRIDE = 33;
-constexpr int EPI_FLOATS = EPI_WARPS * 32 * EPI_STRIDE;
-constexpr int NUM_BARS = 2 * STAGES + 5;
-constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + EPI_FLOATS * 4 + NUM_BARS * 8 + 16;
+constexpr int NUM_THREADS = 32 * (PRODUCERS + 1 + EPI_WARPS);             // 384: 12 warps (a 13th would cap registers at 128)
+constexpr int EPI_SLOT_BYTES = 4096;   // per epilogue warp: one 32 x 32 FP32 chunk, or hi + lo BF16 chunks
+constexpr int NUM_BARS = 2 * MAX_STAGES + 5;
+constexpr int SMEM_BYTES = 1024 + RING_BYTES + EPI_WARPS * EPI_SLOT_BYTES + NUM_BARS * 8 + 16;
 constexpr uint32_t TMEM_COLS = 2 * BN;
 static_assert(SMEM_BYTES <= 232448, "shared memory budget of one CTA");
 
@@ -79,6 +82,10 @@ enum { OUT_F32 = 0, OUT_HILO = 1, OUT_XPAY = 2, OUT_HI = 3 };
 struct Params {
     CUtensorMap amaps[4];
     CUtensorMap bmaps[4];
+    // output tensor maps (box 32 x 32): FP32 vector, hi plane, lo plane;
+    // x axis: {n1, lines}, no swizzle; y/z axes: {C, n, P}, 128B (FP32) /
+    // 64B (BF16) swizzle
+    CUtensorMap omap_f32, omap_hi, omap_lo;
     Segment seg[MAXSEG];
     int nseg;
     int b_kmajor;        // 1: B stored with k contiguous (x axis); 0: lines contiguous (y, z axes)
@@ -92,6 +99,9 @@ struct Params {
     int n1;              // K-major output: Y[l * n1 + m]
     long long plane;     // MN-major output plane stride (C * n)
     int out_mode;
+    int nstages;         // ring stages (2 or 4) and their geometry: A terms at 0, B planes at stage_b_off
+    int stage_bytes;
+    int stage_b_off;
     float alpha;
     float* out_f32;
     __nv_bfloat16* out_hi;
@@ -131,69 +141,78 @@ struct DotAcc {
     }
 };
 
-// The dot_vec elements matching cnt (0..4) consecutive outputs at idx, zero
-// beyond cnt; read through the non-coherent path so that the loads can be
-// issued ahead of the chunk's stores.
-__device__ __forceinline__ float4 dot_load(const float* __restrict__ w, long long idx, int cnt) {
-    if (cnt == 4) return __ldg(reinterpret_cast<const float4*>(w + idx));
-    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (cnt > 0) r.x = __ldg(w + idx);
-    if (cnt > 1) r.y = __ldg(w + idx + 1);
-    if (cnt > 2) r.z = __ldg(w + idx + 2);
-    return r;
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// The old values of cnt (0..4) consecutive in/out elements at idx (zero
-// beyond cnt), by plain loads: this kernel overwrites them afterwards.
-__device__ __forceinline__ float4 old_load(const float* w, long long idx, int cnt) {
-    if (cnt == 4) return *reinterpret_cast<const float4*>(w + idx);
-    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (cnt > 0) r.x = w[idx];
-    if (cnt > 1) r.y = w[idx + 1];
-    if (cnt > 2) r.z = w[idx + 2];
-    return r;
-}
-
-// Four consecutive outputs (already scaled) to global memory at element index idx.
-template <int OM>
-__device__ __forceinline__ void store4(const Params& p, long long idx, float v0, float v1, float v2, float v3) {
-    if constexpr (OM == OUT_F32) {
-        *reinterpret_cast<float4*>(p.out_f32 + idx) = make_float4(v0, v1, v2, v3);
-    } else if constexpr (OM == OUT_HI) {
-        const __nv_bfloat162 h01 = __floats2bfloat162_rn(v0, v1);
-        const __nv_bfloat162 h23 = __floats2bfloat162_rn(v2, v3);
-        uint2 hv;
-        hv.x = *reinterpret_cast<const uint32_t*>(&h01);
-        hv.y = *reinterpret_cast<const uint32_t*>(&h23);
-        *reinterpret_cast<uint2*>(p.out_hi + idx) = hv;
+// The 32 values of this thread (row `lane` of a 32 x 32 chunk, columns 0..31)
+// into an epilogue slot in the layout of the output tensor map's box:
+// x axis (K-major output, element (line, m) at line * 32 + m, rows of 32 m),
+// no swizzle -- a warp writes one contiguous row per column; y / z axes
+// (MN-major output, element (m, c) at m * 32 + c), swizzled so that the
+// 16-byte chunks of 8 consecutive rows fall in distinct banks (FP32: 128-byte
+// rows, chunk ^= row & 7; BF16: 64-byte rows, chunk ^= (row >> 1) & 3).
+template <bool KMAJ>
+__device__ __forceinline__ void slot_f32(uint8_t* slot, int lane, const float (&v)[32]) {
+    if constexpr (KMAJ) {
+        float* f = reinterpret_cast<float*>(slot);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) f[j * 32 + lane] = v[j];
     } else {
-        if constexpr (OM == OUT_XPAY) *reinterpret_cast<float4*>(p.out_f32 + idx) = make_float4(v0, v1, v2, v3);
-        const __nv_bfloat162 h01 = __floats2bfloat162_rn(v0, v1);
-        const __nv_bfloat162 h23 = __floats2bfloat162_rn(v2, v3);
-        const float2 f01 = __bfloat1622float2(h01);
-        const float2 f23 = __bfloat1622float2(h23);
-        const __nv_bfloat162 l01 = __floats2bfloat162_rn(v0 - f01.x, v1 - f01.y);
-        const __nv_bfloat162 l23 = __floats2bfloat162_rn(v2 - f23.x, v3 - f23.y);
-        uint2 hv, lv;
-        hv.x = *reinterpret_cast<const uint32_t*>(&h01);
-        hv.y = *reinterpret_cast<const uint32_t*>(&h23);
-        lv.x = *reinterpret_cast<const uint32_t*>(&l01);
-        lv.y = *reinterpret_cast<const uint32_t*>(&l23);
-        *reinterpret_cast<uint2*>(p.out_hi + idx) = hv;
-        *reinterpret_cast<uint2*>(p.out_lo + idx) = lv;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            *reinterpret_cast<float4*>(slot + lane * 128 + ((k ^ (lane & 7)) << 4)) =
+                make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
     }
 }
-template <int OM>
-__device__ __forceinline__ void store1(const Params& p, long long idx, float v) {
-    if constexpr (OM == OUT_F32) {
-        p.out_f32[idx] = v;
-    } else if constexpr (OM == OUT_HI) {
-        p.out_hi[idx] = __float2bfloat16_rn(v);
+template <bool KMAJ>
+__device__ __forceinline__ void slot_bf16(uint8_t* slot, int lane, const float (&v)[32]) {
+    if constexpr (KMAJ) {
+        __nv_bfloat16* h = reinterpret_cast<__nv_bfloat16*>(slot);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) h[j * 32 + lane] = __float2bfloat16_rn(v[j]);
     } else {
-        if constexpr (OM == OUT_XPAY) p.out_f32[idx] = v;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        p.out_hi[idx] = hi;
-        p.out_lo[idx] = __float2bfloat16_rn(v - __bfloat162float(hi));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint4 w;
+            w.x = pack_bf16(v[8 * k], v[8 * k + 1]);
+            w.y = pack_bf16(v[8 * k + 2], v[8 * k + 3]);
+            w.z = pack_bf16(v[8 * k + 4], v[8 * k + 5]);
+            w.w = pack_bf16(v[8 * k + 6], v[8 * k + 7]);
+            *reinterpret_cast<uint4*>(slot + lane * 64 + ((k ^ ((lane >> 1) & 3)) << 4)) = w;
+        }
+    }
+}
+
+// hi = bf16(v) into slot_hi and lo = bf16(v - hi) into slot_lo, same layout.
+template <bool KMAJ>
+__device__ __forceinline__ void slot_bf16_pair(uint8_t* slot_hi, uint8_t* slot_lo, int lane, const float (&v)[32]) {
+    if constexpr (KMAJ) {
+        __nv_bfloat16* h = reinterpret_cast<__nv_bfloat16*>(slot_hi);
+        __nv_bfloat16* l = reinterpret_cast<__nv_bfloat16*>(slot_lo);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const __nv_bfloat16 hj = __float2bfloat16_rn(v[j]);
+            h[j * 32 + lane] = hj;
+            l[j * 32 + lane] = __float2bfloat16_rn(v[j] - __bfloat162float(hj));
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * k + 2 * e], v[8 * k + 2 * e + 1]);
+                const float2 f2 = __bfloat1622float2(h2);
+                const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[8 * k + 2 * e] - f2.x, v[8 * k + 2 * e + 1] - f2.y);
+                hw[e] = *reinterpret_cast<const uint32_t*>(&h2);
+                lw[e] = *reinterpret_cast<const uint32_t*>(&l2);
+            }
+            const int off = lane * 64 + ((k ^ ((lane >> 1) & 3)) << 4);
+            *reinterpret_cast<uint4*>(slot_hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4*>(slot_lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
     }
 }
 
@@ -213,30 +232,32 @@ __device__ __forceinline__ int find_group(const long long* __restrict__ gstart, 
 // same axis) whose descriptors sit in global memory; tile t belongs to group
 // g with gstart[g] <= t < gstart[g+1], and groups with gactive[g] == 0 are
 // skipped by all three roles alike.  p0 then carries only the common fields
-// (err) and ntiles = gstart[ngroups], mhalves = 1.  KM (= Params::b_kmajor)
-// and OM (= Params::out_mode) are compile-time so that each instance carries
-// one straight-line epilogue.
+// (err, the ring geometry) and ntiles = gstart[ngroups], mhalves = 1.  KM
+// (= Params::b_kmajor) and OM (= Params::out_mode) are compile-time so that
+// each instance carries one straight-line epilogue.
 template <bool GROUPED, int KM, int OM>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     axis_gemm_kernel(const __grid_constant__ Params p0, const Params* __restrict__ groups,
                      const long long* __restrict__ gstart, int ngroups, const int* __restrict__ gactive) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t* stages = smem;
-    float* epi = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(epi + EPI_FLOATS);
+    uint8_t* ring = smem;
+    uint8_t* epi = smem + RING_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(epi + EPI_WARPS * EPI_SLOT_BYTES);
     uint64_t* full = bars;
-    uint64_t* empty = bars + STAGES;
-    uint64_t* tfull = bars + 2 * STAGES;
-    uint64_t* tempty = bars + 2 * STAGES + 2;
-    uint64_t* mma_done = bars + 2 * STAGES + 4;
+    uint64_t* empty = bars + MAX_STAGES;
+    uint64_t* tfull = bars + 2 * MAX_STAGES;
+    uint64_t* tempty = bars + 2 * MAX_STAGES + 2;
+    uint64_t* mma_done = bars + 2 * MAX_STAGES + 4;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NUM_BARS);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    const int nst = p0.nstages;
+    const int sbytes = p0.stage_bytes;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < MAX_STAGES; ++s) {
             mbar_init(&full[s], PRODUCERS);
             mbar_init(&empty[s], 1);
         }
@@ -266,6 +287,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (lane == 0) {
             // ------------------------------------------------ TMA producers
             const int pw = warp;
+            const int boff = p0.stage_b_off;
             int s = 0;
             uint32_t ph = 0;
             uint32_t filled = 0, last_ph = 0;  // per-stage bitmasks
@@ -284,70 +306,72 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const int mh = (int)(lt % p.mhalves);
                 for (int sg = 0; sg < p.nseg && ok; ++sg) {
                     const Segment& S = p.seg[sg];
+                    // boxes of a stage in a fixed order; box i belongs to issuer i % PRODUCERS
+                    // merged boxes: one copy for all A terms and one for both B planes
+                    const int na_box = S.amap2 >= 0 ? 1 : S.na;
+                    const uint32_t abytes = S.amap2 >= 0 ? (uint32_t)(S.na * A_TILE_BYTES) : (uint32_t)A_TILE_BYTES;
+                    const int bbox = S.bmap2 >= 0 ? 1 : (b_kmajor ? 1 : BN / 64);
+                    const int nb_box = S.bmap2 >= 0 ? 1 : S.nb * bbox;
+                    const uint32_t bbytes = S.bmap2 >= 0 ? (uint32_t)(S.nb * B_TILE_BYTES)
+                                                         : (b_kmajor ? (uint32_t)B_TILE_BYTES : (uint32_t)(64 * SK * 2));
+                    uint32_t mine = 0;
+                    for (int i = pw; i < na_box + nb_box; i += PRODUCERS) mine += i < na_box ? abytes : bbytes;
                     for (int kb = 0; kb < S.nkb; ++kb) {
                         if (!mbar_wait(&empty[s], ph ^ 1u, err)) { ok = false; break; }
-                        uint8_t* st = stages + s * STAGE_BYTES;
-                        // boxes of this stage in a fixed order; box i belongs to issuer i % PRODUCERS
-                        // merged boxes: one copy for all A terms and one for both B planes
-                        const int na_box = S.amap2 >= 0 ? 1 : S.na;
-                        const uint32_t abytes = S.amap2 >= 0 ? (uint32_t)(S.na * A_TILE_BYTES) : (uint32_t)A_TILE_BYTES;
-                        const int bbox = S.bmap2 >= 0 ? 1 : (b_kmajor ? 1 : BN / 64);
-                        const int nb_box = S.bmap2 >= 0 ? 1 : S.nb * bbox;
-                        const uint32_t bbytes = S.bmap2 >= 0 ? (uint32_t)(S.nb * B_TILE_BYTES)
-                                                             : (b_kmajor ? (uint32_t)B_TILE_BYTES : (uint32_t)(64 * BK * 2));
-                        uint32_t mine = 0;
-                        for (int i = pw; i < na_box + nb_box; i += PRODUCERS) mine += i < na_box ? abytes : bbytes;
+                        uint8_t* st = ring + s * sbytes;
                         mbar_expect_tx(&full[s], mine);
                         for (int i = pw; i < na_box + nb_box; i += PRODUCERS) {
                             if (i < na_box) {
                                 if (S.amap2 >= 0)
-                                    tma_load_3d(st, &p.amaps[S.amap2], &full[s], kb * BK, mh * BM, 0);
+                                    tma_load_3d(st, &p.amaps[S.amap2], &full[s], kb * SK, mh * BM, 0);
                                 else
-                                    tma_load_2d(st + i * A_TILE_BYTES, &p.amaps[S.amap[i]], &full[s], kb * BK, mh * BM);
+                                    tma_load_2d(st + i * A_TILE_BYTES, &p.amaps[S.amap[i]], &full[s], kb * SK, mh * BM);
                                 continue;
                             }
                             if (S.bmap2 >= 0) {
-                                uint8_t* dstb = st + MAXA * A_TILE_BYTES;
+                                uint8_t* dstb = st + boff;
                                 if (p.b_rank == 3) {
-                                    tma_load_3d(dstb, &p.bmaps[S.bmap2], &full[s], kb * BK, (int)(tile * BN), 0);
+                                    tma_load_3d(dstb, &p.bmaps[S.bmap2], &full[s], kb * SK, (int)(tile * BN), 0);
                                 } else {
                                     const long long gb = tile * (BN / 64);
-                                    tma_load_5d(dstb, &p.bmaps[S.bmap2], &full[s], 0, kb * BK, (int)(gb % p.nbc),
+                                    tma_load_5d(dstb, &p.bmaps[S.bmap2], &full[s], 0, kb * SK, (int)(gb % p.nbc),
                                                 (int)(gb / p.nbc), 0);
                                 }
                                 continue;
                             }
                             const int jb = i - na_box;   // B box index in the per-plane enumeration
                             const int b = jb / bbox, blk = jb % bbox;
-                            uint8_t* dst = st + MAXA * A_TILE_BYTES + b * B_TILE_BYTES;
+                            uint8_t* dst = st + boff + b * B_TILE_BYTES;
                             if (b_kmajor) {
-                                tma_load_2d(dst, &p.bmaps[S.bmap[b]], &full[s], kb * BK, (int)(tile * BN));
+                                tma_load_2d(dst, &p.bmaps[S.bmap[b]], &full[s], kb * SK, (int)(tile * BN));
                             } else {
                                 const long long gb = tile * (BN / 64) + blk;
                                 const int pl = (int)(gb / p.nbc);
                                 const int c0 = (int)(gb % p.nbc) * 64;
-                                tma_load_3d(dst + blk * (64 * BK * 2), &p.bmaps[S.bmap[b]], &full[s], c0, kb * BK, pl);
+                                tma_load_3d(dst + blk * (64 * SK * 2), &p.bmaps[S.bmap[b]], &full[s], c0, kb * SK, pl);
                             }
                         }
                         filled |= 1u << s;
                         if (ph) last_ph |= 1u << s; else last_ph &= ~(1u << s);
-                        if (++s == STAGES) { s = 0; ph ^= 1u; }
+                        if (++s == nst) { s = 0; ph ^= 1u; }
                     }
                 }
             }
             // drain: every issued copy must land before the CTA can exit
-            for (int i = 0; i < STAGES; ++i)
+            for (int i = 0; i < nst; ++i)
                 if (filled & (1u << i)) mbar_wait(&full[i], (last_ph >> i) & 1u, err, false);
         }
     } else if (warp == MMA_WARP) {
         if (lane == 0) {
             // ------------------------------------------------ MMA issuer
             const uint32_t idesc = instr_desc(BM, BN, b_kmajor ? 0 : 1);
-            // descriptor templates at stage 0; in-smem offsets are added to the
-            // start-address field (address >> 4, no carry below 256 KB)
-            const uint64_t a_desc0 = smem_desc(smem_u32(stages), 16, 512, 4);
-            const uint64_t b_desc0 = b_kmajor ? smem_desc(smem_u32(stages + MAXA * A_TILE_BYTES), 16, 512, 4)
-                                                : smem_desc(smem_u32(stages + MAXA * A_TILE_BYTES), 64 * BK * 2, 1024, 2);
+            // descriptor templates at stage 0 (128-byte swizzle, 8-row groups
+            // 1024 bytes apart; MN-major B: 64-line blocks 64 x SK x 2 bytes
+            // apart); in-smem offsets are added to the start-address field
+            // (address >> 4, no carry below 256 KB)
+            const uint64_t a_desc0 = smem_desc(smem_u32(ring), 16, 1024, 2);
+            const uint64_t b_desc0 = b_kmajor ? smem_desc(smem_u32(ring + p0.stage_b_off), 16, 1024, 2)
+                                              : smem_desc(smem_u32(ring + p0.stage_b_off), 64 * SK * 2, 1024, 2);
             const uint32_t b_k16 = b_kmajor ? (32u >> 4) : (2048u >> 4);
             int s = 0;
             uint32_t ph = 0;
@@ -373,19 +397,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     for (int kb = 0; kb < S.nkb; ++kb) {
                         if (!mbar_wait(&full[s], ph, err)) { ok = false; break; }
                         tc_fence_after();
-                        const uint64_t ad_s = a_desc0 + (uint64_t)((s * STAGE_BYTES) >> 4);
-                        const uint64_t bd_s = b_desc0 + (uint64_t)((s * STAGE_BYTES) >> 4);
+                        const uint64_t ad_s = a_desc0 + (uint64_t)((s * sbytes) >> 4);
+                        const uint64_t bd_s = b_desc0 + (uint64_t)((s * sbytes) >> 4);
                         for (int pr = 0; pr < S.npair; ++pr) {
                             const uint64_t ad_p = ad_s + (uint64_t)((S.pa[pr] * A_TILE_BYTES) >> 4);
                             const uint64_t bd_p = bd_s + (uint64_t)((S.pb[pr] * B_TILE_BYTES) >> 4);
 #pragma unroll
-                            for (int k16 = 0; k16 < BK / 16; ++k16) {
+                            for (int k16 = 0; k16 < SK / 16; ++k16) {
                                 const uint32_t acc = (sg == 0 && kb == 0 && pr == 0 && k16 == 0) ? 0u : 1u;
                                 umma_bf16(d_tmem, ad_p + (uint64_t)(k16 * (32 >> 4)), bd_p + k16 * b_k16, idesc, acc);
                             }
                         }
                         umma_commit(&empty[s]);
-                        if (++s == STAGES) { s = 0; ph ^= 1u; }
+                        if (++s == nst) { s = 0; ph ^= 1u; }
                     }
                 }
                 if (ok) umma_commit(&tfull[buf]);
@@ -397,12 +421,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
     } else {
         // ---------------------------------------------------- epilogue warps
+        const int ew = warp - EPI_WARP0;
         const int q = warp & 3;               // TMEM lane quadrant this warp may access
-        const int half = (warp - EPI_WARP0) >> 2;   // which 128 of the 256 columns
-        float* stg = epi + (warp - EPI_WARP0) * 32 * EPI_STRIDE;
-        const int rsub = lane >> 3;           // transposed phase: 4 rows / columns per instruction
-        const int cq = (lane & 7) * 4;        // ... and 4 consecutive elements per lane
+        const int half = ew >> 2;             // which 128 of the 256 columns
+        uint8_t* slot = epi + ew * EPI_SLOT_BYTES;
         long long it = 0;
+        bool pending = false;                 // a store of this warp may still read the slot
         DotAcc da;                            // fused inner product (single launches only)
         float xp_beta = 0.f;                  // OUT_XPAY coefficient
         if constexpr (OM == OUT_XPAY) {
@@ -428,152 +452,137 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             tc_fence_after();
             const long long tile = lt / p.mhalves;
             const int mh = (int)(lt % p.mhalves);
-            const int mrow0 = mh * BM + 32 * q;   // first output row of this warp
-            // Lambda row factors of this lane's 8 rows, once per tile (the rows
-            // are the same for every column chunk below; grouped instances,
-            // short of registers, load them per chunk)
-            float lra[8], lrb[8];
+            const int mrow0 = mh * BM + 32 * q;   // first row of this warp's quadrant
+            const int m = mrow0 + lane;           // this thread's row
+            const bool mval = m < p.n;
             const bool lam = !b_kmajor && p.lam_ra != nullptr;
-            if (!GROUPED && lam) {
-#pragma unroll
-                for (int i8 = 0; i8 < 8; ++i8) {
-                    const int m = mrow0 + i8 * 4 + rsub;
-                    lra[i8] = m < p.n ? __ldg(p.lam_ra + m) : 1.f;
-                    lrb[i8] = m < p.n ? __ldg(p.lam_rb + m) : 0.f;
-                }
+            float ra = 1.f, rb = 0.f;             // Lambda row factors of this row
+            if (lam && mval) {
+                ra = __ldg(p.lam_ra + m);
+                rb = __ldg(p.lam_rb + m);
             }
             for (int cc = 0; cc < BN / 2; cc += 32) {
                 const int c0 = half * (BN / 2) + cc;
-                // Output positions of this lane: 8 groups i8 of up to 4 consecutive
-                // elements, group i8 at oidx0 + i8 * ostep, cnt0 valid ones when
-                // bit i8 of vmask is set, none otherwise.
-                long long oidx0, ostep;
-                int cnt0;
-                unsigned vmask = 0;
+                // chunk position: x axis -> lines line0 .. line0 + 31 (Y[line * n1 + m]);
+                // y / z axes -> plane pl, columns cx .. cx + 31 (Y[pl * plane + m * C + c])
+                long long line0 = 0, gb = 0;
+                int pl = 0, cx = 0, ncol;
                 if (b_kmajor) {
-                    // stg[row][line]; output Y[line * n1 + m], m contiguous
-                    const int m = mrow0 + cq;
-                    const long long l0 = tile * BN + c0 + rsub;
-                    cnt0 = m + 4 <= p.n ? 4 : (m < p.n ? p.n - m : 0);
-                    oidx0 = l0 * p.n1 + m;
-                    ostep = 4LL * p.n1;
-#pragma unroll
-                    for (int i8 = 0; i8 < 8; ++i8)
-                        if (l0 + i8 * 4 < p.lines) vmask |= 1u << i8;
+                    line0 = tile * BN + c0;
+                    const long long rem = p.lines - line0;
+                    ncol = rem >= 32 ? 32 : (rem > 0 ? (int)rem : 0);
                 } else {
-                    // stg[row][c]; output Y[pl * plane + m * C + c], c contiguous
-                    const long long gb = tile * (BN / 64) + c0 / 64;
-                    const int pl = (int)(gb / p.nbc);
-                    const int c = (int)(gb % p.nbc) * 64 + (c0 & 63) + cq;
-                    const int m0 = mrow0 + rsub;
-                    cnt0 = gb < p.nblocks ? (c + 4 <= p.C ? 4 : (c < p.C ? p.C - c : 0)) : 0;
-                    oidx0 = (long long)pl * p.plane + (long long)m0 * p.C + c;
-                    ostep = 4LL * p.C;
-#pragma unroll
-                    for (int i8 = 0; i8 < 8; ++i8)
-                        if (m0 + i8 * 4 < p.n) vmask |= 1u << i8;
+                    gb = tile * (BN / 64) + c0 / 64;
+                    pl = (int)(gb / p.nbc);
+                    cx = (int)(gb % p.nbc) * 64 + (c0 & 63);
+                    const int rem = p.C - cx;
+                    ncol = gb < p.nblocks ? (rem >= 32 ? 32 : (rem > 0 ? rem : 0)) : 0;
                 }
-                if (cnt0 == 0) vmask = 0;
-                const bool dot = OM == OUT_F32 && p.dot_vec != nullptr;
-                float4 w[8];   // dot_vec (fused inner product) or the old p (OUT_XPAY) at the outputs
-                if (dot) {
+                // element (m, column j) of the output in global memory
+                const long long gbase = b_kmajor ? line0 * p.n1 + m : (long long)pl * p.plane + (long long)m * p.C + cx;
+                const long long gstep = b_kmajor ? (long long)p.n1 : 1LL;
+                // the chunk's other global operand (the old direction of the
+                // update, or the vector of the fused inner product), loaded
+                // before the accumulator read so that the two latencies overlap
+                float w[32];
+                bool use_w = false;
+                if constexpr (OM == OUT_XPAY) use_w = xp_beta != 0.f;
+                if constexpr (OM == OUT_F32) use_w = p.dot_vec != nullptr;
+                if (use_w && ncol > 0) {
+                    const float* src = OM == OUT_XPAY ? (p.xp_old ? p.xp_old : p.out_f32) : p.dot_vec;
+                    if (!mval) {
 #pragma unroll
-                    for (int i8 = 0; i8 < 8; ++i8)
-                        w[i8] = dot_load(p.dot_vec, oidx0 + i8 * ostep, (vmask >> i8) & 1u ? cnt0 : 0);
-                }
-                if constexpr (OM == OUT_XPAY) {
-                    if (xp_beta != 0.f) {
+                        for (int j = 0; j < 32; ++j) w[j] = 0.f;
+                    } else if (!b_kmajor && ncol == 32) {
 #pragma unroll
-                        for (int i8 = 0; i8 < 8; ++i8)
-                            w[i8] = old_load(p.xp_old ? p.xp_old : p.out_f32, oidx0 + i8 * ostep,
-                                             (vmask >> i8) & 1u ? cnt0 : 0);
-                    }
-                }
-                // Lambda column factors of this lane's 4 columns, issued before
-                // the accumulator read so that their latency overlaps it
-                float U[4] = {0.f, 0.f, 0.f, 0.f}, V[4] = {0.f, 0.f, 0.f, 0.f};
-                if (lam && (vmask & 1u)) {
-                    const int c = (int)((tile * (BN / 64) + c0 / 64) % p.nbc) * 64 + (c0 & 63) + cq;
-                    if (c + 4 <= p.C && ((reinterpret_cast<uintptr_t>(p.lam_U + c) |
-                                          reinterpret_cast<uintptr_t>(p.lam_V + c)) & 15) == 0) {
-                        const float4 u4 = __ldg(reinterpret_cast<const float4*>(p.lam_U + c));
-                        const float4 v4 = __ldg(reinterpret_cast<const float4*>(p.lam_V + c));
-                        U[0] = u4.x; U[1] = u4.y; U[2] = u4.z; U[3] = u4.w;
-                        V[0] = v4.x; V[1] = v4.y; V[2] = v4.z; V[3] = v4.w;
+                        for (int k = 0; k < 8; ++k) {
+                            const float4 o4 = OM == OUT_XPAY ? *(reinterpret_cast<const float4*>(src + gbase) + k)
+                                                             : __ldg(reinterpret_cast<const float4*>(src + gbase) + k);
+                            w[4 * k] = o4.x; w[4 * k + 1] = o4.y; w[4 * k + 2] = o4.z; w[4 * k + 3] = o4.w;
+                        }
                     } else {
 #pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            if (c + k < p.C) {
-                                U[k] = __ldg(p.lam_U + c + k);
-                                V[k] = __ldg(p.lam_V + c + k);
-                            }
+                        for (int j = 0; j < 32; ++j) w[j] = j < ncol ? src[gbase + j * gstep] : 0.f;
                     }
                 }
                 uint32_t r[32];
                 tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN + c0), r);
+                if (ncol == 0) continue;   // warp-uniform
+                float v[32];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) stg[lane * EPI_STRIDE + j] = p.alpha * __uint_as_float(r[j]);
-                __syncwarp();
-                // Every staged value of this lane first (32 independent shared
-                // loads), then the conversions and stores: with two epilogue
-                // warps per scheduler the chunk is latency-bound, so the
-                // independent work is laid out for the scheduler to overlap.
-                float v[8][4];
+                for (int j = 0; j < 32; ++j) v[j] = p.alpha * __uint_as_float(r[j]);
+                if (lam) {
+                    float tl = 0.f;
+                    float U[32], V[32];
+                    if (ncol == 32) {
 #pragma unroll
-                for (int i8 = 0; i8 < 8; ++i8)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        v[i8][k] = b_kmajor ? stg[(cq + k) * EPI_STRIDE + i8 * 4 + rsub]
-                                            : stg[(i8 * 4 + rsub) * EPI_STRIDE + cq + k];
-                __syncwarp();   // the staging buffer is free for the next chunk
-                if (lam && (vmask & 1u)) {   // rows ascend: none valid if the first is not
-#pragma unroll
-                    for (int i8 = 0; i8 < 8; ++i8)
-                        if ((vmask >> i8) & 1u) {
-                            const int m = mrow0 + i8 * 4 + rsub;
-                            const float ra = GROUPED ? __ldg(p.lam_ra + m) : lra[i8];
-                            const float rb = GROUPED ? __ldg(p.lam_rb + m) : lrb[i8];
-                            float tl = 0.f;
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                const float t = v[i8][k];
-                                v[i8][k] = __fdividef(t, ra * U[k] + rb * V[k]);
-                                if (k < cnt0) tl = fmaf(t, v[i8][k], tl);
-                            }
-                            if (p.dot_lam) da.add(tl);
+                        for (int k = 0; k < 8; ++k) {
+                            const float4 u4 = __ldg(reinterpret_cast<const float4*>(p.lam_U + cx) + k);
+                            const float4 v4 = __ldg(reinterpret_cast<const float4*>(p.lam_V + cx) + k);
+                            U[4 * k] = u4.x; U[4 * k + 1] = u4.y; U[4 * k + 2] = u4.z; U[4 * k + 3] = u4.w;
+                            V[4 * k] = v4.x; V[4 * k + 1] = v4.y; V[4 * k + 2] = v4.z; V[4 * k + 3] = v4.w;
                         }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            U[j] = j < ncol ? __ldg(p.lam_U + cx + j) : 1.f;
+                            V[j] = j < ncol ? __ldg(p.lam_V + cx + j) : 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float t0 = v[j];
+                        v[j] = __fdividef(t0, ra * U[j] + rb * V[j]);
+                        if (j < ncol) tl = fmaf(t0, v[j], tl);
+                    }
+                    if (p.dot_lam && mval) da.add(tl);
                 }
                 if constexpr (OM == OUT_XPAY) {
-                    if (xp_beta != 0.f) {
+                    if (use_w) {
 #pragma unroll
-                        for (int i8 = 0; i8 < 8; ++i8) {
-                            v[i8][0] = fmaf(xp_beta, w[i8].x, v[i8][0]);
-                            v[i8][1] = fmaf(xp_beta, w[i8].y, v[i8][1]);
-                            v[i8][2] = fmaf(xp_beta, w[i8].z, v[i8][2]);
-                            v[i8][3] = fmaf(xp_beta, w[i8].w, v[i8][3]);
-                        }
+                        for (int j = 0; j < 32; ++j) v[j] = fmaf(xp_beta, w[j], v[j]);
                     }
                 }
+                if constexpr (OM == OUT_F32) {
+                    if (use_w && mval) {
+                        float acc = 0.f;
 #pragma unroll
-                for (int i8 = 0; i8 < 8; ++i8) {
-                    const int cnt = cnt0;
-                    if ((vmask >> i8) & 1u) {
-                        const long long idx = oidx0 + i8 * ostep;
-                        if (cnt == 4) {
-                            store4<OM>(p, idx, v[i8][0], v[i8][1], v[i8][2], v[i8][3]);
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < 3; ++k)
-                                if (k < cnt) store1<OM>(p, idx + k, v[i8][k]);
-                        }
-                        if (dot) {
-#pragma unroll
-                            for (int k = 1; k < 4; ++k)
-                                if (k >= cnt) v[i8][k] = 0.f;   // outside the grid (may be 0 / 0 above)
-                            const float4 wv = w[i8];
-                            da.add(fmaf(v[i8][0], wv.x, fmaf(v[i8][1], wv.y, fmaf(v[i8][2], wv.z, v[i8][3] * wv.w))));
-                        }
+                        for (int j = 0; j < 32; ++j) acc = fmaf(v[j], w[j], acc);   // w = 0 beyond ncol
+                        da.add(acc);
                     }
+                }
+                // the slot is free once this warp's previous stores have read it
+                if (pending && lane == 0) bulk_wait_read0();
+                __syncwarp();
+                auto store = [&](const CUtensorMap* map, const uint8_t* src) {
+                    if (b_kmajor) tma_store_2d(map, src, mrow0, (int)line0);
+                    else tma_store_3d(map, src, cx, mrow0, pl);
+                };
+                if constexpr (OM == OUT_F32 || OM == OUT_XPAY) {
+                    slot_f32<KM != 0>(slot, lane, v);
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        store(&p.omap_f32, slot);
+                        bulk_commit();
+                    }
+                    pending = true;
+                }
+                if constexpr (OM == OUT_XPAY) {
+                    if (lane == 0) bulk_wait_read0();
+                    __syncwarp();
+                }
+                if constexpr (OM != OUT_F32) {
+                    if constexpr (OM == OUT_HI) slot_bf16<KM != 0>(slot, lane, v);
+                    else slot_bf16_pair<KM != 0>(slot, slot + 2048, lane, v);
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        store(&p.omap_hi, slot);
+                        if constexpr (OM != OUT_HI) store(&p.omap_lo, slot + 2048);
+                        bulk_commit();
+                    }
+                    pending = true;
                 }
             }
             tc_fence_before();
@@ -581,6 +590,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             if (lane == 0) mbar_arrive(&tempty[buf]);
             ++it;
         }
+        if (lane == 0) bulk_wait0();   // every store of this warp has completed
+        __syncwarp();
         if (p0.dot_out) {
             double t = (double)da.s - (double)da.c;
 #pragma unroll

@@ -41,11 +41,12 @@ class tfde_kernel_stats(Structure):
                 ("bytes", c_double), ("flops", c_double)]
 
 
-TFDE_KIND_SPLIT, TFDE_KIND_EXACT, TFDE_KIND_CONV = 0, 1, 2
+TFDE_KIND_SPLIT, TFDE_KIND_EXACT, TFDE_KIND_CONV, TFDE_KIND_FFT = 0, 1, 2, 3
+TFDE_NKINDS = 4
 
 
 class tfde_stats(Structure):
-    _fields_ = [("kernel_launches", ctypes.c_ulonglong), ("kind", tfde_kernel_stats * 3)]
+    _fields_ = [("kernel_launches", ctypes.c_ulonglong), ("kind", tfde_kernel_stats * 4)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -41,6 +41,9 @@ CASES = [
     ((4, 5, 66), (0.9, 0.1, 0.5), (1.0, 1.0, 1.0), (1.0, 1.0, 1.0), 0.3),
     ((1, 1, 1), (0.5, 0.5, 0.5), (1.0, 1.0, 1.0), (1.0, 1.0, 1.0), 0.1),
     ((1, 9, 2), (0.2, 0.5, 0.8), (1.0, 2.0, 1.0), (1.5, 2.0, 0.5), 0.1),
+    # n + 1 prime on every axis (101, 5, 31): the DST-I transform length has no small factor
+    ((100, 4, 30), (0.35, 0.65, 0.95), (1.5, 1.0, 1.0), (0.7, 1.0, 2.0), 0.02),
+    ((130, 3, 2), (0.6, 0.3, 0.5), (1.0,) * 3, (1.0,) * 3, 0.05),
 ]
 
 

@@ -45,11 +45,14 @@ def test_noalloc_mass_apply_matches_existing_entry_point_twice(T, n):
     """Two calls in a row with different inputs; (1, 512, 512) has more x
     lines than one launch dimension holds (65535 blocks of 4 lines)."""
     shape = (n[2], n[1], n[0])
+    # the reference (A x + (2 A_N - A) x) / 2 cancels the stiffness terms,
+    # which grow with the grid: its own rounding sets the bar on long axes
+    bar = 1e-13 if max(n) <= 64 else 1e-12
     for seed in (61, 62):   # two calls in a row, different inputs
         v = inp.uniform_vector(shape, seed)
         y = to_dev(np.full(shape, np.nan))
         T.tfde_mass_apply_noalloc(n, to_dev(v), y)
-        assert relerr(to_host(y), reference_mass_apply(T, n, v)) < 1e-13
+        assert relerr(to_host(y), reference_mass_apply(T, n, v)) < bar
 
 
 def test_noalloc_in_place_and_allocates_nothing(T):
