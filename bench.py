@@ -330,7 +330,9 @@ def run_ours(args):
     chained_steps(T, h, u, F, dt, 0, args.warmup, tol, stream)
     torch.cuda.synchronize()
     barrier(on)
-    T.tfde_stats_reset(time_tc=True)
+    # the product path as is: no per-launch timing events (those would also
+    # switch the inner PCG to its host-driven loop)
+    T.tfde_stats_reset(time_tc=False)
     clk = ClockSampler(local)
     clk.start()
     torch.cuda.synchronize()
@@ -341,7 +343,7 @@ def run_ours(args):
     clocks = clk.stop()
     barrier(on)
     ms = e0.elapsed_time(e1)
-    st = T.tfde_stats_get()
+    launches = int(T.tfde_stats_get().kernel_launches)
     ms_max = reduce_max(ms, on, dev)
     value = aggregate_value(args.steps, world, ms_max / 1e3)
     t_end = (args.warmup + args.steps) * dt
@@ -373,6 +375,40 @@ def run_ours(args):
         nbytes = u.numel() * u.element_size()
         e2e = {"value": aggregate_value(args.steps, world, ms_e / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    # ---- kernel timing for the roofline: the same chained steps with every
+    # tensor-core launch bracketed by CUDA events (host-driven inner loop)
+    m0 = args.warmup + 2 * args.steps
+    T.tfde_stats_reset(time_tc=True)
+    e0.record(stream)
+    it_t, sw_t, _ = chained_steps(T, h, u, F, dt, m0, args.steps, tol, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_t = e0.elapsed_time(e1)
+    st = T.tfde_stats_get()
+    T.tfde_stats_reset(time_tc=False)
+    # ---- host gap: a second problem marches the same trajectory (warm-up and
+    # timed steps) with the inner loop driven from the host; the iterates are
+    # the same, so the time difference is the host round trips
+    hb = T.tfde_assemble(params, T.TFDE_MIXED, stream)
+    T.tfde_set_guess_order(hb, args.guess_order)
+    T.tfde_set_device_loop(hb, False)
+    ub = u0.clone()
+    chained_steps(T, hb, ub, F, dt, 0, args.warmup, tol, stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    it_h, _, _ = chained_steps(T, hb, ub, F, dt, args.warmup, args.steps, tol, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_h = e0.elapsed_time(e1)
+    T.tfde_destroy(hb)
+    del ub
+    host_gap = {"ms_per_step_device_loop": ms / args.steps, "ms_per_step_host_loop": ms_h / args.steps,
+                "iters_per_step_host_loop": it_h / args.steps, "iters_per_step_device_loop": iters / args.steps,
+                "host_gap_share_removed": (ms_h - ms) / ms_h,
+                "note": "the timed steps again on a second problem with the inner PCG driven from the host "
+                        "(one blocking read of <r, r> per inner iteration) instead of one graph launch per "
+                        "refinement sweep"}
 
     # ---- the survey's C-3 protocol: one warm-up step, then steps m = 2 .. 20 (T = 1)
     c3 = None
@@ -442,7 +478,7 @@ def run_ours(args):
         # frac: the algorithmic bytes of the inner iterations (matvec read p,
         # write Ap; preconditioner read r, write z; FP32) over the summed
         # launch time; schedule_frac: the bytes the launches' schedule moves.
-        alg = iters * survey_bytes_per_iteration(n)
+        alg = it_t * survey_bytes_per_iteration(n)
         achieved = alg / (ks.ms / 1e3) / 1e9
         sched = ks.bytes / (ks.ms / 1e3) / 1e9
         step_bytes = survey_bytes_per_step(n, iters / args.steps, sweeps / args.steps)
@@ -453,11 +489,14 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": alg / ks.launches,
                 "algorithmic_bytes_basis": "16 n^3 bytes per inner iteration (FP32 matvec p -> Ap, "
                                            "preconditioner r -> z)",
-                "split_us_per_inner_iteration": 1e3 * ks.ms / max(iters, 1),
+                "split_us_per_inner_iteration": 1e3 * ks.ms / max(it_t, 1),
+                "timing_run": f"{args.steps} further chained steps with CUDA-event pairs around every "
+                              f"tensor-core launch ({ms_t / args.steps:.3f} ms/step, {it_t / args.steps:.2f} "
+                              "inner iterations per step)",
                 "schedule_bytes_per_launch": ks.bytes / ks.launches, "schedule_achieved": sched,
                 "schedule_frac": sched / peaks["hbm_gbs"],
                 "tensor_tflops": ks.flops / (ks.ms / 1e3) / 1e12,
-                "kernel_share_of_step": ks.ms / ms,
+                "kernel_share_of_step": ks.ms / ms_t,
                 "step": {"algorithmic_bytes_per_step": step_bytes,
                          "achieved": step_bytes / (ms / args.steps / 1e3) / 1e9,
                          "frac": step_bytes / (ms / args.steps / 1e3) / 1e9 / peaks["hbm_gbs"]}}
@@ -468,7 +507,7 @@ def run_ours(args):
                 "tensor_tflops": kx.flops / (kx.ms / 1e3) / 1e12,
                 "frac_of_bf16_peak": kx.flops / (kx.ms / 1e3) / 1e12 / peaks["bf16_tflops_sustained"],
                 "achieved_gbs": kx.bytes / (kx.ms / 1e3) / 1e9,
-                "kernel_share_of_step": kx.ms / ms}
+                "kernel_share_of_step": kx.ms / ms_t}
 
     # ---- CPU baseline (oracle), rank 0 at N = 1 only
     cpu = None
@@ -499,7 +538,7 @@ def run_ours(args):
                        "step_api": "tfde_cn_advance (chained: A u^(m-1) = b^(m-1) - r^(m-1))",
                        "l2": "inputs larger than L2 (each FP64 vector 134 MB, working set > 2 GB)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st.kernel_launches),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "host_gap": host_gap,
             "clocks": clocks, "fp64_path": fp64, "c3_protocol": c3, "parity_n256": parity,
             "c2_nonsymmetric_n128": c2, "batched": batched, "warm_start": warm,
             "iters_per_step": iters / args.steps, "refine_sweeps_per_step": sweeps / args.steps,

@@ -214,6 +214,21 @@ int tfde_cn_advance_guess(const tfde_problem* prob, double* u, const double* F_h
  */
 int tfde_set_guess_order(tfde_problem* prob, int order);
 
+/*
+ * tfde_set_device_loop -- how the inner PCG of a TFDE_MIXED problem runs its
+ * iterations (Sec. 3.1; no effect on TFDE_FP64 problems or on PGMRES).
+ *   enable != 0 (default): each refinement sweep's inner iterations run as one
+ *   CUDA graph launch, a device-side while loop whose stop test (the inner
+ *   residual norm against the sweep's target) is taken on the device; the host
+ *   reads the iteration count and residual once per sweep.  enable = 0: the
+ *   host takes the stop test after every iteration (one blocking read each).
+ *   Both give the same iterates.  While tfde_stats_reset(1) times every
+ *   tensor-core launch, the host-driven loop is used.  The graph is built on
+ *   the problem's first sweep and captures its workspace pointers; it is
+ *   released with the problem.  Errors: TFDE_EINVAL for a NULL problem.
+ */
+int tfde_set_device_loop(tfde_problem* prob, int enable);
+
 /* ------------------------------------------------------------------ batches */
 typedef struct tfde_batch tfde_batch;
 
@@ -370,7 +385,8 @@ typedef struct {
 /*
  * tfde_stats_reset -- zero the counters; `time_tc` != 0 additionally brackets
  * every tensor-core kernel launch with a CUDA event pair on its stream so that
- * kind[k].ms is the sum of their device durations.  Not thread-safe.
+ * kind[k].ms is the sum of their device durations (the inner PCG then runs its
+ * host-driven loop, see tfde_set_device_loop).  Not thread-safe.
  */
 int tfde_stats_reset(int time_tc);
 

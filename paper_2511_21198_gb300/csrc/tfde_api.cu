@@ -32,6 +32,7 @@ int mixed_apply_A(const tfde_problem*, int, const double*, double*, cudaStream_t
 int mixed_apply_Pinv(const tfde_problem*, const double*, double*, cudaStream_t);
 int mixed_pcg(tfde_problem*, const double*, double*, double, int, tfde_info*, cudaStream_t, bool);
 int mixed_pgmres(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t, bool);
+int mixed_set_device_loop(tfde_problem*, int);
 namespace tc {
 int wait_selftest(long long limit_ns, int* tmem_freed, cudaStream_t s);
 }
@@ -294,6 +295,11 @@ int tfde_stats_reset(int time_tc) { return stats_reset(time_tc); }
 int tfde_stats_get(tfde_stats* out) {
     if (!out) return set_error(TFDE_EINVAL, "NULL stats");
     return stats_get(out);
+}
+
+int tfde_set_device_loop(tfde_problem* prob, int enable) {
+    if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
+    return mixed_set_device_loop(prob, enable);
 }
 
 int tfde_selftest_wait(long long limit_ns, int* tmem_freed, void* stream) {

@@ -93,7 +93,8 @@ __global__ __launch_bounds__(kT) void cg_update_r32_kernel(long long N, const do
                                                            const float* __restrict__ q, float* __restrict__ r,
                                                            __nv_bfloat16* __restrict__ rh,
                                                            __nv_bfloat16* __restrict__ rl, double* __restrict__ rr,
-                                                           double* __restrict__ alpha_out) {
+                                                           double* __restrict__ alpha_out, const int* skip) {
+    if (skip && *skip) return;
     __shared__ float s_alpha;
     if (threadIdx.x == 0) {
         const double a = num[0] / den[0];
@@ -133,7 +134,9 @@ __global__ __launch_bounds__(kT) void cg_update_r32_v4_kernel(long long N4, cons
                                                               const double* __restrict__ den,
                                                               const float4* __restrict__ q, float4* __restrict__ r,
                                                               uint2* __restrict__ rh, uint2* __restrict__ rl,
-                                                              double* __restrict__ rr, double* __restrict__ alpha_out) {
+                                                              double* __restrict__ rr, double* __restrict__ alpha_out,
+                                                              const int* skip) {
+    if (skip && *skip) return;
     __shared__ float s_alpha;
     if (threadIdx.x == 0) {
         const double a = num[0] / den[0];
@@ -392,17 +395,102 @@ void launch_cg_update32(size_t N, const double* num, const double* den, const fl
     cg_update32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, num, den, p, q, x, r, rh, rl, rr);
 }
 void launch_cg_update_r32(size_t N, const double* num, const double* den, const float* q, float* r,
-                          __nv_bfloat16* rh, __nv_bfloat16* rl, double* rr, double* alpha_out, cudaStream_t s) {
+                          __nv_bfloat16* rh, __nv_bfloat16* rl, double* rr, double* alpha_out, cudaStream_t s,
+                          const int* skip) {
     stats_count_launch();
     if (aligned16(N, q, r, rh, rl)) {
         const long long N4 = (long long)N / 4;
         cg_update_r32_v4_kernel<<<grid_for(N4), kT, 0, s>>>(N4, num, den, reinterpret_cast<const float4*>(q),
                                                             reinterpret_cast<float4*>(r), reinterpret_cast<uint2*>(rh),
-                                                            reinterpret_cast<uint2*>(rl), rr, alpha_out);
+                                                            reinterpret_cast<uint2*>(rl), rr, alpha_out, skip);
         return;
     }
-    cg_update_r32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, num, den, q, r, rh, rl, rr, alpha_out);
+    cg_update_r32_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, num, den, q, r, rh, rl, rr, alpha_out,
+                                                               skip);
 }
+// ------------------------------------------------ device-side inner PCG loop
+// Control words ctl[0] = iterations done, ctl[1] = done (stop test met or
+// maxit reached), ctl[2] = maxit; device scalars d[] in the inner PCG's slots.
+
+// start of an iteration: <r, z> of the last preconditioner application
+// becomes the current one; the accumulators start at zero
+__global__ void pcg_head_kernel(double* d, int rz, int rzn, int pq, int rr, const int* ctl) {
+    if (ctl[1]) return;
+    d[rz] = d[rzn];
+    d[rzn] = 0.0;
+    d[pq] = 0.0;
+    d[rr] = 0.0;
+}
+
+// after the residual update: count the iteration, take the stop test
+// <r, r> <= thr (or maxit, or a non-finite value) and set the loop condition
+__global__ void pcg_cond_kernel(cudaGraphConditionalHandle h, const double* rr, const double* thr, int* ctl) {
+    if (ctl[1]) return;   // an earlier iteration of this body ended the loop
+    const int k = ctl[0] + 1;
+    ctl[0] = k;
+    const double v = *rr;
+    const int done = (!(v > *thr) || k >= ctl[2] || !isfinite(v)) ? 1 : 0;
+    ctl[1] = done;
+    cudaGraphSetConditional(h, done ? 0u : 1u);
+}
+
+__global__ void pcg_init_kernel(double* d, int rzn, int thr_slot, double thr, int* ctl, int maxit) {
+    d[rzn] = 0.0;
+    d[thr_slot] = thr;
+    ctl[0] = 0;
+    ctl[1] = 0;
+    ctl[2] = maxit;
+}
+
+// fold of a full window of kPRing directions into x32 (skipped once the loop
+// is done: the host combines what is left); the window is the first one
+// (x32 = sum) while ctl[0] <= kPRing, else x32 += sum
+__global__ void pcg_fold_dev_kernel(long long N4, CombineArgs a, float4* __restrict__ x32, const int* ctl) {
+    if (*reinterpret_cast<const volatile int*>(ctl + 1)) return;
+    const bool fold = ctl[0] > kPRing;
+    __shared__ float s_al[kPRing];
+    if (threadIdx.x < kPRing) s_al[threadIdx.x] = (float)*a.alpha[threadIdx.x];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N4; i += (long long)gridDim.x * blockDim.x) {
+        float4 d = fold ? x32[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < kPRing; ++t) {
+            const float4 pv = reinterpret_cast<const float4*>(a.p[t])[i];
+            d.x = fmaf(s_al[t], pv.x, d.x);
+            d.y = fmaf(s_al[t], pv.y, d.y);
+            d.z = fmaf(s_al[t], pv.z, d.z);
+            d.w = fmaf(s_al[t], pv.w, d.w);
+        }
+        x32[i] = d;
+    }
+}
+
+void launch_pcg_head(double* d, int rz, int rzn, int pq, int rr, const int* ctl, cudaStream_t s) {
+    stats_count_launch();
+    pcg_head_kernel<<<1, 1, 0, s>>>(d, rz, rzn, pq, rr, ctl);
+}
+void launch_pcg_cond(cudaGraphConditionalHandle h, const double* rr, const double* thr, int* ctl, cudaStream_t s) {
+    stats_count_launch();
+    pcg_cond_kernel<<<1, 1, 0, s>>>(h, rr, thr, ctl);
+}
+void launch_pcg_init(double* d, int rzn, int thr_slot, double thr, int* ctl, int maxit, cudaStream_t s) {
+    stats_count_launch();
+    pcg_init_kernel<<<1, 1, 0, s>>>(d, rzn, thr_slot, thr, ctl, maxit);
+}
+void launch_pcg_fold_dev(size_t N, const float* const* p, const double* const* alpha, float* x32, const int* ctl,
+                         cudaStream_t s) {
+    stats_count_launch();
+    CombineArgs a;
+    a.cnt = kPRing;
+    a.fold = 0;
+    for (int j = 0; j < kPRing; ++j) {
+        a.p[j] = p[j];
+        a.alpha[j] = alpha[j];
+    }
+    const long long N4 = (long long)N / 4;
+    pcg_fold_dev_kernel<<<grid_for(N4), kT, 0, s>>>(N4, a, reinterpret_cast<float4*>(x32), ctl);
+}
+
 void launch_pcg_combine(size_t N, const PcgPending& pend, const float* x32, double sc, double* c64, double* x64,
                         float* acc32, cudaStream_t s) {
     stats_count_launch();

@@ -9,6 +9,7 @@
 
 #include "tfde_givens.h"
 #include "tfde_mixed.h"
+#include "tfde_stats.h"
 
 namespace tfde {
 
@@ -133,10 +134,11 @@ void gemm_params(const tfde_problem* P, int axis, const SegSpec* segs, int nseg,
 
 int run_gemm(const tfde_problem* P, int axis, const SegSpec* segs, int nseg, int out_mode, float alpha,
              float* out_f32, int out_plane, bool lam_scale, cudaStream_t s, const float* dot_vec = nullptr,
-             double* dot_out = nullptr) {
+             double* dot_out = nullptr, const int* skip = nullptr) {
     tc::Params prm;
     double bytes, flops;
     gemm_params(P, axis, segs, nseg, out_mode, alpha, out_f32, out_plane, lam_scale, prm, &bytes, &flops);
+    prm.skip = skip;
     if (out_mode == tc::OUT_F32 && dot_out) {
         prm.dot_vec = dot_vec;
         prm.dot_out = dot_out;
@@ -187,12 +189,12 @@ int precond_passes(Pass* ps) {
 // The last pass's FP32 output may also be dotted with dot_vec into *dot_out
 // (accumulated: the caller zeroes it).
 int run_passes(const tfde_problem* P, const Pass* ps, int np, float* out_f32, cudaStream_t s,
-               const float* dot_vec = nullptr, double* dot_out = nullptr) {
+               const float* dot_vec = nullptr, double* dot_out = nullptr, const int* skip = nullptr) {
     for (int i = 0; i < np; ++i) {
         const Pass& q = ps[i];
         const bool last = i + 1 == np;
         int st = run_gemm(P, q.axis, q.seg, q.nseg, q.out_mode, 1.f, q.out_mode == tc::OUT_F32 ? out_f32 : nullptr,
-                          q.out_plane, q.lam, s, last ? dot_vec : nullptr, last ? dot_out : nullptr);
+                          q.out_plane, q.lam, s, last ? dot_vec : nullptr, last ? dot_out : nullptr, skip);
         if (st) return st;
     }
     return TFDE_OK;
@@ -233,20 +235,20 @@ int ensure_pairs(const tfde_problem* P, cudaStream_t s) {
 }
 
 int fast_matvec(const tfde_problem* P, int op, float* q32, cudaStream_t s, int out_plane = -1,
-                const float* dot_vec = nullptr, double* dot_out = nullptr) {
+                const float* dot_vec = nullptr, double* dot_out = nullptr, const int* skip = nullptr) {
     Pass ps[5];
     const int np = matvec_passes(op, out_plane, ps);
-    if (op != TFDE_OP_A) return run_passes(P, ps, np, q32, s, dot_vec, dot_out);
+    if (op != TFDE_OP_A) return run_passes(P, ps, np, q32, s, dot_vec, dot_out, skip);
     MixedState* M = mixed(P);
     int st;
     if ((st = ensure_pairs(P, s))) return st;
     for (int g = 0; g < 2; ++g) {
         M->gemm_launches++;
         st = tc::launch_grouped(M->pair_d + 2 * g, M->pair_gstart + 3 * g, 2, M->pair_total[g], g == 0 ? 1 : 0,
-                                tc::OUT_HILO, nullptr, M->err, s, M->pair_bytes[g], M->pair_flops[g]);
+                                tc::OUT_HILO, nullptr, M->err, s, M->pair_bytes[g], M->pair_flops[g], skip);
         if (st) return st;
     }
-    return run_passes(P, ps + 4, 1, q32, s, dot_vec, dot_out);
+    return run_passes(P, ps + 4, 1, q32, s, dot_vec, dot_out, skip);
 }
 
 // z32 = S_N Lambda^{-1} S_N r, r given as the split plane pair PL_R.
@@ -262,7 +264,7 @@ int fast_matvec(const tfde_problem* P, int op, float* q32, cudaStream_t s, int o
 // and converts half the data.  The last pass still writes p in FP32 and in
 // split planes, for the operator.
 int fast_precond_cg(const tfde_problem* P, float* p32, const float* p_old, double* rz, const double* num,
-                    const double* den, cudaStream_t s) {
+                    const double* den, cudaStream_t s, const int* skip = nullptr) {
     MixedState* M = mixed(P);
     Pass ps[6];
     const int np = precond_passes(ps);
@@ -299,6 +301,7 @@ int fast_precond_cg(const tfde_problem* P, float* p32, const float* p_old, doubl
             prm.xp_old = p_old;
             bytes += 8.0 * (double)P->N;   // the old p in, the split planes out
         }
+        prm.skip = skip;
         mixed(P)->gemm_launches++;
         if (int st = tc::launch(prm, s, bytes, flops)) return st;
     }
@@ -333,6 +336,10 @@ double host_scalar(const tfde_problem* P, const double* dev, cudaStream_t s, int
 // Device-scalar slots: <p, A p>, <r, r>, and <r, z> of the current / next
 // iteration in alternating slots (a kernel that reads one writes the other).
 enum { D_PQ = 0, D_RR = 1, D_RZ0 = 2, D_RZ1 = 3 };
+
+int build_pcg_graph(const tfde_problem* P, cudaStream_t s);
+int inner_pcg_graph(const tfde_problem* P, double theta, int maxit, int* iters, PcgPending* pend, cudaStream_t s,
+                    double* reached, double rr0);
 
 // Inner PCG on FP32 vectors: A d = r32 (r32 and its split planes prepared by
 // the caller, x32 = 0), until ||r|| <= theta ||r32_0|| or maxit.  The inner
@@ -369,6 +376,11 @@ int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, PcgPen
     }
     if (reached) *reached = 0.0;
     if (!(rr0 > 0.0) || !std::isfinite(rr0)) return rr0 == 0.0 ? TFDE_OK : set_error(TFDE_ENAN, "non-finite inner residual");
+    // device-side loop unless every launch is to be timed on its own
+    if (M->device_loop && !stats_timing() && maxit > 0) {
+        if ((st = build_pcg_graph(P, s))) return st;
+        if (M->pcg_exec) return inner_pcg_graph(P, theta, maxit, iters, pend, s, reached, rr0);
+    }
     int rz = D_RZ0;
     MX_TRY(cudaMemsetAsync(d + rz, 0, sizeof(double), s));
     if ((st = fast_precond_cg(P, pbuf(0), nullptr, d + rz, nullptr, nullptr, s))) return st;   // p_0 = z
@@ -412,6 +424,127 @@ int inner_pcg(const tfde_problem* P, double theta, int maxit, int* iters, PcgPen
         pend->alpha[j] = d + kAlphaSlot + (j0 + j) % kPRing;
     }
     *iters = k;
+    return check_err(P, s);
+}
+
+// Slots of the device-side loop: <r, z> of the last preconditioner
+// application and the stop threshold theta^2 ||r_0||^2.
+enum { D_RZN = 4, D_THR = 5 };
+
+// The inner PCG's iterations as one graph: a while node whose body runs
+// kPRing iterations (the ring of search directions makes every pointer of a
+// body's kernels fixed), each iteration head -> operator (3 split launches,
+// <p, Ap> fused) -> residual update -> stop test (sets the loop condition
+// and the device flag that turns the rest of the body into no-ops) ->
+// preconditioner and direction update (6 split launches, <r, z> and beta
+// fused), the body's full window of directions folded into F_X before the
+// last direction update.  Built on the first call; a failure to build it
+// leaves the host-driven loop in use.
+int build_pcg_graph(const tfde_problem* P, cudaStream_t s) {
+    MixedState* M = mixed(P);
+    if (M->pcg_exec || M->pcg_graph_failed) return TFDE_OK;
+    const size_t N = P->N;
+    if (!M->pring) MX_TRY(cudaMalloc((void**)&M->pring, (size_t)kPRing * N * sizeof(float)));
+    if (!M->pcg_ctl) {
+        MX_TRY(cudaMalloc((void**)&M->pcg_ctl, 4 * sizeof(int)));
+        MX_TRY(cudaMallocHost((void**)&M->pcg_ctl_host, 4 * sizeof(int)));
+    }
+    if (int st = ensure_pairs(P, s)) return st;
+    if (int st = tc::set_attrs()) return st;   // kernel attributes are set outside the capture
+    float* q = M->f[F_Q];
+    float* r = M->f[F_R];
+    double* d = M->dsc;
+    int* ctl = M->pcg_ctl;
+    auto pbuf = [&](int j) { return M->pring + (size_t)(j % kPRing) * N; };
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+    cudaGraphConditionalHandle h{};
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    if (ok) ok = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+    }
+    if (ok) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+             cudaSuccess;
+        if (ok) {
+            stats_set_capturing(true);
+            int st = TFDE_OK;
+            const float* ps[kPRing];
+            const double* as[kPRing];
+            for (int u = 0; u < kPRing; ++u) {
+                ps[u] = pbuf(u);
+                as[u] = d + kAlphaSlot + u;
+            }
+            for (int u = 0; u < kPRing && !st; ++u) {
+                launch_pcg_head(d, D_RZ0, D_RZN, D_PQ, D_RR, ctl, s);
+                st = fast_matvec(P, TFDE_OP_A, q, s, -1, pbuf(u), d + D_PQ, ctl + 1);
+                if (st) break;
+                launch_cg_update_r32(N, d + D_RZ0, d + D_PQ, q, r, M->hi[PL_R], nullptr, d + D_RR, d + kAlphaSlot + u,
+                                     s, ctl + 1);
+                launch_pcg_cond(h, d + D_RR, d + D_THR, ctl, s);
+                if (u == kPRing - 1) launch_pcg_fold_dev(N, ps, as, M->f[F_X], ctl, s);
+                st = fast_precond_cg(P, pbuf(u + 1), pbuf(u), d + D_RZN, d + D_RZN, d + D_RZ0, s, ctl + 1);
+            }
+            stats_set_capturing(false);
+            cudaGraph_t out = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(s, &out);
+            ok = st == TFDE_OK && e == cudaSuccess;
+        }
+    }
+    if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();   // the host loop stays in use; clear the capture's error state
+        if (g) cudaGraphDestroy(g);
+        M->pcg_graph_failed = true;
+        set_error(TFDE_OK, "");
+        return TFDE_OK;
+    }
+    M->pcg_graph = g;
+    M->pcg_exec = ex;
+    return TFDE_OK;
+}
+
+// inner_pcg (below) with its iterations in the device-side loop: one graph
+// launch and one host read per sweep (iterations done and <r, r>).
+int inner_pcg_graph(const tfde_problem* P, double theta, int maxit, int* iters, PcgPending* pend, cudaStream_t s,
+                    double* reached, double rr0) {
+    MixedState* M = mixed(P);
+    const size_t N = P->N;
+    double* d = M->dsc;
+    auto pbuf = [&](int j) { return M->pring + (size_t)(j % kPRing) * N; };
+    *pend = PcgPending();
+    if (reached) *reached = 0.0;
+    launch_pcg_init(d, D_RZN, D_THR, theta * theta * rr0, M->pcg_ctl, maxit, s);
+    int st = fast_precond_cg(P, pbuf(0), nullptr, d + D_RZN, nullptr, nullptr, s);   // p_0 = z_0
+    if (st) return st;
+    MX_TRY(cudaGraphLaunch(M->pcg_exec, s));
+    MX_TRY(cudaMemcpyAsync(M->pcg_ctl_host, M->pcg_ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    MX_TRY(cudaMemcpyAsync(P->red_host, d + D_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MX_TRY(cudaStreamSynchronize(s));
+    const int k = M->pcg_ctl_host[0];
+    const double rr = P->red_host[0];
+    // launches of the graph: 12 per iteration of a body, the fold once per body
+    const int bodies = (k + kPRing - 1) / kPRing;
+    stats_count_launch((unsigned)(bodies * (12 * kPRing + 1)));
+    *iters = k;
+    if (!std::isfinite(rr)) return set_error(TFDE_ENAN, "non-finite inner residual");
+    if (reached) *reached = std::sqrt(rr / rr0);
+    // the directions of the last (partial or unfolded) window
+    const int j0 = kPRing * ((k - 1) / kPRing);
+    pend->cnt = k - j0;
+    pend->fold = k > kPRing;
+    for (int j = 0; j < pend->cnt; ++j) {
+        pend->p[j] = pbuf(j0 + j);
+        pend->alpha[j] = d + kAlphaSlot + (j0 + j) % kPRing;
+    }
     return check_err(P, s);
 }
 
@@ -687,6 +820,10 @@ void mixed_free(tfde_problem* P) {
     for (auto& v : M->f) cudaFree(v);
     cudaFree(M->V32);
     cudaFree(M->pring);
+    if (M->pcg_exec) cudaGraphExecDestroy(M->pcg_exec);
+    if (M->pcg_graph) cudaGraphDestroy(M->pcg_graph);
+    cudaFree(M->pcg_ctl);
+    if (M->pcg_ctl_host) cudaFreeHost(M->pcg_ctl_host);
     cudaFree(M->pair_d);
     cudaFree(M->pair_gstart);
     cudaFree(M->gm);
@@ -911,6 +1048,12 @@ int mixed_pgmres(tfde_problem* P, const double* b, double* x, int restart, doubl
     loc.ms = (float)std::chrono::duration<double, std::milli>(clk::now() - t0).count();
     if (info) *info = loc;
     return status;
+}
+
+int mixed_set_device_loop(tfde_problem* P, int enable) {
+    MixedState* M = mixed(P);
+    if (M) M->device_loop = enable != 0;
+    return TFDE_OK;
 }
 
 }  // namespace tfde

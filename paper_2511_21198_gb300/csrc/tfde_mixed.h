@@ -31,11 +31,19 @@ void launch_scale64to32_hi(size_t N, const double* r64, double sc, float* r32, _
 // r -= alpha q; split r (rl null: the hi plane alone); *rr += r.r  (the
 // solution is left to the combination)
 void launch_cg_update_r32(size_t N, const double* num, const double* den, const float* q, float* r,
-                          __nv_bfloat16* rh, __nv_bfloat16* rl, double* rr, double* alpha_out, cudaStream_t s);
+                          __nv_bfloat16* rh, __nv_bfloat16* rl, double* rr, double* alpha_out, cudaStream_t s,
+                          const int* skip = nullptr);
 // d = (fold ? x32 : 0) + sum_j alpha_j p_j ; with c64: c64 = sc d, x64 += c64 ;
 // without: x64 += sc d ; with acc32 (and no x64): acc32 = d (the fold itself)
 void launch_pcg_combine(size_t N, const PcgPending& pend, const float* x32, double sc, double* c64, double* x64,
                         float* acc32, cudaStream_t s);
+// device-side inner PCG loop (see pcg_cond_kernel): iteration head, stop
+// test and loop condition, initial control words, fold of a full window
+void launch_pcg_head(double* d, int rz, int rzn, int pq, int rr, const int* ctl, cudaStream_t s);
+void launch_pcg_cond(cudaGraphConditionalHandle h, const double* rr, const double* thr, int* ctl, cudaStream_t s);
+void launch_pcg_init(double* d, int rzn, int thr_slot, double thr, int* ctl, int maxit, cudaStream_t s);
+void launch_pcg_fold_dev(size_t N, const float* const* p, const double* const* alpha, float* x32, const int* ctl,
+                         cudaStream_t s);
 // c64 = sc * d32; x64 += c64
 void launch_widen_add32(size_t N, double sc, const float* d, double* c, double* x, cudaStream_t s);
 // beta = *num / *den on the device; p = z + beta p; split p
@@ -115,6 +123,14 @@ struct MixedState {
     // inner PCG: the search directions of the current window (the solution is
     // combined from them once per sweep, see inner_pcg)
     float* pring = nullptr;   // kPRing vectors
+    // the inner PCG as one graph launch per sweep: a device-side while loop
+    // whose body runs kPRing iterations (ctl: iterations, done, maxit)
+    int* pcg_ctl = nullptr;
+    int* pcg_ctl_host = nullptr;
+    cudaGraph_t pcg_graph = nullptr;
+    cudaGraphExec_t pcg_exec = nullptr;
+    bool pcg_graph_failed = false;
+    bool device_loop = true;   // tfde_set_device_loop
     // the operator's first four split passes as two grouped launches (device
     // descriptors, tile offsets, totals and algorithmic work per launch)
     tc::Params* pair_d = nullptr;

@@ -31,9 +31,17 @@ void harvest(bool all) {
 }
 }  // namespace
 
-void stats_count_launch(unsigned n) { g_stats.kernel_launches += n; }
+bool g_capturing = false;
+
+void stats_count_launch(unsigned n) {
+    if (!g_capturing) g_stats.kernel_launches += n;
+}
+
+bool stats_timing() { return g_time_tc; }
+void stats_set_capturing(bool on) { g_capturing = on; }
 
 void* stats_tc_begin(cudaStream_t s, int kind) {
+    if (g_capturing) return nullptr;
     g_stats.kernel_launches++;
     g_stats.kind[kind].launches++;
     if (!g_time_tc) return nullptr;
@@ -53,6 +61,7 @@ void* stats_tc_begin(cudaStream_t s, int kind) {
 }
 
 void stats_tc_end(void* tok, cudaStream_t s, int kind, double bytes, double flops) {
+    if (g_capturing) return;
     g_stats.kind[kind].bytes += bytes;
     g_stats.kind[kind].flops += flops;
     if (tok) cudaEventRecord(g_pending.back().b, s);

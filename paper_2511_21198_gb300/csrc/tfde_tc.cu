@@ -282,7 +282,8 @@ int launch(const Params& P0, cudaStream_t s, double bytes, double flops) {
 }
 
 int launch_grouped(const Params* groups, const long long* gstart, int ngroups, long long total, int b_kmajor,
-                   int out_mode, const int* gactive, int* err, cudaStream_t s, double bytes, double flops) {
+                   int out_mode, const int* gactive, int* err, cudaStream_t s, double bytes, double flops,
+                   const int* skip) {
     if (int st = set_attrs()) return st;
     if (out_mode == OUT_HI || out_mode == OUT_XPAY)
         return set_error(TFDE_EUNSUPPORTED, "grouped axis_gemm_kernel: split or FP32 output only");   // no such instances
@@ -298,6 +299,7 @@ int launch_grouped(const Params* groups, const long long* gstart, int ngroups, l
     p0.b_kmajor = b_kmajor;
     p0.out_mode = out_mode;
     p0.err = err;
+    p0.skip = skip;
     long long grid = total < num_sms() ? total : num_sms();
     void* tok = stats_tc_begin(s, TFDE_KIND_SPLIT);
     launch_instance<true>(b_kmajor, out_mode, (unsigned)grid, s, p0, groups, gstart, ngroups, gactive);

@@ -10,6 +10,8 @@ namespace tfde {
 namespace tc {
 
 int num_sms();
+// Set the shared-memory attributes of every kernel instance (once).
+int set_attrs();
 // BF16 tiled tensor map (rank <= 5): dims / box innermost first, strides in
 // bytes for dimensions 1.. (rank - 1 entries).
 int encode_map(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
@@ -31,7 +33,8 @@ int launch(const Params& P, cudaStream_t s, double bytes, double flops);
 // Bounded-wait self-test (tfde_selftest_wait).
 int wait_selftest(long long limit_ns, int* tmem_freed, cudaStream_t s);
 int launch_grouped(const Params* groups, const long long* gstart, int ngroups, long long total, int b_kmajor,
-                   int out_mode, const int* gactive, int* err, cudaStream_t s, double bytes, double flops);
+                   int out_mode, const int* gactive, int* err, cudaStream_t s, double bytes, double flops,
+                   const int* skip = nullptr);
 
 }  // namespace tc
 }  // namespace tfde

@@ -120,6 +120,7 @@ struct Params {
     const double* xp_num;   // OUT_XPAY: beta = *xp_num / *xp_den
     const double* xp_den;
     const float* xp_old;    // OUT_XPAY: the old p (null: out_f32 itself, updated in place)
+    const int* skip;        // optional: a launch that finds *skip != 0 does no work (device-side loops)
     int* err;
 };
 
@@ -279,7 +280,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
-    const long long total = p0.ntiles * p0.mhalves;
+    // a device-side loop that has converged turns the launch into a no-op
+    const long long total = (p0.skip && *reinterpret_cast<const volatile int*>(p0.skip)) ? 0 : p0.ntiles * p0.mhalves;
     int* const err = p0.err;
     constexpr int b_kmajor = KM;
 

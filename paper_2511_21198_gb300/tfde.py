@@ -65,7 +65,7 @@ EXPORTS = ["tfde_assemble", "tfde_destroy", "tfde_matvec", "tfde_precond", "tfde
            "tfde_stats_reset", "tfde_stats_get", "tfde_mass_apply_noalloc", "tfde_batch_create", "tfde_batch_destroy",
            "tfde_batch_count", "tfde_batch_set_guess_order", "tfde_batch_cn_advance", "tfde_cn_advance_guess", "tfde_cnn_create", "tfde_cnn_destroy",
            "tfde_cnn_set_params", "tfde_cnn_get_params", "tfde_cnn_get_grads", "tfde_cnn_predict", "tfde_cnn_accumulate",
-           "tfde_cnn_adam_step", "tfde_selftest_wait", "tfde_last_error", "tfde_version"]
+           "tfde_cnn_adam_step", "tfde_selftest_wait", "tfde_set_device_loop", "tfde_last_error", "tfde_version"]
 
 
 def load(path: str | None = None):
@@ -112,6 +112,7 @@ def load(path: str | None = None):
         "tfde_cnn_accumulate": ([vp, vp, vp, POINTER(c_double), vp, POINTER(c_double), vp], c_int),
         "tfde_cnn_adam_step": ([vp, c_float, vp], c_int),
         "tfde_selftest_wait": ([c_longlong, POINTER(c_int), vp], c_int),
+        "tfde_set_device_loop": ([vp, c_int], c_int),
         "tfde_last_error": ([], c_char_p),
         "tfde_version": ([], c_char_p),
     }
@@ -261,6 +262,10 @@ def tfde_mass_apply_noalloc(n, x, y, stream=None) -> None:
     most 2^18 points; the first call on a device must precede stream capture)."""
     dims = (c_int * 3)(*[int(v) for v in n])
     _check(load().tfde_mass_apply_noalloc(dims, _ptr(x), _ptr(y), _stream(stream)), "tfde_mass_apply_noalloc")
+
+
+def tfde_set_device_loop(prob: int, enable: bool) -> None:
+    _check(load().tfde_set_device_loop(prob, int(bool(enable))), "tfde_set_device_loop")
 
 
 def tfde_selftest_wait(limit_ns: int, stream=None) -> tuple[int, int]:
