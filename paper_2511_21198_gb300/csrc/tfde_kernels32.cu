@@ -355,7 +355,8 @@ __global__ void multiaxpy32_kernel(long long N, int m, const float* __restrict__
     __syncthreads();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         float acc = w[i];
-        for (int j = 0; j < m; ++j) acc = fmaf(-hs[j], V[(long long)j * ldv + i], acc);
+        for (int j = 0; j < m; ++j)
+            if (hs[j] != 0.f) acc = fmaf(-hs[j], V[(long long)j * ldv + i], acc);
         w[i] = acc;
     }
 }
@@ -425,7 +426,10 @@ __global__ void pcg_head_kernel(double* d, int rz, int rzn, int pq, int rr, cons
 // after the residual update: count the iteration, take the stop test
 // <r, r> <= thr (or maxit, or a non-finite value) and set the loop condition
 __global__ void pcg_cond_kernel(cudaGraphConditionalHandle h, const double* rr, const double* thr, int* ctl) {
-    if (ctl[1]) return;   // an earlier iteration of this body ended the loop
+    if (ctl[1]) {   // an earlier iteration of this body ended the loop
+        cudaGraphSetConditional(h, 0u);
+        return;
+    }
     const int k = ctl[0] + 1;
     ctl[0] = k;
     const double v = *rr;
@@ -463,6 +467,203 @@ __global__ void pcg_fold_dev_kernel(long long N4, CombineArgs a, float4* __restr
         }
         x32[i] = d;
     }
+}
+
+// ------------------------------------------------ device-side GMRES cycle
+// Control words gctl[0] = j (Arnoldi steps done), gctl[1] = done, gctl[2] =
+// the cycle's step limit, gctl[3] = a non-finite value was met; the
+// least-squares state gs[] (FP64) at the GS_* offsets of tfde_mixed.h.  The
+// step's vector w is the fixed FP32 vector the preconditioner writes; every
+// kernel takes the step index from gctl, so one step is the body of the loop.
+
+// the first m = j + 1 inner products <V_i, w>, 8 basis vectors per sweep of w
+__global__ __launch_bounds__(kT) void gm_multidot_kernel(long long N, const float* __restrict__ V, long long ldv,
+                                                         const float* __restrict__ w, double* __restrict__ part,
+                                                         const int* gctl) {
+    if (gctl[1]) return;
+    const int m = gctl[0] + 1;
+    long long lo, hi;
+    chunk(N, lo, hi);
+    for (int m0 = 0; m0 < m; m0 += 8) {
+        const int mc = m - m0 < 8 ? m - m0 : 8;
+        KSum k[8];
+        for (long long i = lo + threadIdx.x; i < hi; i += kT) {
+            const float wi = w[i];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < mc) k[j].add(V[(long long)(m0 + j) * ldv + i] * wi);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (j < mc) {
+                const double t = block_sum64((double)k[j].s - (double)k[j].c);
+                if (threadIdx.x == 0) part[(long long)(m0 + j) * gridDim.x + blockIdx.x] = t;
+            }
+        }
+    }
+}
+
+// out[j] = sum of the block partials of result j, j < m (m = mfix, or the
+// step's j + 1 when mfix == 0); one warp per result in a fixed order
+__global__ void gm_reduce_kernel(const double* __restrict__ part, int nblk, double* __restrict__ out, int mfix,
+                                 const int* gctl) {
+    if (gctl[1]) return;
+    const int m = mfix > 0 ? mfix : gctl[0] + 1;
+    const int j = blockIdx.x;
+    if (j >= m) return;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) acc += part[(long long)j * nblk + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) out[j] = acc;
+}
+
+// w -= sum_{i <= j} h[i] V_i
+__global__ void gm_multiaxpy_kernel(long long N, const float* __restrict__ V, long long ldv,
+                                    const double* __restrict__ h, float* __restrict__ w, const int* gctl) {
+    if (gctl[1]) return;
+    const int m = gctl[0] + 1;
+    __shared__ float hs[128];
+    for (int j = threadIdx.x; j < m; j += blockDim.x) hs[j] = (float)h[j];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        float acc = w[i];
+        for (int j = 0; j < m; ++j) acc = fmaf(-hs[j], V[(long long)j * ldv + i], acc);
+        w[i] = acc;
+    }
+}
+
+__global__ __launch_bounds__(kT) void gm_dot_kernel(long long N, const float* __restrict__ a, double* __restrict__ part,
+                                                    const int* gctl) {
+    if (gctl[1]) return;
+    long long lo, hi;
+    chunk(N, lo, hi);
+    KSum k;
+    for (long long i = lo + threadIdx.x; i < hi; i += kT) k.add(a[i] * a[i]);
+    const double t = block_sum64((double)k.s - (double)k.c);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// Column j of the Hessenberg matrix (h + h2 from the two Gram-Schmidt
+// passes, ||w|| below the diagonal) rotated by the previous Givens
+// rotations, the new rotation, the residual estimate |g_{j+1}| (Sec. 3.2 left
+// preconditioned GMRES), the stop test and the loop condition.
+__global__ void gm_givens_kernel(double* gs, const double* h, const double* h2, const double* ww, int* gctl,
+                                 cudaGraphConditionalHandle hc) {
+    if (gctl[1]) {   // the loop ends whenever its condition kernel runs on a finished cycle
+        cudaGraphSetConditional(hc, 0u);
+        return;
+    }
+    const int j = gctl[0];
+    double* g = gs + GS_G;
+    double* cs = gs + GS_CS;
+    double* sn = gs + GS_SN;
+    double* R = gs + GS_R + (long long)j * GS_LD;   // column j, entries 0..j+1
+    for (int i = 0; i <= j; ++i) R[i] = h[i] + h2[i];
+    const double hn = sqrt(*ww);
+    R[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * R[i] + sn[i] * R[i + 1];
+        R[i + 1] = -sn[i] * R[i] + cs[i] * R[i + 1];
+        R[i] = t;
+    }
+    const double den = hypot(R[j], R[j + 1]);
+    cs[j] = den > 0.0 ? R[j] / den : 1.0;
+    sn[j] = den > 0.0 ? R[j + 1] / den : 0.0;
+    R[j] = den;
+    R[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    const double est = fabs(g[j + 1]);
+    gs[GS_EST] = est;
+    gs[GS_INV] = 1.0 / hn;
+    const int k = j + 1;
+    gctl[0] = k;
+    int done = (est <= gs[GS_THR] || hn == 0.0 || k >= gctl[2]) ? 1 : 0;
+    if (!isfinite(hn) || !isfinite(est)) {
+        gctl[3] = 1;
+        done = 1;
+    }
+    gctl[1] = done;
+    cudaGraphSetConditional(hc, done ? 0u : 1u);
+}
+
+// V_j (j = the steps done) = w / ||w|| and its split planes, the next
+// operator input
+__global__ void gm_scale_basis_kernel(long long N, const float* __restrict__ w, float* V, long long ldv,
+                                      const double* gs, const int* gctl, __nv_bfloat16* __restrict__ h,
+                                      __nv_bfloat16* __restrict__ l) {
+    if (gctl[1]) return;
+    const float sc = (float)gs[GS_INV];
+    float* out = V + (long long)gctl[0] * ldv;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const float v = w[i] * sc;
+        out[i] = v;
+        split(v, h[i], l[i]);
+    }
+}
+
+// cycle start: beta = ||P^{-1} r|| (from the reduced dot), g = beta e_1, the
+// stop target ptheta beta, control words
+__global__ void gm_start_kernel(double* gs, const double* ww, int* gctl, int maxsteps, double ptheta) {
+    const double beta = sqrt(*ww);
+    gs[GS_BETA] = beta;
+    gs[GS_EST] = beta;
+    gs[GS_INV] = 1.0 / beta;
+    gs[GS_THR] = ptheta * beta;
+    for (int i = 0; i <= GS_MAXM; ++i) gs[GS_G + i] = 0.0;
+    gs[GS_G] = beta;
+    gctl[0] = 0;
+    gctl[1] = (!(beta > 0.0) || !isfinite(beta)) ? 1 : 0;
+    gctl[2] = maxsteps;
+    gctl[3] = isfinite(beta) ? 0 : 1;
+}
+
+// -y (the least-squares solution R y = g over the steps done), zero beyond
+__global__ void gm_solve_kernel(const double* gs, const int* gctl, double* ny, int maxm) {
+    const int k = gctl[0];
+    const double* g = gs + GS_G;
+    const double* R = gs + GS_R;
+    double y[GS_MAXM];
+    for (int i = k - 1; i >= 0; --i) {
+        double t = g[i];
+        for (int j = i + 1; j < k; ++j) t -= R[(long long)j * GS_LD + i] * y[j];
+        y[i] = t / R[(long long)i * GS_LD + i];
+    }
+    for (int i = 0; i < maxm; ++i) ny[i] = i < k ? -y[i] : 0.0;
+}
+
+void launch_gm_step(size_t N, const float* V, float* w, double* part, int nblk, double* hbuf, double* h2buf,
+                    double* wwbuf, double* gs, int* gctl, cudaGraphConditionalHandle hc, float* Vout,
+                    __nv_bfloat16* ph, __nv_bfloat16* pl, int maxm, cudaStream_t s) {
+    stats_count_launch(9);
+    const long long n = (long long)N;
+    gm_multidot_kernel<<<nblk, kT, 0, s>>>(n, V, n, w, part, gctl);
+    gm_reduce_kernel<<<maxm, 32, 0, s>>>(part, nblk, hbuf, 0, gctl);
+    gm_multiaxpy_kernel<<<grid_for(n), kT, 0, s>>>(n, V, n, hbuf, w, gctl);
+    gm_multidot_kernel<<<nblk, kT, 0, s>>>(n, V, n, w, part, gctl);
+    gm_reduce_kernel<<<maxm, 32, 0, s>>>(part, nblk, h2buf, 0, gctl);
+    gm_multiaxpy_kernel<<<grid_for(n), kT, 0, s>>>(n, V, n, h2buf, w, gctl);
+    gm_dot_kernel<<<nblk, kT, 0, s>>>(n, w, part, gctl);
+    gm_reduce_kernel<<<1, 32, 0, s>>>(part, nblk, wwbuf, 1, gctl);
+    gm_givens_kernel<<<1, 1, 0, s>>>(gs, hbuf, h2buf, wwbuf, gctl, hc);
+    (void)Vout;
+    stats_count_launch();
+    gm_scale_basis_kernel<<<grid_for(n), kT, 0, s>>>(n, w, const_cast<float*>(V), n, gs, gctl, ph, pl);
+}
+void launch_gm_start(size_t N, const float* w, double* part, int nblk, double* wwbuf, double* gs, int* gctl,
+                     int maxsteps, double ptheta, float* V0, __nv_bfloat16* ph, __nv_bfloat16* pl, cudaStream_t s) {
+    stats_count_launch(4);
+    const long long n = (long long)N;
+    // gctl[1] = 0 here (set by the caller's reset) so that the dot and reduce run
+    gm_dot_kernel<<<nblk, kT, 0, s>>>(n, w, part, gctl);
+    gm_reduce_kernel<<<1, 32, 0, s>>>(part, nblk, wwbuf, 1, gctl);
+    gm_start_kernel<<<1, 1, 0, s>>>(gs, wwbuf, gctl, maxsteps, ptheta);
+    gm_scale_basis_kernel<<<grid_for(n), kT, 0, s>>>(n, w, V0, n, gs, gctl, ph, pl);
+}
+void launch_gm_solve(const double* gs, const int* gctl, double* ny, int maxm, cudaStream_t s) {
+    stats_count_launch();
+    gm_solve_kernel<<<1, 1, 0, s>>>(gs, gctl, ny, maxm);
 }
 
 void launch_pcg_head(double* d, int rz, int rzn, int pq, int rr, const int* ctl, cudaStream_t s) {

@@ -309,10 +309,10 @@ int fast_precond_cg(const tfde_problem* P, float* p32, const float* p_old, doubl
 }
 
 int fast_precond(const tfde_problem* P, float* z32, cudaStream_t s, const float* dot_vec = nullptr,
-                 double* dot_out = nullptr) {
+                 double* dot_out = nullptr, const int* skip = nullptr) {
     Pass ps[6];
     const int np = precond_passes(ps);
-    return run_passes(P, ps, np, z32, s, dot_vec, dot_out);
+    return run_passes(P, ps, np, z32, s, dot_vec, dot_out, skip);
 }
 
 int check_err(const tfde_problem* P, cudaStream_t s) {
@@ -601,6 +601,108 @@ int ensure_v32(const tfde_problem* P, int restart) {
     return TFDE_OK;
 }
 
+// The inner GMRES cycle's Arnoldi steps as one graph: a while node whose
+// body is one step -- operator (3 split launches, result in the split planes
+// PL_R), preconditioner into the fixed vector F_Z (6), classical Gram-Schmidt
+// with one re-orthogonalisation against V_0..V_j, ||w||, the Givens update
+// and stop test on the device (the loop condition), V_{j+1} = w / ||w|| --
+// with every count and address taken from the control words on the device.
+// Built for one restart length; a failure leaves the host-driven cycle in use.
+int build_gmres_graph(const tfde_problem* P, int restart, cudaStream_t s) {
+    MixedState* M = mixed(P);
+    if (M->gm_graph_failed || restart > GS_MAXM) return TFDE_OK;
+    if (M->gm_exec && M->gm_graph_restart == restart) return TFDE_OK;
+    if (M->gm_exec) {
+        cudaGraphExecDestroy(M->gm_exec);
+        cudaGraphDestroy(M->gm_graph);
+        M->gm_exec = nullptr;
+        M->gm_graph = nullptr;
+    }
+    if (!M->gm_state) {
+        MX_TRY(cudaMalloc((void**)&M->gm_state, GS_WORDS * sizeof(double)));
+        MX_TRY(cudaMalloc((void**)&M->gm_ctl, 4 * sizeof(int)));
+        MX_TRY(cudaMallocHost((void**)&M->gm_ctl_host, 4 * sizeof(int)));
+    }
+    if (int st = ensure_pairs(P, s)) return st;
+    if (int st = tc::set_attrs()) return st;
+    const size_t N = P->N;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+    cudaGraphConditionalHandle h{};
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    if (ok) ok = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+    }
+    if (ok) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+             cudaSuccess;
+        if (ok) {
+            stats_set_capturing(true);
+            const int* skip = M->gm_ctl + 1;
+            int st = fast_matvec(P, TFDE_OP_A, nullptr, s, PL_R, nullptr, nullptr, skip);
+            if (!st) st = fast_precond(P, M->f[F_Z], s, nullptr, nullptr, skip);
+            if (!st)
+                launch_gm_step(N, M->V32, M->f[F_Z], P->red, P->nblk, M->gm + GM_H, M->gm + GM_H2, M->gm + GM_WW,
+                               M->gm_state, M->gm_ctl, h, nullptr, M->hi[PL_P], M->lo[PL_P], restart + 1, s);
+            stats_set_capturing(false);
+            cudaGraph_t out = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(s, &out);
+            ok = st == TFDE_OK && e == cudaSuccess;
+        }
+    }
+    if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        M->gm_graph_failed = true;
+        set_error(TFDE_OK, "");
+        return TFDE_OK;
+    }
+    M->gm_graph = g;
+    M->gm_exec = ex;
+    M->gm_graph_restart = restart;
+    return TFDE_OK;
+}
+
+// inner_gmres (below) with the Arnoldi steps in the device-side loop: the
+// cycle start, one graph launch, the least-squares solve and x32 = sum y_i v_i
+// on the device, one host read per cycle (steps done, residual estimate).
+int inner_gmres_graph(const tfde_problem* P, int restart, double ptheta, int maxit, int* iters, double* est_ratio,
+                      cudaStream_t s) {
+    MixedState* M = mixed(P);
+    const size_t N = P->N;
+    *iters = 0;
+    *est_ratio = 1.0;
+    MX_TRY(cudaMemsetAsync(M->gm_ctl, 0, 4 * sizeof(int), s));
+    int st = fast_precond(P, M->f[F_Z], s);   // w = P^{-1} r
+    if (st) return st;
+    const int maxsteps = restart < maxit ? restart : maxit;
+    launch_gm_start(N, M->f[F_Z], P->red, P->nblk, M->gm + GM_WW, M->gm_state, M->gm_ctl, maxsteps, ptheta, M->V32,
+                    M->hi[PL_P], M->lo[PL_P], s);
+    MX_TRY(cudaGraphLaunch(M->gm_exec, s));
+    launch_gm_solve(M->gm_state, M->gm_ctl, M->gm + GM_Y, restart, s);
+    launch_multiaxpy32(N, restart, M->V32, N, M->gm + GM_Y, M->f[F_X], s);   // x32 = sum_i y_i v_i
+    MX_TRY(cudaMemcpyAsync(M->gm_ctl_host, M->gm_ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    MX_TRY(cudaMemcpyAsync(P->red_host, M->gm_state, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MX_TRY(cudaStreamSynchronize(s));
+    const int k = M->gm_ctl_host[0];
+    stats_count_launch((unsigned)(k > 0 ? k : 1) * 19u);   // the graph's launches, 19 per step
+    const double beta = P->red_host[GS_BETA], est = P->red_host[GS_EST];
+    if (M->gm_ctl_host[3] || !std::isfinite(beta))
+        return set_error(TFDE_ENAN, "non-finite preconditioned residual or Arnoldi vector");
+    *iters = k;
+    *est_ratio = beta > 0.0 ? est / beta : 1.0;
+    return check_err(P, s);
+}
+
 // One cycle of left-preconditioned GMRES on P^{-1} A d = P^{-1} r32 (Sec. 3.2,
 // Eq. (one_side_system)) with FP32 basis vectors, split-BF16 tensor-core
 // operator and preconditioner applications, classical Gram-Schmidt with one
@@ -612,6 +714,10 @@ int ensure_v32(const tfde_problem* P, int restart) {
 int inner_gmres(const tfde_problem* P, int restart, double ptheta, int maxit, int* iters, double* est_ratio,
                 cudaStream_t s) {
     MixedState* M = mixed(P);
+    if (M->device_loop && !stats_timing() && maxit > 0 && restart <= GS_MAXM) {
+        if (int st = build_gmres_graph(P, restart, s)) return st;
+        if (M->gm_exec) return inner_gmres_graph(P, restart, ptheta, maxit, iters, est_ratio, s);
+    }
     const size_t N = P->N;
     float* V = M->V32;
     double* g = M->gm;
@@ -821,6 +927,11 @@ void mixed_free(tfde_problem* P) {
     cudaFree(M->V32);
     cudaFree(M->pring);
     if (M->pcg_exec) cudaGraphExecDestroy(M->pcg_exec);
+    if (M->gm_exec) cudaGraphExecDestroy(M->gm_exec);
+    if (M->gm_graph) cudaGraphDestroy(M->gm_graph);
+    cudaFree(M->gm_state);
+    cudaFree(M->gm_ctl);
+    if (M->gm_ctl_host) cudaFreeHost(M->gm_ctl_host);
     if (M->pcg_graph) cudaGraphDestroy(M->pcg_graph);
     cudaFree(M->pcg_ctl);
     if (M->pcg_ctl_host) cudaFreeHost(M->pcg_ctl_host);

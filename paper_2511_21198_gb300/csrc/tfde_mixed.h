@@ -44,6 +44,23 @@ void launch_pcg_cond(cudaGraphConditionalHandle h, const double* rr, const doubl
 void launch_pcg_init(double* d, int rzn, int thr_slot, double thr, int* ctl, int maxit, cudaStream_t s);
 void launch_pcg_fold_dev(size_t N, const float* const* p, const double* const* alpha, float* x32, const int* ctl,
                          cudaStream_t s);
+// device-side GMRES cycle: least-squares state layout (FP64 words), for at
+// most GS_MAXM Arnoldi steps per cycle
+constexpr int GS_MAXM = 64;
+constexpr int GS_LD = GS_MAXM + 2;   // leading dimension of a Hessenberg column
+enum { GS_BETA = 0, GS_EST = 1, GS_INV = 2, GS_THR = 3, GS_G = 8, GS_CS = GS_G + GS_MAXM + 1,
+       GS_SN = GS_CS + GS_MAXM, GS_R = GS_SN + GS_MAXM, GS_WORDS = GS_R + GS_LD * GS_MAXM };
+// one Arnoldi step on w (the preconditioner's output): CGS2 against V_0..V_j,
+// ||w||, the Givens update and stop test (loop condition hc), V_{j+1} = w/||w||
+// with its split planes; every count and address from the control words
+void launch_gm_step(size_t N, const float* V, float* w, double* part, int nblk, double* hbuf, double* h2buf,
+                    double* wwbuf, double* gs, int* gctl, cudaGraphConditionalHandle hc, float* Vout,
+                    __nv_bfloat16* ph, __nv_bfloat16* pl, int maxm, cudaStream_t s);
+// cycle start on w = P^{-1} r: beta, g = beta e_1, V_0 = w / beta and its planes
+void launch_gm_start(size_t N, const float* w, double* part, int nblk, double* wwbuf, double* gs, int* gctl,
+                     int maxsteps, double ptheta, float* V0, __nv_bfloat16* ph, __nv_bfloat16* pl, cudaStream_t s);
+// ny = -y of the cycle's least-squares problem (zero beyond the steps done)
+void launch_gm_solve(const double* gs, const int* gctl, double* ny, int maxm, cudaStream_t s);
 // c64 = sc * d32; x64 += c64
 void launch_widen_add32(size_t N, double sc, const float* d, double* c, double* x, cudaStream_t s);
 // beta = *num / *den on the device; p = z + beta p; split p
@@ -131,6 +148,14 @@ struct MixedState {
     cudaGraphExec_t pcg_exec = nullptr;
     bool pcg_graph_failed = false;
     bool device_loop = true;   // tfde_set_device_loop
+    // the inner GMRES cycle's Arnoldi steps as one graph launch (while node)
+    double* gm_state = nullptr;   // GS_WORDS
+    int* gm_ctl = nullptr;        // 4 control words
+    int* gm_ctl_host = nullptr;
+    cudaGraph_t gm_graph = nullptr;
+    cudaGraphExec_t gm_exec = nullptr;
+    int gm_graph_restart = 0;
+    bool gm_graph_failed = false;
     // the operator's first four split passes as two grouped launches (device
     // descriptors, tile offsets, totals and algorithmic work per launch)
     tc::Params* pair_d = nullptr;

@@ -440,3 +440,33 @@ def test_device_loop_matches_host_loop(T):
     finally:
         T.tfde_destroy(ha)
         T.tfde_destroy(hb)
+
+
+@pytest.mark.parametrize("restart", [20, 4])
+def test_gmres_device_loop_matches_host_loop(T, restart):
+    """The inner GMRES cycle's device-side loop (Arnoldi steps, Givens
+    rotations, stop test and the small triangular solve on the device; Sec.
+    3.2) against the host-driven cycle: the same steps and solution, including
+    restarts (restart 4) and a tight tolerance."""
+    n = (32, 24, 48)
+    d, kp, km, dt = (0.3, 0.6, 0.8), (1.0,) * 3, (0.5,) * 3, 0.02
+    prm = T.make_params(n, d, kp, km, dt)
+    ha = T.tfde_assemble(prm, T.TFDE_MIXED)
+    hb = T.tfde_assemble(prm, T.TFDE_MIXED)
+    try:
+        T.tfde_set_device_loop(hb, False)
+        op = o.Problem(n=n, delta=d, kp=kp, km=km, dt=dt)
+        u0 = inp.smoothed_uniform(op.shape, 2)
+        b = o.rhs(op, u0, None)
+        xa, xb = to_dev(u0), to_dev(u0)
+        ia = T.tfde_pgmres(ha, to_dev(b), xa, restart, 1e-12, 4000)
+        ib = T.tfde_pgmres(hb, to_dev(b), xb, restart, 1e-12, 4000)
+        assert ia.iters == ib.iters and ia.restarts == ib.restarts and ia.relres <= 1e-12
+        assert relerr(to_host(xa), to_host(xb)) < 1e-13
+        tau = o.build_tau(op)
+        xo, _ = o.gmres_left(lambda v: o.apply_A(op, v), lambda r: o.apply_Pinv(tau, r), b, u0, 1e-14, 4000,
+                             restart=20, criterion="true")
+        assert relerr(to_host(xa), xo) < 1e-10
+    finally:
+        T.tfde_destroy(ha)
+        T.tfde_destroy(hb)
