@@ -59,6 +59,7 @@ def parse_args(argv=None):
                     help="skip the n = 256 run with one warm-up step and steps m = 2..20 (T = 1)")
     ap.add_argument("--no-parity", action="store_true",
                     help="skip the full-size tight-residual comparison of the mixed and FP64 GPU paths")
+    ap.add_argument("--no-spectra", action="store_true", help="skip the Lanczos spectra of the preconditioned systems")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -457,6 +458,11 @@ def run_ours(args):
     if args.c2_steps > 0 and args.n is None:
         c2 = run_c2(T, args.c2_steps, args.guess_order, dev, stream, check_oracle=rank == 0)
 
+    # ---- spectra of the preconditioned systems at the benchmark sizes (Sec. 3)
+    spectra = None
+    if not args.no_spectra and args.n is None:
+        spectra = run_spectra(T, dev, stream)
+
     # ---- batched workload: uneven problems, lock-step batched solve vs a loop
     batched = None
     if args.batch_count > 0 and args.batch_steps > 0:
@@ -540,7 +546,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "host_gap": host_gap,
             "clocks": clocks, "fp64_path": fp64, "c3_protocol": c3, "parity_n256": parity,
-            "c2_nonsymmetric_n128": c2, "batched": batched, "warm_start": warm,
+            "c2_nonsymmetric_n128": c2, "batched": batched, "warm_start": warm, "spectra": spectra,
             "iters_per_step": iters / args.steps, "refine_sweeps_per_step": sweeps / args.steps,
             "max_relres": relres, "max_rel_err_vs_exact": err,
         }
@@ -548,6 +554,25 @@ def run_ours(args):
     if on:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_spectra(T, dev, stream, steps=40):
+    """Lanczos estimates (tfde_spectrum, FP64) of the preconditioned
+    systems' spectra on the n = 256 symmetric and n = 128 non-symmetric
+    workloads, beside the paper's grid-independent bounds."""
+    import torch
+    out = {"lanczos_steps": steps}
+    for key in ("n256_sym_exp", "n128_nonsym"):
+        W = inp.WORKLOADS[key]
+        n = W["n"]
+        v0 = torch.from_numpy(inp.uniform_vector((n, n, n), 10)).to(dev)
+        t0 = time.perf_counter()
+        s = T.tfde_spectrum(T.make_params((n, n, n), W["delta"], W["kp"], W["km"], 1.0 / W["M"]), steps, v0, stream)
+        out[key] = {"sym_min": s.sym_min, "sym_max": s.sym_max, "paper_sym_interval": [0.5, 1.5],
+                    "skew_rho": s.skew_rho, "paper_varsigma": s.varsigma, "paper_omega": s.omega,
+                    "omega_from_estimates": s.omega_est, "seconds": time.perf_counter() - t0}
+        del v0
+    return out
 
 
 def full_size_parity(T, params, u_prev, t_half, dev, stream):

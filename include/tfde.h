@@ -229,6 +229,36 @@ int tfde_set_guess_order(tfde_problem* prob, int order);
  */
 int tfde_set_device_loop(tfde_problem* prob, int enable);
 
+/*
+ * tfde_spectrum -- spectral estimates of the preconditioned system of one
+ * problem (Sec. 3) at sizes far beyond a dense eigensolve, in FP64 on the FFT
+ * passes.  With H(A) = (A + A^T)/2 and S(A) = (A - A^T)/2 (Sec. 2 notation):
+ *   sym_min, sym_max  extreme Ritz values of P^{-1/2} H(A) P^{-1/2} after
+ *                     `steps` Lanczos steps from v0 (Theorem
+ *                     CG_bounded_sprctrum, Lemma prop:eigen_S: the spectrum
+ *                     lies in (1/2, 3/2));
+ *   skew_rho          largest Ritz value of the spectral radius of
+ *                     P^{-1/2} S(A) P^{-1/2} (Lanczos on its negated square;
+ *                     0 when k_+ = k_- on every axis), against
+ *   varsigma          the bound of Lemma eigen_Skew,
+ *                     3/2 max_a tan(delta_a pi / 2) |k_{a,+} - k_{a,-}| / (k_{a,+} + k_{a,-});
+ *   omega             the GMRES rate sqrt((2 + 4 varsigma^2) / (3 + 4 varsigma^2))
+ *                     of Theorem theorem_main, and
+ *   omega_est         the same bound from the estimates:
+ *                     sqrt(1 - sym_min^2 / (sym_min sym_max + skew_rho^2)).
+ *   Ritz values lie inside the spectrum: sym_min / sym_max approach the
+ *   extremes from inside, skew_rho the radius from below.
+ *   params: as tfde_assemble (every n_a <= 2048).  steps: 2..500.  v0: device
+ *   grid function, the start vector (not zero).  out: host.  Errors:
+ *   TFDE_EINVAL, TFDE_EUNSUPPORTED, TFDE_ENOMEM, TFDE_ENAN, TFDE_ECUDA.
+ *   Allocates two FP64 problems for the call.  Synchronises `stream`.
+ */
+typedef struct {
+    int steps;
+    double sym_min, sym_max, skew_rho, varsigma, omega, omega_est;
+} tfde_spectrum_info;
+int tfde_spectrum(const tfde_params* params, int steps, const double* v0, tfde_spectrum_info* out, void* stream);
+
 /* ------------------------------------------------------------------ batches */
 typedef struct tfde_batch tfde_batch;
 

@@ -33,6 +33,7 @@ int mixed_apply_Pinv(const tfde_problem*, const double*, double*, cudaStream_t);
 int mixed_pcg(tfde_problem*, const double*, double*, double, int, tfde_info*, cudaStream_t, bool);
 int mixed_pgmres(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t, bool);
 int mixed_set_device_loop(tfde_problem*, int);
+int spectrum(const tfde_params*, int, const double*, tfde_spectrum_info*, cudaStream_t);
 namespace tc {
 int wait_selftest(long long limit_ns, int* tmem_freed, cudaStream_t s);
 }
@@ -295,6 +296,14 @@ int tfde_stats_reset(int time_tc) { return stats_reset(time_tc); }
 int tfde_stats_get(tfde_stats* out) {
     if (!out) return set_error(TFDE_EINVAL, "NULL stats");
     return stats_get(out);
+}
+
+int tfde_spectrum(const tfde_params* params, int steps, const double* v0, tfde_spectrum_info* out, void* stream) {
+    if (!params || !out) return set_error(TFDE_EINVAL, "NULL params or output");
+    if (steps < 2 || steps > 500) return set_error(TFDE_EINVAL, "steps must lie in 2..500");
+    if (int st = check_dev(v0, "v0")) return st;
+    if (int st = pre_call()) return st;
+    return spectrum(params, steps, v0, out, (cudaStream_t)stream);
 }
 
 int tfde_set_device_loop(tfde_problem* prob, int enable) {

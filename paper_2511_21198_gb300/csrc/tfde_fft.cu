@@ -105,6 +105,7 @@ struct Pass {
     double dst_scale;   // sqrt(2 / (n + 1))
     const double* lam;  // MODE_DST2: [mass x | y | z | tau x | y | z]
     double c0, c1, c2;  // MODE_DST2: eta_a (k+ + k-)
+    int half_power;     // MODE_DST2: divide by Lambda^{1/2} instead of Lambda (P^{-1/2})
 };
 
 __device__ __forceinline__ long long line_offset(const Pass& p, long long l) {
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(NT) fft_pass_kernel(const Pass p) {
                 const int i = (int)(l % p.n1), jy = (int)(l / p.n1);
                 const double lam = mz[k] * my[jy] * mx[i] + p.c0 * mz[k] * my[jy] * tx[i] +
                                    p.c1 * mz[k] * ty[jy] * mx[i] + p.c2 * tz[k] * my[jy] * mx[i];
-                const R u = (R)((double)t / lam);
+                const R u = (R)((double)t / (p.half_power ? sqrt(lam) : lam));
                 w.x = ph.x * u;
                 w.y = ph.y * u;
             }
@@ -587,7 +588,8 @@ int toeplitz_pass(const tfde_problem* P, int axis, const Table& T, double alpha,
 }
 
 template <typename R>
-int dst_pass(const tfde_problem* P, int axis, const R* in, R* out, bool lambda_pair, cudaStream_t s) {
+int dst_pass(const tfde_problem* P, int axis, const R* in, R* out, bool lambda_pair, cudaStream_t s,
+             bool half_power = false) {
     const State* F = static_cast<const State*>(P->fft);
     Pass p = base_pass(P, axis, sizeof(R) == 8);
     p.spec = sizeof(R) == 8 ? (const void*)F->chirp[axis].d : (const void*)F->chirp[axis].f;
@@ -598,6 +600,7 @@ int dst_pass(const tfde_problem* P, int axis, const R* in, R* out, bool lambda_p
         p.c0 = P->csum[0];
         p.c1 = P->csum[1];
         p.c2 = P->csum[2];
+        p.half_power = half_power ? 1 : 0;
         return launch_pass<R, MODE_DST2>(p, s);
     }
     return launch_pass<R, MODE_DST>(p, s);
@@ -630,6 +633,15 @@ int apply_Pinv(const tfde_problem* P, const R* r, R* z, R* t1, R* t2, cudaStream
     if ((st = dst_pass<R>(P, 2, t2, t1, true, s))) return st;   // S_z Lambda^{-1} S_z
     if ((st = dst_pass<R>(P, 1, t1, t2, false, s))) return st;
     return dst_pass<R>(P, 0, t2, z, false, s);
+}
+
+int apply_Pinv_half(const tfde_problem* P, const double* r, double* z, double* t1, double* t2, cudaStream_t s) {
+    int st;
+    if ((st = dst_pass<double>(P, 0, r, t1, false, s))) return st;
+    if ((st = dst_pass<double>(P, 1, t1, t2, false, s))) return st;
+    if ((st = dst_pass<double>(P, 2, t2, t1, true, s, true))) return st;   // S_z Lambda^{-1/2} S_z
+    if ((st = dst_pass<double>(P, 1, t1, t2, false, s))) return st;
+    return dst_pass<double>(P, 0, t2, z, false, s);
 }
 
 template int apply_A<double>(const tfde_problem*, int, const double*, double*, double*, double*, double*, double*,

@@ -42,5 +42,9 @@ int apply_A(const tfde_problem* P, int op, const R* x, R* y, R* a, R* w, R* c, R
 template <typename R>
 int apply_Pinv(const tfde_problem* P, const R* r, R* z, R* t1, R* t2, cudaStream_t s);
 
+// z = P^{-1/2} r = S_N Lambda^{-1/2} S_N r (FP64): the symmetric square root
+// of the preconditioner's inverse, from the same diagonalisation.
+int apply_Pinv_half(const tfde_problem* P, const double* r, double* z, double* t1, double* t2, cudaStream_t s);
+
 }  // namespace fft
 }  // namespace tfde

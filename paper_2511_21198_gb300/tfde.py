@@ -45,6 +45,11 @@ TFDE_KIND_SPLIT, TFDE_KIND_EXACT, TFDE_KIND_CONV, TFDE_KIND_FFT = 0, 1, 2, 3
 TFDE_NKINDS = 4
 
 
+class tfde_spectrum_info(Structure):
+    _fields_ = [("steps", c_int), ("sym_min", c_double), ("sym_max", c_double), ("skew_rho", c_double),
+                ("varsigma", c_double), ("omega", c_double), ("omega_est", c_double)]
+
+
 class tfde_stats(Structure):
     _fields_ = [("kernel_launches", ctypes.c_ulonglong), ("kind", tfde_kernel_stats * 4)]
 
@@ -65,7 +70,7 @@ EXPORTS = ["tfde_assemble", "tfde_destroy", "tfde_matvec", "tfde_precond", "tfde
            "tfde_stats_reset", "tfde_stats_get", "tfde_mass_apply_noalloc", "tfde_batch_create", "tfde_batch_destroy",
            "tfde_batch_count", "tfde_batch_set_guess_order", "tfde_batch_cn_advance", "tfde_cn_advance_guess", "tfde_cnn_create", "tfde_cnn_destroy",
            "tfde_cnn_set_params", "tfde_cnn_get_params", "tfde_cnn_get_grads", "tfde_cnn_predict", "tfde_cnn_accumulate",
-           "tfde_cnn_adam_step", "tfde_selftest_wait", "tfde_set_device_loop", "tfde_last_error", "tfde_version"]
+           "tfde_cnn_adam_step", "tfde_selftest_wait", "tfde_set_device_loop", "tfde_spectrum", "tfde_last_error", "tfde_version"]
 
 
 def load(path: str | None = None):
@@ -113,6 +118,7 @@ def load(path: str | None = None):
         "tfde_cnn_adam_step": ([vp, c_float, vp], c_int),
         "tfde_selftest_wait": ([c_longlong, POINTER(c_int), vp], c_int),
         "tfde_set_device_loop": ([vp, c_int], c_int),
+        "tfde_spectrum": ([POINTER(tfde_params), c_int, vp, POINTER(tfde_spectrum_info), vp], c_int),
         "tfde_last_error": ([], c_char_p),
         "tfde_version": ([], c_char_p),
     }
@@ -262,6 +268,12 @@ def tfde_mass_apply_noalloc(n, x, y, stream=None) -> None:
     most 2^18 points; the first call on a device must precede stream capture)."""
     dims = (c_int * 3)(*[int(v) for v in n])
     _check(load().tfde_mass_apply_noalloc(dims, _ptr(x), _ptr(y), _stream(stream)), "tfde_mass_apply_noalloc")
+
+
+def tfde_spectrum(params: tfde_params, steps: int, v0, stream=None) -> tfde_spectrum_info:
+    out = tfde_spectrum_info()
+    _check(load().tfde_spectrum(byref(params), int(steps), _ptr(v0), byref(out), _stream(stream)), "tfde_spectrum")
+    return out
 
 
 def tfde_set_device_loop(prob: int, enable: bool) -> None:
