@@ -58,9 +58,14 @@ typedef enum {
     TFDE_MIXED = 1
 } tfde_precision;
 
-/* One problem (Sec. 1 and Sec. 2).  Axis a = 0, 1, 2 is x, y, z. */
+/* One problem (Sec. 1 and Sec. 2).  Axis a = 0, 1, 2 is x, y, z.
+ * n[2] = 0 selects the two-dimensional problem of Sec. 4, Example 1 on
+ * (lo_0, hi_0) x (lo_1, hi_1): the system of Eq. (linear_sys) without the
+ * third axis (A = A_2 (x) A_1 + eta_a A_2 (x) B_1 + eta_b B_2 (x) A_1); the
+ * third entries of delta, kp, km, lo, hi are then ignored, grid functions hold
+ * n1*n2 values, and only TFDE_FP64 is available. */
 typedef struct {
-    int n[3];          /* interior grid points per axis, n_a >= 1; h_a = (hi_a - lo_a)/(n_a + 1) */
+    int n[3];          /* interior grid points per axis, n_a >= 1 (n[2] = 0: 2-D); h_a = (hi_a - lo_a)/(n_a + 1) */
     double lo[3];      /* Omega = prod_a (lo_a, hi_a), lo_a < hi_a                  */
     double hi[3];
     double delta[3];   /* alpha, beta, gamma in (0, 1); the derivative order is 2 - delta */
@@ -372,6 +377,8 @@ int tfde_cnn_adam_step(tfde_cnn* net, float lr, void* stream);
  *   P(x) = x^2 (1-x)^2,
  *   S_d(x) = sum_{k=0}^2 (-1)^{2-k} C(2,k) Gamma(5-k)/Gamma(3-k+d) [k_+ x^{2-k+d} + k_- (1-x)^{2-k+d}].
  *   For u = phi(t) P P P:  cP = phi'(t), cS = -phi(t).  Integrals are exact.
+ *   2-D problems (Example 1): the same without the third factor,
+ *   f = cP P(x)P(y) + cS [S_a(x)P(y) + P(x)S_b(y)] (u = 4 e^t P P: cP = 4e^t, cS = -4e^t).
  *   Requires lo = 0, hi = 1 on every axis (else TFDE_EINVAL).  F: device output.
  */
 int tfde_source_example2(const tfde_problem* prob, double cP, double cS, double* F, void* stream);

@@ -206,6 +206,11 @@ class Problem:
     dt: float
     lo: tuple = (0.0, 0.0, 0.0)
     hi: tuple = (1.0, 1.0, 1.0)
+    # dim = 2: the two-dimensional problem of Sec. 4, Example 1 (n[2] must be
+    # 1): the system of Eq. (linear_sys) without the third axis, i.e. its
+    # Kronecker form with the third mass factor the 1 x 1 identity and no
+    # third stiffness term
+    dim: int = 3
     # derived
     h: tuple = field(init=False)
     q: list = field(init=False)
@@ -222,6 +227,12 @@ class Problem:
         self.B = [stiffness_B(self.T[a], self.kp[a], self.km[a]) for a in range(3)]
         self.M = [mass_A(self.n[a]) for a in range(3)]
         self.eta = tuple(eta(self.delta[a], self.h[a], self.dt) for a in range(3))
+        if self.dim == 2:
+            if self.n[2] != 1:
+                raise ValueError("a 2-D problem has n[2] = 1")
+            self.M[2] = np.ones((1, 1))
+            self.B[2] = np.zeros((1, 1))
+            self.eta = (self.eta[0], self.eta[1], 0.0)
 
     @property
     def shape(self):
@@ -230,7 +241,7 @@ class Problem:
     @property
     def symmetric(self) -> bool:
         """k_{i,+} = k_{i,-} for every axis (Sec. 2 remark after Eq. (linear_sys))."""
-        return all(self.kp[a] == self.km[a] for a in range(3))
+        return all(self.kp[a] == self.km[a] for a in range(self.dim))
 
     def nodes(self, axis: int) -> np.ndarray:
         """Interior nodes x_p = a + p h, p = 1..n (Sec. 2)."""
@@ -310,6 +321,9 @@ def build_tau(prob: Problem) -> TauPreconditioner:
     a = [mass_eigenvalues(prob.n[ax]) for ax in range(3)]
     lam = [tau_eigenvalues(prob.q[ax], prob.n[ax]) for ax in range(3)]
     c = [prob.eta[ax] * (prob.kp[ax] + prob.km[ax]) for ax in range(3)]
+    if prob.dim == 2:   # the absent third axis: identity mass factor, no stiffness term
+        a[2] = np.ones(1)
+        c[2] = 0.0
     A1, A2, A3 = (a[0][None, None, :], a[1][None, :, None], a[2][:, None, None])
     L1, L2, L3 = (lam[0][None, None, :], lam[1][None, :, None], lam[2][:, None, None])
     Lam = A3 * A2 * A1 + c[0] * A3 * A2 * L1 + c[1] * A3 * L2 * A1 + c[2] * L3 * A2 * A1
@@ -501,6 +515,7 @@ TIME_FACTORS = {
     # name: (phi, phi')
     "sin": (lambda t: math.sin(t + 1.0), lambda t: math.cos(t + 1.0)),
     "exp": (lambda t: math.exp(-t), lambda t: -math.exp(-t)),
+    "4exp": (lambda t: 4.0 * math.exp(t), lambda t: 4.0 * math.exp(t)),   # Example 1 (2-D)
 }
 
 
@@ -522,7 +537,8 @@ def S_series(x, d, kp, km):
 def exact_u(prob: Problem, t: float, phi: str = "exp") -> np.ndarray:
     """Nodal values of the manufactured solution at time t."""
     x, y, z = (prob.nodes(a) for a in range(3))
-    return TIME_FACTORS[phi][0](t) * (P_poly(z)[:, None, None] * P_poly(y)[None, :, None]
+    Pz = P_poly(z) if prob.dim == 3 else np.ones(1)
+    return TIME_FACTORS[phi][0](t) * (Pz[:, None, None] * P_poly(y)[None, :, None]
                                       * P_poly(x)[None, None, :])
 
 
@@ -570,6 +586,8 @@ def source_cell_average(prob: Problem, t: float, phi: str = "exp") -> np.ndarray
     ph, dph = TIME_FACTORS[phi]
     Px, Py, Pz = (cell_average_P(prob, a) for a in range(3))
     Sx, Sy, Sz = (cell_average_S(prob, a) for a in range(3))
+    if prob.dim == 2:   # Example 1: u = phi(t) P(x) P(y), no third factor
+        Pz, Sz = np.ones(1), np.zeros(1)
     X = lambda v: v[None, None, :]
     Y = lambda v: v[None, :, None]
     Z = lambda v: v[:, None, None]

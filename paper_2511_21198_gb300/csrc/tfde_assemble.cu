@@ -170,14 +170,15 @@ int upload(double* d, const std::vector<double>& h, cudaStream_t s) {
 }  // namespace
 
 int validate_params(const tfde_params* p) {
-    for (int a = 0; a < 3; ++a) {
+    const int dims = p->n[2] == 0 ? 2 : 3;   // n[2] = 0: the 2-D problem
+    for (int a = 0; a < dims; ++a) {
         if (p->n[a] < 1) return set_error(TFDE_EINVAL, "n must be >= 1 on every axis");
         if (!(p->delta[a] > 0.0 && p->delta[a] < 1.0)) return set_error(TFDE_EINVAL, "delta must lie in (0,1)");
         if (!(p->kp[a] > 0.0) || !(p->km[a] > 0.0)) return set_error(TFDE_EINVAL, "k_+ and k_- must be > 0");
         if (!(p->hi[a] > p->lo[a])) return set_error(TFDE_EINVAL, "need lo < hi on every axis");
     }
     if (!(p->dt > 0.0)) return set_error(TFDE_EINVAL, "dt must be > 0");
-    const double N = (double)p->n[0] * p->n[1] * p->n[2];
+    const double N = (double)p->n[0] * p->n[1] * (dims == 3 ? p->n[2] : 1);
     if (N > 2.0e9) return set_error(TFDE_EINVAL, "grid too large");
     return TFDE_OK;
 }
@@ -195,6 +196,22 @@ int assemble_problem(const tfde_params* params, int precision, cudaStream_t s, t
     P->p = *params;
     P->prec = precision;
     for (int a = 0; a < 3; ++a) P->n[a] = params->n[a];
+    if (params->n[2] == 0) {
+        // the 2-D problem: a third axis of one point with an identity mass
+        // factor and no stiffness term reproduces the 2-D system exactly
+        P->dim2 = true;
+        P->n[2] = 1;
+        P->p.n[2] = 1;
+        P->p.delta[2] = 0.5;
+        P->p.kp[2] = P->p.km[2] = 1.0;
+        P->p.lo[2] = 0.0;
+        P->p.hi[2] = 1.0;
+        if (precision == TFDE_MIXED) {
+            delete P;
+            return set_error(TFDE_EUNSUPPORTED, "TFDE_MIXED supports 3-D problems only (2-D runs with TFDE_FP64)");
+        }
+    }
+    params = &P->p;
     P->N = (size_t)P->n[0] * P->n[1] * P->n[2];
     P->symmetric = true;
     for (int a = 0; a < 3; ++a) {
@@ -202,12 +219,14 @@ int assemble_problem(const tfde_params* params, int precision, cudaStream_t s, t
         const double d = params->delta[a];
         P->h[a] = (params->hi[a] - params->lo[a]) / (n + 1);
         P->eta[a] = params->dt / (2.0 * std::tgamma(d + 1.0) * std::pow(P->h[a], 2.0 - d));
+        if (P->dim2 && a == 2) P->eta[a] = 0.0;
         P->csum[a] = P->eta[a] * (params->kp[a] + params->km[a]);
         if (params->kp[a] != params->km[a]) P->symmetric = false;
         P->q[a] = generator_q(d, n);
         P->lam_tau[a] = tau_eigs(P->q[a], n);
         P->lam_mass[a].resize(n);
         for (int k = 1; k <= n; ++k) P->lam_mass[a][k - 1] = (6.0 + 2.0 * cos_pi_frac(k, n)) / 8.0;
+        if (P->dim2 && a == 2) P->lam_mass[a][0] = 1.0;
     }
     P->have_src = true;
     for (int a = 0; a < 3; ++a)
@@ -215,6 +234,10 @@ int assemble_problem(const tfde_params* params, int precision, cudaStream_t s, t
     if (P->have_src)
         for (int a = 0; a < 3; ++a)
             example2_1d(P->n[a], params->delta[a], params->kp[a], params->km[a], P->srcP[a], P->srcS[a]);
+    if (P->have_src && P->dim2) {   // Example 1: no third factor
+        P->srcP[2].assign(1, 1.0);
+        P->srcS[2].assign(1, 0.0);
+    }
 
     auto fail = [&](int code) {
         destroy_problem(P);
@@ -270,6 +293,7 @@ int assemble_problem(const tfde_params* params, int precision, cudaStream_t s, t
     if (cudaMallocHost((void**)&P->red_host, 256 * sizeof(double)) != cudaSuccess)
         return fail(set_error(TFDE_ENOMEM, "cudaMallocHost failed"));
     if ((st = fft::init(P, s))) return fail(st);
+    if (P->dim2 && !P->fft) return fail(set_error(TFDE_EUNSUPPORTED, "2-D problems need n_a <= 2048"));
     if (precision == TFDE_MIXED) {
         if ((st = mixed_init(P, s))) return fail(st);
     }

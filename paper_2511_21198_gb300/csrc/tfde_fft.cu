@@ -619,6 +619,8 @@ int apply_A(const tfde_problem* P, int op, const R* x, R* y, R* a, R* w, R* c, R
     if (stiff) st = toeplitz_pass<R>(P, 0, F->G[0], sg, x, nullptr, 0.0, a, w, s);
     else st = toeplitz_pass<R>(P, 0, F->Ghat[rhs ? 1 : 0], 1.0, x, nullptr, 0.0, a, w, s);
     if (st) return st;
+    // 2-D problem: the y pass gives the result (no third axis)
+    if (P->dim2) return toeplitz_pass<R>(P, 1, F->G[1], sg, w, a, 1.0, y, nullptr, s);
     // y: c = sg G2 w + M2 a, e = M2 w
     if ((st = toeplitz_pass<R>(P, 1, F->G[1], sg, w, a, 1.0, c, e, s))) return st;
     // z: y = sg G3 e + M3 c

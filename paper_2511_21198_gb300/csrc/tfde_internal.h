@@ -101,6 +101,7 @@ struct tfde_problem {
     size_t N = 0;
     double h[3]{}, eta[3]{}, csum[3]{};
     bool symmetric = false;
+    bool dim2 = false;      // params n[2] = 0: the 2-D problem (third axis of extent 1, identity, no stiffness)
     std::vector<double> q[3], lam_tau[3], lam_mass[3];
     std::vector<double> srcP[3], srcS[3];  // 1-D exact cell averages of P and S_delta (if lo=0, hi=1)
     bool have_src = false;

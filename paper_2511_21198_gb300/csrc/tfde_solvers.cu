@@ -310,6 +310,12 @@ int accurate_apply_ex(const tfde_problem*, int, const double*, double*, int, con
 
 // A_N u into `out` (the three tridiagonal sweeps in one pass).
 static void mass_apply(const tfde_problem* P, const double* u, double* out, cudaStream_t s) {
+    if (P->dim2) {   // A_2 (x) A_1: the x and y sweeps (W_E as the intermediate)
+        double* t = P->w[tfde_problem::W_E];
+        launch_axis_stencil_f64(u, t, axis_view(P->n, 0), 1.0, nullptr, 0.0, s);
+        launch_axis_stencil_f64(t, out, axis_view(P->n, 1), 1.0, nullptr, 0.0, s);
+        return;
+    }
     launch_mass3d_f64(u, out, P->n, s);
 }
 

@@ -142,3 +142,51 @@ def test_time_convergence_order():
         sols.append(o.cn_solve(p, o.exact_u(p, 0.0, "sin"), M, tol=1e-13, phi="sin").u)
     ratio = np.linalg.norm(sols[0] - sols[1]) / np.linalg.norm(sols[1] - sols[2])
     assert 3.5 < ratio < 4.5
+
+
+GOLDEN_2D = os.path.join(os.path.dirname(__file__), "golden", "paper_iteration_counts_2d.json")
+
+
+def _example1(deltas, np1, kp, km):
+    n = np1 - 1
+    M = np1 // 8
+    return o.Problem(n=(n, n, 1), delta=(deltas[0], deltas[1], 0.5), kp=(kp[0], kp[1], 1.0),
+                     km=(km[0], km[1], 1.0), dt=1.0 / M, dim=2), M
+
+
+def test_two_dimensional_operator_is_the_2d_kronecker_form():
+    """The 2-D problem (Example 1) against its own Kronecker form written out:
+    A = A2 (x) A1 + eta_1 A2 (x) B1 + eta_2 B2 (x) A1, with no third axis."""
+    p = o.Problem(n=(5, 4, 1), delta=(0.3, 0.7, 0.5), kp=(1.0, 2.0, 1.0), km=(0.5, 3.0, 1.0), dt=0.1, dim=2)
+    T1 = o.toeplitz_T(o.q_coefficients(0.3, 5), 5)
+    T2 = o.toeplitz_T(o.q_coefficients(0.7, 4), 4)
+    B1, B2 = 1.0 * T1 + 0.5 * T1.T, 2.0 * T2 + 3.0 * T2.T
+    A1, A2 = o.mass_A(5), o.mass_A(4)
+    e1 = o.eta(0.3, 1.0 / 6, 0.1)
+    e2 = o.eta(0.7, 1.0 / 5, 0.1)
+    A = np.kron(A2, A1) + e1 * np.kron(A2, B1) + e2 * np.kron(B2, A1)
+    np.testing.assert_allclose(o.dense_A(p), A, rtol=1e-14, atol=1e-15)
+    v = inp.uniform_vector(p.shape, 3)
+    np.testing.assert_allclose(o.apply_A(p, v).ravel(), A @ v.ravel(), rtol=1e-13, atol=1e-14)
+    # P of Eq. (pre_definition) in 2-D and its diagonalised form agree
+    P = o.dense_P_from_definition(p)
+    tau = o.build_tau(p)
+    np.testing.assert_allclose(o.apply_P(tau, v).ravel(), P @ v.ravel(), rtol=1e-12, atol=1e-13)
+    assert p.symmetric is False
+
+
+@pytest.mark.parametrize("key", ["0.1,0.2", "0.4,0.5", "0.8,0.9", "0.1,0.9"])
+def test_table1_table2_iteration_counts_2d(key):
+    """Example 1 with the settings of Sec. 4: PCG(tau) and PGMRES(tau) average
+    iteration counts of Tables 1 and 2 for n+1 = 64 and 128 (the GPU tests
+    cover 256 and 512)."""
+    g = json.load(open(GOLDEN_2D))
+    deltas = tuple(float(v) for v in key.split(","))
+    for idx, np1 in enumerate(g["n_plus_1"][:2]):
+        p, M = _example1(deltas, np1, (5.0, 5.0), (5.0, 5.0))
+        r = o.cn_solve(p, o.exact_u(p, 0.0, "4exp"), M, tol=1e-9, phi="4exp", x0="zero")
+        assert np.mean(r.iters) == g["table1_pcg_tau"][key][idx]
+        pn, M = _example1(deltas, np1, (19.0, 21.0), (21.0, 23.0))
+        r = o.cn_solve(pn, o.exact_u(pn, 0.0, "4exp"), M, tol=1e-9, phi="4exp", x0="zero",
+                       criterion="preconditioned")
+        assert np.mean(r.iters) == g["table2_pgmres_tau"][key][idx]
