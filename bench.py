@@ -70,7 +70,7 @@ def parse_args(argv=None):
                     help="initial guess of the batched workload's chained steps (as --guess-order)")
     ap.add_argument("--cnn-steps", type=int, default=100,
                     help="CN steps of the warm-start evaluation at n = 128 (0 skips training and evaluation)")
-    ap.add_argument("--cnn-train-steps", type=int, default=600, help="Adam steps of the warm-start training")
+    ap.add_argument("--cnn-train-steps", type=int, default=2000, help="Adam steps of the warm-start training")
     ap.add_argument("--guess-order", type=int, default=3,
                     help="initial guess of the mixed path: 0 previous step, 1/2 polynomial extrapolation, "
                          "3 order 2 with its minimal-residual correction over the stored history")
@@ -671,19 +671,22 @@ def run_c2(T, steps, guess_order, dev, stream, check_oracle=True):
 
 
 def run_warm_start(T, train_steps, eval_steps, dev, stream):
-    """The learned warm start: trajectories of the solver at n = 64 (64 seeds,
-    6 steps each, random delta, k+-, dt in {0.005, 0.01, 0.02, 0.04},
-    manufactured source), Adam on mini-batches of 8 samples, then `eval_steps`
-    chained CN steps at n = 128 (delta = (0.3, 0.6, 0.8), k+ = 1, k- = 0.5,
-    dt = 0.01, f = 0, smoothed-noise u0, tol 1e-8) with the network's guess
-    (kept only when its FP64 residual beats the previous-step guess) against
-    the previous-step guess alone.  Timed with CUDA events."""
+    """The learned warm start: trajectories of the solver at n = 64 (128
+    seeds, 8 steps each, random delta, k+-, dt in {0.005, 0.01, 0.02, 0.04},
+    manufactured source), Adam on mini-batches of 8 samples with the two
+    previous levels as history (the network corrects the order-2
+    extrapolation in time), then `eval_steps` chained CN steps at n = 128
+    (delta = (0.3, 0.6, 0.8), k+ = 1, k- = 0.5, dt = 0.01, f = 0,
+    smoothed-noise u0, tol 1e-8) with the network's guess (started from the
+    least-residual point between u^m and it) against the previous-step guess
+    and the order-3 corrected extrapolation.  Timed with CUDA events."""
     import torch
 
     from paper_2511_21198_gb300 import warmstart as W
     t0 = time.time()
-    data = W.generate_trajectories(64, list(range(100, 164)), 6, [0.005, 0.01, 0.02, 0.04], with_source=True,
-                                   stream=stream, device=dev)
+    ntraj, nsteps = 128, 8
+    data = W.generate_trajectories(64, list(range(100, 100 + ntraj)), nsteps, [0.005, 0.01, 0.02, 0.04],
+                                   with_source=True, stream=stream, device=dev)
     net = T.tfde_cnn_create((64, 64, 64))
     try:
         T.tfde_cnn_set_params(net, W.init_params(0))
@@ -702,7 +705,8 @@ def run_warm_start(T, train_steps, eval_steps, dev, stream):
     coef = W.coefficients(prm)
     u0 = torch.from_numpy(inp.smoothed_uniform((n, n, n), 5)).to(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    out = {"train": {"grid": 64, "trajectories": 64, "samples": 64 * 6, "adam_steps": train_steps, "batch": 8,
+    out = {"train": {"grid": 64, "trajectories": ntraj, "samples": ntraj * (nsteps - 2), "history_levels": 2,
+                     "adam_steps": train_steps, "batch": 8,
                      "loss_first10": float(np.mean(hist[:10])), "loss_last10": float(np.mean(hist[-10:])),
                      "data_s": t1 - t0, "train_s": t2 - t1},
            "eval": {"grid": n, "steps": eval_steps, "tol": 1e-8}}
@@ -716,14 +720,19 @@ def run_warm_start(T, train_steps, eval_steps, dev, stream):
                     T.tfde_set_guess_order(h, 3)
                 u = u0.clone()
                 x0 = torch.empty_like(u)
+                hist = [u0.clone()]                                    # u^{m-1}, u^{m-2} for the network
                 T.tfde_cn_advance(h, u, None, True, 1e-8, stream)     # step 1 (no guess yet)
                 its, used, r0 = 0, 0, []
                 torch.cuda.synchronize()
                 e0.record(stream)
                 for m in range(eval_steps):
                     if mode == "network":
-                        T.tfde_cnn_predict(ne, u, None, coef, x0, stream)
+                        u1 = hist[-1]
+                        u2 = hist[-2] if len(hist) > 1 else None
+                        T.tfde_cnn_predict_hist(ne, u, u1, u2, None, coef, x0, stream)
+                        prev = u.clone()
                         info, ug = T.tfde_cn_advance_guess(h, u, None, x0, False, 1e-8, stream)
+                        hist = [hist[-1], prev]
                         used += int(ug)
                     else:
                         info = T.tfde_cn_advance(h, u, None, False, 1e-8, stream)

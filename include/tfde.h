@@ -366,6 +366,20 @@ int tfde_cnn_predict(tfde_cnn* net, const double* u, const double* dtF, const do
  */
 int tfde_cnn_accumulate(tfde_cnn* net, const double* u, const double* dtF, const double* coef, const double* u_next,
                         double* loss, void* stream);
+/*
+ * tfde_cnn_predict_hist / tfde_cnn_accumulate_hist -- the same with the time
+ * history u1 = u^{m-1} and u2 = u^{m-2} (device; u2 may be NULL, both NULL
+ * gives the calls above): input channels 11 and 12 carry the first and
+ * second differences d1 = u - u1, d2 = u - 2 u1 + u2 (divided by s), and the
+ * network predicts the correction to the polynomial extrapolation in time,
+ * base = 3u - 3u1 + u2 (2u - u1 with one level): x0 = base + s * net(...),
+ * training target (u^{m+1} - base) / s.  Weights of channels 11, 12 are
+ * ordinary layer-0 parameters.  Errors: TFDE_EINVAL for u2 without u1.
+ */
+int tfde_cnn_predict_hist(tfde_cnn* net, const double* u, const double* u1, const double* u2, const double* dtF,
+                          const double* coef, double* x0, void* stream);
+int tfde_cnn_accumulate_hist(tfde_cnn* net, const double* u, const double* u1, const double* u2, const double* dtF,
+                             const double* coef, const double* u_next, double* loss, void* stream);
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8) with the accumulated gradients
  * averaged over the samples, then clears the accumulator.  lr > 0. */
 int tfde_cnn_adam_step(tfde_cnn* net, float lr, void* stream);

@@ -118,16 +118,33 @@ def loss_and_grads(params, x: np.ndarray, target: np.ndarray):
     return L, grads
 
 
-def input_channels(u: np.ndarray, dtF: np.ndarray | None, c1, c2, c3) -> tuple[np.ndarray, float]:
-    """The 11 input channels of one sample (constants c1 + c2 + c3, three each)
-    and its scale s = max |u| (1 for u = 0)."""
+def input_channels(u: np.ndarray, dtF: np.ndarray | None, c1, c2, c3, u1: np.ndarray | None = None,
+                   u2: np.ndarray | None = None) -> tuple[np.ndarray, float]:
+    """The input channels of one sample and its scale s = max |u| (1 for
+    u = 0): u / s, dtF / s, the constants c1 + c2 + c3 (three each), and with
+    a time history u1 = u^{m-1} (and u2 = u^{m-2}) the first and second
+    differences (u - u1) / s and (u - 2 u1 + u2) / s (13 channels)."""
     s = float(np.abs(u).max())
     if s == 0.0:
         s = 1.0
     ch = [u / s, (dtF / s) if dtF is not None else np.zeros_like(u)]
     for v in list(c1) + list(c2) + list(c3):
         ch.append(np.full_like(u, float(v)))
+    if u1 is not None:
+        ch.append((u - u1) / s)
+        ch.append((u - 2.0 * u1 + u2) / s if u2 is not None else np.zeros_like(u))
     return np.stack(ch), s
+
+
+def extrapolation_base(u: np.ndarray, u1: np.ndarray | None = None, u2: np.ndarray | None = None) -> np.ndarray:
+    """What the network's output corrects: u, or the polynomial extrapolation
+    in time through the history (2u - u1 with one level, 3u - 3u1 + u2 with
+    two: the interpolating polynomial of degree 1 / 2 evaluated one step on)."""
+    if u1 is None:
+        return u
+    if u2 is None:
+        return 2.0 * u - u1
+    return 3.0 * u - 3.0 * u1 + u2
 
 
 def adam_step(p: np.ndarray, g: np.ndarray, m: np.ndarray, v: np.ndarray, step: int, lr: float,

@@ -14,9 +14,10 @@ int cnn_create(const int n[3], tfde_cnn** out);
 int cnn_destroy(tfde_cnn* C);
 int cnn_set_params(tfde_cnn* C, const float* host);
 int cnn_get(const tfde_cnn* C, int what, float* host);
-int cnn_predict(tfde_cnn* C, const double* u, const double* dtF, const double coef[9], double* x0, cudaStream_t s);
-int cnn_accumulate(tfde_cnn* C, const double* u, const double* dtF, const double coef[9], const double* u_next,
-                   double* loss, cudaStream_t s);
+int cnn_predict(tfde_cnn* C, const double* u, const double* u1, const double* u2, const double* dtF,
+                const double coef[9], double* x0, cudaStream_t s);
+int cnn_accumulate(tfde_cnn* C, const double* u, const double* u1, const double* u2, const double* dtF,
+                   const double coef[9], const double* u_next, double* loss, cudaStream_t s);
 int cnn_adam(tfde_cnn* C, float lr, cudaStream_t s);
 }  // namespace cnn
 int batch_destroy(tfde_batch*);
@@ -246,7 +247,19 @@ int tfde_cnn_predict(tfde_cnn* net, const double* u, const double* dtF, const do
     int st;
     if ((st = pre_call()) || (st = check_dev(u, "u")) || (st = check_dev(x0, "x0"))) return st;
     if (dtF && (st = check_dev(dtF, "dtF"))) return st;
-    return cnn::cnn_predict(net, u, dtF, coef, x0, (cudaStream_t)stream);
+    return cnn::cnn_predict(net, u, nullptr, nullptr, dtF, coef, x0, (cudaStream_t)stream);
+}
+
+int tfde_cnn_predict_hist(tfde_cnn* net, const double* u, const double* u1, const double* u2, const double* dtF,
+                          const double* coef, double* x0, void* stream) {
+    if (!net || !coef) return set_error(TFDE_EINVAL, "NULL argument");
+    if (u2 && !u1) return set_error(TFDE_EINVAL, "u2 needs u1");
+    int st;
+    if ((st = pre_call()) || (st = check_dev(u, "u")) || (st = check_dev(x0, "x0"))) return st;
+    if (dtF && (st = check_dev(dtF, "dtF"))) return st;
+    if (u1 && (st = check_dev(u1, "u1"))) return st;
+    if (u2 && (st = check_dev(u2, "u2"))) return st;
+    return cnn::cnn_predict(net, u, u1, u2, dtF, coef, x0, (cudaStream_t)stream);
 }
 
 int tfde_cnn_accumulate(tfde_cnn* net, const double* u, const double* dtF, const double* coef, const double* u_next,
@@ -255,7 +268,19 @@ int tfde_cnn_accumulate(tfde_cnn* net, const double* u, const double* dtF, const
     int st;
     if ((st = pre_call()) || (st = check_dev(u, "u")) || (st = check_dev(u_next, "u_next"))) return st;
     if (dtF && (st = check_dev(dtF, "dtF"))) return st;
-    return cnn::cnn_accumulate(net, u, dtF, coef, u_next, loss, (cudaStream_t)stream);
+    return cnn::cnn_accumulate(net, u, nullptr, nullptr, dtF, coef, u_next, loss, (cudaStream_t)stream);
+}
+
+int tfde_cnn_accumulate_hist(tfde_cnn* net, const double* u, const double* u1, const double* u2, const double* dtF,
+                             const double* coef, const double* u_next, double* loss, void* stream) {
+    if (!net || !coef) return set_error(TFDE_EINVAL, "NULL argument");
+    if (u2 && !u1) return set_error(TFDE_EINVAL, "u2 needs u1");
+    int st;
+    if ((st = pre_call()) || (st = check_dev(u, "u")) || (st = check_dev(u_next, "u_next"))) return st;
+    if (dtF && (st = check_dev(dtF, "dtF"))) return st;
+    if (u1 && (st = check_dev(u1, "u1"))) return st;
+    if (u2 && (st = check_dev(u2, "u2"))) return st;
+    return cnn::cnn_accumulate(net, u, u1, u2, dtF, coef, u_next, loss, (cudaStream_t)stream);
 }
 
 int tfde_cnn_adam_step(tfde_cnn* net, float lr, void* stream) {

@@ -263,8 +263,11 @@ __global__ void maxabs_kernel(const double* __restrict__ u, long long N, double*
     if (threadIdx.x == 0) out[0] = sh[0] > 0.0 ? sh[0] : 1.0;
 }
 
-// X0[slot] = (u/s, dtF/s, c_0..c_8, 0...) for every interior grid point
-__global__ void pack_input_kernel(const double* __restrict__ u, const double* __restrict__ dtF,
+// X0[slot] = (u/s, dtF/s, c_0..c_8, d1/s, d2/s, 0...) for every interior grid
+// point; d1 = u - u1 and d2 = u - 2 u1 + u2 are the first and second
+// differences of the time history (zero channels without it)
+__global__ void pack_input_kernel(const double* __restrict__ u, const double* __restrict__ u1,
+                                  const double* __restrict__ u2, const double* __restrict__ dtF,
                                   const double* __restrict__ scale, const float* __restrict__ coef, int n1, int n2,
                                   long long N, long long R, long long P, __nv_bfloat16* __restrict__ X) {
     const double inv = 1.0 / scale[0];
@@ -274,8 +277,10 @@ __global__ void pack_input_kernel(const double* __restrict__ u, const double* __
         v[1] = dtF ? (float)(dtF[p] * inv) : 0.f;
 #pragma unroll
         for (int c = 0; c < 9; ++c) v[2 + c] = coef[c];
+        v[11] = u1 ? (float)((u[p] - u1[p]) * inv) : 0.f;
+        v[12] = (u1 && u2) ? (float)((u[p] - 2.0 * u1[p] + u2[p]) * inv) : 0.f;
 #pragma unroll
-        for (int c = 11; c < 16; ++c) v[c] = 0.f;
+        for (int c = 13; c < 16; ++c) v[c] = 0.f;
         uint4 o0, o1;
         __nv_bfloat162* h0 = reinterpret_cast<__nv_bfloat162*>(&o0);
         __nv_bfloat162* h1 = reinterpret_cast<__nv_bfloat162*>(&o1);
@@ -290,16 +295,26 @@ __global__ void pack_input_kernel(const double* __restrict__ u, const double* __
     }
 }
 
-// x0 = u + s * out
-__global__ void guess_kernel(const double* __restrict__ u, const float* __restrict__ out,
+// The base the network corrects: u, or the polynomial extrapolation in time
+// of the history (2u - u1 with one level, 3u - 3u1 + u2 with two).
+__device__ __forceinline__ double guess_base(const double* u, const double* u1, const double* u2, long long p) {
+    if (!u1) return u[p];
+    if (!u2) return 2.0 * u[p] - u1[p];
+    return 3.0 * u[p] - 3.0 * u1[p] + u2[p];
+}
+
+// x0 = base + s * out
+__global__ void guess_kernel(const double* __restrict__ u, const double* __restrict__ u1,
+                             const double* __restrict__ u2, const float* __restrict__ out,
                              const double* __restrict__ scale, long long N, double* __restrict__ x0) {
     const double s = scale[0];
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x)
-        x0[p] = u[p] + s * (double)out[p];
+        x0[p] = guess_base(u, u1, u2, p) + s * (double)out[p];
 }
 
 // loss partials and the output gradient: d = out - (u_next - u)/s ; dZ[slot][0] = 2 d / N
 __global__ void loss_grad_kernel(const float* __restrict__ out, const double* __restrict__ u,
+                                 const double* __restrict__ u1, const double* __restrict__ u2,
                                  const double* __restrict__ un, const double* __restrict__ scale, int n1, int n2,
                                  long long N, long long R, long long P, __nv_bfloat16* __restrict__ dZ,
                                  double* __restrict__ part) {
@@ -307,7 +322,7 @@ __global__ void loss_grad_kernel(const float* __restrict__ out, const double* __
     const double inv = 1.0 / scale[0];
     double acc = 0.0;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-        const double d = (double)out[p] - (un[p] - u[p]) * inv;
+        const double d = (double)out[p] - (un[p] - guess_base(u, u1, u2, p)) * inv;
         acc += d * d;
         dZ[slot_of(p, n1, n2, R, P) * CH] = __float2bfloat16_rn((float)(2.0 * d / (double)N));
     }
@@ -502,7 +517,8 @@ int ensure_packed(tfde_cnn* C, cudaStream_t s) {
 }
 
 // forward pass of (u, dtF, coef) into C->out (plain grid, output channel 0)
-int forward(tfde_cnn* C, const double* u, const double* dtF, const double coef[9], cudaStream_t s) {
+int forward(tfde_cnn* C, const double* u, const double* u1, const double* u2, const double* dtF,
+            const double coef[9], cudaStream_t s) {
     float hc[9];
     for (int i = 0; i < 9; ++i) hc[i] = (float)coef[i];
     CN_TRY(cudaMemcpyAsync(C->coef, hc, sizeof(hc), cudaMemcpyHostToDevice, s));
@@ -510,8 +526,8 @@ int forward(tfde_cnn* C, const double* u, const double* dtF, const double coef[9
     if (st) return st;
     stats_count_launch(2);
     maxabs_kernel<<<1, 256, 0, s>>>(u, C->N, C->scale);
-    pack_input_kernel<<<grid1(C->N), 256, 0, s>>>(u, dtF, C->scale, C->coef, C->n[0], C->n[1], C->N, C->R, C->P,
-                                                    C->act[0]);
+    pack_input_kernel<<<grid1(C->N), 256, 0, s>>>(u, u1, u2, dtF, C->scale, C->coef, C->n[0], C->n[1], C->N, C->R,
+                                                    C->P, C->act[0]);
     for (int l = 0; l < NL; ++l) {
         const bool last = l + 1 == NL;
         if ((st = conv(C, C->amap[l], C->wf + (size_t)l * NTAP * 256, C->prm + (size_t)l * PSZ + WSZ, last ? 0 : 1,
@@ -633,23 +649,24 @@ int cnn_get(const tfde_cnn* C, int what, float* host) {
     return TFDE_OK;
 }
 
-int cnn_predict(tfde_cnn* C, const double* u, const double* dtF, const double coef[9], double* x0, cudaStream_t s) {
-    int st = forward(C, u, dtF, coef, s);
+int cnn_predict(tfde_cnn* C, const double* u, const double* u1, const double* u2, const double* dtF,
+                const double coef[9], double* x0, cudaStream_t s) {
+    int st = forward(C, u, u1, u2, dtF, coef, s);
     if (st) return st;
     stats_count_launch();
-    guess_kernel<<<grid1(C->N), 256, 0, s>>>(u, C->out, C->scale, C->N, x0);
+    guess_kernel<<<grid1(C->N), 256, 0, s>>>(u, u1, u2, C->out, C->scale, C->N, x0);
     return check(C, s);
 }
 
-int cnn_accumulate(tfde_cnn* C, const double* u, const double* dtF, const double coef[9], const double* u_next,
-                   double* loss, cudaStream_t s) {
-    int st = forward(C, u, dtF, coef, s);
+int cnn_accumulate(tfde_cnn* C, const double* u, const double* u1, const double* u2, const double* dtF,
+                   const double coef[9], const double* u_next, double* loss, cudaStream_t s) {
+    int st = forward(C, u, u1, u2, dtF, coef, s);
     if (st) return st;
     const int nb = grid1(C->N);
     stats_count_launch();
     CN_TRY(cudaMemsetAsync(C->dz, 0, (size_t)C->S_total * CH * sizeof(__nv_bfloat16), s));
-    loss_grad_kernel<<<nb, 256, 0, s>>>(C->out, u, u_next, C->scale, C->n[0], C->n[1], C->N, C->R, C->P, C->dz,
-                                         C->lpart);
+    loss_grad_kernel<<<nb, 256, 0, s>>>(C->out, u, u1, u2, u_next, C->scale, C->n[0], C->n[1], C->N, C->R, C->P,
+                                         C->dz, C->lpart);
     const int nchunks = (int)((C->count + WG_CHUNK - 1) / WG_CHUNK);
     __nv_bfloat16* g = C->dz;      // gradient w.r.t. the output of layer l (pre-activation for l < NL - 1 after masking)
     __nv_bfloat16* g2 = C->dz2;

@@ -69,7 +69,7 @@ EXPORTS = ["tfde_assemble", "tfde_destroy", "tfde_matvec", "tfde_precond", "tfde
            "tfde_cn_step", "tfde_cn_advance", "tfde_set_guess_order", "tfde_source_example2", "tfde_coefficients", "tfde_host_coefficients",
            "tfde_stats_reset", "tfde_stats_get", "tfde_mass_apply_noalloc", "tfde_batch_create", "tfde_batch_destroy",
            "tfde_batch_count", "tfde_batch_set_guess_order", "tfde_batch_cn_advance", "tfde_cn_advance_guess", "tfde_cnn_create", "tfde_cnn_destroy",
-           "tfde_cnn_set_params", "tfde_cnn_get_params", "tfde_cnn_get_grads", "tfde_cnn_predict", "tfde_cnn_accumulate",
+           "tfde_cnn_set_params", "tfde_cnn_get_params", "tfde_cnn_get_grads", "tfde_cnn_predict", "tfde_cnn_accumulate", "tfde_cnn_predict_hist", "tfde_cnn_accumulate_hist",
            "tfde_cnn_adam_step", "tfde_selftest_wait", "tfde_set_device_loop", "tfde_spectrum", "tfde_last_error", "tfde_version"]
 
 
@@ -116,6 +116,8 @@ def load(path: str | None = None):
         "tfde_cnn_predict": ([vp, vp, vp, POINTER(c_double), vp, vp], c_int),
         "tfde_cnn_accumulate": ([vp, vp, vp, POINTER(c_double), vp, POINTER(c_double), vp], c_int),
         "tfde_cnn_adam_step": ([vp, c_float, vp], c_int),
+        "tfde_cnn_predict_hist": ([vp, vp, vp, vp, vp, POINTER(c_double), vp, vp], c_int),
+        "tfde_cnn_accumulate_hist": ([vp, vp, vp, vp, vp, POINTER(c_double), vp, POINTER(c_double), vp], c_int),
         "tfde_selftest_wait": ([c_longlong, POINTER(c_int), vp], c_int),
         "tfde_set_device_loop": ([vp, c_int], c_int),
         "tfde_spectrum": ([POINTER(tfde_params), c_int, vp, POINTER(tfde_spectrum_info), vp], c_int),
@@ -389,6 +391,20 @@ def tfde_cnn_accumulate(net: int, u, dtF, coef, u_next, stream=None) -> float:
     loss = c_double(0.0)
     _check(load().tfde_cnn_accumulate(net, _ptr(u), _ptr(dtF), c, _ptr(u_next), byref(loss), _stream(stream)),
            "tfde_cnn_accumulate")
+    return loss.value
+
+
+def tfde_cnn_predict_hist(net: int, u, u1, u2, dtF, coef, x0, stream=None) -> None:
+    c = (c_double * 9)(*[float(v) for v in coef])
+    _check(load().tfde_cnn_predict_hist(net, _ptr(u), _ptr(u1), _ptr(u2), _ptr(dtF), c, _ptr(x0), _stream(stream)),
+           "tfde_cnn_predict_hist")
+
+
+def tfde_cnn_accumulate_hist(net: int, u, u1, u2, dtF, coef, u_next, stream=None) -> float:
+    c = (c_double * 9)(*[float(v) for v in coef])
+    loss = c_double(0.0)
+    _check(load().tfde_cnn_accumulate_hist(net, _ptr(u), _ptr(u1), _ptr(u2), _ptr(dtF), c, _ptr(u_next),
+                                           byref(loss), _stream(stream)), "tfde_cnn_accumulate_hist")
     return loss.value
 
 

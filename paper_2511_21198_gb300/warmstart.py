@@ -2,20 +2,23 @@
 network whose forward pass, gradients and Adam updates run in libtfde's
 kernels (tfde_cnn_* in include/tfde.h).
 
-The network sees, per grid point, (u^m / s, dt F^{m+1/2} / s) and nine
-coefficients as constant planes, s = max |u^m|, and predicts
-(u^{m+1} - u^m) / s.  The coefficients are delta_1..3 and the logarithms of
+The network sees, per grid point, (u^m / s, dt F^{m+1/2} / s), nine
+coefficients as constant planes and the first and second time differences
+(u^m - u^{m-1}) / s, (u^m - 2u^{m-1} + u^{m-2}) / s, s = max |u^m|, and
+predicts the correction (u^{m+1} - x_e) / s to the order-2 extrapolation in
+time x_e = 3u^m - 3u^{m-1} + u^{m-2} (without a history: to u^m).  The coefficients are delta_1..3 and the logarithms of
 the per-axis stiffness scales eta_a k+_a and eta_a k-_a (eta_a = dt /
 (2 Gamma(delta_a + 1) h_a^{2 - delta_a}), Eq. (linear_sys)): with q_k
 depending on delta alone, these nine numbers fix the discrete operator at any
 resolution, so a network trained on one grid applies to finer ones.  Training samples are consecutive time
 levels of trajectories that the solver itself computes (tfde_cn_advance);
-inference proposes x0 = u^m + s * net(...) to tfde_cn_advance_guess, which
-keeps the previous-step guess whenever x0's FP64 residual is not smaller.
+inference proposes x0 = x_e + s * net(...) to tfde_cn_advance_guess, which
+starts from the least-residual point between u^m and x0 (the previous-step
+guess whenever x0's FP64 residual is not smaller).
 
 Parameter layout (flat float32, tfde.CNN_PARAMS values): per layer l = 0..3,
 W_l[co][ci][tap] (16 x 16 x 27, tap = (dz+1) 9 + (dy+1) 3 + (dx+1)) then
-b_l[co] (16); layer 0 reads channels 0..10, layer 3 writes channel 0.
+b_l[co] (16); layer 0 reads channels 0..12, layer 3 writes channel 0.
 """
 from __future__ import annotations
 
@@ -29,7 +32,7 @@ CH = 16
 NTAP = 27
 WSZ = CH * CH * NTAP
 PSZ = WSZ + CH
-IN_CH = 11
+IN_CH = 13   # u, dt F, nine coefficients, two time differences
 HIDDEN = 16
 CHANNELS = [IN_CH, HIDDEN, HIDDEN, HIDDEN, 1]
 
@@ -119,21 +122,23 @@ def generate_trajectories(n: int, seeds, steps: int, dt, with_source: bool, tol:
     return out
 
 
-def train(net: int, data, adam_steps: int, batch: int, lr: float, seed: int, stream=None):
-    """Adam on mini-batches of (u^m, dt F, coef) -> u^{m+1} samples; returns the
-    mean sample loss of every Adam step."""
+def train(net: int, data, adam_steps: int, batch: int, lr: float, seed: int, stream=None, history: bool = True):
+    """Adam on mini-batches of samples (u^m, dt F, coef) -> u^{m+1}, with the
+    two previous levels as history when `history` (samples from m = 2 on);
+    returns the mean sample loss of every Adam step."""
     samples = []
     for coef, us, Fs in data:
-        for m in range(len(us) - 1):
-            samples.append((coef, us[m], None if Fs is None else Fs[m], us[m + 1]))
+        for m in range(2 if history else 0, len(us) - 1):
+            samples.append((coef, us[m], us[m - 1] if history else None, us[m - 2] if history else None,
+                            None if Fs is None else Fs[m], us[m + 1]))
     rng = np.random.default_rng(seed)
     hist = []
     for step in range(adam_steps):
         idx = rng.choice(len(samples), size=min(batch, len(samples)), replace=False)
         tot = 0.0
         for i in idx:
-            coef, u, dtF, un = samples[i]
-            tot += T.tfde_cnn_accumulate(net, u, dtF, coef, un, stream)
+            coef, u, u1, u2, dtF, un = samples[i]
+            tot += T.tfde_cnn_accumulate_hist(net, u, u1, u2, dtF, coef, un, stream)
         T.tfde_cnn_adam_step(net, lr, stream)
         hist.append(tot / len(idx))
     return hist

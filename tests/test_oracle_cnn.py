@@ -162,3 +162,20 @@ def test_input_channels_layout():
     assert s == 18.0 and ch.shape == (11, 2, 3, 4)
     assert np.allclose(ch[0], u / 18.0) and np.allclose(ch[1], 2 * u / 18.0)
     assert np.allclose(ch[2:11, 0, 0, 0], [0.1, 0.2, 0.3, 1, 2, 3, 4, 5, 6])
+
+
+def test_history_channels_and_extrapolation_base():
+    """The history channels are the first and second time differences, and
+    the base is the interpolating polynomial through the last levels
+    evaluated one step ahead: exact for data quadratic (linear) in time."""
+    t = np.arange(4.0)
+    rng = np.random.default_rng(0)
+    a, b, c = (rng.standard_normal((2, 3, 2)) for _ in range(3))
+    lev = [a + b * tt + c * tt * tt for tt in t]        # u^{m-2}, u^{m-1}, u^m, u^{m+1}
+    np.testing.assert_allclose(C.extrapolation_base(lev[2], lev[1], lev[0]), lev[3], rtol=1e-12, atol=1e-12)
+    lin = [a + b * tt for tt in t]
+    np.testing.assert_allclose(C.extrapolation_base(lin[2], lin[1]), lin[3], rtol=1e-12, atol=1e-12)
+    ch, s = C.input_channels(lev[2], None, (0.1,) * 3, (1,) * 3, (2,) * 3, lev[1], lev[0])
+    assert ch.shape[0] == 13
+    np.testing.assert_allclose(ch[11] * s, lev[2] - lev[1])
+    np.testing.assert_allclose(ch[12] * s, 2 * c)   # second difference of a quadratic: 2c (unit steps)
