@@ -507,15 +507,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         for (int j = 0; j < 32; ++j) w[j] = j < ncol ? src[gbase + j * gstep] : 0.f;
                     }
                 }
-                uint32_t r[32];
-                tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN + c0), r);
-                if (ncol == 0) continue;   // warp-uniform
-                float v[32];
-#pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = p.alpha * __uint_as_float(r[j]);
-                if (lam) {
-                    float tl = 0.f;
-                    float U[32], V[32];
+                // the Lambda column factors of the chunk (the same for every
+                // row: broadcast loads), ahead of the accumulator read in the
+                // hi-only instance (the others have no registers to spare)
+                constexpr bool LAM_EARLY = OM == OUT_HI && KM == 0;
+                float U[32], V[32];
+                if (LAM_EARLY && lam && ncol > 0) {
                     if (ncol == 32) {
 #pragma unroll
                         for (int k = 0; k < 8; ++k) {
@@ -525,6 +522,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                             V[4 * k] = v4.x; V[4 * k + 1] = v4.y; V[4 * k + 2] = v4.z; V[4 * k + 3] = v4.w;
                         }
                     } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            U[j] = j < ncol ? __ldg(p.lam_U + cx + j) : 1.f;
+                            V[j] = j < ncol ? __ldg(p.lam_V + cx + j) : 0.f;
+                        }
+                    }
+                }
+                uint32_t r[32];
+                tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN + c0), r);
+                if (ncol == 0) continue;   // warp-uniform
+                float v[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = p.alpha * __uint_as_float(r[j]);
+                if (lam) {
+                    float tl = 0.f;
+                    if (!LAM_EARLY) {
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
                             U[j] = j < ncol ? __ldg(p.lam_U + cx + j) : 1.f;
