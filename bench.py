@@ -53,6 +53,8 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=None, help="override the grid size (testing only)")
     ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--fft-mixed-steps", type=int, default=5,
+                    help="chained steps of TFDE_MIXED on the FFT passes at n = 255 and 480 (0: skip)")
     ap.add_argument("--c2-steps", type=int, default=50,
                     help="CN steps of the n = 128 non-symmetric workload, mixed vs plain FP64 (0 skips it)")
     ap.add_argument("--no-c3-protocol", action="store_true",
@@ -453,6 +455,11 @@ def run_ours(args):
     if not args.no_parity:
         parity = full_size_parity(T, params, u_end, (args.warmup + args.steps + 0.5) * dt, dev, stream)
 
+    # ---- TFDE_MIXED on the FFT passes (grids the tensor-core path does not take)
+    fftm = None
+    if args.fft_mixed_steps > 0 and args.n is None:
+        fftm = run_fft_mixed(T, args.fft_mixed_steps, args.guess_order, dev, stream)
+
     # ---- the non-symmetric workload: n = 128, PGMRES(20), mixed vs plain FP64
     c2 = None
     if args.c2_steps > 0 and args.n is None:
@@ -546,7 +553,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "host_gap": host_gap,
             "clocks": clocks, "fp64_path": fp64, "c3_protocol": c3, "parity_n256": parity,
-            "c2_nonsymmetric_n128": c2, "batched": batched, "warm_start": warm, "spectra": spectra,
+            "c2_nonsymmetric_n128": c2, "mixed_fft_path": fftm, "batched": batched, "warm_start": warm, "spectra": spectra,
             "iters_per_step": iters / args.steps, "refine_sweeps_per_step": sweeps / args.steps,
             "max_relres": relres, "max_rel_err_vs_exact": err,
         }
@@ -599,6 +606,48 @@ def full_size_parity(T, params, u_prev, t_half, dev, stream):
     finally:
         T.tfde_destroy(hm)
         T.tfde_destroy(h64)
+    return out
+
+
+def run_fft_mixed(T, steps, guess_order, dev, stream, sizes=(255, 480)):
+    """TFDE_MIXED on grids the tensor-core contraction does not take: FP32
+    inner PCG on the FFT passes inside FP64 refinement (residual on the FP64
+    FFT passes).  The symmetric manufactured workload's coefficients
+    (delta = 0.7, k+- = 1, dt = 1/20, tol 1e-8) at n = 255 (not a multiple of
+    8, next to the n = 256 headline) and n = 480 (above 448): `steps` chained
+    CN steps after one warm-up step, against the plain FP64 path (FFT passes
+    too) over 2 steps from the same state."""
+    import torch
+    W = inp.WORKLOADS[WORKLOAD]
+    dt, tol = 1.0 / W["M"], W["tol"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for n in sizes:
+        prm = T.make_params((n, n, n), W["delta"], W["kp"], W["km"], dt)
+        u0 = torch.from_numpy(inp.example2_initial(n)).to(dev)
+        F = torch.empty_like(u0)
+        res = {"workload": f"n={n} symmetric, PCG, tol {tol:g}, {steps} chained steps after 1 warm-up",
+               "unknowns": n ** 3}
+        for name, prec, k in (("mixed_fft", T.TFDE_MIXED, steps), ("fp64_fft", T.TFDE_FP64, 2)):
+            h = T.tfde_assemble(prm, prec, stream)
+            try:
+                T.tfde_set_guess_order(h, guess_order)
+                u = u0.clone()
+                chained_steps(T, h, u, F, dt, 0, 1, tol, stream)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                it, sw, rr = chained_steps(T, h, u, F, dt, 1, k, tol, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                res[name] = {"value": k / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k, "steps": k,
+                             "iters_per_step": it / k, "refine_sweeps_per_step": sw / k, "max_relres": rr}
+            finally:
+                T.tfde_destroy(h)
+        res["speedup_mixed_vs_fp64"] = res["mixed_fft"]["value"] / res["fp64_fft"]["value"]
+        out[f"n{n}"] = res
+        del u0, F
+        torch.cuda.empty_cache()
     return out
 
 

@@ -54,7 +54,12 @@ typedef enum {
     /* inner Krylov solves on FP32 vectors with split-BF16 tcgen05 contractions
        (Toeplitz matvec: 3 BF16 products; DST: 2), wrapped in FP64 iterative
        refinement whose residual uses the exact-integer slice (Ozaki) tcgen05
-       contraction; the stopping test is always the true FP64 residual */
+       contraction; the stopping test is always the true FP64 residual.
+       Grids the contraction does not take (an n_a that is not a multiple of
+       8 or above 448, and the 2-D problem) run the same FP64 refinement
+       around FP32 inner solves on the FFT passes (FFT-embedded Toeplitz
+       products, DST-I by FFT), the residual on the FP64 FFT passes; these
+       need every n_a <= 2048 */
     TFDE_MIXED = 1
 } tfde_precision;
 
@@ -63,7 +68,7 @@ typedef enum {
  * (lo_0, hi_0) x (lo_1, hi_1): the system of Eq. (linear_sys) without the
  * third axis (A = A_2 (x) A_1 + eta_a A_2 (x) B_1 + eta_b B_2 (x) A_1); the
  * third entries of delta, kp, km, lo, hi are then ignored, grid functions hold
- * n1*n2 values, and only TFDE_FP64 is available. */
+ * n1*n2 values; TFDE_MIXED runs on the FFT passes. */
 typedef struct {
     int n[3];          /* interior grid points per axis, n_a >= 1 (n[2] = 0: 2-D); h_a = (hi_a - lo_a)/(n_a + 1) */
     double lo[3];      /* Omega = prod_a (lo_a, hi_a), lo_a < hi_a                  */
@@ -91,7 +96,7 @@ typedef struct tfde_problem tfde_problem;
 #define TFDE_OP_A    0   /* y = A x, A the CN-FV matrix of Eq. (linear_sys)          */
 #define TFDE_OP_RHS  1   /* y = (A_N - eta-terms) x = (2 A_N - A) x, the RHS operator */
 #define TFDE_OP_FAST 2   /* OR-able: for TFDE_MIXED problems use the inner (split-BF16,
-                            FP32-accumulated) arithmetic instead of the accurate one */
+                            FP32-accumulated, or FP32 FFT) arithmetic instead of the accurate one */
 #define TFDE_OP_STIFF 4  /* y = (A - A_N) x = eta_a A3(x)A2(x)B1 x + eta_b A3(x)B2(x)A1 x +
                             eta_c B3(x)A2(x)A1 x, the three stiffness terms alone (not with FAST) */
 
@@ -105,9 +110,10 @@ typedef struct tfde_problem tfde_problem;
  *   and the mass eigenvalues (6 + 2 cos t_k)/8, and allocates the workspace.
  *   Errors: TFDE_EINVAL for n_a < 1, delta outside (0,1), k <= 0, dt <= 0,
  *   lo >= hi, NULL pointers; TFDE_EUNSUPPORTED when TFDE_MIXED is requested
- *   with an n_a that is not a multiple of 8 (tensor-map row alignment) or
- *   above 448 (the exact-integer residual keeps every FP32 accumulator below
- *   2^24 only up to there);
+ *   on a grid the tensor-core contraction does not take (an n_a that is not
+ *   a multiple of 8 -- tensor-map row alignment -- or above 448, where the
+ *   exact-integer residual's FP32 accumulators would pass 2^24, or 2-D) and
+ *   the FFT passes do not either (an n_a above 2048);
  *   TFDE_ENOMEM / TFDE_ECUDA.  *out is NULL on failure.  Synchronises `stream`.
  */
 int tfde_assemble(const tfde_params* params, int precision, void* stream, tfde_problem** out);

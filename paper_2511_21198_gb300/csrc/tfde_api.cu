@@ -90,6 +90,7 @@ int tfde_matvec(const tfde_problem* prob, int op, const double* x, double* y, vo
     if (x == y) return set_error(TFDE_EINVAL, "x and y must not alias");
     if (op < 0 || op > 7 || ((op & TFDE_OP_STIFF) && (op & TFDE_OP_FAST)))
         return set_error(TFDE_EINVAL, "unknown op");
+    if (prob->fmix) return fmix_apply_A(prob, op, x, y, (cudaStream_t)stream);
     if (prob->prec == TFDE_MIXED) return mixed_apply_A(prob, op, x, y, (cudaStream_t)stream);
     return apply_A64(prob, op & ~TFDE_OP_FAST, x, y, (cudaStream_t)stream);
 }
@@ -98,6 +99,7 @@ int tfde_precond(const tfde_problem* prob, const double* r, double* z, void* str
     if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
     int st;
     if ((st = pre_call()) || (st = check_dev(r, "r")) || (st = check_dev(z, "z"))) return st;
+    if (prob->fmix) return fmix_apply_Pinv(prob, r, z, (cudaStream_t)stream);
     if (prob->prec == TFDE_MIXED) return mixed_apply_Pinv(prob, r, z, (cudaStream_t)stream);
     return apply_Pinv64(prob, r, z, (cudaStream_t)stream);
 }
@@ -113,6 +115,7 @@ int tfde_pcg(const tfde_problem* prob, const double* b, double* x, double tol, i
     if (maxit < 0) return set_error(TFDE_EINVAL, "maxit must be >= 0");
     tfde_problem* P = const_cast<tfde_problem*>(prob);
     P->chain_ok = false;
+    if (prob->fmix) return fmix_pcg(P, b, x, tol, maxit, info, (cudaStream_t)stream, false);
     if (prob->prec == TFDE_MIXED) return mixed_pcg(P, b, x, tol, maxit, info, (cudaStream_t)stream, false);
     return pcg64(prob, b, x, tol, maxit, info, (cudaStream_t)stream, false);
 }
@@ -128,6 +131,7 @@ int tfde_pgmres(const tfde_problem* prob, const double* b, double* x, int restar
     if (maxit < 0) return set_error(TFDE_EINVAL, "maxit must be >= 0");
     tfde_problem* P = const_cast<tfde_problem*>(prob);
     P->chain_ok = false;
+    if (prob->fmix) return fmix_pgmres(P, b, x, restart, tol, maxit, info, (cudaStream_t)stream, false);
     if (prob->prec == TFDE_MIXED) return mixed_pgmres(P, b, x, restart, tol, maxit, info, (cudaStream_t)stream, false);
     return pgmres64(P, b, x, restart, tol, maxit, info, (cudaStream_t)stream, false);
 }

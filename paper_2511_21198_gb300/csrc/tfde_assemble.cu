@@ -206,10 +206,6 @@ int assemble_problem(const tfde_params* params, int precision, cudaStream_t s, t
         P->p.kp[2] = P->p.km[2] = 1.0;
         P->p.lo[2] = 0.0;
         P->p.hi[2] = 1.0;
-        if (precision == TFDE_MIXED) {
-            delete P;
-            return set_error(TFDE_EUNSUPPORTED, "TFDE_MIXED supports 3-D problems only (2-D runs with TFDE_FP64)");
-        }
     }
     params = &P->p;
     P->N = (size_t)P->n[0] * P->n[1] * P->n[2];
@@ -295,7 +291,9 @@ int assemble_problem(const tfde_params* params, int precision, cudaStream_t s, t
     if ((st = fft::init(P, s))) return fail(st);
     if (P->dim2 && !P->fft) return fail(set_error(TFDE_EUNSUPPORTED, "2-D problems need n_a <= 2048"));
     if (precision == TFDE_MIXED) {
-        if ((st = mixed_init(P, s))) return fail(st);
+        // the tensor-core contraction where the grid suits it, else FP32 FFT
+        // inner solves under the same FP64 refinement
+        if ((st = fmix_wanted(P) ? fmix_init(P, s) : mixed_init(P, s))) return fail(st);
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(set_error(TFDE_ECUDA, "assemble: stream sync failed"));
     *out = P;
@@ -329,6 +327,7 @@ int destroy_problem(tfde_problem* P) {
     if (!P) return TFDE_OK;
     cudaDeviceSynchronize();
     mixed_free(P);
+    fmix_free(P);
     fft::free_state(P);
     for (auto& g : P->Ghat) cudaFree(g);
     for (int a = 0; a < 3; ++a) {

@@ -479,6 +479,10 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
             return st;
         }
         B->P.push_back(P);
+        if (!P->mixed) {   // the grouped launches are the tensor-core contraction's
+            free_batch(B);
+            return set_error(TFDE_EUNSUPPORTED, "tfde_batch_create needs every n_a to be a multiple of 8 and <= 448");
+        }
         // every kernel of the batch, per-problem ones included, reports to one flag
         B->own_err.push_back(mixed(P)->err);
         mixed(P)->err = B->d_err;

@@ -125,6 +125,7 @@ struct tfde_problem {
 
     void* mixed = nullptr;  // mixed-precision state (tensor-core path)
     void* fft = nullptr;    // FFT tables of the FFT-embedded passes (tfde_fft.h), null: dense FP64
+    void* fmix = nullptr;   // mixed-precision state on the FFT passes (tfde_fftmixed.cu)
 
     // chained CN advance: W_B / W_R hold b^{m-1} and its final true residual
     const double* chain_u = nullptr;
@@ -154,4 +155,15 @@ int apply_Pinv64(const tfde_problem* P, const double* r, double* z, cudaStream_t
 int dots64(const tfde_problem* P, int m, const double* V, size_t ldv, const double* w, double* out,
            cudaStream_t s);
 int ensure_gmres_basis(tfde_problem* P, int restart);
+// TFDE_MIXED on the FFT passes (tfde_fftmixed.cu): grids the tensor-core
+// contraction does not take (an n_a not a multiple of 8 or above 448, 2-D)
+bool fmix_wanted(const tfde_problem* P);
+int fmix_init(tfde_problem* P, cudaStream_t s);
+void fmix_free(tfde_problem* P);
+int fmix_apply_A(const tfde_problem* P, int op, const double* x, double* y, cudaStream_t s);
+int fmix_apply_Pinv(const tfde_problem* P, const double* r, double* z, cudaStream_t s);
+int fmix_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit, tfde_info* info, cudaStream_t s,
+             bool r_given);
+int fmix_pgmres(tfde_problem* P, const double* b, double* x, int restart, double tol, int maxit, tfde_info* info,
+                cudaStream_t s, bool r_given);
 }  // namespace tfde

@@ -359,7 +359,7 @@ int cn_prepare(tfde_problem* P, const double* u_prev, const double* F, const dou
     double* b = P->w[tfde_problem::W_B];
     double* r = P->w[tfde_problem::W_R];
     double* an = P->w[tfde_problem::W_T];
-    const bool mixed_prec = P->prec == TFDE_MIXED;
+    const bool mixed_prec = P->mixed != nullptr;   // the tensor-core path's exact-slice products
     const bool guess_is_prev = (x0 == nullptr || x0 == u_prev);
     int st;
     // A_N u_prev: left in W_T by the mixed solver's last (full-width) residual
@@ -450,6 +450,9 @@ int cn_drive(tfde_problem* P, const double* u_prev, const double* F, const doubl
     int st = cn_prepare(P, u_prev, F, x0, u_next, s, chained, &rg, guess, used_guess);
     if (st) return st;
     double* b = P->w[tfde_problem::W_B];
+    if (P->fmix)
+        return P->symmetric ? fmix_pcg(P, b, u_next, tol, 10000, info, s, rg)
+                            : fmix_pgmres(P, b, u_next, 20, tol, 10000, info, s, rg);
     const bool mixed_prec = P->prec == TFDE_MIXED;
     if (P->symmetric)
         return mixed_prec ? mixed_pcg(P, b, u_next, tol, 10000, info, s, rg) : pcg64(P, b, u_next, tol, 10000, info, s, rg);

@@ -58,12 +58,6 @@ def test_2d_operator_preconditioner_source_match_oracle(T, case):
         T.tfde_destroy(h)
 
 
-def test_mixed_precision_rejects_2d(T):
-    with pytest.raises(T.TfdeError) as e:
-        T.tfde_assemble(params2d(T, (16, 16), (0.5, 0.5), (1.0, 1.0), (1.0, 1.0), 0.1), T.TFDE_MIXED)
-    assert e.value.status == T.TFDE_EUNSUPPORTED
-
-
 def gpu_counts(T, op, n, d, kp, km, M):
     """Average iterations per step of M CN steps from the exact initial data
     with a zero initial guess at tol 1e-9, and the final error."""

@@ -160,12 +160,6 @@ def test_mixed_trajectory_n16(T):
         T.tfde_destroy(h)
 
 
-def test_mixed_rejects_unsupported_sizes(T):
-    with pytest.raises(T.TfdeError) as e:
-        T.tfde_assemble(T.make_params((12, 16, 16), (0.5,) * 3, (1.0,) * 3, (1.0,) * 3, 0.1), T.TFDE_MIXED)
-    assert e.value.status == T.TFDE_EUNSUPPORTED
-
-
 def test_accurate_apply_wide_dynamic_range(T):
     """Lines whose entries span many orders of magnitude: the exact-integer
     slice contraction (49-bit fixed point under each row and line maximum) is
@@ -275,9 +269,22 @@ def test_mixed_nonsymmetric_advance_matches_fp64(T):
         T.tfde_destroy(hf)
 
 
-def test_mixed_rejects_sizes_beyond_exact_accumulation(T):
+def test_mixed_beyond_exact_accumulation_takes_the_fft_passes(T):
+    """n_a = 456 > 448 (where the exact-slice residual's FP32 sums would pass
+    2^24): TFDE_MIXED runs on the FFT passes instead, and the batched solver,
+    whose grouped launches are the tensor-core contraction's, refuses it."""
+    prm = T.make_params((456, 8, 8), (0.5,) * 3, (1.0,) * 3, (1.0,) * 3, 0.1)
+    h = T.tfde_assemble(prm, T.TFDE_MIXED)
+    try:
+        op = o.Problem(n=(456, 8, 8), delta=(0.5,) * 3, kp=(1.0,) * 3, km=(1.0,) * 3, dt=0.1)
+        v = inp.uniform_vector(op.shape, 62)
+        y = to_dev(np.zeros_like(v))
+        T.tfde_matvec(h, T.TFDE_OP_A, to_dev(v), y)
+        assert relerr(to_host(y), o.apply_A(op, v)) < 1e-13
+    finally:
+        T.tfde_destroy(h)
     with pytest.raises(T.TfdeError) as e:
-        T.tfde_assemble(T.make_params((456, 8, 8), (0.5,) * 3, (1.0,) * 3, (1.0,) * 3, 0.1), T.TFDE_MIXED)
+        T.tfde_batch_create([prm], 20)
     assert e.value.status == T.TFDE_EUNSUPPORTED
 
 
