@@ -830,7 +830,8 @@ def run_batched(T, count, steps, dev, stream, guess_order=0):
     out["initial_guess_order"] = guess_order
     B = T.tfde_batch_create(params, 20, stream)
     T.tfde_batch_set_guess_order(B, guess_order)
-    try:
+
+    def timed():
         us = [u.clone() for u in u0]
         T.tfde_batch_cn_advance(B, us, None, True, 1e-8, stream)    # warm-up step (restarts the chain)
         us = [u.clone() for u in u0]
@@ -843,10 +844,31 @@ def run_batched(T, count, steps, dev, stream, guess_order=0):
         e1.record(stream)
         torch.cuda.synchronize()
         sec = e0.elapsed_time(e1) / 1e3
-        out["batched"] = {"problem_steps_per_s": count * steps / sec, "unknown_steps_per_s": unknowns * steps / sec,
-                          "ms_per_step": 1e3 * sec / steps, "iters_per_problem_step": iters / (count * steps)}
+        return {"problem_steps_per_s": count * steps / sec, "unknown_steps_per_s": unknowns * steps / sec,
+                "ms_per_step": 1e3 * sec / steps, "iters_per_problem_step": iters / (count * steps)}
+
+    try:
+        T.tfde_tune_clear()
+        out["batched_default_launches"] = timed()
+        # the autotuner on the batch's grouped launch classes, then the same steps
+        t0 = time.perf_counter()
+        T.tfde_batch_tune(B, 10, stream)
+        table = T.tfde_tune_get()
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        out["autotuner"] = {"seconds": time.perf_counter() - t0, "classes": len(table),
+                            "changed": sum(1 for e in table if (e["grid"], e["stages"]) != (min(e["tiles"], sms), 2)),
+                            "trial_us_default": sum(e["us_default"] for e in table),
+                            "trial_us_tuned": sum(e["us"] for e in table), "table": table}
+        out["batched"] = timed()
+        # the defaults once more (interleaved, so that drift between runs shows)
+        T.tfde_tune_clear()
+        again = timed()
+        d0 = out["batched_default_launches"]["problem_steps_per_s"]
+        out["batched_default_launches"]["problem_steps_per_s_again"] = again["problem_steps_per_s"]
+        out["tuned_vs_default"] = out["batched"]["problem_steps_per_s"] / (0.5 * (d0 + again["problem_steps_per_s"]))
     finally:
         T.tfde_batch_destroy(B)
+        T.tfde_tune_clear()
     hs = [T.tfde_assemble(p, T.TFDE_MIXED, stream) for p in params]
     for h in hs:
         T.tfde_set_guess_order(h, guess_order)

@@ -326,6 +326,51 @@ int tfde_batch_set_guess_order(tfde_batch* batch, int order);
 int tfde_batch_cn_advance(tfde_batch* batch, double* const* u, const double* const* F_half, int restart, double tol,
                           tfde_info* infos, void* stream);
 
+/* ---------------------------------------------------------------- autotuner */
+/*
+ * Autotuner of the tensor-core contraction's launch parameters (no
+ * counterpart in the paper): the number of persistent CTAs (the SM count,
+ * the count that deals the tiles evenly over the same number of waves, 7/8
+ * and 3/4 of the SMs) and the depth of the operand ring (2 .. 4 stages of
+ * 48 KB, or 2 of 96 KB), per launch class.  A class is the kernel instance
+ * (grouped, operand layout, output mode), the stage size, the rows n of the
+ * contraction (0 for grouped launches) and the number of 128 x 256 tiles.
+ *
+ * tfde_tune records the launches of one operator and one preconditioner
+ * application of a TFDE_MIXED problem on the tensor-core path, times each
+ * class's candidates (one warm-up launch, then `reps` launches between CUDA
+ * events on `stream`) and keeps the fastest in a process-wide table that
+ * every later launch of that class uses (device-side loop graphs captured
+ * before are recaptured).  tfde_batch_tune does the same for a batch's
+ * grouped launches.  Call between solves: the trials overwrite the inner
+ * solvers' scratch vectors and the batch's activity mask.  Errors:
+ * TFDE_EUNSUPPORTED for a problem off the tensor-core path, TFDE_EINVAL for
+ * NULL or reps outside [1, 1000], TFDE_ECUDA.  Synchronises `stream`.
+ *
+ * tfde_tune_get copies up to `cap` entries of the table into out (host
+ * memory) and sets *count to the number copied; tfde_tune_set adds or
+ * replaces `count` entries (a caller caches the table, e.g. as JSON keyed by
+ * the GPU name, and applies it in a fresh process before assembling);
+ * tfde_tune_clear empties it.  Not thread-safe.
+ */
+typedef struct {
+    int grouped;      /* 1: one launch over the tiles of several contractions   */
+    int kmajor;       /* operand layout: 1 for x-axis contractions              */
+    int out_mode;     /* 0 FP32, 1 split planes, 2 direction update, 3 hi plane */
+    int stage_bytes;  /* ring stage size of the class                            */
+    int n;            /* rows of the contraction (0 for grouped launches)        */
+    long long tiles;  /* 128 x 256 tiles of the launch                           */
+    int grid;         /* chosen persistent CTAs                                  */
+    int stages;       /* chosen ring stages                                      */
+    float us;         /* measured microseconds per launch with the choice        */
+    float us_default; /* measured microseconds per launch with the defaults      */
+} tfde_tune_entry;
+int tfde_tune(tfde_problem* prob, int reps, void* stream);
+int tfde_batch_tune(tfde_batch* batch, int reps, void* stream);
+int tfde_tune_get(tfde_tune_entry* out, int cap, int* count);
+int tfde_tune_set(const tfde_tune_entry* in, int count);
+int tfde_tune_clear(void);
+
 /* ------------------------------------------------------ warm-start network */
 /*
  * The learned initial guess of the CN solves (no counterpart in the paper,

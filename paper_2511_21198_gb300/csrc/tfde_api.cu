@@ -35,8 +35,13 @@ int mixed_pcg(tfde_problem*, const double*, double*, double, int, tfde_info*, cu
 int mixed_pgmres(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t, bool);
 int mixed_set_device_loop(tfde_problem*, int);
 int spectrum(const tfde_params*, int, const double*, tfde_spectrum_info*, cudaStream_t);
+int mixed_tune(tfde_problem*, int, cudaStream_t);
+int batch_tune(tfde_batch*, int, cudaStream_t);
 namespace tc {
 int wait_selftest(long long limit_ns, int* tmem_freed, cudaStream_t s);
+int tune_export(tfde_tune_entry* out, int cap, int* count);
+int tune_import(const tfde_tune_entry* in, int count);
+void tune_clear();
 }
 }  // namespace tfde
 
@@ -191,6 +196,8 @@ int tfde_cn_advance_guess(const tfde_problem* prob, double* u, const double* F_h
 int tfde_set_guess_order(tfde_problem* prob, int order) {
     if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
     if (order < 0 || order > 3) return set_error(TFDE_EINVAL, "guess order must be 0, 1, 2 or 3");
+    if (order > 0)
+        if (int st = ensure_history(prob)) return st;
     prob->guess_order = order;
     return TFDE_OK;
 }
@@ -338,6 +345,33 @@ int tfde_spectrum(const tfde_params* params, int steps, const double* v0, tfde_s
 int tfde_set_device_loop(tfde_problem* prob, int enable) {
     if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
     return mixed_set_device_loop(prob, enable);
+}
+
+int tfde_tune(tfde_problem* prob, int reps, void* stream) {
+    if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
+    if (int st = pre_call()) return st;
+    return mixed_tune(prob, reps, (cudaStream_t)stream);
+}
+
+int tfde_batch_tune(tfde_batch* batch, int reps, void* stream) {
+    if (!batch) return set_error(TFDE_EINVAL, "NULL batch");
+    if (int st = pre_call()) return st;
+    return batch_tune(batch, reps, (cudaStream_t)stream);
+}
+
+int tfde_tune_get(tfde_tune_entry* out, int cap, int* count) {
+    if ((!out && cap > 0) || cap < 0) return set_error(TFDE_EINVAL, "NULL output or negative capacity");
+    return tc::tune_export(out, cap, count);
+}
+
+int tfde_tune_set(const tfde_tune_entry* in, int count) {
+    if ((!in && count > 0) || count < 0) return set_error(TFDE_EINVAL, "NULL input or negative count");
+    return tc::tune_import(in, count);
+}
+
+int tfde_tune_clear(void) {
+    tc::tune_clear();
+    return TFDE_OK;
 }
 
 int tfde_selftest_wait(long long limit_ns, int* tmem_freed, void* stream) {

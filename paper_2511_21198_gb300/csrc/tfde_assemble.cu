@@ -284,6 +284,9 @@ int assemble_problem(const tfde_params* params, int precision, cudaStream_t s, t
     // FP64 workspace
     for (int k = 0; k < tfde_problem::NW; ++k)
         if ((st = dalloc(&P->w[k], P->N))) return fail(st);
+    // the FP64 GMRES basis of the default restart (20) for non-symmetric FP64
+    // problems (a longer restart grows it; the mixed paths keep their own)
+    if (precision == TFDE_FP64 && !P->symmetric && (st = ensure_gmres_basis(P, 20))) return fail(st);
     P->nblk = reduction_blocks(P->N);
     if ((st = dalloc(&P->red, (size_t)128 * P->nblk)) || (st = dalloc(&P->red_out, 256))) return fail(st);
     if (cudaMallocHost((void**)&P->red_host, 256 * sizeof(double)) != cudaSuccess)

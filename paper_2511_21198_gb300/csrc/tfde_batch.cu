@@ -4,9 +4,10 @@
 // through the Arnoldi iterations; every split-BF16 operator or preconditioner
 // pass is ONE persistent tcgen05 launch over a tile work list that spans all
 // problems (largest first), every vector step is one launch over a block table
-// of all problems, and the host reads the Hessenberg columns of all problems
-// with one copy per iteration.  A problem whose cycle has converged is masked
-// out of the work lists.  The FP64 refinement residual of each problem (the
+// of all problems, and each problem's Hessenberg column, Givens rotation and
+// stop test run on the device (one thread per problem); the host reads only
+// the number of problems still iterating, one step late.  A problem whose
+// cycle has converged is masked out of the work lists.  The FP64 refinement residual of each problem (the
 // exact-integer slice contraction) and the per-problem right-hand sides run
 // on a small pool of streams.
 #include <algorithm>
@@ -16,7 +17,6 @@
 #include <string>
 #include <vector>
 
-#include "tfde_givens.h"
 #include "tfde_internal.h"
 #include "tfde_mixed.h"
 #include "tfde_stats.h"
@@ -184,6 +184,107 @@ __global__ __launch_bounds__(kBT) void bk_add32to64(const BVec* __restrict__ vt,
 
 #undef BK_PROLOGUE
 
+// ---- the cycle's least-squares problem on the device, one thread per problem.
+// Per-problem state (stride gs_stride(R) doubles): the rotated Hessenberg
+// matrix (row q, column j at q R + j, rows 0..R), cs[R], sn[R], g[R + 1], beta.
+// The operations are those of GivensLS (tfde_givens.h), in the same order.
+__host__ __device__ constexpr int gs_stride(int R) { return (R + 1) * R + 3 * R + 2; }
+
+// start of a cycle: beta = ||P^{-1} r|| from S_WW, g = beta e_1, V_0 scale;
+// act[i] (on entry: the problem takes part) stays set when beta > 0
+__global__ void bk_cycle_start(int C, int R, double* __restrict__ gs, double* __restrict__ s, int* __restrict__ act,
+                               int* __restrict__ its, double* __restrict__ est, int* __restrict__ cnt,
+                               int* __restrict__ bad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C) return;
+    its[i] = 0;
+    est[i] = 1.0;
+    if (!act[i]) return;
+    double* g = gs + (size_t)i * gs_stride(R) + (R + 1) * R + 2 * R;
+    const double beta = sqrt(s[i * kSS + S_WW]);
+    for (int q = 0; q <= R; ++q) g[q] = 0.0;
+    g[0] = beta;
+    g[R + 1] = beta;
+    if (!isfinite(beta)) {
+        atomicOr(bad, 1);
+        act[i] = 0;
+        return;
+    }
+    if (beta > 0.0) {
+        s[i * kSS + S_SPLIT] = 1.0 / beta;
+        atomicAdd(cnt, 1);
+    } else {
+        act[i] = 0;
+    }
+}
+
+// Arnoldi step j: column j of the Hessenberg matrix (the two CGS projections
+// summed, ||w|| from S_WW) rotated into the least-squares state, the new
+// rotation, the residual estimate |g_{j+1}|; the problem leaves the cycle
+// when that estimate reaches theta beta, else V_{j+1} gets the scale 1/||w||.
+// *cnt counts the problems still in the cycle.
+__global__ void bk_givens(int C, int R, int j, double* __restrict__ gs, const double* __restrict__ h,
+                          double* __restrict__ s, const double* __restrict__ theta, int* __restrict__ act,
+                          int* __restrict__ its, double* __restrict__ est, int* __restrict__ cnt,
+                          int* __restrict__ bad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C || !act[i]) return;
+    double* Rm = gs + (size_t)i * gs_stride(R);
+    double* cs = Rm + (R + 1) * R;
+    double* sn = cs + R;
+    double* g = sn + R;
+    const double beta = g[R + 1];
+    const double* hc = h + (size_t)i * kHS;
+    const double hn = sqrt(s[i * kSS + S_WW]);
+    if (!isfinite(hn)) {
+        atomicOr(bad, 1);
+        act[i] = 0;
+        return;
+    }
+    for (int q = 0; q <= j; ++q) Rm[q * R + j] = hc[q] + hc[64 + q];
+    Rm[(j + 1) * R + j] = hn;
+    for (int q = 0; q < j; ++q) {
+        const double t = cs[q] * Rm[q * R + j] + sn[q] * Rm[(q + 1) * R + j];
+        Rm[(q + 1) * R + j] = -sn[q] * Rm[q * R + j] + cs[q] * Rm[(q + 1) * R + j];
+        Rm[q * R + j] = t;
+    }
+    const double den = hypot(Rm[j * R + j], Rm[(j + 1) * R + j]);
+    cs[j] = den > 0.0 ? Rm[j * R + j] / den : 1.0;
+    sn[j] = den > 0.0 ? Rm[(j + 1) * R + j] / den : 0.0;
+    Rm[j * R + j] = den;
+    Rm[(j + 1) * R + j] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    const double e = fabs(g[j + 1]);
+    its[i] = j + 1;
+    est[i] = e / beta;
+    if (e <= theta[i] * beta || hn == 0.0) {
+        act[i] = 0;
+    } else {
+        s[i * kSS + S_SPLIT] = 1.0 / hn;
+        atomicAdd(cnt, 1);
+    }
+}
+
+// end of a cycle: y from the triangular system R y = g (its[i] columns),
+// -y into the coefficient slots (the multi-axpy subtracts), zeros after it
+__global__ void bk_cycle_solve(int C, int R, const double* __restrict__ gs, const int* __restrict__ its,
+                               double* __restrict__ h) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C) return;
+    double* y = h + (size_t)i * kHS + 128;
+    for (int q = 0; q < 64; ++q) y[q] = 0.0;
+    const int k = its[i];
+    const double* Rm = gs + (size_t)i * gs_stride(R);
+    const double* g = Rm + (R + 1) * R + 2 * R;
+    for (int a = k - 1; a >= 0; --a) {
+        double t = g[a];
+        for (int b = a + 1; b < k; ++b) t -= Rm[a * R + b] * y[b];
+        y[a] = t / Rm[a * R + a];
+    }
+    for (int a = 0; a < k; ++a) y[a] = -y[a];
+}
+
 using clk = std::chrono::steady_clock;
 
 }  // namespace
@@ -213,13 +314,27 @@ struct tfde_batch {
     int NB = 0;
     double* d_part = nullptr;       // (restart + 2) * NB partial sums
     double* d_h = nullptr;          // count * kHS
-    double* h_h = nullptr;
     double* d_s = nullptr;          // count * kSS
     double* h_s = nullptr;
     int* d_act = nullptr;
     int* h_act = nullptr;
     int* d_err = nullptr;
     int* h_err = nullptr;
+    // the device-side cycle: Givens state, per-problem targets, steps and
+    // estimates, the count of problems still active after each step (read
+    // by the host one step late), the non-finite flag
+    double* d_gs = nullptr;
+    double* d_theta = nullptr;
+    double* h_theta = nullptr;
+    int* d_its = nullptr;
+    int* h_its = nullptr;
+    double* d_est = nullptr;
+    double* h_est = nullptr;
+    int* d_cnt = nullptr;           // restart + 1
+    int* h_cnt = nullptr;
+    int* d_bad = nullptr;
+    int* h_bad = nullptr;
+    std::vector<cudaEvent_t> cnt_ev;   // restart + 1
     cudaStream_t aux[tfde::kStreams] = {};
     cudaEvent_t ev[tfde::kStreams] = {};
     cudaEvent_t fork_ev = nullptr;
@@ -267,13 +382,25 @@ int free_batch(tfde_batch* B) {
     cudaFree(B->d_bstart);
     cudaFree(B->d_part);
     cudaFree(B->d_h);
-    if (B->h_h) cudaFreeHost(B->h_h);
     cudaFree(B->d_s);
     if (B->h_s) cudaFreeHost(B->h_s);
     cudaFree(B->d_act);
     if (B->h_act) cudaFreeHost(B->h_act);
     cudaFree(B->d_err);
     if (B->h_err) cudaFreeHost(B->h_err);
+    cudaFree(B->d_gs);
+    cudaFree(B->d_theta);
+    if (B->h_theta) cudaFreeHost(B->h_theta);
+    cudaFree(B->d_its);
+    if (B->h_its) cudaFreeHost(B->h_its);
+    cudaFree(B->d_est);
+    if (B->h_est) cudaFreeHost(B->h_est);
+    cudaFree(B->d_cnt);
+    if (B->h_cnt) cudaFreeHost(B->h_cnt);
+    cudaFree(B->d_bad);
+    if (B->h_bad) cudaFreeHost(B->h_bad);
+    for (cudaEvent_t e : B->cnt_ev)
+        if (e) cudaEventDestroy(e);
     for (int k = 0; k < kStreams; ++k) {
         if (B->aux[k]) cudaStreamDestroy(B->aux[k]);
         if (B->ev[k]) cudaEventDestroy(B->ev[k]);
@@ -329,8 +456,7 @@ int upload_act_scalars(tfde_batch* B, cudaStream_t s) {
     return TFDE_OK;
 }
 
-int read_back(tfde_batch* B, bool hess, cudaStream_t s) {
-    if (hess) B_TRY(cudaMemcpyAsync(B->h_h, B->d_h, (size_t)B->count * kHS * sizeof(double), cudaMemcpyDeviceToHost, s));
+int read_back(tfde_batch* B, cudaStream_t s) {
     B_TRY(cudaMemcpyAsync(B->h_s, B->d_s, (size_t)B->count * kSS * sizeof(double), cudaMemcpyDeviceToHost, s));
     B_TRY(cudaMemcpyAsync(B->h_err, B->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     B_TRY(cudaStreamSynchronize(s));
@@ -339,45 +465,45 @@ int read_back(tfde_batch* B, bool hess, cudaStream_t s) {
 }
 
 // One lock-step left-preconditioned GMRES cycle (Sec. 3.2) for every problem
-// with act[i] set: A d_i = r32_i (x32_i = 0 on entry, d_i on exit), stopping
+// with outer[i] set: A d_i = r32_i (x32_i = 0 on entry, d_i on exit), stopping
 // problem i once its preconditioned residual estimate falls below
 // theta[i] * beta_i.  est[i] = final estimate / beta_i; its[i] = steps.
+// The Hessenberg columns, their Givens rotations, the stop test and the
+// final triangular solve stay on the device; the host only learns how many
+// problems are still in the cycle, one step late (it waits for the count of
+// step j - 2 while the GPU runs step j - 1), so the GPU never idles on a host
+// read, at the price of at most two fully masked steps at the end.  One
+// read per cycle brings back every problem's steps and estimate.
 int batch_cycle(tfde_batch* B, const std::vector<int>& outer, const std::vector<double>& theta,
                 std::vector<double>& est, std::vector<int>& its, cudaStream_t s) {
     const int C = B->count, R = B->restart;
+    const int gb = (C + 63) / 64;
     int st;
-    for (int i = 0; i < C; ++i) B->h_act[i] = outer[i];
+    for (int i = 0; i < C; ++i) {
+        B->h_act[i] = outer[i];
+        B->h_theta[i] = theta[i];
+    }
     B_TRY(cudaMemcpyAsync(B->d_act, B->h_act, C * sizeof(int), cudaMemcpyHostToDevice, s));
+    B_TRY(cudaMemcpyAsync(B->d_theta, B->h_theta, C * sizeof(double), cudaMemcpyHostToDevice, s));
+    B_TRY(cudaMemsetAsync(B->d_cnt, 0, (R + 1) * sizeof(int), s));
+    B_TRY(cudaMemsetAsync(B->d_bad, 0, sizeof(int), s));
     if ((st = grouped_precond(B, 0, s))) return st;
     bdots(B, 0, 1, 0, B->d_s, kSS, S_WW, s);
-    if ((st = read_back(B, false, s))) return st;
-    std::vector<GivensLS> ls;
-    ls.reserve(C);
-    std::vector<double> beta(C, 0.0);
-    std::vector<int> inner(C, 0);
-    int any = 0;
-    for (int i = 0; i < C; ++i) {
-        ls.emplace_back(R);
-        its[i] = 0;
-        est[i] = 1.0;
-        if (!outer[i]) continue;
-        beta[i] = std::sqrt(B->h_s[i * kSS + S_WW]);
-        if (!std::isfinite(beta[i])) return set_error(TFDE_ENAN, "non-finite preconditioned residual");
-        if (beta[i] > 0.0) {
-            inner[i] = 1;
-            ls[i].g[0] = beta[i];
-            B->h_s[i * kSS + S_SPLIT] = 1.0 / beta[i];
-            any = 1;
+    vec_launch_count();
+    bk_cycle_start<<<gb, 64, 0, s>>>(C, R, B->d_gs, B->d_s, B->d_act, B->d_its, B->d_est, B->d_cnt, B->d_bad);
+    B_TRY(cudaMemcpyAsync(B->h_cnt, B->d_cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaEventRecord(B->cnt_ev[0], s));
+    vec_launch_count();
+    bk_scale_split<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, 0, B->d_s);
+    for (int j = 0; j < R; ++j) {
+        // stop issuing once no problem is left: the count after step j - 1
+        // if it is already in, else the one after step j - 2
+        if (cudaEventQuery(B->cnt_ev[j]) == cudaSuccess) {
+            if (B->h_cnt[j] == 0) break;
+        } else if (j >= 1) {
+            B_TRY(cudaEventSynchronize(B->cnt_ev[j - 1]));
+            if (B->h_cnt[j - 1] == 0) break;
         }
-    }
-    for (int i = 0; i < C; ++i) B->h_act[i] = inner[i];
-    if ((st = upload_act_scalars(B, s))) return st;
-    if (any) {
-        vec_launch_count();
-        bk_scale_split<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, 0, B->d_s);
-    }
-    std::vector<double> h(R + 2);
-    for (int j = 0; j < R && any; ++j) {
         if ((st = grouped_matvec(B, s))) return st;
         if ((st = grouped_precond(B, j + 1, s))) return st;
         // CGS2, coefficients on the device
@@ -388,44 +514,33 @@ int batch_cycle(tfde_batch* B, const std::vector<int>& outer, const std::vector<
         vec_launch_count();
         bk_multiaxpy<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, j + 1, j + 1, B->d_h, 64);
         bdots(B, j + 1, 1, j + 1, B->d_s, kSS, S_WW, s);
-        if ((st = read_back(B, true, s))) return st;
-        any = 0;
-        for (int i = 0; i < C; ++i) {
-            if (!inner[i]) continue;
-            for (int q = 0; q <= j; ++q) h[q] = B->h_h[i * kHS + q] + B->h_h[i * kHS + 64 + q];
-            const double hn = std::sqrt(B->h_s[i * kSS + S_WW]);
-            if (!std::isfinite(hn)) return set_error(TFDE_ENAN, "non-finite Arnoldi vector");
-            h[j + 1] = hn;
-            const double e = ls[i].add_column(j, h.data());
-            its[i] = j + 1;
-            est[i] = e / beta[i];
-            if (e <= theta[i] * beta[i] || hn == 0.0) {
-                inner[i] = 0;
-            } else {
-                B->h_s[i * kSS + S_SPLIT] = 1.0 / hn;
-                any = 1;
-            }
-        }
-        if (!any) break;
-        for (int i = 0; i < C; ++i) B->h_act[i] = inner[i];
-        if ((st = upload_act_scalars(B, s))) return st;
+        vec_launch_count();
+        bk_givens<<<gb, 64, 0, s>>>(C, R, j, B->d_gs, B->d_h, B->d_s, B->d_theta, B->d_act, B->d_its, B->d_est,
+                                    B->d_cnt + j + 1, B->d_bad);
+        B_TRY(cudaMemcpyAsync(B->h_cnt + j + 1, B->d_cnt + j + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        B_TRY(cudaEventRecord(B->cnt_ev[j + 1], s));
         vec_launch_count();
         bk_scale_split<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, j + 1, B->d_s);
     }
     // d_i = V_i y_i
+    vec_launch_count();
+    bk_cycle_solve<<<gb, 64, 0, s>>>(C, R, B->d_gs, B->d_its, B->d_h);
+    B_TRY(cudaMemcpyAsync(B->h_its, B->d_its, C * sizeof(int), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaMemcpyAsync(B->h_est, B->d_est, C * sizeof(double), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaMemcpyAsync(B->h_bad, B->d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaMemcpyAsync(B->h_err, B->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaStreamSynchronize(s));
+    if (*B->h_err) return set_error(TFDE_ETIMEOUT, "tensor-core kernel wait ran out (device error flag set)");
+    if (*B->h_bad) return set_error(TFDE_ENAN, "non-finite value in a batched GMRES cycle");
     int kmax = 0;
     for (int i = 0; i < C; ++i) {
-        for (int q = 0; q < 64; ++q) B->h_h[i * kHS + 128 + q] = 0.0;
-        if (!outer[i] || its[i] == 0) continue;
-        std::vector<double> y;
-        ls[i].solve(its[i], y);
-        for (int q = 0; q < its[i]; ++q) B->h_h[i * kHS + 128 + q] = -y[q];
+        its[i] = outer[i] ? B->h_its[i] : 0;
+        est[i] = outer[i] ? B->h_est[i] : 1.0;
         kmax = std::max(kmax, its[i]);
     }
     if (kmax > 0) {
         for (int i = 0; i < C; ++i) B->h_act[i] = outer[i] && its[i] > 0;
         B_TRY(cudaMemcpyAsync(B->d_act, B->h_act, C * sizeof(int), cudaMemcpyHostToDevice, s));
-        B_TRY(cudaMemcpyAsync(B->d_h, B->h_h, (size_t)C * kHS * sizeof(double), cudaMemcpyHostToDevice, s));
         vec_launch_count();
         bk_multiaxpy<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, kmax, -1, B->d_h, 128);
     }
@@ -557,12 +672,26 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
         cudaMalloc((void**)&B->d_bstart, bstart.size() * sizeof(int)) != cudaSuccess ||
         cudaMalloc((void**)&B->d_part, (size_t)(restart + 2) * B->NB * sizeof(double)) != cudaSuccess ||
         cudaMalloc((void**)&B->d_h, C * kHS * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost((void**)&B->h_h, C * kHS * sizeof(double)) != cudaSuccess ||
         cudaMalloc((void**)&B->d_s, C * kSS * sizeof(double)) != cudaSuccess ||
         cudaMallocHost((void**)&B->h_s, C * kSS * sizeof(double)) != cudaSuccess ||
         cudaMalloc((void**)&B->d_act, C * sizeof(int)) != cudaSuccess ||
-        cudaMallocHost((void**)&B->h_act, C * sizeof(int)) != cudaSuccess)
+        cudaMallocHost((void**)&B->h_act, C * sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_gs, C * gs_stride(restart) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_theta, C * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&B->h_theta, C * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_its, C * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&B->h_its, C * sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_est, C * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&B->h_est, C * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_cnt, (restart + 1) * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&B->h_cnt, (restart + 1) * sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_bad, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&B->h_bad, sizeof(int)) != cudaSuccess)
         return fail(TFDE_ENOMEM, "allocation of the batch workspace failed");
+    B->cnt_ev.assign(restart + 1, nullptr);
+    for (auto& e : B->cnt_ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return fail(TFDE_ECUDA, "event creation failed");
     for (size_t i = 0; i < C; ++i) {
         tfde_problem* P = B->P[i];
         MixedState* M = mixed(P);
@@ -579,7 +708,8 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
         v.x64 = nullptr;
     }
     std::memset(B->h_s, 0, C * kSS * sizeof(double));
-    std::memset(B->h_h, 0, C * kHS * sizeof(double));
+    if (cudaMemsetAsync(B->d_h, 0, C * kHS * sizeof(double), s) != cudaSuccess)
+        return fail(TFDE_ECUDA, "batch workspace initialisation failed");
     if (cudaMemcpyAsync(B->d_mv, mv.data(), mv.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(B->d_pc, pc.data(), pc.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(B->d_pcl, pcl.data(), pcl.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -604,6 +734,22 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
 
 int batch_destroy(tfde_batch* B) { return free_batch(B); }
 
+// The autotuner on the batch's grouped launches (tfde_batch_tune): one
+// operator and one preconditioner application over every problem recorded,
+// then timed per launch class.
+int batch_tune(tfde_batch* B, int reps, cudaStream_t s) {
+    if (reps < 1 || reps > 1000) return set_error(TFDE_EINVAL, "reps must lie in [1, 1000]");
+    for (int i = 0; i < B->count; ++i) B->h_act[i] = 1;
+    B_TRY(cudaMemcpyAsync(B->d_act, B->h_act, B->count * sizeof(int), cudaMemcpyHostToDevice, s));
+    tc::tune_record(true);
+    int st = grouped_matvec(B, s);
+    if (!st) st = grouped_precond(B, 0, s);
+    tc::tune_record(false);
+    if (!st) st = tc::tune_recorded(reps, s);
+    if (!st) st = read_back(B, s);
+    return st;
+}
+
 }  // namespace tfde
 
 extern "C" int tfde_batch_count(const tfde_batch* B) { return B ? B->count : 0; }
@@ -611,7 +757,11 @@ extern "C" int tfde_batch_count(const tfde_batch* B) { return B ? B->count : 0; 
 extern "C" int tfde_batch_set_guess_order(tfde_batch* B, int order) {
     if (!B) return tfde::set_error(TFDE_EINVAL, "NULL batch");
     if (order < 0 || order > 3) return tfde::set_error(TFDE_EINVAL, "guess order must be 0, 1, 2 or 3");
-    for (tfde_problem* P : B->P) P->guess_order = order;
+    for (tfde_problem* P : B->P) {
+        if (order > 0)
+            if (int st = tfde::ensure_history(P)) return st;
+        P->guess_order = order;
+    }
     return TFDE_OK;
 }
 
@@ -646,7 +796,7 @@ int batch_cn_advance(tfde_batch* B, double* const* u, const double* const* F, in
     join(B, s);
     std::vector<int> all(C, 1);
     batch_norms(B, all, true, s);
-    if ((st = read_back(B, false, s))) return st;
+    if ((st = read_back(B, s))) return st;
     std::vector<double> nb(C), nr(C), ratio(C, 1.0), theta(C), est(C);
     std::vector<int> its(C), stall(C, 0), done(C, 0), outer(C, 0);
     std::vector<tfde_info> info(C);
@@ -701,7 +851,7 @@ int batch_cn_advance(tfde_batch* B, double* const* u, const double* const* F, in
         }
         join(B, s);
         batch_norms(B, outer, false, s);
-        if ((st = read_back(B, false, s))) return st;
+        if ((st = read_back(B, s))) return st;
         for (int i = 0; i < C; ++i) {
             if (!outer[i]) continue;
             const double nr_old = nr[i];

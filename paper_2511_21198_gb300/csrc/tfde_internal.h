@@ -155,6 +155,7 @@ int apply_Pinv64(const tfde_problem* P, const double* r, double* z, cudaStream_t
 int dots64(const tfde_problem* P, int m, const double* V, size_t ldv, const double* w, double* out,
            cudaStream_t s);
 int ensure_gmres_basis(tfde_problem* P, int restart);
+int ensure_history(tfde_problem* P);
 // TFDE_MIXED on the FFT passes (tfde_fftmixed.cu): grids the tensor-core
 // contraction does not take (an n_a not a multiple of 8 or above 448, 2-D)
 bool fmix_wanted(const tfde_problem* P);

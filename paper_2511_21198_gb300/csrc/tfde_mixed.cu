@@ -442,6 +442,12 @@ enum { D_RZN = 4, D_THR = 5 };
 // leaves the host-driven loop in use.
 int build_pcg_graph(const tfde_problem* P, cudaStream_t s) {
     MixedState* M = mixed(P);
+    if (M->pcg_exec && M->pcg_tune_gen != tc::tune_generation()) {   // launch parameters changed: recapture
+        cudaGraphExecDestroy(M->pcg_exec);
+        cudaGraphDestroy(M->pcg_graph);
+        M->pcg_exec = nullptr;
+        M->pcg_graph = nullptr;
+    }
     if (M->pcg_exec || M->pcg_graph_failed) return TFDE_OK;
     const size_t N = P->N;
     if (!M->pring) MX_TRY(cudaMalloc((void**)&M->pring, (size_t)kPRing * N * sizeof(float)));
@@ -509,6 +515,7 @@ int build_pcg_graph(const tfde_problem* P, cudaStream_t s) {
     }
     M->pcg_graph = g;
     M->pcg_exec = ex;
+    M->pcg_tune_gen = tc::tune_generation();
     return TFDE_OK;
 }
 
@@ -611,7 +618,7 @@ int ensure_v32(const tfde_problem* P, int restart) {
 int build_gmres_graph(const tfde_problem* P, int restart, cudaStream_t s) {
     MixedState* M = mixed(P);
     if (M->gm_graph_failed || restart > GS_MAXM) return TFDE_OK;
-    if (M->gm_exec && M->gm_graph_restart == restart) return TFDE_OK;
+    if (M->gm_exec && M->gm_graph_restart == restart && M->gm_tune_gen == tc::tune_generation()) return TFDE_OK;
     if (M->gm_exec) {
         cudaGraphExecDestroy(M->gm_exec);
         cudaGraphDestroy(M->gm_graph);
@@ -669,6 +676,7 @@ int build_gmres_graph(const tfde_problem* P, int restart, cudaStream_t s) {
     M->gm_graph = g;
     M->gm_exec = ex;
     M->gm_graph_restart = restart;
+    M->gm_tune_gen = tc::tune_generation();
     return TFDE_OK;
 }
 
@@ -913,6 +921,18 @@ int mixed_init(tfde_problem* P, cudaStream_t s) {
     MX_TRY(cudaMalloc((void**)&M->err, sizeof(int)));
     MX_TRY(cudaMemsetAsync(M->err, 0, sizeof(int), s));
     MX_TRY(cudaMallocHost((void**)&M->err_host, sizeof(int)));
+    // the solvers' workspaces up front, so that no solve allocates: the PCG
+    // direction ring and loop control, the grouped operator descriptors, the
+    // GMRES basis of the default restart (20; a longer restart grows it) and
+    // the device-side cycle's state
+    MX_TRY(cudaMalloc((void**)&M->pring, (size_t)kPRing * N * sizeof(float)));
+    MX_TRY(cudaMalloc((void**)&M->pcg_ctl, 4 * sizeof(int)));
+    MX_TRY(cudaMallocHost((void**)&M->pcg_ctl_host, 4 * sizeof(int)));
+    MX_TRY(cudaMalloc((void**)&M->gm_state, GS_WORDS * sizeof(double)));
+    MX_TRY(cudaMalloc((void**)&M->gm_ctl, 4 * sizeof(int)));
+    MX_TRY(cudaMallocHost((void**)&M->gm_ctl_host, 4 * sizeof(int)));
+    if (int st = ensure_pairs(P, s)) return st;
+    if (int st = ensure_v32(P, 20)) return st;
     MX_TRY(cudaStreamSynchronize(s));
     return TFDE_OK;
 }
@@ -1159,6 +1179,26 @@ int mixed_pgmres(tfde_problem* P, const double* b, double* x, int restart, doubl
     loc.ms = (float)std::chrono::duration<double, std::milli>(clk::now() - t0).count();
     if (info) *info = loc;
     return status;
+}
+
+// The autotuner on this problem's launch classes: one operator application
+// (the two grouped pairs and the z pass) and one preconditioner application
+// with the direction update are recorded, then every class is timed over its
+// candidate launch parameters and the fastest kept (tfde_tune).  The trials
+// overwrite the inner solver's scratch vectors only: call between solves.
+int mixed_tune(tfde_problem* P, int reps, cudaStream_t s) {
+    MixedState* M = mixed(P);
+    if (!M) return set_error(TFDE_EUNSUPPORTED, "only the tensor-core mixed path has tunable launches");
+    if (reps < 1 || reps > 1000) return set_error(TFDE_EINVAL, "reps must lie in [1, 1000]");
+    double* d = M->dsc;
+    const size_t N = P->N;
+    tc::tune_record(true);
+    int st = fast_matvec(P, TFDE_OP_A, M->f[F_Q], s, -1, M->pring, d + D_PQ);
+    if (!st) st = fast_precond_cg(P, M->pring + N, M->pring, d + D_RZ0, nullptr, nullptr, s);
+    tc::tune_record(false);
+    if (!st) st = tc::tune_recorded(reps, s);
+    if (!st) st = check_err(P, s);
+    return st;
 }
 
 int mixed_set_device_loop(tfde_problem* P, int enable) {

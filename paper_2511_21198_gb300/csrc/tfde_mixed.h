@@ -147,6 +147,8 @@ struct MixedState {
     cudaGraph_t pcg_graph = nullptr;
     cudaGraphExec_t pcg_exec = nullptr;
     bool pcg_graph_failed = false;
+    unsigned pcg_tune_gen = 0;      // autotuner table generation the graphs were captured with
+    unsigned gm_tune_gen = 0;
     bool device_loop = true;   // tfde_set_device_loop
     // the inner GMRES cycle's Arnoldi steps as one graph launch (while node)
     double* gm_state = nullptr;   // GS_WORDS

@@ -82,6 +82,18 @@ static int dot(const tfde_problem* P, const double* a, const double* b, double* 
     return dots64(P, 1, a, 0, b, out, s);
 }
 
+// The (u, A u) history of the extrapolated initial guess: allocated by
+// tfde_set_guess_order / tfde_batch_set_guess_order (order > 0), not by a solve.
+int ensure_history(tfde_problem* P) {
+    if (P->H[0][0]) return TFDE_OK;
+    for (auto& hk : P->H)
+        for (auto& v : hk)
+            if (cudaMalloc((void**)&v, P->N * sizeof(double)) != cudaSuccess)
+                return set_error(TFDE_ENOMEM, "cudaMalloc of the extrapolation history failed");
+    P->hist = 0;
+    return TFDE_OK;
+}
+
 int ensure_gmres_basis(tfde_problem* P, int restart) {
     if (P->gmres_cap >= restart) return TFDE_OK;
     cudaFree(P->V);
@@ -370,13 +382,7 @@ int cn_prepare(tfde_problem* P, const double* u_prev, const double* F, const dou
     bool guess_in_place = false;  // x0 already written into u_next, r = b - A x0
     if (used_guess) *used_guess = 0;
     if (chained && P->guess_order > 0 && u_next == u_prev && !guess) {
-        if (!P->H[0][0]) {
-            for (auto& hk : P->H)
-                for (auto& v : hk)
-                    if (cudaMalloc((void**)&v, P->N * sizeof(double)) != cudaSuccess)
-                        return set_error(TFDE_ENOMEM, "cudaMalloc of the extrapolation history failed");
-            P->hist = 0;
-        }
+        if ((st = ensure_history(P))) return st;   // allocated when the order was set
         const int order = P->guess_order < P->hist ? P->guess_order : P->hist;
         double g[3];
         const double* gp = nullptr;

@@ -266,13 +266,132 @@ void launch_instance(int kmajor, int out_mode, unsigned grid, cudaStream_t s, co
     }
 }
 
+namespace {
+std::vector<std::pair<TuneKey, TuneVal>> g_tune;
+int g_force_grid = 0, g_force_stages = 0;
+unsigned g_tune_gen = 1;
+
+// a launch kept by the recorder
+struct Rec {
+    TuneKey key;
+    Params p0;                  // after set_ring (single) / the grouped template
+    const Params* groups;
+    const long long* gstart;
+    int ngroups;
+    long long total;
+    const int* gactive;
+};
+bool g_recording = false;
+std::vector<Rec> g_rec;
+
+bool same(const TuneKey& a, const TuneKey& b) {
+    return a.grouped == b.grouped && a.kmajor == b.kmajor && a.out_mode == b.out_mode &&
+           a.stage_bytes == b.stage_bytes && a.n == b.n && a.tiles == b.tiles;
+}
+
+// grid and stages of a launch: the tuner's trial, else the table, else the defaults
+void choose(const TuneKey& k, long long total, int cap, long long* grid, int* stages) {
+    *grid = total < num_sms() ? total : num_sms();
+    *stages = cap;
+    if (g_force_grid > 0) {
+        *grid = g_force_grid;
+        *stages = g_force_stages;
+    } else {
+        for (const auto& e : g_tune)
+            if (same(e.first, k)) {
+                *grid = e.second.grid;
+                *stages = e.second.stages;
+                break;
+            }
+    }
+    if (*grid > total) *grid = total;
+    if (*grid < 1) *grid = 1;
+    if (*stages > cap) *stages = cap;
+    if (*stages < 2) *stages = cap < 2 ? cap : 2;
+}
+}  // namespace
+
+void tune_force(int grid, int stages) {
+    g_force_grid = grid;
+    g_force_stages = stages;
+}
+
+int stage_capacity(int stage_bytes) {
+    const int ns = RING_BYTES / stage_bytes;
+    return ns < MAX_STAGES ? ns : MAX_STAGES;
+}
+
+TuneKey tune_key_single(const Params& P) {
+    return TuneKey{0, P.b_kmajor, P.out_mode, P.stage_bytes, P.n, P.ntiles * P.mhalves};
+}
+
+TuneKey tune_key_grouped(int b_kmajor, int out_mode, long long total) {
+    return TuneKey{1, b_kmajor, out_mode, MAXA * A_TILE_BYTES + MAXB * B_TILE_BYTES, 0, total};
+}
+
+void tune_put(const TuneKey& k, const TuneVal& v) {
+    ++g_tune_gen;
+    for (auto& e : g_tune)
+        if (same(e.first, k)) {
+            e.second = v;
+            return;
+        }
+    g_tune.emplace_back(k, v);
+}
+
+int tune_count() { return (int)g_tune.size(); }
+
+bool tune_entry(int i, TuneKey* k, TuneVal* v) {
+    if (i < 0 || i >= (int)g_tune.size()) return false;
+    *k = g_tune[i].first;
+    *v = g_tune[i].second;
+    return true;
+}
+
+void tune_clear() {
+    g_tune.clear();
+    ++g_tune_gen;
+}
+
+unsigned tune_generation() { return g_tune_gen; }
+
+void tune_record(bool on) {
+    g_recording = on;
+    if (on) g_rec.clear();
+}
+
+std::vector<std::pair<int, int>> tune_candidates(long long total, int stage_bytes) {
+    const long long sms = num_sms();
+    std::vector<long long> grids;
+    auto add = [&](long long g) {
+        if (g > total) g = total;
+        if (g < 1) g = 1;
+        for (long long x : grids)
+            if (x == g) return;
+        grids.push_back(g);
+    };
+    add(sms);
+    const long long waves = (total + sms - 1) / sms;
+    add((total + waves - 1) / waves);   // the same number of waves, tiles dealt evenly
+    add(sms - sms / 8);
+    add(sms * 3 / 4);
+    std::vector<std::pair<int, int>> c;
+    const int cap = stage_capacity(stage_bytes);
+    for (long long g : grids)
+        for (int st = 2; st <= cap; ++st) c.emplace_back((int)g, st);
+    if (cap < 2)
+        for (long long g : grids) c.emplace_back((int)g, cap);
+    return c;
+}
+
 int launch(const Params& P0, cudaStream_t s, double bytes, double flops) {
     if (int st = set_attrs()) return st;
     Params P = P0;
     set_ring(P);
     const long long total = P.ntiles * P.mhalves;
-    long long grid = total < num_sms() ? total : num_sms();
-    if (grid < 1) grid = 1;
+    long long grid;
+    choose(tune_key_single(P), total, stage_capacity(P.stage_bytes), &grid, &P.nstages);
+    if (g_recording) g_rec.push_back(Rec{tune_key_single(P), P, nullptr, nullptr, 0, total, nullptr});
     void* tok = stats_tc_begin(s, TFDE_KIND_SPLIT);
     launch_instance<false>(P.b_kmajor, P.out_mode, (unsigned)grid, s, P, nullptr, nullptr, 0, nullptr);
     cudaError_t e = cudaGetLastError();
@@ -295,12 +414,14 @@ int launch_grouped(const Params* groups, const long long* gstart, int ngroups, l
     // the largest stage any group may need: two operator terms, two planes
     p0.stage_b_off = MAXA * A_TILE_BYTES;
     p0.stage_bytes = p0.stage_b_off + MAXB * B_TILE_BYTES;
-    p0.nstages = RING_BYTES / p0.stage_bytes;
     p0.b_kmajor = b_kmajor;
     p0.out_mode = out_mode;
     p0.err = err;
     p0.skip = skip;
-    long long grid = total < num_sms() ? total : num_sms();
+    long long grid;
+    choose(tune_key_grouped(b_kmajor, out_mode, total), total, stage_capacity(p0.stage_bytes), &grid, &p0.nstages);
+    if (g_recording)
+        g_rec.push_back(Rec{tune_key_grouped(b_kmajor, out_mode, total), p0, groups, gstart, ngroups, total, gactive});
     void* tok = stats_tc_begin(s, TFDE_KIND_SPLIT);
     launch_instance<true>(b_kmajor, out_mode, (unsigned)grid, s, p0, groups, gstart, ngroups, gactive);
     cudaError_t e = cudaGetLastError();
@@ -308,6 +429,96 @@ int launch_grouped(const Params* groups, const long long* gstart, int ngroups, l
     if (e != cudaSuccess)
         return set_error(TFDE_ECUDA, std::string("grouped axis_gemm_kernel launch: ") + cudaGetErrorString(e));
     return TFDE_OK;
+}
+
+int tune_export(tfde_tune_entry* out, int cap, int* count) {
+    int k = 0;
+    for (const auto& e : g_tune) {
+        if (k >= cap) break;
+        tfde_tune_entry& t = out[k++];
+        t.grouped = e.first.grouped;
+        t.kmajor = e.first.kmajor;
+        t.out_mode = e.first.out_mode;
+        t.stage_bytes = e.first.stage_bytes;
+        t.n = e.first.n;
+        t.tiles = e.first.tiles;
+        t.grid = e.second.grid;
+        t.stages = e.second.stages;
+        t.us = e.second.us;
+        t.us_default = e.second.us_default;
+    }
+    if (count) *count = k;
+    return TFDE_OK;
+}
+
+int tune_import(const tfde_tune_entry* in, int count) {
+    for (int i = 0; i < count; ++i) {
+        const tfde_tune_entry& t = in[i];
+        if (t.grid < 1 || t.stages < 1 || t.stages > MAX_STAGES || t.stage_bytes < 1 || t.tiles < 1 ||
+            t.stage_bytes * t.stages > RING_BYTES || t.out_mode < OUT_F32 || t.out_mode > OUT_HI)
+            return set_error(TFDE_EINVAL, "tfde_tune_set: entry " + std::to_string(i) + " out of range");
+    }
+    for (int i = 0; i < count; ++i) {
+        const tfde_tune_entry& t = in[i];
+        tune_put(TuneKey{t.grouped, t.kmajor, t.out_mode, t.stage_bytes, t.n, t.tiles},
+                 TuneVal{t.grid, t.stages, t.us, t.us_default});
+    }
+    return TFDE_OK;
+}
+
+int tune_recorded(int reps, cudaStream_t s) {
+    if (reps < 1) return set_error(TFDE_EINVAL, "reps must be >= 1");
+    std::vector<Rec> recs;
+    for (const Rec& r : g_rec) {   // one trial set per launch class
+        bool seen = false;
+        for (const Rec& q : recs) seen = seen || same(q.key, r.key);
+        if (!seen) recs.push_back(r);
+    }
+    g_rec.clear();
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return set_error(TFDE_ECUDA, "event creation failed");
+    int st = TFDE_OK;
+    for (const Rec& r : recs) {
+        const int cap = stage_capacity(r.p0.stage_bytes);
+        const long long dgrid = r.total < num_sms() ? r.total : num_sms();
+        std::vector<std::pair<int, int>> cand = tune_candidates(r.total, r.p0.stage_bytes);
+        TuneVal best{(int)dgrid, cap, 1e30f, 0.f};
+        for (size_t c = 0; c < cand.size() && !st; ++c) {
+            Params P = r.p0;
+            const int grid = cand[c].first;
+            P.nstages = cand[c].second;
+            auto go = [&]() {
+                if (r.key.grouped)
+                    launch_instance<true>(r.key.kmajor, r.key.out_mode, (unsigned)grid, s, P, r.groups, r.gstart,
+                                          r.ngroups, r.gactive);
+                else
+                    launch_instance<false>(P.b_kmajor, P.out_mode, (unsigned)grid, s, P, nullptr, nullptr, 0, nullptr);
+            };
+            go();
+            cudaEventRecord(e0, s);
+            for (int i = 0; i < reps; ++i) go();
+            cudaEventRecord(e1, s);
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess ||
+                cudaGetLastError() != cudaSuccess) {
+                st = set_error(TFDE_ECUDA, "autotuner trial launch failed");
+                break;
+            }
+            const float us = 1e3f * ms / reps;
+            if (grid == dgrid && P.nstages == cap) best.us_default = us;
+            if (us < best.us) {
+                best.us = us;
+                best.grid = grid;
+                best.stages = P.nstages;
+            }
+        }
+        if (st) break;
+        tune_put(r.key, best);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
 }
 
 // Self-test of the bounded-wait path shared by the tensor-core kernels: one

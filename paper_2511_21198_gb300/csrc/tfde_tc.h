@@ -4,6 +4,9 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <utility>
+#include <vector>
+
 #include "tfde_tc_kernel.cuh"
 
 namespace tfde {
@@ -35,6 +38,44 @@ int wait_selftest(long long limit_ns, int* tmem_freed, cudaStream_t s);
 int launch_grouped(const Params* groups, const long long* gstart, int ngroups, long long total, int b_kmajor,
                    int out_mode, const int* gactive, int* err, cudaStream_t s, double bytes, double flops,
                    const int* skip = nullptr);
+
+// Launch parameters chosen by the autotuner (tfde_tune, tfde_batch_tune):
+// the number of persistent CTAs and of ring stages, per launch class.  A
+// class is the kernel instance (grouped, operand layout, output mode), the
+// stage size, the rows n of the contraction (0 for grouped launches) and the
+// number of 128 x 256 tiles of the launch.
+struct TuneKey {
+    int grouped, kmajor, out_mode, stage_bytes, n;
+    long long tiles;
+};
+struct TuneVal {
+    int grid, stages;
+    float us, us_default;
+};
+// While set (grid > 0), every launch uses these values (the tuner's trials).
+void tune_force(int grid, int stages);
+// The class of a single launch with descriptor P (after set_ring) / of a grouped launch.
+TuneKey tune_key_single(const Params& P);
+TuneKey tune_key_grouped(int b_kmajor, int out_mode, long long total);
+int stage_capacity(int stage_bytes);
+void tune_put(const TuneKey& k, const TuneVal& v);
+int tune_count();
+// entries in insertion order
+bool tune_entry(int i, TuneKey* k, TuneVal* v);
+void tune_clear();
+// Candidate (grid, stages) pairs of a launch class: the persistent grid at
+// the SM count, the grid that deals the tiles evenly, and two smaller ones;
+// 2 .. capacity ring stages.
+std::vector<std::pair<int, int>> tune_candidates(long long total, int stage_bytes);
+// Changes whenever the table changes (graphs captured before hold stale
+// launch parameters and are rebuilt).
+unsigned tune_generation();
+// While recording, launch() and launch_grouped() also keep their arguments;
+// tune_recorded then times every candidate of each recorded class (reps
+// launches between CUDA events on s, after one warm-up launch) and keeps the
+// fastest in the table.
+void tune_record(bool on);
+int tune_recorded(int reps, cudaStream_t s);
 
 }  // namespace tc
 }  // namespace tfde

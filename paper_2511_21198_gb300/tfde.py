@@ -50,6 +50,14 @@ class tfde_spectrum_info(Structure):
                 ("varsigma", c_double), ("omega", c_double), ("omega_est", c_double)]
 
 
+class tfde_tune_entry(Structure):
+    _fields_ = [("grouped", c_int), ("kmajor", c_int), ("out_mode", c_int), ("stage_bytes", c_int), ("n", c_int),
+                ("tiles", c_longlong), ("grid", c_int), ("stages", c_int), ("us", c_float), ("us_default", c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class tfde_stats(Structure):
     _fields_ = [("kernel_launches", ctypes.c_ulonglong), ("kind", tfde_kernel_stats * 4)]
 
@@ -70,7 +78,8 @@ EXPORTS = ["tfde_assemble", "tfde_destroy", "tfde_matvec", "tfde_precond", "tfde
            "tfde_stats_reset", "tfde_stats_get", "tfde_mass_apply_noalloc", "tfde_batch_create", "tfde_batch_destroy",
            "tfde_batch_count", "tfde_batch_set_guess_order", "tfde_batch_cn_advance", "tfde_cn_advance_guess", "tfde_cnn_create", "tfde_cnn_destroy",
            "tfde_cnn_set_params", "tfde_cnn_get_params", "tfde_cnn_get_grads", "tfde_cnn_predict", "tfde_cnn_accumulate", "tfde_cnn_predict_hist", "tfde_cnn_accumulate_hist",
-           "tfde_cnn_adam_step", "tfde_selftest_wait", "tfde_set_device_loop", "tfde_spectrum", "tfde_last_error", "tfde_version"]
+           "tfde_cnn_adam_step", "tfde_selftest_wait", "tfde_set_device_loop", "tfde_spectrum", "tfde_tune", "tfde_batch_tune",
+           "tfde_tune_get", "tfde_tune_set", "tfde_tune_clear", "tfde_last_error", "tfde_version"]
 
 
 def load(path: str | None = None):
@@ -121,6 +130,11 @@ def load(path: str | None = None):
         "tfde_selftest_wait": ([c_longlong, POINTER(c_int), vp], c_int),
         "tfde_set_device_loop": ([vp, c_int], c_int),
         "tfde_spectrum": ([POINTER(tfde_params), c_int, vp, POINTER(tfde_spectrum_info), vp], c_int),
+        "tfde_tune": ([vp, c_int, vp], c_int),
+        "tfde_batch_tune": ([vp, c_int, vp], c_int),
+        "tfde_tune_get": ([POINTER(tfde_tune_entry), c_int, POINTER(c_int)], c_int),
+        "tfde_tune_set": ([POINTER(tfde_tune_entry), c_int], c_int),
+        "tfde_tune_clear": ([], c_int),
         "tfde_last_error": ([], c_char_p),
         "tfde_version": ([], c_char_p),
     }
@@ -288,6 +302,62 @@ def tfde_selftest_wait(limit_ns: int, stream=None) -> tuple[int, int]:
     freed = c_int(0)
     st = load().tfde_selftest_wait(int(limit_ns), ctypes.byref(freed), _stream(stream))
     return st, freed.value
+
+
+def tfde_tune(prob: int, reps: int = 20, stream=None) -> None:
+    _check(load().tfde_tune(prob, reps, _stream(stream)), "tfde_tune")
+
+
+def tfde_batch_tune(batch: int, reps: int = 20, stream=None) -> None:
+    _check(load().tfde_batch_tune(batch, reps, _stream(stream)), "tfde_batch_tune")
+
+
+def tfde_tune_get() -> list[dict]:
+    """The autotuner's table as a list of dicts (the tfde_tune_entry fields)."""
+    cnt = c_int(0)
+    arr = (tfde_tune_entry * 4096)()
+    _check(load().tfde_tune_get(arr, 4096, byref(cnt)), "tfde_tune_get")
+    return [arr[i].as_dict() for i in range(cnt.value)]
+
+
+def tfde_tune_set(entries: list[dict]) -> None:
+    arr = (tfde_tune_entry * max(len(entries), 1))()
+    for i, e in enumerate(entries):
+        for k, _ in tfde_tune_entry._fields_:
+            setattr(arr[i], k, e[k])
+    _check(load().tfde_tune_set(arr, len(entries)), "tfde_tune_set")
+
+
+def tfde_tune_clear() -> None:
+    _check(load().tfde_tune_clear(), "tfde_tune_clear")
+
+
+def save_tuning(path: str, gpu_name: str) -> None:
+    """Write the autotuner's table to a JSON cache, under this GPU's name
+    (other GPUs' entries in the file are kept)."""
+    import json
+    cache = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            cache = json.load(f)
+    cache[gpu_name] = tfde_tune_get()
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1)
+    os.replace(tmp, path)
+
+
+def load_tuning(path: str, gpu_name: str) -> int:
+    """Apply the cached table of this GPU from a JSON cache; returns the
+    number of entries applied (0 when the file or the GPU is absent)."""
+    import json
+    if not os.path.exists(path):
+        return 0
+    with open(path) as f:
+        entries = json.load(f).get(gpu_name, [])
+    if entries:
+        tfde_tune_set(entries)
+    return len(entries)
 
 
 def tfde_last_error() -> str:

@@ -65,3 +65,32 @@ def test_host_validation(lib, bad):
     with pytest.raises(lib.TfdeError) as e:
         lib.tfde_host_coefficients(p, 0)
     assert e.value.status == lib.TFDE_EINVAL
+
+
+def test_tune_table_round_trip_on_the_host(lib, tmp_path):
+    """The autotuner's table is host state: entries set, read back, replaced
+    per launch class, rejected when out of range, cached as JSON per GPU
+    name and applied again (no GPU work)."""
+    lib.load()
+    lib.tfde_tune_clear()
+    e1 = dict(grouped=0, kmajor=1, out_mode=3, stage_bytes=49152, n=256, tiles=512, grid=128, stages=3,
+              us=15.5, us_default=16.25)
+    e2 = dict(grouped=1, kmajor=0, out_mode=1, stage_bytes=98304, n=0, tiles=1024, grid=152, stages=2,
+              us=60.0, us_default=60.0)
+    lib.tfde_tune_set([e1, e2])
+    got = lib.tfde_tune_get()
+    assert got == [e1, e2]
+    lib.tfde_tune_set([dict(e1, grid=144, stages=4)])          # same class: replaced, not added
+    got = lib.tfde_tune_get()
+    assert len(got) == 2 and got[0]["grid"] == 144 and got[0]["stages"] == 4
+    with pytest.raises(lib.TfdeError) as e:
+        lib.tfde_tune_set([dict(e2, stages=3)])                # 3 x 96 KB exceeds the 192 KB ring
+    assert e.value.status == lib.TFDE_EINVAL
+    path = str(tmp_path / "tuning.json")
+    lib.save_tuning(path, "GPU A")
+    lib.tfde_tune_clear()
+    assert lib.tfde_tune_get() == []
+    assert lib.load_tuning(path, "GPU B") == 0
+    assert lib.load_tuning(path, "GPU A") == 2
+    assert lib.tfde_tune_get() == got
+    lib.tfde_tune_clear()
