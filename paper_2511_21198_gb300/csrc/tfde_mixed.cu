@@ -110,7 +110,7 @@ void gemm_params(const tfde_problem* P, int axis, const SegSpec* segs, int nseg,
         prm.out_hi = M->hi[out_plane];
         prm.out_lo = M->lo[out_plane];
         prm.omap_hi = M->omap_hi[out_plane][axis];
-        prm.omap_lo = M->omap_lo[out_plane][axis];
+        prm.omap_hl = M->omap_hl[out_plane][axis];
     }
     if (lam_scale) {
         const long long n1n2 = (long long)P->n[0] * P->n[1];
@@ -889,7 +889,7 @@ int mixed_init(tfde_problem* P, cudaStream_t s) {
             M->bmap2_rank[pl][a] = tc::make_map_B_pair(&M->bmap2[pl][a], M->hi[pl], P->n, a);
             M->bmap1_rank[pl][a] = tc::make_map_B_pair(&M->bmap1[pl][a], M->hi[pl], P->n, a, 1);
             if ((st = tc::make_out_map(&M->omap_hi[pl][a], M->hi[pl], P->n, a, false)) ||
-                (st = tc::make_out_map(&M->omap_lo[pl][a], M->lo[pl], P->n, a, false)))
+                (st = tc::make_out_map_pair(&M->omap_hl[pl][a], M->hi[pl], P->n, a)))
                 return st;
         }
     }

@@ -126,7 +126,7 @@ struct MixedState {
     CUtensorMap bmap1[NPL][3];     // the hi plane alone, same box otherwise
     int bmap1_rank[NPL][3] = {};
     CUtensorMap omap_hi[NPL][3];   // the planes as outputs of the epilogue's tensor stores
-    CUtensorMap omap_lo[NPL][3];
+    CUtensorMap omap_hl[NPL][3];   // hi and lo as one tensor (lo = hi + N): one store per chunk
     float* f[NF] = {};
     float* lam = nullptr;   // [ra (n3) | rb (n3) | U (n1 n2) | V (n1 n2)]
     double* dsc = nullptr;  // device scalars

@@ -162,6 +162,27 @@ int make_out_map(CUtensorMap* m, const void* base, const int n[3], int axis, boo
     return encode(m, base, 3, dims, strides, box, f32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, dt);
 }
 
+// The hi plane at base and the lo plane N elements after it as one tensor
+// with a last dimension of 2: one tensor store writes a chunk of both.
+int make_out_map_pair(CUtensorMap* m, const void* base, const int n[3], int axis) {
+    const cuuint64_t n1 = n[0], n2 = n[1], n3 = n[2];
+    const cuuint64_t N = n1 * n2 * n3;
+    const CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    if (axis == 0) {
+        const cuuint64_t dims[3] = {n1, n2 * n3, 2};
+        const cuuint64_t strides[2] = {n1 * 2, N * 2};
+        const cuuint32_t box[3] = {32, 32, 2};
+        return encode(m, base, 3, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE, dt);
+    }
+    cuuint64_t C, K, P;
+    if (axis == 1) { C = n1; K = n2; P = n3; }
+    else { C = n1 * n2; K = n3; P = 1; }
+    const cuuint64_t dims[4] = {C, K, P, 2};
+    const cuuint64_t strides[3] = {C * 2, C * K * 2, N * 2};
+    const cuuint32_t box[4] = {32, 32, 1, 2};
+    return encode(m, base, 4, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B, dt);
+}
+
 // Ring geometry of a launch from its segments: A terms at the start of a
 // stage, B planes after the largest A region, as many stages as fit.
 void set_ring(Params& P) {

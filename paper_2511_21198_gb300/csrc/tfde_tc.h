@@ -22,6 +22,8 @@ int encode_map(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dim
 int make_map_A(CUtensorMap* m, const __nv_bfloat16* base, int n);
 int make_split_map_A(CUtensorMap* m, const __nv_bfloat16* base, int n);
 int make_out_map(CUtensorMap* m, const void* base, const int n[3], int axis, bool f32);
+// the split-plane pair (hi at base, lo N elements after it) as one output tensor
+int make_out_map_pair(CUtensorMap* m, const void* base, const int n[3], int axis);
 void set_ring(Params& P);
 int make_map_B(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis);
 int make_map_B_box(CUtensorMap* m, const __nv_bfloat16* base, const int n[3], int axis, int box_lines);

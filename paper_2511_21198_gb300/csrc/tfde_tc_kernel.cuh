@@ -85,7 +85,7 @@ struct Params {
     // output tensor maps (box 32 x 32): FP32 vector, hi plane, lo plane;
     // x axis: {n1, lines}, no swizzle; y/z axes: {C, n, P}, 128B (FP32) /
     // 64B (BF16) swizzle
-    CUtensorMap omap_f32, omap_hi, omap_lo;
+    CUtensorMap omap_f32, omap_hi, omap_hl;   // FP32 output, hi plane, hi and lo planes as one tensor
     Segment seg[MAXSEG];
     int nseg;
     int b_kmajor;        // 1: B stored with k contiguous (x axis); 0: lines contiguous (y, z axes)
@@ -427,6 +427,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int q = warp & 3;               // TMEM lane quadrant this warp may access
         const int half = ew >> 2;             // which 128 of the 256 columns
         uint8_t* slot = epi + ew * EPI_SLOT_BYTES;
+        // the hi-plane output (one 2 KB chunk) alternates between the two
+        // halves of the slot, so that a chunk is converted while the previous
+        // chunk's store still reads the other half
+        int half_sel = 0;
         long long it = 0;
         bool pending = false;                 // a store of this warp may still read the slot
         DotAcc da;                            // fused inner product (single launches only)
@@ -566,12 +570,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         da.add(acc);
                     }
                 }
-                // the slot is free once this warp's previous stores have read it
-                if (pending && lane == 0) bulk_wait_read0();
+                // the slot is free once this warp's previous stores have read
+                // it (the hi-only output: the store before the previous one)
+                if (pending && lane == 0) {
+                    if constexpr (OM == OUT_HI) bulk_wait_read1();
+                    else bulk_wait_read0();
+                }
                 __syncwarp();
                 auto store = [&](const CUtensorMap* map, const uint8_t* src) {
                     if (b_kmajor) tma_store_2d(map, src, mrow0, (int)line0);
                     else tma_store_3d(map, src, cx, mrow0, pl);
+                };
+                // both split planes of the chunk (hi at src, lo 2 KB after it) in one store
+                auto store_pair = [&](const CUtensorMap* map, const uint8_t* src) {
+                    if (b_kmajor) tma_store_3d(map, src, mrow0, (int)line0, 0);
+                    else tma_store_4d(map, src, cx, mrow0, pl, 0);
                 };
                 if constexpr (OM == OUT_F32 || OM == OUT_XPAY) {
                     slot_f32<KM != 0>(slot, lane, v);
@@ -588,13 +601,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     __syncwarp();
                 }
                 if constexpr (OM != OUT_F32) {
-                    if constexpr (OM == OUT_HI) slot_bf16<KM != 0>(slot, lane, v);
-                    else slot_bf16_pair<KM != 0>(slot, slot + 2048, lane, v);
+                    uint8_t* hs = slot;
+                    if constexpr (OM == OUT_HI) {
+                        hs = slot + half_sel * 2048;
+                        half_sel ^= 1;
+                        slot_bf16<KM != 0>(hs, lane, v);
+                    } else {
+                        slot_bf16_pair<KM != 0>(slot, slot + 2048, lane, v);
+                    }
                     fence_proxy_async_smem();
                     __syncwarp();
                     if (lane == 0) {
-                        store(&p.omap_hi, slot);
-                        if constexpr (OM != OUT_HI) store(&p.omap_lo, slot + 2048);
+                        if constexpr (OM == OUT_HI) store(&p.omap_hi, hs);
+                        else store_pair(&p.omap_hl, slot);
                         bulk_commit();
                     }
                     pending = true;
