@@ -104,17 +104,67 @@ struct Pass {
     const void* pre;    // R2[n]: DST phases w_j
     double dst_scale;   // sqrt(2 / (n + 1))
     const double* lam;  // MODE_DST2: [mass x | y | z | tau x | y | z]
+    const float* lamf;  // the same in FP32 (the FP32 passes form Lambda in FP32)
     double c0, c1, c2;  // MODE_DST2: eta_a (k+ + k-)
     int half_power;     // MODE_DST2: divide by Lambda^{1/2} instead of Lambda (P^{-1/2})
 };
 
-__device__ __forceinline__ long long line_offset(const Pass& p, long long l) {
-    if (p.axis == 0) return l * p.n1;
-    if (p.axis == 1) return (l % p.n1) + (l / p.n1) * (long long)p.n1 * p.n2;
-    return l;
-}
 __device__ __forceinline__ long long axis_stride(const Pass& p) {
     return p.axis == 0 ? 1LL : (p.axis == 1 ? (long long)p.n1 : (long long)p.n1 * p.n2);
+}
+
+// Offsets of the block's lines l0 + g, g < G, without a 64-bit division per
+// element: along y a line is (i, q) = (l % n1, l / n1), taken from the
+// block's first line by a carry.
+struct LineMap {
+    long long l0;
+    unsigned i0;
+    long long q0;
+};
+__device__ __forceinline__ LineMap line_map(const Pass& p, long long l0) {
+    LineMap m;
+    m.l0 = l0;
+    m.i0 = 0;
+    m.q0 = 0;
+    if (p.axis == 1) {
+        m.i0 = (unsigned)(l0 % p.n1);
+        m.q0 = l0 / p.n1;
+    }
+    return m;
+}
+__device__ __forceinline__ long long line_off(const Pass& p, const LineMap& m, int g) {
+    if (p.axis == 0) return (m.l0 + g) * (long long)p.n1;
+    if (p.axis == 2) return m.l0 + g;
+    unsigned i = m.i0 + (unsigned)g;
+    long long q = m.q0;
+    if (i >= (unsigned)p.n1) {
+        q += i / (unsigned)p.n1;
+        i %= (unsigned)p.n1;
+    }
+    return (long long)i + q * (long long)p.n1 * p.n2;
+}
+// element e of the block's (line g, position j < n) rows: along x j runs
+// fastest (a 32-bit division by n), along y / z g does
+__device__ __forceinline__ void row_index(int axis, int e, int lgG, int n, int* g, int* j) {
+    if (axis == 0) {
+        *g = (int)((unsigned)e / (unsigned)n);
+        *j = e - *g * n;
+    } else {
+        *g = e & ((1 << lgG) - 1);
+        *j = e >> lgG;
+    }
+}
+// element e of the block's (line g, position j) grid with j < 2^lgJ: along x
+// the lines are contiguous, so j runs fastest; along y and z consecutive
+// lines are adjacent in memory, so g runs fastest
+__device__ __forceinline__ void grid_index(int axis, int e, int lgG, int lgJ, int* g, int* j) {
+    if (axis == 0) {
+        *g = e >> lgJ;
+        *j = e & ((1 << lgJ) - 1);
+    } else {
+        *g = e & ((1 << lgG) - 1);
+        *j = e >> lgG;
+    }
 }
 
 // Forward DFT of the block's complex lines in place (stride ls between lines).
@@ -214,19 +264,6 @@ __device__ __forceinline__ void block_spectral_scale(typename C2<R>::T* buf, int
 
 enum { MODE_TOEPLITZ = 0, MODE_DST = 1, MODE_DST2 = 2 };
 
-// Element e of the block's (line g, position j) grid, j < jmax: lines along
-// x are contiguous, so j runs fastest there; along y and z consecutive lines
-// are adjacent in memory, so g runs fastest.
-__device__ __forceinline__ void split_index(int axis, int e, int lgG, int G, int jmax, int* g, int* j) {
-    if (axis == 0) {
-        *g = e / jmax;
-        *j = e - *g * jmax;
-    } else {
-        *g = e & (G - 1);
-        *j = e >> lgG;
-    }
-}
-
 template <typename R, int MODE>
 __global__ void __launch_bounds__(NT) fft_pass_kernel(const Pass p) {
     using T2 = typename C2<R>::T;
@@ -248,13 +285,15 @@ __global__ void __launch_bounds__(NT) fft_pass_kernel(const Pass p) {
     const T2* __restrict__ spec = static_cast<const T2*>(p.spec);
     const T2* __restrict__ pre = static_cast<const T2*>(p.pre);
 
+    const LineMap lm = line_map(p, l0);
+
     // ---- load (zero padding beyond n and beyond the last line)
     for (int e = threadIdx.x; e < G * L; e += NT) {
         int g, j;
-        split_index(p.axis, e, lgG, G, L, &g, &j);
+        grid_index(p.axis, e, lgG, lg, &g, &j);
         const long long l = l0 + g;
         R v = R(0);
-        if (j < n && l < p.lines) v = in0[line_offset(p, l) + j * st];
+        if (j < n && l < p.lines) v = in0[line_off(p, lm, g) + j * st];
         if constexpr (MODE == MODE_TOEPLITZ) {
             T2* q = buf + (size_t)(g >> 1) * ls + j;
             if (g & 1) q->y = v; else q->x = v;
@@ -277,7 +316,7 @@ __global__ void __launch_bounds__(NT) fft_pass_kernel(const Pass p) {
         if (out1) {
             for (int e = threadIdx.x; e < G * n; e += NT) {
                 int g, j;
-                split_index(p.axis, e, lgG, G, n, &g, &j);
+                row_index(p.axis, e, lgG, n, &g, &j);
                 const long long l = l0 + g;
                 if (l >= p.lines) continue;
                 const T2* q = buf + (size_t)(g >> 1) * ls + j;
@@ -285,7 +324,7 @@ __global__ void __launch_bounds__(NT) fft_pass_kernel(const Pass p) {
                 R nb = R(0);
                 if (j > 0) nb += (g & 1) ? q[-1].y : q[-1].x;
                 if (j + 1 < n) nb += (g & 1) ? q[1].y : q[1].x;
-                out1[line_offset(p, l) + j * st] = fma(R(0.75), c, R(0.125) * nb);
+                out1[line_off(p, lm, g) + j * st] = fma(R(0.75), c, R(0.125) * nb);
             }
         }
         __syncthreads();
@@ -303,9 +342,13 @@ __global__ void __launch_bounds__(NT) fft_pass_kernel(const Pass p) {
         const double* ty = tx + p.n1;
         const double* tz = ty + p.n2;
         const R s = (R)p.dst_scale;
+        // lines along z: l = i + n1 j, taken from the block's first line by a carry
+        const unsigned i0 = (unsigned)(l0 % p.n1);
+        const long long j0 = l0 / p.n1;
+        const float fc0 = (float)p.c0, fc1 = (float)p.c1, fc2 = (float)p.c2;
         for (int e = threadIdx.x; e < G * L; e += NT) {
             int g, k;
-            split_index(p.axis, e, lgG, G, L, &g, &k);
+            grid_index(p.axis, e, lgG, lg, &g, &k);
             T2* q = buf + (size_t)g * ls + k;
             T2 w;
             w.x = R(0);
@@ -315,10 +358,31 @@ __global__ void __launch_bounds__(NT) fft_pass_kernel(const Pass p) {
                 const T2 ph = __ldg(pre + k);
                 const T2 r = *q;   // conj of the product: (r.x, -r.y)
                 const R t = s * (ph.y * r.x - ph.x * r.y);
-                const int i = (int)(l % p.n1), jy = (int)(l / p.n1);
-                const double lam = mz[k] * my[jy] * mx[i] + p.c0 * mz[k] * my[jy] * tx[i] +
-                                   p.c1 * mz[k] * ty[jy] * mx[i] + p.c2 * tz[k] * my[jy] * mx[i];
-                const R u = (R)((double)t / (p.half_power ? sqrt(lam) : lam));
+                unsigned i = i0 + (unsigned)g;
+                int jy = (int)j0;
+                if (i >= (unsigned)p.n1) {
+                    jy += (int)(i / (unsigned)p.n1);
+                    i %= (unsigned)p.n1;
+                }
+                R u;
+                if constexpr (sizeof(R) == 4) {
+                    // Lambda = mz (my (mx + c0 tx) + c1 ty mx) + tz c2 my mx, in FP32
+                    const float* fx = p.lamf;
+                    const float* fy = fx + p.n1;
+                    const float* fz = fy + p.n2;
+                    const float* gx = fz + p.n3;
+                    const float* gy = gx + p.n1;
+                    const float* gz = gy + p.n2;
+                    const float mxi = __ldg(fx + i), myj = __ldg(fy + jy);
+                    const float U = fmaf(myj, fmaf(fc0, __ldg(gx + i), mxi), fc1 * __ldg(gy + jy) * mxi);
+                    const float V = fc2 * myj * mxi;
+                    const float lam = fmaf(__ldg(fz + k), U, __ldg(gz + k) * V);
+                    u = (R)(t / (p.half_power ? sqrtf(lam) : lam));
+                } else {
+                    const double lam = mz[k] * my[jy] * mx[i] + p.c0 * mz[k] * my[jy] * tx[i] +
+                                       p.c1 * mz[k] * ty[jy] * mx[i] + p.c2 * tz[k] * my[jy] * mx[i];
+                    u = (R)((double)t / (p.half_power ? sqrt(lam) : lam));
+                }
                 w.x = ph.x * u;
                 w.y = ph.y * u;
             }
@@ -333,10 +397,10 @@ __global__ void __launch_bounds__(NT) fft_pass_kernel(const Pass p) {
     // ---- store
     for (int e = threadIdx.x; e < G * n; e += NT) {
         int g, j;
-        split_index(p.axis, e, lgG, G, n, &g, &j);
+        row_index(p.axis, e, lgG, n, &g, &j);
         const long long l = l0 + g;
         if (l >= p.lines) continue;
-        const long long o = line_offset(p, l) + j * st;
+        const long long o = line_off(p, lm, g) + j * st;
         R v;
         if constexpr (MODE == MODE_TOEPLITZ) {
             const T2 q = buf[(size_t)(g >> 1) * ls + j];
@@ -500,6 +564,14 @@ int init(tfde_problem* P, cudaStream_t s) {
             F->dst_scale[a] = std::sqrt(2.0 / (n + 1));
         }
     }
+    {   // the eigenvalue arrays of Lambda in FP32, layout [mass x | y | z | tau x | y | z]
+        std::vector<float> lf;
+        for (int a = 0; a < 3; ++a)
+            for (double v : P->lam_mass[a]) lf.push_back((float)v);
+        for (int a = 0; a < 3; ++a)
+            for (double v : P->lam_tau[a]) lf.push_back((float)v);
+        if (int st = dcopy(&F->lamf, lf, s)) return st;
+    }
     return TFDE_OK;
 }
 
@@ -518,6 +590,7 @@ void free_state(tfde_problem* P) {
     }
     rel(F->Ghat[0]);
     rel(F->Ghat[1]);
+    cudaFree(F->lamf);
     delete F;
     P->fft = nullptr;
 }
@@ -597,6 +670,7 @@ int dst_pass(const tfde_problem* P, int axis, const R* in, R* out, bool lambda_p
     p.out0 = out;
     if (lambda_pair) {
         p.lam = P->lam;
+        p.lamf = F->lamf;
         p.c0 = P->csum[0];
         p.c1 = P->csum[1];
         p.c2 = P->csum[2];

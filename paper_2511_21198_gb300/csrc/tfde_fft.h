@@ -26,6 +26,7 @@ struct State {
     Table pre[3];       // DST phases exp(i pi j^2 / (2(n+1))), j = 1..n
     Table chirp[3];     // spectrum / L of the chirp exp(-i pi m^2 / (2(n+1)))
     double dst_scale[3] = {0, 0, 0};
+    float* lamf = nullptr;   // the mass and tau eigenvalues of every axis in FP32 (as tfde_problem::lam)
 };
 
 bool available(const int n[3]);
