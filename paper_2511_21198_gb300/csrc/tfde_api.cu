@@ -34,6 +34,7 @@ int mixed_apply_Pinv(const tfde_problem*, const double*, double*, cudaStream_t);
 int mixed_pcg(tfde_problem*, const double*, double*, double, int, tfde_info*, cudaStream_t, bool);
 int mixed_pgmres(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t, bool);
 int mixed_set_device_loop(tfde_problem*, int);
+int mixed_set_spectral(tfde_problem*, int);
 int spectrum(const tfde_params*, int, const double*, tfde_spectrum_info*, cudaStream_t);
 int mixed_tune(tfde_problem*, int, cudaStream_t);
 int batch_tune(tfde_batch*, int, cudaStream_t);
@@ -345,6 +346,11 @@ int tfde_spectrum(const tfde_params* params, int steps, const double* v0, tfde_s
 int tfde_set_device_loop(tfde_problem* prob, int enable) {
     if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
     return mixed_set_device_loop(prob, enable);
+}
+
+int tfde_set_spectral_inner(tfde_problem* prob, int enable) {
+    if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
+    return mixed_set_spectral(prob, enable);
 }
 
 int tfde_tune(tfde_problem* prob, int reps, void* stream) {

@@ -169,6 +169,118 @@ __global__ __launch_bounds__(kT) void cg_update_r32_v4_kernel(long long N4, cons
     if (threadIdx.x == 0) atomicAdd(rr, t);
 }
 
+// ---------------------------------------------- inner PCG in the DST eigenbasis
+// Lambda(i, j, k) = ra[k] U[c] + rb[k] V[c], c = i + n1 j (Eq. (diag_tau_pre)):
+// the preconditioner is this diagonal once the vectors live in the
+// sine-transform eigenbasis.  Launched on a 2-D grid: x over the float4
+// groups of one z plane (n1 n2 is a multiple of 4), y over the planes.
+struct LamView {
+    const float* ra;
+    const float* rb;
+    const float4* U;
+    const float4* V;
+    long long nc4;   // n1 n2 / 4
+    int n3;
+};
+
+__device__ __forceinline__ float4 lam4(const LamView& L, float ra, float rb, long long c4) {
+    const float4 u = L.U[c4], v = L.V[c4];
+    return make_float4(fmaf(ra, u.x, rb * v.x), fmaf(ra, u.y, rb * v.y), fmaf(ra, u.z, rb * v.z),
+                       fmaf(ra, u.w, rb * v.w));
+}
+
+// alpha = num / den; r -= alpha q; *rz += <r, r / Lambda>; *rr += <r, r>
+__global__ __launch_bounds__(kT) void spec_update_kernel(LamView L, const double* __restrict__ num,
+                                                         const double* __restrict__ den, const float4* __restrict__ q,
+                                                         float4* __restrict__ r, double* __restrict__ rz,
+                                                         double* __restrict__ rr, double* __restrict__ alpha_out,
+                                                         const int* skip) {
+    if (skip && *skip) return;
+    __shared__ float s_alpha;
+    if (threadIdx.x == 0) {
+        const double a = num[0] / den[0];
+        s_alpha = (float)a;
+        if (blockIdx.x == 0 && blockIdx.y == 0) *alpha_out = (double)(float)a;
+    }
+    __syncthreads();
+    const float alpha = s_alpha;
+    KSum kz, kr;
+    for (int k = blockIdx.y; k < L.n3; k += gridDim.y) {
+        const float ra = L.ra[k], rb = L.rb[k];
+        for (long long c4 = (long long)blockIdx.x * kT + threadIdx.x; c4 < L.nc4; c4 += (long long)gridDim.x * kT) {
+            const long long i = (long long)k * L.nc4 + c4;
+            const float4 qv = q[i];
+            float4 v = r[i];
+            v.x = fmaf(-alpha, qv.x, v.x);
+            v.y = fmaf(-alpha, qv.y, v.y);
+            v.z = fmaf(-alpha, qv.z, v.z);
+            v.w = fmaf(-alpha, qv.w, v.w);
+            r[i] = v;
+            const float4 l = lam4(L, ra, rb, c4);
+            kz.add(v.x * (v.x / l.x));
+            kz.add(v.y * (v.y / l.y));
+            kz.add(v.z * (v.z / l.z));
+            kz.add(v.w * (v.w / l.w));
+            kr.add(v.x * v.x);
+            kr.add(v.y * v.y);
+            kr.add(v.z * v.z);
+            kr.add(v.w * v.w);
+        }
+    }
+    const double tz = block_sum64((double)kz.s - (double)kz.c);
+    const double tr = block_sum64((double)kr.s - (double)kr.c);
+    if (threadIdx.x == 0) {
+        atomicAdd(rz, tz);
+        atomicAdd(rr, tr);
+    }
+}
+
+// beta = num / den (0 when den is null); p = r / Lambda + beta p_old, written
+// in FP32 and as split planes (ph, pl); with rz: *rz += <r, r / Lambda>
+__global__ __launch_bounds__(kT) void spec_direction_kernel(LamView L, const double* __restrict__ num,
+                                                            const double* __restrict__ den,
+                                                            const float4* __restrict__ r,
+                                                            const float4* __restrict__ pold, float4* __restrict__ p,
+                                                            uint2* __restrict__ ph, uint2* __restrict__ pl,
+                                                            double* __restrict__ rz, const int* skip) {
+    if (skip && *skip) return;
+    __shared__ float s_beta;
+    if (threadIdx.x == 0) s_beta = den ? (float)(num[0] / den[0]) : 0.f;
+    __syncthreads();
+    const float beta = s_beta;
+    KSum kz;
+    for (int k = blockIdx.y; k < L.n3; k += gridDim.y) {
+        const float ra = L.ra[k], rb = L.rb[k];
+        for (long long c4 = (long long)blockIdx.x * kT + threadIdx.x; c4 < L.nc4; c4 += (long long)gridDim.x * kT) {
+            const long long i = (long long)k * L.nc4 + c4;
+            const float4 rv = r[i];
+            const float4 l = lam4(L, ra, rb, c4);
+            float4 z = make_float4(rv.x / l.x, rv.y / l.y, rv.z / l.z, rv.w / l.w);
+            if (rz) {
+                kz.add(rv.x * z.x);
+                kz.add(rv.y * z.y);
+                kz.add(rv.z * z.z);
+                kz.add(rv.w * z.w);
+            }
+            if (pold) {
+                const float4 o = pold[i];
+                z.x = fmaf(beta, o.x, z.x);
+                z.y = fmaf(beta, o.y, z.y);
+                z.z = fmaf(beta, o.z, z.z);
+                z.w = fmaf(beta, o.w, z.w);
+            }
+            p[i] = z;
+            const uint2 h = bf16x4_hi(z);
+            ph[i] = h;
+            pl[i] = bf16x4_lo(z, h);
+        }
+    }
+    if (rz) {
+        const double t = block_sum64((double)kz.s - (double)kz.c);
+        if (threadIdx.x == 0) atomicAdd(rz, t);
+    }
+}
+
 // d = (x32 when fold) + sum_j alpha_j p_j (FP32, in the order of the
 // directions, as the per-iteration update x += alpha p would form it); then
 // c64 = sc d and x64 += c64 (c64 set), x64 += sc d (x64 only), or acc32 = d
@@ -235,6 +347,30 @@ __global__ void pcg_combine_pow2_kernel(long long N4, CombineArgs a, const float
     }
 }
 
+// d = (x32 when fold) + sum_j alpha_j p_j as split planes (h, l) alone, four
+// elements at a time (the eigenbasis correction before its sine transform)
+__global__ void pcg_combine_split_kernel(long long N4, CombineArgs a, const float4* __restrict__ x32,
+                                         uint2* __restrict__ h, uint2* __restrict__ l) {
+    __shared__ float s_al[kPRing];
+    if (threadIdx.x < a.cnt) s_al[threadIdx.x] = (float)*a.alpha[threadIdx.x];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N4; i += (long long)gridDim.x * blockDim.x) {
+        float4 d = a.fold ? x32[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < kPRing; ++t)
+            if (t < a.cnt) {
+                const float4 pv = reinterpret_cast<const float4*>(a.p[t])[i];
+                d.x = fmaf(s_al[t], pv.x, d.x);
+                d.y = fmaf(s_al[t], pv.y, d.y);
+                d.z = fmaf(s_al[t], pv.z, d.z);
+                d.w = fmaf(s_al[t], pv.w, d.w);
+            }
+        const uint2 hv = bf16x4_hi(d);
+        h[i] = hv;
+        l[i] = bf16x4_lo(d, hv);
+    }
+}
+
 // beta = num / den (device scalars); p = z + beta p ; (ph, pl) = split(p)
 __global__ void xpay32_kernel(long long N, const double* __restrict__ num, const double* __restrict__ den,
                               const float* __restrict__ z, float* __restrict__ p, __nv_bfloat16* __restrict__ ph,
@@ -270,6 +406,20 @@ __global__ void scale64to32_hi_pow2_kernel(long long N4, const ulonglong2* __res
                                      f64_pow2_to_f32(b.y, k));
         r32[i] = v;
         rh[i] = bf16x4_hi(v);
+    }
+}
+
+// (rh, rl) = split(r64 2^k), four elements at a time: the scaled conversion
+// by integer operations (no FP64 arithmetic), as scale64to32_hi_pow2
+__global__ void split64_pow2_kernel(long long N4, const ulonglong2* __restrict__ r64, int k, uint2* __restrict__ rh,
+                                    uint2* __restrict__ rl) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N4; i += (long long)gridDim.x * blockDim.x) {
+        const ulonglong2 a = r64[2 * i], b = r64[2 * i + 1];
+        const float4 v = make_float4(f64_pow2_to_f32(a.x, k), f64_pow2_to_f32(a.y, k), f64_pow2_to_f32(b.x, k),
+                                     f64_pow2_to_f32(b.y, k));
+        const uint2 h = bf16x4_hi(v);
+        rh[i] = h;
+        rl[i] = bf16x4_lo(v, h);
     }
 }
 
@@ -666,6 +816,58 @@ void launch_gm_solve(const double* gs, const int* gctl, double* ny, int maxm, cu
     gm_solve_kernel<<<1, 1, 0, s>>>(gs, gctl, ny, maxm);
 }
 
+namespace {
+LamView lam_view(const float* lam, const int n[3]) {
+    const long long nc = (long long)n[0] * n[1];
+    LamView L;
+    L.ra = lam;
+    L.rb = lam + n[2];
+    L.U = reinterpret_cast<const float4*>(lam + 2 * n[2]);
+    L.V = reinterpret_cast<const float4*>(lam + 2 * n[2] + nc);
+    L.nc4 = nc / 4;
+    L.n3 = n[2];
+    return L;
+}
+// x over the float4 groups of a plane, y over planes: about 8 blocks of 256 per SM in all
+dim3 spec_grid(const LamView& L) {
+    long long gx = (L.nc4 + kT - 1) / kT;
+    if (gx > 1024) gx = 1024;
+    long long gy = (8LL * tc::num_sms() + gx - 1) / gx;
+    if (gy > L.n3) gy = L.n3;
+    if (gy < 1) gy = 1;
+    return dim3((unsigned)gx, (unsigned)gy);
+}
+}  // namespace
+
+int launch_spec_update(const float* lam, const int n[3], const double* num, const double* den, const float* q,
+                       float* r, double* rz, double* rr, double* alpha_out, cudaStream_t s, const int* skip) {
+    const long long nc = (long long)n[0] * n[1];
+    if (nc % 4 || !aligned16((size_t)nc * n[2], q, r, nullptr, nullptr) || (reinterpret_cast<uintptr_t>(lam) & 15) ||
+        (n[2] % 4))
+        return set_error(TFDE_EUNSUPPORTED, "spectral update: n1 n2 a multiple of 4 and 16-byte aligned vectors");
+    stats_count_launch();
+    const LamView L = lam_view(lam, n);
+    spec_update_kernel<<<spec_grid(L), kT, 0, s>>>(L, num, den, reinterpret_cast<const float4*>(q),
+                                                   reinterpret_cast<float4*>(r), rz, rr, alpha_out, skip);
+    return TFDE_OK;
+}
+
+int launch_spec_direction(const float* lam, const int n[3], const double* num, const double* den, const float* r,
+                          const float* pold, float* p, __nv_bfloat16* ph, __nv_bfloat16* pl, double* rz,
+                          cudaStream_t s, const int* skip) {
+    const long long nc = (long long)n[0] * n[1];
+    if (nc % 4 || !aligned16((size_t)nc * n[2], r, p, ph, pl) || (reinterpret_cast<uintptr_t>(lam) & 15) ||
+        (n[2] % 4) || (pold && (reinterpret_cast<uintptr_t>(pold) & 15)))
+        return set_error(TFDE_EUNSUPPORTED, "spectral direction: n1 n2 a multiple of 4 and 16-byte aligned vectors");
+    stats_count_launch();
+    const LamView L = lam_view(lam, n);
+    spec_direction_kernel<<<spec_grid(L), kT, 0, s>>>(L, num, den, reinterpret_cast<const float4*>(r),
+                                                      reinterpret_cast<const float4*>(pold),
+                                                      reinterpret_cast<float4*>(p), reinterpret_cast<uint2*>(ph),
+                                                      reinterpret_cast<uint2*>(pl), rz, skip);
+    return TFDE_OK;
+}
+
 void launch_pcg_head(double* d, int rz, int rzn, int pq, int rr, const int* ctl, cudaStream_t s) {
     stats_count_launch();
     pcg_head_kernel<<<1, 1, 0, s>>>(d, rz, rzn, pq, rr, ctl);
@@ -714,6 +916,24 @@ void launch_pcg_combine(size_t N, const PcgPending& pend, const float* x32, doub
     }
     pcg_combine_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, a, x32, sc, c64, x64, acc32);
 }
+int launch_pcg_combine_split(size_t N, const PcgPending& pend, const float* x32, __nv_bfloat16* h, __nv_bfloat16* l,
+                             cudaStream_t s) {
+    bool vec = aligned16(N, x32, h, l, nullptr);
+    for (int t = 0; t < pend.cnt; ++t) vec = vec && aligned16(N, pend.p[t], nullptr, nullptr, nullptr);
+    if (!vec) return set_error(TFDE_EUNSUPPORTED, "combine to split planes: 16-byte aligned vectors, N % 4 == 0");
+    stats_count_launch();
+    CombineArgs a;
+    a.cnt = pend.cnt;
+    a.fold = pend.fold ? 1 : 0;
+    for (int j = 0; j < kPRing; ++j) {
+        a.p[j] = j < pend.cnt ? pend.p[j] : nullptr;
+        a.alpha[j] = j < pend.cnt ? pend.alpha[j] : nullptr;
+    }
+    const long long N4 = (long long)N / 4;
+    pcg_combine_split_kernel<<<grid_for(N4), kT, 0, s>>>(N4, a, reinterpret_cast<const float4*>(x32),
+                                                         reinterpret_cast<uint2*>(h), reinterpret_cast<uint2*>(l));
+    return TFDE_OK;
+}
 void launch_scale64to32_hi(size_t N, const double* r64, double sc, float* r32, __nv_bfloat16* rh, cudaStream_t s) {
     stats_count_launch();
     int k = 0;
@@ -746,6 +966,13 @@ void launch_split32(size_t N, const float* v, __nv_bfloat16* h, __nv_bfloat16* l
 }
 void launch_split64(size_t N, const double* v, double sc, __nv_bfloat16* h, __nv_bfloat16* l, cudaStream_t s) {
     stats_count_launch();
+    int k = 0;
+    if (pow2_exponent(sc, &k) && aligned16(N, v, h, l, nullptr)) {
+        const long long N4 = (long long)N / 4;
+        split64_pow2_kernel<<<grid_for(N4), kT, 0, s>>>(N4, reinterpret_cast<const ulonglong2*>(v), k,
+                                                        reinterpret_cast<uint2*>(h), reinterpret_cast<uint2*>(l));
+        return;
+    }
     split64_kernel<<<grid_for((long long)N), kT, 0, s>>>((long long)N, v, sc, h, l);
 }
 void launch_add32to64(size_t N, double sc, const float* d, double* x, cudaStream_t s) {

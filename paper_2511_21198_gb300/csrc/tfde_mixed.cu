@@ -50,6 +50,18 @@ std::vector<double> dense_etaB(const tfde_problem* P, int a) {
 
 double mass_entry(int i, int j) { return i == j ? 0.75 : ((i - j == 1 || j - i == 1) ? 0.125 : 0.0); }
 
+// S_n of Eq. (diag_tau_pre), S(i, j) = sqrt(2 / (n + 1)) sin(pi (i + 1)(j + 1) / (n + 1))
+// (row-major, FP64), the product reduced modulo 2(n + 1) before the sine.
+std::vector<double> dst_dense(int n) {
+    std::vector<double> S((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            const long long r = ((long long)(i + 1) * (j + 1)) % (2LL * (n + 1));
+            S[(size_t)i * n + j] = std::sqrt(2.0 / (n + 1)) * std::sin(M_PI * (double)r / (double)(n + 1));
+        }
+    return S;
+}
+
 struct SegSpec {
     int a_hi, a_lo, plane;  // a_lo < 0: single-term A
 };
@@ -555,6 +567,266 @@ int inner_pcg_graph(const tfde_problem* P, double theta, int maxit, int* iters, 
     return check_err(P, s);
 }
 
+// ------------------------------------------------------------------
+// The inner PCG in the sine-transform eigenbasis (symmetric problems).
+// S_N = S3 (x) S2 (x) S1 is symmetric and orthogonal and diagonalises both the
+// mass operator (A_n = S diag(mu) S, A_n tridiagonal Toeplitz) and the tau
+// preconditioner (P = S_N Lambda S_N, Eq. (diag_tau_pre)).  PCG on A c = r
+// with P is therefore PCG on (S_N A S_N) c~ = S_N r with the diagonal Lambda,
+// c = S_N c~ (the same iterates in exact arithmetic: an orthogonal change of
+// basis, Sec. 3.1).  In that basis an iteration is three split contractions
+// (one per axis, Kronecker sum with diagonal factors on the other axes) and
+// pointwise work: 3 instead of 9 split passes, the preconditioner free.
+
+// out_f32 = S_N v, v the split planes `in`; the x and y passes write split
+// planes mid1 and mid2, the z pass FP32.
+int spec_transform(const tfde_problem* P, int in, int mid1, int mid2, float* out_f32, cudaStream_t s,
+                   const int* skip = nullptr) {
+    MixedState* M = mixed(P);
+    const SegSpec sx[1] = {{OM_S2X_H, OM_S2X_L, in}}, sy[1] = {{OM_S2Y_H, OM_S2Y_L, mid1}},
+                  sz[1] = {{OM_S2Z_H, OM_S2Z_L, mid2}};
+    int st;
+    if ((st = run_gemm(P, 0, sx, 1, tc::OUT_HILO, 1.f, nullptr, mid1, false, s, nullptr, nullptr, skip))) return st;
+    if ((st = run_gemm(P, 1, sy, 1, tc::OUT_HILO, 1.f, nullptr, mid2, false, s, nullptr, nullptr, skip))) return st;
+    if ((st = run_gemm(P, 2, sz, 1, tc::OUT_F32, 1.f, out_f32, -1, false, s, nullptr, nullptr, skip))) return st;
+    M->spec_transforms++;
+    return TFDE_OK;
+}
+
+// q = (S_N A S_N) p, p given as the split planes PL_P and in FP32 (pf: the
+// z term's mass part D3 D2 D1 p and the fused <p, q> into *pq):
+//   x: s1 = cs_x . (Bh1 p)_x ; y: s2 = s1 + cs_y . (Bh2 p)_y ;
+//   z: q = s2 + cs_z . ((Bh3 p)_z + mu3 p)
+// with Bh_a = S (eta_a B_a) S and cs the products of the other axes' mass
+// eigenvalues per line.  s1, s2 live in F_Z, F_P.
+int spec_matvec(const tfde_problem* P, const float* pf, float* q, double* pq, cudaStream_t s,
+                const int* skip = nullptr) {
+    MixedState* M = mixed(P);
+    const long long n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
+    const float* cs_x = M->spec;
+    const float* cs_y = cs_x + n2 * n3;
+    const float* cs_z = cs_y + n1 * n3;
+    const float* mu3 = cs_z + n1 * n2;
+    float* s1 = M->f[F_Z];
+    float* s2 = M->f[F_P];
+    const double N = (double)P->N;
+    for (int a = 0; a < 3; ++a) {
+        const SegSpec sg[1] = {{OM_BX_H + 2 * a, OM_BX_L + 2 * a, PL_P}};
+        tc::Params prm;
+        double bytes, flops;
+        float* out = a == 0 ? s1 : (a == 1 ? s2 : q);
+        gemm_params(P, a, sg, 1, tc::OUT_SUM, 1.f, out, -1, false, prm, &bytes, &flops);
+        prm.col_scale = a == 0 ? cs_x : (a == 1 ? cs_y : cs_z);
+        if (a > 0) {
+            prm.addend = a == 1 ? s1 : s2;
+            bytes += 4.0 * N;
+        }
+        if (a == 2) {
+            prm.mass_row = mu3;
+            prm.dot_vec = pf;
+            prm.dot_out = pq;
+            bytes += 4.0 * N;
+        }
+        prm.skip = skip;
+        M->gemm_launches++;
+        if (int st = tc::launch(prm, s, bytes, flops)) return st;
+    }
+    return TFDE_OK;
+}
+
+int build_pcg_graph_spec(const tfde_problem* P, cudaStream_t s);
+int inner_pcg_spec_graph(const tfde_problem* P, double theta, int maxit, int* iters, PcgPending* pend,
+                         cudaStream_t s, double* reached, double rr0);
+
+// Inner PCG in the eigenbasis: the caller has written the (scaled) residual as
+// the split planes PL_R; on return F_R holds S_N r updated by the iterations
+// and *pend the directions (in the eigenbasis) left to combine, as inner_pcg.
+int inner_pcg_spec(const tfde_problem* P, double theta, int maxit, int* iters, PcgPending* pend, cudaStream_t s,
+                   double* reached, double rr0) {
+    MixedState* M = mixed(P);
+    const size_t N = P->N;
+    float* r = M->f[F_R];
+    float* q = M->f[F_Q];
+    double* d = M->dsc;
+    int st = TFDE_OK;
+    *pend = PcgPending();
+    if (reached) *reached = 0.0;
+    if (!(rr0 > 0.0) || !std::isfinite(rr0)) return rr0 == 0.0 ? TFDE_OK : set_error(TFDE_ENAN, "non-finite inner residual");
+    auto pbuf = [&](int j) { return M->pring + (size_t)(j % kPRing) * N; };
+    if ((st = spec_transform(P, PL_R, PL_T1, PL_T2, r, s))) return st;   // r~ = S_N r
+    if (M->device_loop && !stats_timing() && maxit > 0) {
+        if ((st = build_pcg_graph_spec(P, s))) return st;
+        if (M->spec_exec) return inner_pcg_spec_graph(P, theta, maxit, iters, pend, s, reached, rr0);
+    }
+    int rz = D_RZ0;
+    MX_TRY(cudaMemsetAsync(d + rz, 0, sizeof(double), s));
+    // p_0 = Lambda^{-1} r~, <r~, Lambda^{-1} r~>
+    if ((st = launch_spec_direction(M->lam, P->n, nullptr, nullptr, r, nullptr, pbuf(0), M->hi[PL_P], M->lo[PL_P],
+                                    d + rz, s)))
+        return st;
+    int k = 0, j0 = 0;
+    bool folded = false;
+    while (k < maxit) {
+        const int rzn = rz == D_RZ0 ? D_RZ1 : D_RZ0;
+        MX_TRY(cudaMemsetAsync(d + D_PQ, 0, 2 * sizeof(double), s));   // <p, Ap> and <r, r>
+        MX_TRY(cudaMemsetAsync(d + rzn, 0, sizeof(double), s));
+        if ((st = spec_matvec(P, pbuf(k), q, d + D_PQ, s))) return st;
+        if ((st = launch_spec_update(M->lam, P->n, d + rz, d + D_PQ, q, r, d + rzn, d + D_RR,
+                                     d + kAlphaSlot + k % kPRing, s)))
+            return st;
+        const double rr = host_scalar(P, d + D_RR, s, &st);
+        if (st) return st;
+        ++k;
+        if (!std::isfinite(rr)) return set_error(TFDE_ENAN, "non-finite inner residual");
+        if (reached) *reached = std::sqrt(rr / rr0);
+        if (rr <= theta * theta * rr0 || k >= maxit) break;
+        if (k - j0 == kPRing) {
+            PcgPending w;
+            w.cnt = kPRing;
+            w.fold = folded;
+            for (int j = 0; j < kPRing; ++j) {
+                w.p[j] = pbuf(j0 + j);
+                w.alpha[j] = d + kAlphaSlot + (j0 + j) % kPRing;
+            }
+            launch_pcg_combine(N, w, M->f[F_X], 0.0, nullptr, nullptr, M->f[F_X], s);
+            folded = true;
+            j0 = k;
+        }
+        // p_k = Lambda^{-1} r~ + beta p_{k-1}, beta = <r, z>_new / <r, z>
+        if ((st = launch_spec_direction(M->lam, P->n, d + rzn, d + rz, r, pbuf(k - 1), pbuf(k), M->hi[PL_P],
+                                        M->lo[PL_P], nullptr, s)))
+            return st;
+        rz = rzn;
+    }
+    pend->cnt = k - j0;
+    pend->fold = folded;
+    for (int j = 0; j < pend->cnt; ++j) {
+        pend->p[j] = pbuf(j0 + j);
+        pend->alpha[j] = d + kAlphaSlot + (j0 + j) % kPRing;
+    }
+    *iters = k;
+    return check_err(P, s);
+}
+
+// The iterations of inner_pcg_spec as one graph launch per sweep: a while node
+// whose body runs kPRing iterations, each head -> the three eigenbasis
+// passes (<p, q> fused) -> update (alpha, <r, z>, <r, r>) -> stop test ->
+// direction (beta, p and its split planes); the body's window of directions
+// folded into F_X before its last direction update.
+int build_pcg_graph_spec(const tfde_problem* P, cudaStream_t s) {
+    MixedState* M = mixed(P);
+    if (M->spec_exec && M->spec_tune_gen != tc::tune_generation()) {
+        cudaGraphExecDestroy(M->spec_exec);
+        cudaGraphDestroy(M->spec_graph);
+        M->spec_exec = nullptr;
+        M->spec_graph = nullptr;
+    }
+    if (M->spec_exec || M->spec_graph_failed) return TFDE_OK;
+    const size_t N = P->N;
+    if (int st = tc::set_attrs()) return st;
+    float* q = M->f[F_Q];
+    float* r = M->f[F_R];
+    double* d = M->dsc;
+    int* ctl = M->pcg_ctl;
+    auto pbuf = [&](int j) { return M->pring + (size_t)(j % kPRing) * N; };
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+    cudaGraphConditionalHandle h{};
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    if (ok) ok = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+    }
+    if (ok) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+             cudaSuccess;
+        if (ok) {
+            stats_set_capturing(true);
+            int st = TFDE_OK;
+            const float* ps[kPRing];
+            const double* as[kPRing];
+            for (int u = 0; u < kPRing; ++u) {
+                ps[u] = pbuf(u);
+                as[u] = d + kAlphaSlot + u;
+            }
+            for (int u = 0; u < kPRing && !st; ++u) {
+                launch_pcg_head(d, D_RZ0, D_RZN, D_PQ, D_RR, ctl, s);
+                st = spec_matvec(P, pbuf(u), q, d + D_PQ, s, ctl + 1);
+                if (!st) st = launch_spec_update(M->lam, P->n, d + D_RZ0, d + D_PQ, q, r, d + D_RZN, d + D_RR,
+                                                 d + kAlphaSlot + u, s, ctl + 1);
+                if (st) break;
+                launch_pcg_cond(h, d + D_RR, d + D_THR, ctl, s);
+                if (u == kPRing - 1) launch_pcg_fold_dev(N, ps, as, M->f[F_X], ctl, s);
+                st = launch_spec_direction(M->lam, P->n, d + D_RZN, d + D_RZ0, r, pbuf(u), pbuf(u + 1), M->hi[PL_P],
+                                           M->lo[PL_P], nullptr, s, ctl + 1);
+            }
+            stats_set_capturing(false);
+            cudaGraph_t out = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(s, &out);
+            ok = st == TFDE_OK && e == cudaSuccess;
+        }
+    }
+    if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        M->spec_graph_failed = true;
+        set_error(TFDE_OK, "");
+        return TFDE_OK;
+    }
+    M->spec_graph = g;
+    M->spec_exec = ex;
+    M->spec_tune_gen = tc::tune_generation();
+    return TFDE_OK;
+}
+
+int inner_pcg_spec_graph(const tfde_problem* P, double theta, int maxit, int* iters, PcgPending* pend,
+                         cudaStream_t s, double* reached, double rr0) {
+    MixedState* M = mixed(P);
+    const size_t N = P->N;
+    double* d = M->dsc;
+    auto pbuf = [&](int j) { return M->pring + (size_t)(j % kPRing) * N; };
+    launch_pcg_init(d, D_RZN, D_THR, theta * theta * rr0, M->pcg_ctl, maxit, s);
+    int st = launch_spec_direction(M->lam, P->n, nullptr, nullptr, M->f[F_R], nullptr, pbuf(0), M->hi[PL_P],
+                                   M->lo[PL_P], d + D_RZN, s);   // p_0 = Lambda^{-1} r~
+    if (st) return st;
+    MX_TRY(cudaGraphLaunch(M->spec_exec, s));
+    MX_TRY(cudaMemcpyAsync(M->pcg_ctl_host, M->pcg_ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    MX_TRY(cudaMemcpyAsync(P->red_host, d + D_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MX_TRY(cudaStreamSynchronize(s));
+    const int k = M->pcg_ctl_host[0];
+    const double rr = P->red_host[0];
+    // launches of the graph: 7 per iteration of a body (3 of them split), the fold once per body
+    const int bodies = (k + kPRing - 1) / kPRing;
+    stats_count_launch((unsigned)(bodies * (7 * kPRing + 1)));
+    *iters = k;
+    if (!std::isfinite(rr)) return set_error(TFDE_ENAN, "non-finite inner residual");
+    if (reached) *reached = std::sqrt(rr / rr0);
+    const int j0 = kPRing * ((k - 1) / kPRing);
+    pend->cnt = k - j0;
+    pend->fold = k > kPRing;
+    for (int j = 0; j < pend->cnt; ++j) {
+        pend->p[j] = pbuf(j0 + j);
+        pend->alpha[j] = d + kAlphaSlot + (j0 + j) % kPRing;
+    }
+    return check_err(P, s);
+}
+
+// The eigenbasis solution d~ = (fold ? F_X : 0) + sum alpha_j p_j back to the
+// grid: F_X = S_N d~ (the combination and its split planes, then three passes).
+int spec_finish(const tfde_problem* P, const PcgPending& pend, cudaStream_t s) {
+    MixedState* M = mixed(P);
+    if (int st = launch_pcg_combine_split(P->N, pend, M->f[F_X], M->hi[PL_T1], M->lo[PL_T1], s)) return st;
+    return spec_transform(P, PL_T1, PL_T2, PL_R, M->f[F_X], s);
+}
+
 // r = b - A x (accurate) and ||r||, the norm accumulated by the last pass of
 // the contraction with the terms scaled by 2^-ilogb(nb).
 // With an_out, A_N x also goes there (from the z-pass digit slicing).
@@ -802,6 +1074,34 @@ int fast_pass_descriptors(const tfde_problem* P, int kind, float* out_f32, tc::P
 
 int mixed_prepare_gmres(const tfde_problem* P, int restart) { return ensure_v32(P, restart); }
 
+namespace {
+// Device copy of operator matrix om (n x n BF16) with its tensor maps; the lo
+// of a hi / lo pair lives in the second half of the pair's allocation, and
+// the hi of a pair also gets the merged 3-D box that loads both terms.
+int upload_matrix(MixedState* M, int om, const std::vector<__nv_bfloat16>& h, int n, bool pair_hi, bool pair_lo,
+                  cudaStream_t s) {
+    if (pair_lo) {
+        M->mat[om] = M->mat[om - 1] + h.size();
+    } else {
+        MX_TRY(cudaMalloc((void**)&M->mat[om], (pair_hi ? 2 : 1) * h.size() * sizeof(__nv_bfloat16)));
+        M->own_mat[om] = true;
+    }
+    MX_TRY(cudaMemcpyAsync(M->mat[om], h.data(), h.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, s));
+    MX_TRY(cudaStreamSynchronize(s));
+    int st = tc::make_split_map_A(&M->amap[om], M->mat[om], n);
+    if (st) return st;
+    if (pair_hi) {
+        // hi and lo of the pair as one 3-D tensor (k, row, term)
+        const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, 2};
+        const cuuint64_t strides[2] = {(cuuint64_t)n * 2, (cuuint64_t)n * n * 2};
+        const cuuint32_t box[3] = {(cuuint32_t)tc::SK, (cuuint32_t)tc::BM, 2};
+        M->has_amap2[om] = tc::encode_map(&M->amap2[om], M->mat[om], 3, dims, strides, box,
+                                          CU_TENSOR_MAP_SWIZZLE_128B) == TFDE_OK;
+    }
+    return TFDE_OK;
+}
+}  // namespace
+
 int mixed_init(tfde_problem* P, cudaStream_t s) {
     for (int a = 0; a < 3; ++a)
     {
@@ -815,7 +1115,7 @@ int mixed_init(tfde_problem* P, cudaStream_t s) {
     P->mixed = M;
     const size_t N = P->N;
     // operator matrices
-    for (int om = 0; om < NOM; ++om) {
+    for (int om = 0; om < NOM_BASE; ++om) {
         int a;
         if (om <= OM_GHATR_L || om == OM_MX || om == OM_SX) a = 0;
         else if ((om >= OM_GY_H && om <= OM_GYN_L) || om == OM_MY || om == OM_SY) a = 1;
@@ -826,12 +1126,8 @@ int mixed_init(tfde_problem* P, cudaStream_t s) {
             for (int i = 0; i < n; ++i)
                 for (int j = 0; j < n; ++j) h[(size_t)i * n + j] = __float2bfloat16_rn((float)mass_entry(i, j));
         } else if (om == OM_SX || om == OM_SY || om == OM_SZ) {
-            for (int i = 0; i < n; ++i)
-                for (int j = 0; j < n; ++j) {
-                    const long long r = ((long long)(i + 1) * (j + 1)) % (2LL * (n + 1));
-                    const double v = std::sqrt(2.0 / (n + 1)) * std::sin(M_PI * (double)r / (double)(n + 1));
-                    h[(size_t)i * n + j] = __float2bfloat16_rn((float)v);
-                }
+            const std::vector<double> S = dst_dense(n);
+            for (size_t e = 0; e < h.size(); ++e) h[e] = __float2bfloat16_rn((float)S[e]);
         } else {
             const std::vector<double> B = dense_etaB(P, a);
             const bool lo = (om == OM_GHAT_L || om == OM_GHATR_L || om == OM_GY_L || om == OM_GYN_L ||
@@ -852,23 +1148,39 @@ int mixed_init(tfde_problem* P, cudaStream_t s) {
                              om == OM_GZN_H;
         const bool pair_lo = om == OM_GHAT_L || om == OM_GHATR_L || om == OM_GY_L || om == OM_GYN_L || om == OM_GZ_L ||
                              om == OM_GZN_L;
-        if (pair_lo) {
-            M->mat[om] = M->mat[om - 1] + h.size();   // second half of the pair's allocation
-        } else {
-            MX_TRY(cudaMalloc((void**)&M->mat[om], (pair_hi ? 2 : 1) * h.size() * sizeof(__nv_bfloat16)));
-            M->own_mat[om] = true;
-        }
-        MX_TRY(cudaMemcpyAsync(M->mat[om], h.data(), h.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, s));
-        MX_TRY(cudaStreamSynchronize(s));
-        int st = tc::make_split_map_A(&M->amap[om], M->mat[om], n);
-        if (st) return st;
-        if (pair_hi) {
-            // hi and lo of the pair as one 3-D tensor (k, row, term)
-            const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, 2};
-            const cuuint64_t strides[2] = {(cuuint64_t)n * 2, (cuuint64_t)n * n * 2};
-            const cuuint32_t box[3] = {(cuuint32_t)tc::SK, (cuuint32_t)tc::BM, 2};
-            M->has_amap2[om] = tc::encode_map(&M->amap2[om], M->mat[om], 3, dims, strides, box,
-                                              CU_TENSOR_MAP_SWIZZLE_128B) == TFDE_OK;
+        if (int st = upload_matrix(M, om, h, n, pair_hi, pair_lo, s)) return st;
+    }
+    // the inner PCG in the sine-transform eigenbasis (symmetric problems, Sec. 3.1):
+    // per axis S_n (eta_a B_a) S_n and S_n itself, each split into hi + lo
+    if (P->symmetric) {
+        for (int a = 0; a < 3; ++a) {
+            const int n = P->n[a];
+            const std::vector<double> S = dst_dense(n);
+            const std::vector<double> E = dense_etaB(P, a);
+            std::vector<double> T((size_t)n * n, 0.0), Bh((size_t)n * n, 0.0);
+            for (int i = 0; i < n; ++i)          // T = S E
+                for (int k = 0; k < n; ++k) {
+                    const double sik = S[(size_t)i * n + k];
+                    const double* er = E.data() + (size_t)k * n;
+                    double* tr = T.data() + (size_t)i * n;
+                    for (int j = 0; j < n; ++j) tr[j] += sik * er[j];
+                }
+            for (int i = 0; i < n; ++i)          // Bh = T S
+                for (int k = 0; k < n; ++k) {
+                    const double tik = T[(size_t)i * n + k];
+                    const double* sr = S.data() + (size_t)k * n;
+                    double* br = Bh.data() + (size_t)i * n;
+                    for (int j = 0; j < n; ++j) br[j] += tik * sr[j];
+                }
+            const int ob = OM_BX_H + 2 * a, os = OM_S2X_H + 2 * a;
+            for (int part = 0; part < 2; ++part) {
+                const std::vector<double>& src = part == 0 ? Bh : S;
+                const int om = part == 0 ? ob : os;
+                std::vector<__nv_bfloat16> hh((size_t)n * n), hl((size_t)n * n);
+                for (size_t e = 0; e < hh.size(); ++e) to_bf16_pair(src[e], hh[e], hl[e]);
+                if (int st = upload_matrix(M, om, hh, n, true, false, s)) return st;
+                if (int st = upload_matrix(M, om + 1, hl, n, false, true, s)) return st;
+            }
         }
     }
     {
@@ -915,6 +1227,30 @@ int mixed_init(tfde_problem* P, cudaStream_t s) {
             }
         MX_TRY(cudaMalloc((void**)&M->lam, lam.size() * sizeof(float)));
         MX_TRY(cudaMemcpyAsync(M->lam, lam.data(), lam.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+        MX_TRY(cudaStreamSynchronize(s));   // the host array goes out of scope
+    }
+    // per-line factors of the operator in the sine-transform eigenbasis:
+    // S_N A S_N = D3 D2 (D1 + Bh1) + D3 Bh2 D1 + Bh3 D2 D1 (Kronecker
+    // products, D_a = diag of the mass eigenvalues, Bh_a = S (eta_a B_a) S),
+    // so each axis term is the contraction along its axis scaled by the mass
+    // eigenvalues of the other two axes, and D3 D2 D1 is the z term's mass part
+    if (P->symmetric) {
+        const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
+        const std::vector<double>&m1 = P->lam_mass[0], &m2 = P->lam_mass[1], &m3 = P->lam_mass[2];
+        std::vector<float> f;
+        f.reserve((size_t)n2 * n3 + (size_t)n1 * n3 + (size_t)n1 * n2 + n3);
+        for (int k = 0; k < n3; ++k)
+            for (int j = 0; j < n2; ++j) f.push_back((float)(m2[j] * m3[k]));   // x lines j + n2 k
+        for (int k = 0; k < n3; ++k)
+            for (int i = 0; i < n1; ++i) f.push_back((float)(m1[i] * m3[k]));   // y lines i + n1 k
+        for (int j = 0; j < n2; ++j)
+            for (int i = 0; i < n1; ++i) f.push_back((float)(m1[i] * m2[j]));   // z lines i + n1 j
+        for (int k = 0; k < n3; ++k) f.push_back((float)m3[k]);
+        MX_TRY(cudaMalloc((void**)&M->spec, f.size() * sizeof(float)));
+        MX_TRY(cudaMemcpyAsync(M->spec, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+        MX_TRY(cudaStreamSynchronize(s));
+        M->spectral_ok = true;
+        M->spectral = true;
     }
     MX_TRY(cudaMalloc((void**)&M->dsc, 32 * sizeof(double)));
     MX_TRY(cudaMemsetAsync(M->dsc, 0, 32 * sizeof(double), s));
@@ -953,6 +1289,8 @@ void mixed_free(tfde_problem* P) {
     cudaFree(M->gm_ctl);
     if (M->gm_ctl_host) cudaFreeHost(M->gm_ctl_host);
     if (M->pcg_graph) cudaGraphDestroy(M->pcg_graph);
+    if (M->spec_exec) cudaGraphExecDestroy(M->spec_exec);
+    if (M->spec_graph) cudaGraphDestroy(M->spec_graph);
     cudaFree(M->pcg_ctl);
     if (M->pcg_ctl_host) cudaFreeHost(M->pcg_ctl_host);
     cudaFree(M->pair_d);
@@ -961,6 +1299,7 @@ void mixed_free(tfde_problem* P) {
     if (M->gm_host) cudaFreeHost(M->gm_host);
     oz_free(M);
     cudaFree(M->lam);
+    cudaFree(M->spec);
     cudaFree(M->dsc);
     cudaFree(M->err);
     if (M->err_host) cudaFreeHost(M->err_host);
@@ -1081,16 +1420,26 @@ int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit
         // up to the FP32 rounding of its elements; the inner PCG reads no lo plane
         const int k = -std::ilogb(nr) - 1;
         const double un = std::ldexp(nr, k);
-        launch_scale64to32_hi(P->N, r64, std::ldexp(1.0, k), M->f[F_R], M->hi[PL_R], s);
         int it = 0;
         double reached = 1.0;
         PcgPending pend;
-        if ((st = inner_pcg(P, theta, maxit - loc.iters, &it, &pend, s, &reached, un * un))) return st;
+        const bool spec = M->spectral;
+        if (spec) {
+            // the eigenbasis solve reads the split planes of r and returns S_N d~ in F_X
+            launch_split64(P->N, r64, std::ldexp(1.0, k), M->hi[PL_R], M->lo[PL_R], s);
+            if ((st = inner_pcg_spec(P, theta, maxit - loc.iters, &it, &pend, s, &reached, un * un))) return st;
+            if ((st = spec_finish(P, pend, s))) return st;
+        } else {
+            launch_scale64to32_hi(P->N, r64, std::ldexp(1.0, k), M->f[F_R], M->hi[PL_R], s);
+            if ((st = inner_pcg(P, theta, maxit - loc.iters, &it, &pend, s, &reached, un * un))) return st;
+        }
         loc.iters += it;
         loc.refine_sweeps++;
         const double nr_old = nr;
+        PcgPending whole;   // eigenbasis: the transformed correction is F_X itself
+        whole.fold = true;
         if ((st = apply_correction(P, b, x, r64, &nr, std::max(reached, kInnerFloor), tol, nb, std::ldexp(1.0, -k), s,
-                                   &pend)))
+                                   spec ? &whole : &pend)))
             return st;
         stall = (nr > 0.5 * nr_old) ? stall + 1 : 0;
         if (stall >= 2) {
@@ -1195,10 +1544,24 @@ int mixed_tune(tfde_problem* P, int reps, cudaStream_t s) {
     tc::tune_record(true);
     int st = fast_matvec(P, TFDE_OP_A, M->f[F_Q], s, -1, M->pring, d + D_PQ);
     if (!st) st = fast_precond_cg(P, M->pring + N, M->pring, d + D_RZ0, nullptr, nullptr, s);
+    if (!st && M->spectral_ok) {   // the eigenbasis passes and the sine transform
+        st = spec_matvec(P, M->pring, M->f[F_Q], d + D_PQ, s);
+        if (!st) st = spec_transform(P, PL_R, PL_T1, PL_T2, M->f[F_R], s);
+    }
     tc::tune_record(false);
     if (!st) st = tc::tune_recorded(reps, s);
     if (!st) st = check_err(P, s);
     return st;
+}
+
+int mixed_set_spectral(tfde_problem* P, int enable) {
+    MixedState* M = mixed(P);
+    if (!M || !M->spectral_ok) {
+        if (enable) return set_error(TFDE_EUNSUPPORTED, "the eigenbasis inner PCG needs a symmetric TFDE_MIXED problem on the tensor-core path");
+        return TFDE_OK;
+    }
+    M->spectral = enable != 0;
+    return TFDE_OK;
 }
 
 int mixed_set_device_loop(tfde_problem* P, int enable) {

@@ -37,6 +37,21 @@ void launch_cg_update_r32(size_t N, const double* num, const double* den, const 
 // without: x64 += sc d ; with acc32 (and no x64): acc32 = d (the fold itself)
 void launch_pcg_combine(size_t N, const PcgPending& pend, const float* x32, double sc, double* c64, double* x64,
                         float* acc32, cudaStream_t s);
+// The inner PCG in the sine-transform eigenbasis, where the tau preconditioner
+// is the diagonal Lambda (lam: the [ra | rb | U | V] factors of MixedState).
+// Update: alpha = *num / *den (also to *alpha_out); r -= alpha q;
+// *rz += <r, r / Lambda>; *rr += <r, r>.
+int launch_spec_update(const float* lam, const int n[3], const double* num, const double* den, const float* q,
+                       float* r, double* rz, double* rr, double* alpha_out, cudaStream_t s, const int* skip = nullptr);
+// Direction: beta = *num / *den (0 when den is null); p = r / Lambda + beta
+// pold (pold may be null), in FP32 and as split planes; with rz:
+// *rz += <r, r / Lambda>.
+int launch_spec_direction(const float* lam, const int n[3], const double* num, const double* den, const float* r,
+                          const float* pold, float* p, __nv_bfloat16* ph, __nv_bfloat16* pl, double* rz,
+                          cudaStream_t s, const int* skip = nullptr);
+// d = (fold ? x32 : 0) + sum_j alpha_j p_j written as split planes (h, l) only
+int launch_pcg_combine_split(size_t N, const PcgPending& pend, const float* x32, __nv_bfloat16* h, __nv_bfloat16* l,
+                             cudaStream_t s);
 // device-side inner PCG loop (see pcg_cond_kernel): iteration head, stop
 // test and loop condition, initial control words, fold of a full window
 void launch_pcg_head(double* d, int rz, int rzn, int pq, int rr, const int* ctl, cudaStream_t s);
@@ -94,8 +109,12 @@ enum OpMat {
     OM_GZ_H, OM_GZ_L, OM_GZN_H, OM_GZN_L,   // +- eta3 B3
     OM_MX, OM_MY, OM_MZ,         // mass A_n (exact in BF16)
     OM_SX, OM_SY, OM_SZ,         // DST-I S_n (rounded once to BF16)
+    // the inner PCG in the sine-transform eigenbasis (symmetric problems):
+    OM_BX_H, OM_BX_L, OM_BY_H, OM_BY_L, OM_BZ_H, OM_BZ_L,        // S_n (eta_a B_a) S_n, split
+    OM_S2X_H, OM_S2X_L, OM_S2Y_H, OM_S2Y_L, OM_S2Z_H, OM_S2Z_L,  // S_n split into hi + lo
     NOM
 };
+constexpr int NOM_BASE = OM_SZ + 1;   // the matrices every TFDE_MIXED problem carries
 
 // Digit slices of the exact-integer (Ozaki-type) contraction: 7 base-128
 // digits, 49 bits below each row / line maximum.
@@ -129,6 +148,17 @@ struct MixedState {
     CUtensorMap omap_hl[NPL][3];   // hi and lo as one tensor (lo = hi + N): one store per chunk
     float* f[NF] = {};
     float* lam = nullptr;   // [ra (n3) | rb (n3) | U (n1 n2) | V (n1 n2)]
+    // inner PCG in the sine-transform eigenbasis (built for symmetric
+    // problems): per-line factors of the three axis terms and the z-axis
+    // mass eigenvalues, [cs_x (n2 n3) | cs_y (n1 n3) | cs_z (n1 n2) | mu3 (n3)]
+    float* spec = nullptr;
+    bool spectral_ok = false;    // the matrices and factors exist
+    bool spectral = false;       // tfde_set_spectral_inner (default on when available)
+    long long spec_transforms = 0;   // sine transforms run (statistics)
+    cudaGraph_t spec_graph = nullptr;    // the eigenbasis inner PCG as one graph launch per sweep
+    cudaGraphExec_t spec_exec = nullptr;
+    bool spec_graph_failed = false;
+    unsigned spec_tune_gen = 0;
     double* dsc = nullptr;  // device scalars
     int* err = nullptr;     // device error flag of the tensor-core kernels
     int* err_host = nullptr;

@@ -235,7 +235,8 @@ int set_attrs() {
                         set_attr_one<true, 0, OUT_F32>() && set_attr_one<true, 0, OUT_HILO>() &&
                         set_attr_one<true, 1, OUT_F32>() && set_attr_one<true, 1, OUT_HILO>() &&
                         set_attr_one<false, 0, OUT_XPAY>() && set_attr_one<false, 1, OUT_XPAY>() &&
-                        set_attr_one<false, 0, OUT_HI>() && set_attr_one<false, 1, OUT_HI>();
+                        set_attr_one<false, 0, OUT_HI>() && set_attr_one<false, 1, OUT_HI>() &&
+                        set_attr_one<false, 0, OUT_SUM>() && set_attr_one<false, 1, OUT_SUM>();
         if (!ok) return set_error(TFDE_ECUDA, "cudaFuncSetAttribute(smem) failed");
         attr_done = true;
     }
@@ -275,6 +276,11 @@ void launch_instance(int kmajor, int out_mode, unsigned grid, cudaStream_t s, co
         if (out_mode == OUT_HI) {
             if (kmajor) launch_one<G, 1, OUT_HI>(grid, s, p0, groups, gstart, ngroups, gactive);
             else launch_one<G, 0, OUT_HI>(grid, s, p0, groups, gstart, ngroups, gactive);
+            return;
+        }
+        if (out_mode == OUT_SUM) {
+            if (kmajor) launch_one<G, 1, OUT_SUM>(grid, s, p0, groups, gstart, ngroups, gactive);
+            else launch_one<G, 0, OUT_SUM>(grid, s, p0, groups, gstart, ngroups, gactive);
             return;
         }
     }
@@ -425,7 +431,7 @@ int launch_grouped(const Params* groups, const long long* gstart, int ngroups, l
                    int out_mode, const int* gactive, int* err, cudaStream_t s, double bytes, double flops,
                    const int* skip) {
     if (int st = set_attrs()) return st;
-    if (out_mode == OUT_HI || out_mode == OUT_XPAY)
+    if (out_mode == OUT_HI || out_mode == OUT_XPAY || out_mode == OUT_SUM)
         return set_error(TFDE_EUNSUPPORTED, "grouped axis_gemm_kernel: split or FP32 output only");   // no such instances
     if (total <= 0 || ngroups <= 0) return TFDE_OK;
     Params p0;
@@ -476,7 +482,7 @@ int tune_import(const tfde_tune_entry* in, int count) {
     for (int i = 0; i < count; ++i) {
         const tfde_tune_entry& t = in[i];
         if (t.grid < 1 || t.stages < 1 || t.stages > MAX_STAGES || t.stage_bytes < 1 || t.tiles < 1 ||
-            t.stage_bytes * t.stages > RING_BYTES || t.out_mode < OUT_F32 || t.out_mode > OUT_HI)
+            t.stage_bytes * t.stages > RING_BYTES || t.out_mode < OUT_F32 || t.out_mode > OUT_SUM)
             return set_error(TFDE_EINVAL, "tfde_tune_set: entry " + std::to_string(i) + " out of range");
     }
     for (int i = 0; i < count; ++i) {

@@ -77,7 +77,12 @@ struct Segment {
 // preconditioner.  p_old is xp_old, or out_f32 itself (in place).
 // OUT_HI: the BF16 rounding of Y alone (out_hi), for consumers that read
 // only the hi plane.
-enum { OUT_F32 = 0, OUT_HILO = 1, OUT_XPAY = 2, OUT_HI = 3 };
+// OUT_SUM: FP32 output (out_f32) of addend + cs[line] (Y + mass_row[m] w),
+// w = dot_vec (optional, also dotted with the result into *dot_out), cs the
+// per-line factor col_scale (1 when null), addend optional: one axis term of
+// a Kronecker sum with diagonal factors on the other axes, accumulated pass
+// by pass (the operator in the sine-transform eigenbasis).
+enum { OUT_F32 = 0, OUT_HILO = 1, OUT_XPAY = 2, OUT_HI = 3, OUT_SUM = 4 };
 
 struct Params {
     CUtensorMap amaps[4];
@@ -120,6 +125,11 @@ struct Params {
     const double* xp_num;   // OUT_XPAY: beta = *xp_num / *xp_den
     const double* xp_den;
     const float* xp_old;    // OUT_XPAY: the old p (null: out_f32 itself, updated in place)
+    // OUT_SUM: per-line factor (indexed by the output's line), an FP32
+    // addend in the output's layout, and a per-row factor of dot_vec
+    const float* col_scale;
+    const float* addend;
+    const float* mass_row;
     const int* skip;        // optional: a launch that finds *skip != 0 does no work (device-side loops)
     int* err;
 };
@@ -467,6 +477,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 ra = __ldg(p.lam_ra + m);
                 rb = __ldg(p.lam_rb + m);
             }
+            float mrow = 0.f;                     // OUT_SUM: this row's factor of dot_vec
+            if constexpr (OM == OUT_SUM) {
+                if (p.mass_row && mval) mrow = __ldg(p.mass_row + m);
+            }
             for (int cc = 0; cc < BN / 2; cc += 32) {
                 const int c0 = half * (BN / 2) + cc;
                 // chunk position: x axis -> lines line0 .. line0 + 31 (Y[line * n1 + m]);
@@ -487,6 +501,95 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 // element (m, column j) of the output in global memory
                 const long long gbase = b_kmajor ? line0 * p.n1 + m : (long long)pl * p.plane + (long long)m * p.C + cx;
                 const long long gstep = b_kmajor ? (long long)p.n1 : 1LL;
+                if constexpr (OM == OUT_SUM) {
+                    const bool use_w = p.dot_vec != nullptr;
+                    const bool use_ad = p.addend != nullptr;
+                    if constexpr (KM != 0) {
+                        // x axis (no addend or dot vector): the column factor
+                        // of this lane's line, broadcast by shuffles
+                        float csl = 1.f;
+                        if (p.col_scale && lane < ncol) csl = __ldg(p.col_scale + line0 + lane);
+                        if (pending && lane == 0) bulk_wait_read0();
+                        __syncwarp();
+#pragma unroll
+                        for (int hf = 0; hf < 2; ++hf) {
+                            uint32_t r[16];
+                            tmem_ld16(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN + c0 + 16 * hf), r);
+                            float* f = reinterpret_cast<float*>(slot);
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                f[(16 * hf + j) * 32 + lane] =
+                                    __shfl_sync(0xffffffffu, csl, 16 * hf + j) * (p.alpha * __uint_as_float(r[j]));
+                        }
+                    } else {
+                        // y / z axes: the chunk's addend and dot vector are read
+                        // coalesced (lane l: rows 4i + l / 8, columns 4 (l % 8)
+                        // .. + 3, a 128-byte row segment per 8 lanes), issued
+                        // before the accumulator read; the accumulator goes
+                        // through the slot from its row layout to that one
+                        const int rr = lane >> 3, c4 = (lane & 7) * 4;
+                        const bool cval = c4 < ncol;
+                        const long long cbase = (long long)pl * p.plane + cx + c4;
+                        float4 ad4[8], w4[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int row = mrow0 + 4 * i + rr;   // the warp's first row + 4 i + l / 8
+                            const bool ok = cval && row < p.n;
+                            const long long g = cbase + (long long)row * p.C;
+                            ad4[i] = (use_ad && ok) ? __ldg(reinterpret_cast<const float4*>(p.addend + g))
+                                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+                            w4[i] = (use_w && ok) ? __ldg(reinterpret_cast<const float4*>(p.dot_vec + g))
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                        float4 cs4 = make_float4(1.f, 1.f, 1.f, 1.f);
+                        if (p.col_scale && cval)
+                            cs4 = __ldg(reinterpret_cast<const float4*>(p.col_scale + (long long)pl * p.C + cx + c4));
+                        if (pending && lane == 0) bulk_wait_read0();
+                        __syncwarp();
+#pragma unroll
+                        for (int hf = 0; hf < 2; ++hf) {
+                            uint32_t r[16];
+                            tmem_ld16(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN + c0 + 16 * hf), r);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                *reinterpret_cast<float4*>(slot + lane * 128 + (((4 * hf + k) ^ (lane & 7)) << 4)) =
+                                    make_float4(p.alpha * __uint_as_float(r[4 * k]),
+                                                p.alpha * __uint_as_float(r[4 * k + 1]),
+                                                p.alpha * __uint_as_float(r[4 * k + 2]),
+                                                p.alpha * __uint_as_float(r[4 * k + 3]));
+                        }
+                        __syncwarp();
+                        float dacc = 0.f;
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int row = 4 * i + rr;
+                            const int grow = mrow0 + row;
+                            const float mr = (p.mass_row && grow < p.n) ? __ldg(p.mass_row + grow) : 0.f;
+                            float4* e = reinterpret_cast<float4*>(slot + row * 128 + (((lane & 7) ^ (row & 7)) << 4));
+                            float4 t = *e;
+                            t.x = fmaf(cs4.x, fmaf(mr, w4[i].x, t.x), ad4[i].x);
+                            t.y = fmaf(cs4.y, fmaf(mr, w4[i].y, t.y), ad4[i].y);
+                            t.z = fmaf(cs4.z, fmaf(mr, w4[i].z, t.z), ad4[i].z);
+                            t.w = fmaf(cs4.w, fmaf(mr, w4[i].w, t.w), ad4[i].w);
+                            *e = t;
+                            dacc = fmaf(t.x, w4[i].x, dacc);   // w = 0 beyond ncol and below row n
+                            dacc = fmaf(t.y, w4[i].y, dacc);
+                            dacc = fmaf(t.z, w4[i].z, dacc);
+                            dacc = fmaf(t.w, w4[i].w, dacc);
+                        }
+                        if (use_w) da.add(dacc);
+                    }
+                    if (ncol == 0) continue;   // warp-uniform
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (b_kmajor) tma_store_2d(&p.omap_f32, slot, mrow0, (int)line0);
+                        else tma_store_3d(&p.omap_f32, slot, cx, mrow0, pl);
+                        bulk_commit();
+                    }
+                    pending = true;
+                    continue;
+                }
                 // the chunk's other global operand (the old direction of the
                 // update, or the vector of the fused inner product), loaded
                 // before the accumulator read so that the two latencies overlap
@@ -600,7 +703,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     if (lane == 0) bulk_wait_read0();
                     __syncwarp();
                 }
-                if constexpr (OM != OUT_F32) {
+                if constexpr (OM == OUT_HILO || OM == OUT_XPAY || OM == OUT_HI) {
                     uint8_t* hs = slot;
                     if constexpr (OM == OUT_HI) {
                         hs = slot + half_sel * 2048;

@@ -78,7 +78,7 @@ EXPORTS = ["tfde_assemble", "tfde_destroy", "tfde_matvec", "tfde_precond", "tfde
            "tfde_stats_reset", "tfde_stats_get", "tfde_mass_apply_noalloc", "tfde_batch_create", "tfde_batch_destroy",
            "tfde_batch_count", "tfde_batch_set_guess_order", "tfde_batch_cn_advance", "tfde_cn_advance_guess", "tfde_cnn_create", "tfde_cnn_destroy",
            "tfde_cnn_set_params", "tfde_cnn_get_params", "tfde_cnn_get_grads", "tfde_cnn_predict", "tfde_cnn_accumulate", "tfde_cnn_predict_hist", "tfde_cnn_accumulate_hist",
-           "tfde_cnn_adam_step", "tfde_selftest_wait", "tfde_set_device_loop", "tfde_spectrum", "tfde_tune", "tfde_batch_tune",
+           "tfde_cnn_adam_step", "tfde_selftest_wait", "tfde_set_device_loop", "tfde_set_spectral_inner", "tfde_spectrum", "tfde_tune", "tfde_batch_tune",
            "tfde_tune_get", "tfde_tune_set", "tfde_tune_clear", "tfde_last_error", "tfde_version"]
 
 
@@ -129,6 +129,7 @@ def load(path: str | None = None):
         "tfde_cnn_accumulate_hist": ([vp, vp, vp, vp, vp, POINTER(c_double), vp, POINTER(c_double), vp], c_int),
         "tfde_selftest_wait": ([c_longlong, POINTER(c_int), vp], c_int),
         "tfde_set_device_loop": ([vp, c_int], c_int),
+        "tfde_set_spectral_inner": ([vp, c_int], c_int),
         "tfde_spectrum": ([POINTER(tfde_params), c_int, vp, POINTER(tfde_spectrum_info), vp], c_int),
         "tfde_tune": ([vp, c_int, vp], c_int),
         "tfde_batch_tune": ([vp, c_int, vp], c_int),
@@ -294,6 +295,10 @@ def tfde_spectrum(params: tfde_params, steps: int, v0, stream=None) -> tfde_spec
 
 def tfde_set_device_loop(prob: int, enable: bool) -> None:
     _check(load().tfde_set_device_loop(prob, int(bool(enable))), "tfde_set_device_loop")
+
+
+def tfde_set_spectral_inner(prob: int, enable: bool) -> None:
+    _check(load().tfde_set_spectral_inner(prob, int(bool(enable))), "tfde_set_spectral_inner")
 
 
 def tfde_selftest_wait(limit_ns: int, stream=None) -> tuple[int, int]:
