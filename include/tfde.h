@@ -241,25 +241,28 @@ int tfde_set_guess_order(tfde_problem* prob, int order);
 int tfde_set_device_loop(tfde_problem* prob, int enable);
 
 /*
- * tfde_set_spectral_inner -- the basis in which the inner PCG of a symmetric
- * TFDE_MIXED problem (tensor-core path) iterates (Sec. 3.1 PCG with the tau
- * preconditioner P = S_N Lambda S_N of Eq. (diag_tau_pre)).
- *   enable != 0 (default where available): in the sine-transform
- *   eigenbasis.  S_N is symmetric and orthogonal and diagonalises P and the
- *   mass operator A_N, so PCG on A c = r with P is PCG on S_N A S_N with the
- *   diagonal Lambda: the residual is transformed once per refinement sweep
- *   (three split-BF16 passes with S_n split into hi + lo), each iteration
- *   applies S_N A S_N as three split passes (one per axis: S_n eta_a B_a S_n
- *   along the axis, the other axes' mass eigenvalues as per-line factors) and
- *   the preconditioner pointwise, and the combined correction goes back
- *   through S_N once per sweep.  The same iterates as enable = 0 in exact
- *   arithmetic; 3 instead of 9 tensor-core passes per iteration.
- *   enable = 0: the physical basis (operator in 3 and preconditioner in 6
- *   split passes per iteration).
+ * tfde_set_spectral_inner -- the basis in which the inner Krylov solves of a
+ * TFDE_MIXED problem on the tensor-core path iterate: PCG (Sec. 3.1) and
+ * left-preconditioned GMRES (Sec. 3.2, Eq. (one_side_system)) with the tau
+ * preconditioner P = S_N Lambda S_N of Eq. (diag_tau_pre).
+ *   enable != 0 (default): in the sine-transform eigenbasis.  S_N is
+ *   symmetric and orthogonal and diagonalises P and the mass operator A_N, so
+ *   the preconditioned system becomes S_N A S_N with the diagonal Lambda: the
+ *   residual is transformed once per refinement sweep (three split-BF16
+ *   passes with S_n split into hi + lo), each iteration applies S_N A S_N as
+ *   three split passes (one per axis: S_n eta_a B_a S_n along the axis, the
+ *   other axes' mass eigenvalues as per-line factors; for GMRES Lambda^{-1}
+ *   fused into the last) and the preconditioner pointwise, and the
+ *   correction goes back through S_N once per sweep.  The same iterates as
+ *   enable = 0 in exact arithmetic; 3 instead of 9 tensor-core passes per
+ *   iteration.
+ *   enable = 0: the grid basis (operator in 3 and preconditioner in 6 split
+ *   passes per iteration).
  * The refinement's FP64 residual, and so the result's accuracy, are the same
- * either way.  Errors: TFDE_EINVAL for a NULL problem; TFDE_EUNSUPPORTED when
- * enable != 0 for a non-symmetric, TFDE_FP64 or FFT-path problem (enable = 0
- * is accepted and has no effect there).
+ * either way.  The batched solver always iterates in the grid basis.
+ * Errors: TFDE_EINVAL for a NULL problem; TFDE_EUNSUPPORTED when enable != 0
+ * for a TFDE_FP64 problem or a TFDE_MIXED problem on the FFT passes (enable =
+ * 0 is accepted and has no effect there).
  */
 int tfde_set_spectral_inner(tfde_problem* prob, int enable);
 

@@ -348,6 +348,8 @@ double host_scalar(const tfde_problem* P, const double* dev, cudaStream_t s, int
 // Device-scalar slots: <p, A p>, <r, r>, and <r, z> of the current / next
 // iteration in alternating slots (a kernel that reads one writes the other).
 enum { D_PQ = 0, D_RR = 1, D_RZ0 = 2, D_RZ1 = 3 };
+// Device / host Hessenberg scratch offsets (MixedState::gm).
+enum { GM_H = 0, GM_H2 = 128, GM_WW = 256, GM_Y = 384, GM_SIZE = 512 };
 
 int build_pcg_graph(const tfde_problem* P, cudaStream_t s);
 int inner_pcg_graph(const tfde_problem* P, double theta, int maxit, int* iters, PcgPending* pend, cudaStream_t s,
@@ -599,8 +601,10 @@ int spec_transform(const tfde_problem* P, int in, int mid1, int mid2, float* out
 //   z: q = s2 + cs_z . ((Bh3 p)_z + mu3 p)
 // with Bh_a = S (eta_a B_a) S and cs the products of the other axes' mass
 // eigenvalues per line.  s1, s2 live in F_Z, F_P.
+// With lam_div (PGMRES): q = Lambda^{-1} (S_N A S_N) p, the mass part taken
+// from the split planes of p, no inner product.
 int spec_matvec(const tfde_problem* P, const float* pf, float* q, double* pq, cudaStream_t s,
-                const int* skip = nullptr) {
+                const int* skip = nullptr, bool lam_div = false) {
     MixedState* M = mixed(P);
     const long long n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
     const float* cs_x = M->spec;
@@ -615,7 +619,7 @@ int spec_matvec(const tfde_problem* P, const float* pf, float* q, double* pq, cu
         tc::Params prm;
         double bytes, flops;
         float* out = a == 0 ? s1 : (a == 1 ? s2 : q);
-        gemm_params(P, a, sg, 1, tc::OUT_SUM, 1.f, out, -1, false, prm, &bytes, &flops);
+        gemm_params(P, a, sg, 1, tc::OUT_SUM, 1.f, out, -1, lam_div && a == 2, prm, &bytes, &flops);
         prm.col_scale = a == 0 ? cs_x : (a == 1 ? cs_y : cs_z);
         if (a > 0) {
             prm.addend = a == 1 ? s1 : s2;
@@ -623,8 +627,13 @@ int spec_matvec(const tfde_problem* P, const float* pf, float* q, double* pq, cu
         }
         if (a == 2) {
             prm.mass_row = mu3;
-            prm.dot_vec = pf;
-            prm.dot_out = pq;
+            if (lam_div) {
+                prm.dot_hi = M->hi[PL_P];
+                prm.dot_lo = M->lo[PL_P];
+            } else {
+                prm.dot_vec = pf;
+                prm.dot_out = pq;
+            }
             bytes += 4.0 * N;
         }
         prm.skip = skip;
@@ -827,6 +836,163 @@ int spec_finish(const tfde_problem* P, const PcgPending& pend, cudaStream_t s) {
     return spec_transform(P, PL_T1, PL_T2, PL_R, M->f[F_X], s);
 }
 
+// ---- left-preconditioned GMRES in the eigenbasis (Sec. 3.2): the Arnoldi
+// vectors live in the eigenbasis, Lambda^{-1} S_N A S_N v is three split
+// passes with the division fused into the last, and the cycle's correction
+// goes back through S_N once.  Inner products and norms are those of the grid
+// basis (S_N is orthogonal), so the cycle's iterates are the grid-basis ones.
+int build_gmres_graph_spec(const tfde_problem* P, int restart, cudaStream_t s) {
+    MixedState* M = mixed(P);
+    if (M->gms_graph_failed || restart > GS_MAXM) return TFDE_OK;
+    if (M->gms_exec && M->gms_graph_restart == restart && M->gms_tune_gen == tc::tune_generation()) return TFDE_OK;
+    if (M->gms_exec) {
+        cudaGraphExecDestroy(M->gms_exec);
+        cudaGraphDestroy(M->gms_graph);
+        M->gms_exec = nullptr;
+        M->gms_graph = nullptr;
+    }
+    if (int st = tc::set_attrs()) return st;
+    const size_t N = P->N;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+    cudaGraphConditionalHandle h{};
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    if (ok) ok = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+    }
+    if (ok) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+             cudaSuccess;
+        if (ok) {
+            stats_set_capturing(true);
+            const int* skip = M->gm_ctl + 1;
+            int st = spec_matvec(P, nullptr, M->f[F_Z], nullptr, s, skip, true);   // w = Lambda^{-1} A~ v_j
+            if (!st)
+                launch_gm_step(N, M->V32, M->f[F_Z], P->red, P->nblk, M->gm + GM_H, M->gm + GM_H2, M->gm + GM_WW,
+                               M->gm_state, M->gm_ctl, h, nullptr, M->hi[PL_P], M->lo[PL_P], restart + 1, s);
+            stats_set_capturing(false);
+            cudaGraph_t out = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(s, &out);
+            ok = st == TFDE_OK && e == cudaSuccess;
+        }
+    }
+    if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        M->gms_graph_failed = true;
+        set_error(TFDE_OK, "");
+        return TFDE_OK;
+    }
+    M->gms_graph = g;
+    M->gms_exec = ex;
+    M->gms_graph_restart = restart;
+    M->gms_tune_gen = tc::tune_generation();
+    return TFDE_OK;
+}
+
+// One GMRES cycle in the eigenbasis: the caller has written the scaled
+// residual as split planes PL_R; on return F_X = S_N d~ (the cycle's
+// correction in the grid basis), as inner_gmres leaves d in F_X.
+int inner_gmres_spec(const tfde_problem* P, int restart, double ptheta, int maxit, int* iters, double* est_ratio,
+                     cudaStream_t s) {
+    MixedState* M = mixed(P);
+    const size_t N = P->N;
+    float* V = M->V32;
+    double* g = M->gm;
+    int st;
+    *iters = 0;
+    *est_ratio = 1.0;
+    if ((st = spec_transform(P, PL_R, PL_T1, PL_T2, M->f[F_R], s))) return st;   // r~ = S_N r
+    // w = Lambda^{-1} r~ (FP32 into F_Z; its planes are overwritten by the cycle start)
+    if ((st = launch_spec_direction(M->lam, P->n, nullptr, nullptr, M->f[F_R], nullptr, M->f[F_Z], M->hi[PL_P],
+                                    M->lo[PL_P], nullptr, s)))
+        return st;
+    MX_TRY(cudaMemsetAsync(M->f[F_X], 0, N * sizeof(float), s));
+    int k = 0;
+    if (M->device_loop && !stats_timing() && maxit > 0 && restart <= GS_MAXM) {
+        if ((st = build_gmres_graph_spec(P, restart, s))) return st;
+    }
+    if (M->device_loop && !stats_timing() && maxit > 0 && M->gms_exec && M->gms_graph_restart == restart) {
+        MX_TRY(cudaMemsetAsync(M->gm_ctl, 0, 4 * sizeof(int), s));
+        const int maxsteps = restart < maxit ? restart : maxit;
+        launch_gm_start(N, M->f[F_Z], P->red, P->nblk, g + GM_WW, M->gm_state, M->gm_ctl, maxsteps, ptheta, V,
+                        M->hi[PL_P], M->lo[PL_P], s);
+        MX_TRY(cudaGraphLaunch(M->gms_exec, s));
+        launch_gm_solve(M->gm_state, M->gm_ctl, g + GM_Y, restart, s);
+        launch_multiaxpy32(N, restart, V, N, g + GM_Y, M->f[F_X], s);   // x32 = sum_i y_i v_i
+        MX_TRY(cudaMemcpyAsync(M->gm_ctl_host, M->gm_ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        MX_TRY(cudaMemcpyAsync(P->red_host, M->gm_state, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        MX_TRY(cudaStreamSynchronize(s));
+        k = M->gm_ctl_host[0];
+        stats_count_launch((unsigned)(k > 0 ? k : 1) * 13u);   // the graph's launches, 13 per step
+        const double beta = P->red_host[GS_BETA], est = P->red_host[GS_EST];
+        if (M->gm_ctl_host[3] || !std::isfinite(beta))
+            return set_error(TFDE_ENAN, "non-finite preconditioned residual or Arnoldi vector");
+        *iters = k;
+        *est_ratio = beta > 0.0 ? est / beta : 1.0;
+    } else {
+        double* gh = M->gm_host;
+        MX_TRY(cudaMemcpyAsync(V, M->f[F_Z], N * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        launch_dot32(N, V, V, P->red, P->nblk, s);
+        launch_reduce_finish(P->red, P->nblk, 1, g + GM_WW, s);
+        MX_TRY(cudaMemcpyAsync(gh + GM_WW, g + GM_WW, sizeof(double), cudaMemcpyDeviceToHost, s));
+        MX_TRY(cudaStreamSynchronize(s));
+        const double beta = std::sqrt(gh[GM_WW]);
+        if (!std::isfinite(beta)) return set_error(TFDE_ENAN, "non-finite preconditioned residual");
+        if (beta > 0.0) {
+            launch_scale_split32(N, (float)(1.0 / beta), V, V, M->hi[PL_P], M->lo[PL_P], s);
+            GivensLS ls(restart);
+            ls.g[0] = beta;
+            std::vector<double> h(restart + 2);
+            double est = beta;
+            for (int j = 0; j < restart && j < maxit; ++j) {
+                float* w = V + (size_t)(j + 1) * N;
+                if ((st = spec_matvec(P, nullptr, w, nullptr, s, nullptr, true))) return st;   // w = Lambda^{-1} A~ v_j
+                launch_multidot32(N, j + 1, V, N, w, P->red, P->nblk, s);
+                launch_reduce_finish(P->red, P->nblk, j + 1, g + GM_H, s);
+                launch_multiaxpy32(N, j + 1, V, N, g + GM_H, w, s);
+                launch_multidot32(N, j + 1, V, N, w, P->red, P->nblk, s);
+                launch_reduce_finish(P->red, P->nblk, j + 1, g + GM_H2, s);
+                launch_multiaxpy32(N, j + 1, V, N, g + GM_H2, w, s);
+                launch_dot32(N, w, w, P->red, P->nblk, s);
+                launch_reduce_finish(P->red, P->nblk, 1, g + GM_WW, s);
+                MX_TRY(cudaMemcpyAsync(gh, g, (GM_WW + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+                MX_TRY(cudaStreamSynchronize(s));
+                for (int i = 0; i <= j; ++i) h[i] = gh[GM_H + i] + gh[GM_H2 + i];
+                const double hn = std::sqrt(gh[GM_WW]);
+                if (!std::isfinite(hn)) return set_error(TFDE_ENAN, "non-finite Arnoldi vector");
+                h[j + 1] = hn;
+                est = ls.add_column(j, h.data());
+                k = j + 1;
+                if (est <= ptheta * beta || hn == 0.0) break;
+                launch_scale_split32(N, (float)(1.0 / hn), w, w, M->hi[PL_P], M->lo[PL_P], s);
+            }
+            *iters = k;
+            *est_ratio = est / beta;
+            if (k > 0) {
+                std::vector<double> y;
+                ls.solve(k, y);
+                for (int i = 0; i < k; ++i) gh[GM_Y + i] = -y[i];
+                MX_TRY(cudaMemcpyAsync(g + GM_Y, gh + GM_Y, k * sizeof(double), cudaMemcpyHostToDevice, s));
+                launch_multiaxpy32(N, k, V, N, g + GM_Y, M->f[F_X], s);   // x32 = sum_i y_i v_i
+            }
+        }
+    }
+    // back to the grid basis: F_X = S_N x32
+    launch_split32(N, M->f[F_X], M->hi[PL_T1], M->lo[PL_T1], s);
+    if ((st = spec_transform(P, PL_T1, PL_T2, PL_R, M->f[F_X], s))) return st;
+    return check_err(P, s);
+}
+
 // r = b - A x (accurate) and ||r||, the norm accumulated by the last pass of
 // the contraction with the terms scaled by 2^-ilogb(nb).
 // With an_out, A_N x also goes there (from the z-pass digit slicing).
@@ -861,8 +1027,6 @@ int initial_norms(tfde_problem* P, const double* b, const double* r, bool r_give
     return TFDE_OK;
 }
 
-// Device / host Hessenberg scratch offsets (MixedState::gm).
-enum { GM_H = 0, GM_H2 = 128, GM_WW = 256, GM_Y = 384, GM_SIZE = 512 };
 
 int ensure_v32(const tfde_problem* P, int restart) {
     MixedState* M = mixed(P);
@@ -1150,9 +1314,9 @@ int mixed_init(tfde_problem* P, cudaStream_t s) {
                              om == OM_GZN_L;
         if (int st = upload_matrix(M, om, h, n, pair_hi, pair_lo, s)) return st;
     }
-    // the inner PCG in the sine-transform eigenbasis (symmetric problems, Sec. 3.1):
-    // per axis S_n (eta_a B_a) S_n and S_n itself, each split into hi + lo
-    if (P->symmetric) {
+    // the inner solves in the sine-transform eigenbasis (Sec. 3.1, 3.2): per
+    // axis S_n (eta_a B_a) S_n and S_n itself, each split into hi + lo
+    {
         for (int a = 0; a < 3; ++a) {
             const int n = P->n[a];
             const std::vector<double> S = dst_dense(n);
@@ -1234,7 +1398,7 @@ int mixed_init(tfde_problem* P, cudaStream_t s) {
     // products, D_a = diag of the mass eigenvalues, Bh_a = S (eta_a B_a) S),
     // so each axis term is the contraction along its axis scaled by the mass
     // eigenvalues of the other two axes, and D3 D2 D1 is the z term's mass part
-    if (P->symmetric) {
+    {
         const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
         const std::vector<double>&m1 = P->lam_mass[0], &m2 = P->lam_mass[1], &m3 = P->lam_mass[2];
         std::vector<float> f;
@@ -1291,6 +1455,8 @@ void mixed_free(tfde_problem* P) {
     if (M->pcg_graph) cudaGraphDestroy(M->pcg_graph);
     if (M->spec_exec) cudaGraphExecDestroy(M->spec_exec);
     if (M->spec_graph) cudaGraphDestroy(M->spec_graph);
+    if (M->gms_exec) cudaGraphExecDestroy(M->gms_exec);
+    if (M->gms_graph) cudaGraphDestroy(M->gms_graph);
     cudaFree(M->pcg_ctl);
     if (M->pcg_ctl_host) cudaFreeHost(M->pcg_ctl_host);
     cudaFree(M->pair_d);
@@ -1499,7 +1665,11 @@ int mixed_pgmres(tfde_problem* P, const double* b, double* x, int restart, doubl
         launch_scale64to32(P->N, r64, 1.0 / nr, M->f[F_R], M->hi[PL_R], M->lo[PL_R], M->f[F_X], s);
         int it = 0;
         double est_ratio = 1.0;
-        if ((st = inner_gmres(P, restart, theta, maxit - loc.iters, &it, &est_ratio, s))) return st;
+        if (M->spectral) {
+            if ((st = inner_gmres_spec(P, restart, theta, maxit - loc.iters, &it, &est_ratio, s))) return st;
+        } else if ((st = inner_gmres(P, restart, theta, maxit - loc.iters, &it, &est_ratio, s))) {
+            return st;
+        }
         loc.iters += it;
         loc.restarts++;
         loc.refine_sweeps++;
@@ -1557,7 +1727,7 @@ int mixed_tune(tfde_problem* P, int reps, cudaStream_t s) {
 int mixed_set_spectral(tfde_problem* P, int enable) {
     MixedState* M = mixed(P);
     if (!M || !M->spectral_ok) {
-        if (enable) return set_error(TFDE_EUNSUPPORTED, "the eigenbasis inner PCG needs a symmetric TFDE_MIXED problem on the tensor-core path");
+        if (enable) return set_error(TFDE_EUNSUPPORTED, "the eigenbasis inner solves need a TFDE_MIXED problem on the tensor-core path");
         return TFDE_OK;
     }
     M->spectral = enable != 0;

@@ -148,13 +148,17 @@ struct MixedState {
     CUtensorMap omap_hl[NPL][3];   // hi and lo as one tensor (lo = hi + N): one store per chunk
     float* f[NF] = {};
     float* lam = nullptr;   // [ra (n3) | rb (n3) | U (n1 n2) | V (n1 n2)]
-    // inner PCG in the sine-transform eigenbasis (built for symmetric
-    // problems): per-line factors of the three axis terms and the z-axis
+    // inner solves in the sine-transform eigenbasis: per-line factors of the three axis terms and the z-axis
     // mass eigenvalues, [cs_x (n2 n3) | cs_y (n1 n3) | cs_z (n1 n2) | mu3 (n3)]
     float* spec = nullptr;
     bool spectral_ok = false;    // the matrices and factors exist
     bool spectral = false;       // tfde_set_spectral_inner (default on when available)
     long long spec_transforms = 0;   // sine transforms run (statistics)
+    cudaGraph_t gms_graph = nullptr;     // the eigenbasis GMRES cycle's Arnoldi steps as one graph launch
+    cudaGraphExec_t gms_exec = nullptr;
+    bool gms_graph_failed = false;
+    int gms_graph_restart = 0;
+    unsigned gms_tune_gen = 0;
     cudaGraph_t spec_graph = nullptr;    // the eigenbasis inner PCG as one graph launch per sweep
     cudaGraphExec_t spec_exec = nullptr;
     bool spec_graph_failed = false;

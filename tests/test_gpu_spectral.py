@@ -1,13 +1,13 @@
-"""The inner PCG in the sine-transform eigenbasis (tfde_set_spectral_inner).
+"""The inner solves in the sine-transform eigenbasis (tfde_set_spectral_inner).
 
 S_N is symmetric and orthogonal and diagonalises the tau preconditioner and
 the mass operator (Eq. (diag_tau_pre); the mass matrices are tridiagonal
 Toeplitz), so PCG with P on A c = r is PCG with the diagonal Lambda on
-S_N A S_N (Sec. 3.1): the same iterates in exact arithmetic.  The refined
-solutions of both bases must match the oracle's PCG solution, with the same
-iteration counts up to rounding, and the eigenbasis must run three
-tensor-core passes per inner iteration (plus two sine transforms of three
-passes per refinement sweep)."""
+S_N A S_N (Sec. 3.1), and left-preconditioned GMRES likewise (Sec. 3.2): the
+same iterates in exact arithmetic.  The refined solutions of both bases must
+match the oracle's, with the same iteration counts up to rounding, and the
+eigenbasis must run three tensor-core passes per inner iteration (plus two
+sine transforms of three passes per refinement sweep)."""
 import math
 
 import numpy as np
@@ -133,15 +133,53 @@ def test_chained_cn_steps_in_the_eigenbasis_match_oracle(T):
         T.tfde_destroy(h)
 
 
+NONSYM = [
+    ((40, 32, 24), (0.3, 0.6, 0.8), (1.0, 1.5, 2.0), (0.5, 2.0, 1.0), 0.1, 20),
+    ((64, 24, 136), (0.7, 0.2, 0.9), (2.0, 1.0, 0.5), (1.0, 0.5, 1.5), 0.05, 4),   # short cycles, ragged tiles
+]
+
+
+@pytest.mark.parametrize("case", NONSYM, ids=lambda c: "x".join(map(str, c[0])) + f"_m{c[5]}")
+def test_eigenbasis_and_grid_basis_pgmres_match_oracle(T, case):
+    """Left-preconditioned GMRES (Sec. 3.2) in both bases: Lambda^{-1} S_N A S_N
+    in the eigenbasis is the grid basis's P^{-1} A transformed by S_N, so the
+    refined solutions match the oracle's and the Arnoldi step counts agree."""
+    n, d, kp, km, dt, restart = case
+    op = o.Problem(n=n, delta=d, kp=kp, km=km, dt=dt)
+    b = inp.uniform_vector(op.shape, 74)
+    tau = o.build_tau(op)
+    xref, _ = o.gmres_left(lambda v: o.apply_A(op, v), lambda r: o.apply_Pinv(tau, r), b, np.zeros_like(b), 1e-14,
+                           4000, restart=20, criterion="true")
+    iters = {}
+    for spectral in (True, False):
+        for dev_loop in ((True, False) if spectral else (True,)):
+            h = T.tfde_assemble(T.make_params(n, d, kp, km, dt), T.TFDE_MIXED)
+            try:
+                T.tfde_set_spectral_inner(h, spectral)
+                T.tfde_set_device_loop(h, dev_loop)
+                x = to_dev(np.zeros_like(b))
+                info = T.tfde_pgmres(h, to_dev(b), x, restart, 1e-12, 4000)
+                assert info.relres <= 1e-12 and info.fallback == 0, (spectral, dev_loop, info.relres)
+                assert relerr(to_host(x), xref) < 1e-10
+                iters[(spectral, dev_loop)] = info.iters
+            finally:
+                T.tfde_destroy(h)
+    assert iters[(True, True)] == iters[(True, False)], iters
+    assert abs(iters[(True, True)] - iters[(False, True)]) <= max(2, iters[(False, True)] // 5), iters
+
+
 def test_toggle_rejected_where_unavailable(T):
-    ns = T.tfde_assemble(T.make_params((16, 16, 16), (0.5,) * 3, (1.0,) * 3, (0.5,) * 3, 0.1), T.TFDE_MIXED)
     f64 = T.tfde_assemble(T.make_params((16, 16, 16), (0.5,) * 3, (1.0,) * 3, (1.0,) * 3, 0.1), T.TFDE_FP64)
+    fft = T.tfde_assemble(T.make_params((15, 16, 17), (0.5,) * 3, (1.0,) * 3, (1.0,) * 3, 0.1), T.TFDE_MIXED)
+    ns = T.tfde_assemble(T.make_params((16, 16, 16), (0.5,) * 3, (1.0,) * 3, (0.5,) * 3, 0.1), T.TFDE_MIXED)
     try:
-        for h in (ns, f64):
+        for h in (f64, fft):
             with pytest.raises(T.TfdeError) as e:
                 T.tfde_set_spectral_inner(h, True)
             assert e.value.status == T.TFDE_EUNSUPPORTED
             T.tfde_set_spectral_inner(h, False)   # accepted, no effect
+        T.tfde_set_spectral_inner(ns, True)        # non-symmetric tensor-core problems have it too
+        T.tfde_set_spectral_inner(ns, False)
     finally:
-        T.tfde_destroy(ns)
-        T.tfde_destroy(f64)
+        for h in (f64, fft, ns):
+            T.tfde_destroy(h)
