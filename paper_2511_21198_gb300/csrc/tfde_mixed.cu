@@ -595,14 +595,14 @@ int spec_transform(const tfde_problem* P, int in, int mid1, int mid2, float* out
     return TFDE_OK;
 }
 
-// q = (S_N A S_N) p, p given as the split planes PL_P and in FP32 (pf: the
-// z term's mass part D3 D2 D1 p and the fused <p, q> into *pq):
-//   x: s1 = cs_x . (Bh1 p)_x ; y: s2 = s1 + cs_y . (Bh2 p)_y ;
-//   z: q = s2 + cs_z . ((Bh3 p)_z + mu3 p)
-// with Bh_a = S (eta_a B_a) S and cs the products of the other axes' mass
-// eigenvalues per line.  s1, s2 live in F_Z, F_P.
-// With lam_div (PGMRES): q = Lambda^{-1} (S_N A S_N) p, the mass part taken
-// from the split planes of p, no inner product.
+// q = (S_N A S_N) p, p given as the split planes PL_P (and in FP32 as pf for
+// the fused <p, q> into *pq):
+//   x: s1 = cs_x . ((D1 + Bh1) p)_x ; y: s2 = s1 + cs_y . (Bh2 p)_y ;
+//   z: q = s2 + cs_z . (Bh3 p)_z
+// with Bh_a = S (eta_a B_a) S, D1 = diag(mu_1) and cs the products of the
+// other axes' mass eigenvalues per line (cs_x D1 = D3 D2 D1, the mass part).
+// s1, s2 live in F_Z, F_P.
+// With lam_div (PGMRES): q = Lambda^{-1} (S_N A S_N) p, no inner product.
 int spec_matvec(const tfde_problem* P, const float* pf, float* q, double* pq, cudaStream_t s,
                 const int* skip = nullptr, bool lam_div = false) {
     MixedState* M = mixed(P);
@@ -610,7 +610,6 @@ int spec_matvec(const tfde_problem* P, const float* pf, float* q, double* pq, cu
     const float* cs_x = M->spec;
     const float* cs_y = cs_x + n2 * n3;
     const float* cs_z = cs_y + n1 * n3;
-    const float* mu3 = cs_z + n1 * n2;
     float* s1 = M->f[F_Z];
     float* s2 = M->f[F_P];
     const double N = (double)P->N;
@@ -625,15 +624,9 @@ int spec_matvec(const tfde_problem* P, const float* pf, float* q, double* pq, cu
             prm.addend = a == 1 ? s1 : s2;
             bytes += 4.0 * N;
         }
-        if (a == 2) {
-            prm.mass_row = mu3;
-            if (lam_div) {
-                prm.dot_hi = M->hi[PL_P];
-                prm.dot_lo = M->lo[PL_P];
-            } else {
-                prm.dot_vec = pf;
-                prm.dot_out = pq;
-            }
+        if (a == 2 && !lam_div) {
+            prm.dot_vec = pf;
+            prm.dot_out = pq;
             bytes += 4.0 * N;
         }
         prm.skip = skip;
@@ -1336,6 +1329,10 @@ int mixed_init(tfde_problem* P, cudaStream_t s) {
                     double* br = Bh.data() + (size_t)i * n;
                     for (int j = 0; j < n; ++j) br[j] += tik * sr[j];
                 }
+            // the x axis also carries the mass eigenvalues mu_1 on its diagonal:
+            // its per-line factor mu_2 mu_3 then gives the whole D3 D2 D1 term
+            if (a == 0)
+                for (int i = 0; i < n; ++i) Bh[(size_t)i * n + i] += P->lam_mass[0][i];
             const int ob = OM_BX_H + 2 * a, os = OM_S2X_H + 2 * a;
             for (int part = 0; part < 2; ++part) {
                 const std::vector<double>& src = part == 0 ? Bh : S;

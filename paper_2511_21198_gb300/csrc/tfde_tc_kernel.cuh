@@ -77,9 +77,9 @@ struct Segment {
 // preconditioner.  p_old is xp_old, or out_f32 itself (in place).
 // OUT_HI: the BF16 rounding of Y alone (out_hi), for consumers that read
 // only the hi plane.
-// OUT_SUM: FP32 output (out_f32) of addend + cs[line] (Y + mass_row[m] w),
-// w = dot_vec (optional, also dotted with the result into *dot_out), cs the
-// per-line factor col_scale (1 when null), addend optional: one axis term of
+// OUT_SUM: FP32 output (out_f32) of addend + cs[line] Y, optionally dotted
+// with dot_vec into *dot_out, cs the per-line factor col_scale (1 when
+// null), addend optional: one axis term of
 // a Kronecker sum with diagonal factors on the other axes, accumulated pass
 // by pass (the operator in the sine-transform eigenbasis); on the z axis
 // with lam_ra set, the result is divided by Lambda (the preconditioned
@@ -127,14 +127,10 @@ struct Params {
     const double* xp_num;   // OUT_XPAY: beta = *xp_num / *xp_den
     const double* xp_den;
     const float* xp_old;    // OUT_XPAY: the old p (null: out_f32 itself, updated in place)
-    // OUT_SUM: per-line factor (indexed by the output's line), an FP32
-    // addend in the output's layout, and a per-row factor of dot_vec
+    // OUT_SUM: per-line factor (indexed by the output's line) and an FP32
+    // addend in the output's layout
     const float* col_scale;
     const float* addend;
-    const float* mass_row;
-    // OUT_SUM, y / z axes: w given as split planes (w = hi + lo) instead of dot_vec
-    const __nv_bfloat16* dot_hi;
-    const __nv_bfloat16* dot_lo;
     const int* skip;        // optional: a launch that finds *skip != 0 does no work (device-side loops)
     int* err;
 };
@@ -482,10 +478,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 ra = __ldg(p.lam_ra + m);
                 rb = __ldg(p.lam_rb + m);
             }
-            float mrow = 0.f;                     // OUT_SUM: this row's factor of dot_vec
-            if constexpr (OM == OUT_SUM) {
-                if (p.mass_row && mval) mrow = __ldg(p.mass_row + m);
-            }
             for (int cc = 0; cc < BN / 2; cc += 32) {
                 const int c0 = half * (BN / 2) + cc;
                 // chunk position: x axis -> lines line0 .. line0 + 31 (Y[line * n1 + m]);
@@ -507,7 +499,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const long long gbase = b_kmajor ? line0 * p.n1 + m : (long long)pl * p.plane + (long long)m * p.C + cx;
                 const long long gstep = b_kmajor ? (long long)p.n1 : 1LL;
                 if constexpr (OM == OUT_SUM) {
-                    const bool use_w = p.dot_vec != nullptr || p.dot_hi != nullptr;
+                    const bool use_w = p.dot_vec != nullptr;
                     const bool use_ad = p.addend != nullptr;
                     if constexpr (KM != 0) {
                         // x axis (no addend or dot vector): the column factor
@@ -543,30 +535,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                             const long long g = cbase + (long long)row * p.C;
                             ad4[i] = (use_ad && ok) ? __ldg(reinterpret_cast<const float4*>(p.addend + g))
                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
-                            if (use_w && ok && p.dot_hi) {
-                                const uint2 hv = __ldg(reinterpret_cast<const uint2*>(p.dot_hi + g));
-                                const uint2 lv = __ldg(reinterpret_cast<const uint2*>(p.dot_lo + g));
-                                w4[i] = make_float4(__uint_as_float(hv.x << 16) + __uint_as_float(lv.x << 16),
-                                                    __uint_as_float(hv.x & 0xffff0000u) +
-                                                        __uint_as_float(lv.x & 0xffff0000u),
-                                                    __uint_as_float(hv.y << 16) + __uint_as_float(lv.y << 16),
-                                                    __uint_as_float(hv.y & 0xffff0000u) +
-                                                        __uint_as_float(lv.y & 0xffff0000u));
-                            } else {
-                                w4[i] = (use_w && ok) ? __ldg(reinterpret_cast<const float4*>(p.dot_vec + g))
-                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
-                            }
+                            w4[i] = (use_w && ok) ? __ldg(reinterpret_cast<const float4*>(p.dot_vec + g))
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
                         }
                         float4 cs4 = make_float4(1.f, 1.f, 1.f, 1.f);
                         if (p.col_scale && cval)
                             cs4 = __ldg(reinterpret_cast<const float4*>(p.col_scale + (long long)pl * p.C + cx + c4));
-                        // optional Lambda^{-1} (z pass: rows k, columns i + n1 j): column factors here, row factors per row
+                        // optional Lambda^{-1} (z pass: rows k, columns i + n1 j)
                         const bool ldiv = p.lam_ra != nullptr;
-                        float4 lu4 = make_float4(1.f, 1.f, 1.f, 1.f), lv4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (ldiv && cval) {
-                            lu4 = __ldg(reinterpret_cast<const float4*>(p.lam_U + cx + c4));
-                            lv4 = __ldg(reinterpret_cast<const float4*>(p.lam_V + cx + c4));
-                        }
                         if (pending && lane == 0) bulk_wait_read0();
                         __syncwarp();
 #pragma unroll
@@ -587,16 +563,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         for (int i = 0; i < 8; ++i) {
                             const int row = 4 * i + rr;
                             const int grow = mrow0 + row;
-                            const float mr = (p.mass_row && grow < p.n) ? __ldg(p.mass_row + grow) : 0.f;
                             float4* e = reinterpret_cast<float4*>(slot + row * 128 + (((lane & 7) ^ (row & 7)) << 4));
                             float4 t = *e;
-                            t.x = fmaf(cs4.x, fmaf(mr, w4[i].x, t.x), ad4[i].x);
-                            t.y = fmaf(cs4.y, fmaf(mr, w4[i].y, t.y), ad4[i].y);
-                            t.z = fmaf(cs4.z, fmaf(mr, w4[i].z, t.z), ad4[i].z);
-                            t.w = fmaf(cs4.w, fmaf(mr, w4[i].w, t.w), ad4[i].w);
+                            t.x = fmaf(cs4.x, t.x, ad4[i].x);
+                            t.y = fmaf(cs4.y, t.y, ad4[i].y);
+                            t.z = fmaf(cs4.z, t.z, ad4[i].z);
+                            t.w = fmaf(cs4.w, t.w, ad4[i].w);
                             if (ldiv) {
                                 const float a = grow < p.n ? __ldg(p.lam_ra + grow) : 1.f;
                                 const float b = grow < p.n ? __ldg(p.lam_rb + grow) : 0.f;
+                                float4 lu4 = make_float4(1.f, 1.f, 1.f, 1.f), lv4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                                if (cval) {   // the column factors (L1-resident after the first row)
+                                    lu4 = __ldg(reinterpret_cast<const float4*>(p.lam_U + cx + c4));
+                                    lv4 = __ldg(reinterpret_cast<const float4*>(p.lam_V + cx + c4));
+                                }
                                 t.x = __fdividef(t.x, fmaf(a, lu4.x, b * lv4.x));
                                 t.y = __fdividef(t.y, fmaf(a, lu4.y, b * lv4.y));
                                 t.z = __fdividef(t.z, fmaf(a, lu4.z, b * lv4.z));
