@@ -1571,11 +1571,12 @@ int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit
         // accuracy); when the target needs more, two sweeps share it evenly
         // (theta = sqrt of the target, floored) instead of the first one
         // spending iterations below what it can deliver.  The inner target is
-        // 0.7 of what the sweep must reach: the split operator's error adds
-        // ~1e-4 of ||r|| on top (measured at the n = 256 workload: final
-        // residuals <= 0.7 tol in one sweep, 3.4 inner iterations per step
-        // instead of 3.6 with 0.5).
-        double theta = 0.7 * tol * nb / nr;
+        // 0.8 of what the sweep must reach: the split operator's error adds
+        // ~1e-4 of ||r|| on top (measured at the n = 256 workload with the
+        // eigenbasis inner PCG: final residuals <= 0.76 tol in one sweep, 3.1
+        // inner iterations per step against 3.2 with 0.7 and 3.3 with 0.6;
+        // 0.9 gives the same counts as 0.8).
+        double theta = 0.8 * tol * nb / nr;
         if (theta < kInnerFloor) theta = std::max(kInnerFloor, std::sqrt(theta));
         // r32 = r 2^k with 2^k the power of two nearest below 1 / ||r|| (an
         // exact scale: the conversion and, later, the scale back of the
