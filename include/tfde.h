@@ -336,6 +336,17 @@ int tfde_batch_count(const tfde_batch* batch);
 int tfde_batch_set_guess_order(tfde_batch* batch, int order);
 
 /*
+ * tfde_batch_set_spectral_inner -- the basis of the batched GMRES cycles
+ * (Sec. 3.2), as tfde_set_spectral_inner for one problem: enable != 0
+ * (default) runs every Arnoldi step as three grouped split passes of
+ * Lambda^{-1} S_N A S_N over all problems' tiles, with one forward (Lambda^{-1}
+ * fused) and one backward sine transform per cycle; enable = 0 the grid basis
+ * (five operator and six preconditioner passes per step).  Errors:
+ * TFDE_EINVAL for a NULL batch.
+ */
+int tfde_batch_set_spectral_inner(tfde_batch* batch, int enable);
+
+/*
  * tfde_batch_cn_advance -- one CN step u_i^{m-1} -> u_i^m IN PLACE for every
  * problem i of the batch, with the chained right-hand side and initial
  * residual of tfde_cn_advance (x0 = u_i^{m-1}).

@@ -49,6 +49,8 @@ struct BVec {
     __nv_bfloat16* pl;
     __nv_bfloat16* rh;
     __nv_bfloat16* rl;
+    __nv_bfloat16* th;   // split planes of the eigenbasis correction (PL_T1)
+    __nv_bfloat16* tl;
     const double* r64;
     double* x64;
 };
@@ -171,6 +173,14 @@ __global__ __launch_bounds__(kBT) void bk_scale_split(const BVec* __restrict__ v
         w[e] = x;
         split_bf16(x, v.ph[e], v.pl[e]);
     }
+}
+
+// (th, tl) = split(x32): the cycle's correction in the eigenbasis, before
+// its sine transform back to the grid
+__global__ __launch_bounds__(kBT) void bk_split_x32(const BVec* __restrict__ vt, const int* __restrict__ bi,
+                                                   const long long* __restrict__ bo, const int* __restrict__ act) {
+    BK_PROLOGUE
+    for (long long e = e0 + threadIdx.x; e < e1; e += kBT) split_bf16(v.x32[e], v.th[e], v.tl[e]);
 }
 
 // x64 += sc * x32
@@ -303,6 +313,17 @@ struct tfde_batch {
     int mv_axis[5] = {}, pc_axis[6] = {};
     int mv_out[5] = {}, pc_out[6] = {};   // output mode of each pass
     double mv_bytes[5] = {}, mv_flops[5] = {}, pc_bytes[6] = {}, pc_flops[6] = {};
+    // the eigenbasis cycle (spectral, default): forward sine transform with
+    // Lambda^{-1} fused [3][count] (the z pass writes V_0), the operator's x
+    // and y passes [2][count], its z pass writing V_j [restart+1][count], the
+    // backward transform [3][count]
+    bool spectral = true;
+    tfde::tc::Params* d_sfw = nullptr;
+    tfde::tc::Params* d_sop = nullptr;
+    tfde::tc::Params* d_sopz = nullptr;
+    tfde::tc::Params* d_sbw = nullptr;
+    double sfw_bytes[3] = {}, sfw_flops[3] = {}, sop_bytes[3] = {}, sop_flops[3] = {}, sbw_bytes[3] = {},
+           sbw_flops[3] = {};
     long long* d_gstart = nullptr;  // [3][count + 1]
     long long gtotal[3] = {};
     // vector kernels: per-problem pointers and the block table
@@ -371,6 +392,10 @@ int free_batch(tfde_batch* B) {
         if (i < B->own_err.size()) tfde::mixed(B->P[i])->err = B->own_err[i];
         destroy_problem(B->P[i]);
     }
+    cudaFree(B->d_sfw);
+    cudaFree(B->d_sop);
+    cudaFree(B->d_sopz);
+    cudaFree(B->d_sbw);
     cudaFree(B->d_mv);
     cudaFree(B->d_pc);
     cudaFree(B->d_pcl);
@@ -436,6 +461,37 @@ int grouped_precond(tfde_batch* B, int j, cudaStream_t s) {
                    B->pc_flops[5], s);
 }
 
+// eigenbasis: the scaled residual planes PL_R -> V_0 = Lambda^{-1} S_N r
+int grouped_spec_start(tfde_batch* B, cudaStream_t s) {
+    for (int a = 0; a < 3; ++a) {
+        int st = grouped(B, B->d_sfw + (size_t)a * B->count, a, a < 2 ? tc::OUT_HILO : tc::OUT_SUM, B->sfw_bytes[a],
+                         B->sfw_flops[a], s);
+        if (st) return st;
+    }
+    return TFDE_OK;
+}
+
+// eigenbasis: v_j (split planes PL_P) -> V_{j+1} = Lambda^{-1} S_N A S_N v_j
+int grouped_spec_step(tfde_batch* B, int j, cudaStream_t s) {
+    for (int a = 0; a < 2; ++a) {
+        int st = grouped(B, B->d_sop + (size_t)a * B->count, a, tc::OUT_SUM, B->sop_bytes[a], B->sop_flops[a], s);
+        if (st) return st;
+    }
+    return grouped(B, B->d_sopz + (size_t)j * B->count, 2, tc::OUT_SUM, B->sop_bytes[2], B->sop_flops[2], s);
+}
+
+// eigenbasis: x32 = S_N x32 for the problems with act set (planes PL_T1 -> PL_T2 -> PL_R -> x32)
+int grouped_spec_back(tfde_batch* B, cudaStream_t s) {
+    stats_count_launch();
+    bk_split_x32<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act);
+    for (int a = 0; a < 3; ++a) {
+        int st = grouped(B, B->d_sbw + (size_t)a * B->count, a, a < 2 ? tc::OUT_HILO : tc::OUT_F32, B->sbw_bytes[a],
+                         B->sbw_flops[a], s);
+        if (st) return st;
+    }
+    return TFDE_OK;
+}
+
 void vec_launch_count() { stats_count_launch(); }
 
 // dots <V_{p0+j}, V_jw>, j < m, of every active problem into out (stride, offset)
@@ -487,7 +543,7 @@ int batch_cycle(tfde_batch* B, const std::vector<int>& outer, const std::vector<
     B_TRY(cudaMemcpyAsync(B->d_theta, B->h_theta, C * sizeof(double), cudaMemcpyHostToDevice, s));
     B_TRY(cudaMemsetAsync(B->d_cnt, 0, (R + 1) * sizeof(int), s));
     B_TRY(cudaMemsetAsync(B->d_bad, 0, sizeof(int), s));
-    if ((st = grouped_precond(B, 0, s))) return st;
+    if ((st = B->spectral ? grouped_spec_start(B, s) : grouped_precond(B, 0, s))) return st;
     bdots(B, 0, 1, 0, B->d_s, kSS, S_WW, s);
     vec_launch_count();
     bk_cycle_start<<<gb, 64, 0, s>>>(C, R, B->d_gs, B->d_s, B->d_act, B->d_its, B->d_est, B->d_cnt, B->d_bad);
@@ -504,8 +560,12 @@ int batch_cycle(tfde_batch* B, const std::vector<int>& outer, const std::vector<
             B_TRY(cudaEventSynchronize(B->cnt_ev[j - 1]));
             if (B->h_cnt[j - 1] == 0) break;
         }
-        if ((st = grouped_matvec(B, s))) return st;
-        if ((st = grouped_precond(B, j + 1, s))) return st;
+        if (B->spectral) {
+            if ((st = grouped_spec_step(B, j + 1, s))) return st;
+        } else {
+            if ((st = grouped_matvec(B, s))) return st;
+            if ((st = grouped_precond(B, j + 1, s))) return st;
+        }
         // CGS2, coefficients on the device
         bdots(B, 0, j + 1, j + 1, B->d_h, kHS, 0, s);
         vec_launch_count();
@@ -543,6 +603,7 @@ int batch_cycle(tfde_batch* B, const std::vector<int>& outer, const std::vector<
         B_TRY(cudaMemcpyAsync(B->d_act, B->h_act, C * sizeof(int), cudaMemcpyHostToDevice, s));
         vec_launch_count();
         bk_multiaxpy<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, kmax, -1, B->d_h, 128);
+        if (B->spectral && (st = grouped_spec_back(B, s))) return st;   // back to the grid basis
     }
     return TFDE_OK;
 }
@@ -613,6 +674,7 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
     // grouped descriptors
     const size_t C = count, PS = sizeof(tc::Params);
     std::vector<tc::Params> mv(5 * C), pc(5 * C), pcl((size_t)(restart + 1) * C);
+    std::vector<tc::Params> sfw(3 * C), sop(2 * C), sopz((size_t)(restart + 1) * C), sbw(3 * C);
     std::vector<long long> gstart(3 * (C + 1), 0);
     for (size_t i = 0; i < C; ++i) {
         tfde_problem* P = B->P[i];
@@ -640,6 +702,28 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
                 }
             pcl[(size_t)j * C + i] = tmp[5];
         }
+        spec_pass_descriptors(P, 2, M->V32, tmp, axes, by, fl);
+        for (int a = 0; a < 3; ++a) {
+            sfw[a * C + i] = tmp[a];
+            B->sfw_bytes[a] += by[a];
+            B->sfw_flops[a] += fl[a];
+        }
+        for (int j = 0; j <= restart; ++j) {
+            spec_pass_descriptors(P, 3, M->V32 + (size_t)j * P->N, tmp, axes, by, fl);
+            if (j == 0)
+                for (int a = 0; a < 3; ++a) {
+                    if (a < 2) sop[a * C + i] = tmp[a];
+                    B->sop_bytes[a] += by[a];
+                    B->sop_flops[a] += fl[a];
+                }
+            sopz[(size_t)j * C + i] = tmp[2];
+        }
+        spec_pass_descriptors(P, 4, M->f[F_X], tmp, axes, by, fl);
+        for (int a = 0; a < 3; ++a) {
+            sbw[a * C + i] = tmp[a];
+            B->sbw_bytes[a] += by[a];
+            B->sbw_flops[a] += fl[a];
+        }
         for (int a = 0; a < 3; ++a) {
             tc::Params g;
             tc::set_geometry(g, P->n, a);
@@ -650,7 +734,11 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
     if (cudaMalloc((void**)&B->d_mv, mv.size() * PS) != cudaSuccess ||
         cudaMalloc((void**)&B->d_pc, pc.size() * PS) != cudaSuccess ||
         cudaMalloc((void**)&B->d_pcl, pcl.size() * PS) != cudaSuccess ||
-        cudaMalloc((void**)&B->d_gstart, gstart.size() * sizeof(long long)) != cudaSuccess)
+        cudaMalloc((void**)&B->d_gstart, gstart.size() * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_sfw, sfw.size() * PS) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_sop, sop.size() * PS) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_sopz, sopz.size() * PS) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_sbw, sbw.size() * PS) != cudaSuccess)
         return fail(TFDE_ENOMEM, "cudaMalloc of the grouped descriptors failed");
     // block table
     std::vector<int> bstart(C + 1, 0), bi;
@@ -704,6 +792,8 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
         v.pl = M->lo[PL_P];
         v.rh = M->hi[PL_R];
         v.rl = M->lo[PL_R];
+        v.th = M->hi[PL_T1];
+        v.tl = M->lo[PL_T1];
         v.r64 = P->w[tfde_problem::W_R];
         v.x64 = nullptr;
     }
@@ -713,6 +803,10 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
     if (cudaMemcpyAsync(B->d_mv, mv.data(), mv.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(B->d_pc, pc.data(), pc.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(B->d_pcl, pcl.data(), pcl.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(B->d_sfw, sfw.data(), sfw.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(B->d_sop, sop.data(), sop.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(B->d_sopz, sopz.data(), sopz.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(B->d_sbw, sbw.data(), sbw.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(B->d_gstart, gstart.data(), gstart.size() * sizeof(long long), cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
         cudaMemcpyAsync(B->d_bi, bi.data(), bi.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -744,6 +838,8 @@ int batch_tune(tfde_batch* B, int reps, cudaStream_t s) {
     tc::tune_record(true);
     int st = grouped_matvec(B, s);
     if (!st) st = grouped_precond(B, 0, s);
+    if (!st) st = grouped_spec_start(B, s);
+    if (!st) st = grouped_spec_step(B, 1, s);
     tc::tune_record(false);
     if (!st) st = tc::tune_recorded(reps, s);
     if (!st) st = read_back(B, s);
@@ -753,6 +849,12 @@ int batch_tune(tfde_batch* B, int reps, cudaStream_t s) {
 }  // namespace tfde
 
 extern "C" int tfde_batch_count(const tfde_batch* B) { return B ? B->count : 0; }
+
+extern "C" int tfde_batch_set_spectral_inner(tfde_batch* B, int enable) {
+    if (!B) return tfde::set_error(TFDE_EINVAL, "NULL batch");
+    B->spectral = enable != 0;
+    return TFDE_OK;
+}
 
 extern "C" int tfde_batch_set_guess_order(tfde_batch* B, int order) {
     if (!B) return tfde::set_error(TFDE_EINVAL, "NULL batch");

@@ -221,6 +221,15 @@ inline MixedState* mixed(const tfde_problem* P) { return static_cast<MixedState*
 // Returns the pass count; axes[i], bytes[i], flops[i] per pass.
 int fast_pass_descriptors(const tfde_problem* P, int kind, float* out_f32, tc::Params* prm, int* axes, double* bytes,
                           double* flops);
+// Descriptors of the eigenbasis passes of one problem (left-preconditioned
+// GMRES, Sec. 3.2): kind 2 = forward sine transform of the residual planes
+// PL_R with Lambda^{-1} fused, out_f32 = Lambda^{-1} S_N r; kind 3 = the
+// preconditioned operator on the basis planes PL_P, out_f32 = Lambda^{-1}
+// S_N A S_N v (x and y passes chained through F_Z, F_P); kind 4 = backward
+// sine transform of the planes PL_T1, out_f32 = S_N t (through PL_T2, PL_R).
+// Returns 3 (passes); axes[i], bytes[i], flops[i] per pass.
+int spec_pass_descriptors(const tfde_problem* P, int kind, float* out_f32, tc::Params* prm, int* axes, double* bytes,
+                          double* flops);
 // Allocate the FP32 GMRES basis (restart + 1 vectors) and Hessenberg scratch.
 int mixed_prepare_gmres(const tfde_problem* P, int restart);
 

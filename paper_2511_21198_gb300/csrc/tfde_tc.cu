@@ -236,7 +236,8 @@ int set_attrs() {
                         set_attr_one<true, 1, OUT_F32>() && set_attr_one<true, 1, OUT_HILO>() &&
                         set_attr_one<false, 0, OUT_XPAY>() && set_attr_one<false, 1, OUT_XPAY>() &&
                         set_attr_one<false, 0, OUT_HI>() && set_attr_one<false, 1, OUT_HI>() &&
-                        set_attr_one<false, 0, OUT_SUM>() && set_attr_one<false, 1, OUT_SUM>();
+                        set_attr_one<false, 0, OUT_SUM>() && set_attr_one<false, 1, OUT_SUM>() &&
+                        set_attr_one<true, 0, OUT_SUM>() && set_attr_one<true, 1, OUT_SUM>();
         if (!ok) return set_error(TFDE_ECUDA, "cudaFuncSetAttribute(smem) failed");
         attr_done = true;
     }
@@ -267,6 +268,11 @@ void launch_one(unsigned grid, cudaStream_t s, const Params& p0, const Params* g
 template <bool G>
 void launch_instance(int kmajor, int out_mode, unsigned grid, cudaStream_t s, const Params& p0, const Params* groups,
                      const long long* gstart, int ngroups, const int* gactive) {
+    if (out_mode == OUT_SUM) {   // the eigenbasis passes: single and grouped (the batched solver)
+        if (kmajor) launch_one<G, 1, OUT_SUM>(grid, s, p0, groups, gstart, ngroups, gactive);
+        else launch_one<G, 0, OUT_SUM>(grid, s, p0, groups, gstart, ngroups, gactive);
+        return;
+    }
     if constexpr (!G) {   // the fused direction update exists for single launches only
         if (out_mode == OUT_XPAY) {
             if (kmajor) launch_one<G, 1, OUT_XPAY>(grid, s, p0, groups, gstart, ngroups, gactive);
@@ -276,11 +282,6 @@ void launch_instance(int kmajor, int out_mode, unsigned grid, cudaStream_t s, co
         if (out_mode == OUT_HI) {
             if (kmajor) launch_one<G, 1, OUT_HI>(grid, s, p0, groups, gstart, ngroups, gactive);
             else launch_one<G, 0, OUT_HI>(grid, s, p0, groups, gstart, ngroups, gactive);
-            return;
-        }
-        if (out_mode == OUT_SUM) {
-            if (kmajor) launch_one<G, 1, OUT_SUM>(grid, s, p0, groups, gstart, ngroups, gactive);
-            else launch_one<G, 0, OUT_SUM>(grid, s, p0, groups, gstart, ngroups, gactive);
             return;
         }
     }
@@ -431,8 +432,8 @@ int launch_grouped(const Params* groups, const long long* gstart, int ngroups, l
                    int out_mode, const int* gactive, int* err, cudaStream_t s, double bytes, double flops,
                    const int* skip) {
     if (int st = set_attrs()) return st;
-    if (out_mode == OUT_HI || out_mode == OUT_XPAY || out_mode == OUT_SUM)
-        return set_error(TFDE_EUNSUPPORTED, "grouped axis_gemm_kernel: split or FP32 output only");   // no such instances
+    if (out_mode == OUT_HI || out_mode == OUT_XPAY)
+        return set_error(TFDE_EUNSUPPORTED, "grouped axis_gemm_kernel: split, FP32 or eigenbasis output only");   // no such instances
     if (total <= 0 || ngroups <= 0) return TFDE_OK;
     Params p0;
     std::memset(&p0, 0, sizeof(p0));

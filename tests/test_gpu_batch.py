@@ -165,3 +165,30 @@ def test_batch_argument_errors(T):
         assert float(np.abs(to_host(u)).max()) == 0.0
     finally:
         T.tfde_batch_destroy(B)
+
+
+@pytest.mark.parametrize("spectral", [True, False], ids=["eigenbasis", "grid"])
+def test_batch_both_bases_match_oracle(T, spectral):
+    """The batched GMRES cycles in the sine-transform eigenbasis (grouped
+    Lambda^{-1} S_N A S_N passes, one forward and one backward transform per
+    cycle; the default) and in the grid basis: one step of five uneven
+    problems (ragged tiles, a short restart) against the oracle's solutions."""
+    probs = small_batch(5, 13, sizes=(8, 16, 24, 40, 136))
+    dt = 0.05
+    params = [T.make_params(p["n"], p["delta"], p["kp"], p["km"], dt) for p in probs]
+    B = T.tfde_batch_create(params, 6)
+    try:
+        T.tfde_batch_set_spectral_inner(B, spectral)
+        u0 = [inp.smoothed_uniform(tuple(reversed(p["n"])), 40 + i) for i, p in enumerate(probs)]
+        us = [to_dev(u) for u in u0]
+        infos = T.tfde_batch_cn_advance(B, us, None, True, 1e-12)
+        for i, p in enumerate(probs):
+            op = o.Problem(n=p["n"], delta=p["delta"], kp=p["kp"], km=p["km"], dt=dt)
+            b = o.rhs(op, u0[i], None)
+            tau = o.build_tau(op)
+            xo, _ = o.gmres_left(lambda v: o.apply_A(op, v), lambda r: o.apply_Pinv(tau, r), b, u0[i], 1e-14, 4000,
+                                 restart=20, criterion="true")
+            assert infos[i].relres <= 1e-12 and infos[i].fallback == 0, (i, infos[i].relres)
+            assert relerr(to_host(us[i]), xo) < 1e-10, i
+    finally:
+        T.tfde_batch_destroy(B)
