@@ -62,6 +62,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-parity", action="store_true",
                     help="skip the full-size tight-residual comparison of the mixed and FP64 GPU paths")
     ap.add_argument("--no-spectra", action="store_true", help="skip the Lanczos spectra of the preconditioned systems")
+    ap.add_argument("--no-comparisons", action="store_true",
+                    help="skip the host-loop and grid-basis comparison problems (one problem on the device)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -390,49 +392,50 @@ def run_ours(args):
     ms_t = e0.elapsed_time(e1)
     st = T.tfde_stats_get()
     T.tfde_stats_reset(time_tc=False)
-    # ---- host gap: a second problem marches the same trajectory (warm-up and
-    # timed steps) with the inner loop driven from the host; the iterates are
-    # the same, so the time difference is the host round trips
-    hb = T.tfde_assemble(params, T.TFDE_MIXED, stream)
-    T.tfde_set_guess_order(hb, args.guess_order)
-    T.tfde_set_device_loop(hb, False)
-    ub = u0.clone()
-    chained_steps(T, hb, ub, F, dt, 0, args.warmup, tol, stream)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    it_h, _, _ = chained_steps(T, hb, ub, F, dt, args.warmup, args.steps, tol, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_h = e0.elapsed_time(e1)
-    T.tfde_destroy(hb)
-    del ub
-    # ---- the same steps with the inner PCG in the grid basis (tfde_set_spectral_inner(h, 0))
-    hg = T.tfde_assemble(params, T.TFDE_MIXED, stream)
-    T.tfde_set_guess_order(hg, args.guess_order)
-    T.tfde_set_spectral_inner(hg, False)
-    ug = u0.clone()
-    chained_steps(T, hg, ug, F, dt, 0, args.warmup, tol, stream)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    it_g, _, rr_g = chained_steps(T, hg, ug, F, dt, args.warmup, args.steps, tol, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_g = e0.elapsed_time(e1)
-    T.tfde_destroy(hg)
-    del ug
-    inner_basis = {"ms_per_step_eigenbasis": ms / args.steps, "ms_per_step_grid_basis": ms_g / args.steps,
-                   "iters_per_step_eigenbasis": iters / args.steps, "iters_per_step_grid_basis": it_g / args.steps,
-                   "max_relres_grid_basis": rr_g,
-                   "note": "the timed steps again on a problem whose inner PCG iterates in the grid basis "
-                           "(operator 3 and preconditioner 6 split launches per iteration) instead of the "
-                           "sine-transform eigenbasis (3 split launches per iteration)"}
-    host_gap = {"ms_per_step_device_loop": ms / args.steps, "ms_per_step_host_loop": ms_h / args.steps,
-                "iters_per_step_host_loop": it_h / args.steps, "iters_per_step_device_loop": iters / args.steps,
-                "host_gap_share_removed": (ms_h - ms) / ms_h,
-                "note": "the timed steps again on a second problem with the inner PCG driven from the host "
-                        "(one blocking read of <r, r> per inner iteration) instead of one graph launch per "
-                        "refinement sweep"}
-
+    host_gap = inner_basis = None
+    if not args.no_comparisons:
+        # ---- host gap: a second problem marches the same trajectory (warm-up and
+        # timed steps) with the inner loop driven from the host; the iterates are
+        # the same, so the time difference is the host round trips
+        hb = T.tfde_assemble(params, T.TFDE_MIXED, stream)
+        T.tfde_set_guess_order(hb, args.guess_order)
+        T.tfde_set_device_loop(hb, False)
+        ub = u0.clone()
+        chained_steps(T, hb, ub, F, dt, 0, args.warmup, tol, stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        it_h, _, _ = chained_steps(T, hb, ub, F, dt, args.warmup, args.steps, tol, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_h = e0.elapsed_time(e1)
+        T.tfde_destroy(hb)
+        del ub
+        # ---- the same steps with the inner PCG in the grid basis (tfde_set_spectral_inner(h, 0))
+        hg = T.tfde_assemble(params, T.TFDE_MIXED, stream)
+        T.tfde_set_guess_order(hg, args.guess_order)
+        T.tfde_set_spectral_inner(hg, False)
+        ug = u0.clone()
+        chained_steps(T, hg, ug, F, dt, 0, args.warmup, tol, stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        it_g, _, rr_g = chained_steps(T, hg, ug, F, dt, args.warmup, args.steps, tol, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_g = e0.elapsed_time(e1)
+        T.tfde_destroy(hg)
+        del ug
+        inner_basis = {"ms_per_step_eigenbasis": ms / args.steps, "ms_per_step_grid_basis": ms_g / args.steps,
+                       "iters_per_step_eigenbasis": iters / args.steps, "iters_per_step_grid_basis": it_g / args.steps,
+                       "max_relres_grid_basis": rr_g,
+                       "note": "the timed steps again on a problem whose inner PCG iterates in the grid basis "
+                               "(operator 3 and preconditioner 6 split launches per iteration) instead of the "
+                               "sine-transform eigenbasis (3 split launches per iteration)"}
+        host_gap = {"ms_per_step_device_loop": ms / args.steps, "ms_per_step_host_loop": ms_h / args.steps,
+                    "iters_per_step_host_loop": it_h / args.steps, "iters_per_step_device_loop": iters / args.steps,
+                    "host_gap_share_removed": (ms_h - ms) / ms_h,
+                    "note": "the timed steps again on a second problem with the inner PCG driven from the host "
+                            "(one blocking read of <r, r> per inner iteration) instead of one graph launch per "
+                            "refinement sweep"}
     # ---- the survey's C-3 protocol: one warm-up step, then steps m = 2 .. 20 (T = 1)
     c3 = None
     if not args.no_c3_protocol and args.n is None:
