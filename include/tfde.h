@@ -241,6 +241,16 @@ int tfde_set_guess_order(tfde_problem* prob, int order);
 int tfde_set_device_loop(tfde_problem* prob, int enable);
 
 /*
+ * tfde_device_loop_launches -- how many inner solves of a TFDE_MIXED problem
+ * on the tensor-core path (PCG sweeps and GMRES cycles, Sec. 3.1-3.2) so far
+ * ran as one CUDA-graph launch with the stop test on the device (see
+ * tfde_set_device_loop); 0 for other problems and a NULL problem.  The
+ * graphs are captured on a stream of the library's own, so they serve
+ * callers on any stream, the legacy default stream included.
+ */
+long long tfde_device_loop_launches(const tfde_problem* prob);
+
+/*
  * tfde_set_spectral_inner -- the basis in which the inner Krylov solves of a
  * TFDE_MIXED problem on the tensor-core path iterate: PCG (Sec. 3.1) and
  * left-preconditioned GMRES (Sec. 3.2, Eq. (one_side_system)) with the tau
@@ -345,6 +355,17 @@ int tfde_batch_set_guess_order(tfde_batch* batch, int order);
  * TFDE_EINVAL for a NULL batch.
  */
 int tfde_batch_set_spectral_inner(tfde_batch* batch, int enable);
+
+/*
+ * tfde_batch_graph_cycles -- how many batched GMRES cycles (Sec. 3.2) so far
+ * ran their Arnoldi steps as one CUDA-graph launch (a while node: the step
+ * index, each problem's Hessenberg column, Givens rotation and stop test,
+ * and the loop condition on the device; no host read inside a cycle).  The
+ * eigenbasis cycles take that path unless tfde_stats_reset(1) times every
+ * tensor-core launch (the host then drives the steps) or the graph could not
+ * be built.  Returns 0 for a NULL batch.
+ */
+long long tfde_batch_graph_cycles(const tfde_batch* batch);
 
 /*
  * tfde_batch_cn_advance -- one CN step u_i^{m-1} -> u_i^m IN PLACE for every

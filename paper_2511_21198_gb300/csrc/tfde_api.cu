@@ -6,6 +6,18 @@
 #include "tfde_stats.h"
 
 namespace tfde {
+
+cudaStream_t capture_stream() {
+    constexpr int kMaxDev = 64;
+    thread_local cudaStream_t cs[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return nullptr;
+    if (!cs[dev] && cudaStreamCreateWithFlags(&cs[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        cs[dev] = nullptr;
+    }
+    return cs[dev];
+}
 const char* last_error_text();
 int assemble_problem(const tfde_params*, int, cudaStream_t, tfde_problem**);
 int batch_create(const tfde_params*, int, int, cudaStream_t, tfde_batch**);
@@ -35,6 +47,7 @@ int mixed_pcg(tfde_problem*, const double*, double*, double, int, tfde_info*, cu
 int mixed_pgmres(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t, bool);
 int mixed_set_device_loop(tfde_problem*, int);
 int mixed_set_spectral(tfde_problem*, int);
+long long mixed_graph_launches(const tfde_problem*);
 int spectrum(const tfde_params*, int, const double*, tfde_spectrum_info*, cudaStream_t);
 int mixed_tune(tfde_problem*, int, cudaStream_t);
 int batch_tune(tfde_batch*, int, cudaStream_t);
@@ -347,6 +360,8 @@ int tfde_set_device_loop(tfde_problem* prob, int enable) {
     if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
     return mixed_set_device_loop(prob, enable);
 }
+
+long long tfde_device_loop_launches(const tfde_problem* prob) { return prob ? mixed_graph_launches(prob) : 0; }
 
 int tfde_set_spectral_inner(tfde_problem* prob, int enable) {
     if (!prob) return set_error(TFDE_EINVAL, "NULL problem");

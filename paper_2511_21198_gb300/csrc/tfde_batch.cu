@@ -51,6 +51,7 @@ struct BVec {
     __nv_bfloat16* rl;
     __nv_bfloat16* th;   // split planes of the eigenbasis correction (PL_T1)
     __nv_bfloat16* tl;
+    float* W;            // the graph-captured cycle's new Arnoldi vector before it joins the basis
     const double* r64;
     double* x64;
 };
@@ -192,6 +193,91 @@ __global__ __launch_bounds__(kBT) void bk_add32to64(const BVec* __restrict__ vt,
     for (long long e = e0 + threadIdx.x; e < e1; e += kBT) v.x64[e] += f * (double)v.x32[e];
 }
 
+// ---- the same steps for the graph-captured cycle: the step index j comes
+// from *jd (device), the new vector is the fixed per-problem W.
+// Block partial sums of <V_{m0+t}, W> for t < min(8, j + 1 - m0), or (ww) of
+// <W, W> into row R + 1.
+__global__ __launch_bounds__(kBT) void bkg_dots(const BVec* __restrict__ vt, const int* __restrict__ bi,
+                                               const long long* __restrict__ bo, const int* __restrict__ act,
+                                               int m0, const int* __restrict__ jd, int R, int ww,
+                                               double* __restrict__ part) {
+    const int inst = bi[blockIdx.x];
+    const int j = *jd;
+    const int mc = ww ? 1 : min(8, j + 1 - m0);
+    if (mc <= 0) return;
+    const bool on = act[inst] != 0;
+    KSum k[8];
+    if (on) {
+        const BVec& v = vt[inst];
+        const long long e0 = bo[blockIdx.x];
+        const long long e1 = e0 + kCH < v.N ? e0 + kCH : v.N;
+        for (long long e = e0 + threadIdx.x; e < e1; e += kBT) {
+            const float we = v.W[e];
+            if (ww) {
+                k[0].add(we * we);
+                continue;
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                if (t < mc) k[t].add(v.V[(long long)(m0 + t) * v.N + e] * we);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        if (t < mc) {
+            const double sum = block_sum((double)k[t].s - (double)k[t].c);
+            const int row = ww ? R + 1 : m0 + t;
+            if (threadIdx.x == 0) part[(long long)row * gridDim.x + blockIdx.x] = sum;
+        }
+    }
+}
+
+// out[i * ostride + ooff + t] = sum over problem i's blocks, t <= j (rows
+// 0 .. j), or (ww) row R + 1 into out[i * ostride + ooff]
+__global__ void bkg_reduce(const double* __restrict__ part, int NB, const int* __restrict__ bstart,
+                           const int* __restrict__ act, const int* __restrict__ jd, int R, int ww,
+                           double* __restrict__ out, int ostride, int ooff) {
+    const int inst = blockIdx.x, t = blockIdx.y;
+    if (!act[inst] || t > (ww ? 0 : *jd)) return;
+    const int row = ww ? R + 1 : t;
+    double acc = 0.0;
+    for (int b = bstart[inst] + threadIdx.x; b < bstart[inst + 1]; b += 32) acc += part[(long long)row * NB + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) out[inst * ostride + ooff + t] = acc;
+}
+
+// W -= sum_{t <= j} coef[i * kHS + coff + t] V_t
+__global__ __launch_bounds__(kBT) void bkg_axpy_w(const BVec* __restrict__ vt, const int* __restrict__ bi,
+                                                 const long long* __restrict__ bo, const int* __restrict__ act,
+                                                 const int* __restrict__ jd, const double* __restrict__ coef,
+                                                 int coff) {
+    BK_PROLOGUE
+    const int m = *jd + 1;
+    __shared__ float hs[64];
+    for (int t = threadIdx.x; t < m; t += blockDim.x) hs[t] = (float)coef[inst * kHS + coff + t];
+    __syncthreads();
+    for (long long e = e0 + threadIdx.x; e < e1; e += kBT) {
+        float acc = v.W[e];
+        for (int t = 0; t < m; ++t) acc = fmaf(-hs[t], v.V[(long long)t * v.N + e], acc);
+        v.W[e] = acc;
+    }
+}
+
+// V_{j+1} = W sc and its split planes (ph, pl)
+__global__ __launch_bounds__(kBT) void bkg_scale_split(const BVec* __restrict__ vt, const int* __restrict__ bi,
+                                                      const long long* __restrict__ bo, const int* __restrict__ act,
+                                                      const int* __restrict__ jd, const double* __restrict__ sc) {
+    BK_PROLOGUE
+    const float f = (float)sc[inst * kSS + S_SPLIT];
+    float* w = v.V + (long long)(*jd + 1) * v.N;
+    for (long long e = e0 + threadIdx.x; e < e1; e += kBT) {
+        const float x = v.W[e] * f;
+        w[e] = x;
+        split_bf16(x, v.ph[e], v.pl[e]);
+    }
+}
+
 #undef BK_PROLOGUE
 
 // ---- the cycle's least-squares problem on the device, one thread per problem.
@@ -233,12 +319,45 @@ __global__ void bk_cycle_start(int C, int R, double* __restrict__ gs, double* __
 // rotation, the residual estimate |g_{j+1}|; the problem leaves the cycle
 // when that estimate reaches theta beta, else V_{j+1} gets the scale 1/||w||.
 // *cnt counts the problems still in the cycle.
+__device__ __forceinline__ void givens_step(int i, int R, int j, double* __restrict__ gs,
+                                            const double* __restrict__ h, double* __restrict__ s,
+                                            const double* __restrict__ theta, int* __restrict__ act,
+                                            int* __restrict__ its, double* __restrict__ est, int* __restrict__ cnt,
+                                            int* __restrict__ bad);
+
 __global__ void bk_givens(int C, int R, int j, double* __restrict__ gs, const double* __restrict__ h,
                           double* __restrict__ s, const double* __restrict__ theta, int* __restrict__ act,
                           int* __restrict__ its, double* __restrict__ est, int* __restrict__ cnt,
                           int* __restrict__ bad) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= C || !act[i]) return;
+    givens_step(i, R, j, gs, h, s, theta, act, its, est, cnt, bad);
+}
+
+// the same with j = *jd, the count into cnt[j + 1]
+__global__ void bkg_givens(int C, int R, const int* __restrict__ jd, double* __restrict__ gs,
+                           const double* __restrict__ h, double* __restrict__ s, const double* __restrict__ theta,
+                           int* __restrict__ act, int* __restrict__ its, double* __restrict__ est,
+                           int* __restrict__ cnt, int* __restrict__ bad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C || !act[i]) return;
+    const int j = *jd;
+    givens_step(i, R, j, gs, h, s, theta, act, its, est, cnt + j + 1, bad);
+}
+
+// the loop condition of the graph-captured cycle: another step while a
+// problem is still in the cycle and the restart length is not reached
+__global__ void bkg_next(int* __restrict__ jd, const int* __restrict__ cnt, int R, cudaGraphConditionalHandle hc) {
+    const int j = *jd + 1;
+    *jd = j;
+    cudaGraphSetConditional(hc, (cnt[j] > 0 && j < R) ? 1u : 0u);
+}
+
+__device__ __forceinline__ void givens_step(int i, int R, int j, double* __restrict__ gs,
+                                            const double* __restrict__ h, double* __restrict__ s,
+                                            const double* __restrict__ theta, int* __restrict__ act,
+                                            int* __restrict__ its, double* __restrict__ est, int* __restrict__ cnt,
+                                            int* __restrict__ bad) {
     double* Rm = gs + (size_t)i * gs_stride(R);
     double* cs = Rm + (R + 1) * R;
     double* sn = cs + R;
@@ -318,6 +437,16 @@ struct tfde_batch {
     // and y passes [2][count], its z pass writing V_j [restart+1][count], the
     // backward transform [3][count]
     bool spectral = true;
+    // the eigenbasis Arnoldi steps as one graph launch per cycle (a while
+    // node; the step index on the device, the z pass writing each problem's W)
+    bool device_loop = true;
+    tfde::tc::Params* d_sopzw = nullptr;   // [count]
+    int* d_j = nullptr;
+    cudaGraph_t cyc_graph = nullptr;
+    cudaGraphExec_t cyc_exec = nullptr;
+    bool cyc_failed = false;
+    unsigned cyc_tune_gen = 0;
+    long long graph_cycles = 0;   // cycles run through the graph (tfde_batch_graph_cycles)
     tfde::tc::Params* d_sfw = nullptr;
     tfde::tc::Params* d_sop = nullptr;
     tfde::tc::Params* d_sopz = nullptr;
@@ -392,6 +521,10 @@ int free_batch(tfde_batch* B) {
         if (i < B->own_err.size()) tfde::mixed(B->P[i])->err = B->own_err[i];
         destroy_problem(B->P[i]);
     }
+    cudaFree(B->d_sopzw);
+    cudaFree(B->d_j);
+    if (B->cyc_exec) cudaGraphExecDestroy(B->cyc_exec);
+    if (B->cyc_graph) cudaGraphDestroy(B->cyc_graph);
     cudaFree(B->d_sfw);
     cudaFree(B->d_sop);
     cudaFree(B->d_sopz);
@@ -494,6 +627,89 @@ int grouped_spec_back(tfde_batch* B, cudaStream_t s) {
 
 void vec_launch_count() { stats_count_launch(); }
 
+// The eigenbasis Arnoldi step of every problem as the body of a while node:
+// the three grouped passes (the z pass into W), CGS2 against V_0 .. V_j with
+// the coefficients on the device, ||W||, the Givens update and stop test per
+// problem, V_{j+1} = W / ||W|| with its split planes, and the loop condition
+// (a problem still in the cycle and j + 1 < restart).  Built once per batch
+// (rebuilt when the autotuner's table changes); a failure leaves the host
+// loop in use.
+int build_cycle_graph(tfde_batch* B, cudaStream_t s) {
+    if (B->cyc_exec && B->cyc_tune_gen != tc::tune_generation()) {
+        cudaGraphExecDestroy(B->cyc_exec);
+        cudaGraphDestroy(B->cyc_graph);
+        B->cyc_exec = nullptr;
+        B->cyc_graph = nullptr;
+    }
+    if (B->cyc_exec || B->cyc_failed) return TFDE_OK;
+    if (int st = tc::set_attrs()) return st;
+    const int C = B->count, R = B->restart;
+    const int gb = (C + 63) / 64;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+    cudaGraphConditionalHandle h{};
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    if (ok) ok = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+    }
+    if (ok) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        // captured on a stream of its own (the caller's may be the legacy default stream)
+        const cudaStream_t s = capture_stream();
+        ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+             cudaSuccess;
+        if (ok) {
+            stats_set_capturing(true);
+            int st = TFDE_OK;
+            for (int a = 0; a < 2 && !st; ++a)
+                st = grouped(B, B->d_sop + (size_t)a * C, a, tc::OUT_SUM, B->sop_bytes[a], B->sop_flops[a], s);
+            if (!st) st = grouped(B, B->d_sopzw, 2, tc::OUT_SUM, B->sop_bytes[2], B->sop_flops[2], s);
+            for (int pass = 0; pass < 2 && !st; ++pass) {   // CGS2
+                for (int m0 = 0; m0 < R; m0 += 8)
+                    bkg_dots<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, m0, B->d_j, R, 0, B->d_part);
+                bkg_reduce<<<dim3((unsigned)C, (unsigned)R), 32, 0, s>>>(B->d_part, B->NB, B->d_bstart, B->d_act,
+                                                                         B->d_j, R, 0, B->d_h, kHS, 64 * pass);
+                bkg_axpy_w<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, B->d_j, B->d_h, 64 * pass);
+            }
+            if (!st) {
+                bkg_dots<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, 0, B->d_j, R, 1, B->d_part);
+                bkg_reduce<<<dim3((unsigned)C, 1u), 32, 0, s>>>(B->d_part, B->NB, B->d_bstart, B->d_act, B->d_j, R,
+                                                               1, B->d_s, kSS, S_WW);
+                bkg_givens<<<gb, 64, 0, s>>>(C, R, B->d_j, B->d_gs, B->d_h, B->d_s, B->d_theta, B->d_act, B->d_its,
+                                             B->d_est, B->d_cnt, B->d_bad);
+                bkg_scale_split<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, B->d_j, B->d_s);
+                bkg_next<<<1, 1, 0, s>>>(B->d_j, B->d_cnt, R, h);
+            }
+            stats_set_capturing(false);
+            cudaGraph_t out = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(s, &out);
+            ok = st == TFDE_OK && e == cudaSuccess;
+        }
+    }
+    if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        B->cyc_failed = true;
+        tfde::set_error(TFDE_OK, "");
+        return TFDE_OK;
+    }
+    B->cyc_graph = g;
+    B->cyc_exec = ex;
+    B->cyc_tune_gen = tc::tune_generation();
+    return TFDE_OK;
+}
+
+// launches of one captured step: 3 grouped + 2 x (ceil(R / 8) + 2) + 5
+unsigned cycle_step_launches(int R) { return 3u + 2u * (unsigned)((R + 7) / 8 + 2) + 5u; }
+
 // dots <V_{p0+j}, V_jw>, j < m, of every active problem into out (stride, offset)
 void bdots(tfde_batch* B, int p0, int m, int jw, double* out, int ostride, int ooff, cudaStream_t s) {
     for (int m0 = p0; m0 < p0 + m; m0 += 8) {
@@ -551,7 +767,15 @@ int batch_cycle(tfde_batch* B, const std::vector<int>& outer, const std::vector<
     B_TRY(cudaEventRecord(B->cnt_ev[0], s));
     vec_launch_count();
     bk_scale_split<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, 0, B->d_s);
-    for (int j = 0; j < R; ++j) {
+    const bool graph = B->spectral && B->device_loop && !stats_timing();
+    if (graph && (st = build_cycle_graph(B, s))) return st;
+    if (graph && B->cyc_exec) {
+        // every Arnoldi step on the device: one graph launch for the cycle
+        B_TRY(cudaMemsetAsync(B->d_j, 0, sizeof(int), s));
+        B_TRY(cudaGraphLaunch(B->cyc_exec, s));
+        ++B->graph_cycles;
+    }
+    for (int j = 0; j < R && !(graph && B->cyc_exec); ++j) {
         // stop issuing once no problem is left: the count after step j - 1
         // if it is already in, else the one after step j - 2
         if (cudaEventQuery(B->cnt_ev[j]) == cudaSuccess) {
@@ -593,6 +817,9 @@ int batch_cycle(tfde_batch* B, const std::vector<int>& outer, const std::vector<
     if (*B->h_err) return set_error(TFDE_ETIMEOUT, "tensor-core kernel wait ran out (device error flag set)");
     if (*B->h_bad) return set_error(TFDE_ENAN, "non-finite value in a batched GMRES cycle");
     int kmax = 0;
+    for (int i = 0; i < C; ++i) kmax = std::max(kmax, outer[i] ? B->h_its[i] : 0);
+    if (graph && B->cyc_exec) stats_count_launch((unsigned)(kmax > 0 ? kmax : 1) * cycle_step_launches(R));
+    kmax = 0;
     for (int i = 0; i < C; ++i) {
         its[i] = outer[i] ? B->h_its[i] : 0;
         est[i] = outer[i] ? B->h_est[i] : 1.0;
@@ -674,7 +901,7 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
     // grouped descriptors
     const size_t C = count, PS = sizeof(tc::Params);
     std::vector<tc::Params> mv(5 * C), pc(5 * C), pcl((size_t)(restart + 1) * C);
-    std::vector<tc::Params> sfw(3 * C), sop(2 * C), sopz((size_t)(restart + 1) * C), sbw(3 * C);
+    std::vector<tc::Params> sfw(3 * C), sop(2 * C), sopz((size_t)(restart + 1) * C), sbw(3 * C), sopzw(C);
     std::vector<long long> gstart(3 * (C + 1), 0);
     for (size_t i = 0; i < C; ++i) {
         tfde_problem* P = B->P[i];
@@ -718,6 +945,8 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
                 }
             sopz[(size_t)j * C + i] = tmp[2];
         }
+        spec_pass_descriptors(P, 3, M->f[F_Q], tmp, axes, by, fl);
+        sopzw[i] = tmp[2];
         spec_pass_descriptors(P, 4, M->f[F_X], tmp, axes, by, fl);
         for (int a = 0; a < 3; ++a) {
             sbw[a * C + i] = tmp[a];
@@ -738,7 +967,9 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
         cudaMalloc((void**)&B->d_sfw, sfw.size() * PS) != cudaSuccess ||
         cudaMalloc((void**)&B->d_sop, sop.size() * PS) != cudaSuccess ||
         cudaMalloc((void**)&B->d_sopz, sopz.size() * PS) != cudaSuccess ||
-        cudaMalloc((void**)&B->d_sbw, sbw.size() * PS) != cudaSuccess)
+        cudaMalloc((void**)&B->d_sbw, sbw.size() * PS) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_sopzw, sopzw.size() * PS) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_j, sizeof(int)) != cudaSuccess)
         return fail(TFDE_ENOMEM, "cudaMalloc of the grouped descriptors failed");
     // block table
     std::vector<int> bstart(C + 1, 0), bi;
@@ -794,6 +1025,7 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
         v.rl = M->lo[PL_R];
         v.th = M->hi[PL_T1];
         v.tl = M->lo[PL_T1];
+        v.W = M->f[F_Q];
         v.r64 = P->w[tfde_problem::W_R];
         v.x64 = nullptr;
     }
@@ -807,6 +1039,7 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
         cudaMemcpyAsync(B->d_sop, sop.data(), sop.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(B->d_sopz, sopz.data(), sopz.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(B->d_sbw, sbw.data(), sbw.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(B->d_sopzw, sopzw.data(), sopzw.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(B->d_gstart, gstart.data(), gstart.size() * sizeof(long long), cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
         cudaMemcpyAsync(B->d_bi, bi.data(), bi.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -849,6 +1082,8 @@ int batch_tune(tfde_batch* B, int reps, cudaStream_t s) {
 }  // namespace tfde
 
 extern "C" int tfde_batch_count(const tfde_batch* B) { return B ? B->count : 0; }
+
+extern "C" long long tfde_batch_graph_cycles(const tfde_batch* B) { return B ? B->graph_cycles : 0; }
 
 extern "C" int tfde_batch_set_spectral_inner(tfde_batch* B, int enable) {
     if (!B) return tfde::set_error(TFDE_EINVAL, "NULL batch");

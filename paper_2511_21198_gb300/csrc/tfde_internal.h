@@ -38,6 +38,11 @@ inline AxisView axis_view(const int n[3], int axis) {
 
 // Thread-local error text; set_error returns the status for convenience.
 int set_error(int status, const std::string& msg);
+// A non-blocking stream of the calling thread on the current device, used to
+// capture the device-side loops into CUDA graphs: the caller's stream may be
+// the legacy default stream, on which no capture is possible.  The graphs are
+// launched on the caller's stream.
+cudaStream_t capture_stream();
 
 // ---------------------------------------------------------------- FP64 kernels
 // Y = alpha * (Mat along axis) X + beta * (tridiag(1,6,1)/8 along axis) Z  (Z may be null)

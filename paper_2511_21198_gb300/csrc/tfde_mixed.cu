@@ -492,6 +492,8 @@ int build_pcg_graph(const tfde_problem* P, cudaStream_t s) {
     }
     if (ok) {
         cudaGraph_t body = cp.conditional.phGraph_out[0];
+        // captured on a stream of its own (the caller's may be the legacy default stream)
+        const cudaStream_t s = capture_stream();
         ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
              cudaSuccess;
         if (ok) {
@@ -547,6 +549,7 @@ int inner_pcg_graph(const tfde_problem* P, double theta, int maxit, int* iters, 
     int st = fast_precond_cg(P, pbuf(0), nullptr, d + D_RZN, nullptr, nullptr, s);   // p_0 = z_0
     if (st) return st;
     MX_TRY(cudaGraphLaunch(M->pcg_exec, s));
+    ++M->graph_launches;
     MX_TRY(cudaMemcpyAsync(M->pcg_ctl_host, M->pcg_ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     MX_TRY(cudaMemcpyAsync(P->red_host, d + D_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
     MX_TRY(cudaStreamSynchronize(s));
@@ -747,6 +750,8 @@ int build_pcg_graph_spec(const tfde_problem* P, cudaStream_t s) {
     }
     if (ok) {
         cudaGraph_t body = cp.conditional.phGraph_out[0];
+        // captured on a stream of its own (the caller's may be the legacy default stream)
+        const cudaStream_t s = capture_stream();
         ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
              cudaSuccess;
         if (ok) {
@@ -800,6 +805,7 @@ int inner_pcg_spec_graph(const tfde_problem* P, double theta, int maxit, int* it
                                    M->lo[PL_P], d + D_RZN, s);   // p_0 = Lambda^{-1} r~
     if (st) return st;
     MX_TRY(cudaGraphLaunch(M->spec_exec, s));
+    ++M->graph_launches;
     MX_TRY(cudaMemcpyAsync(M->pcg_ctl_host, M->pcg_ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     MX_TRY(cudaMemcpyAsync(P->red_host, d + D_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
     MX_TRY(cudaStreamSynchronize(s));
@@ -862,6 +868,8 @@ int build_gmres_graph_spec(const tfde_problem* P, int restart, cudaStream_t s) {
     }
     if (ok) {
         cudaGraph_t body = cp.conditional.phGraph_out[0];
+        // captured on a stream of its own (the caller's may be the legacy default stream)
+        const cudaStream_t s = capture_stream();
         ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
              cudaSuccess;
         if (ok) {
@@ -920,6 +928,7 @@ int inner_gmres_spec(const tfde_problem* P, int restart, double ptheta, int maxi
         launch_gm_start(N, M->f[F_Z], P->red, P->nblk, g + GM_WW, M->gm_state, M->gm_ctl, maxsteps, ptheta, V,
                         M->hi[PL_P], M->lo[PL_P], s);
         MX_TRY(cudaGraphLaunch(M->gms_exec, s));
+        ++M->graph_launches;
         launch_gm_solve(M->gm_state, M->gm_ctl, g + GM_Y, restart, s);
         launch_multiaxpy32(N, restart, V, N, g + GM_Y, M->f[F_X], s);   // x32 = sum_i y_i v_i
         MX_TRY(cudaMemcpyAsync(M->gm_ctl_host, M->gm_ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1078,6 +1087,8 @@ int build_gmres_graph(const tfde_problem* P, int restart, cudaStream_t s) {
     }
     if (ok) {
         cudaGraph_t body = cp.conditional.phGraph_out[0];
+        // captured on a stream of its own (the caller's may be the legacy default stream)
+        const cudaStream_t s = capture_stream();
         ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
              cudaSuccess;
         if (ok) {
@@ -1125,6 +1136,7 @@ int inner_gmres_graph(const tfde_problem* P, int restart, double ptheta, int max
     launch_gm_start(N, M->f[F_Z], P->red, P->nblk, M->gm + GM_WW, M->gm_state, M->gm_ctl, maxsteps, ptheta, M->V32,
                     M->hi[PL_P], M->lo[PL_P], s);
     MX_TRY(cudaGraphLaunch(M->gm_exec, s));
+    ++M->graph_launches;
     launch_gm_solve(M->gm_state, M->gm_ctl, M->gm + GM_Y, restart, s);
     launch_multiaxpy32(N, restart, M->V32, N, M->gm + GM_Y, M->f[F_X], s);   // x32 = sum_i y_i v_i
     MX_TRY(cudaMemcpyAsync(M->gm_ctl_host, M->gm_ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1761,6 +1773,11 @@ int mixed_set_spectral(tfde_problem* P, int enable) {
     }
     M->spectral = enable != 0;
     return TFDE_OK;
+}
+
+long long mixed_graph_launches(const tfde_problem* P) {
+    const MixedState* M = mixed(P);
+    return M ? M->graph_launches : 0;
 }
 
 int mixed_set_device_loop(tfde_problem* P, int enable) {

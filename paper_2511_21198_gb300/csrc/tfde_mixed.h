@@ -184,6 +184,7 @@ struct MixedState {
     unsigned pcg_tune_gen = 0;      // autotuner table generation the graphs were captured with
     unsigned gm_tune_gen = 0;
     bool device_loop = true;   // tfde_set_device_loop
+    long long graph_launches = 0;   // inner solves run as one graph launch (tfde_device_loop_launches)
     // the inner GMRES cycle's Arnoldi steps as one graph launch (while node)
     double* gm_state = nullptr;   // GS_WORDS
     int* gm_ctl = nullptr;        // 4 control words

@@ -192,3 +192,35 @@ def test_batch_both_bases_match_oracle(T, spectral):
             assert relerr(to_host(us[i]), xo) < 1e-10, i
     finally:
         T.tfde_batch_destroy(B)
+
+
+def test_batch_graph_cycle_and_host_loop_agree(T):
+    """The batched eigenbasis cycle as one graph launch per cycle (step index,
+    Givens updates and loop condition on the device) and driven step by step
+    from the host (the path taken while every tensor-core launch is timed)
+    give the same iteration counts and solutions, both matching the oracle."""
+    probs = small_batch(4, 17, sizes=(8, 16, 24, 32))
+    dt = 0.1
+    params = [T.make_params(p["n"], p["delta"], p["kp"], p["km"], dt) for p in probs]
+    u0 = [inp.smoothed_uniform(tuple(reversed(p["n"])), 60 + i) for i, p in enumerate(probs)]
+    runs = {}
+    for timed in (False, True):
+        B = T.tfde_batch_create(params, 8)
+        try:
+            T.tfde_stats_reset(time_tc=timed)
+            us = [to_dev(u) for u in u0]
+            infos = T.tfde_batch_cn_advance(B, us, None, True, 1e-12)
+            runs[timed] = ([i.iters for i in infos], [to_host(u) for u in us])
+            graph_cycles = T.tfde_batch_graph_cycles(B)
+            assert (graph_cycles == 0) if timed else (graph_cycles > 0), (timed, graph_cycles)
+        finally:
+            T.tfde_stats_reset(time_tc=False)
+            T.tfde_batch_destroy(B)
+    assert runs[False][0] == runs[True][0]
+    for i, p in enumerate(probs):
+        op = o.Problem(n=p["n"], delta=p["delta"], kp=p["kp"], km=p["km"], dt=dt)
+        b = o.rhs(op, u0[i], None)
+        tau = o.build_tau(op)
+        xo, _ = o.gmres_left(lambda v: o.apply_A(op, v), lambda r: o.apply_Pinv(tau, r), b, u0[i], 1e-14, 4000,
+                             restart=20, criterion="true")
+        assert relerr(runs[False][1][i], xo) < 1e-10 and relerr(runs[True][1][i], xo) < 1e-10, i

@@ -99,6 +99,8 @@ def test_device_loop_and_host_loop_agree(T):
             info = T.tfde_pcg(h, to_dev(b), x, 1e-11, 4000)
             assert info.relres <= 1e-11
             out[dev_loop] = (info.iters, to_host(x))
+            launches = T.tfde_device_loop_launches(h)
+            assert (launches == info.refine_sweeps) if dev_loop else (launches == 0), (dev_loop, launches)
         finally:
             T.tfde_destroy(h)
     assert out[True][0] == out[False][0]
@@ -160,6 +162,8 @@ def test_eigenbasis_and_grid_basis_pgmres_match_oracle(T, case):
                 x = to_dev(np.zeros_like(b))
                 info = T.tfde_pgmres(h, to_dev(b), x, restart, 1e-12, 4000)
                 assert info.relres <= 1e-12 and info.fallback == 0, (spectral, dev_loop, info.relres)
+                launches = T.tfde_device_loop_launches(h)
+                assert (launches == info.restarts) if dev_loop else (launches == 0), (spectral, dev_loop, launches)
                 assert relerr(to_host(x), xref) < 1e-10
                 iters[(spectral, dev_loop)] = info.iters
             finally:
