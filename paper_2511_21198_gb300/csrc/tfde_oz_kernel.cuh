@@ -19,10 +19,11 @@
 // One CTA per SM, persistent over tiles of 128 rows x 64 lines; warps 0..3
 // TMA (the boxes of a stage dealt round-robin to four issuing threads), warp 4
 // TMEM allocation + MMA issue (M=128, N = 64 per input slice, K=16), warps
-// 5..20 epilogue (four per TMEM lane quadrant, 16 columns each, read four at
-// a time: the epilogue is integer-ALU work that cannot overlap the next
-// tile's MMAs, so it gets every warp the register file allows).  Bounded
-// waits as in the split-BF16 kernel.
+// 5..20 epilogue (four per TMEM lane quadrant, 16 columns each).  Above four
+// slices the diagonals of one tile fill TMEM, so the epilogue first reads
+// them all into integer registers and hands TMEM back; its integer-ALU work
+// (FP64 assembly, addend, stores) then overlaps the next tile's MMAs.
+// Bounded waits as in the split-BF16 kernel.
 #pragma once
 
 #include <cuda.h>
@@ -111,38 +112,13 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                  : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// The double nearest to I * 2^s (I a signed 128-bit integer), built from the
-// integer bits with round-to-nearest-even; results below the normal range are
-// flushed to zero.
-__device__ __forceinline__ double i128_ldexp(__int128 I, int s) {
-    if (I == 0) return 0.0;
-    const bool neg = I < 0;
-    const unsigned __int128 mag = neg ? (unsigned __int128)(-I) : (unsigned __int128)I;
-    const unsigned long long hi = (unsigned long long)(mag >> 64), lo = (unsigned long long)mag;
-    const int nbits = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
-    unsigned long long m;
-    int e2 = nbits - 1 + s;  // exponent of the leading bit
-    if (nbits > 53) {
-        const int sh = nbits - 53;
-        m = (unsigned long long)(mag >> sh);
-        const unsigned __int128 rem = mag & ((((unsigned __int128)1) << sh) - 1);
-        const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
-        if (rem > half || (rem == half && (m & 1ull))) ++m;
-        if (m == (1ull << 53)) {
-            m >>= 1;
-            ++e2;
-        }
-    } else {
-        m = (unsigned long long)mag << (53 - nbits);
-    }
-    const int be = e2 + 1023;
-    if (be <= 0) return 0.0;
-    const unsigned long long bits =
-        ((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1));
-    return __longlong_as_double((long long)bits);
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // The double nearest to I * 2^s for a signed 64-bit I (|I| < 2^62), rounded
 // to nearest even from the integer bits, without branches: normalise the
@@ -366,20 +342,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
             const int m = mh * BM + 32 * q + lane;
             const bool mvalid = m < p.n;
             const int es = mvalid ? __ldg(p.row_exp + m) : 0;
-            for (int cc = 0; cc < EPI_COLS; cc += CH) {
+            // Up to six slices the accumulators of this thread's row and EPI_COLS
+            // columns are read diagonal by diagonal (8 columns per TMEM load) and
+            // folded into integers at once (I = sum_d a_d 2^{7(D-d)}, |a_d| < 2^24
+            // exact in FP32), and TMEM goes back to the MMA warp before any output
+            // work: the next tile's products overlap this tile's FP64 assembly,
+            // addend reads and stores.  Seven slices need two integers per column
+            // (the register file of 21 warps allows 80 per thread), so they are
+            // read chunk by chunk and TMEM is handed back at the last chunk.
+            static_assert(EPI_COLS % 8 == 0, "8-column TMEM loads");
+            const uint32_t trow = dbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(part * EPI_COLS);
+            // Output of the CH columns c0.. of row m: value(j, el) is the FP64 value of
+            // column j (el its line exponent); plus the addend, the store and the norm.
+            auto emit = [&](int cc, auto value) {
                 const int c0 = part * EPI_COLS + cc;
-                uint32_t r[MAXS][CH];
-#pragma unroll
-                for (int d = 0; d < MAXS; ++d)
-                    if (d < S) tmem_ld4(dbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(d * BN + c0), r[d]);
-                tmem_wait_ld();
-                if (cc == EPI_COLS - CH) {
-                    // last TMEM read of this tile: the accumulators go back to the MMA
-                    // warp now, so the next tile's products overlap this chunk's epilogue
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&tempty[buf]);
-                }
                 long long lbase, base;
                 int cbase = 0;
                 if (p.b_kmajor) {
@@ -394,79 +370,102 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                 // every CH-column chunk is either wholly valid or wholly outside: the
                 // line count (x axis) and the plane width C (y, z axes) are multiples of 8
                 const bool cvalid = p.b_kmajor ? (lbase < p.lines) : (tile < p.nblocks && cbase < p.C);
-                if (mvalid && cvalid) {
-                    // line exponents of the CH columns: consecutive lines, 16-byte aligned
-                    const int4 e0 = __ldg(reinterpret_cast<const int4*>(p.line_exp + lbase));
-                    const int el[CH] = {e0.x, e0.y, e0.z, e0.w};
-                    double o[CH];
+                if (!(mvalid && cvalid)) return;
+                // line exponents of the CH columns: consecutive lines, 16-byte aligned
+                const int4 e0 = __ldg(reinterpret_cast<const int4*>(p.line_exp + lbase));
+                const int el[CH] = {e0.x, e0.y, e0.z, e0.w};
+                double o[CH];
+#pragma unroll
+                for (int j = 0; j < CH; ++j) o[j] = value(j, el[j]);
+                if (p.b_kmajor) {
+                    // lanes are consecutive rows m: each store is one coalesced 256-byte row
 #pragma unroll
                     for (int j = 0; j < CH; ++j) {
-                        // I = sum_d a_d 2^{7(D-d)} exactly; |a_d| < 2^24
-                        if (S <= 6) {   // |I| < 2^{24 + 35}: int64
-                            long long I6 = 0;
-#pragma unroll
-                            for (int dd = 0; dd < 6; ++dd)
-                                if (dd < S) I6 = I6 * 128 + (long long)__float2int_rn(__uint_as_float(r[dd][j]));
-                            o[j] = i64_ldexp(p.value_sign < 0 ? -I6 : I6, es + el[j] - 7 * (D + 2));
-                            continue;
+                        const long long idx = base + (long long)j * p.n1;
+                        double v = o[j];
+                        if (p.addend) v = fma(p.addend_sign, p.addend[idx], v);
+                        p.out[idx] = v;
+                        if (p.norm2) {
+                            const float f = scaled_f32(v, p.norm_shift);
+                            nacc = fmaf(f, f, nacc);
                         }
-                        if (S == 7) {
-                            // I = hi 2^21 + lo needs up to 67 bits.  Below 2^62 it is formed exactly in
-                            // int64; above, floor(I / 2^8) keeps at least 54 significant bits, so the
-                            // rounded double moves by at most one ulp
-                            long long av[7];
-#pragma unroll
-                            for (int dd = 0; dd < 7; ++dd) av[dd] = __float2int_rn(__uint_as_float(r[dd][j]));
-                            const long long hi = ((av[0] * 128 + av[1]) * 128 + av[2]) * 128 + av[3];
-                            const long long lo = (av[4] * 128 + av[5]) * 128 + av[6];
-                            const bool big = hi >= (1LL << 40) || hi <= -(1LL << 40);
-                            const long long Iv = big ? hi * (1LL << 13) + (lo >> 8) : hi * (1LL << 21) + lo;
-                            o[j] = i64_ldexp(p.value_sign < 0 ? -Iv : Iv, es + el[j] - 7 * (D + 2) + (big ? 8 : 0));
-                            continue;
-                        }
-                        __int128 I = 0;
-#pragma unroll
-                        for (int dd = 0; dd < MAXS; ++dd)
-                            if (dd < S) I = I * 128 + __float2int_rn(__uint_as_float(r[dd][j]));
-                        o[j] = i128_ldexp(p.value_sign < 0 ? -I : I, es + el[j] - 7 * (D + 2));
                     }
-                    if (p.b_kmajor) {
-                        // lanes are consecutive rows m: each store is one coalesced 256-byte row
+                } else {
+                    // the CH columns are 8 CH contiguous, 8 CH-byte aligned bytes of row m
+                    double2* dst = reinterpret_cast<double2*>(p.out + base);
+                    if (p.addend) {
+                        const double2* ad = reinterpret_cast<const double2*>(p.addend + base);
+#pragma unroll
+                        for (int v = 0; v < CH / 2; ++v) {
+                            const double2 a2 = ad[v];
+                            o[2 * v] = fma(p.addend_sign, a2.x, o[2 * v]);
+                            o[2 * v + 1] = fma(p.addend_sign, a2.y, o[2 * v + 1]);
+                        }
+                    }
+#pragma unroll
+                    for (int v = 0; v < CH / 2; ++v) dst[v] = make_double2(o[2 * v], o[2 * v + 1]);
+                    if (p.norm2) {
 #pragma unroll
                         for (int j = 0; j < CH; ++j) {
-                            const long long idx = base + (long long)j * p.n1;
-                            double v = o[j];
-                            if (p.addend) v = fma(p.addend_sign, p.addend[idx], v);
-                            p.out[idx] = v;
-                            if (p.norm2) {
-                                const float f = scaled_f32(v, p.norm_shift);
-                                nacc = fmaf(f, f, nacc);
-                            }
-                        }
-                    } else {
-                        // the CH columns are 8 CH contiguous, 8 CH-byte aligned bytes of row m
-                        double2* dst = reinterpret_cast<double2*>(p.out + base);
-                        if (p.addend) {
-                            const double2* ad = reinterpret_cast<const double2*>(p.addend + base);
-#pragma unroll
-                            for (int v = 0; v < CH / 2; ++v) {
-                                const double2 a2 = ad[v];
-                                o[2 * v] = fma(p.addend_sign, a2.x, o[2 * v]);
-                                o[2 * v + 1] = fma(p.addend_sign, a2.y, o[2 * v + 1]);
-                            }
-                        }
-#pragma unroll
-                        for (int v = 0; v < CH / 2; ++v) dst[v] = make_double2(o[2 * v], o[2 * v + 1]);
-                        if (p.norm2) {
-#pragma unroll
-                            for (int j = 0; j < CH; ++j) {
-                                const float f = scaled_f32(o[j], p.norm_shift);
-                                nacc = fmaf(f, f, nacc);
-                            }
+                            const float f = scaled_f32(o[j], p.norm_shift);
+                            nacc = fmaf(f, f, nacc);
                         }
                     }
                 }
+            };
+            const int sh = es - 7 * (D + 2);
+            if (S <= 6) {
+                long long I[EPI_COLS];   // |I| < 2^{24 + 35}: int64
+#pragma unroll
+                for (int j = 0; j < EPI_COLS; ++j) I[j] = 0;
+#pragma unroll
+                for (int h8 = 0; h8 < EPI_COLS; h8 += 8) {
+                    for (int d = 0; d < S; ++d) {
+                        uint32_t r[8];
+                        tmem_ld8(trow + (uint32_t)(d * BN + h8), r);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            I[h8 + j] = I[h8 + j] * 128 + (long long)__float2int_rn(__uint_as_float(r[j]));
+                    }
+                }
+                tc_fence_before();
                 __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[buf]);
+#pragma unroll
+                for (int cc = 0; cc < EPI_COLS; cc += CH) {
+                    emit(cc, [&](int j, int el) {
+                        const long long v = I[cc + j];
+                        return i64_ldexp(p.value_sign < 0 ? -v : v, sh + el);
+                    });
+                    __syncwarp();
+                }
+            } else {
+#pragma unroll
+                for (int cc = 0; cc < EPI_COLS; cc += CH) {
+                    uint32_t r[7][CH];
+#pragma unroll
+                    for (int d = 0; d < 7; ++d) tmem_ld4(trow + (uint32_t)(d * BN + cc), r[d]);
+                    tmem_wait_ld();
+                    if (cc == EPI_COLS - CH) {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&tempty[buf]);
+                    }
+                    // I = h 2^21 + l needs up to 67 bits.  Below 2^62 it is formed exactly
+                    // in int64; above, floor(I / 2^8) keeps at least 54 significant bits,
+                    // so the rounded double moves by at most one ulp
+                    emit(cc, [&](int j, int el) {
+                        long long av[7];
+#pragma unroll
+                        for (int d = 0; d < 7; ++d) av[d] = __float2int_rn(__uint_as_float(r[d][j]));
+                        const long long h = ((av[0] * 128 + av[1]) * 128 + av[2]) * 128 + av[3];
+                        const long long l = (av[4] * 128 + av[5]) * 128 + av[6];
+                        const bool big = h >= (1LL << 40) || h <= -(1LL << 40);
+                        const long long v = big ? h * (1LL << 13) + (l >> 8) : h * (1LL << 21) + l;
+                        return i64_ldexp(p.value_sign < 0 ? -v : v, sh + el + (big ? 8 : 0));
+                    });
+                    __syncwarp();
+                }
             }
         }
         if (p.norm2) {
