@@ -313,10 +313,11 @@ typedef struct tfde_batch tfde_batch;
  * tfde_batch_create -- `count` independent problems of possibly different
  * sizes and coefficients (params[0..count-1], each as for tfde_assemble with
  * TFDE_MIXED: every n_a a multiple of 8 and at most 448), solved together.
- *   Each problem takes the CN step of Eq. (CN) / Eq. (linear_sys) with
- *   left-preconditioned restarted GMRES(restart) (Sec. 3.2, Eq.
- *   (one_side_system)) inside FP64 iterative refinement, whatever its symmetry.
- *   The problems advance in lock step through the Arnoldi iterations: every
+ *   Each problem takes the CN step of Eq. (CN) / Eq. (linear_sys) inside FP64
+ *   iterative refinement, with PCG (Sec. 3.1) when it is symmetric (k+ = k-
+ *   on every axis; see tfde_batch_set_symmetric_pcg) and left-preconditioned
+ *   restarted GMRES(restart) (Sec. 3.2, Eq. (one_side_system)) otherwise.
+ *   The problems advance in lock step through the Krylov iterations: every
  *   split-BF16 operator or preconditioner pass is one persistent tensor-core
  *   launch over a work list of the tiles of all problems (largest problems
  *   first), every vector step one launch over all problems, and a problem
@@ -355,6 +356,26 @@ int tfde_batch_set_guess_order(tfde_batch* batch, int order);
  * TFDE_EINVAL for a NULL batch.
  */
 int tfde_batch_set_spectral_inner(tfde_batch* batch, int enable);
+
+/*
+ * tfde_batch_set_symmetric_pcg -- the inner solver of the batch's symmetric
+ * problems (k+ = k- on every axis): enable != 0 (default) solves them by PCG
+ * (Sec. 3.1) in lock step, in the sine-transform eigenbasis where the tau
+ * preconditioner is the diagonal Lambda (Eq. (diag_tau_pre)): per iteration
+ * three grouped split passes of S_N A S_N over every symmetric problem's
+ * tiles, <p, A p> per problem fused into the last, then one update, one
+ * stop-test and one direction launch over all of them; per refinement sweep
+ * one forward and one backward sine transform.  A problem leaves when its
+ * inner residual has dropped by the sweep's target or after 100 iterations.
+ * The non-symmetric problems keep GMRES.  enable = 0, or the grid basis
+ * (tfde_batch_set_spectral_inner(batch, 0)), sends every problem through
+ * GMRES.  Errors: TFDE_EINVAL for a NULL batch.
+ */
+int tfde_batch_set_symmetric_pcg(tfde_batch* batch, int enable);
+
+/* tfde_batch_pcg_solves -- inner solves (one per problem and refinement
+ * sweep) run so far by the batched PCG; 0 for a NULL batch. */
+long long tfde_batch_pcg_solves(const tfde_batch* batch);
 
 /*
  * tfde_batch_graph_cycles -- how many batched GMRES cycles (Sec. 3.2) so far

@@ -27,6 +27,7 @@ int assemble_problem(const tfde_params* params, int precision, cudaStream_t s, t
 int destroy_problem(tfde_problem* P);
 int cn_prepare(tfde_problem* P, const double* u_prev, const double* F, const double* x0, double* u_next,
                cudaStream_t s, bool chained, bool* r_given, const double* guess, int* used_guess);
+int pcg64(const tfde_problem*, const double*, double*, double, int, tfde_info*, cudaStream_t, bool);
 int pgmres64(tfde_problem*, const double*, double*, int, double, int, tfde_info*, cudaStream_t, bool);
 
 namespace {
@@ -34,10 +35,12 @@ namespace {
 constexpr int kBT = 256;       // threads per block of the vector kernels
 constexpr int kCH = 4096;      // elements per block chunk
 constexpr int kHS = 192;       // per-problem Hessenberg stride: H (64) | H2 (64) | -y (64)
-constexpr int kSS = 8;         // per-problem scalar stride
+constexpr int kSS = 16;        // per-problem scalar stride
 constexpr int kStreams = 8;    // stream pool of the per-problem work
-// scalar slots
-enum { S_SC32 = 0, S_SPLIT = 1, S_ADD = 2, S_BB = 3, S_RR = 4, S_WW = 5 };
+constexpr int kPcgMaxIt = 100; // inner PCG iterations per refinement sweep at most
+// scalar slots (S_RZ .. S_BETA: the batched inner PCG)
+enum { S_SC32 = 0, S_SPLIT = 1, S_ADD = 2, S_BB = 3, S_RR = 4, S_WW = 5, S_RZ = 6, S_RZN = 7, S_PQ = 8, S_RR0 = 9,
+       S_BETA = 10 };
 
 // Per-problem vector pointers of the batched kernels.
 struct BVec {
@@ -54,6 +57,12 @@ struct BVec {
     float* W;            // the graph-captured cycle's new Arnoldi vector before it joins the basis
     const double* r64;
     double* x64;
+    // the batched inner PCG in the eigenbasis: the direction p (FP32, basis
+    // slot V_0) and Lambda's factors [ra (n3) | rb (n3) | U (n1 n2) | V (n1 n2)]
+    float* p32;
+    const float* lam;
+    unsigned nc4;        // n1 n2 / 4
+    int n3;
 };
 
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
@@ -191,6 +200,123 @@ __global__ __launch_bounds__(kBT) void bk_add32to64(const BVec* __restrict__ vt,
     BK_PROLOGUE
     const double f = sc[inst * kSS + S_ADD];
     for (long long e = e0 + threadIdx.x; e < e1; e += kBT) v.x64[e] += f * (double)v.x32[e];
+}
+
+// ---- the batched inner PCG (Sec. 3.1) in the sine-transform eigenbasis,
+// where the tau preconditioner is the diagonal Lambda (Eq. (diag_tau_pre)):
+// per problem r~ = S_N r (r32), p (p32 and its split planes), x~ (x32),
+// q = S_N A S_N p (W); the scalars in the problem's slots.  Elements go four
+// at a time (a chunk holds whole groups: N and kCH are multiples of 4).
+__device__ __forceinline__ float4 bk_lam4(const BVec& v, unsigned e4) {
+    const unsigned k = e4 / v.nc4, c4 = e4 - k * v.nc4;
+    const float ra = __ldg(v.lam + k), rb = __ldg(v.lam + v.n3 + k);
+    const float4 u = __ldg(reinterpret_cast<const float4*>(v.lam + 2 * v.n3) + c4);
+    const float4 w = __ldg(reinterpret_cast<const float4*>(v.lam + 2 * v.n3) + v.nc4 + c4);
+    return make_float4(fmaf(ra, u.x, rb * w.x), fmaf(ra, u.y, rb * w.y), fmaf(ra, u.z, rb * w.z),
+                       fmaf(ra, u.w, rb * w.w));
+}
+__device__ __forceinline__ void split4(const float4 z, __nv_bfloat16* hi, __nv_bfloat16* lo, long long e) {
+    split_bf16(z.x, hi[e], lo[e]);
+    split_bf16(z.y, hi[e + 1], lo[e + 1]);
+    split_bf16(z.z, hi[e + 2], lo[e + 2]);
+    split_bf16(z.w, hi[e + 3], lo[e + 3]);
+}
+__device__ __forceinline__ void ksum4(KSum& k, float4 a, float4 b) {
+    k.add(a.x * b.x);
+    k.add(a.y * b.y);
+    k.add(a.z * b.z);
+    k.add(a.w * b.w);
+}
+
+// zero the sums of a new inner solve
+__global__ void bkp_reset(int C, double* __restrict__ s, const int* __restrict__ act) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C || !act[i]) return;
+    s[i * kSS + S_RZ] = 0.0;
+    s[i * kSS + S_RR0] = 0.0;
+}
+
+// p = Lambda^{-1} r~ and its split planes; S_RZ += <r~, p>, S_RR0 += <r~, r~>
+__global__ __launch_bounds__(kBT) void bkp_first(const BVec* __restrict__ vt, const int* __restrict__ bi,
+                                                const long long* __restrict__ bo, const int* __restrict__ act,
+                                                double* __restrict__ s) {
+    BK_PROLOGUE
+    KSum kz, kr;
+    const float4* r4 = reinterpret_cast<const float4*>(v.r32);
+    float4* p4 = reinterpret_cast<float4*>(v.p32);
+    for (long long e = e0 + 4 * threadIdx.x; e < e1; e += 4 * kBT) {
+        const unsigned e4 = (unsigned)(e >> 2);
+        const float4 rv = r4[e4];
+        const float4 l = bk_lam4(v, e4);
+        const float4 z = make_float4(rv.x / l.x, rv.y / l.y, rv.z / l.z, rv.w / l.w);
+        p4[e4] = z;
+        split4(z, v.ph, v.pl, e);
+        ksum4(kz, rv, z);
+        ksum4(kr, rv, rv);
+    }
+    const double tz = block_sum((double)kz.s - (double)kz.c);
+    const double tr = block_sum((double)kr.s - (double)kr.c);
+    if (threadIdx.x == 0) {
+        atomicAdd(s + inst * kSS + S_RZ, tz);
+        atomicAdd(s + inst * kSS + S_RR0, tr);
+    }
+}
+
+// alpha = S_RZ / S_PQ; x~ += alpha p; r~ -= alpha q; S_RZN += <r~, Lambda^{-1} r~>,
+// S_RR += <r~, r~>
+__global__ __launch_bounds__(kBT) void bkp_update(const BVec* __restrict__ vt, const int* __restrict__ bi,
+                                                 const long long* __restrict__ bo, const int* __restrict__ act,
+                                                 double* __restrict__ s) {
+    BK_PROLOGUE
+    const float alpha = (float)(s[inst * kSS + S_RZ] / s[inst * kSS + S_PQ]);
+    KSum kz, kr;
+    float4* r4 = reinterpret_cast<float4*>(v.r32);
+    float4* x4 = reinterpret_cast<float4*>(v.x32);
+    const float4* p4 = reinterpret_cast<const float4*>(v.p32);
+    const float4* q4 = reinterpret_cast<const float4*>(v.W);
+    for (long long e = e0 + 4 * threadIdx.x; e < e1; e += 4 * kBT) {
+        const unsigned e4 = (unsigned)(e >> 2);
+        const float4 pv = p4[e4], qv = q4[e4];
+        float4 xv = x4[e4], rv = r4[e4];
+        xv.x = fmaf(alpha, pv.x, xv.x);
+        xv.y = fmaf(alpha, pv.y, xv.y);
+        xv.z = fmaf(alpha, pv.z, xv.z);
+        xv.w = fmaf(alpha, pv.w, xv.w);
+        rv.x = fmaf(-alpha, qv.x, rv.x);
+        rv.y = fmaf(-alpha, qv.y, rv.y);
+        rv.z = fmaf(-alpha, qv.z, rv.z);
+        rv.w = fmaf(-alpha, qv.w, rv.w);
+        x4[e4] = xv;
+        r4[e4] = rv;
+        const float4 l = bk_lam4(v, e4);
+        ksum4(kz, rv, make_float4(rv.x / l.x, rv.y / l.y, rv.z / l.z, rv.w / l.w));
+        ksum4(kr, rv, rv);
+    }
+    const double tz = block_sum((double)kz.s - (double)kz.c);
+    const double tr = block_sum((double)kr.s - (double)kr.c);
+    if (threadIdx.x == 0) {
+        atomicAdd(s + inst * kSS + S_RZN, tz);
+        atomicAdd(s + inst * kSS + S_RR, tr);
+    }
+}
+
+// p = Lambda^{-1} r~ + S_BETA p and its split planes
+__global__ __launch_bounds__(kBT) void bkp_direction(const BVec* __restrict__ vt, const int* __restrict__ bi,
+                                                    const long long* __restrict__ bo, const int* __restrict__ act,
+                                                    const double* __restrict__ s) {
+    BK_PROLOGUE
+    const float beta = (float)s[inst * kSS + S_BETA];
+    const float4* r4 = reinterpret_cast<const float4*>(v.r32);
+    float4* p4 = reinterpret_cast<float4*>(v.p32);
+    for (long long e = e0 + 4 * threadIdx.x; e < e1; e += 4 * kBT) {
+        const unsigned e4 = (unsigned)(e >> 2);
+        const float4 rv = r4[e4], po = p4[e4];
+        const float4 l = bk_lam4(v, e4);
+        const float4 z = make_float4(fmaf(beta, po.x, rv.x / l.x), fmaf(beta, po.y, rv.y / l.y),
+                                     fmaf(beta, po.z, rv.z / l.z), fmaf(beta, po.w, rv.w / l.w));
+        p4[e4] = z;
+        split4(z, v.ph, v.pl, e);
+    }
 }
 
 // ---- the same steps for the graph-captured cycle: the step index j comes
@@ -414,6 +540,61 @@ __global__ void bk_cycle_solve(int C, int R, const double* __restrict__ gs, cons
     for (int a = 0; a < k; ++a) y[a] = -y[a];
 }
 
+// start of a batched inner PCG: a problem with <r~, Lambda^{-1} r~> > 0 takes
+// part (act stays set, *cnt counts it), its sums of the first iteration zeroed
+__global__ void bkp_start(int C, double* __restrict__ s, int* __restrict__ act, int* __restrict__ its,
+                          double* __restrict__ est, int* __restrict__ cnt, int* __restrict__ bad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C) return;
+    its[i] = 0;
+    est[i] = 1.0;
+    if (!act[i]) return;
+    double* si = s + (size_t)i * kSS;
+    if (!isfinite(si[S_RZ]) || !isfinite(si[S_RR0])) {
+        atomicOr(bad, 1);
+        act[i] = 0;
+        return;
+    }
+    if (!(si[S_RZ] > 0.0) || !(si[S_RR0] > 0.0)) {
+        act[i] = 0;
+        return;
+    }
+    si[S_PQ] = 0.0;
+    si[S_RZN] = 0.0;
+    si[S_RR] = 0.0;
+    atomicAdd(cnt, 1);
+}
+
+// stop test after PCG iteration j: the problem leaves once ||r~|| <= theta
+// ||r~_0|| (r~ is S_N r and S_N is orthogonal: the true inner residual) or
+// after maxit iterations; else beta = S_RZN / S_RZ for the direction, the
+// sums rotated and zeroed for the next iteration, and *cnt counts it
+__global__ void bkp_stop(int C, int j, int maxit, double* __restrict__ s, const double* __restrict__ theta,
+                         int* __restrict__ act, int* __restrict__ its, double* __restrict__ est,
+                         int* __restrict__ cnt, int* __restrict__ bad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C || !act[i]) return;
+    double* si = s + (size_t)i * kSS;
+    const double rr = si[S_RR], rr0 = si[S_RR0];
+    its[i] = j + 1;
+    est[i] = sqrt(rr / rr0);
+    if (!isfinite(rr) || !isfinite(si[S_RZN]) || !isfinite(si[S_PQ])) {
+        atomicOr(bad, 1);
+        act[i] = 0;
+        return;
+    }
+    if (rr <= theta[i] * theta[i] * rr0 || j + 1 >= maxit || !(si[S_RZN] > 0.0)) {
+        act[i] = 0;
+        return;
+    }
+    si[S_BETA] = si[S_RZN] / si[S_RZ];
+    si[S_RZ] = si[S_RZN];
+    si[S_RZN] = 0.0;
+    si[S_RR] = 0.0;
+    si[S_PQ] = 0.0;
+    atomicAdd(cnt, 1);
+}
+
 using clk = std::chrono::steady_clock;
 
 }  // namespace
@@ -453,6 +634,14 @@ struct tfde_batch {
     tfde::tc::Params* d_sbw = nullptr;
     double sfw_bytes[3] = {}, sfw_flops[3] = {}, sop_bytes[3] = {}, sop_flops[3] = {}, sbw_bytes[3] = {},
            sbw_flops[3] = {};
+    // symmetric problems take the batched inner PCG (Sec. 3.1) in the
+    // eigenbasis (tfde_batch_set_symmetric_pcg): the forward transform to
+    // S_N r [3][count] and the operator's z pass with <p, q> [count]
+    bool sym_pcg = true;
+    tfde::tc::Params* d_sfp = nullptr;
+    tfde::tc::Params* d_sopq = nullptr;
+    double sfp_bytes[3] = {}, sfp_flops[3] = {}, sopq_bytes = 0.0, sopq_flops = 0.0;
+    long long pcg_solves = 0;       // problem-sweeps solved by the batched PCG
     long long* d_gstart = nullptr;  // [3][count + 1]
     long long gtotal[3] = {};
     // vector kernels: per-problem pointers and the block table
@@ -480,11 +669,11 @@ struct tfde_batch {
     int* h_its = nullptr;
     double* d_est = nullptr;
     double* h_est = nullptr;
-    int* d_cnt = nullptr;           // restart + 1
+    int* d_cnt = nullptr;           // max(restart, kPcgMaxIt) + 1
     int* h_cnt = nullptr;
     int* d_bad = nullptr;
     int* h_bad = nullptr;
-    std::vector<cudaEvent_t> cnt_ev;   // restart + 1
+    std::vector<cudaEvent_t> cnt_ev;   // max(restart, kPcgMaxIt) + 1
     cudaStream_t aux[tfde::kStreams] = {};
     cudaEvent_t ev[tfde::kStreams] = {};
     cudaEvent_t fork_ev = nullptr;
@@ -529,6 +718,8 @@ int free_batch(tfde_batch* B) {
     cudaFree(B->d_sop);
     cudaFree(B->d_sopz);
     cudaFree(B->d_sbw);
+    cudaFree(B->d_sfp);
+    cudaFree(B->d_sopq);
     cudaFree(B->d_mv);
     cudaFree(B->d_pc);
     cudaFree(B->d_pcl);
@@ -835,6 +1026,86 @@ int batch_cycle(tfde_batch* B, const std::vector<int>& outer, const std::vector<
     return TFDE_OK;
 }
 
+// One lock-step inner PCG (Sec. 3.1) for every problem with outer[i] set
+// (symmetric problems), in the sine-transform eigenbasis: the scaled residual
+// r32 (planes PL_R) goes to r~ = S_N r, PCG with the diagonal Lambda runs on
+// S_N A S_N x~ = r~ until ||r~_k|| <= theta[i] ||r~_0|| (r~_k is the true inner
+// residual in that basis), and x32 = S_N x~ on return.  Per iteration: the
+// operator's three grouped passes over all active problems' tiles (the z pass
+// adds <p, q> per problem), then one update, one stop test and one direction
+// launch over all of them; the host learns how many problems are left one
+// iteration late, as in batch_cycle.  est[i] = ||r~_k|| / ||r~_0||, its[i] =
+// iterations.
+int batch_pcg(tfde_batch* B, const std::vector<int>& outer, const std::vector<double>& theta,
+              std::vector<double>& est, std::vector<int>& its, cudaStream_t s) {
+    const int C = B->count;
+    const int gb = (C + 63) / 64;
+    int st;
+    for (int i = 0; i < C; ++i) {
+        B->h_act[i] = outer[i];
+        B->h_theta[i] = theta[i];
+    }
+    B_TRY(cudaMemcpyAsync(B->d_act, B->h_act, C * sizeof(int), cudaMemcpyHostToDevice, s));
+    B_TRY(cudaMemcpyAsync(B->d_theta, B->h_theta, C * sizeof(double), cudaMemcpyHostToDevice, s));
+    B_TRY(cudaMemsetAsync(B->d_cnt, 0, (kPcgMaxIt + 1) * sizeof(int), s));
+    B_TRY(cudaMemsetAsync(B->d_bad, 0, sizeof(int), s));
+    for (int a = 0; a < 3; ++a)   // r~ = S_N r into r32
+        if ((st = grouped(B, B->d_sfp + (size_t)a * C, a, a < 2 ? tc::OUT_HILO : tc::OUT_F32, B->sfp_bytes[a],
+                          B->sfp_flops[a], s)))
+            return st;
+    vec_launch_count();
+    bkp_reset<<<gb, 64, 0, s>>>(C, B->d_s, B->d_act);
+    vec_launch_count();
+    bkp_first<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, B->d_s);
+    vec_launch_count();
+    bkp_start<<<gb, 64, 0, s>>>(C, B->d_s, B->d_act, B->d_its, B->d_est, B->d_cnt, B->d_bad);
+    B_TRY(cudaMemcpyAsync(B->h_cnt, B->d_cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaEventRecord(B->cnt_ev[0], s));
+    for (int j = 0; j < kPcgMaxIt; ++j) {
+        // stop issuing once no problem is left: the count after iteration j - 1
+        // if it is already in, else the one after iteration j - 2
+        if (cudaEventQuery(B->cnt_ev[j]) == cudaSuccess) {
+            if (B->h_cnt[j] == 0) break;
+        } else if (j >= 1) {
+            B_TRY(cudaEventSynchronize(B->cnt_ev[j - 1]));
+            if (B->h_cnt[j - 1] == 0) break;
+        }
+        for (int a = 0; a < 2; ++a)
+            if ((st = grouped(B, B->d_sop + (size_t)a * C, a, tc::OUT_SUM, B->sop_bytes[a], B->sop_flops[a], s)))
+                return st;
+        if ((st = grouped(B, B->d_sopq, 2, tc::OUT_SUM, B->sopq_bytes, B->sopq_flops, s))) return st;
+        vec_launch_count();
+        bkp_update<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, B->d_s);
+        vec_launch_count();
+        bkp_stop<<<gb, 64, 0, s>>>(C, j, kPcgMaxIt, B->d_s, B->d_theta, B->d_act, B->d_its, B->d_est,
+                                   B->d_cnt + j + 1, B->d_bad);
+        B_TRY(cudaMemcpyAsync(B->h_cnt + j + 1, B->d_cnt + j + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        B_TRY(cudaEventRecord(B->cnt_ev[j + 1], s));
+        vec_launch_count();
+        bkp_direction<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, B->d_s);
+    }
+    B_TRY(cudaMemcpyAsync(B->h_its, B->d_its, C * sizeof(int), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaMemcpyAsync(B->h_est, B->d_est, C * sizeof(double), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaMemcpyAsync(B->h_bad, B->d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaMemcpyAsync(B->h_err, B->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaStreamSynchronize(s));
+    if (*B->h_err) return set_error(TFDE_ETIMEOUT, "tensor-core kernel wait ran out (device error flag set)");
+    if (*B->h_bad) return set_error(TFDE_ENAN, "non-finite value in a batched PCG solve");
+    int kmax = 0;
+    for (int i = 0; i < C; ++i) {
+        its[i] = outer[i] ? B->h_its[i] : 0;
+        est[i] = outer[i] ? B->h_est[i] : 1.0;
+        kmax = std::max(kmax, its[i]);
+        if (outer[i]) ++B->pcg_solves;
+    }
+    if (kmax > 0) {   // x32 = S_N x~ (a problem without iterations keeps x32 = 0)
+        for (int i = 0; i < C; ++i) B->h_act[i] = outer[i] && its[i] > 0;
+        B_TRY(cudaMemcpyAsync(B->d_act, B->h_act, C * sizeof(int), cudaMemcpyHostToDevice, s));
+        if ((st = grouped_spec_back(B, s))) return st;
+    }
+    return TFDE_OK;
+}
+
 // FP64 norms of W_B and W_R of every problem with act set, into S_BB / S_RR.
 void batch_norms(tfde_batch* B, const std::vector<int>& act, bool with_b, cudaStream_t s) {
     fork(B, s);
@@ -984,6 +1255,7 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
         bstart[i + 1] = bstart[i] + (int)nb;
     }
     B->NB = bstart[C];
+    const int ncnt = std::max(restart, kPcgMaxIt);
     if (cudaMalloc((void**)&B->d_vt, C * sizeof(BVec)) != cudaSuccess ||
         cudaMallocHost((void**)&B->h_vt, C * sizeof(BVec)) != cudaSuccess ||
         cudaMalloc((void**)&B->d_bi, bi.size() * sizeof(int)) != cudaSuccess ||
@@ -1002,12 +1274,12 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
         cudaMallocHost((void**)&B->h_its, C * sizeof(int)) != cudaSuccess ||
         cudaMalloc((void**)&B->d_est, C * sizeof(double)) != cudaSuccess ||
         cudaMallocHost((void**)&B->h_est, C * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void**)&B->d_cnt, (restart + 1) * sizeof(int)) != cudaSuccess ||
-        cudaMallocHost((void**)&B->h_cnt, (restart + 1) * sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_cnt, (size_t)(ncnt + 1) * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&B->h_cnt, (size_t)(ncnt + 1) * sizeof(int)) != cudaSuccess ||
         cudaMalloc((void**)&B->d_bad, sizeof(int)) != cudaSuccess ||
         cudaMallocHost((void**)&B->h_bad, sizeof(int)) != cudaSuccess)
         return fail(TFDE_ENOMEM, "allocation of the batch workspace failed");
-    B->cnt_ev.assign(restart + 1, nullptr);
+    B->cnt_ev.assign(ncnt + 1, nullptr);
     for (auto& e : B->cnt_ev)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
             return fail(TFDE_ECUDA, "event creation failed");
@@ -1028,7 +1300,33 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
         v.W = M->f[F_Q];
         v.r64 = P->w[tfde_problem::W_R];
         v.x64 = nullptr;
+        v.p32 = M->V32;
+        v.lam = M->lam;
+        v.nc4 = (unsigned)((long long)P->n[0] * P->n[1] / 4);
+        v.n3 = P->n[2];
     }
+    // the batched PCG's descriptors (the z pass adds <p, q> into the problem's S_PQ)
+    std::vector<tc::Params> sfp(3 * C), sopq(C);
+    for (size_t i = 0; i < C; ++i) {
+        tfde_problem* P = B->P[i];
+        MixedState* M = mixed(P);
+        tc::Params tmp[6];
+        int axes[6];
+        double by[6], fl[6];
+        spec_pass_descriptors(P, 5, M->f[F_R], tmp, axes, by, fl);
+        for (int a = 0; a < 3; ++a) {
+            sfp[a * C + i] = tmp[a];
+            B->sfp_bytes[a] += by[a];
+            B->sfp_flops[a] += fl[a];
+        }
+        spec_pass_descriptors(P, 3, M->f[F_Q], tmp, axes, by, fl, M->V32, B->d_s + i * kSS + S_PQ);
+        sopq[i] = tmp[2];
+        B->sopq_bytes += by[2];
+        B->sopq_flops += fl[2];
+    }
+    if (cudaMalloc((void**)&B->d_sfp, sfp.size() * PS) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_sopq, sopq.size() * PS) != cudaSuccess)
+        return fail(TFDE_ENOMEM, "cudaMalloc of the grouped descriptors failed");
     std::memset(B->h_s, 0, C * kSS * sizeof(double));
     if (cudaMemsetAsync(B->d_h, 0, C * kHS * sizeof(double), s) != cudaSuccess)
         return fail(TFDE_ECUDA, "batch workspace initialisation failed");
@@ -1040,6 +1338,8 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
         cudaMemcpyAsync(B->d_sopz, sopz.data(), sopz.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(B->d_sbw, sbw.data(), sbw.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(B->d_sopzw, sopzw.data(), sopzw.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(B->d_sfp, sfp.data(), sfp.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(B->d_sopq, sopq.data(), sopq.size() * PS, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(B->d_gstart, gstart.data(), gstart.size() * sizeof(long long), cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
         cudaMemcpyAsync(B->d_bi, bi.data(), bi.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -1090,6 +1390,14 @@ extern "C" int tfde_batch_set_spectral_inner(tfde_batch* B, int enable) {
     B->spectral = enable != 0;
     return TFDE_OK;
 }
+
+extern "C" int tfde_batch_set_symmetric_pcg(tfde_batch* B, int enable) {
+    if (!B) return tfde::set_error(TFDE_EINVAL, "NULL batch");
+    B->sym_pcg = enable != 0;
+    return TFDE_OK;
+}
+
+extern "C" long long tfde_batch_pcg_solves(const tfde_batch* B) { return B ? B->pcg_solves : 0; }
 
 extern "C" int tfde_batch_set_guess_order(tfde_batch* B, int order) {
     if (!B) return tfde::set_error(TFDE_EINVAL, "NULL batch");
@@ -1170,7 +1478,35 @@ int batch_cn_advance(tfde_batch* B, double* const* u, const double* const* F, in
         if ((st = upload_act_scalars(B, s))) return st;
         stats_count_launch();
         bk_scale64to32<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, B->d_s);
-        if ((st = batch_cycle(B, outer, theta, est, its, s))) return st;
+        // symmetric problems: batched PCG; the others: batched GMRES cycles
+        std::vector<int> og(C, 0), op(C, 0);
+        bool anyg = false, anyp = false;
+        for (int i = 0; i < C; ++i) {
+            if (!outer[i]) continue;
+            if (B->sym_pcg && B->spectral && B->P[i]->symmetric) {
+                op[i] = 1;
+                anyp = true;
+            } else {
+                og[i] = 1;
+                anyg = true;
+            }
+        }
+        if (anyg) {
+            if ((st = batch_cycle(B, og, theta, est, its, s))) return st;
+        } else {
+            std::fill(est.begin(), est.end(), 1.0);
+            std::fill(its.begin(), its.end(), 0);
+        }
+        if (anyp) {
+            std::vector<double> est_p(C, 1.0);
+            std::vector<int> its_p(C, 0);
+            if ((st = batch_pcg(B, op, theta, est_p, its_p, s))) return st;
+            for (int i = 0; i < C; ++i)
+                if (op[i]) {
+                    est[i] = est_p[i];
+                    its[i] = its_p[i];
+                }
+        }
         for (int i = 0; i < C; ++i) B->h_act[i] = outer[i];
         B_TRY(cudaMemcpyAsync(B->d_act, B->h_act, C * sizeof(int), cudaMemcpyHostToDevice, s));
         stats_count_launch();
@@ -1211,7 +1547,9 @@ int batch_cn_advance(tfde_batch* B, double* const* u, const double* const* F, in
                 tfde_problem* P = B->P[i];
                 tfde_info sub{};
                 info[i].fallback = 1;
-                status[i] = pgmres64(P, P->w[tfde_problem::W_B], uu[i], B->restart, tol, 10000, &sub, s, false);
+                status[i] = (B->sym_pcg && B->spectral && P->symmetric)
+                                ? pcg64(P, P->w[tfde_problem::W_B], uu[i], tol, 10000, &sub, s, false)
+                                : pgmres64(P, P->w[tfde_problem::W_B], uu[i], B->restart, tol, 10000, &sub, s, false);
                 info[i].iters += sub.iters;
                 info[i].restarts += sub.restarts;
                 nr[i] = sub.relres * nb[i];

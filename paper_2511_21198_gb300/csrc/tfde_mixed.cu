@@ -1242,7 +1242,7 @@ int fast_pass_descriptors(const tfde_problem* P, int kind, float* out_f32, tc::P
 }
 
 int spec_pass_descriptors(const tfde_problem* P, int kind, float* out_f32, tc::Params* prm, int* axes, double* bytes,
-                          double* flops) {
+                          double* flops, const float* dot_vec, double* dot_out) {
     MixedState* M = mixed(P);
     const long long n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
     const double N = (double)P->N;
@@ -1252,16 +1252,21 @@ int spec_pass_descriptors(const tfde_problem* P, int kind, float* out_f32, tc::P
         if (kind == 3) {
             const SegSpec sg[1] = {{OM_BX_H + 2 * a, OM_BX_L + 2 * a, PL_P}};
             float* out = a == 0 ? M->f[F_Z] : (a == 1 ? M->f[F_P] : out_f32);
-            gemm_params(P, a, sg, 1, tc::OUT_SUM, 1.f, out, -1, a == 2, q, &bytes[a], &flops[a]);
+            gemm_params(P, a, sg, 1, tc::OUT_SUM, 1.f, out, -1, a == 2 && !dot_out, q, &bytes[a], &flops[a]);
             q.col_scale = M->spec + (a == 0 ? 0 : (a == 1 ? n2 * n3 : n2 * n3 + n1 * n3));
             if (a > 0) {
                 q.addend = a == 1 ? M->f[F_Z] : M->f[F_P];
                 bytes[a] += 4.0 * N;
             }
+            if (a == 2 && dot_out) {
+                q.dot_vec = dot_vec;
+                q.dot_out = dot_out;
+                bytes[a] += 4.0 * N;
+            }
         } else {
-            const int in = kind == 2 ? (a == 0 ? PL_R : (a == 1 ? PL_T1 : PL_T2))
-                                     : (a == 0 ? PL_T1 : (a == 1 ? PL_T2 : PL_R));
-            const int outp = kind == 2 ? (a == 0 ? PL_T1 : PL_T2) : (a == 0 ? PL_T2 : PL_R);
+            const bool fwd = kind == 2 || kind == 5;
+            const int in = fwd ? (a == 0 ? PL_R : (a == 1 ? PL_T1 : PL_T2)) : (a == 0 ? PL_T1 : (a == 1 ? PL_T2 : PL_R));
+            const int outp = fwd ? (a == 0 ? PL_T1 : PL_T2) : (a == 0 ? PL_T2 : PL_R);
             const SegSpec sg[1] = {{OM_S2X_H + 2 * a, OM_S2X_L + 2 * a, in}};
             const int mode = a < 2 ? tc::OUT_HILO : (kind == 2 ? tc::OUT_SUM : tc::OUT_F32);
             gemm_params(P, a, sg, 1, mode, 1.f, a == 2 ? out_f32 : nullptr, a < 2 ? outp : -1, kind == 2 && a == 2, q,

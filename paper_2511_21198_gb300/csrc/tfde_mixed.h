@@ -227,10 +227,13 @@ int fast_pass_descriptors(const tfde_problem* P, int kind, float* out_f32, tc::P
 // PL_R with Lambda^{-1} fused, out_f32 = Lambda^{-1} S_N r; kind 3 = the
 // preconditioned operator on the basis planes PL_P, out_f32 = Lambda^{-1}
 // S_N A S_N v (x and y passes chained through F_Z, F_P); kind 4 = backward
-// sine transform of the planes PL_T1, out_f32 = S_N t (through PL_T2, PL_R).
-// Returns 3 (passes); axes[i], bytes[i], flops[i] per pass.
+// sine transform of the planes PL_T1, out_f32 = S_N t (through PL_T2, PL_R);
+// kind 5 = forward sine transform of PL_R without Lambda, out_f32 = S_N r
+// (PCG, Sec. 3.1).  With dot_out set, kind 3's z pass leaves out Lambda^{-1}
+// (out_f32 = S_N A S_N v, the PCG operator) and adds <dot_vec, out_f32> into
+// *dot_out.  Returns 3 (passes); axes[i], bytes[i], flops[i] per pass.
 int spec_pass_descriptors(const tfde_problem* P, int kind, float* out_f32, tc::Params* prm, int* axes, double* bytes,
-                          double* flops);
+                          double* flops, const float* dot_vec = nullptr, double* dot_out = nullptr);
 // Allocate the FP32 GMRES basis (restart + 1 vectors) and Hessenberg scratch.
 int mixed_prepare_gmres(const tfde_problem* P, int restart);
 

@@ -118,7 +118,8 @@ struct Params {
     const float* lam_rb;
     const float* lam_U;
     const float* lam_V;
-    // optional fused inner product (OUT_F32 only): *dot_out += sum out[i] dot_vec[i]
+    // optional fused inner product (OUT_F32, OUT_SUM): *dot_out += sum out[i] dot_vec[i];
+    // a grouped launch adds each group's sum into that group's dot_out
     const float* dot_vec;
     double* dot_out;
     // optional, with lam_ra (z-axis DST pass): *dot_out += sum t[i] (t / Lambda)[i],
@@ -444,7 +445,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         int half_sel = 0;
         long long it = 0;
         bool pending = false;                 // a store of this warp may still read the slot
-        DotAcc da;                            // fused inner product (single launches only)
+        DotAcc da;                            // fused inner product
+        // grouped launches: the destination of da (each group has its own; the
+        // tiles of a CTA visit the groups in increasing order, so da is flushed
+        // into a group's destination when the next group's first tile comes)
+        double* dot_dst = GROUPED ? nullptr : p0.dot_out;
+        auto flush_dot = [&]() {
+            double t = (double)da.s - (double)da.c;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0 && dot_dst) atomicAdd(dot_dst, t);
+            da = DotAcc();
+        };
         float xp_beta = 0.f;                  // OUT_XPAY coefficient
         if constexpr (OM == OUT_XPAY) {
             if (p0.xp_den) xp_beta = (float)(__ldg(p0.xp_num) / __ldg(p0.xp_den));
@@ -459,6 +471,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 lt = t - __ldg(gstart + g);
             }
             const Params& p = *pp;
+            if (GROUPED && p.dot_out != dot_dst) {   // warp-uniform
+                if (dot_dst) flush_dot();
+                dot_dst = p.dot_out;
+            }
             const int buf = (int)(it & 1);
             const uint32_t use = (uint32_t)(it >> 1);
             int ok = 1;
@@ -740,12 +756,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         if (lane == 0) bulk_wait0();   // every store of this warp has completed
         __syncwarp();
-        if (p0.dot_out) {
-            double t = (double)da.s - (double)da.c;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) atomicAdd(p0.dot_out, t);
-        }
+        if (dot_dst) flush_dot();
     }
 
     tc_fence_before();

@@ -224,3 +224,107 @@ def test_batch_graph_cycle_and_host_loop_agree(T):
         xo, _ = o.gmres_left(lambda v: o.apply_A(op, v), lambda r: o.apply_Pinv(tau, r), b, u0[i], 1e-14, 4000,
                              restart=20, criterion="true")
         assert relerr(runs[False][1][i], xo) < 1e-10 and relerr(runs[True][1][i], xo) < 1e-10, i
+
+
+def symmetric_batch(count, seed, sizes):
+    """Uneven symmetric problems (k+ = k- on every axis, drawn per axis)."""
+    probs = small_batch(count, seed, sizes=sizes)
+    for p in probs:
+        p["km"] = p["kp"]
+    return probs
+
+
+def oracle_step(p, u0, dt):
+    """The oracle's CN solution from u0: PCG (Sec. 3.1) when the problem is
+    symmetric, left-preconditioned GMRES (Sec. 3.2) otherwise."""
+    op = o.Problem(n=p["n"], delta=p["delta"], kp=p["kp"], km=p["km"], dt=dt)
+    b = o.rhs(op, u0, None)
+    tau = o.build_tau(op)
+    if tuple(p["kp"]) == tuple(p["km"]):
+        x, _ = o.pcg(lambda v: o.apply_A(op, v), lambda r: o.apply_Pinv(tau, r), b, u0.copy(), 1e-14, 4000)
+    else:
+        x, _ = o.gmres_left(lambda v: o.apply_A(op, v), lambda r: o.apply_Pinv(tau, r), b, u0, 1e-14, 4000,
+                            restart=20, criterion="true")
+    return x
+
+
+def test_batch_symmetric_problems_take_pcg(T):
+    """Five uneven symmetric problems (ragged tiles): one batched step runs
+    their inner solves as the lock-step PCG (no GMRES cycle at all) and each
+    solution equals the oracle's PCG solution of its CN system."""
+    probs = symmetric_batch(5, 19, sizes=(8, 16, 24, 40, 136))
+    dt = 0.05
+    params = [T.make_params(p["n"], p["delta"], p["kp"], p["km"], dt) for p in probs]
+    B = T.tfde_batch_create(params, 20)
+    try:
+        u0 = [inp.smoothed_uniform(tuple(reversed(p["n"])), 70 + i) for i, p in enumerate(probs)]
+        us = [to_dev(u) for u in u0]
+        infos = T.tfde_batch_cn_advance(B, us, None, True, 1e-12)
+        sweeps = sum(i.refine_sweeps for i in infos)
+        assert T.tfde_batch_pcg_solves(B) == sweeps > 0
+        assert T.tfde_batch_graph_cycles(B) == 0
+        for i, p in enumerate(probs):
+            assert infos[i].relres <= 1e-12 and infos[i].fallback == 0, (i, infos[i].relres)
+            assert relerr(to_host(us[i]), oracle_step(p, u0[i], dt)) < 1e-10, i
+    finally:
+        T.tfde_batch_destroy(B)
+
+
+def test_batch_mixed_symmetry_pcg_and_gmres(T):
+    """Three symmetric and three non-symmetric problems in one batch: the
+    symmetric ones take the batched PCG, the others the batched GMRES cycles,
+    in the same refinement sweeps; every solution matches the oracle's."""
+    sym = symmetric_batch(3, 23, sizes=(8, 16, 24, 32))
+    nonsym = small_batch(3, 29, sizes=(8, 16, 24, 32))
+    probs = [sym[0], nonsym[0], sym[1], nonsym[1], sym[2], nonsym[2]]
+    dt = 0.1
+    params = [T.make_params(p["n"], p["delta"], p["kp"], p["km"], dt) for p in probs]
+    B = T.tfde_batch_create(params, 20)
+    try:
+        u0 = [inp.smoothed_uniform(tuple(reversed(p["n"])), 80 + i) for i, p in enumerate(probs)]
+        us = [to_dev(u) for u in u0]
+        infos = T.tfde_batch_cn_advance(B, us, None, True, 1e-12)
+        assert T.tfde_batch_pcg_solves(B) == sum(infos[i].refine_sweeps for i in (0, 2, 4))
+        assert T.tfde_batch_graph_cycles(B) > 0
+        for i, p in enumerate(probs):
+            assert infos[i].relres <= 1e-12 and infos[i].fallback == 0, (i, infos[i].relres)
+            assert relerr(to_host(us[i]), oracle_step(p, u0[i], dt)) < 1e-10, i
+    finally:
+        T.tfde_batch_destroy(B)
+
+
+def test_batch_symmetric_pcg_chained_steps_and_toggle(T):
+    """Four chained steps of a symmetric batch with the batched PCG, and the
+    same steps with it switched off (every problem through GMRES): both
+    trajectories equal the single-problem mixed path's at tight residuals,
+    and only the first run uses the PCG."""
+    probs = symmetric_batch(4, 31, sizes=(16, 24, 32, 48))
+    dt = 0.05
+    params = [T.make_params(p["n"], p["delta"], p["kp"], p["km"], dt) for p in probs]
+    u0 = [inp.smoothed_uniform(tuple(reversed(p["n"])), 90 + i) for i, p in enumerate(probs)]
+    singles = [T.tfde_assemble(pp, T.TFDE_MIXED) for pp in params]
+    try:
+        ref = [to_dev(u) for u in u0]
+        for m in range(4):
+            for i in range(len(probs)):
+                assert T.tfde_cn_advance(singles[i], ref[i], None, m == 0, 1e-12).relres <= 1e-12
+        for pcg in (True, False):
+            B = T.tfde_batch_create(params, 20)
+            try:
+                T.tfde_batch_set_symmetric_pcg(B, pcg)
+                ub = [to_dev(u) for u in u0]
+                for m in range(4):
+                    infos = T.tfde_batch_cn_advance(B, ub, None, m == 0, 1e-12)
+                    assert all(i.relres <= 1e-12 and i.fallback == 0 for i in infos), m
+                assert (T.tfde_batch_pcg_solves(B) > 0) if pcg else (T.tfde_batch_pcg_solves(B) == 0)
+                assert (T.tfde_batch_graph_cycles(B) == 0) if pcg else (T.tfde_batch_graph_cycles(B) > 0)
+                for i in range(len(probs)):
+                    assert relerr(to_host(ub[i]), to_host(ref[i])) < 1e-10, (pcg, i)
+            finally:
+                T.tfde_batch_destroy(B)
+        with pytest.raises(T.TfdeError) as e:
+            T.tfde_batch_set_symmetric_pcg(0, True)
+        assert e.value.status == T.TFDE_EINVAL
+    finally:
+        for h in singles:
+            T.tfde_destroy(h)
