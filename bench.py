@@ -928,6 +928,21 @@ def run_batched(T, count, steps, dev, stream, guess_order=0):
         for h in hs:
             T.tfde_destroy(h)
     out["speedup_vs_loop"] = out["batched"]["problem_steps_per_s"] / out["loop_of_single_calls"]["problem_steps_per_s"]
+    # the symmetric variant of the same problems (k- = k+): the batched PCG
+    # against every problem through the batched GMRES cycles
+    sym_params = [T.make_params(p["n"], p["delta"], p["kp"], p["kp"], dt) for p in probs]
+    B = T.tfde_batch_create(sym_params, 20, stream)
+    T.tfde_batch_set_guess_order(B, guess_order)
+    try:
+        sym = {"workload": f"the same {count} problems with k- = k+ (symmetric), {steps} CN steps, tol 1e-8"}
+        for key, pcg in (("pcg", True), ("gmres", False)):
+            T.tfde_batch_set_symmetric_pcg(B, pcg)
+            sym[key] = timed()
+        sym["pcg_solves"] = T.tfde_batch_pcg_solves(B)
+        sym["pcg_vs_gmres"] = sym["pcg"]["problem_steps_per_s"] / sym["gmres"]["problem_steps_per_s"]
+        out["symmetric_variant"] = sym
+    finally:
+        T.tfde_batch_destroy(B)
     return out
 
 

@@ -367,6 +367,10 @@ int tfde_batch_set_spectral_inner(tfde_batch* batch, int enable);
  * stop-test and one direction launch over all of them; per refinement sweep
  * one forward and one backward sine transform.  A problem leaves when its
  * inner residual has dropped by the sweep's target or after 100 iterations.
+ * The iterations of a sweep run as one CUDA-graph launch (a while node; the
+ * iteration index, the stop tests and the loop condition on the device)
+ * unless tfde_stats_reset(1) times every tensor-core launch (the host then
+ * drives them, learning the count of problems left one iteration late).
  * The non-symmetric problems keep GMRES.  enable = 0, or the grid basis
  * (tfde_batch_set_spectral_inner(batch, 0)), sends every problem through
  * GMRES.  Errors: TFDE_EINVAL for a NULL batch.
@@ -376,6 +380,10 @@ int tfde_batch_set_symmetric_pcg(tfde_batch* batch, int enable);
 /* tfde_batch_pcg_solves -- inner solves (one per problem and refinement
  * sweep) run so far by the batched PCG; 0 for a NULL batch. */
 long long tfde_batch_pcg_solves(const tfde_batch* batch);
+
+/* tfde_batch_pcg_graph_launches -- refinement sweeps whose batched PCG
+ * iterations ran as one graph launch; 0 for a NULL batch. */
+long long tfde_batch_pcg_graph_launches(const tfde_batch* batch);
 
 /*
  * tfde_batch_graph_cycles -- how many batched GMRES cycles (Sec. 3.2) so far

@@ -569,9 +569,10 @@ __global__ void bkp_start(int C, double* __restrict__ s, int* __restrict__ act, 
 // ||r~_0|| (r~ is S_N r and S_N is orthogonal: the true inner residual) or
 // after maxit iterations; else beta = S_RZN / S_RZ for the direction, the
 // sums rotated and zeroed for the next iteration, and *cnt counts it
-__global__ void bkp_stop(int C, int j, int maxit, double* __restrict__ s, const double* __restrict__ theta,
-                         int* __restrict__ act, int* __restrict__ its, double* __restrict__ est,
-                         int* __restrict__ cnt, int* __restrict__ bad) {
+__device__ __forceinline__ void bkp_stop_body(int C, int j, int maxit, double* __restrict__ s,
+                                              const double* __restrict__ theta, int* __restrict__ act,
+                                              int* __restrict__ its, double* __restrict__ est, int* __restrict__ cnt,
+                                              int* __restrict__ bad) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= C || !act[i]) return;
     double* si = s + (size_t)i * kSS;
@@ -593,6 +594,19 @@ __global__ void bkp_stop(int C, int j, int maxit, double* __restrict__ s, const 
     si[S_RR] = 0.0;
     si[S_PQ] = 0.0;
     atomicAdd(cnt, 1);
+}
+__global__ void bkp_stop(int C, int j, int maxit, double* __restrict__ s, const double* __restrict__ theta,
+                         int* __restrict__ act, int* __restrict__ its, double* __restrict__ est,
+                         int* __restrict__ cnt, int* __restrict__ bad) {
+    bkp_stop_body(C, j, maxit, s, theta, act, its, est, cnt, bad);
+}
+
+// bkp_stop with the iteration index j = *jd (the graph-captured loop)
+__global__ void bkpg_stop(int C, const int* __restrict__ jd, int maxit, double* __restrict__ s,
+                          const double* __restrict__ theta, int* __restrict__ act, int* __restrict__ its,
+                          double* __restrict__ est, int* __restrict__ cnt, int* __restrict__ bad) {
+    const int j = *jd;
+    bkp_stop_body(C, j, maxit, s, theta, act, its, est, cnt + j + 1, bad);
 }
 
 using clk = std::chrono::steady_clock;
@@ -642,6 +656,13 @@ struct tfde_batch {
     tfde::tc::Params* d_sopq = nullptr;
     double sfp_bytes[3] = {}, sfp_flops[3] = {}, sopq_bytes = 0.0, sopq_flops = 0.0;
     long long pcg_solves = 0;       // problem-sweeps solved by the batched PCG
+    // its iterations as one graph launch per sweep (a while node, the
+    // iteration index and each problem's stop test on the device)
+    cudaGraph_t pcg_graph = nullptr;
+    cudaGraphExec_t pcg_exec = nullptr;
+    bool pcg_failed = false;
+    unsigned pcg_tune_gen = 0;
+    long long pcg_graph_launches = 0;
     long long* d_gstart = nullptr;  // [3][count + 1]
     long long gtotal[3] = {};
     // vector kernels: per-problem pointers and the block table
@@ -714,6 +735,8 @@ int free_batch(tfde_batch* B) {
     cudaFree(B->d_j);
     if (B->cyc_exec) cudaGraphExecDestroy(B->cyc_exec);
     if (B->cyc_graph) cudaGraphDestroy(B->cyc_graph);
+    if (B->pcg_exec) cudaGraphExecDestroy(B->pcg_exec);
+    if (B->pcg_graph) cudaGraphDestroy(B->pcg_graph);
     cudaFree(B->d_sfw);
     cudaFree(B->d_sop);
     cudaFree(B->d_sopz);
@@ -901,6 +924,75 @@ int build_cycle_graph(tfde_batch* B, cudaStream_t s) {
 // launches of one captured step: 3 grouped + 2 x (ceil(R / 8) + 2) + 5
 unsigned cycle_step_launches(int R) { return 3u + 2u * (unsigned)((R + 7) / 8 + 2) + 5u; }
 
+// The batched PCG iteration of every symmetric problem as the body of a while
+// node: the operator's three grouped passes (<p, q> per problem), the update,
+// the stop test at j = *d_j, the direction, and the loop condition (a problem
+// still iterating and j + 1 < kPcgMaxIt).  Built once per batch (rebuilt
+// when the autotuner's table changes); a failure leaves the host loop in use.
+int build_pcg_graph(tfde_batch* B) {
+    if (B->pcg_exec && B->pcg_tune_gen != tc::tune_generation()) {
+        cudaGraphExecDestroy(B->pcg_exec);
+        cudaGraphDestroy(B->pcg_graph);
+        B->pcg_exec = nullptr;
+        B->pcg_graph = nullptr;
+    }
+    if (B->pcg_exec || B->pcg_failed) return TFDE_OK;
+    if (int st = tc::set_attrs()) return st;
+    const int C = B->count;
+    const int gb = (C + 63) / 64;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+    cudaGraphConditionalHandle h{};
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    if (ok) ok = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+    }
+    if (ok) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        // captured on a stream of its own (the caller's may be the legacy default stream)
+        const cudaStream_t s = capture_stream();
+        ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+             cudaSuccess;
+        if (ok) {
+            stats_set_capturing(true);
+            int st = TFDE_OK;
+            for (int a = 0; a < 2 && !st; ++a)
+                st = grouped(B, B->d_sop + (size_t)a * C, a, tc::OUT_SUM, B->sop_bytes[a], B->sop_flops[a], s);
+            if (!st) st = grouped(B, B->d_sopq, 2, tc::OUT_SUM, B->sopq_bytes, B->sopq_flops, s);
+            if (!st) {
+                bkp_update<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, B->d_s);
+                bkpg_stop<<<gb, 64, 0, s>>>(C, B->d_j, kPcgMaxIt, B->d_s, B->d_theta, B->d_act, B->d_its, B->d_est,
+                                            B->d_cnt, B->d_bad);
+                bkp_direction<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, B->d_s);
+                bkg_next<<<1, 1, 0, s>>>(B->d_j, B->d_cnt, kPcgMaxIt, h);
+            }
+            stats_set_capturing(false);
+            cudaGraph_t out = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(s, &out);
+            ok = st == TFDE_OK && e == cudaSuccess;
+        }
+    }
+    if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        B->pcg_failed = true;
+        tfde::set_error(TFDE_OK, "");
+        return TFDE_OK;
+    }
+    B->pcg_graph = g;
+    B->pcg_exec = ex;
+    B->pcg_tune_gen = tc::tune_generation();
+    return TFDE_OK;
+}
+
 // dots <V_{p0+j}, V_jw>, j < m, of every active problem into out (stride, offset)
 void bdots(tfde_batch* B, int p0, int m, int jw, double* out, int ostride, int ooff, cudaStream_t s) {
     for (int m0 = p0; m0 < p0 + m; m0 += 8) {
@@ -1059,9 +1151,18 @@ int batch_pcg(tfde_batch* B, const std::vector<int>& outer, const std::vector<do
     bkp_first<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, B->d_s);
     vec_launch_count();
     bkp_start<<<gb, 64, 0, s>>>(C, B->d_s, B->d_act, B->d_its, B->d_est, B->d_cnt, B->d_bad);
-    B_TRY(cudaMemcpyAsync(B->h_cnt, B->d_cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
-    B_TRY(cudaEventRecord(B->cnt_ev[0], s));
-    for (int j = 0; j < kPcgMaxIt; ++j) {
+    const bool graph = B->device_loop && !stats_timing();
+    if (graph && (st = build_pcg_graph(B))) return st;
+    if (graph && B->pcg_exec) {
+        // every iteration on the device: one graph launch for the solve
+        B_TRY(cudaMemsetAsync(B->d_j, 0, sizeof(int), s));
+        B_TRY(cudaGraphLaunch(B->pcg_exec, s));
+        ++B->pcg_graph_launches;
+    } else {
+        B_TRY(cudaMemcpyAsync(B->h_cnt, B->d_cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+        B_TRY(cudaEventRecord(B->cnt_ev[0], s));
+    }
+    for (int j = 0; j < kPcgMaxIt && !(graph && B->pcg_exec); ++j) {
         // stop issuing once no problem is left: the count after iteration j - 1
         // if it is already in, else the one after iteration j - 2
         if (cudaEventQuery(B->cnt_ev[j]) == cudaSuccess) {
@@ -1098,6 +1199,7 @@ int batch_pcg(tfde_batch* B, const std::vector<int>& outer, const std::vector<do
         kmax = std::max(kmax, its[i]);
         if (outer[i]) ++B->pcg_solves;
     }
+    if (graph && B->pcg_exec) stats_count_launch(7u * (unsigned)(kmax > 0 ? kmax : 1));   // per body: 3 grouped + 4
     if (kmax > 0) {   // x32 = S_N x~ (a problem without iterations keeps x32 = 0)
         for (int i = 0; i < C; ++i) B->h_act[i] = outer[i] && its[i] > 0;
         B_TRY(cudaMemcpyAsync(B->d_act, B->h_act, C * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -1398,6 +1500,8 @@ extern "C" int tfde_batch_set_symmetric_pcg(tfde_batch* B, int enable) {
 }
 
 extern "C" long long tfde_batch_pcg_solves(const tfde_batch* B) { return B ? B->pcg_solves : 0; }
+
+extern "C" long long tfde_batch_pcg_graph_launches(const tfde_batch* B) { return B ? B->pcg_graph_launches : 0; }
 
 extern "C" int tfde_batch_set_guess_order(tfde_batch* B, int order) {
     if (!B) return tfde::set_error(TFDE_EINVAL, "NULL batch");

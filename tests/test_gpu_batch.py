@@ -328,3 +328,33 @@ def test_batch_symmetric_pcg_chained_steps_and_toggle(T):
     finally:
         for h in singles:
             T.tfde_destroy(h)
+
+
+def test_batch_pcg_graph_and_host_loop_agree(T):
+    """The batched PCG iterations as one graph launch per sweep (iteration
+    index, stop tests and loop condition on the device) and driven from the
+    host (while every tensor-core launch is timed): the same iteration counts
+    and, up to the order of the atomic inner-product sums, the same
+    solutions, both matching the oracle's PCG."""
+    probs = symmetric_batch(4, 37, sizes=(8, 16, 24, 32))
+    dt = 0.1
+    params = [T.make_params(p["n"], p["delta"], p["kp"], p["km"], dt) for p in probs]
+    u0 = [inp.smoothed_uniform(tuple(reversed(p["n"])), 100 + i) for i, p in enumerate(probs)]
+    runs = {}
+    for timed in (False, True):
+        B = T.tfde_batch_create(params, 20)
+        try:
+            T.tfde_stats_reset(time_tc=timed)
+            us = [to_dev(u) for u in u0]
+            infos = T.tfde_batch_cn_advance(B, us, None, True, 1e-12)
+            runs[timed] = ([i.iters for i in infos], [to_host(u) for u in us])
+            launches = T.tfde_batch_pcg_graph_launches(B)
+            sweeps = max(i.refine_sweeps for i in infos)
+            assert (launches == 0) if timed else (launches == sweeps > 0), (timed, launches, sweeps)
+        finally:
+            T.tfde_stats_reset(time_tc=False)
+            T.tfde_batch_destroy(B)
+    assert runs[False][0] == runs[True][0]
+    for i, p in enumerate(probs):
+        xo = oracle_step(p, u0[i], dt)
+        assert relerr(runs[False][1][i], xo) < 1e-10 and relerr(runs[True][1][i], xo) < 1e-10, i
