@@ -214,8 +214,9 @@ int tfde_cn_advance_guess(const tfde_problem* prob, double* u, const double* F_h
  *   costs one fused vector pass.  Order 3: the order-2 guess plus
  *   c1 (u^{m-1} - u^{m-2}) + c2 (u^{m-1} - 2u^{m-2} + u^{m-3}), with (c1, c2)
  *   minimising the 2-norm of the initial residual over that plane, from five
- *   sums over the stored A u (one more read-only vector pass and one 40-byte
- *   device-to-host read per step; the polynomial coefficients do not follow
+ *   sums over the stored A u (one more read-only vector pass; the 2 x 2
+ *   system is solved on the device, no host read; the polynomial
+ *   coefficients do not follow
  *   the CN transient of the stiff modes, and at the n = 256 workload the
  *   correction lowers the initial residual ~40-fold).  The order in force is
  *   limited by the history the chain has built since its last restart (0 on
@@ -340,8 +341,7 @@ int tfde_batch_count(const tfde_batch* batch);
 /*
  * tfde_batch_set_guess_order -- the initial guess of tfde_batch_cn_advance's
  *   chained steps for every problem of the batch, as tfde_set_guess_order
- *   (orders 0..3, 0 by default; each problem keeps its own history, and
- *   order 3 reads its correction sums back once per problem and step).
+ *   (orders 0..3, 0 by default; each problem keeps its own history).
  *   Errors: TFDE_EINVAL for a NULL batch or an order outside 0..3.
  */
 int tfde_batch_set_guess_order(tfde_batch* batch, int order);

@@ -40,7 +40,7 @@ constexpr int kStreams = 8;    // stream pool of the per-problem work
 constexpr int kPcgMaxIt = 100; // inner PCG iterations per refinement sweep at most
 // scalar slots (S_RZ .. S_BETA: the batched inner PCG)
 enum { S_SC32 = 0, S_SPLIT = 1, S_ADD = 2, S_BB = 3, S_RR = 4, S_WW = 5, S_RZ = 6, S_RZN = 7, S_PQ = 8, S_RR0 = 9,
-       S_BETA = 10 };
+       S_BETA = 10, S_PRR = 11 };
 
 // Per-problem vector pointers of the batched kernels.
 struct BVec {
@@ -63,6 +63,7 @@ struct BVec {
     const float* lam;
     unsigned nc4;        // n1 n2 / 4
     int n3;
+    const double* norms; // ||b||^2, ||r_0||^2 of the problem's last cn_prepare
 };
 
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
@@ -228,6 +229,14 @@ __device__ __forceinline__ void ksum4(KSum& k, float4 a, float4 b) {
     k.add(a.w * b.w);
 }
 
+// S_BB, S_RR of every problem from the norms its cn_prepare formed
+__global__ void bk_gather_norms(int C, const BVec* __restrict__ vt, double* __restrict__ s) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C) return;
+    s[i * kSS + S_BB] = vt[i].norms[0];
+    s[i * kSS + S_RR] = vt[i].norms[1];
+}
+
 // zero the sums of a new inner solve
 __global__ void bkp_reset(int C, double* __restrict__ s, const int* __restrict__ act) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -263,7 +272,7 @@ __global__ __launch_bounds__(kBT) void bkp_first(const BVec* __restrict__ vt, co
 }
 
 // alpha = S_RZ / S_PQ; x~ += alpha p; r~ -= alpha q; S_RZN += <r~, Lambda^{-1} r~>,
-// S_RR += <r~, r~>
+// S_PRR += <r~, r~>
 __global__ __launch_bounds__(kBT) void bkp_update(const BVec* __restrict__ vt, const int* __restrict__ bi,
                                                  const long long* __restrict__ bo, const int* __restrict__ act,
                                                  double* __restrict__ s) {
@@ -296,7 +305,7 @@ __global__ __launch_bounds__(kBT) void bkp_update(const BVec* __restrict__ vt, c
     const double tr = block_sum((double)kr.s - (double)kr.c);
     if (threadIdx.x == 0) {
         atomicAdd(s + inst * kSS + S_RZN, tz);
-        atomicAdd(s + inst * kSS + S_RR, tr);
+        atomicAdd(s + inst * kSS + S_PRR, tr);
     }
 }
 
@@ -561,7 +570,7 @@ __global__ void bkp_start(int C, double* __restrict__ s, int* __restrict__ act, 
     }
     si[S_PQ] = 0.0;
     si[S_RZN] = 0.0;
-    si[S_RR] = 0.0;
+    si[S_PRR] = 0.0;
     atomicAdd(cnt, 1);
 }
 
@@ -576,7 +585,7 @@ __device__ __forceinline__ void bkp_stop_body(int C, int j, int maxit, double* _
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= C || !act[i]) return;
     double* si = s + (size_t)i * kSS;
-    const double rr = si[S_RR], rr0 = si[S_RR0];
+    const double rr = si[S_PRR], rr0 = si[S_RR0];
     its[i] = j + 1;
     est[i] = sqrt(rr / rr0);
     if (!isfinite(rr) || !isfinite(si[S_RZN]) || !isfinite(si[S_PQ])) {
@@ -591,7 +600,7 @@ __device__ __forceinline__ void bkp_stop_body(int C, int j, int maxit, double* _
     si[S_BETA] = si[S_RZN] / si[S_RZ];
     si[S_RZ] = si[S_RZN];
     si[S_RZN] = 0.0;
-    si[S_RR] = 0.0;
+    si[S_PRR] = 0.0;
     si[S_PQ] = 0.0;
     atomicAdd(cnt, 1);
 }
@@ -1208,25 +1217,6 @@ int batch_pcg(tfde_batch* B, const std::vector<int>& outer, const std::vector<do
     return TFDE_OK;
 }
 
-// FP64 norms of W_B and W_R of every problem with act set, into S_BB / S_RR.
-void batch_norms(tfde_batch* B, const std::vector<int>& act, bool with_b, cudaStream_t s) {
-    fork(B, s);
-    for (int i = 0; i < B->count; ++i) {
-        if (!act[i]) continue;
-        tfde_problem* P = B->P[i];
-        cudaStream_t a = B->aux[i % kStreams];
-        const double* b = P->w[tfde_problem::W_B];
-        const double* r = P->w[tfde_problem::W_R];
-        if (with_b) {
-            launch_multidot_f64(P->N, 1, b, 0, b, P->red, P->nblk, a);
-            launch_reduce_finish(P->red, P->nblk, 1, B->d_s + i * kSS + S_BB, a);
-        }
-        launch_multidot_f64(P->N, 1, r, 0, r, P->red, P->nblk, a);
-        launch_reduce_finish(P->red, P->nblk, 1, B->d_s + i * kSS + S_RR, a);
-    }
-    join(B, s);
-}
-
 }  // namespace
 
 int batch_create(const tfde_params* params, int count, int restart, cudaStream_t s, tfde_batch** out) {
@@ -1406,6 +1396,7 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
         v.lam = M->lam;
         v.nc4 = (unsigned)((long long)P->n[0] * P->n[1] / 4);
         v.n3 = P->n[2];
+        v.norms = P->red_out + kNormsSlot;
     }
     // the batched PCG's descriptors (the z pass adds <p, q> into the problem's S_PQ)
     std::vector<tc::Params> sfp(3 * C), sopq(C);
@@ -1543,8 +1534,9 @@ int batch_cn_advance(tfde_batch* B, double* const* u, const double* const* F, in
         }
     }
     join(B, s);
-    std::vector<int> all(C, 1);
-    batch_norms(B, all, true, s);
+    // ||b||^2 and ||r_0||^2 as every cn_prepare formed them, into S_BB / S_RR
+    vec_launch_count();
+    bk_gather_norms<<<(C + 63) / 64, 64, 0, s>>>(C, B->d_vt, B->d_s);
     if ((st = read_back(B, s))) return st;
     std::vector<double> nb(C), nr(C), ratio(C, 1.0), theta(C), est(C);
     std::vector<int> its(C), stall(C, 0), done(C, 0), outer(C, 0);
@@ -1615,24 +1607,30 @@ int batch_cn_advance(tfde_batch* B, double* const* u, const double* const* F, in
         B_TRY(cudaMemcpyAsync(B->d_act, B->h_act, C * sizeof(int), cudaMemcpyHostToDevice, s));
         stats_count_launch();
         bk_add32to64<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, B->d_s);
-        // accurate FP64 residuals r = b - A x
+        // accurate FP64 residuals r = b - A x, their norms (summed in the z pass
+        // under the scale 2^shift, shift = -ilogb ||b||, into S_RR) and A_N x
+        // (formed exactly in the z-pass slicing, for the next chained step)
+        std::vector<int> shift(C, 0);
         fork(B, s);
         for (int i = 0; i < C; ++i) {
             if (!outer[i]) continue;
             tfde_problem* P = B->P[i];
+            shift[i] = -std::ilogb(nb[i]);
+            P->an_ready = false;
             if ((st = accurate_apply_ex(P, TFDE_OP_A, uu[i], P->w[tfde_problem::W_R], -1, P->w[tfde_problem::W_B], 1.0,
-                                        B->aux[i % kStreams], oz_slices_for_tol(tol)))) {
+                                        B->aux[i % kStreams], oz_slices_for_tol(tol), B->d_s + i * kSS + S_RR,
+                                        shift[i], P->w[tfde_problem::W_T]))) {
                 join(B, s);
                 return st;
             }
+            P->an_ready = true;
         }
         join(B, s);
-        batch_norms(B, outer, false, s);
         if ((st = read_back(B, s))) return st;
         for (int i = 0; i < C; ++i) {
             if (!outer[i]) continue;
             const double nr_old = nr[i];
-            nr[i] = std::sqrt(B->h_s[i * kSS + S_RR]);
+            nr[i] = std::ldexp(std::sqrt(B->h_s[i * kSS + S_RR]), -shift[i]);
             info[i].iters += its[i];
             info[i].restarts++;
             info[i].refine_sweeps++;
@@ -1651,6 +1649,7 @@ int batch_cn_advance(tfde_batch* B, double* const* u, const double* const* F, in
                 tfde_problem* P = B->P[i];
                 tfde_info sub{};
                 info[i].fallback = 1;
+                P->an_ready = false;   // the FP64 cycles move x past the last exact residual
                 status[i] = (B->sym_pcg && B->spectral && P->symmetric)
                                 ? pcg64(P, P->w[tfde_problem::W_B], uu[i], tol, 10000, &sub, s, false)
                                 : pgmres64(P, P->w[tfde_problem::W_B], uu[i], B->restart, tol, 10000, &sub, s, false);

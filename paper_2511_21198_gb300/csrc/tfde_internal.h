@@ -84,7 +84,8 @@ void launch_cn_first(size_t N, const double* AN, const double* Ku, const double*
 void launch_cn_chain(size_t N, const double* AN, const double* F, double dt, double* b, double* r, double* part,
                      double* norms2, cudaStream_t s);
 // chained CN step with extrapolated initial guess written into u (see
-// tfde_kernels64.cu); order 3: x0 = g[0] u + g[1] U1 + g[2] U2 (order 2 when g is null)
+// tfde_kernels64.cu); order 3: x0 = g[0] u + g[1] U1 + g[2] U2 with g in DEVICE
+// memory (order 2 when g is null)
 void launch_cn_chain_extrap(size_t N, const double* AN, const double* F, double dt, double* b, double* r, double* u,
                             const double* U1, const double* AU1, double* U2, double* AU2, int order, const double* g,
                             double* part, double* norms2, cudaStream_t s);
@@ -92,6 +93,8 @@ void launch_cn_chain_extrap(size_t N, const double* AN, const double* F, double 
 // out5 (device): <e1,e1>, <e1,e2>, <e2,e2>, <e1,r_e>, <e2,r_e> (see tfde_kernels64.cu)
 void launch_cn_mr_dots(size_t N, const double* AN, const double* F, double dt, const double* b, const double* r,
                        const double* AU1, const double* AU2, double* part, double* out5, cudaStream_t s);
+// g3[0..2] = coefficients of the corrected guess from the five sums m5 (device, one thread)
+void launch_cn_mr_coefficients(const double* m5, double* g3, cudaStream_t s);
 // F = cP PPP + cS (SPP + PSP + PPS) from 1-D arrays [Px|Py|Pz|Sx|Sy|Sz]
 void launch_source_assemble_f64(const double* oned, const int n[3], double cP, double cS, double* F,
                                 cudaStream_t s);

@@ -436,7 +436,7 @@ __global__ void cn_chain_extrap_kernel(long long N, const double* __restrict__ A
                                        double dt, double* __restrict__ b, double* __restrict__ r,
                                        double* __restrict__ u, const double* __restrict__ U1,
                                        const double* __restrict__ AU1, double* __restrict__ U2,
-                                       double* __restrict__ AU2, int order, double g0, double g1, double g2,
+                                       double* __restrict__ AU2, int order, const double* __restrict__ g,
                                        double* __restrict__ part) {
     // GB300 issues FP64 at ~1/64 of its FP32 rate and this pass moves 112
     // bytes per point: it is FP64-bound unless every FP64 operation that is
@@ -445,6 +445,12 @@ __global__ void cn_chain_extrap_kernel(long long N, const double* __restrict__ A
     // threshold and the first sweep's scale) are summed in FP32 from values
     // truncated by integer operations: 10 FP64 operations per point instead of 13.
     float bb = 0.f, rr = 0.f;
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0;   // order 3: the corrected guess's coefficients (device)
+    if (order >= 3) {
+        g0 = g[0];
+        g1 = g[1];
+        g2 = g[2];
+    }
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const double ui = u[i];
         const double au = b[i] - r[i];
@@ -519,6 +525,27 @@ __global__ void cn_mr_dots_kernel(long long N, const double* __restrict__ AN, co
         const double t = block_sum((double)s[q]);
         if (threadIdx.x == 0) part[(long long)q * gridDim.x + blockIdx.x] = t;
     }
+}
+
+// Coefficients g of the corrected guess x0 = g0 u^{m-1} + g1 u^{m-2} +
+// g2 u^{m-3} from the five sums m of cn_mr_dots_kernel (one thread): the
+// order-2 extrapolation 3, -3, 1 plus c1 d1 + c2 d2 (d1 = u^{m-1} - u^{m-2},
+// d2 = u^{m-1} - 2 u^{m-2} + u^{m-3}), c solving the 2 x 2 normal equations
+// [m0 m1; m1 m2] c = [m3; m4].  An ill-conditioned or non-finite system, or
+// |c| > 1e3, leaves c = 0.
+__global__ void cn_mr_coef_kernel(const double* __restrict__ m, double* __restrict__ g) {
+    double c1 = 0.0, c2 = 0.0;
+    bool ok = true;
+    for (int q = 0; q < 5; ++q) ok = ok && isfinite(m[q]);
+    const double det = m[0] * m[2] - m[1] * m[1];
+    if (ok && m[0] > 0.0 && m[2] > 0.0 && det > 1e-12 * m[0] * m[2]) {
+        c1 = (m[2] * m[3] - m[1] * m[4]) / det;
+        c2 = (m[0] * m[4] - m[1] * m[3]) / det;
+        if (!isfinite(c1) || !isfinite(c2) || fabs(c1) > 1e3 || fabs(c2) > 1e3) c1 = c2 = 0.0;
+    }
+    g[0] = 3.0 + c1 + c2;
+    g[1] = -3.0 - c1 - 2.0 * c2;
+    g[2] = 1.0 + c2;
 }
 
 inline int grid_for(long long N) {
@@ -640,10 +667,8 @@ void launch_cn_chain_extrap(size_t N, const double* AN, const double* F, double 
                             double* part, double* norms2, cudaStream_t s) {
     stats_count_launch();
     const int grid = grid_for((long long)N);
-    const double g0 = g ? g[0] : 0.0, g1 = g ? g[1] : 0.0, g2 = g ? g[2] : 0.0;
     cn_chain_extrap_kernel<<<grid, kThreads, 0, s>>>((long long)N, AN, F, dt, b, r, u, U1, AU1, U2, AU2,
-                                                     order >= 3 && !g ? 2 : order, g0, g1, g2,
-                                                     norms2 ? part : nullptr);
+                                                     order >= 3 && !g ? 2 : order, g, norms2 ? part : nullptr);
     finish_norms(part, grid, norms2, s);
 }
 
@@ -653,6 +678,11 @@ void launch_cn_mr_dots(size_t N, const double* AN, const double* F, double dt, c
     const int grid = grid_for((long long)N);
     cn_mr_dots_kernel<<<grid, kThreads, 0, s>>>((long long)N, AN, F, (float)dt, b, r, AU1, AU2, part);
     launch_reduce_finish(part, grid, 5, out5, s);
+}
+
+void launch_cn_mr_coefficients(const double* m5, double* g3, cudaStream_t s) {
+    stats_count_launch();
+    cn_mr_coef_kernel<<<1, 1, 0, s>>>(m5, g3);
 }
 
 void launch_source_assemble_f64(const double* oned, const int n[3], double cP, double cS, double* F,

@@ -332,33 +332,17 @@ static void mass_apply(const tfde_problem* P, const double* u, double* out, cuda
 }
 
 // Coefficients g of the corrected guess x0 = g0 u^{m-1} + g1 u^{m-2} +
-// g2 u^{m-3}: the order-2 extrapolation x_e = 3 u^{m-1} - 3 u^{m-2} + u^{m-3}
-// plus c1 d1 + c2 d2 (d1 = u^{m-1} - u^{m-2}, d2 = u^{m-1} - 2 u^{m-2} +
-// u^{m-3}), c minimising the residual ||r_e - c1 A d1 - c2 A d2|| over the
-// stored A u of the history (normal equations of the five sums of
-// cn_mr_dots_kernel).  The polynomial coefficients are not optimal for the
-// CN transient of the stiff modes; the correction uses no operator
-// application.  An ill-conditioned or non-finite system leaves c = 0.
-static int mr_guess_coefficients(tfde_problem* P, const double* an, const double* F, const double* b,
-                                 const double* r, double g[3], cudaStream_t s) {
+// g2 u^{m-3}, into g (device): the order-2 extrapolation x_e = 3 u^{m-1} -
+// 3 u^{m-2} + u^{m-3} plus c1 d1 + c2 d2 (d1 = u^{m-1} - u^{m-2}, d2 =
+// u^{m-1} - 2 u^{m-2} + u^{m-3}), c minimising the residual ||r_e - c1 A d1 -
+// c2 A d2|| over the stored A u of the history (normal equations of the five
+// sums of cn_mr_dots_kernel, solved by one device thread: no host read).  The
+// polynomial coefficients are not optimal for the CN transient of the stiff
+// modes; the correction uses no operator application.
+static void mr_guess_coefficients(tfde_problem* P, const double* an, const double* F, const double* b,
+                                  const double* r, double* g, cudaStream_t s) {
     launch_cn_mr_dots(P->N, an, F, P->p.dt, b, r, P->H[0][1], P->H[1][1], P->red, P->red_out + kMrSlot, s);
-    TFDE_CUDA_TRY(cudaMemcpyAsync(P->red_host + kMrSlot, P->red_out + kMrSlot, 5 * sizeof(double),
-                                  cudaMemcpyDeviceToHost, s));
-    TFDE_CUDA_TRY(cudaStreamSynchronize(s));
-    const double* m = P->red_host + kMrSlot;   // <e1,e1>, <e1,e2>, <e2,e2>, <e1,r_e>, <e2,r_e>
-    const double det = m[0] * m[2] - m[1] * m[1];
-    double c1 = 0.0, c2 = 0.0;
-    bool ok = true;
-    for (int q = 0; q < 5; ++q) ok = ok && std::isfinite(m[q]);
-    if (ok && m[0] > 0.0 && m[2] > 0.0 && det > 1e-12 * m[0] * m[2]) {
-        c1 = (m[2] * m[3] - m[1] * m[4]) / det;
-        c2 = (m[0] * m[4] - m[1] * m[3]) / det;
-        if (!std::isfinite(c1) || !std::isfinite(c2) || std::fabs(c1) > 1e3 || std::fabs(c2) > 1e3) c1 = c2 = 0.0;
-    }
-    g[0] = 3.0 + c1 + c2;
-    g[1] = -3.0 - c1 - 2.0 * c2;
-    g[2] = 1.0 + c2;
-    return TFDE_OK;
+    launch_cn_mr_coefficients(P->red_out + kMrSlot, g, s);
 }
 
 // One CN step (Eq. (CN), Eq. (linear_sys)) for either precision.  `chained`:
@@ -384,11 +368,10 @@ int cn_prepare(tfde_problem* P, const double* u_prev, const double* F, const dou
     if (chained && P->guess_order > 0 && u_next == u_prev && !guess) {
         if ((st = ensure_history(P))) return st;   // allocated when the order was set
         const int order = P->guess_order < P->hist ? P->guess_order : P->hist;
-        double g[3];
-        const double* gp = nullptr;
+        double* gp = nullptr;   // device coefficients of the corrected guess
         if (P->guess_order >= 3 && P->hist >= 2) {
-            if ((st = mr_guess_coefficients(P, an, F, b, r, g, s))) return st;
-            gp = g;
+            gp = P->red_out + kMrSlot + 5;
+            mr_guess_coefficients(P, an, F, b, r, gp, s);
         }
         launch_cn_chain_extrap(P->N, an, F, P->p.dt, b, r, u_next, P->H[0][0], P->H[0][1], P->H[1][0], P->H[1][1],
                                gp ? 3 : std::min(order, 2), gp, P->red, P->red_out + kNormsSlot, s);
