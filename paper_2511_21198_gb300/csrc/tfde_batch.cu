@@ -710,6 +710,7 @@ struct tfde_batch {
     bool chain_ok = false;
     std::vector<double*> chain_u;
     std::vector<int*> own_err;      // each problem's own error flag while it reports to d_err
+    tfde::OzBatch* oz = nullptr;    // the exact residuals as grouped launches
 };
 
 namespace tfde {
@@ -740,6 +741,7 @@ int free_batch(tfde_batch* B) {
         if (i < B->own_err.size()) tfde::mixed(B->P[i])->err = B->own_err[i];
         destroy_problem(B->P[i]);
     }
+    tfde::oz_batch_destroy(B->oz);
     cudaFree(B->d_sopzw);
     cudaFree(B->d_j);
     if (B->cyc_exec) cudaGraphExecDestroy(B->cyc_exec);
@@ -1448,6 +1450,14 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
     }
     if (cudaEventCreateWithFlags(&B->fork_ev, cudaEventDisableTiming) != cudaSuccess)
         return fail(TFDE_ECUDA, "event creation failed");
+    {
+        std::vector<double*> norm2(C);
+        for (size_t i = 0; i < C; ++i) norm2[i] = B->d_s + i * kSS + S_RR;
+        if ((st = oz_batch_create(B->P.data(), count, norm2.data(), &B->oz))) {
+            free_batch(B);
+            return st;
+        }
+    }
     *out = B;
     return TFDE_OK;
 }
@@ -1607,25 +1617,22 @@ int batch_cn_advance(tfde_batch* B, double* const* u, const double* const* F, in
         B_TRY(cudaMemcpyAsync(B->d_act, B->h_act, C * sizeof(int), cudaMemcpyHostToDevice, s));
         stats_count_launch();
         bk_add32to64<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, B->d_s);
-        // accurate FP64 residuals r = b - A x, their norms (summed in the z pass
-        // under the scale 2^shift, shift = -ilogb ||b||, into S_RR) and A_N x
-        // (formed exactly in the z-pass slicing, for the next chained step)
+        // accurate FP64 residuals r = b - A x of every problem still refining,
+        // as three grouped slicing and three grouped exact-contraction launches,
+        // with their norms (summed in the z pass under the scale 2^shift, shift =
+        // -ilogb ||b||, into S_RR) and A_N x (formed exactly in the z-pass
+        // slicing, for the next chained step)
         std::vector<int> shift(C, 0);
-        fork(B, s);
+        std::vector<const double*> xs(uu.begin(), uu.end());
         for (int i = 0; i < C; ++i) {
             if (!outer[i]) continue;
-            tfde_problem* P = B->P[i];
+            B->P[i]->an_ready = false;
             shift[i] = -std::ilogb(nb[i]);
-            P->an_ready = false;
-            if ((st = accurate_apply_ex(P, TFDE_OP_A, uu[i], P->w[tfde_problem::W_R], -1, P->w[tfde_problem::W_B], 1.0,
-                                        B->aux[i % kStreams], oz_slices_for_tol(tol), B->d_s + i * kSS + S_RR,
-                                        shift[i], P->w[tfde_problem::W_T]))) {
-                join(B, s);
-                return st;
-            }
-            P->an_ready = true;
         }
-        join(B, s);
+        if ((st = oz_batch_residual(B->oz, xs.data(), outer.data(), B->d_act, shift.data(), oz_slices_for_tol(tol), s)))
+            return st;
+        for (int i = 0; i < C; ++i)
+            if (outer[i]) B->P[i]->an_ready = true;
         if ((st = read_back(B, s))) return st;
         for (int i = 0; i < C; ++i) {
             if (!outer[i]) continue;

@@ -249,6 +249,20 @@ int accurate_apply(const tfde_problem* P, int op, const double* x, double* y, cu
 int accurate_apply_ex(const tfde_problem* P, int op, const double* x, double* y, int vsign, const double* addend,
                       double asign, cudaStream_t s, int slices = OZ_SLICES, double* norm2 = nullptr,
                       int norm_shift = 0, double* an_out = nullptr);
+// Exact residuals of the problems of a batch as grouped launches (tfde_oz.cu).
+struct OzBatch;
+// norm2[i]: the device double that receives ||r_i||^2 (FP32 terms under the
+// call's scale) of problem i.
+int oz_batch_create(tfde_problem* const* P, int count, double* const* norm2, OzBatch** out);
+void oz_batch_destroy(OzBatch* ob);
+// For every problem i with act[i] != 0 (host copy act, device copy d_act):
+// r_i = b_i - A_i x_i into W_R, FP64-accurate at S digit slices, with
+// sum (r_i 2^shift[i])^2 (FP32 terms) into *norm2[i] and A_N x_i into W_T
+// (the next chained step's mass term): three grouped slicing and three
+// grouped exact-contraction launches over all problems' lines and tiles.
+int oz_batch_residual(OzBatch* ob, const double* const* x, const int* act, const int* d_act, const int* shift, int S,
+                      cudaStream_t s);
+
 // Digit slices for a refinement residual at relative tolerance tol: 6 (42
 // bits, a worst-case error n 2^-42 < 1.1e-10 of |A||x| for n <= 448) while
 // tol >= 1e-9, else 7.

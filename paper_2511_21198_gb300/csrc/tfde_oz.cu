@@ -118,64 +118,69 @@ __device__ __forceinline__ double i64_ldexp_exact(long long Y, int s) {
 // (w_k = (X_{k-1} + 6 X_k + X_{k+1}) 2^{E - 7S - 3}, |sum| < 2^53: exact).
 // S (digits) is a template argument: every digit shift is a constant.
 template <int S>
+__device__ __forceinline__ void slice_x_line(const double* __restrict__ x0, int n1, __nv_bfloat16* __restrict__ p0,
+                                             long long N, int* __restrict__ lexp, double* __restrict__ wout, long long l,
+                                             int lane) {
+    const longlong2* r2 = reinterpret_cast<const longlong2*>(x0 + l * n1);   // n1 even: pairs stay in the line
+    const int np = n1 / 2;
+    uint32_t hmax = 0, lor = 0;
+#pragma unroll 4
+    for (int q = lane; q < np; q += 32) {
+        const longlong2 v = r2[q];
+        hmax = max(hmax, max((uint32_t)((unsigned long long)v.x >> 32) & 0x7FFFFFFFu,
+                             (uint32_t)((unsigned long long)v.y >> 32) & 0x7FFFFFFFu));
+        lor |= (uint32_t)v.x | (uint32_t)v.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        hmax = max(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+        lor |= __shfl_xor_sync(0xffffffffu, lor, o);
+    }
+    const int E = line_exponent(hmax, lor);
+    long long left_carry = 0;   // X just before this iteration's first point
+    long long Xa = 0, Xb = 0;
+    if (lane < np) {
+        const longlong2 v = r2[lane];
+        Xa = fixed_point<S>(v.x, E);
+        Xb = fixed_point<S>(v.y, E);
+    }
+    for (int base = 0; base < np; base += 32) {
+        const int q = base + lane;
+        const int qn = q + 32;
+        long long Na = 0, Nb = 0;
+        if (qn < np) {
+            const longlong2 v = r2[qn];
+            Na = fixed_point<S>(v.x, E);
+            Nb = fixed_point<S>(v.y, E);
+        }
+        if (q < np) write_digits2<S>(Xa, Xb, p0, N, l * n1 + 2 * q);
+        if (wout) {
+            long long left = __shfl_up_sync(0xffffffffu, Xb, 1);
+            long long right = __shfl_down_sync(0xffffffffu, Xa, 1);
+            const long long first_next = __shfl_sync(0xffffffffu, Na, 0);
+            if (lane == 0) left = left_carry;
+            if (lane == 31) right = first_next;
+            if (q < np) {
+                const int sc = E - 7 * S - 3;
+                *reinterpret_cast<double2*>(wout + l * n1 + 2 * q) =
+                    make_double2(i64_ldexp_exact(left + 6 * Xa + Xb, sc), i64_ldexp_exact(Xa + 6 * Xb + right, sc));
+            }
+            left_carry = __shfl_sync(0xffffffffu, Xb, 31);
+        }
+        Xa = Na;
+        Xb = Nb;
+    }
+    if (lane == 0) lexp[l] = E;
+}
+
+template <int S>
 __global__ void slice_x_kernel(const double* __restrict__ x0, int n1, long long lines,
                                __nv_bfloat16* __restrict__ p0, long long N, int* __restrict__ lexp,
                                double* __restrict__ wout) {
     const int lane = threadIdx.x & 31;
     const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long l = wg; l < lines; l += nw) {
-        const longlong2* r2 = reinterpret_cast<const longlong2*>(x0 + l * n1);   // n1 even: pairs stay in the line
-        const int np = n1 / 2;
-        uint32_t hmax = 0, lor = 0;
-#pragma unroll 4
-        for (int q = lane; q < np; q += 32) {
-            const longlong2 v = r2[q];
-            hmax = max(hmax, max((uint32_t)((unsigned long long)v.x >> 32) & 0x7FFFFFFFu,
-                                 (uint32_t)((unsigned long long)v.y >> 32) & 0x7FFFFFFFu));
-            lor |= (uint32_t)v.x | (uint32_t)v.y;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            hmax = max(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
-            lor |= __shfl_xor_sync(0xffffffffu, lor, o);
-        }
-        const int E = line_exponent(hmax, lor);
-        long long left_carry = 0;   // X just before this iteration's first point
-        long long Xa = 0, Xb = 0;
-        if (lane < np) {
-            const longlong2 v = r2[lane];
-            Xa = fixed_point<S>(v.x, E);
-            Xb = fixed_point<S>(v.y, E);
-        }
-        for (int base = 0; base < np; base += 32) {
-            const int q = base + lane;
-            const int qn = q + 32;
-            long long Na = 0, Nb = 0;
-            if (qn < np) {
-                const longlong2 v = r2[qn];
-                Na = fixed_point<S>(v.x, E);
-                Nb = fixed_point<S>(v.y, E);
-            }
-            if (q < np) write_digits2<S>(Xa, Xb, p0, N, l * n1 + 2 * q);
-            if (wout) {
-                long long left = __shfl_up_sync(0xffffffffu, Xb, 1);
-                long long right = __shfl_down_sync(0xffffffffu, Xa, 1);
-                const long long first_next = __shfl_sync(0xffffffffu, Na, 0);
-                if (lane == 0) left = left_carry;
-                if (lane == 31) right = first_next;
-                if (q < np) {
-                    const int sc = E - 7 * S - 3;
-                    *reinterpret_cast<double2*>(wout + l * n1 + 2 * q) =
-                        make_double2(i64_ldexp_exact(left + 6 * Xa + Xb, sc), i64_ldexp_exact(Xa + 6 * Xb + right, sc));
-                }
-                left_carry = __shfl_sync(0xffffffffu, Xb, 31);
-            }
-            Xa = Na;
-            Xb = Nb;
-        }
-        if (lane == 0) lexp[l] = E;
-    }
+    for (long long l = wg; l < lines; l += nw) slice_x_line<S>(x0, n1, p0, N, lexp, wout, l, lane);
 }
 
 // y / z axes: LB consecutive lines (contiguous in memory) per 512-thread
@@ -193,106 +198,177 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
                  : "memory");
 }
 
+// One group of LB lines starting at line l0 of slice_staged_kernel (the whole
+// block; s0 / s1 the staged lines of the two inputs in shared memory).
+template <int LB, int S>
+__device__ __forceinline__ void slice_staged_group(const double* __restrict__ x0, const double* __restrict__ x1,
+                                                   int sh1, const AxisView& v, __nv_bfloat16* __restrict__ p0,
+                                                   __nv_bfloat16* __restrict__ p1, long long N,
+                                                   int* __restrict__ lexp, double* __restrict__ eout, long long l0,
+                                                   unsigned long long* s0, unsigned long long* s1,
+                                                   uint32_t (*shmax)[LB], uint32_t (*slor)[LB], int* sexp) {
+    constexpr int LP = LB / 2;               // line pairs per block
+    constexpr int NKG = SL_THREADS / LP;     // k rows in flight
+    const int lp = threadIdx.x % LP, kg = threadIdx.x / LP;
+    const int la = 2 * lp;                   // first line of the pair within the block
+    const long long* b0 = reinterpret_cast<const long long*>(x0);
+    const long long* b1 = reinterpret_cast<const long long*>(x1);
+    const long long l = l0 + la;          // lines l, l + 1 (same run: runs hold a multiple of 8 lines)
+    const bool valid = l < v.lines;
+    const long long off = valid ? (l % v.l_in) * v.s_in + (l / v.l_in) * v.s_out : 0;
+    if (valid) {
+        for (int k = kg; k < v.n; k += NKG) {
+            const long long idx = off + (long long)k * v.stride;
+            cp_async16(s0 + k * LB + la, b0 + idx);
+            if (b1) cp_async16(s1 + k * LB + la, b1 + idx);
+        }
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    uint32_t ha = 0, hb = 0, oa = 0, ob = 0;
+    if (valid) {
+        for (int k = kg; k < v.n; k += NKG) {
+            const unsigned long long wa = s0[k * LB + la], wb = s0[k * LB + la + 1];
+            ha = max(ha, (uint32_t)(wa >> 32) & 0x7FFFFFFFu);
+            hb = max(hb, (uint32_t)(wb >> 32) & 0x7FFFFFFFu);
+            oa |= (uint32_t)wa;
+            ob |= (uint32_t)wb;
+            if (b1) {
+                const unsigned long long ua = s1[k * LB + la], ub = s1[k * LB + la + 1];
+                ha = max(ha, abs_hi_shifted(ua, sh1));
+                hb = max(hb, abs_hi_shifted(ub, sh1));
+                oa |= (uint32_t)ua;
+                ob |= (uint32_t)ub;
+            }
+        }
+    }
+    shmax[kg][la] = ha;
+    shmax[kg][la + 1] = hb;
+    slor[kg][la] = oa;
+    slor[kg][la + 1] = ob;
+    __syncthreads();
+    if (threadIdx.x < LB) {
+        uint32_t m = shmax[0][threadIdx.x], o = slor[0][threadIdx.x];
+#pragma unroll 8
+        for (int g = 1; g < NKG; ++g) {
+            m = max(m, shmax[g][threadIdx.x]);
+            o |= slor[g][threadIdx.x];
+        }
+        const int E = line_exponent(m, o);
+        sexp[threadIdx.x] = E;
+        if (l0 + threadIdx.x < v.lines) lexp[l0 + threadIdx.x] = E;
+    }
+    __syncthreads();
+    const int Ea = sexp[la], Eb = sexp[la + 1];
+    if (valid) {
+        for (int k = kg; k < v.n; k += NKG) {
+            const long long idx = off + (long long)k * v.stride;
+            write_digits2<S>(fixed_point<S>((long long)s0[k * LB + la], Ea),
+                             fixed_point<S>((long long)s0[k * LB + la + 1], Eb), p0, N, idx);
+            if (b1) {
+                const long long Wa = fixed_point<S>((long long)s1[k * LB + la], Ea - sh1);
+                const long long Wb = fixed_point<S>((long long)s1[k * LB + la + 1], Eb - sh1);
+                write_digits2<S>(Wa, Wb, p1, N, idx);
+                if (eout) {
+                    s1[k * LB + la] = (unsigned long long)Wa;
+                    s1[k * LB + la + 1] = (unsigned long long)Wb;
+                }
+            }
+        }
+    }
+    if (eout && b1) {
+        __syncthreads();
+        if (valid) {
+            for (int k = kg; k < v.n; k += NKG) {
+                double e2[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int c = la + q;
+                    const long long Wp = k > 0 ? (long long)s1[(k - 1) * LB + c] : 0;
+                    const long long Wn = k + 1 < v.n ? (long long)s1[(k + 1) * LB + c] : 0;
+                    const long long W = (long long)s1[k * LB + c];
+                    e2[q] = i64_ldexp_exact(Wp + 6 * W + Wn, (q ? Eb : Ea) - sh1 - 7 * S - 3);
+                }
+                *reinterpret_cast<double2*>(eout + off + (long long)k * v.stride) = make_double2(e2[0], e2[1]);
+            }
+        }
+    }
+    __syncthreads();
+}
+
 template <int LB, int S>
 __global__ __launch_bounds__(SL_THREADS) void slice_staged_kernel(const double* __restrict__ x0,
                                                                   const double* __restrict__ x1, int sh1, AxisView v,
                                                                   __nv_bfloat16* __restrict__ p0,
                                                                   __nv_bfloat16* __restrict__ p1, long long N,
                                                                   int* __restrict__ lexp, double* __restrict__ eout) {
-    constexpr int LP = LB / 2;               // line pairs per block
-    constexpr int NKG = SL_THREADS / LP;     // k rows in flight
+    constexpr int NKG = SL_THREADS / (LB / 2);
     extern __shared__ unsigned long long sl_smem[];   // [input][k][LB]
     __shared__ uint32_t shmax[NKG][LB];
     __shared__ uint32_t slor[NKG][LB];
     __shared__ int sexp[LB];
-    unsigned long long* s0 = sl_smem;
-    unsigned long long* s1 = sl_smem + (size_t)v.n * LB;
-    const int lp = threadIdx.x % LP, kg = threadIdx.x / LP;
-    const int la = 2 * lp;                   // first line of the pair within the block
-    const long long* b0 = reinterpret_cast<const long long*>(x0);
-    const long long* b1 = reinterpret_cast<const long long*>(x1);
-    for (long long l0 = (long long)blockIdx.x * LB; l0 < v.lines; l0 += (long long)gridDim.x * LB) {
-        const long long l = l0 + la;          // lines l, l + 1 (same run: runs hold a multiple of 8 lines)
-        const bool valid = l < v.lines;
-        const long long off = valid ? (l % v.l_in) * v.s_in + (l / v.l_in) * v.s_out : 0;
-        if (valid) {
-            for (int k = kg; k < v.n; k += NKG) {
-                const long long idx = off + (long long)k * v.stride;
-                cp_async16(s0 + k * LB + la, b0 + idx);
-                if (b1) cp_async16(s1 + k * LB + la, b1 + idx);
-            }
-        }
-        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-        __syncthreads();
-        uint32_t ha = 0, hb = 0, oa = 0, ob = 0;
-        if (valid) {
-            for (int k = kg; k < v.n; k += NKG) {
-                const unsigned long long wa = s0[k * LB + la], wb = s0[k * LB + la + 1];
-                ha = max(ha, (uint32_t)(wa >> 32) & 0x7FFFFFFFu);
-                hb = max(hb, (uint32_t)(wb >> 32) & 0x7FFFFFFFu);
-                oa |= (uint32_t)wa;
-                ob |= (uint32_t)wb;
-                if (b1) {
-                    const unsigned long long ua = s1[k * LB + la], ub = s1[k * LB + la + 1];
-                    ha = max(ha, abs_hi_shifted(ua, sh1));
-                    hb = max(hb, abs_hi_shifted(ub, sh1));
-                    oa |= (uint32_t)ua;
-                    ob |= (uint32_t)ub;
-                }
-            }
-        }
-        shmax[kg][la] = ha;
-        shmax[kg][la + 1] = hb;
-        slor[kg][la] = oa;
-        slor[kg][la + 1] = ob;
-        __syncthreads();
-        if (threadIdx.x < LB) {
-            uint32_t m = shmax[0][threadIdx.x], o = slor[0][threadIdx.x];
-#pragma unroll 8
-            for (int g = 1; g < NKG; ++g) {
-                m = max(m, shmax[g][threadIdx.x]);
-                o |= slor[g][threadIdx.x];
-            }
-            const int E = line_exponent(m, o);
-            sexp[threadIdx.x] = E;
-            if (l0 + threadIdx.x < v.lines) lexp[l0 + threadIdx.x] = E;
-        }
-        __syncthreads();
-        const int Ea = sexp[la], Eb = sexp[la + 1];
-        if (valid) {
-            for (int k = kg; k < v.n; k += NKG) {
-                const long long idx = off + (long long)k * v.stride;
-                write_digits2<S>(fixed_point<S>((long long)s0[k * LB + la], Ea),
-                                 fixed_point<S>((long long)s0[k * LB + la + 1], Eb), p0, N, idx);
-                if (b1) {
-                    const long long Wa = fixed_point<S>((long long)s1[k * LB + la], Ea - sh1);
-                    const long long Wb = fixed_point<S>((long long)s1[k * LB + la + 1], Eb - sh1);
-                    write_digits2<S>(Wa, Wb, p1, N, idx);
-                    if (eout) {
-                        s1[k * LB + la] = (unsigned long long)Wa;
-                        s1[k * LB + la + 1] = (unsigned long long)Wb;
-                    }
-                }
-            }
-        }
-        if (eout && b1) {
-            __syncthreads();
-            if (valid) {
-                for (int k = kg; k < v.n; k += NKG) {
-                    double e2[2];
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const int c = la + q;
-                        const long long Wp = k > 0 ? (long long)s1[(k - 1) * LB + c] : 0;
-                        const long long Wn = k + 1 < v.n ? (long long)s1[(k + 1) * LB + c] : 0;
-                        const long long W = (long long)s1[k * LB + c];
-                        e2[q] = i64_ldexp_exact(Wp + 6 * W + Wn, (q ? Eb : Ea) - sh1 - 7 * S - 3);
-                    }
-                    *reinterpret_cast<double2*>(eout + off + (long long)k * v.stride) = make_double2(e2[0], e2[1]);
-                }
-            }
-        }
-        __syncthreads();
+    for (long long l0 = (long long)blockIdx.x * LB; l0 < v.lines; l0 += (long long)gridDim.x * LB)
+        slice_staged_group<LB, S>(x0, x1, sh1, v, p0, p1, N, lexp, eout, l0, sl_smem, sl_smem + (size_t)v.n * LB, shmax,
+                                  slor, sexp);
+}
+
+// ---- grouped slicing over the problems of a batch: every problem's lines
+// in one launch, the work items (x: lines, y / z: groups of LB lines) of
+// problem g at start[g] .. start[g + 1] - 1; problems with act[g] == 0 are
+// skipped.
+struct SliceDesc {
+    const double* x0;
+    const double* x1;
+    int sh1;
+    int n1;
+    AxisView v;
+    __nv_bfloat16* p0;
+    __nv_bfloat16* p1;
+    long long N;
+    int* lexp;
+    double* eout;
+};
+
+__device__ __forceinline__ int slice_find(const long long* __restrict__ start, int ng, long long t) {
+    int lo = 0, hi = ng - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(start + mid) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int S>
+__global__ void slice_x_grouped_kernel(const SliceDesc* __restrict__ d, const long long* __restrict__ start, int ng,
+                                       const int* __restrict__ act) {
+    const int lane = threadIdx.x & 31;
+    const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long total = __ldg(start + ng);
+    for (long long t = wg; t < total; t += nw) {   // warp-uniform
+        const int g = slice_find(start, ng, t);
+        if (!__ldg(act + g)) continue;
+        const SliceDesc& D = d[g];
+        slice_x_line<S>(D.x0, D.n1, D.p0, D.N, D.lexp, D.eout, t - __ldg(start + g), lane);
+    }
+}
+
+template <int LB, int S>
+__global__ __launch_bounds__(SL_THREADS) void slice_staged_grouped_kernel(const SliceDesc* __restrict__ d,
+                                                                          const long long* __restrict__ start, int ng,
+                                                                          const int* __restrict__ act) {
+    constexpr int NKG = SL_THREADS / (LB / 2);
+    extern __shared__ unsigned long long sl_smem[];   // [input][k][LB], sized for the longest lines
+    __shared__ uint32_t shmax[NKG][LB];
+    __shared__ uint32_t slor[NKG][LB];
+    __shared__ int sexp[LB];
+    const long long total = __ldg(start + ng);
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) {   // block-uniform
+        const int g = slice_find(start, ng, t);
+        if (!__ldg(act + g)) continue;
+        const SliceDesc& D = d[g];
+        slice_staged_group<LB, S>(D.x0, D.x1, D.sh1, D.v, D.p0, D.p1, D.N, D.lexp, D.eout, (t - __ldg(start + g)) * LB,
+                                  sl_smem, sl_smem + (size_t)D.v.n * LB, shmax, slor, sexp);
     }
 }
 
@@ -568,13 +644,14 @@ struct OzSegSpec {
     int input;  // digit planes 0 or 1
 };
 
-int oz_contract(const tfde_problem* P, int axis, const OzSegSpec* segs, int nseg, int vsign, const double* addend,
-                double asign, double* out, int S, cudaStream_t s, double* norm2 = nullptr, int norm_shift = 0) {
+// The descriptor of one exact contraction out = vsign * sum_seg Op_seg (planes
+// of input seg.input) [+ asign * addend] along `axis` at S slices; *pairs =
+// the digit products per grid point and input.
+void oz_params(const tfde_problem* P, int axis, const OzSegSpec* segs, int nseg, int vsign, const double* addend,
+               double asign, double* out, int S, double* norm2, int norm_shift, oz::Params& prm, double* pairs) {
     MixedState* M = mixed(P);
-    const long long N = (long long)P->N;
-    oz::Params prm;
     std::memset(&prm, 0, sizeof(prm));
-    double pairs = 0.0;
+    *pairs = 0.0;
     for (int g = 0; g < nseg; ++g) {
         oz::Segment& G = prm.seg[g];
         G.na = std::min(segs[g].op->na, S);
@@ -586,7 +663,7 @@ int oz_contract(const tfde_problem* P, int axis, const OzSegSpec* segs, int nseg
             G.amaps[t] = segs[g].op->amap[t];
             G.bmaps[t] = M->oz_bmap[segs[g].input][t][axis];
         }
-        for (int sa = 0; sa < G.na; ++sa) pairs += S - sa;
+        for (int sa = 0; sa < G.na; ++sa) *pairs += S - sa;
     }
     prm.nseg = nseg;
     prm.nslices = S;
@@ -617,14 +694,31 @@ int oz_contract(const tfde_problem* P, int axis, const OzSegSpec* segs, int nseg
     prm.norm2 = norm2;
     prm.norm_shift = norm_shift;
     prm.err = M->err;
+}
+
+int oz_set_attrs() {
     if (!g_oz_attr) {
-        OZ_TRY(cudaFuncSetAttribute(oz::oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM_BYTES));
+        OZ_TRY(cudaFuncSetAttribute(oz::oz_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    oz::SMEM_BYTES));
+        OZ_TRY(cudaFuncSetAttribute(oz::oz_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    oz::SMEM_BYTES));
         g_oz_attr = true;
     }
+    return TFDE_OK;
+}
+
+int oz_contract(const tfde_problem* P, int axis, const OzSegSpec* segs, int nseg, int vsign, const double* addend,
+                double asign, double* out, int S, cudaStream_t s, double* norm2 = nullptr, int norm_shift = 0) {
+    const long long N = (long long)P->N;
+    oz::Params prm;
+    double pairs = 0.0;
+    oz_params(P, axis, segs, nseg, vsign, addend, asign, out, S, norm2, norm_shift, prm, &pairs);
+    if (int st = oz_set_attrs()) return st;
     const long long total = prm.ntiles * prm.mhalves;
     long long grid = total < tc::num_sms() ? total : tc::num_sms();
     void* tok = stats_tc_begin(s, TFDE_KIND_EXACT);
-    oz::oz_gemm_kernel<<<(unsigned)(grid < 1 ? 1 : grid), oz::NUM_THREADS, oz::SMEM_BYTES, s>>>(prm);
+    oz::oz_gemm_kernel<false><<<(unsigned)(grid < 1 ? 1 : grid), oz::NUM_THREADS, oz::SMEM_BYTES, s>>>(
+        prm, nullptr, nullptr, 0, nullptr);
     cudaError_t e = cudaGetLastError();
     // algorithmic bytes: digit planes of each input read once, FP64 out (+ addend);
     // flops: 2 n per grid point per digit pair
@@ -666,6 +760,234 @@ int accurate_apply_ex(const tfde_problem* P, int op, const double* x, double* y,
 
 int accurate_apply(const tfde_problem* P, int op, const double* x, double* y, cudaStream_t s) {
     return accurate_apply_ex(P, op, x, y, 1, nullptr, 0.0, s);
+}
+
+namespace {
+// zero *norm2 of every active problem (the z-pass descriptors carry the pointers)
+__global__ void oz_zero_norms(const oz::Params* __restrict__ prm, int C, const int* __restrict__ act) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < C && act[i] && prm[i].norm2) *prm[i].norm2 = 0.0;
+}
+}  // namespace
+
+struct OzBatch {
+    int count = 0;
+    std::vector<tfde_problem*> P;
+    std::vector<double*> norm2;
+    // work-item starts [6][count + 1]: exact contraction x, y, z (row halves of
+    // line tiles); slicing x (lines), y and z (groups of 16 lines)
+    long long* d_start = nullptr;
+    long long total[6] = {};
+    int nmax[3] = {};
+    oz::Params* d_prm[OZ_SLICES + 1] = {};   // [3][count] per slice count, built on first use
+    double flops[OZ_SLICES + 1][3] = {};      // digit-product flops per axis (all problems)
+    SliceDesc* d_sd = nullptr;                // [3][count]
+    SliceDesc* h_sd = nullptr;
+    int* d_shift = nullptr;
+    int* h_shift = nullptr;
+    cudaEvent_t copied = nullptr;             // the last upload of h_sd / h_shift has been read
+};
+
+namespace {
+// the segments of the operator A along each axis (as accurate_apply_ex with op = A)
+void batch_segs(const MixedState* M, int axis, OzSegSpec* sg, int* nseg) {
+    if (axis == 0) {
+        sg[0] = {&M->oz_x_plus, 0};
+        *nseg = 1;
+    } else if (axis == 1) {
+        sg[0] = {&M->oz_y_mass_c, 0};
+        sg[1] = {&M->oz_y_plus, 1};
+        *nseg = 2;
+    } else {
+        sg[0] = {&M->oz_z_mass_c, 0};
+        sg[1] = {&M->oz_z_plus, 1};
+        *nseg = 2;
+    }
+}
+
+int batch_params(OzBatch* ob, int S) {
+    if (ob->d_prm[S]) return TFDE_OK;
+    const int C = ob->count;
+    std::vector<oz::Params> prm((size_t)3 * C);
+    for (int i = 0; i < C; ++i) {
+        tfde_problem* P = ob->P[i];
+        MixedState* M = mixed(P);
+        for (int a = 0; a < 3; ++a) {
+            OzSegSpec sg[2];
+            int nseg;
+            batch_segs(M, a, sg, &nseg);
+            double pairs = 0.0;
+            oz::Params& q = prm[(size_t)a * C + i];
+            if (a == 0)
+                oz_params(P, 0, sg, nseg, 1, nullptr, 0.0, P->w[tfde_problem::W_A], S, nullptr, 0, q, &pairs);
+            else if (a == 1)
+                oz_params(P, 1, sg, nseg, 1, nullptr, 0.0, P->w[tfde_problem::W_C], S, nullptr, 0, q, &pairs);
+            else
+                oz_params(P, 2, sg, nseg, -1, P->w[tfde_problem::W_B], 1.0, P->w[tfde_problem::W_R], S, ob->norm2[i], 0,
+                          q, &pairs);
+            if (a == 2) q.norm_shift_dev = ob->d_shift + i;
+            ob->flops[S][a] += 2.0 * pairs * P->n[a] * (double)P->N;
+        }
+    }
+    OZ_TRY(cudaMalloc((void**)&ob->d_prm[S], prm.size() * sizeof(oz::Params)));
+    OZ_TRY(cudaMemcpy(ob->d_prm[S], prm.data(), prm.size() * sizeof(oz::Params), cudaMemcpyHostToDevice));
+    return TFDE_OK;
+}
+
+template <int S>
+void batch_slice(OzBatch* ob, int axis, const int* d_act, cudaStream_t s) {
+    const int C = ob->count;
+    const long long* start = ob->d_start + (size_t)(3 + axis) * (C + 1);
+    const long long tot = ob->total[3 + axis];
+    const SliceDesc* d = ob->d_sd + (size_t)axis * C;
+    stats_count_launch();
+    if (axis == 0) {
+        const long long blocks = std::max<long long>(1, std::min<long long>((tot + 7) / 8, 152LL * 16));
+        slice_x_grouped_kernel<S><<<(unsigned)blocks, 256, 0, s>>>(d, start, C, d_act);
+        return;
+    }
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(slice_staged_grouped_kernel<16, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        attr = true;
+    }
+    const size_t smem = (size_t)2 * ob->nmax[axis] * 16 * 8;
+    const long long per_sm = std::max<long long>(1, (long long)(220 * 1024 / smem));
+    const long long blocks = std::max<long long>(1, std::min<long long>(tot, 152LL * per_sm));
+    slice_staged_grouped_kernel<16, S><<<(unsigned)blocks, SL_THREADS, smem, s>>>(d, start, C, d_act);
+}
+
+void batch_slice_s(OzBatch* ob, int axis, int S, const int* d_act, cudaStream_t s) {
+    switch (S) {
+        case 2: batch_slice<2>(ob, axis, d_act, s); break;
+        case 3: batch_slice<3>(ob, axis, d_act, s); break;
+        case 4: batch_slice<4>(ob, axis, d_act, s); break;
+        case 5: batch_slice<5>(ob, axis, d_act, s); break;
+        case 6: batch_slice<6>(ob, axis, d_act, s); break;
+        default: batch_slice<7>(ob, axis, d_act, s); break;
+    }
+}
+
+int batch_contract(OzBatch* ob, int axis, int S, const int* act, const int* d_act, cudaStream_t s) {
+    const int C = ob->count;
+    oz::Params p0;
+    std::memset(&p0, 0, sizeof(p0));
+    p0.nslices = S;
+    p0.b_kmajor = axis == 0 ? 1 : 0;
+    p0.ntiles = ob->total[axis];
+    p0.mhalves = 1;
+    p0.err = mixed(ob->P[0])->err;
+    if (int st = oz_set_attrs()) return st;
+    double bytes = 0.0;
+    for (int i = 0; i < C; ++i)
+        if (act[i]) bytes += (2.0 * S * (axis == 0 ? 1 : 2) + 8.0 + (axis == 2 ? 8.0 : 0.0)) * (double)ob->P[i]->N;
+    const long long grid = std::max<long long>(1, std::min<long long>(ob->total[axis], tc::num_sms()));
+    stats_count_launch();
+    void* tok = stats_tc_begin(s, TFDE_KIND_EXACT);
+    oz::oz_gemm_kernel<true><<<(unsigned)grid, oz::NUM_THREADS, oz::SMEM_BYTES, s>>>(
+        p0, ob->d_prm[S] + (size_t)axis * C, ob->d_start + (size_t)axis * (C + 1), C, d_act);
+    const cudaError_t e = cudaGetLastError();
+    stats_tc_end(tok, s, TFDE_KIND_EXACT, bytes, ob->flops[S][axis]);
+    if (e != cudaSuccess) return set_error(TFDE_ECUDA, std::string("grouped oz_gemm_kernel launch: ") + cudaGetErrorString(e));
+    return TFDE_OK;
+}
+}  // namespace
+
+int oz_batch_create(tfde_problem* const* P, int count, double* const* norm2, OzBatch** out) {
+    *out = nullptr;
+    OzBatch* ob = new OzBatch();
+    ob->count = count;
+    ob->P.assign(P, P + count);
+    ob->norm2.assign(norm2, norm2 + count);
+    std::vector<long long> start((size_t)6 * (count + 1), 0);
+    for (int i = 0; i < count; ++i) {
+        const tfde_problem* Pi = P[i];
+        const long long n1 = Pi->n[0], n2 = Pi->n[1], n3 = Pi->n[2];
+        long long w[6];
+        for (int a = 0; a < 3; ++a) {
+            const long long n = Pi->n[a];
+            const long long mh = (n + oz::BM - 1) / oz::BM;
+            long long tiles;
+            if (a == 0) tiles = (n2 * n3 + oz::BN - 1) / oz::BN;
+            else if (a == 1) tiles = ((n1 + oz::BN - 1) / oz::BN) * n3;
+            else tiles = (n1 * n2 + oz::BN - 1) / oz::BN;
+            w[a] = tiles * mh;
+            ob->nmax[a] = std::max(ob->nmax[a], (int)n);
+        }
+        w[3] = n2 * n3;                    // x lines
+        w[4] = (n1 * n3 + 15) / 16;        // y groups of 16 lines
+        w[5] = (n1 * n2 + 15) / 16;        // z groups of 16 lines
+        for (int k = 0; k < 6; ++k) start[(size_t)k * (count + 1) + i + 1] = start[(size_t)k * (count + 1) + i] + w[k];
+    }
+    for (int k = 0; k < 6; ++k) ob->total[k] = start[(size_t)k * (count + 1) + count];
+    auto fail = [&](const char* what) {
+        oz_batch_destroy(ob);
+        return set_error(TFDE_ENOMEM, what);
+    };
+    if (cudaMalloc((void**)&ob->d_start, start.size() * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc((void**)&ob->d_sd, (size_t)3 * count * sizeof(SliceDesc)) != cudaSuccess ||
+        cudaMallocHost((void**)&ob->h_sd, (size_t)3 * count * sizeof(SliceDesc)) != cudaSuccess ||
+        cudaMalloc((void**)&ob->d_shift, count * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&ob->h_shift, count * sizeof(int)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ob->copied, cudaEventDisableTiming) != cudaSuccess)
+        return fail("allocation of the batched exact-residual tables failed");
+    if (cudaMemcpy(ob->d_start, start.data(), start.size() * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail("upload of the batched exact-residual tables failed");
+    *out = ob;
+    return TFDE_OK;
+}
+
+void oz_batch_destroy(OzBatch* ob) {
+    if (!ob) return;
+    cudaFree(ob->d_start);
+    for (auto* d : ob->d_prm) cudaFree(d);
+    cudaFree(ob->d_sd);
+    if (ob->h_sd) cudaFreeHost(ob->h_sd);
+    cudaFree(ob->d_shift);
+    if (ob->h_shift) cudaFreeHost(ob->h_shift);
+    if (ob->copied) cudaEventDestroy(ob->copied);
+    delete ob;
+}
+
+int oz_batch_residual(OzBatch* ob, const double* const* x, const int* act, const int* d_act, const int* shift, int S,
+                      cudaStream_t s) {
+    if (S < 2 || S > OZ_SLICES) S = OZ_SLICES;
+    const int C = ob->count;
+    bool any = false;
+    for (int i = 0; i < C; ++i) any = any || act[i];
+    if (!any) return TFDE_OK;
+    if (int st = batch_params(ob, S)) return st;
+    OZ_TRY(cudaEventSynchronize(ob->copied));   // the previous call's upload has been read
+    for (int i = 0; i < C; ++i) {
+        tfde_problem* P = ob->P[i];
+        MixedState* M = mixed(P);
+        double* const* w = P->w;
+        const long long N = (long long)P->N;
+        SliceDesc* d = ob->h_sd;
+        d[i] = SliceDesc{x[i], nullptr, 0, P->n[0], axis_view(P->n, 0), M->oz_planes[0], M->oz_planes[1], N,
+                         M->oz_lexp, w[tfde_problem::W_W]};
+        d[C + i] = SliceDesc{w[tfde_problem::W_A], w[tfde_problem::W_W], M->oz_shift[1], P->n[0], axis_view(P->n, 1),
+                             M->oz_planes[0], M->oz_planes[1], N, M->oz_lexp, w[tfde_problem::W_E]};
+        d[2 * C + i] = SliceDesc{w[tfde_problem::W_C], w[tfde_problem::W_E], M->oz_shift[2], P->n[0],
+                                 axis_view(P->n, 2), M->oz_planes[0], M->oz_planes[1], N, M->oz_lexp,
+                                 w[tfde_problem::W_T]};
+        ob->h_shift[i] = shift[i];
+    }
+    OZ_TRY(cudaMemcpyAsync(ob->d_sd, ob->h_sd, (size_t)3 * C * sizeof(SliceDesc), cudaMemcpyHostToDevice, s));
+    OZ_TRY(cudaMemcpyAsync(ob->d_shift, ob->h_shift, C * sizeof(int), cudaMemcpyHostToDevice, s));
+    OZ_TRY(cudaEventRecord(ob->copied, s));
+    int st;
+    // x pass: a = (A1 + G1) x, w = A1 x; y pass: c = A2 a + G2 w, e = A2 w;
+    // z pass: r = b - (A3 c + G3 e), A_N x = A3 e
+    batch_slice_s(ob, 0, S, d_act, s);
+    if ((st = batch_contract(ob, 0, S, act, d_act, s))) return st;
+    batch_slice_s(ob, 1, S, d_act, s);
+    if ((st = batch_contract(ob, 1, S, act, d_act, s))) return st;
+    batch_slice_s(ob, 2, S, d_act, s);
+    stats_count_launch();
+    oz_zero_norms<<<(C + 63) / 64, 64, 0, s>>>(ob->d_prm[S] + (size_t)2 * C, C, d_act);
+    return batch_contract(ob, 2, S, act, d_act, s);
 }
 
 }  // namespace tfde

@@ -95,6 +95,7 @@ struct Params {
     double* out;
     double* norm2;             // optional: += sum over outputs of (out 2^norm_shift)^2 (FP32 terms)
     int norm_shift;
+    const int* norm_shift_dev; // when set, the shift is *norm_shift_dev (set per call on the device)
     int* err;
 };
 
@@ -151,7 +152,27 @@ __device__ __forceinline__ float scaled_f32(double v, int shift) {
     return (e == 0 || fe <= 0) ? 0.f : __uint_as_float(bits);
 }
 
-__global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_constant__ Params p) {
+// Group of work item t in a grouped launch: gstart[g] <= t < gstart[g + 1].
+__device__ __forceinline__ int oz_find_group(const long long* __restrict__ gstart, int ngroups, long long t) {
+    int lo = 0, hi = ngroups - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(gstart + mid) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// GROUPED = false: one contraction described by p0.  GROUPED = true: a work
+// list over `ngroups` contractions of the same axis and slice count (one per
+// problem of a batch) whose descriptors sit in global memory; work item t
+// (a row half of a line tile) belongs to group g with gstart[g] <= t <
+// gstart[g + 1], groups with gactive[g] == 0 are skipped by all three roles
+// alike, and p0 carries only the common fields (nslices, err) and ntiles =
+// gstart[ngroups], mhalves = 1.
+template <bool GROUPED>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    oz_gemm_kernel(const __grid_constant__ Params p0, const Params* __restrict__ groups,
+                   const long long* __restrict__ gstart, int ngroups, const int* __restrict__ gactive) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* stages = smem;
@@ -165,9 +186,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int S = p.nslices;
+    const int S = p0.nslices;
     const int D = S - 1;
-    const int nkb = (p.n + BK - 1) / BK;
     const int nst = stage_count(S);                              // ring stages in use
     // TMEM buffers: two when the S diagonals of a tile fit in half of TMEM
     // (S <= 4), so that the epilogue of one tile overlaps the next tile's MMAs
@@ -192,7 +212,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const long long total = p.ntiles * p.mhalves;
+    const long long total = p0.ntiles * p0.mhalves;
+    int* const err = p0.err;
+    // the descriptor and local work item of work item t (nullptr: a skipped group)
+    auto item = [&](long long t, long long& lt) -> const Params* {
+        lt = t;
+        if (!GROUPED) return &p0;
+        const int g = oz_find_group(gstart, ngroups, t);
+        if (gactive && !__ldg(gactive + g)) return nullptr;
+        lt = t - __ldg(gstart + g);
+        return groups + g;
+    };
 
     if (warp < PRODUCERS) {
         if (lane == 0) {
@@ -201,12 +231,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
             uint32_t ph = 0, filled = 0, last_ph = 0;
             bool ok = true;
             for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                const long long tile = t / p.mhalves;
-                const int mh = (int)(t % p.mhalves);
+                long long lt;
+                const Params* pp = item(t, lt);
+                if (!pp) continue;
+                const Params& p = *pp;
+                const int nkb = (p.n + BK - 1) / BK;
+                const long long tile = lt / p.mhalves;
+                const int mh = (int)(lt % p.mhalves);
                 for (int sg = 0; sg < p.nseg && ok; ++sg) {
                     const Segment& G = p.seg[sg];
                     for (int kb = 0; kb < nkb; ++kb) {
-                        if (!mbar_wait(&empty[s], ph ^ 1u, p.err)) { ok = false; break; }
+                        if (!mbar_wait(&empty[s], ph ^ 1u, err)) { ok = false; break; }
                         uint8_t* st = stages + s * stage_bytes;
                         // box i of this stage (operator slices, then input slices) belongs to issuer i % PRODUCERS
                         uint32_t mine = 0;
@@ -258,7 +293,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                 }
             }
             for (int i = 0; i < nst; ++i)
-                if (filled & (1u << i)) mbar_wait(&full[i], (last_ph >> i) & 1u, p.err, false);
+                if (filled & (1u << i)) mbar_wait(&full[i], (last_ph >> i) & 1u, err, false);
         }
     } else if (warp == MMA_WARP) {
         if (lane == 0) {
@@ -270,27 +305,33 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
             // is read once per 256 columns instead of once per 64.
             uint32_t idesc[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) idesc[c] = instr_desc(BM, BN * (c + 1), p.b_kmajor ? 0 : 1);
+            for (int c = 0; c < 4; ++c) idesc[c] = instr_desc(BM, BN * (c + 1), p0.b_kmajor ? 0 : 1);
             // descriptor templates at stage 0, tile 0; the start-address field
             // (bits 0..13, address >> 4) absorbs every in-smem offset without carry
             const uint64_t a_desc0 = smem_desc(smem_u32(stages), 16, 512, 4);
-            const uint64_t b_desc0 = p.b_kmajor ? smem_desc(smem_u32(stages + b_off), 16, 512, 4)
-                                                : smem_desc(smem_u32(stages + b_off), 4096, 1024, 2);
-            const uint32_t b_k16 = p.b_kmajor ? (32u >> 4) : (2048u >> 4);
+            const uint64_t b_desc0 = p0.b_kmajor ? smem_desc(smem_u32(stages + b_off), 16, 512, 4)
+                                                 : smem_desc(smem_u32(stages + b_off), 4096, 1024, 2);
+            const uint32_t b_k16 = p0.b_kmajor ? (32u >> 4) : (2048u >> 4);
             int s = 0;
             uint32_t ph = 0;
             bool ok = true;
-            long long it = 0;
-            for (long long t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
+            long long it = 0;   // work items this CTA has processed (skipped groups not counted)
+            for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                long long lt;
+                const Params* pp = item(t, lt);
+                if (!pp) continue;
+                const Params& p = *pp;
+                const int nkb = (p.n + BK - 1) / BK;
                 const int buf = (int)(it % nbuf);
                 const uint32_t use = (uint32_t)(it / nbuf);
+                ++it;
                 const uint32_t dbase = tmem_base + (uint32_t)(buf * (TMEM_COLS / 2));
-                if (!mbar_wait(&tempty[buf], (use & 1u) ^ 1u, p.err)) { ok = false; break; }
+                if (!mbar_wait(&tempty[buf], (use & 1u) ^ 1u, err)) { ok = false; break; }
                 tc_fence_after();
                 for (int sg = 0; sg < p.nseg && ok; ++sg) {
                     const int na = p.seg[sg].na;
                     for (int kb = 0; kb < nkb; ++kb) {
-                        if (!mbar_wait(&full[s], ph, p.err)) { ok = false; break; }
+                        if (!mbar_wait(&full[s], ph, err)) { ok = false; break; }
                         tc_fence_after();
                         const uint64_t ad_s = a_desc0 + (uint64_t)((s * stage_bytes) >> 4);
                         const uint64_t bd_s = b_desc0 + (uint64_t)((s * stage_bytes) >> 4);
@@ -320,25 +361,45 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                 if (ok) umma_commit(&tfull[buf]);
             }
             umma_commit(mma_done);
-            mbar_wait(mma_done, 0, p.err, false);
+            mbar_wait(mma_done, 0, err, false);
         }
     } else {
         const int q = warp & 3;                 // TMEM lane quadrant
         const int part = (warp - EPI_WARP0) >> 2;   // columns [EPI_COLS part, EPI_COLS (part + 1))
         long long it = 0;
         float nacc = 0.f;                       // this thread's share of the output norm
-        for (long long t = blockIdx.x; t < total; t += gridDim.x, ++it) {
+        // destination of nacc: each group of a grouped launch has its own, and
+        // the groups come in increasing order, so a warp flushes its share when
+        // the next group's first tile arrives
+        double* ndst = GROUPED ? nullptr : p0.norm2;
+        auto flush_norm = [&]() {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) nacc += __shfl_xor_sync(0xffffffffu, nacc, o);
+            if (lane == 0 && ndst) atomicAdd(ndst, (double)nacc);
+            nacc = 0.f;
+        };
+        for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+            long long lt;
+            const Params* pp = item(t, lt);
+            if (!pp) continue;
+            const Params& p = *pp;
+            if (GROUPED && p.norm2 != ndst) {   // warp-uniform
+                if (ndst) flush_norm();
+                ndst = p.norm2;
+            }
+            const int nsh = p.norm_shift_dev ? __ldg(p.norm_shift_dev) : p.norm_shift;
             const int buf = (int)(it % nbuf);
             const uint32_t use = (uint32_t)(it / nbuf);
+            ++it;
             const uint32_t dbase = tmem_base + (uint32_t)(buf * (TMEM_COLS / 2));
             int ok = 1;
-            if (lane == 0) ok = mbar_wait(&tfull[buf], use & 1u, p.err) ? 1 : 0;
+            if (lane == 0) ok = mbar_wait(&tfull[buf], use & 1u, err) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             __syncwarp();
             tc_fence_after();
-            const long long tile = t / p.mhalves;
-            const int mh = (int)(t % p.mhalves);
+            const long long tile = lt / p.mhalves;
+            const int mh = (int)(lt % p.mhalves);
             const int m = mh * BM + 32 * q + lane;
             const bool mvalid = m < p.n;
             const int es = mvalid ? __ldg(p.row_exp + m) : 0;
@@ -386,7 +447,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                         if (p.addend) v = fma(p.addend_sign, p.addend[idx], v);
                         p.out[idx] = v;
                         if (p.norm2) {
-                            const float f = scaled_f32(v, p.norm_shift);
+                            const float f = scaled_f32(v, nsh);
                             nacc = fmaf(f, f, nacc);
                         }
                     }
@@ -407,7 +468,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                     if (p.norm2) {
 #pragma unroll
                         for (int j = 0; j < CH; ++j) {
-                            const float f = scaled_f32(o[j], p.norm_shift);
+                            const float f = scaled_f32(o[j], nsh);
                             nacc = fmaf(f, f, nacc);
                         }
                     }
@@ -468,11 +529,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) oz_gemm_kernel(const __grid_co
                 }
             }
         }
-        if (p.norm2) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) nacc += __shfl_xor_sync(0xffffffffu, nacc, o);
-            if (lane == 0) atomicAdd(p.norm2, (double)nacc);
-        }
+        if (ndst) flush_norm();
     }
 
     tc_fence_before();
