@@ -382,11 +382,15 @@ __global__ void bkg_reduce(const double* __restrict__ part, int NB, const int* _
     if (threadIdx.x == 0) out[inst * ostride + ooff + t] = acc;
 }
 
-// W -= sum_{t <= j} coef[i * kHS + coff + t] V_t
-__global__ __launch_bounds__(kBT) void bkg_axpy_w(const BVec* __restrict__ vt, const int* __restrict__ bi,
-                                                 const long long* __restrict__ bo, const int* __restrict__ act,
-                                                 const int* __restrict__ jd, const double* __restrict__ coef,
-                                                 int coff) {
+// The second Gram-Schmidt pass's projections fused with the first pass's
+// update: W -= sum_{t <= j} coef[i * kHS + coff + t] V_t over the block's
+// chunk, then the block partial sums of <V_t, W> (t <= j) of the updated
+// chunk into rows t of part (each thread re-reads the elements it wrote):
+// the arithmetic of a plain multi-axpy followed by bkg_dots.
+__global__ __launch_bounds__(kBT) void bkg_axpy_dots(const BVec* __restrict__ vt, const int* __restrict__ bi,
+                                                    const long long* __restrict__ bo, const int* __restrict__ act,
+                                                    const int* __restrict__ jd, const double* __restrict__ coef,
+                                                    int coff, double* __restrict__ part) {
     BK_PROLOGUE
     const int m = *jd + 1;
     __shared__ float hs[64];
@@ -397,6 +401,45 @@ __global__ __launch_bounds__(kBT) void bkg_axpy_w(const BVec* __restrict__ vt, c
         for (int t = 0; t < m; ++t) acc = fmaf(-hs[t], v.V[(long long)t * v.N + e], acc);
         v.W[e] = acc;
     }
+    for (int m0 = 0; m0 < m; m0 += 8) {
+        const int mc = min(8, m - m0);
+        KSum k[8];
+        for (long long e = e0 + threadIdx.x; e < e1; e += kBT) {
+            const float we = v.W[e];
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                if (t < mc) k[t].add(v.V[(long long)(m0 + t) * v.N + e] * we);
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            if (t < mc) {
+                const double sum = block_sum((double)k[t].s - (double)k[t].c);
+                if (threadIdx.x == 0) part[(long long)(m0 + t) * gridDim.x + blockIdx.x] = sum;
+            }
+        }
+    }
+}
+
+// The second pass's update fused with ||W||^2: W -= sum_{t <= j} coef V_t and
+// the block partial sum of the updated W^2 into row R + 1 of part.
+__global__ __launch_bounds__(kBT) void bkg_axpy_ww(const BVec* __restrict__ vt, const int* __restrict__ bi,
+                                                  const long long* __restrict__ bo, const int* __restrict__ act,
+                                                  const int* __restrict__ jd, const double* __restrict__ coef,
+                                                  int coff, int R, double* __restrict__ part) {
+    BK_PROLOGUE
+    const int m = *jd + 1;
+    __shared__ float hs[64];
+    for (int t = threadIdx.x; t < m; t += blockDim.x) hs[t] = (float)coef[inst * kHS + coff + t];
+    __syncthreads();
+    KSum k;
+    for (long long e = e0 + threadIdx.x; e < e1; e += kBT) {
+        float acc = v.W[e];
+        for (int t = 0; t < m; ++t) acc = fmaf(-hs[t], v.V[(long long)t * v.N + e], acc);
+        v.W[e] = acc;
+        k.add(acc * acc);
+    }
+    const double sum = block_sum((double)k.s - (double)k.c);
+    if (threadIdx.x == 0) part[(long long)(R + 1) * gridDim.x + blockIdx.x] = sum;
 }
 
 // V_{j+1} = W sc and its split planes (ph, pl)
@@ -896,15 +939,16 @@ int build_cycle_graph(tfde_batch* B, cudaStream_t s) {
             for (int a = 0; a < 2 && !st; ++a)
                 st = grouped(B, B->d_sop + (size_t)a * C, a, tc::OUT_SUM, B->sop_bytes[a], B->sop_flops[a], s);
             if (!st) st = grouped(B, B->d_sopzw, 2, tc::OUT_SUM, B->sop_bytes[2], B->sop_flops[2], s);
-            for (int pass = 0; pass < 2 && !st; ++pass) {   // CGS2
+            if (!st) {   // CGS2: <V, W>; W -= V h and <V, W> again (one pass); W -= V h2 and ||W||^2 (one pass)
                 for (int m0 = 0; m0 < R; m0 += 8)
                     bkg_dots<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, m0, B->d_j, R, 0, B->d_part);
                 bkg_reduce<<<dim3((unsigned)C, (unsigned)R), 32, 0, s>>>(B->d_part, B->NB, B->d_bstart, B->d_act,
-                                                                         B->d_j, R, 0, B->d_h, kHS, 64 * pass);
-                bkg_axpy_w<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, B->d_j, B->d_h, 64 * pass);
-            }
-            if (!st) {
-                bkg_dots<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, 0, B->d_j, R, 1, B->d_part);
+                                                                         B->d_j, R, 0, B->d_h, kHS, 0);
+                bkg_axpy_dots<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, B->d_j, B->d_h, 0, B->d_part);
+                bkg_reduce<<<dim3((unsigned)C, (unsigned)R), 32, 0, s>>>(B->d_part, B->NB, B->d_bstart, B->d_act,
+                                                                         B->d_j, R, 0, B->d_h, kHS, 64);
+                bkg_axpy_ww<<<B->NB, kBT, 0, s>>>(B->d_vt, B->d_bi, B->d_bo, B->d_act, B->d_j, B->d_h, 64, R,
+                                                  B->d_part);
                 bkg_reduce<<<dim3((unsigned)C, 1u), 32, 0, s>>>(B->d_part, B->NB, B->d_bstart, B->d_act, B->d_j, R,
                                                                1, B->d_s, kSS, S_WW);
                 bkg_givens<<<gb, 64, 0, s>>>(C, R, B->d_j, B->d_gs, B->d_h, B->d_s, B->d_theta, B->d_act, B->d_its,
@@ -932,8 +976,9 @@ int build_cycle_graph(tfde_batch* B, cudaStream_t s) {
     return TFDE_OK;
 }
 
-// launches of one captured step: 3 grouped + 2 x (ceil(R / 8) + 2) + 5
-unsigned cycle_step_launches(int R) { return 3u + 2u * (unsigned)((R + 7) / 8 + 2) + 5u; }
+// launches of one captured step: 3 grouped + ceil(R / 8) + 1 (first projections)
+// + 4 (fused second pass and norm with their reductions) + 3 (Givens, scale, loop)
+unsigned cycle_step_launches(int R) { return 3u + (unsigned)((R + 7) / 8 + 1) + 4u + 3u; }
 
 // The batched PCG iteration of every symmetric problem as the body of a while
 // node: the operator's three grouped passes (<p, q> per problem), the update,

@@ -668,19 +668,67 @@ __global__ void gm_reduce_kernel(const double* __restrict__ part, int nblk, doub
     if (threadIdx.x == 0) out[j] = acc;
 }
 
-// w -= sum_{i <= j} h[i] V_i
-__global__ void gm_multiaxpy_kernel(long long N, const float* __restrict__ V, long long ldv,
-                                    const double* __restrict__ h, float* __restrict__ w, const int* gctl) {
+// The second Gram-Schmidt pass's projections fused with the first pass's
+// update: w -= sum_{i <= j} h[i] V_i over the block's chunk, then the first
+// m = j + 1 inner products <V_i, w> of the updated chunk (each thread re-reads
+// the elements it wrote), 8 basis vectors per sweep; the same arithmetic as
+// a plain multi-axpy followed by gm_multidot_kernel.
+__global__ __launch_bounds__(kT) void gm_axpy_dot_kernel(long long N, const float* __restrict__ V, long long ldv,
+                                                         const double* __restrict__ h, float* __restrict__ w,
+                                                         double* __restrict__ part, const int* gctl) {
     if (gctl[1]) return;
     const int m = gctl[0] + 1;
     __shared__ float hs[128];
     for (int j = threadIdx.x; j < m; j += blockDim.x) hs[j] = (float)h[j];
     __syncthreads();
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    long long lo, hi;
+    chunk(N, lo, hi);
+    for (long long i = lo + threadIdx.x; i < hi; i += kT) {
         float acc = w[i];
         for (int j = 0; j < m; ++j) acc = fmaf(-hs[j], V[(long long)j * ldv + i], acc);
         w[i] = acc;
     }
+    for (int m0 = 0; m0 < m; m0 += 8) {
+        const int mc = m - m0 < 8 ? m - m0 : 8;
+        KSum k[8];
+        for (long long i = lo + threadIdx.x; i < hi; i += kT) {
+            const float wi = w[i];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < mc) k[j].add(V[(long long)(m0 + j) * ldv + i] * wi);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (j < mc) {
+                const double t = block_sum64((double)k[j].s - (double)k[j].c);
+                if (threadIdx.x == 0) part[(long long)(m0 + j) * gridDim.x + blockIdx.x] = t;
+            }
+        }
+    }
+}
+
+// The second pass's update fused with ||w||^2: w -= sum_{i <= j} h[i] V_i over
+// the block's chunk and the block's partial sum of the updated w^2 (the
+// arithmetic of a plain multi-axpy followed by gm_dot_kernel).
+__global__ __launch_bounds__(kT) void gm_axpy_norm_kernel(long long N, const float* __restrict__ V, long long ldv,
+                                                          const double* __restrict__ h, float* __restrict__ w,
+                                                          double* __restrict__ part, const int* gctl) {
+    if (gctl[1]) return;
+    const int m = gctl[0] + 1;
+    __shared__ float hs[128];
+    for (int j = threadIdx.x; j < m; j += blockDim.x) hs[j] = (float)h[j];
+    __syncthreads();
+    long long lo, hi;
+    chunk(N, lo, hi);
+    KSum k;
+    for (long long i = lo + threadIdx.x; i < hi; i += kT) {
+        float acc = w[i];
+        for (int j = 0; j < m; ++j) acc = fmaf(-hs[j], V[(long long)j * ldv + i], acc);
+        w[i] = acc;
+        k.add(acc * acc);
+    }
+    const double t = block_sum64((double)k.s - (double)k.c);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 __global__ __launch_bounds__(kT) void gm_dot_kernel(long long N, const float* __restrict__ a, double* __restrict__ part,
@@ -786,15 +834,15 @@ __global__ void gm_solve_kernel(const double* gs, const int* gctl, double* ny, i
 void launch_gm_step(size_t N, const float* V, float* w, double* part, int nblk, double* hbuf, double* h2buf,
                     double* wwbuf, double* gs, int* gctl, cudaGraphConditionalHandle hc, float* Vout,
                     __nv_bfloat16* ph, __nv_bfloat16* pl, int maxm, cudaStream_t s) {
-    stats_count_launch(9);
+    stats_count_launch(7);
     const long long n = (long long)N;
+    // CGS2: <V, w>; w -= V h and <V, w> again (one pass over the block's chunk);
+    // w -= V h2 and ||w||^2 (one pass)
     gm_multidot_kernel<<<nblk, kT, 0, s>>>(n, V, n, w, part, gctl);
     gm_reduce_kernel<<<maxm, 32, 0, s>>>(part, nblk, hbuf, 0, gctl);
-    gm_multiaxpy_kernel<<<grid_for(n), kT, 0, s>>>(n, V, n, hbuf, w, gctl);
-    gm_multidot_kernel<<<nblk, kT, 0, s>>>(n, V, n, w, part, gctl);
+    gm_axpy_dot_kernel<<<nblk, kT, 0, s>>>(n, V, n, hbuf, w, part, gctl);
     gm_reduce_kernel<<<maxm, 32, 0, s>>>(part, nblk, h2buf, 0, gctl);
-    gm_multiaxpy_kernel<<<grid_for(n), kT, 0, s>>>(n, V, n, h2buf, w, gctl);
-    gm_dot_kernel<<<nblk, kT, 0, s>>>(n, w, part, gctl);
+    gm_axpy_norm_kernel<<<nblk, kT, 0, s>>>(n, V, n, h2buf, w, part, gctl);
     gm_reduce_kernel<<<1, 32, 0, s>>>(part, nblk, wwbuf, 1, gctl);
     gm_givens_kernel<<<1, 1, 0, s>>>(gs, hbuf, h2buf, wwbuf, gctl, hc);
     (void)Vout;

@@ -935,7 +935,7 @@ int inner_gmres_spec(const tfde_problem* P, int restart, double ptheta, int maxi
         MX_TRY(cudaMemcpyAsync(P->red_host, M->gm_state, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
         MX_TRY(cudaStreamSynchronize(s));
         k = M->gm_ctl_host[0];
-        stats_count_launch((unsigned)(k > 0 ? k : 1) * 13u);   // the graph's launches, 13 per step
+        stats_count_launch((unsigned)(k > 0 ? k : 1) * 11u);   // the graph's launches, 11 per step
         const double beta = P->red_host[GS_BETA], est = P->red_host[GS_EST];
         if (M->gm_ctl_host[3] || !std::isfinite(beta))
             return set_error(TFDE_ENAN, "non-finite preconditioned residual or Arnoldi vector");
@@ -1143,7 +1143,7 @@ int inner_gmres_graph(const tfde_problem* P, int restart, double ptheta, int max
     MX_TRY(cudaMemcpyAsync(P->red_host, M->gm_state, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     MX_TRY(cudaStreamSynchronize(s));
     const int k = M->gm_ctl_host[0];
-    stats_count_launch((unsigned)(k > 0 ? k : 1) * 19u);   // the graph's launches, 19 per step
+    stats_count_launch((unsigned)(k > 0 ? k : 1) * 17u);   // the graph's launches, 17 per step
     const double beta = P->red_host[GS_BETA], est = P->red_host[GS_EST];
     if (M->gm_ctl_host[3] || !std::isfinite(beta))
         return set_error(TFDE_ENAN, "non-finite preconditioned residual or Arnoldi vector");
