@@ -188,6 +188,25 @@ int tfde_cn_advance(const tfde_problem* prob, double* u, const double* F_half, i
                     tfde_info* info, void* stream);
 
 /*
+ * tfde_cn_advance_host -- tfde_cn_advance (Sec. 2, Eq. (CN)) for a state kept
+ * in HOST memory: u^{m-1} is copied from u_host_in into the device state u,
+ * the step runs as tfde_cn_advance(prob, u, F_half, restart, tol), and u^m is
+ * copied to u_host_out (and stays in u, so that the next call chains on it).
+ *   The copies overlap the step's own work: the input copy runs on a stream
+ *   of the problem's own, beside the work that reads no u (the minimal-
+ *   residual sums of the order-3 guess), and the output copy leaves as soon
+ *   as an iterate that may be final exists, while the exact residual that
+ *   decides it is formed (a later write of u waits for that copy and is
+ *   copied again).  Page-locked host buffers are needed for the copies to
+ *   overlap; u_host_out may alias u_host_in.
+ *   u_host_in, u_host_out: host, N doubles each.  u: device, N doubles.
+ *   Chain, F_half and errors as tfde_cn_advance (TFDE_EINVAL also for a NULL
+ *   or device host buffer).  Synchronises `stream`.
+ */
+int tfde_cn_advance_host(const tfde_problem* prob, const double* u_host_in, double* u_host_out, double* u,
+                         const double* F_half, int restart, double tol, tfde_info* info, void* stream);
+
+/*
  * tfde_cn_advance_guess -- tfde_cn_advance with a candidate initial guess x0
  * (e.g. from the warm-start network): the solve starts from the point
  * u^{m-1} + c (x0 - u^{m-1}) of least FP64 residual ||b^m - A x||, c >= 0

@@ -189,6 +189,69 @@ int tfde_cn_advance(const tfde_problem* prob, double* u, const double* F_half, i
     return st;
 }
 
+int tfde_cn_advance_host(const tfde_problem* prob, const double* u_host_in, double* u_host_out, double* u,
+                         const double* F_half, int restart, double tol, tfde_info* info, void* stream) {
+    if (!prob) return set_error(TFDE_EINVAL, "NULL problem");
+    int st;
+    if ((st = pre_call()) || (st = check_dev(u, "u")) || (st = check_tol(tol))) return st;
+    if (F_half && (st = check_dev(F_half, "F_half"))) return st;
+    if (F_half == u) return set_error(TFDE_EINVAL, "F_half aliases u");
+    for (const void* hp : {(const void*)u_host_in, (const void*)u_host_out}) {
+        if (!hp) return set_error(TFDE_EINVAL, "NULL host buffer");
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, hp) != cudaSuccess) {
+            cudaGetLastError();
+        } else if (at.type == cudaMemoryTypeDevice) {
+            return set_error(TFDE_EINVAL, "u_host_in / u_host_out must be host memory");
+        }
+    }
+    tfde_problem* P = const_cast<tfde_problem*>(prob);
+    const cudaStream_t s = (cudaStream_t)stream;
+    auto& io = P->io;
+    if (!io.stream) {
+        if (cudaStreamCreateWithFlags(&io.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&io.ev_start, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&io.ev_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&io.ev_ready, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&io.ev_out, cudaEventDisableTiming) != cudaSuccess)
+            return set_error(TFDE_ECUDA, "creation of the copy stream failed");
+    }
+    const size_t bytes = P->N * sizeof(double);
+    io.in = u_host_in;
+    io.out = u_host_out;
+    io.dev = u;
+    io.out_pending = io.out_valid = false;
+    // u^{m-1} host -> u on the copy stream, after the work queued on `stream`
+    // so far; the step waits for it only before its first read of u
+    cudaEventRecord(io.ev_start, s);
+    cudaStreamWaitEvent(io.stream, io.ev_start, 0);
+    cudaMemcpyAsync(u, u_host_in, bytes, cudaMemcpyHostToDevice, io.stream);
+    cudaEventRecord(io.ev_in, io.stream);
+    io.in_pending = true;
+    const bool chained = !restart && P->chain_ok && P->chain_u == u;
+    P->chain_ok = false;
+    st = cn_drive(P, u, F_half, nullptr, u, tol, info, s, chained, nullptr, nullptr);
+    io_wait_input(P, s);
+    if (st == TFDE_OK && !io.out_valid) {
+        // no copy was offered after the last write of u (or none at all)
+        if (io.out_pending) cudaStreamWaitEvent(s, io.ev_out, 0);
+        cudaMemcpyAsync(u_host_out, u, bytes, cudaMemcpyDeviceToHost, s);
+    }
+    const cudaError_t e1 = cudaStreamSynchronize(io.stream);
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    io.in = nullptr;
+    io.out = nullptr;
+    io.dev = nullptr;
+    io.in_pending = io.out_pending = io.out_valid = false;
+    if (st == TFDE_OK && (e1 != cudaSuccess || e2 != cudaSuccess))
+        st = set_error(TFDE_ECUDA, std::string("host copies: ") + cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+    if (st == TFDE_OK) {
+        P->chain_ok = true;
+        P->chain_u = u;
+    }
+    return st;
+}
+
 int tfde_cn_advance_guess(const tfde_problem* prob, double* u, const double* F_half, const double* x0, int restart,
                           double tol, tfde_info* info, int* used_guess, void* stream) {
     if (!prob) return set_error(TFDE_EINVAL, "NULL problem");

@@ -135,6 +135,22 @@ struct tfde_problem {
     void* fft = nullptr;    // FFT tables of the FFT-embedded passes (tfde_fft.h), null: dense FP64
     void* fmix = nullptr;   // mixed-precision state on the FFT passes (tfde_fftmixed.cu)
 
+    // host copies of a tfde_cn_advance_host step (out == null otherwise): the
+    // input goes host -> dev on `stream` while the step starts its work that
+    // does not read u; the output goes dev -> host as soon as an iterate that
+    // may be final exists (during the residual that decides it), again after
+    // any later write of dev
+    struct HostIO {
+        const double* in = nullptr;
+        double* out = nullptr;
+        double* dev = nullptr;
+        cudaStream_t stream = nullptr;       // copy stream (per problem, created on first use)
+        cudaEvent_t ev_start = nullptr, ev_in = nullptr, ev_ready = nullptr, ev_out = nullptr;
+        bool in_pending = false;             // the main stream has not yet waited for the input
+        bool out_pending = false;            // an output copy may still read dev
+        bool out_valid = false;              // the last output copy was issued after the last write of dev
+    } io;
+
     // chained CN advance: W_B / W_R hold b^{m-1} and its final true residual
     const double* chain_u = nullptr;
     bool chain_ok = false;
@@ -155,6 +171,13 @@ struct tfde_problem {
 namespace tfde {
 // red_out slot of the fused ||b||^2, ||r_0||^2 of cn_prepare
 constexpr int kNormsSlot = 250;
+// host copies of tfde_cn_advance_host (tfde_solvers.cu): the main stream s
+// waits for the input before the first read of u; an iterate x that may be
+// final is offered to the output copy; a write of x first waits for a copy
+// still reading it.  No-ops unless x is the step's device state.
+void io_wait_input(tfde_problem* P, cudaStream_t s);
+void io_offer_output(tfde_problem* P, const double* x, cudaStream_t s);
+void io_before_write(tfde_problem* P, const double* x, cudaStream_t s);
 // red_out slots of the five sums of the minimal-residual guess correction
 constexpr int kMrSlot = 240;
 // solver internals (tfde_solvers.cu)

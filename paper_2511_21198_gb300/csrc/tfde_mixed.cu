@@ -1544,6 +1544,7 @@ constexpr double kInnerFloor = 1e-4;
 // b - A x at full width, with A_N x into W_T for the next chained CN step.
 int exact_residual(tfde_problem* P, const double* b, const double* x, double* r64, double* nr, double tol, double nb,
                    cudaStream_t s) {
+    io_offer_output(P, x, s);   // x may be final: a host copy may leave while its residual is formed
     const int st = accurate_residual(P, b, x, r64, nr, tol, nb, s, P->w[tfde_problem::W_T]);
     P->an_ready = st == TFDE_OK;
     return st;
@@ -1564,6 +1565,7 @@ int apply_correction(tfde_problem* P, const double* b, double* x, double* r64, d
     MixedState* M = mixed(P);
     int st;
     double* an = P->w[tfde_problem::W_T];
+    io_before_write(P, x, s);
     if (*nr * pred > tol * nb) {
         double* c64 = an;
         P->an_ready = false;
@@ -1597,6 +1599,7 @@ int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit
     const double nb = std::sqrt(bb);
     if (!std::isfinite(nb)) return set_error(TFDE_ENAN, "non-finite right-hand side");
     if (nb == 0.0) {
+        io_before_write(P, x, s);
         MX_TRY(cudaMemsetAsync(x, 0, P->N * sizeof(double), s));
         if (info) *info = loc;
         return TFDE_OK;
@@ -1659,6 +1662,7 @@ int mixed_pcg(tfde_problem* P, const double* b, double* x, double tol, int maxit
             loc.fallback = 1;
             P->an_ready = false;
             tfde_info sub{};
+            io_before_write(P, x, s);
             status = pcg64(P, b, x, tol, maxit > loc.iters ? maxit - loc.iters : 1, &sub, s, false);
             loc.iters += sub.iters;
             nr = sub.relres * nb;
@@ -1688,6 +1692,7 @@ int mixed_pgmres(tfde_problem* P, const double* b, double* x, int restart, doubl
     const double nb = std::sqrt(bb);
     if (!std::isfinite(nb)) return set_error(TFDE_ENAN, "non-finite right-hand side");
     if (nb == 0.0) {
+        io_before_write(P, x, s);
         MX_TRY(cudaMemsetAsync(x, 0, P->N * sizeof(double), s));
         if (info) *info = loc;
         return TFDE_OK;
@@ -1732,6 +1737,7 @@ int mixed_pgmres(tfde_problem* P, const double* b, double* x, int restart, doubl
             loc.fallback = 1;
             P->an_ready = false;
             tfde_info sub{};
+            io_before_write(P, x, s);
             status = pgmres64(P, b, x, restart, tol, maxit > loc.iters ? maxit - loc.iters : 1, &sub, s, false);
             loc.iters += sub.iters;
             loc.restarts += sub.restarts;

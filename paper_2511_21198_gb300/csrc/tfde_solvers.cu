@@ -331,6 +331,32 @@ static void mass_apply(const tfde_problem* P, const double* u, double* out, cuda
     launch_mass3d_f64(u, out, P->n, s);
 }
 
+void io_wait_input(tfde_problem* P, cudaStream_t s) {
+    if (!P->io.in_pending) return;
+    cudaStreamWaitEvent(s, P->io.ev_in, 0);
+    P->io.in_pending = false;
+}
+
+void io_offer_output(tfde_problem* P, const double* x, cudaStream_t s) {
+    if (!P->io.out || x != P->io.dev) return;
+    cudaEventRecord(P->io.ev_ready, s);
+    cudaStreamWaitEvent(P->io.stream, P->io.ev_ready, 0);
+    cudaMemcpyAsync(P->io.out, P->io.dev, P->N * sizeof(double), cudaMemcpyDeviceToHost, P->io.stream);
+    cudaEventRecord(P->io.ev_out, P->io.stream);
+    P->io.out_pending = true;
+    P->io.out_valid = true;
+}
+
+void io_before_write(tfde_problem* P, const double* x, cudaStream_t s) {
+    if (!P->io.out || x != P->io.dev) return;
+    io_wait_input(P, s);
+    if (P->io.out_pending) {
+        cudaStreamWaitEvent(s, P->io.ev_out, 0);
+        P->io.out_pending = false;
+    }
+    P->io.out_valid = false;
+}
+
 // Coefficients g of the corrected guess x0 = g0 u^{m-1} + g1 u^{m-2} +
 // g2 u^{m-3}, into g (device): the order-2 extrapolation x_e = 3 u^{m-1} -
 // 3 u^{m-2} + u^{m-3} plus c1 d1 + c2 d2 (d1 = u^{m-1} - u^{m-2}, d2 =
@@ -361,7 +387,10 @@ int cn_prepare(tfde_problem* P, const double* u_prev, const double* F, const dou
     // A_N u_prev: left in W_T by the mixed solver's last (full-width) residual
     // of a chained step, whose z-pass digit slicing forms it exactly; else the
     // fused stencil
-    if (!(chained && P->an_ready)) mass_apply(P, u_prev, an, s);
+    if (!(chained && P->an_ready)) {
+        io_wait_input(P, s);
+        mass_apply(P, u_prev, an, s);
+    }
     P->an_ready = false;
     bool guess_in_place = false;  // x0 already written into u_next, r = b - A x0
     if (used_guess) *used_guess = 0;
@@ -371,8 +400,9 @@ int cn_prepare(tfde_problem* P, const double* u_prev, const double* F, const dou
         double* gp = nullptr;   // device coefficients of the corrected guess
         if (P->guess_order >= 3 && P->hist >= 2) {
             gp = P->red_out + kMrSlot + 5;
-            mr_guess_coefficients(P, an, F, b, r, gp, s);
+            mr_guess_coefficients(P, an, F, b, r, gp, s);   // reads no u: overlaps a host copy of u
         }
+        io_wait_input(P, s);
         launch_cn_chain_extrap(P->N, an, F, P->p.dt, b, r, u_next, P->H[0][0], P->H[0][1], P->H[1][0], P->H[1][1],
                                gp ? 3 : std::min(order, 2), gp, P->red, P->red_out + kNormsSlot, s);
         std::swap(P->H[0][0], P->H[1][0]);
@@ -381,15 +411,18 @@ int cn_prepare(tfde_problem* P, const double* u_prev, const double* F, const dou
         guess_in_place = true;
     } else if (chained) {
         if (guess) P->hist = 0;
+        io_wait_input(P, s);
         launch_cn_chain(P->N, an, F, P->p.dt, b, r, P->red, P->red_out + kNormsSlot, s);
     } else {
         P->hist = 0;
+        io_wait_input(P, s);
         double* ku = P->w[tfde_problem::W_Q];
         st = mixed_prec ? accurate_apply(P, TFDE_OP_STIFF, u_prev, ku, s) : apply_A64(P, TFDE_OP_STIFF, u_prev, ku, s);
         if (st) return st;
         launch_cn_first(P->N, an, ku, F, P->p.dt, b, r, P->red, P->red_out + kNormsSlot, s);
     }
     const double* start = guess_is_prev ? u_prev : x0;
+    io_wait_input(P, s);
     if (!guess_in_place && start != u_next)
         TFDE_CUDA_TRY(cudaMemcpyAsync(u_next, start, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     *r_given = guess_is_prev;  // r = b - A x0 is the residual of the initial guess

@@ -76,7 +76,7 @@ _lib = None
 EXPORTS = ["tfde_assemble", "tfde_destroy", "tfde_matvec", "tfde_precond", "tfde_pcg", "tfde_pgmres",
            "tfde_cn_step", "tfde_cn_advance", "tfde_set_guess_order", "tfde_source_example2", "tfde_coefficients", "tfde_host_coefficients",
            "tfde_stats_reset", "tfde_stats_get", "tfde_mass_apply_noalloc", "tfde_batch_create", "tfde_batch_destroy",
-           "tfde_batch_count", "tfde_batch_set_guess_order", "tfde_batch_set_spectral_inner", "tfde_batch_graph_cycles", "tfde_batch_set_symmetric_pcg", "tfde_batch_pcg_solves", "tfde_batch_pcg_graph_launches", "tfde_batch_cn_advance", "tfde_cn_advance_guess", "tfde_cnn_create", "tfde_cnn_destroy",
+           "tfde_batch_count", "tfde_batch_set_guess_order", "tfde_batch_set_spectral_inner", "tfde_batch_graph_cycles", "tfde_batch_set_symmetric_pcg", "tfde_batch_pcg_solves", "tfde_batch_pcg_graph_launches", "tfde_batch_cn_advance", "tfde_cn_advance_host", "tfde_cn_advance_guess", "tfde_cnn_create", "tfde_cnn_destroy",
            "tfde_cnn_set_params", "tfde_cnn_get_params", "tfde_cnn_get_grads", "tfde_cnn_predict", "tfde_cnn_accumulate", "tfde_cnn_predict_hist", "tfde_cnn_accumulate_hist",
            "tfde_cnn_adam_step", "tfde_selftest_wait", "tfde_set_device_loop", "tfde_device_loop_launches", "tfde_set_spectral_inner", "tfde_spectrum", "tfde_tune", "tfde_batch_tune",
            "tfde_tune_get", "tfde_tune_set", "tfde_tune_clear", "tfde_last_error", "tfde_version"]
@@ -102,6 +102,7 @@ def load(path: str | None = None):
         "tfde_pgmres": ([vp, vp, vp, c_int, c_double, c_int, POINTER(tfde_info), vp], c_int),
         "tfde_cn_step": ([vp, vp, vp, vp, vp, c_double, POINTER(tfde_info), vp], c_int),
         "tfde_cn_advance": ([vp, vp, vp, c_int, c_double, POINTER(tfde_info), vp], c_int),
+        "tfde_cn_advance_host": ([vp, vp, vp, vp, vp, c_int, c_double, POINTER(tfde_info), vp], c_int),
         "tfde_set_guess_order": ([vp, c_int], c_int),
         "tfde_source_example2": ([vp, c_double, c_double, vp, vp], c_int),
         "tfde_coefficients": ([vp, c_int, POINTER(c_double), POINTER(c_double), POINTER(c_double)], c_int),
@@ -432,6 +433,19 @@ def tfde_batch_cn_advance(batch: int, u_list, F_list, restart: bool, tol: float,
 
 
 CNN_PARAMS = 4 * (16 * 16 * 27 + 16)
+
+
+def tfde_cn_advance_host(prob: int, u_host_in, u_host_out, u, F_half, restart: bool, tol: float, stream=None,
+                         check: bool = True) -> tfde_info:
+    """tfde_cn_advance with the state copied from and to host tensors (CPU,
+    page-locked for the copies to overlap the step); u is the device state."""
+    info = tfde_info()
+    st = load().tfde_cn_advance_host(prob, _ptr(u_host_in), _ptr(u_host_out), _ptr(u), _ptr(F_half),
+                                     1 if restart else 0, tol, byref(info), _stream(stream))
+    if check:
+        _check(st, "tfde_cn_advance_host")
+    info.status = st
+    return info
 
 
 def tfde_cn_advance_guess(prob: int, u, F_half, x0, restart: bool, tol: float, stream=None,
