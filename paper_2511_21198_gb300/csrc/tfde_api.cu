@@ -215,6 +215,9 @@ int tfde_cn_advance_host(const tfde_problem* prob, const double* u_host_in, doub
             cudaEventCreateWithFlags(&io.ev_ready, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&io.ev_out, cudaEventDisableTiming) != cudaSuccess)
             return set_error(TFDE_ECUDA, "creation of the copy stream failed");
+        for (auto& e : io.ev_chunk)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+                return set_error(TFDE_ECUDA, "creation of the copy stream failed");
     }
     const size_t bytes = P->N * sizeof(double);
     io.in = u_host_in;
@@ -225,7 +228,18 @@ int tfde_cn_advance_host(const tfde_problem* prob, const double* u_host_in, doub
     // so far; the step waits for it only before its first read of u
     cudaEventRecord(io.ev_start, s);
     cudaStreamWaitEvent(io.stream, io.ev_start, 0);
-    cudaMemcpyAsync(u, u_host_in, bytes, cudaMemcpyHostToDevice, io.stream);
+    // large grids: in pieces, so that the right-hand-side and guess pass can
+    // start on each range as it arrives (an event per piece)
+    io.nchunks = P->N >= ((size_t)1 << 20) ? tfde_problem::HostIO::kChunks : 1;
+    const size_t per = (P->N + io.nchunks - 1) / io.nchunks;
+    for (int k = 0; k < io.nchunks; ++k) {
+        const size_t o = per * k;
+        if (o < P->N) {
+            const size_t len = P->N - o < per ? P->N - o : per;
+            cudaMemcpyAsync(u + o, u_host_in + o, len * sizeof(double), cudaMemcpyHostToDevice, io.stream);
+        }
+        cudaEventRecord(io.ev_chunk[k], io.stream);
+    }
     cudaEventRecord(io.ev_in, io.stream);
     io.in_pending = true;
     const bool chained = !restart && P->chain_ok && P->chain_u == u;
@@ -243,6 +257,7 @@ int tfde_cn_advance_host(const tfde_problem* prob, const double* u_host_in, doub
     io.out = nullptr;
     io.dev = nullptr;
     io.in_pending = io.out_pending = io.out_valid = false;
+    io.nchunks = 1;
     if (st == TFDE_OK && (e1 != cudaSuccess || e2 != cudaSuccess))
         st = set_error(TFDE_ECUDA, std::string("host copies: ") + cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
     if (st == TFDE_OK) {

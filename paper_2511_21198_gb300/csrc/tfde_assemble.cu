@@ -342,6 +342,8 @@ int destroy_problem(tfde_problem* P) {
     if (P->io.stream) cudaStreamDestroy(P->io.stream);
     for (cudaEvent_t e : {P->io.ev_start, P->io.ev_in, P->io.ev_ready, P->io.ev_out})
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : P->io.ev_chunk)
+        if (e) cudaEventDestroy(e);
     for (auto& v : P->w) cudaFree(v);
     cudaFree(P->V);
     for (auto& hk : P->H)

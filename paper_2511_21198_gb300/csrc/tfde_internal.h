@@ -89,6 +89,12 @@ void launch_cn_chain(size_t N, const double* AN, const double* F, double dt, dou
 void launch_cn_chain_extrap(size_t N, const double* AN, const double* F, double dt, double* b, double* r, double* u,
                             const double* U1, const double* AU1, double* U2, double* AU2, int order, const double* g,
                             double* part, double* norms2, cudaStream_t s);
+// the same in `nchunks` consecutive element ranges, range k after event ready[k]
+// (the ranges of a host copy of u arriving in pieces); the same norms
+void launch_cn_chain_extrap_chunks(size_t N, int nchunks, const cudaEvent_t* ready, const double* AN, const double* F,
+                                   double dt, double* b, double* r, double* u, const double* U1, const double* AU1,
+                                   double* U2, double* AU2, int order, const double* g, double* part, double* norms2,
+                                   cudaStream_t s);
 // the five sums of the minimal-residual correction of the order-2 guess into
 // out5 (device): <e1,e1>, <e1,e2>, <e2,e2>, <e1,r_e>, <e2,r_e> (see tfde_kernels64.cu)
 void launch_cn_mr_dots(size_t N, const double* AN, const double* F, double dt, const double* b, const double* r,
@@ -146,6 +152,9 @@ struct tfde_problem {
         double* dev = nullptr;
         cudaStream_t stream = nullptr;       // copy stream (per problem, created on first use)
         cudaEvent_t ev_start = nullptr, ev_in = nullptr, ev_ready = nullptr, ev_out = nullptr;
+        static constexpr int kChunks = 8;    // pieces of the input copy (large grids)
+        cudaEvent_t ev_chunk[kChunks] = {};  // piece k has arrived
+        int nchunks = 1;
         bool in_pending = false;             // the main stream has not yet waited for the input
         bool out_pending = false;            // an output copy may still read dev
         bool out_valid = false;              // the last output copy was issued after the last write of dev

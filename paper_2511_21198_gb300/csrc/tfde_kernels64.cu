@@ -437,7 +437,7 @@ __global__ void cn_chain_extrap_kernel(long long N, const double* __restrict__ A
                                        double* __restrict__ u, const double* __restrict__ U1,
                                        const double* __restrict__ AU1, double* __restrict__ U2,
                                        double* __restrict__ AU2, int order, const double* __restrict__ g,
-                                       double* __restrict__ part) {
+                                       double* __restrict__ part, long long pstride) {
     // GB300 issues FP64 at ~1/64 of its FP32 rate and this pass moves 112
     // bytes per point: it is FP64-bound unless every FP64 operation that is
     // not needed goes.  2 A_N u is formed by the exponent, dt F is fused into
@@ -483,7 +483,7 @@ __global__ void cn_chain_extrap_kernel(long long N, const double* __restrict__ A
         const double t2 = block_sum((double)rr);
         if (threadIdx.x == 0) {
             part[blockIdx.x] = t1;
-            part[gridDim.x + blockIdx.x] = t2;
+            part[pstride + blockIdx.x] = t2;   // ||r||^2 partials one row below (pstride >= gridDim.x)
         }
     }
 }
@@ -668,8 +668,35 @@ void launch_cn_chain_extrap(size_t N, const double* AN, const double* F, double 
     stats_count_launch();
     const int grid = grid_for((long long)N);
     cn_chain_extrap_kernel<<<grid, kThreads, 0, s>>>((long long)N, AN, F, dt, b, r, u, U1, AU1, U2, AU2,
-                                                     order >= 3 && !g ? 2 : order, g, norms2 ? part : nullptr);
+                                                     order >= 3 && !g ? 2 : order, g, norms2 ? part : nullptr, grid);
     finish_norms(part, grid, norms2, s);
+}
+
+void launch_cn_chain_extrap_chunks(size_t N, int nchunks, const cudaEvent_t* ready, const double* AN, const double* F,
+                                   double dt, double* b, double* r, double* u, const double* U1, const double* AU1,
+                                   double* U2, double* AU2, int order, const double* g, double* part, double* norms2,
+                                   cudaStream_t s) {
+    const size_t per = (N + nchunks - 1) / nchunks;
+    const int grid = grid_for((long long)per);
+    const long long pstride = (long long)grid * nchunks;
+    for (int k = 0; k < nchunks; ++k) {
+        const size_t o = per * k;
+        if (o >= N) {   // an empty tail chunk: zero partials, so the sums below stay right
+            if (norms2) {
+                cudaMemsetAsync(part + (size_t)k * grid, 0, grid * sizeof(double), s);
+                cudaMemsetAsync(part + pstride + (size_t)k * grid, 0, grid * sizeof(double), s);
+            }
+            continue;
+        }
+        const size_t len = N - o < per ? N - o : per;
+        cudaStreamWaitEvent(s, ready[k], 0);
+        stats_count_launch();
+        cn_chain_extrap_kernel<<<grid, kThreads, 0, s>>>((long long)len, AN + o, F ? F + o : nullptr, dt, b + o, r + o,
+                                                         u + o, U1 + o, AU1 + o, U2 + o, AU2 + o,
+                                                         order >= 3 && !g ? 2 : order, g,
+                                                         norms2 ? part + (size_t)k * grid : nullptr, pstride);
+    }
+    if (norms2) launch_reduce_finish(part, (int)pstride, 2, norms2, s);
 }
 
 void launch_cn_mr_dots(size_t N, const double* AN, const double* F, double dt, const double* b, const double* r,

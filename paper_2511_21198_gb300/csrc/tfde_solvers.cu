@@ -402,9 +402,17 @@ int cn_prepare(tfde_problem* P, const double* u_prev, const double* F, const dou
             gp = P->red_out + kMrSlot + 5;
             mr_guess_coefficients(P, an, F, b, r, gp, s);   // reads no u: overlaps a host copy of u
         }
-        io_wait_input(P, s);
-        launch_cn_chain_extrap(P->N, an, F, P->p.dt, b, r, u_next, P->H[0][0], P->H[0][1], P->H[1][0], P->H[1][1],
-                               gp ? 3 : std::min(order, 2), gp, P->red, P->red_out + kNormsSlot, s);
+        if (P->io.in_pending && P->io.nchunks > 1 && u_next == P->io.dev) {
+            // u arrives from the host in pieces: each range starts when its piece is in
+            launch_cn_chain_extrap_chunks(P->N, P->io.nchunks, P->io.ev_chunk, an, F, P->p.dt, b, r, u_next,
+                                          P->H[0][0], P->H[0][1], P->H[1][0], P->H[1][1],
+                                          gp ? 3 : std::min(order, 2), gp, P->red, P->red_out + kNormsSlot, s);
+            io_wait_input(P, s);
+        } else {
+            io_wait_input(P, s);
+            launch_cn_chain_extrap(P->N, an, F, P->p.dt, b, r, u_next, P->H[0][0], P->H[0][1], P->H[1][0],
+                                   P->H[1][1], gp ? 3 : std::min(order, 2), gp, P->red, P->red_out + kNormsSlot, s);
+        }
         std::swap(P->H[0][0], P->H[1][0]);
         std::swap(P->H[0][1], P->H[1][1]);
         P->hist = P->hist < 2 ? P->hist + 1 : 2;

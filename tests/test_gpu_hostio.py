@@ -29,6 +29,9 @@ CASES = [
     ("mixed_sym_order3", (24, 32, 40), (0.7, 0.6, 0.5), (1.0, 1.0, 1.0), (1.0, 1.0, 1.0), "MIXED", 3),
     ("mixed_nonsym", (32, 24, 16), (0.3, 0.6, 0.8), (1.0, 1.5, 0.5), (0.5, 1.0, 2.0), "MIXED", 0),
     ("fp64_sym", (16, 16, 24), (0.5, 0.5, 0.5), (1.0, 1.0, 1.0), (1.0, 1.0, 1.0), "FP64", 2),
+    # over 2^20 points: the input arrives in eight pieces and the right-hand-side
+    # and guess pass runs range by range as they come in
+    ("mixed_sym_order3_pieces", (96, 104, 112), (0.7, 0.7, 0.7), (1.0, 1.0, 1.0), (1.0, 1.0, 1.0), "MIXED", 3),
 ]
 
 
