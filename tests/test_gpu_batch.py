@@ -358,3 +358,29 @@ def test_batch_pcg_graph_and_host_loop_agree(T):
     for i, p in enumerate(probs):
         xo = oracle_step(p, u0[i], dt)
         assert relerr(runs[False][1][i], xo) < 1e-10 and relerr(runs[True][1][i], xo) < 1e-10, i
+
+
+def test_batch_extreme_axis_lengths_match_oracle(T):
+    """Axes of 448 points (the largest the tensor-core path takes: four row
+    halves per tile in the grouped exact contraction, the longest lines in
+    the grouped slicing) beside axes of 8, along every axis, symmetric and
+    non-symmetric problems in one batch: one step each against the oracle."""
+    probs = [
+        dict(n=(448, 8, 16), delta=(0.7, 0.3, 0.5), kp=(1.0, 1.0, 1.0), km=(1.0, 1.0, 1.0)),
+        dict(n=(16, 448, 8), delta=(0.4, 0.8, 0.6), kp=(1.5, 0.5, 1.0), km=(0.5, 1.5, 2.0)),
+        dict(n=(8, 16, 448), delta=(0.2, 0.6, 0.9), kp=(1.0, 2.0, 0.7), km=(1.0, 2.0, 0.7)),
+        dict(n=(8, 8, 8), delta=(0.5, 0.5, 0.5), kp=(1.0, 0.6, 1.2), km=(0.8, 1.1, 0.9)),
+    ]
+    dt = 0.05
+    params = [T.make_params(p["n"], p["delta"], p["kp"], p["km"], dt) for p in probs]
+    B = T.tfde_batch_create(params, 20)
+    try:
+        u0 = [inp.smoothed_uniform(tuple(reversed(p["n"])), 110 + i) for i, p in enumerate(probs)]
+        us = [to_dev(u) for u in u0]
+        infos = T.tfde_batch_cn_advance(B, us, None, True, 1e-12)
+        assert T.tfde_batch_pcg_solves(B) > 0 and T.tfde_batch_graph_cycles(B) > 0
+        for i, p in enumerate(probs):
+            assert infos[i].relres <= 1e-12 and infos[i].fallback == 0, (i, infos[i].relres)
+            assert relerr(to_host(us[i]), oracle_step(p, u0[i], dt)) < 1e-10, i
+    finally:
+        T.tfde_batch_destroy(B)
