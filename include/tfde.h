@@ -404,6 +404,14 @@ long long tfde_batch_pcg_solves(const tfde_batch* batch);
  * iterations ran as one graph launch; 0 for a NULL batch. */
 long long tfde_batch_pcg_graph_launches(const tfde_batch* batch);
 
+/* tfde_batch_grouped_prepares -- batched CN steps whose right-hand sides,
+ * corrected order-3 guesses and initial residuals (Eq. (linear_sys) on the
+ * chain) ran as grouped launches over all problems: the steady state of a
+ * chain in which every problem has its mass term from the previous step's
+ * exact residual and two history levels (else each problem prepares its own
+ * step).  0 for a NULL batch. */
+long long tfde_batch_grouped_prepares(const tfde_batch* batch);
+
 /*
  * tfde_batch_graph_cycles -- how many batched GMRES cycles (Sec. 3.2) so far
  * ran their Arnoldi steps as one CUDA-graph launch (a while node: the step

@@ -20,6 +20,7 @@
 #include "tfde_internal.h"
 #include "tfde_mixed.h"
 #include "tfde_stats.h"
+#include "tfde_chain.cuh"
 
 namespace tfde {
 
@@ -227,6 +228,69 @@ __device__ __forceinline__ void ksum4(KSum& k, float4 a, float4 b) {
     k.add(a.y * b.y);
     k.add(a.z * b.z);
     k.add(a.w * b.w);
+}
+
+// ---- the chained steps' right-hand sides and corrected guesses of every
+// problem at once (the per-point arithmetic of tfde_chain.cuh, as
+// cn_prepare's order-3 path): the five sums of the guess correction, their
+// 2 x 2 solve per problem, then b^m, x0 and r = b^m - A x0 with ||b||^2,
+// ||r||^2.  Per-problem pointers in a ChainDesc.
+struct ChainDesc {
+    const double* AN;
+    const double* F;
+    double* b;
+    double* r;
+    double* u;
+    const double* U1;
+    const double* AU1;
+    double* U2;
+    double* AU2;
+    double dt;
+};
+
+__global__ __launch_bounds__(kBT) void bkc_mr_dots(const ChainDesc* __restrict__ cd, const BVec* __restrict__ vt,
+                                                  const int* __restrict__ bi, const long long* __restrict__ bo,
+                                                  const int* __restrict__ act, double* __restrict__ part) {
+    BK_PROLOGUE
+    const ChainDesc& c = cd[inst];
+    const float dtf = (float)c.dt;
+    float s5[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (long long e = e0 + threadIdx.x; e < e1; e += kBT)
+        chain_mr_terms(__ldg(c.AN + e), c.F, e, dtf, __ldg(c.b + e), __ldg(c.r + e), __ldg(c.AU1 + e),
+                       __ldg(c.AU2 + e), s5);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const double t = block_sum((double)s5[q]);
+        if (threadIdx.x == 0) part[(long long)q * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+__global__ void bkc_coef(int C, const double* __restrict__ mr, double* __restrict__ g, const int* __restrict__ act) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < C && act[i]) chain_mr_coefficients(mr + (size_t)i * 8, g + (size_t)i * 4);
+}
+
+__global__ __launch_bounds__(kBT) void bkc_chain(const ChainDesc* __restrict__ cd, const BVec* __restrict__ vt,
+                                                const int* __restrict__ bi, const long long* __restrict__ bo,
+                                                const int* __restrict__ act, const double* __restrict__ g,
+                                                double* __restrict__ part) {
+    BK_PROLOGUE
+    const ChainDesc& c = cd[inst];
+    const double g0 = g[(size_t)inst * 4], g1 = g[(size_t)inst * 4 + 1], g2 = g[(size_t)inst * 4 + 2];
+    float bb = 0.f, rr = 0.f;
+    for (long long e = e0 + threadIdx.x; e < e1; e += kBT) {
+        double bn, rn;
+        chain_extrap_point(e, c.AN, c.F, c.dt, c.b, c.r, c.u, c.U1, c.AU1, c.U2, c.AU2, 3, g0, g1, g2, &bn, &rn);
+        const float bf = chain_f32(bn), rf = chain_f32(rn);
+        bb = fmaf(bf, bf, bb);
+        rr = fmaf(rf, rf, rr);
+    }
+    const double t1 = block_sum((double)bb);
+    const double t2 = block_sum((double)rr);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = t1;
+        part[(long long)gridDim.x + blockIdx.x] = t2;
+    }
 }
 
 // S_BB, S_RR of every problem from the norms its cn_prepare formed
@@ -724,7 +788,7 @@ struct tfde_batch {
     long long* d_bo = nullptr;
     int* d_bstart = nullptr;
     int NB = 0;
-    double* d_part = nullptr;       // (restart + 2) * NB partial sums
+    double* d_part = nullptr;       // max(restart + 2, 5) * NB partial sums
     double* d_h = nullptr;          // count * kHS
     double* d_s = nullptr;          // count * kSS
     double* h_s = nullptr;
@@ -754,6 +818,12 @@ struct tfde_batch {
     std::vector<double*> chain_u;
     std::vector<int*> own_err;      // each problem's own error flag while it reports to d_err
     tfde::OzBatch* oz = nullptr;    // the exact residuals as grouped launches
+    // the chained steps' right-hand sides as grouped launches
+    tfde::ChainDesc* d_chain = nullptr;
+    tfde::ChainDesc* h_chain = nullptr;
+    double* d_mr = nullptr;         // count * 8: the five correction sums per problem
+    double* d_g = nullptr;          // count * 4: the guess coefficients per problem
+    long long grouped_prepares = 0; // steps whose right-hand sides ran grouped
 };
 
 namespace tfde {
@@ -785,6 +855,10 @@ int free_batch(tfde_batch* B) {
         destroy_problem(B->P[i]);
     }
     tfde::oz_batch_destroy(B->oz);
+    cudaFree(B->d_chain);
+    if (B->h_chain) cudaFreeHost(B->h_chain);
+    cudaFree(B->d_mr);
+    cudaFree(B->d_g);
     cudaFree(B->d_sopzw);
     cudaFree(B->d_j);
     if (B->cyc_exec) cudaGraphExecDestroy(B->cyc_exec);
@@ -1400,7 +1474,7 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
         cudaMalloc((void**)&B->d_bi, bi.size() * sizeof(int)) != cudaSuccess ||
         cudaMalloc((void**)&B->d_bo, bo.size() * sizeof(long long)) != cudaSuccess ||
         cudaMalloc((void**)&B->d_bstart, bstart.size() * sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&B->d_part, (size_t)(restart + 2) * B->NB * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_part, (size_t)std::max(restart + 2, 5) * B->NB * sizeof(double)) != cudaSuccess ||
         cudaMalloc((void**)&B->d_h, C * kHS * sizeof(double)) != cudaSuccess ||
         cudaMalloc((void**)&B->d_s, C * kSS * sizeof(double)) != cudaSuccess ||
         cudaMallocHost((void**)&B->h_s, C * kSS * sizeof(double)) != cudaSuccess ||
@@ -1495,6 +1569,11 @@ int batch_create(const tfde_params* params, int count, int restart, cudaStream_t
     }
     if (cudaEventCreateWithFlags(&B->fork_ev, cudaEventDisableTiming) != cudaSuccess)
         return fail(TFDE_ECUDA, "event creation failed");
+    if (cudaMalloc((void**)&B->d_chain, C * sizeof(ChainDesc)) != cudaSuccess ||
+        cudaMallocHost((void**)&B->h_chain, C * sizeof(ChainDesc)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_mr, C * 8 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_g, C * 4 * sizeof(double)) != cudaSuccess)
+        return fail(TFDE_ENOMEM, "allocation of the batch workspace failed");
     {
         std::vector<double*> norm2(C);
         for (size_t i = 0; i < C; ++i) norm2[i] = B->d_s + i * kSS + S_RR;
@@ -1549,6 +1628,8 @@ extern "C" long long tfde_batch_pcg_solves(const tfde_batch* B) { return B ? B->
 
 extern "C" long long tfde_batch_pcg_graph_launches(const tfde_batch* B) { return B ? B->pcg_graph_launches : 0; }
 
+extern "C" long long tfde_batch_grouped_prepares(const tfde_batch* B) { return B ? B->grouped_prepares : 0; }
+
 extern "C" int tfde_batch_set_guess_order(tfde_batch* B, int order) {
     if (!B) return tfde::set_error(TFDE_EINVAL, "NULL batch");
     if (order < 0 || order > 3) return tfde::set_error(TFDE_EINVAL, "guess order must be 0, 1, 2 or 3");
@@ -1578,20 +1659,58 @@ int batch_cn_advance(tfde_batch* B, double* const* u, const double* const* F, in
     const bool chained = !restart_chain && B->chain_ok && B->chain_u == uu;
     B->chain_ok = false;
     B_TRY(cudaMemcpyAsync(B->d_vt, B->h_vt, C * sizeof(BVec), cudaMemcpyHostToDevice, s));
-    // right-hand sides and initial residuals (x0 = u^{m-1}), stream pool
-    fork(B, s);
-    for (int i = 0; i < C; ++i) {
-        bool rg = false;
-        if ((st = cn_prepare(B->P[i], uu[i], ff[i], nullptr, uu[i], B->aux[i % kStreams], chained, &rg, nullptr,
-                             nullptr))) {
-            join(B, s);
-            return st;
-        }
+    // right-hand sides and initial residuals.  In the steady state of a chain
+    // (every problem has A_N u^{m-1} from its last exact residual and two
+    // history levels for the order-3 guess) they run grouped over all
+    // problems; otherwise per problem (cn_prepare) on the stream pool
+    bool grouped_prep = chained;
+    for (int i = 0; i < C && grouped_prep; ++i) {
+        const tfde_problem* P = B->P[i];
+        grouped_prep = P->an_ready && P->guess_order >= 3 && P->hist >= 2;
     }
-    join(B, s);
-    // ||b||^2 and ||r_0||^2 as every cn_prepare formed them, into S_BB / S_RR
-    vec_launch_count();
-    bk_gather_norms<<<(C + 63) / 64, 64, 0, s>>>(C, B->d_vt, B->d_s);
+    if (grouped_prep) {
+        for (int i = 0; i < C; ++i) {
+            tfde_problem* P = B->P[i];
+            B->h_chain[i] = ChainDesc{P->w[tfde_problem::W_T], ff[i], P->w[tfde_problem::W_B], P->w[tfde_problem::W_R],
+                                      uu[i], P->H[0][0], P->H[0][1], P->H[1][0], P->H[1][1], P->p.dt};
+            B->h_act[i] = 1;
+        }
+        B_TRY(cudaMemcpyAsync(B->d_chain, B->h_chain, C * sizeof(ChainDesc), cudaMemcpyHostToDevice, s));
+        B_TRY(cudaMemcpyAsync(B->d_act, B->h_act, C * sizeof(int), cudaMemcpyHostToDevice, s));
+        const int gb = (C + 63) / 64;
+        vec_launch_count();
+        bkc_mr_dots<<<B->NB, kBT, 0, s>>>(B->d_chain, B->d_vt, B->d_bi, B->d_bo, B->d_act, B->d_part);
+        vec_launch_count();
+        bk_reduce<<<dim3((unsigned)C, 5u), 32, 0, s>>>(B->d_part, B->NB, B->d_bstart, B->d_act, 0, B->d_mr, 8, 0);
+        vec_launch_count();
+        bkc_coef<<<gb, 64, 0, s>>>(C, B->d_mr, B->d_g, B->d_act);
+        vec_launch_count();
+        bkc_chain<<<B->NB, kBT, 0, s>>>(B->d_chain, B->d_vt, B->d_bi, B->d_bo, B->d_act, B->d_g, B->d_part);
+        vec_launch_count();
+        bk_reduce<<<dim3((unsigned)C, 2u), 32, 0, s>>>(B->d_part, B->NB, B->d_bstart, B->d_act, 0, B->d_s, kSS, S_BB);
+        for (int i = 0; i < C; ++i) {   // as cn_prepare: the mass term is used up, the history moves on
+            tfde_problem* P = B->P[i];
+            P->an_ready = false;
+            std::swap(P->H[0][0], P->H[1][0]);
+            std::swap(P->H[0][1], P->H[1][1]);
+            P->hist = 2;
+        }
+        ++B->grouped_prepares;
+    } else {
+        fork(B, s);
+        for (int i = 0; i < C; ++i) {
+            bool rg = false;
+            if ((st = cn_prepare(B->P[i], uu[i], ff[i], nullptr, uu[i], B->aux[i % kStreams], chained, &rg, nullptr,
+                                 nullptr))) {
+                join(B, s);
+                return st;
+            }
+        }
+        join(B, s);
+        // ||b||^2 and ||r_0||^2 as every cn_prepare formed them, into S_BB / S_RR
+        vec_launch_count();
+        bk_gather_norms<<<(C + 63) / 64, 64, 0, s>>>(C, B->d_vt, B->d_s);
+    }
     if ((st = read_back(B, s))) return st;
     std::vector<double> nb(C), nr(C), ratio(C, 1.0), theta(C), est(C);
     std::vector<int> its(C), stall(C, 0), done(C, 0), outer(C, 0);

@@ -4,6 +4,7 @@
 // deterministic reductions shared by both precisions.
 #include "tfde_internal.h"
 #include "tfde_pow2conv.cuh"
+#include "tfde_chain.cuh"
 #include "tfde_stats.h"
 
 namespace tfde {
@@ -414,13 +415,6 @@ __global__ void cn_chain_kernel(long long N, const double* __restrict__ AN, cons
     }
 }
 
-// 2 v by the exponent field (exact; zero, subnormal, huge and non-finite
-// values take the FP64 add)
-__device__ __forceinline__ double twice(double v) {
-    const long long bits = __double_as_longlong(v);
-    const unsigned e = (unsigned)(bits >> 52) & 0x7FFu;
-    return (e != 0u && e < 0x7FEu) ? __longlong_as_double(bits + (1LL << 52)) : v + v;
-}
 
 // Chained CN step with a polynomial-extrapolation initial guess.  In: u =
 // u^{m-1}, AN = A_N u^{m-1}, (b, r) = the previous step's RHS and final true
@@ -452,27 +446,8 @@ __global__ void cn_chain_extrap_kernel(long long N, const double* __restrict__ A
         g2 = g[2];
     }
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const double ui = u[i];
-        const double au = b[i] - r[i];
-        const double an2 = twice(AN[i]);
-        const double bn = (F ? fma(dt, F[i], an2) : an2) - au;
-        double x = ui, ax = au;
-        if (order == 1) {
-            x = fma(2.0, ui, -U1[i]);
-            ax = fma(2.0, au, -AU1[i]);
-        } else if (order == 2) {
-            x = fma(3.0, ui - U1[i], U2[i]);
-            ax = fma(3.0, au - AU1[i], AU2[i]);
-        } else if (order >= 3) {
-            x = fma(g0, ui, fma(g1, U1[i], g2 * U2[i]));
-            ax = fma(g0, au, fma(g1, AU1[i], g2 * AU2[i]));
-        }
-        const double rn = bn - ax;
-        b[i] = bn;
-        r[i] = rn;
-        u[i] = x;
-        U2[i] = ui;
-        AU2[i] = au;
+        double bn, rn;
+        chain_extrap_point(i, AN, F, dt, b, r, u, U1, AU1, U2, AU2, order, g0, g1, g2, &bn, &rn);
         const float bf = f64_to_f32_rz((unsigned long long)__double_as_longlong(bn));
         const float rf = f64_to_f32_rz((unsigned long long)__double_as_longlong(rn));
         bb = fmaf(bf, bf, bb);
@@ -505,21 +480,9 @@ __global__ void cn_mr_dots_kernel(long long N, const double* __restrict__ AN, co
                                   const double* __restrict__ b, const double* __restrict__ r,
                                   const double* __restrict__ AU1, const double* __restrict__ AU2,
                                   double* __restrict__ part) {
-    auto cv = [](const double* p, long long i) {
-        return f64_to_f32_rz((unsigned long long)__double_as_longlong(__ldg(p + i)));
-    };
     float s[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const float a0 = cv(b, i) - cv(r, i), a1 = cv(AU1, i), a2 = cv(AU2, i);
-        const float bn = fmaf(2.f, cv(AN, i), F ? dtf * cv(F, i) : 0.f) - a0;
-        const float e1 = a0 - a1, e2 = e1 - (a1 - a2);
-        const float re = bn - fmaf(3.f, e1, a2);
-        s[0] = fmaf(e1, e1, s[0]);
-        s[1] = fmaf(e1, e2, s[1]);
-        s[2] = fmaf(e2, e2, s[2]);
-        s[3] = fmaf(e1, re, s[3]);
-        s[4] = fmaf(e2, re, s[4]);
-    }
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        chain_mr_terms(__ldg(AN + i), F, i, dtf, __ldg(b + i), __ldg(r + i), __ldg(AU1 + i), __ldg(AU2 + i), s);
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         const double t = block_sum((double)s[q]);
@@ -533,20 +496,7 @@ __global__ void cn_mr_dots_kernel(long long N, const double* __restrict__ AN, co
 // d2 = u^{m-1} - 2 u^{m-2} + u^{m-3}), c solving the 2 x 2 normal equations
 // [m0 m1; m1 m2] c = [m3; m4].  An ill-conditioned or non-finite system, or
 // |c| > 1e3, leaves c = 0.
-__global__ void cn_mr_coef_kernel(const double* __restrict__ m, double* __restrict__ g) {
-    double c1 = 0.0, c2 = 0.0;
-    bool ok = true;
-    for (int q = 0; q < 5; ++q) ok = ok && isfinite(m[q]);
-    const double det = m[0] * m[2] - m[1] * m[1];
-    if (ok && m[0] > 0.0 && m[2] > 0.0 && det > 1e-12 * m[0] * m[2]) {
-        c1 = (m[2] * m[3] - m[1] * m[4]) / det;
-        c2 = (m[0] * m[4] - m[1] * m[3]) / det;
-        if (!isfinite(c1) || !isfinite(c2) || fabs(c1) > 1e3 || fabs(c2) > 1e3) c1 = c2 = 0.0;
-    }
-    g[0] = 3.0 + c1 + c2;
-    g[1] = -3.0 - c1 - 2.0 * c2;
-    g[2] = 1.0 + c2;
-}
+__global__ void cn_mr_coef_kernel(const double* __restrict__ m, double* __restrict__ g) { chain_mr_coefficients(m, g); }
 
 inline int grid_for(long long N) {
     long long g = (N + kThreads - 1) / kThreads;

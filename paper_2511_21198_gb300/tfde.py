@@ -76,7 +76,7 @@ _lib = None
 EXPORTS = ["tfde_assemble", "tfde_destroy", "tfde_matvec", "tfde_precond", "tfde_pcg", "tfde_pgmres",
            "tfde_cn_step", "tfde_cn_advance", "tfde_set_guess_order", "tfde_source_example2", "tfde_coefficients", "tfde_host_coefficients",
            "tfde_stats_reset", "tfde_stats_get", "tfde_mass_apply_noalloc", "tfde_batch_create", "tfde_batch_destroy",
-           "tfde_batch_count", "tfde_batch_set_guess_order", "tfde_batch_set_spectral_inner", "tfde_batch_graph_cycles", "tfde_batch_set_symmetric_pcg", "tfde_batch_pcg_solves", "tfde_batch_pcg_graph_launches", "tfde_batch_cn_advance", "tfde_cn_advance_host", "tfde_cn_advance_guess", "tfde_cnn_create", "tfde_cnn_destroy",
+           "tfde_batch_count", "tfde_batch_set_guess_order", "tfde_batch_set_spectral_inner", "tfde_batch_graph_cycles", "tfde_batch_set_symmetric_pcg", "tfde_batch_pcg_solves", "tfde_batch_pcg_graph_launches", "tfde_batch_grouped_prepares", "tfde_batch_cn_advance", "tfde_cn_advance_host", "tfde_cn_advance_guess", "tfde_cnn_create", "tfde_cnn_destroy",
            "tfde_cnn_set_params", "tfde_cnn_get_params", "tfde_cnn_get_grads", "tfde_cnn_predict", "tfde_cnn_accumulate", "tfde_cnn_predict_hist", "tfde_cnn_accumulate_hist",
            "tfde_cnn_adam_step", "tfde_selftest_wait", "tfde_set_device_loop", "tfde_device_loop_launches", "tfde_set_spectral_inner", "tfde_spectrum", "tfde_tune", "tfde_batch_tune",
            "tfde_tune_get", "tfde_tune_set", "tfde_tune_clear", "tfde_last_error", "tfde_version"]
@@ -137,6 +137,7 @@ def load(path: str | None = None):
         "tfde_batch_set_symmetric_pcg": ([vp, c_int], c_int),
         "tfde_batch_pcg_solves": ([vp], c_longlong),
         "tfde_batch_pcg_graph_launches": ([vp], c_longlong),
+        "tfde_batch_grouped_prepares": ([vp], c_longlong),
         "tfde_spectrum": ([POINTER(tfde_params), c_int, vp, POINTER(tfde_spectrum_info), vp], c_int),
         "tfde_tune": ([vp, c_int, vp], c_int),
         "tfde_batch_tune": ([vp, c_int, vp], c_int),
@@ -326,6 +327,10 @@ def tfde_batch_pcg_solves(batch: int) -> int:
 
 def tfde_batch_pcg_graph_launches(batch: int) -> int:
     return int(load().tfde_batch_pcg_graph_launches(batch))
+
+
+def tfde_batch_grouped_prepares(batch: int) -> int:
+    return int(load().tfde_batch_grouped_prepares(batch))
 
 
 def tfde_set_spectral_inner(prob: int, enable: bool) -> None:

@@ -136,6 +136,9 @@ def test_batch_guess_order_same_trajectory(T):
         for a, b in zip(ua, ub):
             assert relerr(to_host(a), to_host(b)) < 1e-10
         assert it3 < it0
+        # once every problem has two history levels and its mass term, the
+        # right-hand sides and guesses run grouped (order 0 never does)
+        assert T.tfde_batch_grouped_prepares(B3) >= 3 and T.tfde_batch_grouped_prepares(B0) == 0
         with pytest.raises(T.TfdeError):
             T.tfde_batch_set_guess_order(B3, 4)
     finally:
@@ -384,3 +387,37 @@ def test_batch_extreme_axis_lengths_match_oracle(T):
             assert relerr(to_host(us[i]), oracle_step(p, u0[i], dt)) < 1e-10, i
     finally:
         T.tfde_batch_destroy(B)
+
+
+def test_batch_grouped_prepare_matches_single_problem_steps(T):
+    """Six chained steps with the order-3 guess and a source on one problem:
+    the batch (whose right-hand sides and guesses run grouped once the
+    history is built) and the single-problem mixed path reach the same
+    trajectories at tight residuals."""
+    probs = small_batch(4, 41, sizes=(16, 24, 32))
+    probs[1]["km"] = probs[1]["kp"]
+    dt = 0.05
+    params = [T.make_params(p["n"], p["delta"], p["kp"], p["km"], dt) for p in probs]
+    B = T.tfde_batch_create(params, 20)
+    singles = [T.tfde_assemble(pp, T.TFDE_MIXED) for pp in params]
+    try:
+        T.tfde_batch_set_guess_order(B, 3)
+        for h in singles:
+            T.tfde_set_guess_order(h, 3)
+        u0 = [inp.smoothed_uniform(tuple(reversed(p["n"])), 120 + i) for i, p in enumerate(probs)]
+        ub = [to_dev(u) for u in u0]
+        us = [to_dev(u) for u in u0]
+        Fs = [None] * len(probs)
+        Fs[2] = to_dev(inp.uniform_vector(tuple(reversed(probs[2]["n"])), 9))
+        for m in range(6):
+            infos = T.tfde_batch_cn_advance(B, ub, Fs, m == 0, 1e-12)
+            for i in range(len(probs)):
+                assert T.tfde_cn_advance(singles[i], us[i], Fs[i], m == 0, 1e-12).relres <= 1e-12
+                assert infos[i].relres <= 1e-12 and infos[i].fallback == 0, (m, i)
+        assert T.tfde_batch_grouped_prepares(B) >= 2
+        for i in range(len(probs)):
+            assert relerr(to_host(ub[i]), to_host(us[i])) < 1e-10, i
+    finally:
+        T.tfde_batch_destroy(B)
+        for h in singles:
+            T.tfde_destroy(h)
