@@ -99,6 +99,9 @@ void launch_cn_chain_extrap_chunks(size_t N, int nchunks, const cudaEvent_t* rea
 // out5 (device): <e1,e1>, <e1,e2>, <e2,e2>, <e1,r_e>, <e2,r_e> (see tfde_kernels64.cu)
 void launch_cn_mr_dots(size_t N, const double* AN, const double* F, double dt, const double* b, const double* r,
                        const double* AU1, const double* AU2, double* part, double* out5, cudaStream_t s);
+// H0 = u, AH0 = AN + Ku: the guess history's first level at a chain's restart
+void launch_history_first(size_t N, const double* u, const double* AN, const double* Ku, double* H0, double* AH0,
+                          cudaStream_t s);
 // g3[0..2] = coefficients of the corrected guess from the five sums m5 (device, one thread)
 void launch_cn_mr_coefficients(const double* m5, double* g3, cudaStream_t s);
 // F = cP PPP + cS (SPP + PSP + PPS) from 1-D arrays [Px|Py|Pz|Sx|Sy|Sz]

@@ -657,6 +657,22 @@ void launch_cn_mr_dots(size_t N, const double* AN, const double* F, double dt, c
     launch_reduce_finish(part, grid, 5, out5, s);
 }
 
+// The first level of the guess history at a chain's restart: H0 = u,
+// AH0 = A u = A_N u + K u (the two products the restart step has formed).
+__global__ void history_first_kernel(long long N, const double* __restrict__ u, const double* __restrict__ AN,
+                                     const double* __restrict__ Ku, double* __restrict__ H0, double* __restrict__ AH0) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        H0[i] = u[i];
+        AH0[i] = AN[i] + Ku[i];
+    }
+}
+
+void launch_history_first(size_t N, const double* u, const double* AN, const double* Ku, double* H0, double* AH0,
+                          cudaStream_t s) {
+    stats_count_launch();
+    history_first_kernel<<<grid_for((long long)N), kThreads, 0, s>>>((long long)N, u, AN, Ku, H0, AH0);
+}
+
 void launch_cn_mr_coefficients(const double* m5, double* g3, cudaStream_t s) {
     stats_count_launch();
     cn_mr_coef_kernel<<<1, 1, 0, s>>>(m5, g3);

@@ -428,6 +428,12 @@ int cn_prepare(tfde_problem* P, const double* u_prev, const double* F, const dou
         st = mixed_prec ? accurate_apply(P, TFDE_OP_STIFF, u_prev, ku, s) : apply_A64(P, TFDE_OP_STIFF, u_prev, ku, s);
         if (st) return st;
         launch_cn_first(P->N, an, ku, F, P->p.dt, b, r, P->red, P->red_out + kNormsSlot, s);
+        if (P->guess_order > 0 && P->H[0][0] && P->H[0][1]) {
+            // the restart has A u^{m-1} = A_N u + K u at hand: it becomes the
+            // history's first level, so that the next chained step extrapolates
+            launch_history_first(P->N, u_prev, an, ku, P->H[0][0], P->H[0][1], s);
+            P->hist = 1;
+        }
     }
     const double* start = guess_is_prev ? u_prev : x0;
     io_wait_input(P, s);
