@@ -238,8 +238,10 @@ int tfde_cn_advance_guess(const tfde_problem* prob, double* u, const double* F_h
  *   coefficients do not follow
  *   the CN transient of the stiff modes, and at the n = 256 workload the
  *   correction lowers the initial residual ~40-fold).  The order in force is
- *   limited by the history the chain has built since its last restart (0 on
- *   the first step, at most 1 on the second; order 3 needs two levels).
+ *   limited by the history the chain has built since its last restart (the
+ *   restart step stores the first level from the products it forms anyway,
+ *   so the next step extrapolates at order 1 and the one after at up to
+ *   order 3).
  *   The guess changes only the iterations, not the stopping rule.
  *   Errors: TFDE_EINVAL for order outside 0..3 or a NULL problem.
  */
